@@ -1,0 +1,126 @@
+"""Plain FP64 CPU oracle of the super-resolution (SR) prolongation.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU-baseline leg, never by the product library.
+
+The paper replaces the multigrid prolongation by the generator of an SRGAN
+(Sec. 2.3 and Fig. 1b, after Ledig et al.; Sec. 3.1; Appendix A, Algorithm 5).
+The generator here is the one-channel, whole-grid variant:
+
+    G = conv3x3(1 -> 64) + PReLU
+        -> 8 x [ y = x + conv3x3(PReLU(conv3x3(x))) ]      (64 -> 64 each)
+        -> conv3x3(64 -> 256) -> pixel-shuffle x2 -> PReLU
+        -> conv3x3(64 -> 1)
+
+All convolutions are 3x3 cross-correlations with bias and circular padding
+(the error fields are periodic, so the windowing and stitching of Sec. 3.1
+becomes plain periodic convolution over the whole grid).  PReLU has one slope
+per channel.  Pixel-shuffle: out[c, 2y + dy, 2x + dx] = in[4c + 2dy + dx, y, x].
+
+SR prolongation of a coarse error e_c (Algorithm 5, with a linear scale in
+place of the symmetric-log normalisation of Algorithms 3-4):
+    s = max |e_c| (s = 1 when e_c = 0),
+    e_f = P_cubic e_c + s * G(e_c / s).
+
+Optional bf16 emulation rounds (round-to-nearest-even) the weights of every
+layer and the activations at the layer boundaries where the GPU path stores
+bf16 tensors, so that the two can be compared tightly.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .multigrid import prolong_cubic
+
+N_FEAT = 64
+N_BLOCKS = 8
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 value (ties to even), returned as float64.
+
+    bfloat16 keeps the top 16 bits of the IEEE binary32 pattern; rounding adds
+    0x7FFF plus the lowest kept bit before truncating.
+    """
+    f32 = np.asarray(a, dtype=np.float32)
+    bits = f32.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> np.uint64(16)) & np.uint64(1)
+    rounded = ((bits + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    out = (rounded & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
+    return out.astype(np.float64)
+
+
+def weight_shapes(n_feat: int = N_FEAT, n_blocks: int = N_BLOCKS):
+    """Ordered (name, shape) list of the generator's parameters."""
+    shapes = [("in.w", (n_feat, 1, 3, 3)), ("in.b", (n_feat,)), ("in.a", (n_feat,))]
+    for k in range(n_blocks):
+        shapes += [(f"b{k}.w1", (n_feat, n_feat, 3, 3)), (f"b{k}.b1", (n_feat,)),
+                   (f"b{k}.a", (n_feat,)),
+                   (f"b{k}.w2", (n_feat, n_feat, 3, 3)), (f"b{k}.b2", (n_feat,))]
+    shapes += [("up.w", (4 * n_feat, n_feat, 3, 3)), ("up.b", (4 * n_feat,)),
+               ("up.a", (n_feat,)),
+               ("out.w", (1, n_feat, 3, 3)), ("out.b", (1,))]
+    return shapes
+
+
+def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """out[o, y, x] = b[o] + sum_{c, ky, kx} w[o, c, ky, kx] in[c, y+ky-1, x+kx-1].
+
+    Indices wrap (circular padding).  Each of the nine taps is a shifted copy
+    of the input contracted over channels.
+    """
+    cout = w.shape[0]
+    out = np.broadcast_to(b[:, None, None], (cout,) + x.shape[1:]).astype(np.float64).copy()
+    for ky in range(3):
+        for kx in range(3):
+            shifted = np.roll(x, (1 - ky, 1 - kx), axis=(1, 2))
+            out += np.einsum("oc,chw->ohw", w[:, :, ky, kx], shifted)
+    return out
+
+
+def prelu(x: np.ndarray, a: np.ndarray) -> np.ndarray:
+    """y = x where x > 0, a_c x otherwise, one slope per channel."""
+    return np.where(x > 0, x, a[:, None, None] * x)
+
+
+def pixel_shuffle2(x: np.ndarray) -> np.ndarray:
+    """(4C, H, W) -> (C, 2H, 2W): out[c, 2y+dy, 2x+dx] = in[4c + 2dy + dx, y, x]."""
+    c4, H, W = x.shape
+    c = c4 // 4
+    out = np.empty((c, 2 * H, 2 * W))
+    for dy in range(2):
+        for dx in range(2):
+            out[:, dy::2, dx::2] = x[np.arange(c) * 4 + 2 * dy + dx]
+    return out
+
+
+def generator_forward(q: np.ndarray, weights: dict, n_blocks: int = N_BLOCKS,
+                      emulate_bf16: bool = False) -> np.ndarray:
+    """G(q) for a normalised coarse field q (H, W) -> fine field (2H, 2W)."""
+    rnd = bf16_round if emulate_bf16 else (lambda a: a)
+    W = {k: (rnd(v) if (emulate_bf16 and k.endswith(("w", "w1", "w2"))) else v)
+         for k, v in weights.items()}
+    x = q[None, :, :].astype(np.float64)
+    x = rnd(prelu(conv3x3(x, W["in.w"], W["in.b"]), W["in.a"]))
+    for k in range(n_blocks):
+        t = rnd(prelu(conv3x3(x, W[f"b{k}.w1"], W[f"b{k}.b1"]), W[f"b{k}.a"]))
+        x = rnd(x + conv3x3(t, W[f"b{k}.w2"], W[f"b{k}.b2"]))
+    u = conv3x3(x, W["up.w"], W["up.b"])
+    u = rnd(prelu(pixel_shuffle2(u), W["up.a"]))
+    return conv3x3(u, W["out.w"], W["out.b"])[0]
+
+
+def sr_scale(ec: np.ndarray) -> float:
+    """Input scale s = max |e_c|, or 1 for a zero field."""
+    s = float(np.max(np.abs(ec)))
+    return s if s > 0.0 else 1.0
+
+
+def sr_prolong(ec: np.ndarray, weights: dict, n_blocks: int = N_BLOCKS,
+               emulate_bf16: bool = False) -> np.ndarray:
+    """SR prolongation e_f = P_cubic e_c + s G(e_c / s)."""
+    s = sr_scale(ec)
+    q = ec / s
+    if emulate_bf16:
+        q = np.asarray(q, dtype=np.float32).astype(np.float64)
+    return prolong_cubic(ec) + s * generator_forward(q, weights, n_blocks, emulate_bf16)

@@ -1,0 +1,343 @@
+"""Pins of the FP64 multigrid oracle against closed forms, brute force,
+library routines and textbook values (no GPU).
+
+Every test here checks oracle/multigrid.py against something other than
+itself: Fourier-mode eigenvalues and symbols, a dense brute-force solve written
+point by point, numpy/LAPACK's pseudo-inverse, SciPy's periodic CubicSpline,
+invariants of the operators, and the textbook local-Fourier-analysis (LFA)
+two-grid factors of red-black Gauss-Seidel with full weighting.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import multigrid as mg
+from synthetic.sources import config_seed, turbulent_source
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _mode(n, kx, ky, phase=0.3):
+    h = mg.grid_h(n)
+    j = np.arange(n) * h
+    return np.cos(kx * j[None, :] + ky * j[:, None] + phase)
+
+
+def _rand_zero_mean(n, seed):
+    f = np.random.default_rng(seed).standard_normal((n, n))
+    return f - f.mean()
+
+
+# --------------------------------------------------------------------------
+# Operator and exact solution (Sec. 2.2, Eq. poissoneq)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,kx,ky", [(8, 1, 0), (16, 3, 2), (32, 5, 7), (64, 16, 1)])
+def test_operator_on_fourier_modes(n, kx, ky):
+    """A cos(k.x) = lambda cos(k.x), lambda = (4/h^2)(sin^2(kx h/2) + sin^2(ky h/2))."""
+    h = mg.grid_h(n)
+    v = _mode(n, kx, ky)
+    lam = 4.0 / h**2 * (np.sin(kx * h / 2) ** 2 + np.sin(ky * h / 2) ** 2)
+    np.testing.assert_allclose(mg.apply_A(v, h), lam * v, atol=1e-11 * lam)
+
+
+def test_operator_continuum_limit():
+    """The discrete eigenvalue tends to |k|^2 (the symbol of -Lap) as h -> 0."""
+    n = 4096
+    h = mg.grid_h(n)
+    lam = mg.laplacian_eigenvalues(n, h)
+    assert abs(lam[3, 4] - 25.0) < 25.0 * 1e-5
+    assert lam[0, 0] == 0.0
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_exact_fft_equals_dense_and_pinv(n):
+    """FFT closed form == own bordered Gaussian elimination == LAPACK pinv."""
+    h = mg.grid_h(n)
+    f = _rand_zero_mean(n, n)
+    x_fft = mg.exact_solve_fft(f, h)
+    x_dense = mg.dense_solve(f, h)
+    A = mg.dense_operator(n, h)
+    x_pinv = (np.linalg.pinv(A) @ f.ravel()).reshape(n, n)
+    scale = np.abs(x_fft).max()
+    assert np.abs(x_fft - x_dense).max() <= 1e-12 * scale
+    assert np.abs(x_fft - x_pinv).max() <= 1e-12 * scale
+    assert abs(x_fft.mean()) <= 1e-14 * scale
+
+
+def test_dense_operator_matches_stencil():
+    n = 8
+    h = mg.grid_h(n)
+    x = np.random.default_rng(5).standard_normal((n, n))
+    A = mg.dense_operator(n, h)
+    np.testing.assert_allclose((A @ x.ravel()).reshape(n, n), mg.apply_A(x, h), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(A, A.T)
+    np.testing.assert_allclose(A @ np.ones(n * n), 0.0, atol=1e-12)
+
+
+def test_exact_solution_single_mode():
+    n = 32
+    h = mg.grid_h(n)
+    v = _mode(n, 3, 5)
+    lam = 4.0 / h**2 * (np.sin(3 * h / 2) ** 2 + np.sin(5 * h / 2) ** 2)
+    np.testing.assert_allclose(mg.exact_solve_fft(v, h), v / lam, atol=1e-14)
+
+
+def test_exact_solution_turbulent_source_residual():
+    n = 64
+    f = turbulent_source(n, 8, config_seed(0, 0))
+    x = mg.exact_solve_fft(f)
+    r = mg.residual(f, x, mg.grid_h(n))
+    assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(f)
+
+
+# --------------------------------------------------------------------------
+# Red-black Gauss-Seidel (Sec. 2.2; Algorithm 6 relaxation)
+# --------------------------------------------------------------------------
+
+def test_rbgs_half_sweeps_zero_their_colour_residual():
+    n = 16
+    h = mg.grid_h(n)
+    f = _rand_zero_mean(n, 1)
+    x = np.random.default_rng(2).standard_normal((n, n))
+    red = mg.red_mask(n)
+    assert red[0, 0] and not red[0, 1]
+    mg.rbgs_half_sweep(x, f, h, 0)
+    r = mg.residual(f, x, h)
+    assert np.abs(r[red]).max() <= 1e-12 * np.abs(f).max()
+    assert np.abs(r[~red]).max() > 1e-3
+    mg.rbgs_half_sweep(x, f, h, 1)
+    r = mg.residual(f, x, h)
+    assert np.abs(r[~red]).max() <= 1e-12 * np.abs(f).max()
+    assert np.abs(r[red]).max() > 1e-3
+
+
+def test_rbgs_equals_sequential_gauss_seidel_loop():
+    """Brute force: a point-by-point Gauss-Seidel loop over red then black points."""
+    n = 6
+    h = mg.grid_h(n)
+    f = _rand_zero_mean(n, 3)
+    x0 = np.random.default_rng(4).standard_normal((n, n))
+    x_loop = x0.copy()
+    for colour in (0, 1):
+        for i in range(n):
+            for j in range(n):
+                if (i + j) % 2 != colour:
+                    continue
+                s = (x_loop[(i - 1) % n, j] + x_loop[(i + 1) % n, j]
+                     + x_loop[i, (j - 1) % n] + x_loop[i, (j + 1) % n])
+                x_loop[i, j] = (h * h * f[i, j] + s) / 4.0
+    x_vec = x0.copy()
+    mg.rbgs(x_vec, f, h, 1)
+    np.testing.assert_allclose(x_vec, x_loop, rtol=0, atol=1e-14)
+
+
+def test_rbgs_fixed_point_is_exact_solution():
+    n = 8
+    h = mg.grid_h(n)
+    f = _rand_zero_mean(n, 7)
+    x = np.zeros((n, n))
+    mg.rbgs(x, f, h, 400)
+    x -= x.mean()
+    xe = mg.exact_solve_fft(f, h)
+    assert np.abs(x - xe).max() <= 1e-10 * np.abs(xe).max()
+
+
+# --------------------------------------------------------------------------
+# Full-weighting restriction
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,kx,ky", [(16, 1, 2), (32, 3, 7), (64, 15, 4)])
+def test_restriction_symbol(n, kx, ky):
+    """FW of cos(t1 j + t2 i) = cos^2(t1/2) cos^2(t2/2) cos(2 t1 J + 2 t2 I)."""
+    t1, t2 = 2 * np.pi * kx / n, 2 * np.pi * ky / n
+    i = np.arange(n)
+    r = np.cos(t1 * i[None, :] + t2 * i[:, None])
+    I = np.arange(n // 2)
+    expect = (np.cos(t1 / 2) ** 2 * np.cos(t2 / 2) ** 2
+              * np.cos(2 * t1 * I[None, :] + 2 * t2 * I[:, None]))
+    np.testing.assert_allclose(mg.restrict_fw(r), expect, atol=1e-14)
+
+
+def test_restriction_conserves_quarter_sum_and_constants():
+    r = np.random.default_rng(8).standard_normal((32, 32))
+    rc = mg.restrict_fw(r)
+    assert rc.shape == (16, 16)
+    assert abs(rc.sum() - r.sum() / 4) <= 1e-12
+    np.testing.assert_allclose(mg.restrict_fw(np.full((16, 16), 2.5)), 2.5, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Periodic cubic-spline prolongation (Sec. 2.2: bivariate spline)
+# --------------------------------------------------------------------------
+
+def test_spline_midpoints_match_scipy_periodic_cubicspline():
+    from scipy.interpolate import CubicSpline
+    for m in (8, 16, 33):
+        v = np.random.default_rng(m).standard_normal(m)
+        H = 2 * np.pi / m
+        t = np.arange(m + 1) * H
+        cs = CubicSpline(t, np.append(v, v[0]), bc_type="periodic")
+        mid = mg.spline_midpoints(v[:, None], H)[:, 0]
+        np.testing.assert_allclose(mid, cs(t[:-1] + H / 2), atol=1e-13)
+
+
+def test_prolong_cubic_matches_scipy_tensor_product():
+    from scipy.interpolate import CubicSpline
+    nc = 16
+    ec = np.random.default_rng(11).standard_normal((nc, nc))
+    H = 2 * np.pi / nc
+    t = np.arange(nc + 1) * H
+    tf = np.arange(2 * nc) * H / 2
+    rows = np.stack([CubicSpline(t, np.append(r, r[0]), bc_type="periodic")(tf) for r in ec])
+    cols = np.stack([CubicSpline(t, np.append(c, c[0]), bc_type="periodic")(tf)
+                     for c in rows.T], axis=1)
+    np.testing.assert_allclose(mg.prolong_cubic(ec), cols, atol=1e-13)
+
+
+@pytest.mark.parametrize("m,k", [(8, 1), (16, 3), (64, 20)])
+def test_spline_midpoint_symbol(m, k):
+    """Midpoint filter symbol from the B-spline form: G(w) = (1 + e^{iw})(11 + cos w) / (8 (2 + cos w))."""
+    w = 2 * np.pi * k / m
+    I = np.arange(m)
+    v = np.cos(w * I + 0.7)
+    G = (1 + np.exp(1j * w)) * (11 + np.cos(w)) / (8 * (2 + np.cos(w)))
+    expect = np.real(G * np.exp(1j * (w * I + 0.7)))
+    np.testing.assert_allclose(mg.spline_midpoints(v[:, None], 2 * np.pi / m)[:, 0], expect,
+                               atol=1e-14)
+
+
+def test_prolong_cubic_invariants():
+    ec = np.random.default_rng(12).standard_normal((8, 8))
+    p = mg.prolong_cubic(ec)
+    np.testing.assert_array_equal(p[0::2, 0::2], ec)  # exact at coarse nodes
+    np.testing.assert_allclose(mg.prolong_cubic(np.ones((8, 8))), 1.0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Coarsest solve and the V-cycle (Fig. 1a; Algorithm 6)
+# --------------------------------------------------------------------------
+
+def test_coarse_solve_is_pseudo_inverse():
+    h = mg.grid_h(8)
+    r = np.random.default_rng(13).standard_normal((8, 8)) + 0.25  # nonzero mean
+    e = mg.coarse_solve(r, h)
+    np.testing.assert_allclose(e, mg.exact_solve_fft(r - r.mean(), h), atol=1e-13)
+
+
+def _read_golden_lfa():
+    rows = []
+    with open(os.path.join(GOLDEN, "lfa_twogrid_rbgs_fw_bilinear.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                nu, rho = line.split()
+                rows.append((int(nu), float(rho)))
+    return rows
+
+
+def _lfa_twogrid(theta1, theta2, nu, prolong_kind):
+    """Two-grid error-propagation symbol on the 4 harmonics of (theta1, theta2).
+
+    Harmonic order: (0,0), (pi,pi), (pi,0), (0,pi).  Red/black masks couple a
+    frequency with its (pi,pi) shift; FW maps the 4 harmonics to one coarse
+    frequency; the prolongation's 1D symbol is (1 +- e^{-it} G(2t)) / 2.
+    The mesh width cancels and is taken as 1.
+    """
+    harm = [(0, 0), (1, 1), (1, 0), (0, 1)]
+    th = [(theta1 + a * np.pi, theta2 + b * np.pi) for a, b in harm]
+    lam = np.array([4 - 2 * np.cos(a) - 2 * np.cos(b) for a, b in th])
+
+    def half_sweep(colour):
+        M = np.zeros((4, 4), complex)
+        sg = 1.0 if colour == 0 else -1.0
+        for i, j in ((0, 1), (2, 3)):
+            s = (np.cos(th[i][0]) + np.cos(th[i][1])) / 2
+            M[i, i] = (1 + s) / 2
+            M[j, i] = sg * (s - 1) / 2
+            M[j, j] = (1 - s) / 2
+            M[i, j] = sg * (-s - 1) / 2
+        return M
+
+    S = half_sweep(1) @ half_sweep(0)
+    R = np.array([[(1 + np.cos(a)) * (1 + np.cos(b)) / 4 for a, b in th]])
+
+    def eG(t):  # e^{-it} G(2t), real for both interpolants
+        if prolong_kind == "linear":
+            return np.cos(t)
+        return 2 * np.cos(t) * (11 + np.cos(2 * t)) / (8 * (2 + np.cos(2 * t)))
+
+    p = lambda t, a: (1 + eG(t)) / 2 if a == 0 else (1 - eG(t)) / 2
+    P = np.array([[p(theta1, a) * p(theta2, b)] for a, b in harm])
+    Ac = (4 - 2 * np.cos(2 * theta1) - 2 * np.cos(2 * theta2)) / 4.0
+    K = np.eye(4) - P @ (R @ np.diag(lam)) / Ac
+    M = np.linalg.matrix_power(S, nu) @ K
+    return np.abs(np.linalg.eigvals(M)).max()
+
+
+def _lfa_max(n, nu, kind):
+    best = 0.0
+    for k1 in range(-n // 4, n // 4):
+        for k2 in range(-n // 4, n // 4):
+            if k1 or k2:
+                best = max(best, _lfa_twogrid(2 * np.pi * k1 / n, 2 * np.pi * k2 / n, nu, kind))
+    return best
+
+
+def test_lfa_symbol_reproduces_textbook_factors():
+    """The symbol computation gives the textbook rho_loc (pins the LFA code)."""
+    for nu, rho in _read_golden_lfa():
+        assert abs(_lfa_max(256, nu, "linear") - rho) <= 6e-4
+
+
+def _dense_twogrid_rho(n, nu1, nu2, prolong):
+    h = mg.grid_h(n)
+    N = n * n
+    M = np.zeros((N, N))
+    for p in range(N):
+        e = np.zeros(N)
+        e[p] = 1.0
+        M[:, p] = mg.vcycle(e.reshape(n, n), np.zeros((n, n)), h, nu1, nu2,
+                            coarsest=n // 2, prolong=prolong).ravel()
+    Q = np.eye(N) - 1.0 / N
+    return np.abs(np.linalg.eigvals(Q @ M @ Q)).max()
+
+
+@pytest.mark.parametrize("kind,nu1,nu2", [("linear", 1, 1), ("cubic", 2, 2)])
+def test_oracle_twogrid_matrix_matches_lfa(kind, nu1, nu2):
+    """Spectral radius of the oracle's explicit two-grid operator on a 16^2
+    periodic grid equals the LFA prediction on the same discrete frequencies
+    (LFA is exact for periodic problems)."""
+    prolong = mg.prolong_linear if kind == "linear" else mg.prolong_cubic
+    rho_dense = _dense_twogrid_rho(16, nu1, nu2, prolong)
+    rho_lfa = _lfa_max(16, nu1 + nu2, kind)
+    assert abs(rho_dense - rho_lfa) <= 1e-10
+
+
+def test_vcycle_solve_converges_to_exact_solution_64():
+    """64^2, 4 levels (64 -> 8), V(2,2), k <= 8 source, tol 1e-10."""
+    f = turbulent_source(64, 8, config_seed(0, 0))
+    x, info = mg.solve(f, tol=1e-10)
+    xe = mg.exact_solve_fft(f)
+    assert info["rel_residual"] <= 1e-10
+    assert info["cycles"] <= 10
+    assert np.abs(x - xe).max() <= 1e-9 * np.abs(xe).max()
+    h = info["history"]
+    # per-cycle factor within 2x of the V(2,2) two-grid LFA value (0.0216 with
+    # cubic prolongation): the recursive coarse solve is inexact, so the
+    # multilevel factor settles near 0.03
+    assert max(h[k + 1] / h[k] for k in range(len(h) - 1)) <= 0.04
+
+
+def test_solve_special_cases():
+    n = 32
+    x, info = mg.solve(np.zeros((n, n)))
+    assert info["cycles"] == 0 and not x.any()
+    v = _mode(n, 2, 3)
+    x, _ = mg.solve(v, tol=1e-12)
+    np.testing.assert_allclose(x, mg.exact_solve_fft(v), atol=1e-12)
+    f = _rand_zero_mean(n, 21) + 3.0  # nonzero mean is projected out
+    x, info = mg.solve(f, tol=1e-10)
+    np.testing.assert_allclose(x, mg.exact_solve_fft(f - f.mean()),
+                               atol=1e-9 * np.abs(x).max())
+    assert abs(x.mean()) < 1e-13
