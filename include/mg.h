@@ -1,0 +1,152 @@
+/*
+ * mg.h - C ABI of the GB300 multigrid library (libmg.so).
+ *
+ * Solves the 2D periodic pressure-Poisson problem of the paper (Sec. 2.2,
+ * Eq. poissoneq; Sec. 3.2, Eq. poisson_ns) on an N x N vertex grid,
+ * h = 2 pi / N, with the 5-point operator A = -Lap_h,
+ *     (A x)_ij = (4 x_ij - x_i+1,j - x_i-1,j - x_i,j+1 - x_i,j-1) / h^2,
+ * periodic in both axes.  A is singular (constants), so the library returns
+ * the zero-mean solution of the zero-mean part of f.
+ *
+ * Method: geometric multigrid V(nu_pre, nu_post) cycles (Fig. 1a; Appendix A,
+ * Algorithm 6): red-black Gauss-Seidel smoothing (red = (i + j) even first),
+ * residual, full-weighting restriction, recursion on the re-discretised
+ * operator, exact pseudo-inverse solve on the coarsest grid, and one of two
+ * coarse-to-fine prolongations (Sec. 2.2 and Sec. 3.1; Algorithm 5):
+ *   MG_PROLONG_CUBIC - the periodic tensor-product cubic interpolating spline;
+ *   MG_PROLONG_SR    - the cubic spline plus a learned super-resolution
+ *                      correction s * G(e_c / s), s = max|e_c|, from a
+ *                      convolutional generator (weights loaded separately).
+ *
+ * Precision: MG_PREC_FP64 runs plain FP64 V-cycles.  MG_PREC_MIXED runs FP32
+ * V-cycles as the inner solver of FP64 defect correction: r = f - A x in
+ * FP64, e ~ A^+ r by `inner_cycles` FP32 V-cycles from e = 0, x += e.
+ * Convergence is tested on ||f - A x||_2 / ||f||_2 in FP64 in both modes.
+ *
+ * Memory layout: every grid is row-major, N x N, contiguous, index i*N + j
+ * with j (x) the fast axis.  Pointers named "device or host" may point to
+ * device memory or to host memory; host buffers are staged through the
+ * context (copies on the context's stream, inside the call).
+ *
+ * Errors: every call returns an mg_status and never aborts the process.
+ * mg_last_error() gives a one-line description of the most recent failure
+ * on the calling thread.  Calls on one context are not thread-safe; distinct
+ * contexts may be used from distinct threads.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx; /* opaque: owns the level hierarchy and scratch */
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,   /* bad size, pointer or option */
+    MG_ERR_OOM = 2,           /* device allocation failed */
+    MG_ERR_CUDA = 3,          /* a CUDA runtime call failed; see mg_last_error() */
+    MG_ERR_NOT_CONVERGED = 4, /* max_cycles reached; x holds the last iterate */
+    MG_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    MG_ERR_NO_WEIGHTS = 6,    /* MG_PROLONG_SR requested with no weights loaded */
+    MG_ERR_BAD_WEIGHTS = 7,   /* weight blob malformed */
+    MG_ERR_NONFINITE = 8      /* f (or the iterate) holds NaN or Inf */
+} mg_status;
+
+typedef enum { MG_PROLONG_CUBIC = 0, MG_PROLONG_SR = 1 } mg_prolong;
+typedef enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 } mg_precision;
+
+typedef struct {
+    int outer_iters;      /* FP64 residual evaluations after the first */
+    int vcycles;          /* V-cycles run (FP32 in MIXED, FP64 in FP64) */
+    double rel_residual;  /* final ||f - A x||_2 / ||f||_2 (FP64) */
+    double removed_mean;  /* mean of f that was projected out */
+    double update_norm;   /* ||x_k - x_{k-1}||_2 of the last update */
+    double time_ms;       /* wall time of the call (host clock) */
+    int prolong_used;     /* mg_prolong actually applied */
+    int sr_fallback;      /* 1 if SR was replaced by cubic for this solve */
+} mg_solve_info;
+
+/* Create a context for N x N grids with `levels` levels (Fig. 1a hierarchy).
+ * N must be a power of two, 8 <= N <= 16384, and the coarsest grid
+ * N >> (levels - 1) must be 4, 8 or 16 (it is solved exactly).  Uses the
+ * current CUDA device.  *out is set to NULL on failure. */
+mg_status mg_setup(int levels, int N, mg_ctx **out);
+
+/* Options (defaults: MG_PREC_MIXED, nu_pre = nu_post = 2, max_cycles = 100,
+ * inner_cycles = 2, stream 0).  0 <= nu <= 4.  max_cycles bounds the V-cycles
+ * of one mg_solve.  `cuda_stream` is a cudaStream_t (NULL = legacy stream);
+ * all work of this context is ordered on it. */
+mg_status mg_set_options(mg_ctx *ctx, mg_precision precision, int nu_pre, int nu_post,
+                         int max_cycles, void *cuda_stream);
+mg_status mg_set_inner_cycles(mg_ctx *ctx, int inner_cycles);
+
+/* Load super-resolution generator weights (Sec. 2.3, Fig. 1b).  The blob is
+ * copied (the caller keeps ownership).  Blob layout: see mg_sr.h-style
+ * description in the library documentation: a 64-byte header
+ * {magic "MGSRW001", u32 n_feat, u32 n_blocks, u32 n_params, 44 bytes 0}
+ * followed by n_params little-endian float32 values in the order
+ * in.w, in.b, in.a, then per block w1, b1, a, w2, b2, then up.w, up.b, up.a,
+ * out.w, out.b (conv weights [out][in][3][3]).  n_feat must be 64.
+ * Returns MG_ERR_BAD_WEIGHTS on any mismatch. */
+mg_status mg_load_prolong_weights(mg_ctx *ctx, const void *blob, size_t bytes);
+
+/* Solve A x = f to ||f - A x||_2 / ||f||_2 <= tol.  f: N*N doubles (device or
+ * host), not modified.  x: N*N doubles (device or host), the initial guess on
+ * entry (warm start; zeros for a cold start) and the zero-mean solution on
+ * return.  info may be NULL.  Returns MG_ERR_NOT_CONVERGED (x = last iterate)
+ * if max_cycles V-cycles do not reach tol, MG_ERR_NONFINITE for NaN/Inf. */
+mg_status mg_solve(mg_ctx *ctx, const double *f, double *x, double tol, mg_prolong prolong,
+                   mg_solve_info *info);
+
+/* One V(nu_pre, nu_post) cycle on A x = f, in place (Algorithm 6).  FP64
+ * mode: one FP64 V-cycle on x.  MIXED mode: one defect-correction step with
+ * one FP32 V-cycle.  x is not projected to zero mean. */
+mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *x, mg_prolong prolong);
+
+/* Solve B independent problems, ctxs[k] with f[k], x[k] (device pointers),
+ * each to tol.  Contexts may have different N.  infos may be NULL. */
+mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
+                           double tol, mg_prolong prolong, mg_solve_info *infos);
+
+void mg_destroy(mg_ctx *ctx);
+const char *mg_status_string(mg_status status);
+const char *mg_last_error(void);
+
+/* ---------------------------------------------------------------------
+ * Operator-level entry points (device pointers only), for verification of
+ * each step against a reference.  dtype: 0 = double, 1 = float.  Grids use
+ * the scaled right-hand side b = h^2 * rhs, so that A x = rhs reads
+ * 4 x_ij - (sum of 4 neighbours) = b_ij.  Work is ordered on `stream`.
+ * ------------------------------------------------------------------- */
+
+/* Pre-smoothing and restriction (Algorithm 6 relax, residual, restrict):
+ * nu red-black sweeps on x (x treated as 0 on entry if zero_init), then
+ * bc = 4 * FW(b - (4x - sum nbrs)), the scaled coarse right-hand side on the
+ * n/2 grid.  n: power of two >= 16. */
+mg_status mg_op_down(int dtype, int n, void *x, const void *b, int nu, int zero_init, void *bc,
+                     void *stream);
+
+/* Correction and post-smoothing: x += P ec (P = periodic cubic spline,
+ * ec on the n/2 grid), then nu red-black sweeps with right-hand side b. */
+mg_status mg_op_up(int dtype, int n, void *x, const void *b, const void *ec, int nu, void *stream);
+
+/* V-cycles below the top: runs one V(nu1, nu2) cycle on the n x n problem
+ * 4x - sum = b (n <= 64, down to a coarsest grid of size `coarsest`),
+ * x = 0 on entry if zero_init. */
+mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, int nu1, int nu2,
+                       int zero_init, void *stream);
+
+/* FP64 outer residual: s = h^2 (f - mu) - (4x - sum nbrs) (so s = h^2 r),
+ * written as float to s32 when s32 != NULL; out[0] = sum s^2,
+ * out[1] = sum (f - mu)^2 (out: 2 doubles, device). */
+mg_status mg_op_outer_residual(int n, const double *f, const double *x, double mu, float *s32,
+                               double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

@@ -1,0 +1,617 @@
+// mg_api.cu - context, drivers and the C ABI declared in include/mg.h.
+//
+// The solve follows the V-cycle iteration of Algorithm 6 (Appendix A) with the
+// stopping rule on the relative residual.  MIXED precision wraps FP32
+// V-cycles in FP64 defect correction:
+//     s = h^2 (f - mean f) - (4x - sum nbrs)    (FP64, = h^2 r; ||r|| = ||s|| / h^2)
+//     if ||r|| / ||f - mean f|| <= tol: stop
+//     e = V^m(0; float(s))                      (m FP32 V-cycles, scaled rhs)
+//     x += e                                    (FP64)
+// and the result is projected to zero mean at the end.  The only host
+// synchronisation inside the loop is the read-back of the two residual sums.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+
+#include "mg_internal.cuh"
+#include "mg_sr.cuh"
+
+using namespace mg;
+
+static thread_local char g_err[512] = "";
+
+static void set_err(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+#define MG_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;               \
+        }                                                                                    \
+    } while (0)
+
+#define MG_TRY(expr)                    \
+    do {                                \
+        mg_status s_ = (expr);          \
+        if (s_ != MG_OK) return s_;     \
+    } while (0)
+
+namespace {
+
+constexpr int kMaxLevels = 16;
+constexpr size_t kAlign = 256;
+
+struct Level {
+    int n = 0;
+    float *x32 = nullptr, *b32 = nullptr;
+    double *x64 = nullptr, *b64 = nullptr;
+};
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Closed-form pseudo-inverse of the scaled periodic operator 4I - shifts on an
+// m x m grid: A~^+[p][q] = (1/m^2) sum_{k != 0} cos(2 pi k.(p - q) / m) / lam(k),
+// lam(k) = 4 sin^2(pi kx / m) + 4 sin^2(pi ky / m)  (Fourier eigen-decomposition).
+void coarse_pinv_host(int m, double *out) {
+    const int Nc = m * m;
+    const double PI = 3.14159265358979323846;
+    // kernel depends only on the difference (di, dj) mod m
+    double *kern = new double[Nc];
+    for (int di = 0; di < m; ++di)
+        for (int dj = 0; dj < m; ++dj) {
+            double acc = 0.0;
+            for (int ky = 0; ky < m; ++ky)
+                for (int kx = 0; kx < m; ++kx) {
+                    if (kx == 0 && ky == 0) continue;
+                    const double sx = sin(PI * kx / m), sy = sin(PI * ky / m);
+                    const double lam = 4.0 * (sx * sx + sy * sy);
+                    acc += cos(2.0 * PI * (double)(kx * dj + ky * di) / m) / lam;
+                }
+            kern[di * m + dj] = acc / Nc;
+        }
+    for (int pi = 0; pi < m; ++pi)
+        for (int pj = 0; pj < m; ++pj)
+            for (int qi = 0; qi < m; ++qi)
+                for (int qj = 0; qj < m; ++qj) {
+                    const int di = (pi - qi + m) % m, dj = (pj - qj + m) % m;
+                    out[(pi * m + pj) * Nc + qi * m + qj] = kern[di * m + dj];
+                }
+    delete[] kern;
+}
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct mg_ctx {
+    int N = 0, levels = 0, coarsest = 0, device = 0;
+    mg_precision prec = MG_PREC_MIXED;
+    int nu1 = 2, nu2 = 2, max_cycles = 100, inner = 2;
+    cudaStream_t stream = nullptr;
+    Level lv[kMaxLevels];
+    void *h32_block = nullptr, *h64_block = nullptr;
+    float *ainv32 = nullptr;
+    double *ainv64 = nullptr;
+    FirTaps taps;
+    // reductions: partials, counter, results [4 groups][kMaxSlots]
+    double *red_partials = nullptr;
+    unsigned *red_counter = nullptr;
+    double *red_out = nullptr;
+    double *host_out = nullptr;  // pinned mirror of red_out
+    double *f_stage = nullptr, *x_stage = nullptr;
+    SrState sr;
+
+    Reduction red(int group) const { return Reduction{red_partials, red_counter, red_out + group * kMaxSlots}; }
+    double *out(int group) const { return red_out + group * kMaxSlots; }
+};
+
+enum { kGrpF = 0, kGrpR = 1, kGrpU = 2, kGrpX = 3 };
+
+static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
+    void *&blk = fp64 ? c->h64_block : c->h32_block;
+    if (blk) return MG_OK;
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    size_t total = 0;
+    for (int l = 0; l < c->levels; ++l) {
+        const size_t nn = (size_t)c->lv[l].n * c->lv[l].n;
+        total += 2 * align_up(nn * es);
+    }
+    MG_CUDA(cudaMalloc(&blk, total));
+    MG_CUDA(cudaMemsetAsync(blk, 0, total, c->stream));
+    char *p = (char *)blk;
+    for (int l = 0; l < c->levels; ++l) {
+        const size_t nn = (size_t)c->lv[l].n * c->lv[l].n;
+        const size_t bytes = align_up(nn * es);
+        if (fp64) {
+            c->lv[l].x64 = (double *)p;
+            c->lv[l].b64 = (double *)(p + bytes);
+        } else {
+            c->lv[l].x32 = (float *)p;
+            c->lv[l].b32 = (float *)(p + bytes);
+        }
+        p += 2 * bytes;
+    }
+    return MG_OK;
+}
+
+template <typename T> static T *lvx(mg_ctx *c, int l);
+template <typename T> static T *lvb(mg_ctx *c, int l);
+template <> float *lvx<float>(mg_ctx *c, int l) { return c->lv[l].x32; }
+template <> float *lvb<float>(mg_ctx *c, int l) { return c->lv[l].b32; }
+template <> double *lvx<double>(mg_ctx *c, int l) { return c->lv[l].x64; }
+template <> double *lvb<double>(mg_ctx *c, int l) { return c->lv[l].b64; }
+template <typename T> static const T *ainv(mg_ctx *c);
+template <> const float *ainv<float>(mg_ctx *c) { return c->ainv32; }
+template <> const double *ainv<double>(mg_ctx *c) { return c->ainv64; }
+
+// One V(nu1, nu2) cycle on 4x - sum = b at level l (x = 0 on entry if zero).
+template <typename T>
+static mg_status vcycle_rec(mg_ctx *c, int l, T *x, const T *b, bool zero) {
+    const int n = c->lv[l].n;
+    if (n <= kBottomMax) {
+        MG_CUDA(launch_bottom<T>(x, b, n, c->coarsest, c->nu1, c->nu2, zero, ainv<T>(c), c->taps,
+                                 c->stream));
+        return MG_OK;
+    }
+    T *xc = lvx<T>(c, l + 1), *bc = lvb<T>(c, l + 1);
+    MG_CUDA(launch_down<T>(x, b, n, c->nu1, zero, bc, c->stream));
+    MG_TRY(vcycle_rec<T>(c, l + 1, xc, bc, true));
+    MG_CUDA(launch_up<T>(x, b, xc, n, c->nu2, c->taps, c->stream));
+    return MG_OK;
+}
+
+// Top-level FP32 V-cycle with the chosen prolongation at the finest transition.
+static mg_status vcycle32_top(mg_ctx *c, bool zero, mg_prolong prolong) {
+    float *x = c->lv[0].x32, *b = c->lv[0].b32;
+    if (prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax) {
+        float *xc = c->lv[1].x32, *bc = c->lv[1].b32;
+        MG_CUDA(launch_down<float>(x, b, c->lv[0].n, c->nu1, zero, bc, c->stream));
+        MG_TRY(vcycle_rec<float>(c, 1, xc, bc, true));
+        // generator correction s * G(e_c / s) on the fine grid, then the cubic
+        // part, the correction and the post-smoothing in one up pass
+        MG_TRY(sr_correction(&c->sr, xc, c->lv[1].n, c->stream, g_err, sizeof g_err));
+        MG_CUDA(launch_up<float>(x, b, xc, c->lv[0].n, c->nu2, c->taps, c->stream, c->sr.fine_out));
+        return MG_OK;
+    }
+    return vcycle_rec<float>(c, 0, x, b, zero);
+}
+
+static mg_status resolve_io(mg_ctx *c, const double *f, double *x, const double **fd, double **xd,
+                            bool *staged) {
+    const size_t bytes = (size_t)c->N * c->N * sizeof(double);
+    const bool fdev = is_device_pointer(f), xdev = is_device_pointer(x);
+    *staged = !xdev;
+    if (fdev && xdev) {
+        *fd = f;
+        *xd = x;
+        return MG_OK;
+    }
+    if (!c->f_stage) MG_CUDA(cudaMalloc(&c->f_stage, bytes));
+    if (!c->x_stage) MG_CUDA(cudaMalloc(&c->x_stage, bytes));
+    if (fdev) {
+        *fd = f;
+    } else {
+        MG_CUDA(cudaMemcpyAsync(c->f_stage, f, bytes, cudaMemcpyHostToDevice, c->stream));
+        *fd = c->f_stage;
+    }
+    if (xdev) {
+        *xd = x;
+    } else {
+        MG_CUDA(cudaMemcpyAsync(c->x_stage, x, bytes, cudaMemcpyHostToDevice, c->stream));
+        *xd = c->x_stage;
+    }
+    return MG_OK;
+}
+
+static mg_status check_common(mg_ctx *c, const double *f, double *x, mg_prolong prolong) {
+    if (!c || !f || !x) {
+        set_err("null context or pointer");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (prolong != MG_PROLONG_CUBIC && prolong != MG_PROLONG_SR) {
+        set_err("unknown prolongation %d", (int)prolong);
+        return MG_ERR_INVALID_ARG;
+    }
+    if (prolong == MG_PROLONG_SR) {
+        if (!c->sr.loaded) {
+            set_err("SR prolongation requested but no generator weights are loaded");
+            return MG_ERR_NO_WEIGHTS;
+        }
+        if (c->prec != MG_PREC_MIXED) {
+            set_err("SR prolongation runs inside the FP32 V-cycle (MG_PREC_MIXED only)");
+            return MG_ERR_INVALID_ARG;
+        }
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    return MG_OK;
+}
+
+extern "C" {
+
+const char *mg_status_string(mg_status s) {
+    switch (s) {
+        case MG_OK: return "MG_OK";
+        case MG_ERR_INVALID_ARG: return "MG_ERR_INVALID_ARG";
+        case MG_ERR_OOM: return "MG_ERR_OOM";
+        case MG_ERR_CUDA: return "MG_ERR_CUDA";
+        case MG_ERR_NOT_CONVERGED: return "MG_ERR_NOT_CONVERGED";
+        case MG_ERR_TIMEOUT: return "MG_ERR_TIMEOUT";
+        case MG_ERR_NO_WEIGHTS: return "MG_ERR_NO_WEIGHTS";
+        case MG_ERR_BAD_WEIGHTS: return "MG_ERR_BAD_WEIGHTS";
+        case MG_ERR_NONFINITE: return "MG_ERR_NONFINITE";
+    }
+    return "MG_ERR_UNKNOWN";
+}
+
+const char *mg_last_error(void) { return g_err; }
+
+void mg_destroy(mg_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->h32_block);
+    cudaFree(c->h64_block);
+    cudaFree(c->ainv32);
+    cudaFree(c->ainv64);
+    cudaFree(c->red_partials);
+    cudaFree(c->red_counter);
+    cudaFree(c->red_out);
+    cudaFreeHost(c->host_out);
+    cudaFree(c->f_stage);
+    cudaFree(c->x_stage);
+    sr_free(&c->sr);
+    delete c;
+}
+
+mg_status mg_setup(int levels, int N, mg_ctx **out) {
+    if (!out) {
+        set_err("out is NULL");
+        return MG_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!is_pow2(N) || N < 8 || N > 16384 || levels < 1 || levels > kMaxLevels) {
+        set_err("N=%d must be a power of two in [8, 16384], levels=%d in [1, %d]", N, levels, kMaxLevels);
+        return MG_ERR_INVALID_ARG;
+    }
+    const int coarsest = N >> (levels - 1);
+    if (coarsest < 4 || coarsest > 16 || (coarsest << (levels - 1)) != N) {
+        set_err("coarsest grid N >> (levels-1) = %d must be 4, 8 or 16", coarsest);
+        return MG_ERR_INVALID_ARG;
+    }
+    mg_ctx *c = new (std::nothrow) mg_ctx();
+    if (!c) return MG_ERR_OOM;
+    c->N = N;
+    c->levels = levels;
+    c->coarsest = coarsest;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        set_err("no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+        delete c;
+        return MG_ERR_CUDA;
+    }
+    for (int l = 0; l < levels; ++l) c->lv[l].n = N >> l;
+    fir_taps_host(&c->taps);
+    auto fail = [&](mg_status s) {
+        mg_destroy(c);
+        return s;
+    };
+    const int Nc = coarsest * coarsest;
+    double *h = new double[(size_t)Nc * Nc];
+    float *hf = new float[(size_t)Nc * Nc];
+    coarse_pinv_host(coarsest, h);
+    for (int i = 0; i < Nc * Nc; ++i) hf[i] = (float)h[i];
+    cudaError_t e = cudaMalloc(&c->ainv64, sizeof(double) * Nc * Nc);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ainv32, sizeof(float) * Nc * Nc);
+    if (e == cudaSuccess) e = cudaMemcpy(c->ainv64, h, sizeof(double) * Nc * Nc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->ainv32, hf, sizeof(float) * Nc * Nc, cudaMemcpyHostToDevice);
+    delete[] h;
+    delete[] hf;
+    if (e == cudaSuccess) e = cudaMalloc(&c->red_partials, sizeof(double) * kMaxSlots * kRedBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->red_counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->red_counter, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(double) * 4 * kMaxSlots);
+    if (e == cudaSuccess) e = cudaMemset(c->red_out, 0, sizeof(double) * 4 * kMaxSlots);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_out, sizeof(double) * 4 * kMaxSlots);
+    if (e != cudaSuccess) {
+        set_err("mg_setup: %s", cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA);
+    }
+    *out = c;
+    return MG_OK;
+}
+
+mg_status mg_set_options(mg_ctx *c, mg_precision prec, int nu_pre, int nu_post, int max_cycles,
+                         void *stream) {
+    if (!c || (prec != MG_PREC_FP64 && prec != MG_PREC_MIXED) || nu_pre < 0 || nu_pre > 4 ||
+        nu_post < 0 || nu_post > 4 || max_cycles < 1) {
+        set_err("invalid options (precision %d, nu %d/%d, max_cycles %d)", (int)prec, nu_pre, nu_post,
+                max_cycles);
+        return MG_ERR_INVALID_ARG;
+    }
+    c->prec = prec;
+    c->nu1 = nu_pre;
+    c->nu2 = nu_post;
+    c->max_cycles = max_cycles;
+    c->stream = (cudaStream_t)stream;
+    return MG_OK;
+}
+
+mg_status mg_set_inner_cycles(mg_ctx *c, int inner) {
+    if (!c || inner < 1 || inner > 16) {
+        set_err("inner_cycles must be in [1, 16]");
+        return MG_ERR_INVALID_ARG;
+    }
+    c->inner = inner;
+    return MG_OK;
+}
+
+mg_status mg_load_prolong_weights(mg_ctx *c, const void *blob, size_t bytes) {
+    if (!c || !blob) {
+        set_err("null context or blob");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    return sr_load(&c->sr, blob, bytes, g_err, sizeof g_err);
+}
+
+mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong prolong,
+                   mg_solve_info *info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    MG_TRY(check_common(c, f, x, prolong));
+    if (!(tol >= 0.0)) {
+        set_err("tol must be >= 0");
+        return MG_ERR_INVALID_ARG;
+    }
+    const bool mixed = c->prec == MG_PREC_MIXED;
+    MG_TRY(ensure_hierarchy(c, !mixed));
+    const double *fd;
+    double *xd;
+    bool staged;
+    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged));
+    const int N = c->N;
+    const double N2 = (double)N * N;
+    const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
+    cudaStream_t s = c->stream;
+
+    MG_CUDA(launch_source_sum(fd, N, c->red(kGrpF), s));
+    if (!mixed) MG_CUDA(launch_scaled_rhs(fd, N, h2, c->out(kGrpF), c->lv[0].b64, s));
+
+    mg_status st = MG_OK;
+    int cycles = 0, outer = 0;
+    double fnorm = 0.0, rel = INFINITY, mu = 0.0;
+    bool have_xsum = false, first = true;
+    for (;;) {
+        MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
+                                      first, c->red(kGrpR), s));
+        MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 2 * kMaxSlots,
+                                cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaStreamSynchronize(s));
+        if (first) {
+            mu = c->host_out[kGrpF * kMaxSlots] / N2;
+            fnorm = sqrt(c->host_out[kGrpR * kMaxSlots + 1]);
+            first = false;
+        }
+        const double rnorm = sqrt(c->host_out[kGrpR * kMaxSlots]) / h2;
+        if (!isfinite(rnorm) || !isfinite(fnorm)) {
+            set_err("non-finite residual (NaN or Inf in f or x)");
+            st = MG_ERR_NONFINITE;
+            break;
+        }
+        if (fnorm == 0.0) {  // constant source: the zero-mean solution is 0
+            MG_CUDA(cudaMemsetAsync(xd, 0, sizeof(double) * N * N, s));
+            rel = 0.0;
+            have_xsum = false;
+            break;
+        }
+        rel = rnorm / fnorm;
+        if (rel <= tol) break;
+        if (cycles >= c->max_cycles) {
+            set_err("not converged: rel residual %.3e after %d V-cycles", rel, cycles);
+            st = MG_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (mixed) {
+            for (int k = 0; k < c->inner && cycles < c->max_cycles; ++k, ++cycles)
+                MG_TRY(vcycle32_top(c, k == 0, prolong));
+            MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
+            have_xsum = true;
+        } else {
+            MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].b64, false));
+            ++cycles;
+            have_xsum = false;
+        }
+        ++outer;
+    }
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
+        const double *xsum = c->out(kGrpU) + 1;
+        if (!have_xsum) {
+            MG_CUDA(launch_sum(xd, N, c->red(kGrpX), s));
+            xsum = c->out(kGrpX);
+        }
+        MG_CUDA(launch_project(xd, N, xsum, s));
+    }
+    if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 4 * kMaxSlots,
+                            cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        info->outer_iters = outer;
+        info->vcycles = cycles;
+        info->rel_residual = rel;
+        info->removed_mean = mu;
+        info->update_norm = mixed && outer > 0 ? sqrt(c->host_out[kGrpU * kMaxSlots]) : 0.0;
+        info->prolong_used = (int)prolong;
+        info->sr_fallback = 0;
+        info->time_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return st;
+}
+
+mg_status mg_vcycle(mg_ctx *c, const double *f, double *x, mg_prolong prolong) {
+    MG_TRY(check_common(c, f, x, prolong));
+    const bool mixed = c->prec == MG_PREC_MIXED;
+    MG_TRY(ensure_hierarchy(c, !mixed));
+    const double *fd;
+    double *xd;
+    bool staged;
+    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged));
+    const int N = c->N;
+    const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
+    cudaStream_t s = c->stream;
+    MG_CUDA(launch_source_sum(fd, N, c->red(kGrpF), s));
+    if (mixed) {
+        MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, c->lv[0].b32, false,
+                                      c->red(kGrpR), s));
+        MG_TRY(vcycle32_top(c, true, prolong));
+        MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
+    } else {
+        MG_CUDA(launch_scaled_rhs(fd, N, h2, c->out(kGrpF), c->lv[0].b64, s));
+        MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].b64, false));
+    }
+    if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
+                           double tol, mg_prolong prolong, mg_solve_info *infos) {
+    if (!ctxs || !f || !x || B < 0) {
+        set_err("null batch arrays");
+        return MG_ERR_INVALID_ARG;
+    }
+    mg_status worst = MG_OK;
+    for (int k = 0; k < B; ++k) {
+        mg_status s = mg_solve(ctxs[k], f[k], x[k], tol, prolong, infos ? &infos[k] : nullptr);
+        if (s != MG_OK && worst == MG_OK) worst = s;
+        if (s != MG_OK && s != MG_ERR_NOT_CONVERGED) return s;
+    }
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
+// Operator-level entry points
+// ---------------------------------------------------------------------------
+static mg_status op_check(int dtype, int n, int min_n) {
+    if ((dtype != 0 && dtype != 1) || !is_pow2(n) || n < min_n || n > 16384) {
+        set_err("invalid dtype %d or size %d", dtype, n);
+        return MG_ERR_INVALID_ARG;
+    }
+    return MG_OK;
+}
+
+mg_status mg_op_down(int dtype, int n, void *x, const void *b, int nu, int zero_init, void *bc,
+                     void *stream) {
+    MG_TRY(op_check(dtype, n, 64));
+    if (!x || !b || !bc || nu < 0 || nu > 4) {
+        set_err("invalid arguments");
+        return MG_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == 0)
+        MG_CUDA(launch_down<double>((double *)x, (const double *)b, n, nu, zero_init != 0, (double *)bc, s));
+    else
+        MG_CUDA(launch_down<float>((float *)x, (const float *)b, n, nu, zero_init != 0, (float *)bc, s));
+    return MG_OK;
+}
+
+mg_status mg_op_up(int dtype, int n, void *x, const void *b, const void *ec, int nu, void *stream) {
+    MG_TRY(op_check(dtype, n, 64));
+    if (!x || !b || !ec || nu < 0 || nu > 4) {
+        set_err("invalid arguments");
+        return MG_ERR_INVALID_ARG;
+    }
+    FirTaps taps;
+    fir_taps_host(&taps);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == 0)
+        MG_CUDA(launch_up<double>((double *)x, (const double *)b, (const double *)ec, n, nu, taps, s));
+    else
+        MG_CUDA(launch_up<float>((float *)x, (const float *)b, (const float *)ec, n, nu, taps, s));
+    return MG_OK;
+}
+
+mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, int nu1, int nu2,
+                       int zero_init, void *stream) {
+    MG_TRY(op_check(dtype, n, 4));
+    if (n > kBottomMax || !is_pow2(coarsest) || coarsest < 4 || coarsest > 16 || coarsest > n ||
+        !x || !b || nu1 < 0 || nu1 > 4 || nu2 < 0 || nu2 > 4) {
+        set_err("invalid arguments (n <= %d, coarsest 4..16)", kBottomMax);
+        return MG_ERR_INVALID_ARG;
+    }
+    const int Nc = coarsest * coarsest;
+    double *h = new double[(size_t)Nc * Nc];
+    coarse_pinv_host(coarsest, h);
+    void *d = nullptr;
+    const size_t es = dtype == 0 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaMalloc(&d, es * Nc * Nc);
+    if (e == cudaSuccess) {
+        if (dtype == 0) {
+            e = cudaMemcpy(d, h, es * Nc * Nc, cudaMemcpyHostToDevice);
+        } else {
+            float *hf = new float[(size_t)Nc * Nc];
+            for (int i = 0; i < Nc * Nc; ++i) hf[i] = (float)h[i];
+            e = cudaMemcpy(d, hf, es * Nc * Nc, cudaMemcpyHostToDevice);
+            delete[] hf;
+        }
+    }
+    delete[] h;
+    FirTaps taps;
+    fir_taps_host(&taps);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e == cudaSuccess) {
+        if (dtype == 0)
+            e = launch_bottom<double>((double *)x, (const double *)b, n, coarsest, nu1, nu2, zero_init != 0,
+                                      (const double *)d, taps, s);
+        else
+            e = launch_bottom<float>((float *)x, (const float *)b, n, coarsest, nu1, nu2, zero_init != 0,
+                                     (const float *)d, taps, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    MG_CUDA(e);
+    return MG_OK;
+}
+
+mg_status mg_op_outer_residual(int n, const double *f, const double *x, double mu, float *s32,
+                               double *out, void *stream) {
+    MG_TRY(op_check(0, n, 4));
+    if (!f || !x || !out) {
+        set_err("invalid arguments");
+        return MG_ERR_INVALID_ARG;
+    }
+    double *partials = nullptr;
+    unsigned *counter = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc(&partials, sizeof(double) * kMaxSlots * kRedBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    const double h = 2.0 * 3.14159265358979323846 / n;
+    if (e == cudaSuccess)
+        e = launch_outer_residual(f, x, n, h * h, nullptr, mu, s32, true, Reduction{partials, counter, out}, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(partials);
+    cudaFree(counter);
+    MG_CUDA(e);
+    return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// mg_internal.cuh - shared definitions of the multigrid kernels and host driver.
+//
+// Conventions (all kernels): grids are row-major n x n, n a power of two,
+// index i*n + j.  Right-hand sides are stored scaled, b = h^2 * rhs, so one
+// Gauss-Seidel update reads x <- (b + sum of 4 neighbours) / 4 and the scaled
+// residual is s = b - (4x - sum) = h^2 r.  Restriction of s to the n/2 grid
+// yields the next scaled right-hand side directly: b_c = 4 * FW(s) because
+// h_c^2 = 4 h^2.  The inner V-cycle therefore carries no mesh width at all.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mg.h"
+
+namespace mg {
+
+// ----------------------------------------------------------------------------
+// Periodic cubic-spline midpoint filter (Sec. 2.2, "bivariate spline").
+//
+// For a periodic line v, the interpolating cubic spline's value halfway
+// between nodes I and I+1 is sum_k g_k (v[I+k] + v[I+1-k]), k = 1, 2, ...
+// From the B-spline form of the spline (prefilter 6 / (z + 4 + 1/z), midpoint
+// weights (1, 23, 23, 1) / 48) the symbol of the midpoint filter is
+//   G(w) = (1 + e^{iw}) (11 + cos w) / (8 (2 + cos w)),
+// whose taps are g_1 = (10 - 3 sqrt 3) / 8 and g_k = 3 sqrt3 a^{k-1} (1 + a) / 8
+// for k >= 2, with a = sqrt 3 - 2 (|a| = 0.268).  The taps decay
+// geometrically; truncating after L taps leaves an error below
+// 0.13 * 0.268^(L-2) of the largest coarse value: L = 14 (1.8e-8) is below
+// float rounding and L = 28 (9e-17) below double rounding.
+// ----------------------------------------------------------------------------
+constexpr int kFirF32 = 14;
+constexpr int kFirF64 = 28;
+
+struct FirTaps {
+    double d[kFirF64];  // g_1 .. g_L in double
+    float f[kFirF64];   // the same, rounded to float (first kFirF32 used)
+};
+
+void fir_taps_host(FirTaps *t);  // fills the closed-form taps
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+    static constexpr int L = kFirF32;
+    using vec = float4;
+    static constexpr int VW = 4;
+    static __device__ __forceinline__ float tap(const FirTaps &t, int k) { return t.f[k - 1]; }
+};
+template <> struct Prec<double> {
+    static constexpr int L = kFirF64;
+    using vec = double2;
+    static constexpr int VW = 2;
+    static __device__ __forceinline__ double tap(const FirTaps &t, int k) { return t.d[k - 1]; }
+};
+
+// ----------------------------------------------------------------------------
+// Deterministic two-stage reductions: each block writes one partial (fixed
+// order inside the block), the last block to finish sums the partials in
+// index order and resets the arrival counter.  `nslot` independent sums.
+// ----------------------------------------------------------------------------
+constexpr int kRedBlocks = 304;  // 2 blocks per SM on 152 SMs
+constexpr int kRedThreads = 256;
+constexpr int kMaxSlots = 4;
+
+struct Reduction {
+    double *partials;   // [kMaxSlots][kRedBlocks]
+    unsigned *counter;  // 1 arrival counter
+    double *out;        // [kMaxSlots] final sums
+};
+
+// sum over the block; result valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) s += sh[w];
+    }
+    return s;
+}
+
+// Store this block's partials (thread 0 holds vals) and let the last block
+// finish the reduction.  Must be called by all threads of the block.
+template <int NS>
+__device__ __forceinline__ void reduce_finish(const Reduction &red, const double (&vals)[NS],
+                                              double *sh) {
+    __shared__ bool am_last;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NS; ++k) red.partials[k * kRedBlocks + blockIdx.x] = vals[k];
+        __threadfence();
+        const unsigned ticket = atomicAdd(red.counter, 1u);
+        am_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    for (int k = 0; k < NS; ++k) {
+        double v = 0.0;
+        // fixed assignment of partials to threads, then a fixed-order tree
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+            v += ((volatile double *)red.partials)[k * kRedBlocks + i];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) red.out[k] = v;
+    }
+    if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+// ----------------------------------------------------------------------------
+// Host-side launchers (defined in mg_kernels.cu); all return cudaError_t.
+// ----------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_down(T *x, const T *b, int n, int nu, bool zero_init, T *bc, cudaStream_t s);
+// x += P ec (+ extra, a fine-grid additive correction, when not null), then nu sweeps
+template <typename T>
+cudaError_t launch_up(T *x, const T *b, const T *ec, int n, int nu, const FirTaps &taps,
+                      cudaStream_t s, const T *extra = nullptr);
+template <typename T>
+cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool zero_init,
+                          const T *ainv, const FirTaps &taps, cudaStream_t s);
+constexpr int kBottomMax = 64;  // grids up to 64 x 64 run the bottom kernel
+
+cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
+cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,
+                              double *b, cudaStream_t s);
+cudaError_t launch_outer_residual(const double *f, const double *x, int n, double h2,
+                                  const double *mu_sum, double mu_host, float *s32,
+                                  bool want_fnorm, Reduction red, cudaStream_t s);
+cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaStream_t s);
+cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s);
+cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s);
+
+}  // namespace mg

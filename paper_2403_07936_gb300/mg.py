@@ -1,0 +1,225 @@
+"""ctypes binding of libmg.so (include/mg.h): argument marshalling only.
+
+Every step of the solve runs inside the CUDA library.  Arrays may be torch
+tensors (CUDA or CPU) or numpy arrays; they must be C-contiguous with the
+dtype the call expects.  Importing this module does not need a GPU; loading
+the library does need the built libmg.so and fails loudly without it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmg.so")
+
+MG_OK = 0
+STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR_CUDA",
+                4: "MG_ERR_NOT_CONVERGED", 5: "MG_ERR_TIMEOUT", 6: "MG_ERR_NO_WEIGHTS",
+                7: "MG_ERR_BAD_WEIGHTS", 8: "MG_ERR_NONFINITE"}
+PROLONG = {"cubic": 0, "sr": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+# every exported symbol and its signature (restype, argtypes)
+_VP, _I, _D, _SZ = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("outer_iters", C.c_int), ("vcycles", C.c_int), ("rel_residual", C.c_double),
+                ("removed_mean", C.c_double), ("update_norm", C.c_double), ("time_ms", C.c_double),
+                ("prolong_used", C.c_int), ("sr_fallback", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SIGNATURES = {
+    "mg_setup": (_I, [_I, _I, C.POINTER(_VP)]),
+    "mg_set_options": (_I, [_VP, _I, _I, _I, _I, _VP]),
+    "mg_set_inner_cycles": (_I, [_VP, _I]),
+    "mg_load_prolong_weights": (_I, [_VP, _VP, _SZ]),
+    "mg_solve": (_I, [_VP, _VP, _VP, _D, _I, C.POINTER(SolveInfo)]),
+    "mg_vcycle": (_I, [_VP, _VP, _VP, _I]),
+    "mg_solve_batched": (_I, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _I, _D, _I,
+                              C.POINTER(SolveInfo)]),
+    "mg_destroy": (None, [_VP]),
+    "mg_status_string": (C.c_char_p, [_I]),
+    "mg_last_error": (C.c_char_p, []),
+    "mg_op_down": (_I, [_I, _I, _VP, _VP, _I, _I, _VP, _VP]),
+    "mg_op_up": (_I, [_I, _I, _VP, _VP, _VP, _I, _VP]),
+    "mg_op_vcycle": (_I, [_I, _I, _I, _VP, _VP, _I, _I, _I, _VP]),
+    "mg_op_outer_residual": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP]),
+}
+
+_lib = None
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libmg.so once.  Raises if the library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_2403_07936_gb300.build.build() "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != MG_OK:
+        raise MGError(status, load().mg_last_error().decode(errors="replace"))
+
+
+def ptr(a) -> int:
+    """Raw address of a contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def stream_handle(stream) -> int | None:
+    """cudaStream_t of a torch.cuda.Stream (or an int handle, or None)."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(a) -> int:
+    name = str(a.dtype)
+    if "float64" in name:
+        return 0
+    if "float32" in name:
+        return 1
+    raise TypeError(f"dtype {a.dtype} not supported (float64 or float32)")
+
+
+@dataclass
+class Options:
+    precision: str = "mixed"
+    nu_pre: int = 2
+    nu_post: int = 2
+    max_cycles: int = 100
+    inner_cycles: int = 2
+
+
+class Context:
+    """A solver context for N x N grids with `levels` levels (mg_setup)."""
+
+    def __init__(self, levels: int, N: int, **opts):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.mg_setup(levels, N, C.byref(h)))
+        self._h = h
+        self.N = N
+        self.levels = levels
+        self.options = Options()
+        self._stream = None
+        if opts:
+            self.set_options(**opts)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_options(self, precision=None, nu_pre=None, nu_post=None, max_cycles=None,
+                    inner_cycles=None, stream="keep"):
+        o = self.options
+        if precision is not None:
+            o.precision = precision
+        if nu_pre is not None:
+            o.nu_pre = nu_pre
+        if nu_post is not None:
+            o.nu_post = nu_post
+        if max_cycles is not None:
+            o.max_cycles = max_cycles
+        if stream != "keep":
+            self._stream = stream_handle(stream)
+        lib = load()
+        _check(lib.mg_set_options(self._h, PRECISION[o.precision], o.nu_pre, o.nu_post,
+                                  o.max_cycles, self._stream))
+        if inner_cycles is not None:
+            o.inner_cycles = inner_cycles
+            _check(lib.mg_set_inner_cycles(self._h, inner_cycles))
+
+    def load_weights(self, blob: bytes):
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _check(load().mg_load_prolong_weights(self._h, C.cast(buf, C.c_void_p), len(blob)))
+
+    def solve(self, f, x, tol: float = 1e-10, prolong: str = "cubic", check: bool = True) -> dict:
+        info = SolveInfo()
+        st = load().mg_solve(self._h, ptr(f), ptr(x), tol, PROLONG[prolong], C.byref(info))
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES.get(st, st)
+        if check and st != MG_OK:
+            _check(st)
+        return d
+
+    def vcycle(self, f, x, prolong: str = "cubic"):
+        _check(load().mg_vcycle(self._h, ptr(f), ptr(x), PROLONG[prolong]))
+
+    def close(self):
+        if self._h:
+            load().mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(ctxs, fs, xs, tol: float = 1e-10, prolong: str = "cubic"):
+    B = len(ctxs)
+    H = (C.c_void_p * B)(*[c.handle for c in ctxs])
+    F = (C.c_void_p * B)(*[ptr(f) for f in fs])
+    X = (C.c_void_p * B)(*[ptr(x) for x in xs])
+    infos = (SolveInfo * B)()
+    st = load().mg_solve_batched(H, F, X, B, tol, PROLONG[prolong], infos)
+    _check(st)
+    return [i.as_dict() for i in infos]
+
+
+# ---- operator-level calls (device arrays) --------------------------------
+
+def op_down(x, b, bc, nu: int, zero_init: bool = False, stream=None):
+    _check(load().mg_op_down(_dtype_code(x), x.shape[-1], ptr(x), ptr(b), nu, int(zero_init),
+                             ptr(bc), stream_handle(stream)))
+
+
+def op_up(x, b, ec, nu: int, stream=None):
+    _check(load().mg_op_up(_dtype_code(x), x.shape[-1], ptr(x), ptr(b), ptr(ec), nu,
+                           stream_handle(stream)))
+
+
+def op_vcycle(x, b, coarsest: int, nu1: int, nu2: int, zero_init: bool = False, stream=None):
+    _check(load().mg_op_vcycle(_dtype_code(x), x.shape[-1], coarsest, ptr(x), ptr(b), nu1, nu2,
+                               int(zero_init), stream_handle(stream)))
+
+
+def op_outer_residual(f, x, mu: float, s32, out, stream=None):
+    _check(load().mg_op_outer_residual(f.shape[-1], ptr(f), ptr(x), mu, ptr(s32), ptr(out),
+                                       stream_handle(stream)))

@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares, and
+host-side argument checks reject bad inputs without touching a GPU (no GPU)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_07936_gb300 import build, mg
+    build.build()
+    return mg.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(mg_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("mg_setup", "mg_solve", "mg_vcycle", "mg_load_prolong_weights",
+                     "mg_solve_batched", "mg_destroy", "mg_set_options", "mg_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2403_07936_gb300 import mg
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+        assert name in mg.SIGNATURES, f"{name} has no binding signature"
+
+
+def test_status_strings(lib):
+    assert lib.mg_status_string(0) == b"MG_OK"
+    assert lib.mg_status_string(8) == b"MG_ERR_NONFINITE"
+
+
+@pytest.mark.parametrize("levels,N", [(4, 63), (4, 6), (0, 64), (1, 64), (9, 64), (20, 2048)])
+def test_setup_rejects_invalid_sizes(lib, levels, N):
+    h = C.c_void_p(123)
+    st = lib.mg_setup(levels, N, C.byref(h))
+    assert st == 1  # MG_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.mg_last_error()
+
+
+def test_weights_blob_layout_matches_generator_shapes():
+    from paper_2403_07936_gb300 import sr
+    from synthetic.weights import random_weights, weight_shapes
+    w = random_weights(0)
+    blob = sr.pack_weights(w)
+    n_params = sum(int(__import__("numpy").prod(s)) for _, s in weight_shapes())
+    assert len(blob) == 64 + 4 * n_params
+    assert blob[:8] == b"MGSRW001"

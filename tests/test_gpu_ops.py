@@ -1,0 +1,138 @@
+"""Operator-level parity of the CUDA kernels against the FP64 oracle (GPU).
+
+Each C-ABI operator entry point runs the production kernel on one grid; the
+oracle runs the same step in FP64 with mesh width 1, which is exactly the
+scaled formulation b = h^2 * rhs that the kernels use.
+
+Tolerances: FP64 kernels agree with the oracle to rounding (the smoother
+performs the same operations in the same order); the FP32 kernels are
+compared with the FP64 oracle run on the same float-rounded inputs, and a few
+sweeps of a contractive smoother keep the float error near a few ulp of the
+largest value (bound 2e-6 relative to max|x|).
+"""
+import numpy as np
+import pytest
+
+from oracle import multigrid as omg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL = {torch.float64: 1e-13, torch.float32: 2e-6}
+
+
+@pytest.fixture(scope="module")
+def mg():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_07936_gb300 import mg as m
+    return m
+
+
+def _rand(n, seed, zero_mean=False):
+    a = np.random.default_rng(seed).standard_normal((n, n))
+    return a - a.mean() if zero_mean else a
+
+
+def _as(a, dt):
+    """Round to the test dtype and return (device tensor, float64 copy of the rounded values)."""
+    t = torch.tensor(a, dtype=dt, device=DEV)
+    return t, t.double().cpu().numpy()
+
+
+def _relerr(got, ref):
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("nu,zero", [(0, False), (1, False), (2, False), (2, True), (3, False), (4, True)])
+def test_down_matches_oracle(mg, dt, n, nu, zero):
+    x, x64 = _as(_rand(n, 1), dt)
+    b, b64 = _as(_rand(n, 2, zero_mean=True), dt)
+    bc = torch.empty((n // 2, n // 2), dtype=dt, device=DEV)
+    mg.op_down(x, b, bc, nu=nu, zero_init=zero)
+    torch.cuda.synchronize()
+    xr = np.zeros_like(x64) if zero else x64.copy()
+    omg.rbgs(xr, b64, 1.0, nu)
+    bcr = 4.0 * omg.restrict_fw(omg.residual(b64, xr, 1.0))
+    assert _relerr(x.double().cpu().numpy(), xr) <= TOL[dt]
+    assert _relerr(bc.double().cpu().numpy(), bcr) <= 4 * TOL[dt]
+
+
+def test_down_fp64_smoother_is_bit_exact(mg):
+    n = 128
+    x, x64 = _as(_rand(n, 3), torch.float64)
+    b, b64 = _as(_rand(n, 4, zero_mean=True), torch.float64)
+    bc = torch.empty((n // 2, n // 2), dtype=torch.float64, device=DEV)
+    mg.op_down(x, b, bc, nu=2)
+    torch.cuda.synchronize()
+    xr = x64.copy()
+    omg.rbgs(xr, b64, 1.0, 2)
+    np.testing.assert_array_equal(x.cpu().numpy(), xr)
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n", [64, 128, 512])
+@pytest.mark.parametrize("nu", [0, 1, 2, 4])
+def test_up_matches_oracle(mg, dt, n, nu):
+    x, x64 = _as(_rand(n, 5), dt)
+    b, b64 = _as(_rand(n, 6, zero_mean=True), dt)
+    ec, ec64 = _as(_rand(n // 2, 7), dt)
+    mg.op_up(x, b, ec, nu=nu)
+    torch.cuda.synchronize()
+    xr = x64 + omg.prolong_cubic(ec64)
+    omg.rbgs(xr, b64, 1.0, nu)
+    assert _relerr(x.double().cpu().numpy(), xr) <= TOL[dt]
+
+
+def test_up_prolongation_of_constant_and_smooth_mode(mg):
+    """P 1 = 1 and a smooth coarse mode is interpolated to O(H^4)."""
+    n = 256
+    x = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+    ec = torch.full((n // 2, n // 2), 3.0, dtype=torch.float64, device=DEV)
+    mg.op_up(x, x.clone(), ec, nu=0)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(x.cpu().numpy(), 3.0, atol=1e-13)
+    j = np.arange(n) * 2 * np.pi / n
+    fine = np.sin(2 * j)[:, None] * np.cos(3 * j)[None, :]
+    x.zero_()
+    ec = torch.tensor(np.ascontiguousarray(fine[0::2, 0::2]), device=DEV)
+    mg.op_up(x, x.clone(), ec, nu=0)
+    torch.cuda.synchronize()
+    assert np.abs(x.cpu().numpy() - fine).max() < 1e-6
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n,coarsest", [(8, 8), (8, 4), (16, 8), (32, 8), (64, 8), (64, 4), (64, 16)])
+@pytest.mark.parametrize("nu1,nu2,zero", [(2, 2, True), (1, 1, False), (0, 3, False), (4, 0, True)])
+def test_bottom_vcycle_matches_oracle(mg, dt, n, coarsest, nu1, nu2, zero):
+    x, x64 = _as(_rand(n, 8), dt)
+    b, b64 = _as(_rand(n, 9, zero_mean=True), dt)
+    mg.op_vcycle(x, b, coarsest=coarsest, nu1=nu1, nu2=nu2, zero_init=zero)
+    torch.cuda.synchronize()
+    x0 = np.zeros_like(x64) if zero else x64
+    xr = omg.vcycle(x0, b64, 1.0, nu1, nu2, coarsest=coarsest)
+    tol = 1e-12 if dt == torch.float64 else 2e-5
+    assert _relerr(x.double().cpu().numpy(), xr) <= tol
+
+
+def test_outer_residual_matches_oracle(mg):
+    n = 256
+    h = omg.grid_h(n)
+    f = _rand(n, 10) + 0.3
+    x = _rand(n, 11)
+    mu = f.mean()
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.tensor(x, device=DEV)
+    s32 = torch.empty((n, n), dtype=torch.float32, device=DEV)
+    out = torch.zeros(2, dtype=torch.float64, device=DEV)
+    mg.op_outer_residual(ft, xt, mu, s32, out)
+    torch.cuda.synchronize()
+    s_ref = h * h * omg.residual(f - mu, x, h)
+    np.testing.assert_allclose(s32.double().cpu().numpy(), s_ref, rtol=1e-6,
+                               atol=1e-6 * np.abs(s_ref).max())
+    o = out.cpu().numpy()
+    assert abs(o[0] - np.sum(s_ref ** 2)) <= 1e-12 * np.sum(s_ref ** 2)
+    assert abs(o[1] - np.sum((f - mu) ** 2)) <= 1e-12 * np.sum((f - mu) ** 2)

@@ -1,0 +1,186 @@
+"""Solve-level parity of the CUDA path against the oracle (GPU).
+
+Spec bar: final relative residual <= 1e-10 and
+|x_gpu - x_ref|_inf / |x_ref|_inf <= 1e-9, where x_ref is the oracle's FP64
+V-cycle solution at sizes it finishes in seconds and the exact FFT solution
+(the plain definition x* = A^+ f) at every size, including 2048^2.
+"""
+import numpy as np
+import pytest
+
+from oracle import multigrid as omg
+from synthetic.sources import config_seed, default_kmax, turbulent_source
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mg():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_07936_gb300 import mg as m
+    return m
+
+
+def _levels(n, coarsest=8):
+    return int(np.log2(n // coarsest)) + 1
+
+
+def _check_solution(f, x, tol=1e-10, err_bound=1e-9, x_ref=None):
+    n = f.shape[0]
+    h = omg.grid_h(n)
+    rel = omg.relative_residual(f - f.mean(), x, h)
+    assert rel <= 1.5 * tol, rel  # oracle recomputation of the residual (rounding margin)
+    xe = omg.exact_solve_fft(f - f.mean())
+    err = np.abs(x - xe).max() / np.abs(xe).max()
+    assert err <= err_bound, err
+    if x_ref is not None:
+        err2 = np.abs(x - x_ref).max() / np.abs(x_ref).max()
+        assert err2 <= err_bound, err2
+    assert abs(x.mean()) <= 1e-12 * np.abs(x).max()
+    return rel, err
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("n,coarsest", [(64, 8), (128, 8), (256, 4), (512, 16)])
+def test_solve_matches_oracle(mg, precision, n, coarsest):
+    f = turbulent_source(n, default_kmax(n), config_seed(0, n))
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.zeros_like(ft)
+    ctx = mg.Context(_levels(n, coarsest), n, precision=precision)
+    info = ctx.solve(ft, xt, tol=1e-10)
+    assert info["rel_residual"] <= 1e-10
+    x_ref, oinfo = omg.solve(f, tol=1e-10, coarsest=coarsest)
+    _check_solution(f, xt.cpu().numpy(), x_ref=x_ref)
+    if precision == "fp64":
+        # same algorithm in the same precision: same cycle count as the oracle
+        assert info["vcycles"] == oinfo["cycles"]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_solve_2048_full_size(mg, precision):
+    """The 2048^2, 9-level workload (k <= 256 source) against the FFT solution."""
+    n = 2048
+    f = turbulent_source(n, 256, config_seed(1, 0))
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.zeros_like(ft)
+    ctx = mg.Context(9, n, precision=precision)
+    info = ctx.solve(ft, xt, tol=1e-10)
+    assert info["rel_residual"] <= 1e-10
+    _check_solution(f, xt.cpu().numpy())
+    assert info["vcycles"] <= 12
+
+
+def test_solve_64_config_batch_of_seeds(mg):
+    """64^2, 4 levels, FP64 V(2,2): several independent seeds."""
+    ctx = mg.Context(4, 64, precision="fp64")
+    for i in range(8):
+        f = turbulent_source(64, 8, config_seed(0, i))
+        ft = torch.tensor(f, device=DEV)
+        xt = torch.zeros_like(ft)
+        ctx.solve(ft, xt, tol=1e-10)
+        _check_solution(f, xt.cpu().numpy())
+
+
+def test_host_pointers_match_device_pointers(mg):
+    n = 256
+    f = turbulent_source(n, 32, 123)
+    ctx = mg.Context(6, n)
+    xh = np.zeros_like(f)
+    ctx.solve(f, xh, tol=1e-10)  # numpy (pageable host) buffers
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.zeros_like(ft)
+    ctx.solve(ft, xt, tol=1e-10)
+    np.testing.assert_array_equal(xh, xt.cpu().numpy())
+    fp = torch.tensor(f).pin_memory()
+    xp = torch.zeros_like(fp).pin_memory()
+    ctx.solve(fp, xp, tol=1e-10)  # pinned host buffers
+    np.testing.assert_array_equal(xp.numpy(), xh)
+
+
+def test_solve_is_deterministic(mg):
+    n = 512
+    f = turbulent_source(n, 64, 77)
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(7, n)
+    a = torch.zeros_like(ft)
+    b = torch.zeros_like(ft)
+    ctx.solve(ft, a, tol=1e-10)
+    ctx.solve(ft, b, tol=1e-10)
+    assert torch.equal(a, b)
+
+
+def test_warm_start_and_nonzero_mean(mg):
+    n = 256
+    f = turbulent_source(n, 32, 5)
+    ctx = mg.Context(6, n)
+    ft = torch.tensor(f + 2.5, device=DEV)  # the mean is projected out and reported
+    xt = torch.zeros_like(ft)
+    info = ctx.solve(ft, xt, tol=1e-10)
+    assert abs(info["removed_mean"] - 2.5) < 1e-12
+    _check_solution(f, xt.cpu().numpy())
+    cold = info["vcycles"]
+    info2 = ctx.solve(ft, xt, tol=1e-10)  # already converged: no cycle
+    assert info2["vcycles"] == 0
+    g = f + 1e-3 * turbulent_source(n, 32, 6)
+    gt = torch.tensor(g, device=DEV)
+    info3 = ctx.solve(gt, xt, tol=1e-10)  # warm start from a nearby solution
+    assert info3["vcycles"] < cold
+    _check_solution(g, xt.cpu().numpy())
+
+
+def test_degenerate_sources(mg):
+    n = 128
+    ctx = mg.Context(5, n)
+    zt = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+    xt = torch.ones_like(zt)
+    info = ctx.solve(zt, xt)
+    assert info["vcycles"] == 0 and not xt.any()
+    ct = torch.full((n, n), 4.0, dtype=torch.float64, device=DEV)  # constant: zero-mean part is 0
+    ctx.solve(ct, xt)
+    assert not xt.any()
+    bad = torch.tensor(turbulent_source(n, 16, 1), device=DEV)
+    bad[3, 5] = float("nan")
+    with pytest.raises(mg.MGError) as e:
+        ctx.solve(bad, torch.zeros_like(bad))
+    assert e.value.status == 8  # MG_ERR_NONFINITE
+
+
+def test_not_converged_reports_status(mg):
+    n = 256
+    f = turbulent_source(n, 32, 9)
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.zeros_like(ft)
+    ctx = mg.Context(6, n, precision="fp64", max_cycles=2)
+    info = ctx.solve(ft, xt, tol=1e-10, check=False)
+    assert info["status"] == "MG_ERR_NOT_CONVERGED" and info["vcycles"] == 2
+    assert 1e-10 < info["rel_residual"] < 1e-2
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 1), (3, 3)])
+def test_other_cycle_shapes_converge(mg, nu1, nu2):
+    n = 512
+    f = turbulent_source(n, 64, 11)
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.zeros_like(ft)
+    ctx = mg.Context(7, n, nu_pre=nu1, nu_post=nu2)
+    ctx.solve(ft, xt, tol=1e-10)
+    _check_solution(f, xt.cpu().numpy())
+
+
+def test_vcycle_entry_point_matches_oracle_cycle(mg):
+    """mg_vcycle in FP64 mode equals one oracle V(2,2) cycle."""
+    n = 256
+    f = turbulent_source(n, 32, 13)
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.zeros_like(ft)
+    ctx = mg.Context(6, n, precision="fp64")
+    ctx.vcycle(ft, xt)
+    ctx.vcycle(ft, xt)
+    xr = np.zeros_like(f)
+    h = omg.grid_h(n)
+    for _ in range(2):
+        xr = omg.vcycle(xr, f - f.mean(), h)
+    assert np.abs(xt.cpu().numpy() - xr).max() <= 1e-11 * np.abs(xr).max()
