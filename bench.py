@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark: solves/s to ||r||/||f|| <= 1e-10 on the 2048^2 periodic
+pressure-Poisson workload, FP32 V-cycles in FP64 defect correction (the
+headline) next to the plain FP64 V-cycle on the same GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete solve of one right-hand side from x = 0 through the
+C ABI (mg_solve).  Inputs are resident in HBM when a timed step starts; L2 is
+flushed (a 512 MB write) and x reset between steps, outside the timed events.
+Under torchrun (N > 1) every rank solves its own right-hand sides (replicas,
+weak scaling, no collective on the data path); the time is the max over ranks.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 2048
+LEVELS = 9
+KMAX = 256
+TOL = 1e-10
+METRIC = "solves/s to ||r||/||f||<=1e-10, mixed vs FP64 V-cycle; serve p50/p99 ms"
+WORKLOAD = ("2048^2 periodic pressure-Poisson -Lap_h p = f (5-point, h = 2pi/2048), 9 levels to 8^2, "
+            "V(2,2) red-black Gauss-Seidel, full weighting, periodic cubic-spline prolongation, exact "
+            "8^2 coarse solve; FP32 V-cycles (2 per outer step) in FP64 defect correction; "
+            "tol ||r||/||f|| <= 1e-10; seeded k^-5/3 turbulent source, 1 <= k <= 256")
+# algorithmic bytes per grid point of each probed kernel kind
+PROBE_NAMES = {1: "k_down<float,2> (finest: 2 RB-GS sweeps + residual + FW)",
+               2: "k_up<float,2> (finest: cubic prolongation + correction + 2 RB-GS sweeps)",
+               3: "k_outer_residual<f64> (FP64 residual, norms, float conversion)",
+               4: "k_update (FP64 x += e)"}
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha1()
+    for name in ("mg_kernels.cu", "mg_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2403_07936_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def read_traffic(kernel_kind):
+    """DRAM bytes per launch from a committed ncu capture, if it matches this source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    ent = d.get(str(kernel_kind))
+    if not ent or ent.get("source_sha1") != kernel_source_sha():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for k, name in enumerate(names):
+                    if parts[5 + k].lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+
+def oracle_cycle_sample(f, cycles):
+    """Time `cycles` iterations of the FP64 oracle solve loop (V-cycle + residual)."""
+    from oracle import multigrid as omg
+    h = omg.grid_h(f.shape[0])
+    fz = f - f.mean()
+    x = np.zeros_like(fz)
+    t0 = time.perf_counter()
+    rels = []
+    for _ in range(cycles):
+        x = omg.vcycle(x, fz, h)
+        rels.append(omg.relative_residual(fz, x, h))
+    return time.perf_counter() - t0, rels
+
+
+ORACLE_CYCLES_PER_SOLVE = 7  # FP64 V(2,2) cycles the oracle needs on this workload (tests pin it)
+
+
+def cpu_baseline_leg(f, cycles=3):
+    dt, rels = oracle_cycle_sample(f, cycles)
+    per_cycle = dt / cycles
+    value = 1.0 / (per_cycle * ORACLE_CYCLES_PER_SOLVE)
+    return {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{cycles} FP64 oracle V(2,2) cycles + residuals on the 2048^2 source "
+                      f"({dt:.1f} s, {per_cycle:.2f} s/cycle), scaled by the oracle's "
+                      f"{ORACLE_CYCLES_PER_SOLVE} cycles per solve; numpy, single thread, "
+                      f"host {os.uname().machine} x{os.cpu_count()}"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from synthetic.sources import config_seed, turbulent_source
+    f = turbulent_source(N, KMAX, config_seed(1, 0))
+    for _ in range(args.warmup):
+        oracle_cycle_sample(f, 1)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = oracle_cycle_sample(f, 1)
+        times.append(dt)
+    per_cycle = sum(times) / len(times)
+    value = 1.0 / (per_cycle * ORACLE_CYCLES_PER_SOLVE)
+    sample = (f"each step = 1 FP64 oracle V(2,2) cycle + residual on the 2048^2 source "
+              f"({per_cycle:.2f} s); solves/s = 1 / (step time x {ORACLE_CYCLES_PER_SOLVE} cycles "
+              f"per solve); numpy, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_cycle * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+
+    global np
+    import numpy as np
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_07936_gb300 import mg
+    from synthetic.sources import config_seed, turbulent_source
+
+    stream = torch.cuda.current_stream(dev)
+    srcs = [turbulent_source(N, KMAX, config_seed(1, rank * 100 + i)) for i in range(2)]
+    f_dev = [torch.tensor(s, device=dev) for s in srcs]
+    x = torch.zeros_like(f_dev[0])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make_ctx(precision):
+        c = mg.Context(LEVELS, N)
+        c.set_options(precision=precision, stream=stream)
+        return c
+
+    def timed_solves(ctx, k_steps, f_list, xbuf, host=False):
+        times, infos = [], []
+        for k in range(k_steps):
+            f = f_list[k % len(f_list)]
+            xbuf.zero_()
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(ctx.solve(f, xbuf, tol=TOL))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1) / 1e3)
+        return times, infos
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- mixed precision (headline) -------------------------------------
+    ctx = make_ctx("mixed")
+    timed_solves(ctx, args.warmup, f_dev, x)
+    # choose the kernel with the largest share of the solve for the roofline probe
+    kernel_ms = {}
+    for kind in (1, 2, 3, 4):
+        ctx.probe(kind, 256)
+        timed_solves(ctx, 1, f_dev, x)
+        n_l, ms, by = ctx.probe_read()
+        kernel_ms[kind] = (n_l, ms, by)
+    dom = max(kernel_ms, key=lambda k: kernel_ms[k][1])
+    ctx.probe(dom, 64 * args.steps)
+
+    barrier()
+    l0 = mg.kernel_launches()
+    with ClockSampler(local_rank) as clk:
+        t_wall0 = time.perf_counter()
+        times, infos = timed_solves(ctx, args.steps, f_dev, x)
+        t_wall = time.perf_counter() - t_wall0
+    launches = mg.kernel_launches() - l0
+    barrier()
+    n_l, probe_ms, probe_bytes = ctx.probe_read()
+    ctx.probe(0, 0)
+    total = max_over_ranks(sum(times))
+    value = world * args.steps / total
+    clocks = clk.summary()
+
+    # accuracy of the last solve against the exact FFT solution (plain definition)
+    from oracle import multigrid as omg
+    f_last = srcs[(args.steps - 1) % len(srcs)]
+    x_last = x.cpu().numpy()
+    xe = omg.exact_solve_fft(f_last)
+    err = float(np.abs(x_last - xe).max() / np.abs(xe).max())
+    rel = omg.relative_residual(f_last, x_last, omg.grid_h(N))
+
+    # ---- plain FP64 V-cycle on the same GPU ------------------------------
+    ctx64 = make_ctx("fp64")
+    timed_solves(ctx64, args.warmup, f_dev, x)
+    k64 = max(3, args.steps // 2)
+    t64, info64 = timed_solves(ctx64, k64, f_dev, x)
+    value64 = world * k64 / max_over_ranks(sum(t64))
+    err64 = float(np.abs(x.cpu().numpy() - omg.exact_solve_fft(srcs[(k64 - 1) % 2])).max()
+                  / np.abs(omg.exact_solve_fft(srcs[(k64 - 1) % 2])).max())
+
+    # ---- end to end through host (pinned) buffers --------------------------
+    f_host = [torch.tensor(s).pin_memory() for s in srcs]
+    x_host = torch.zeros_like(f_host[0]).pin_memory()
+    timed_solves(ctx, 2, f_host, x_host)
+    te2e, _ = timed_solves(ctx, args.steps, f_host, x_host)
+    value_e2e = world * args.steps / max_over_ranks(sum(te2e))
+    bytes_grid = N * N * 8
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    peak, peak_src = read_peaks()
+    achieved = (probe_bytes / n_l) / (probe_ms / n_l / 1e3) / 1e9 if n_l else None
+    roofline = {"bound": "hbm", "kernel": PROBE_NAMES[dom], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                "peak_source": f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if peak_src == 'measured' else 'recipe fallback'})",
+                "traffic": read_traffic(dom),
+                "algorithmic_bytes_per_launch": probe_bytes / n_l if n_l else None,
+                "avg_launch_us": probe_ms / n_l * 1e3 if n_l else None, "launches": n_l,
+                "share_of_solve": None}
+    mean_step = sum(times) / len(times)
+    roofline["share_of_solve"] = (probe_ms / args.steps / 1e3) / mean_step
+    kernels = {PROBE_NAMES[k]: {"launches_per_solve": v[0], "ms_per_solve": v[1],
+                                "gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None}
+               for k, v in kernel_ms.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg(srcs[0])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (V-cycles) + f64 (outer residual, update, norms)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": N, "levels": LEVELS, "rhs_per_step": 1,
+                       "precision": "mixed", "prolongation": "cubic",
+                       "l2": "flushed between steps (512 MB write), x reset to 0",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": value_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * bytes_grid,
+                    "d2h_bytes_per_step": bytes_grid,
+                    "path": "mg_solve with pinned host f and x (copies inside the call)"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "wall_s_timed_region": t_wall,
+            "solve": {"vcycles": infos[-1]["vcycles"], "outer_iters": infos[-1]["outer_iters"],
+                      "rel_residual": rel, "err_inf_vs_exact_fft": err},
+            "fp64_vcycle": {"value": value64, "unit": "solves/s", "steps": k64,
+                            "ms_per_step": sum(t64) / k64 * 1e3,
+                            "vcycles": info64[-1]["vcycles"], "err_inf_vs_exact_fft": err64},
+            "mixed_over_fp64": value / value64,
+            "kernels_per_solve": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

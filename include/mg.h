@@ -117,22 +117,45 @@ const char *mg_status_string(mg_status status);
 const char *mg_last_error(void);
 
 /* ---------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper): used by the benchmark to
+ * time one kernel kind live inside a solve and to count launches.
+ * ------------------------------------------------------------------- */
+
+/* Number of kernels this library has launched in this process so far. */
+unsigned long long mg_kernel_launches(void);
+
+/* Record a CUDA event pair around each launch of one kernel kind on the
+ * context's stream: 1 = finest-level pre-smoothing/restriction kernel,
+ * 2 = finest-level prolongation/post-smoothing kernel, 3 = FP64 outer
+ * residual, 4 = FP64 update; 0 disables.  At most `capacity` launches are
+ * recorded until mg_probe_read. */
+mg_status mg_probe_kernel(mg_ctx *ctx, int kind, int capacity);
+
+/* Synchronise the context's stream and return the number of recorded
+ * launches, their summed device time (ms) and their summed algorithmic
+ * bytes (compulsory reads + writes); resets the probe's accumulators. */
+mg_status mg_probe_read(mg_ctx *ctx, int *launches, double *total_ms, double *bytes);
+
+/* ---------------------------------------------------------------------
  * Operator-level entry points (device pointers only), for verification of
  * each step against a reference.  dtype: 0 = double, 1 = float.  Grids use
  * the scaled right-hand side b = h^2 * rhs, so that A x = rhs reads
  * 4 x_ij - (sum of 4 neighbours) = b_ij.  Work is ordered on `stream`.
  * ------------------------------------------------------------------- */
 
-/* Pre-smoothing and restriction (Algorithm 6 relax, residual, restrict):
- * nu red-black sweeps on x (x treated as 0 on entry if zero_init), then
- * bc = 4 * FW(b - (4x - sum nbrs)), the scaled coarse right-hand side on the
- * n/2 grid.  n: power of two >= 16. */
-mg_status mg_op_down(int dtype, int n, void *x, const void *b, int nu, int zero_init, void *bc,
-                     void *stream);
+/* Pre-smoothing and restriction (Algorithm 6: relax, residual, restrict):
+ * x_out = nu red-black sweeps applied to x (x read as 0 if zero_init), then
+ * bc = 4 * FW(b - (4 x_out - sum nbrs)), the scaled coarse right-hand side on
+ * the n/2 grid.  n: power of two >= 64.  x and x_out must not overlap (the
+ * kernel is out of place). */
+mg_status mg_op_down(int dtype, int n, const void *x, void *x_out, const void *b, int nu,
+                     int zero_init, void *bc, void *stream);
 
-/* Correction and post-smoothing: x += P ec (P = periodic cubic spline,
- * ec on the n/2 grid), then nu red-black sweeps with right-hand side b. */
-mg_status mg_op_up(int dtype, int n, void *x, const void *b, const void *ec, int nu, void *stream);
+/* Correction and post-smoothing (Algorithm 6: prolongate, correct; Sec. 2.2
+ * spline): x_out = nu red-black sweeps applied to x + P ec, P the periodic
+ * tensor-product cubic spline from the n/2 grid.  x, x_out distinct. */
+mg_status mg_op_up(int dtype, int n, const void *x, void *x_out, const void *b, const void *ec,
+                   int nu, void *stream);
 
 /* V-cycles below the top: runs one V(nu1, nu2) cycle on the n x n problem
  * 4x - sum = b (n <= 64, down to a coarsest grid of size `coarsest`),

@@ -51,10 +51,12 @@ namespace {
 constexpr int kMaxLevels = 16;
 constexpr size_t kAlign = 256;
 
+// Per level: the iterate x, a second buffer t for the out-of-place tile
+// passes (down: x -> t, up: t -> x), and the scaled right-hand side b.
 struct Level {
     int n = 0;
-    float *x32 = nullptr, *b32 = nullptr;
-    double *x64 = nullptr, *b64 = nullptr;
+    float *x32 = nullptr, *t32 = nullptr, *b32 = nullptr;
+    double *x64 = nullptr, *t64 = nullptr, *b64 = nullptr;
 };
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -119,12 +121,37 @@ struct mg_ctx {
     double *host_out = nullptr;  // pinned mirror of red_out
     double *f_stage = nullptr, *x_stage = nullptr;
     SrState sr;
+    // optional CUDA-event probe around one kernel kind (instrumentation)
+    int probe_kind = 0, probe_cap = 0, probe_used = 0;
+    cudaEvent_t *probe_ev = nullptr;
+    double probe_bytes = 0.0;
 
     Reduction red(int group) const { return Reduction{red_partials, red_counter, red_out + group * kMaxSlots}; }
     double *out(int group) const { return red_out + group * kMaxSlots; }
 };
 
 enum { kGrpF = 0, kGrpR = 1, kGrpU = 2, kGrpX = 3 };
+enum { kProbeNone = 0, kProbeDown = 1, kProbeUp = 2, kProbeResidual = 3, kProbeUpdate = 4 };
+
+static void probe_begin(mg_ctx *c, int kind) {
+    if (c->probe_kind == kind && c->probe_used < c->probe_cap)
+        cudaEventRecord(c->probe_ev[2 * c->probe_used], c->stream);
+}
+static void probe_end(mg_ctx *c, int kind, double bytes) {
+    if (c->probe_kind == kind && c->probe_used < c->probe_cap) {
+        cudaEventRecord(c->probe_ev[2 * c->probe_used + 1], c->stream);
+        ++c->probe_used;
+        c->probe_bytes += bytes;
+    }
+}
+static void probe_free(mg_ctx *c) {
+    for (int i = 0; i < 2 * c->probe_cap; ++i) cudaEventDestroy(c->probe_ev[i]);
+    delete[] c->probe_ev;
+    c->probe_ev = nullptr;
+    c->probe_cap = c->probe_used = 0;
+    c->probe_kind = kProbeNone;
+    c->probe_bytes = 0.0;
+}
 
 static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
     void *&blk = fp64 ? c->h64_block : c->h32_block;
@@ -133,7 +160,7 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
     size_t total = 0;
     for (int l = 0; l < c->levels; ++l) {
         const size_t nn = (size_t)c->lv[l].n * c->lv[l].n;
-        total += 2 * align_up(nn * es);
+        total += 3 * align_up(nn * es);
     }
     MG_CUDA(cudaMalloc(&blk, total));
     MG_CUDA(cudaMemsetAsync(blk, 0, total, c->stream));
@@ -143,56 +170,72 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
         const size_t bytes = align_up(nn * es);
         if (fp64) {
             c->lv[l].x64 = (double *)p;
-            c->lv[l].b64 = (double *)(p + bytes);
+            c->lv[l].t64 = (double *)(p + bytes);
+            c->lv[l].b64 = (double *)(p + 2 * bytes);
         } else {
             c->lv[l].x32 = (float *)p;
-            c->lv[l].b32 = (float *)(p + bytes);
+            c->lv[l].t32 = (float *)(p + bytes);
+            c->lv[l].b32 = (float *)(p + 2 * bytes);
         }
-        p += 2 * bytes;
+        p += 3 * bytes;
     }
     return MG_OK;
 }
 
 template <typename T> static T *lvx(mg_ctx *c, int l);
+template <typename T> static T *lvt(mg_ctx *c, int l);
 template <typename T> static T *lvb(mg_ctx *c, int l);
 template <> float *lvx<float>(mg_ctx *c, int l) { return c->lv[l].x32; }
+template <> float *lvt<float>(mg_ctx *c, int l) { return c->lv[l].t32; }
 template <> float *lvb<float>(mg_ctx *c, int l) { return c->lv[l].b32; }
 template <> double *lvx<double>(mg_ctx *c, int l) { return c->lv[l].x64; }
+template <> double *lvt<double>(mg_ctx *c, int l) { return c->lv[l].t64; }
 template <> double *lvb<double>(mg_ctx *c, int l) { return c->lv[l].b64; }
 template <typename T> static const T *ainv(mg_ctx *c);
 template <> const float *ainv<float>(mg_ctx *c) { return c->ainv32; }
 template <> const double *ainv<double>(mg_ctx *c) { return c->ainv64; }
 
-// One V(nu1, nu2) cycle on 4x - sum = b at level l (x = 0 on entry if zero).
+// One V(nu1, nu2) cycle on 4x - sum = b at level l (x = 0 on entry if zero);
+// t is the level's second buffer, the result is left in x.
 template <typename T>
-static mg_status vcycle_rec(mg_ctx *c, int l, T *x, const T *b, bool zero) {
+static mg_status vcycle_rec(mg_ctx *c, int l, T *x, T *t, const T *b, bool zero) {
     const int n = c->lv[l].n;
     if (n <= kBottomMax) {
         MG_CUDA(launch_bottom<T>(x, b, n, c->coarsest, c->nu1, c->nu2, zero, ainv<T>(c), c->taps,
                                  c->stream));
         return MG_OK;
     }
-    T *xc = lvx<T>(c, l + 1), *bc = lvb<T>(c, l + 1);
-    MG_CUDA(launch_down<T>(x, b, n, c->nu1, zero, bc, c->stream));
-    MG_TRY(vcycle_rec<T>(c, l + 1, xc, bc, true));
-    MG_CUDA(launch_up<T>(x, b, xc, n, c->nu2, c->taps, c->stream));
+    T *xc = lvx<T>(c, l + 1), *tc = lvt<T>(c, l + 1), *bc = lvb<T>(c, l + 1);
+    const double nn = (double)n * n * sizeof(T);
+    if (l == 0) probe_begin(c, kProbeDown);
+    MG_CUDA(launch_down<T>(x, t, b, n, c->nu1, zero, bc, c->stream));
+    if (l == 0) probe_end(c, kProbeDown, nn * ((zero ? 0 : 1) + 1 + 1 + 0.25));
+    MG_TRY(vcycle_rec<T>(c, l + 1, xc, tc, bc, true));
+    if (l == 0) probe_begin(c, kProbeUp);
+    MG_CUDA(launch_up<T>(t, x, b, xc, n, c->nu2, c->taps, c->stream));
+    if (l == 0) probe_end(c, kProbeUp, nn * (2 + (c->nu2 > 0 ? 1 : 0) + 0.25));
     return MG_OK;
 }
 
 // Top-level FP32 V-cycle with the chosen prolongation at the finest transition.
 static mg_status vcycle32_top(mg_ctx *c, bool zero, mg_prolong prolong) {
-    float *x = c->lv[0].x32, *b = c->lv[0].b32;
+    float *x = c->lv[0].x32, *t = c->lv[0].t32, *b = c->lv[0].b32;
     if (prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax) {
-        float *xc = c->lv[1].x32, *bc = c->lv[1].b32;
-        MG_CUDA(launch_down<float>(x, b, c->lv[0].n, c->nu1, zero, bc, c->stream));
-        MG_TRY(vcycle_rec<float>(c, 1, xc, bc, true));
+        float *xc = c->lv[1].x32, *tc = c->lv[1].t32, *bc = c->lv[1].b32;
+        const double nn = (double)c->lv[0].n * c->lv[0].n * sizeof(float);
+        probe_begin(c, kProbeDown);
+        MG_CUDA(launch_down<float>(x, t, b, c->lv[0].n, c->nu1, zero, bc, c->stream));
+        probe_end(c, kProbeDown, nn * ((zero ? 0 : 1) + 1 + 1 + 0.25));
+        MG_TRY(vcycle_rec<float>(c, 1, xc, tc, bc, true));
         // generator correction s * G(e_c / s) on the fine grid, then the cubic
         // part, the correction and the post-smoothing in one up pass
         MG_TRY(sr_correction(&c->sr, xc, c->lv[1].n, c->stream, g_err, sizeof g_err));
-        MG_CUDA(launch_up<float>(x, b, xc, c->lv[0].n, c->nu2, c->taps, c->stream, c->sr.fine_out));
+        probe_begin(c, kProbeUp);
+        MG_CUDA(launch_up<float>(t, x, b, xc, c->lv[0].n, c->nu2, c->taps, c->stream, c->sr.fine_out));
+        probe_end(c, kProbeUp, nn * (3 + (c->nu2 > 0 ? 1 : 0) + 0.25));
         return MG_OK;
     }
-    return vcycle_rec<float>(c, 0, x, b, zero);
+    return vcycle_rec<float>(c, 0, x, t, b, zero);
 }
 
 static mg_status resolve_io(mg_ctx *c, const double *f, double *x, const double **fd, double **xd,
@@ -279,6 +322,7 @@ void mg_destroy(mg_ctx *c) {
     cudaFree(c->f_stage);
     cudaFree(c->x_stage);
     sr_free(&c->sr);
+    probe_free(c);
     delete c;
 }
 
@@ -399,8 +443,10 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     double fnorm = 0.0, rel = INFINITY, mu = 0.0;
     bool have_xsum = false, first = true;
     for (;;) {
+        probe_begin(c, kProbeResidual);
         MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
                                       first, c->red(kGrpR), s));
+        probe_end(c, kProbeResidual, N2 * (16.0 + (mixed ? 4.0 : 0.0)));
         MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 2 * kMaxSlots,
                                 cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
@@ -431,10 +477,12 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         if (mixed) {
             for (int k = 0; k < c->inner && cycles < c->max_cycles; ++k, ++cycles)
                 MG_TRY(vcycle32_top(c, k == 0, prolong));
+            probe_begin(c, kProbeUpdate);
             MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
+            probe_end(c, kProbeUpdate, N2 * 20.0);
             have_xsum = true;
         } else {
-            MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].b64, false));
+            MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].t64, c->lv[0].b64, false));
             ++cycles;
             have_xsum = false;
         }
@@ -485,7 +533,7 @@ mg_status mg_vcycle(mg_ctx *c, const double *f, double *x, mg_prolong prolong) {
         MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
     } else {
         MG_CUDA(launch_scaled_rhs(fd, N, h2, c->out(kGrpF), c->lv[0].b64, s));
-        MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].b64, false));
+        MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].t64, c->lv[0].b64, false));
     }
     if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
@@ -507,6 +555,52 @@ mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *
     return worst;
 }
 
+unsigned long long mg_kernel_launches(void) { return launches_total(); }
+
+mg_status mg_probe_kernel(mg_ctx *c, int kind, int capacity) {
+    if (!c || kind < kProbeNone || kind > kProbeUpdate || capacity < 0 || capacity > 4096) {
+        set_err("invalid probe request");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    probe_free(c);
+    if (kind == kProbeNone || capacity == 0) return MG_OK;
+    c->probe_ev = new cudaEvent_t[2 * capacity];
+    for (int i = 0; i < 2 * capacity; ++i) {
+        cudaError_t e = cudaEventCreate(&c->probe_ev[i]);
+        if (e != cudaSuccess) {
+            c->probe_cap = i / 2;
+            for (int k = 2 * c->probe_cap; k < i; ++k) cudaEventDestroy(c->probe_ev[k]);
+            probe_free(c);
+            MG_CUDA(e);
+        }
+    }
+    c->probe_cap = capacity;
+    c->probe_kind = kind;
+    return MG_OK;
+}
+
+mg_status mg_probe_read(mg_ctx *c, int *launches, double *total_ms, double *bytes) {
+    if (!c) {
+        set_err("null context");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+    double tot = 0.0;
+    for (int i = 0; i < c->probe_used; ++i) {
+        float ms = 0.f;
+        MG_CUDA(cudaEventElapsedTime(&ms, c->probe_ev[2 * i], c->probe_ev[2 * i + 1]));
+        tot += ms;
+    }
+    if (launches) *launches = c->probe_used;
+    if (total_ms) *total_ms = tot;
+    if (bytes) *bytes = c->probe_bytes;
+    c->probe_used = 0;
+    c->probe_bytes = 0.0;
+    return MG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Operator-level entry points
 // ---------------------------------------------------------------------------
@@ -518,34 +612,39 @@ static mg_status op_check(int dtype, int n, int min_n) {
     return MG_OK;
 }
 
-mg_status mg_op_down(int dtype, int n, void *x, const void *b, int nu, int zero_init, void *bc,
-                     void *stream) {
+mg_status mg_op_down(int dtype, int n, const void *x, void *x_out, const void *b, int nu,
+                     int zero_init, void *bc, void *stream) {
     MG_TRY(op_check(dtype, n, 64));
-    if (!x || !b || !bc || nu < 0 || nu > 4) {
-        set_err("invalid arguments");
+    if (!x || !x_out || x == x_out || !b || !bc || nu < 0 || nu > 4) {
+        set_err("invalid arguments (x and x_out must be distinct)");
         return MG_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == 0)
-        MG_CUDA(launch_down<double>((double *)x, (const double *)b, n, nu, zero_init != 0, (double *)bc, s));
+        MG_CUDA(launch_down<double>((const double *)x, (double *)x_out, (const double *)b, n, nu,
+                                    zero_init != 0, (double *)bc, s));
     else
-        MG_CUDA(launch_down<float>((float *)x, (const float *)b, n, nu, zero_init != 0, (float *)bc, s));
+        MG_CUDA(launch_down<float>((const float *)x, (float *)x_out, (const float *)b, n, nu,
+                                   zero_init != 0, (float *)bc, s));
     return MG_OK;
 }
 
-mg_status mg_op_up(int dtype, int n, void *x, const void *b, const void *ec, int nu, void *stream) {
+mg_status mg_op_up(int dtype, int n, const void *x, void *x_out, const void *b, const void *ec, int nu,
+                   void *stream) {
     MG_TRY(op_check(dtype, n, 64));
-    if (!x || !b || !ec || nu < 0 || nu > 4) {
-        set_err("invalid arguments");
+    if (!x || !x_out || x == x_out || !b || !ec || nu < 0 || nu > 4) {
+        set_err("invalid arguments (x and x_out must be distinct)");
         return MG_ERR_INVALID_ARG;
     }
     FirTaps taps;
     fir_taps_host(&taps);
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == 0)
-        MG_CUDA(launch_up<double>((double *)x, (const double *)b, (const double *)ec, n, nu, taps, s));
+        MG_CUDA(launch_up<double>((const double *)x, (double *)x_out, (const double *)b,
+                                  (const double *)ec, n, nu, taps, s));
     else
-        MG_CUDA(launch_up<float>((float *)x, (const float *)b, (const float *)ec, n, nu, taps, s));
+        MG_CUDA(launch_up<float>((const float *)x, (float *)x_out, (const float *)b,
+                                 (const float *)ec, n, nu, taps, s));
     return MG_OK;
 }
 

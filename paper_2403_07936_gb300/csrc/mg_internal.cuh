@@ -112,16 +112,23 @@ __device__ __forceinline__ void reduce_finish(const Reduction &red, const double
 // ----------------------------------------------------------------------------
 // Host-side launchers (defined in mg_kernels.cu); all return cudaError_t.
 // ----------------------------------------------------------------------------
+// xout = nu sweeps of x (x = 0 if zero_init); bc = 4 FW(b - (4 xout - sum)).  x != xout.
 template <typename T>
-cudaError_t launch_down(T *x, const T *b, int n, int nu, bool zero_init, T *bc, cudaStream_t s);
-// x += P ec (+ extra, a fine-grid additive correction, when not null), then nu sweeps
+cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zero_init, T *bc,
+                        cudaStream_t s);
+// xout = nu sweeps of (x + P ec + extra); extra is a fine-grid additive
+// correction or null.  x != xout.
 template <typename T>
-cudaError_t launch_up(T *x, const T *b, const T *ec, int n, int nu, const FirTaps &taps,
-                      cudaStream_t s, const T *extra = nullptr);
+cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
+                      const FirTaps &taps, cudaStream_t s, const T *extra = nullptr);
 template <typename T>
 cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool zero_init,
                           const T *ainv, const FirTaps &taps, cudaStream_t s);
 constexpr int kBottomMax = 64;  // grids up to 64 x 64 run the bottom kernel
+
+// Process-wide count of kernels this library has launched (instrumentation).
+void count_launches(unsigned long long k);
+unsigned long long launches_total();
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,

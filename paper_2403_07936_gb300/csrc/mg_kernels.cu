@@ -7,6 +7,9 @@
 //   k_up     : periodic cubic-spline prolongation of the coarse error (Sec. 2.2)
 //              added to x, then nu sweeps; one read of x, b and the coarse
 //              error, one write of x.
+//   Both read x from one buffer and write the result to another: a block's
+//   halo overlaps its neighbours' interiors, so an in-place update would let a
+//   block of a later wave read values another block has already smoothed.
 //   k_bottom : every level from <= 64 x 64 down to the coarsest grid in one
 //              thread block, with all grids resident in shared memory and the
 //              coarsest grid solved exactly by a pseudo-inverse matvec.
@@ -22,9 +25,15 @@
 // fixed-order trees, last-block finish).
 #include <math.h>
 
+#include <atomic>
+
 #include "mg_internal.cuh"
 
 namespace mg {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 void fir_taps_host(FirTaps *t) {
     const double s3 = sqrt(3.0), a = s3 - 2.0;
@@ -109,8 +118,9 @@ struct DownCfg {
 };
 
 template <typename T, int NU, bool ZERO>
-__global__ void __launch_bounds__(kThreads) k_down(T *__restrict__ x, const T *__restrict__ b,
-                                                   int n, T *__restrict__ bc) {
+__global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *__restrict__ xout,
+                                                   const T *__restrict__ b, int n,
+                                                   T *__restrict__ bc) {
     using Cfg = DownCfg<T, NU>;
     constexpr int H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C, SP = Cfg::SP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -156,8 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_down(T *__restrict__ x, const T *_
         const T corner = ((bs[p - SP - 1] + bs[p - SP + 1]) + bs[p + SP - 1]) + bs[p + SP + 1];
         bc[(size_t)(ty0 / 2 + I) * nc + tx0 / 2 + J] = (T(4) * bs[p] + T(2) * edge + corner) * T(0.25);
     }
-    // x changed unless no sweep ran on a loaded guess (zeros assumed must be written)
-    if (NU > 0 || ZERO) store_tile<T, SP>(x, xs, n, ty0, tx0, H, HX);
+    store_tile<T, SP>(xout, xs, n, ty0, tx0, H, HX);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,8 +191,8 @@ struct UpCfg {
 };
 
 template <typename T, int NU>
-__global__ void __launch_bounds__(kThreads) k_up(T *__restrict__ x, const T *__restrict__ b,
-                                                 const T *__restrict__ ec,
+__global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__restrict__ xout,
+                                                 const T *__restrict__ b, const T *__restrict__ ec,
                                                  const T *__restrict__ extra, int n, FirTaps taps) {
     using Cfg = UpCfg<T, NU>;
     constexpr int H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C, SP = Cfg::SP, L = Cfg::L;
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_up(T *__restrict__ x, const T *__r
             __syncthreads();
         }
     }
-    store_tile<T, SP>(x, xs, n, ty0, tx0, H, HX);
+    store_tile<T, SP>(xout, xs, n, ty0, tx0, H, HX);
 }
 
 // ---------------------------------------------------------------------------
@@ -463,36 +472,40 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 }
 
 template <typename T, int NU, bool ZERO>
-cudaError_t down_impl(T *x, const T *b, int n, T *bc, cudaStream_t s) {
+cudaError_t down_impl(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_t s) {
     using Cfg = DownCfg<T, NU>;
     auto k = k_down<T, NU, ZERO>;
     cudaError_t e = set_smem(k, Cfg::smem);
     if (e != cudaSuccess) return e;
     dim3 grid(n / kTX, n / kTY);
-    k<<<grid, kThreads, Cfg::smem, s>>>(x, b, n, bc);
+    k<<<grid, kThreads, Cfg::smem, s>>>(x, xout, b, n, bc);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T, int NU>
-cudaError_t up_impl(T *x, const T *b, const T *ec, const T *extra, int n, const FirTaps &taps,
-                    cudaStream_t s) {
+cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra, int n,
+                    const FirTaps &taps, cudaStream_t s) {
     using Cfg = UpCfg<T, NU>;
     auto k = k_up<T, NU>;
     cudaError_t e = set_smem(k, Cfg::smem);
     if (e != cudaSuccess) return e;
     dim3 grid(n / kTX, n / kTY);
-    k<<<grid, kThreads, Cfg::smem, s>>>(x, b, ec, extra, n, taps);
+    k<<<grid, kThreads, Cfg::smem, s>>>(x, xout, b, ec, extra, n, taps);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_down(T *x, const T *b, int n, int nu, bool zero_init, T *bc, cudaStream_t s) {
-    if (n < kTX || n % kTX || n % kTY) return cudaErrorInvalidValue;
+cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zero_init, T *bc,
+                        cudaStream_t s) {
+    if (n < kTX || n % kTX || n % kTY || x == xout) return cudaErrorInvalidValue;
 #define MG_DOWN_CASE(NU)                                                                  \
     case NU:                                                                              \
-        return zero_init ? down_impl<T, NU, true>(x, b, n, bc, s) : down_impl<T, NU, false>(x, b, n, bc, s);
+        return zero_init ? down_impl<T, NU, true>(x, xout, b, n, bc, s)                   \
+                         : down_impl<T, NU, false>(x, xout, b, n, bc, s);
     switch (nu) {
         MG_DOWN_CASE(0)
         MG_DOWN_CASE(1)
@@ -505,15 +518,15 @@ cudaError_t launch_down(T *x, const T *b, int n, int nu, bool zero_init, T *bc, 
 }
 
 template <typename T>
-cudaError_t launch_up(T *x, const T *b, const T *ec, int n, int nu, const FirTaps &taps,
-                      cudaStream_t s, const T *extra) {
-    if (n < kTX || n % kTX || n % kTY || !ec) return cudaErrorInvalidValue;
+cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
+                      const FirTaps &taps, cudaStream_t s, const T *extra) {
+    if (n < kTX || n % kTX || n % kTY || !ec || x == xout) return cudaErrorInvalidValue;
     switch (nu) {
-        case 0: return up_impl<T, 0>(x, b, ec, extra, n, taps, s);
-        case 1: return up_impl<T, 1>(x, b, ec, extra, n, taps, s);
-        case 2: return up_impl<T, 2>(x, b, ec, extra, n, taps, s);
-        case 3: return up_impl<T, 3>(x, b, ec, extra, n, taps, s);
-        case 4: return up_impl<T, 4>(x, b, ec, extra, n, taps, s);
+        case 0: return up_impl<T, 0>(x, xout, b, ec, extra, n, taps, s);
+        case 1: return up_impl<T, 1>(x, xout, b, ec, extra, n, taps, s);
+        case 2: return up_impl<T, 2>(x, xout, b, ec, extra, n, taps, s);
+        case 3: return up_impl<T, 3>(x, xout, b, ec, extra, n, taps, s);
+        case 4: return up_impl<T, 4>(x, xout, b, ec, extra, n, taps, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -535,15 +548,18 @@ cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
     k<<<1, kBottomThreads, smem, s>>>(x, b, n, nlev, nu1, nu2, zero_init ? 1 : 0, ainv, taps);
+    count_launches(1);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_down<float>(float *, const float *, int, int, bool, float *, cudaStream_t);
-template cudaError_t launch_down<double>(double *, const double *, int, int, bool, double *, cudaStream_t);
-template cudaError_t launch_up<float>(float *, const float *, const float *, int, int, const FirTaps &,
-                                      cudaStream_t, const float *);
-template cudaError_t launch_up<double>(double *, const double *, const double *, int, int,
-                                       const FirTaps &, cudaStream_t, const double *);
+template cudaError_t launch_down<float>(const float *, float *, const float *, int, int, bool, float *,
+                                        cudaStream_t);
+template cudaError_t launch_down<double>(const double *, double *, const double *, int, int, bool,
+                                         double *, cudaStream_t);
+template cudaError_t launch_up<float>(const float *, float *, const float *, const float *, int, int,
+                                      const FirTaps &, cudaStream_t, const float *);
+template cudaError_t launch_up<double>(const double *, double *, const double *, const double *, int,
+                                       int, const FirTaps &, cudaStream_t, const double *);
 template cudaError_t launch_bottom<float>(float *, const float *, int, int, int, int, bool, const float *,
                                           const FirTaps &, cudaStream_t);
 template cudaError_t launch_bottom<double>(double *, const double *, int, int, int, int, bool,
@@ -551,6 +567,7 @@ template cudaError_t launch_bottom<double>(double *, const double *, int, int, i
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s) {
     k_sum<<<kRedBlocks, kRedThreads, 0, s>>>(f, (size_t)n * n, red);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s) {
@@ -559,6 +576,7 @@ cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s) {
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum, double *b,
                               cudaStream_t s) {
     k_scaled_rhs<<<kRedBlocks, kRedThreads, 0, s>>>(f, n, h2, f_sum, b);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_outer_residual(const double *f, const double *x, int n, double h2,
@@ -575,14 +593,17 @@ cudaError_t launch_outer_residual(const double *f, const double *x, int n, doubl
         else
             k_outer_residual<false, false><<<kRedBlocks, kRedThreads, 0, s>>>(f, x, n, h2, mu_sum, mu_host, s32, red);
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaStream_t s) {
     k_update<<<kRedBlocks, kRedThreads, 0, s>>>(x, e, (size_t)n * n, red);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s) {
     k_project<<<kRedBlocks, kRedThreads, 0, s>>>(x, (size_t)n * n, sum);
+    count_launches(1);
     return cudaGetLastError();
 }
 

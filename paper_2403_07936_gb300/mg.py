@@ -46,8 +46,11 @@ SIGNATURES = {
     "mg_destroy": (None, [_VP]),
     "mg_status_string": (C.c_char_p, [_I]),
     "mg_last_error": (C.c_char_p, []),
-    "mg_op_down": (_I, [_I, _I, _VP, _VP, _I, _I, _VP, _VP]),
-    "mg_op_up": (_I, [_I, _I, _VP, _VP, _VP, _I, _VP]),
+    "mg_kernel_launches": (C.c_ulonglong, []),
+    "mg_probe_kernel": (_I, [_VP, _I, _I]),
+    "mg_probe_read": (_I, [_VP, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D)]),
+    "mg_op_down": (_I, [_I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
+    "mg_op_up": (_I, [_I, _I, _VP, _VP, _VP, _VP, _I, _VP]),
     "mg_op_vcycle": (_I, [_I, _I, _I, _VP, _VP, _I, _I, _I, _VP]),
     "mg_op_outer_residual": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP]),
 }
@@ -180,6 +183,15 @@ class Context:
     def vcycle(self, f, x, prolong: str = "cubic"):
         _check(load().mg_vcycle(self._h, ptr(f), ptr(x), PROLONG[prolong]))
 
+    def probe(self, kind: int, capacity: int = 256):
+        """Time one kernel kind with CUDA events (1 down, 2 up, 3 residual, 4 update)."""
+        _check(load().mg_probe_kernel(self._h, kind, capacity))
+
+    def probe_read(self):
+        n, ms, by = C.c_int(), C.c_double(), C.c_double()
+        _check(load().mg_probe_read(self._h, C.byref(n), C.byref(ms), C.byref(by)))
+        return n.value, ms.value, by.value
+
     def close(self):
         if self._h:
             load().mg_destroy(self._h)
@@ -190,6 +202,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libmg in this process so far."""
+    return int(load().mg_kernel_launches())
 
 
 def solve_batched(ctxs, fs, xs, tol: float = 1e-10, prolong: str = "cubic"):
@@ -205,13 +222,13 @@ def solve_batched(ctxs, fs, xs, tol: float = 1e-10, prolong: str = "cubic"):
 
 # ---- operator-level calls (device arrays) --------------------------------
 
-def op_down(x, b, bc, nu: int, zero_init: bool = False, stream=None):
-    _check(load().mg_op_down(_dtype_code(x), x.shape[-1], ptr(x), ptr(b), nu, int(zero_init),
-                             ptr(bc), stream_handle(stream)))
+def op_down(x, x_out, b, bc, nu: int, zero_init: bool = False, stream=None):
+    _check(load().mg_op_down(_dtype_code(x), x.shape[-1], ptr(x), ptr(x_out), ptr(b), nu,
+                             int(zero_init), ptr(bc), stream_handle(stream)))
 
 
-def op_up(x, b, ec, nu: int, stream=None):
-    _check(load().mg_op_up(_dtype_code(x), x.shape[-1], ptr(x), ptr(b), ptr(ec), nu,
+def op_up(x, x_out, b, ec, nu: int, stream=None):
+    _check(load().mg_op_up(_dtype_code(x), x.shape[-1], ptr(x), ptr(x_out), ptr(b), ptr(ec), nu,
                            stream_handle(stream)))
 
 
