@@ -163,6 +163,25 @@ mg_status mg_op_up(int dtype, int n, const void *x, void *x_out, const void *b, 
 mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, int nu1, int nu2,
                        int zero_init, void *stream);
 
+/* Allocation-free variant of mg_op_vcycle (no counterpart in the paper; the
+ * paper's method has no memory-management side).  mg_op_vcycle allocates
+ * device memory on every call for the coarsest-grid pseudo-inverse; callers
+ * that cannot call cudaMalloc use this one instead - for example a solver
+ * stepped inside a fixed-rate simulation loop, which cannot take the
+ * device-wide synchronisation cudaMalloc implies, or a process whose framework
+ * allocator already reserved most device memory, where a raw cudaMalloc fails
+ * although the framework holds free blocks.  Same arguments and results as
+ * mg_op_vcycle.  The pseudo-inverse is built on the device, on `stream`, into
+ * one static device array of 256*256 doubles (512 KiB) that every GPU loading
+ * the library keeps until exit, so coarsest must be 4, 8 or 16 and n <= 64;
+ * larger sizes return MG_ERR_INVALID_ARG.  No cudaMalloc/cudaFree or other
+ * allocating call is made.  The first call on a device looks up the array's
+ * address there (cudaGetSymbolAddress) - make that first call before any
+ * stream capture.  All calls share the array and rewrite it, so calls that
+ * overlap on the GPU (unordered streams) race.  Asynchronous on `stream`. */
+mg_status mg_op_vcycle_static(int dtype, int n, int coarsest, void *x, const void *b, int nu1,
+                              int nu2, int zero_init, void *stream);
+
 /* FP64 outer residual: s = h^2 (f - mu) - (4x - sum nbrs) (so s = h^2 r),
  * written as float to s32 when s32 != NULL; out[0] = sum s^2,
  * out[1] = sum (f - mu)^2 (out: 2 doubles, device). */

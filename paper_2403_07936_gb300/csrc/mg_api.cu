@@ -31,6 +31,8 @@ static void set_err(const char *fmt, ...) {
     va_end(ap);
 }
 
+void mg::set_last_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 #define MG_CUDA(call)                                                                        \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \

@@ -126,6 +126,9 @@ cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu
                           const T *ainv, const FirTaps &taps, cudaStream_t s);
 constexpr int kBottomMax = 64;  // grids up to 64 x 64 run the bottom kernel
 
+// Set the message mg_last_error() returns on the calling thread.
+void set_last_error(const char *msg);
+
 // Process-wide count of kernels this library has launched (instrumentation).
 void count_launches(unsigned long long k);
 unsigned long long launches_total();

@@ -52,6 +52,7 @@ SIGNATURES = {
     "mg_op_down": (_I, [_I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
     "mg_op_up": (_I, [_I, _I, _VP, _VP, _VP, _VP, _I, _VP]),
     "mg_op_vcycle": (_I, [_I, _I, _I, _VP, _VP, _I, _I, _I, _VP]),
+    "mg_op_vcycle_static": (_I, [_I, _I, _I, _VP, _VP, _I, _I, _I, _VP]),
     "mg_op_outer_residual": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP]),
 }
 
