@@ -84,6 +84,15 @@ mg_status mg_set_options(mg_ctx *ctx, mg_precision precision, int nu_pre, int nu
                          int max_cycles, void *cuda_stream);
 mg_status mg_set_inner_cycles(mg_ctx *ctx, int inner_cycles);
 
+/* Execution mode of mg_solve (default 1).  1: the whole solve is one CUDA
+ * graph launch - a WHILE conditional node runs the outer steps on the device
+ * and a test kernel decides convergence, so the host synchronises once per
+ * solve; graphs are recorded on first use per (f, x, prolongation, tol) and
+ * cached (up to 4).  In this mode max_cycles is rounded down to a multiple of
+ * inner_cycles.  0: a host loop with one residual read-back per outer step
+ * (also used while a probe is active). */
+mg_status mg_set_graph_execution(mg_ctx *ctx, int enable);
+
 /* Load super-resolution generator weights (Sec. 2.3, Fig. 1b).  The blob is
  * copied (the caller keeps ownership).  Blob layout: see mg_sr.h-style
  * description in the library documentation: a 64-byte header

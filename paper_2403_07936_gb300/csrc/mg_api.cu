@@ -16,6 +16,7 @@
 
 #include <chrono>
 #include <new>
+#include <vector>
 
 #include "mg_internal.cuh"
 #include "mg_sr.cuh"
@@ -106,6 +107,22 @@ bool is_device_pointer(const void *p) {
 
 }  // namespace
 
+// One instantiated solve graph: prologue (source sum, first residual, test),
+// a WHILE node whose body runs one outer step (V-cycles, update, residual,
+// test), and the zero-mean projection.  Keyed by the buffers and the
+// prolongation it was recorded with.
+struct SolveGraph {
+    const double *f = nullptr;
+    double *x = nullptr;
+    int prolong = -1;
+    double tol = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long n_pro = 0, n_body = 0, n_epi = 0;  // kernels per part
+    unsigned long long stamp = 0;               // last use (LRU)
+};
+constexpr int kGraphCache = 4;
+
 struct mg_ctx {
     int N = 0, levels = 0, coarsest = 0, device = 0;
     mg_precision prec = MG_PREC_MIXED;
@@ -123,6 +140,12 @@ struct mg_ctx {
     double *host_out = nullptr;  // pinned mirror of red_out
     double *f_stage = nullptr, *x_stage = nullptr;
     SrState sr;
+    // graph execution
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;  // private stream used only for recording graphs
+    DevState *dstate = nullptr, *hstate = nullptr;
+    SolveGraph graphs[kGraphCache];
+    unsigned long long graph_clock = 0;
     // optional CUDA-event probe around one kernel kind (instrumentation)
     int probe_kind = 0, probe_cap = 0, probe_used = 0;
     cudaEvent_t *probe_ev = nullptr;
@@ -290,6 +313,157 @@ static mg_status check_common(mg_ctx *c, const double *f, double *x, mg_prolong 
     return MG_OK;
 }
 
+static void drop_graphs(mg_ctx *c) {
+    for (SolveGraph &g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = SolveGraph();
+    }
+}
+
+// Record the solve of A x = f for fixed buffers as one graph.  All launches go
+// to the private capture stream; on any failure the capture is ended and the
+// partial graph destroyed.
+static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_prolong prolong,
+                                    double tol, SolveGraph *out) {
+    const bool mixed = c->prec == MG_PREC_MIXED;
+    const int N = c->N;
+    const double N2 = (double)N * N;
+    const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
+    const int step = mixed ? c->inner : 1;
+    cudaStream_t user_stream = c->stream;
+    cudaStream_t s = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle handle;
+    bool capturing = false;
+    mg_status st = MG_OK;
+    long long n_pro = 0, n_body = 0, n_epi = 0;
+    auto fail = [&](cudaError_t e, const char *what) {
+        set_err("graph recording (%s) failed: %s", what, cudaGetErrorString(e));
+        st = MG_ERR_CUDA;
+    };
+    c->stream = s;  // the V-cycle helpers launch on c->stream
+    do {
+        cudaError_t e = cudaGraphCreate(&g, 0);
+        if (e != cudaSuccess) { fail(e, "create"); break; }
+        e = cudaGraphConditionalHandleCreate(&handle, g, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { fail(e, "conditional handle"); break; }
+        // prologue
+        long long l0 = (long long)launches_total();
+        e = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { fail(e, "begin prologue"); break; }
+        capturing = true;
+        e = launch_source_sum(fd, N, c->red(kGrpF), s);
+        if (e == cudaSuccess && !mixed) e = launch_scaled_rhs(fd, N, h2, c->out(kGrpF), c->lv[0].b64, s);
+        if (e == cudaSuccess)
+            e = launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
+                                      true, c->red(kGrpR), s);
+        if (e == cudaSuccess)
+            e = launch_check(c->dstate, c->out(kGrpR), nullptr, c->out(kGrpF), N2, h2, tol, step,
+                             c->max_cycles, true, handle, s);
+        if (e != cudaSuccess) { fail(e, "prologue"); break; }
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) { fail(e, "capture info"); break; }
+        std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+        e = cudaStreamEndCapture(s, &g);
+        capturing = false;
+        if (e != cudaSuccess) { fail(e, "end prologue"); break; }
+        n_pro = (long long)launches_total() - l0;
+        // WHILE node: one outer step per iteration
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cond;
+        e = cudaGraphAddNode(&cond, g, tail.data(), nullptr, tail.size(), &cp);
+        if (e != cudaSuccess) { fail(e, "while node"); break; }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        l0 = (long long)launches_total();
+        e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { fail(e, "begin body"); break; }
+        capturing = true;
+        if (mixed) {
+            for (int k = 0; k < c->inner && st == MG_OK; ++k) st = vcycle32_top(c, k == 0, prolong);
+            if (st != MG_OK) break;
+            e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
+        } else {
+            st = vcycle_rec<double>(c, 0, xd, c->lv[0].t64, c->lv[0].b64, false);
+            if (st != MG_OK) break;
+        }
+        if (e == cudaSuccess)
+            e = launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
+                                      false, c->red(kGrpR), s);
+        if (e == cudaSuccess)
+            e = launch_check(c->dstate, c->out(kGrpR), mixed ? c->out(kGrpU) : nullptr, c->out(kGrpF),
+                             N2, h2, tol, step, c->max_cycles, false, handle, s);
+        if (e != cudaSuccess) { fail(e, "body"); break; }
+        e = cudaStreamEndCapture(s, &body);
+        capturing = false;
+        if (e != cudaSuccess) { fail(e, "end body"); break; }
+        n_body = (long long)launches_total() - l0;
+        // epilogue: zero-mean projection (or zero for a constant source)
+        l0 = (long long)launches_total();
+        e = cudaStreamBeginCaptureToGraph(s, g, &cond, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { fail(e, "begin epilogue"); break; }
+        capturing = true;
+        e = launch_sum(xd, N, c->red(kGrpX), s);
+        if (e == cudaSuccess) e = launch_project(xd, N, c->out(kGrpX), s, &c->dstate->zero_source);
+        if (e != cudaSuccess) { fail(e, "epilogue"); break; }
+        e = cudaStreamEndCapture(s, &g);
+        capturing = false;
+        if (e != cudaSuccess) { fail(e, "end epilogue"); break; }
+        n_epi = (long long)launches_total() - l0;
+        e = cudaGraphInstantiate(&out->exec, g, 0);
+        if (e != cudaSuccess) { fail(e, "instantiate"); break; }
+    } while (false);
+    c->stream = user_stream;
+    count_launches(-(n_pro + n_body + n_epi));  // recording is not execution
+    if (capturing) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(s, &junk);
+        if (junk && junk != g) cudaGraphDestroy(junk);
+    }
+    if (st != MG_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        out->exec = nullptr;
+        return st;
+    }
+    out->graph = g;
+    out->f = fd;
+    out->x = xd;
+    out->prolong = (int)prolong;
+    out->tol = tol;
+    out->n_pro = n_pro;
+    out->n_body = n_body;
+    out->n_epi = n_epi;
+    return MG_OK;
+}
+
+static mg_status get_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_prolong prolong, double tol,
+                                 SolveGraph **out) {
+    SolveGraph *lru = &c->graphs[0];
+    for (SolveGraph &g : c->graphs) {
+        if (g.exec && g.f == fd && g.x == xd && g.prolong == (int)prolong && g.tol == tol) {
+            g.stamp = ++c->graph_clock;
+            *out = &g;
+            return MG_OK;
+        }
+        if (!g.exec || g.stamp < lru->stamp) lru = &g;
+    }
+    if (lru->exec) cudaGraphExecDestroy(lru->exec);
+    if (lru->graph) cudaGraphDestroy(lru->graph);
+    *lru = SolveGraph();
+    MG_TRY(record_solve_graph(c, fd, xd, prolong, tol, lru));
+    lru->stamp = ++c->graph_clock;
+    *out = lru;
+    return MG_OK;
+}
+
 extern "C" {
 
 const char *mg_status_string(mg_status s) {
@@ -325,6 +499,10 @@ void mg_destroy(mg_ctx *c) {
     cudaFree(c->x_stage);
     sr_free(&c->sr);
     probe_free(c);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    cudaFree(c->dstate);
+    cudaFreeHost(c->hstate);
     delete c;
 }
 
@@ -376,6 +554,11 @@ mg_status mg_setup(int levels, int N, mg_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(double) * 4 * kMaxSlots);
     if (e == cudaSuccess) e = cudaMemset(c->red_out, 0, sizeof(double) * 4 * kMaxSlots);
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_out, sizeof(double) * 4 * kMaxSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&c->dstate, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMemset(c->dstate, 0, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->hstate, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = prepare_kernels();
     if (e != cudaSuccess) {
         set_err("mg_setup: %s", cudaGetErrorString(e));
         return fail(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA);
@@ -392,6 +575,8 @@ mg_status mg_set_options(mg_ctx *c, mg_precision prec, int nu_pre, int nu_post, 
                 max_cycles);
         return MG_ERR_INVALID_ARG;
     }
+    if (prec != c->prec || nu_pre != c->nu1 || nu_post != c->nu2 || max_cycles != c->max_cycles)
+        drop_graphs(c);
     c->prec = prec;
     c->nu1 = nu_pre;
     c->nu2 = nu_post;
@@ -405,6 +590,7 @@ mg_status mg_set_inner_cycles(mg_ctx *c, int inner) {
         set_err("inner_cycles must be in [1, 16]");
         return MG_ERR_INVALID_ARG;
     }
+    if (inner != c->inner) drop_graphs(c);
     c->inner = inner;
     return MG_OK;
 }
@@ -415,6 +601,7 @@ mg_status mg_load_prolong_weights(mg_ctx *c, const void *blob, size_t bytes) {
         return MG_ERR_INVALID_ARG;
     }
     MG_CUDA(cudaSetDevice(c->device));
+    drop_graphs(c);
     return sr_load(&c->sr, blob, bytes, g_err, sizeof g_err);
 }
 
@@ -437,13 +624,41 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
     cudaStream_t s = c->stream;
 
+    if (c->use_graphs && c->probe_kind == kProbeNone) {
+        // the whole solve as one graph launch; the loop runs on the device
+        SolveGraph *sg = nullptr;
+        MG_TRY(get_solve_graph(c, fd, xd, prolong, tol, &sg));
+        MG_CUDA(cudaGraphLaunch(sg->exec, s));
+        MG_CUDA(cudaMemcpyAsync(c->hstate, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaStreamSynchronize(s));
+        const DevState &ds = *c->hstate;
+        count_launches(sg->n_pro + (long long)ds.outer * sg->n_body + sg->n_epi);
+        mg_status gst = (mg_status)ds.status;
+        if (gst == MG_ERR_NONFINITE) set_err("non-finite residual (NaN or Inf in f or x)");
+        if (gst == MG_ERR_NOT_CONVERGED)
+            set_err("not converged: rel residual %.3e after %d V-cycles", ds.rel, ds.cycles);
+        if (info) {
+            info->outer_iters = ds.outer;
+            info->vcycles = ds.cycles;
+            info->rel_residual = ds.rel;
+            info->removed_mean = ds.mu;
+            info->update_norm = ds.unorm;
+            info->prolong_used = (int)prolong;
+            info->sr_fallback = 0;
+            info->time_ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        return gst;
+    }
+
     MG_CUDA(launch_source_sum(fd, N, c->red(kGrpF), s));
     if (!mixed) MG_CUDA(launch_scaled_rhs(fd, N, h2, c->out(kGrpF), c->lv[0].b64, s));
 
     mg_status st = MG_OK;
     int cycles = 0, outer = 0;
     double fnorm = 0.0, rel = INFINITY, mu = 0.0;
-    bool have_xsum = false, first = true;
+    bool first = true;
     for (;;) {
         probe_begin(c, kProbeResidual);
         MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
@@ -466,7 +681,6 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         if (fnorm == 0.0) {  // constant source: the zero-mean solution is 0
             MG_CUDA(cudaMemsetAsync(xd, 0, sizeof(double) * N * N, s));
             rel = 0.0;
-            have_xsum = false;
             break;
         }
         rel = rnorm / fnorm;
@@ -482,21 +696,15 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
             probe_begin(c, kProbeUpdate);
             MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
             probe_end(c, kProbeUpdate, N2 * 20.0);
-            have_xsum = true;
         } else {
             MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].t64, c->lv[0].b64, false));
             ++cycles;
-            have_xsum = false;
         }
         ++outer;
     }
     if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
-        const double *xsum = c->out(kGrpU) + 1;
-        if (!have_xsum) {
-            MG_CUDA(launch_sum(xd, N, c->red(kGrpX), s));
-            xsum = c->out(kGrpX);
-        }
-        MG_CUDA(launch_project(xd, N, xsum, s));
+        MG_CUDA(launch_sum(xd, N, c->red(kGrpX), s));
+        MG_CUDA(launch_project(xd, N, c->out(kGrpX), s));
     }
     if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 4 * kMaxSlots,
@@ -558,6 +766,15 @@ mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *
 }
 
 unsigned long long mg_kernel_launches(void) { return launches_total(); }
+
+mg_status mg_set_graph_execution(mg_ctx *c, int enable) {
+    if (!c) {
+        set_err("null context");
+        return MG_ERR_INVALID_ARG;
+    }
+    c->use_graphs = enable != 0;
+    return MG_OK;
+}
 
 mg_status mg_probe_kernel(mg_ctx *c, int kind, int capacity) {
     if (!c || kind < kProbeNone || kind > kProbeUpdate || capacity < 0 || capacity > 4096) {

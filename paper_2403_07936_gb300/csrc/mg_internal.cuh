@@ -130,8 +130,33 @@ constexpr int kBottomMax = 64;  // grids up to 64 x 64 run the bottom kernel
 void set_last_error(const char *msg);
 
 // Process-wide count of kernels this library has launched (instrumentation).
-void count_launches(unsigned long long k);
+// Launches recorded into a CUDA graph are taken back after capture and
+// counted again for every replay.
+void count_launches(long long k);
 unsigned long long launches_total();
+
+// Set the shared-memory attributes of every tile kernel on the current device
+// (called once per context, so that later launches, including those recorded
+// into graphs, need no attribute calls).
+cudaError_t prepare_kernels();
+
+// Device-side state of one solve, advanced by k_check (graph execution).
+struct DevState {
+    int cycles;       // V-cycles run
+    int outer;        // outer steps (loop iterations) run
+    int status;       // MG_OK, MG_ERR_NOT_CONVERGED or MG_ERR_NONFINITE
+    int zero_source;  // f is constant: the zero-mean solution is 0
+    double fnorm;     // ||f - mean f||_2
+    double rel;       // last relative residual
+    double unorm;     // ||e||_2 of the last update
+    double mu;        // mean of f
+};
+
+// Convergence test of one outer step: reads the residual sums, updates the
+// state and sets the graph's loop condition (1 = run another step).
+cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
+                         double n2, double h2, double tol, int step, int max_cycles, bool first,
+                         cudaGraphConditionalHandle handle, cudaStream_t s);
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,
@@ -140,7 +165,9 @@ cudaError_t launch_outer_residual(const double *f, const double *x, int n, doubl
                                   const double *mu_sum, double mu_host, float *s32,
                                   bool want_fnorm, Reduction red, cudaStream_t s);
 cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaStream_t s);
-cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s);
+// x -= sum / n^2, or x = 0 where *zero_flag is set (zero_flag may be null)
+cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s,
+                           const int *zero_flag = nullptr);
 cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s);
 
 }  // namespace mg

@@ -31,9 +31,9 @@
 
 namespace mg {
 
-static std::atomic<unsigned long long> g_launches{0};
-void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
-unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+static std::atomic<long long> g_launches{0};
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launches_total() { return (unsigned long long)g_launches.load(std::memory_order_relaxed); }
 
 void fir_taps_host(FirTaps *t) {
     const double s3 = sqrt(3.0), a = s3 - 2.0;
@@ -48,14 +48,26 @@ void fir_taps_host(FirTaps *t) {
 
 namespace {
 
-constexpr int kTY = 32;        // tile rows
-constexpr int kTX = 64;        // tile columns
 constexpr int kThreads = 256;  // threads per tile block
 
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Output tile per precision.  FP32 tiles are taller (less halo per point);
+// FP64 tiles are halved to keep the staged tiles within shared memory.
+// NJ = spline midpoints a thread computes per work item (the window of
+// coarse values they share is loaded once).
+template <typename T> struct Tile;
+template <> struct Tile<float> {
+    static constexpr int TY = 64, TX = 64, NJ = 2;
+};
+template <> struct Tile<double> {
+    static constexpr int TY = 32, TX = 64, NJ = 1;
+};
 
 // Copy rows [r0, r0+R) x cols [c0, c0+C) of the periodic n x n grid g into
-// shared memory s (pitch SP).  c0, C, SP are multiples of the vector width.
+// shared memory s (pitch SP), with 16-byte vector loads.  c0 and C are
+// multiples of the vector width.
 template <typename T, int R, int C, int SP>
 __device__ __forceinline__ void load_tile(T *__restrict__ s, const T *__restrict__ g, int n, int r0,
                                           int c0) {
@@ -70,37 +82,106 @@ __device__ __forceinline__ void load_tile(T *__restrict__ s, const T *__restrict
     }
 }
 
-// Store the interior rows [r_s, r_s+TY) x cols [c_s, c_s+TX) of a staged tile
-// to global rows [gy, gy+TY) x cols [gx, gx+TX).
-template <typename T, int SP>
-__device__ __forceinline__ void store_tile(T *__restrict__ g, const T *__restrict__ s, int n, int gy,
-                                           int gx, int r_s, int c_s) {
+// ---------------------------------------------------------------------------
+// Colour-split staging.  A staged R x C tile (C even) is held as two arrays,
+// red and black, of R x CK entries (CK = C / 2): staged point (r, c) of
+// colour q = (r + c) & 1 is entry r * CK + (c >> 1) of array q.  Tile
+// origins and halos are even, so q is the point's red-black colour on the
+// grid.  For a point (r, k) of colour q, with o = (r + q) & 1 and P the other
+// colour's array, the neighbours are N = P[r-1][k], S = P[r+1][k],
+// W = P[r][k-1+o], E = P[r][k+o]: unit stride across a warp, no bank
+// conflicts, and no division in the index arithmetic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scatter_vec(float *red, float *black, int rr, int c, int CK, float4 v) {
+    float2 a = make_float2(v.x, v.z), b2 = make_float2(v.y, v.w);
+    const bool even = (rr & 1) == 0;  // c is a multiple of 4: parity of (rr + c) is rr's
+    *reinterpret_cast<float2 *>(red + rr * CK + (c >> 1)) = even ? a : b2;
+    *reinterpret_cast<float2 *>(black + rr * CK + (c >> 1)) = even ? b2 : a;
+}
+__device__ __forceinline__ void scatter_vec(double *red, double *black, int rr, int c, int CK, double2 v) {
+    const bool even = (rr & 1) == 0;
+    red[rr * CK + (c >> 1)] = even ? v.x : v.y;
+    black[rr * CK + (c >> 1)] = even ? v.y : v.x;
+}
+__device__ __forceinline__ float4 gather_vec(const float *red, const float *black, int rr, int c, int CK) {
+    const float2 r = *reinterpret_cast<const float2 *>(red + rr * CK + (c >> 1));
+    const float2 b2 = *reinterpret_cast<const float2 *>(black + rr * CK + (c >> 1));
+    return (rr & 1) == 0 ? make_float4(r.x, b2.x, r.y, b2.y) : make_float4(b2.x, r.x, b2.y, r.y);
+}
+__device__ __forceinline__ double2 gather_vec(const double *red, const double *black, int rr, int c, int CK) {
+    const double r = red[rr * CK + (c >> 1)], b2 = black[rr * CK + (c >> 1)];
+    return (rr & 1) == 0 ? make_double2(r, b2) : make_double2(b2, r);
+}
+
+// Load rows [r0, r0+R) x cols [c0, c0+C) of the periodic grid into a split tile.
+template <typename T, int R, int C>
+__device__ __forceinline__ void load_split(T *red, T *black, const T *__restrict__ g, int n, int r0,
+                                           int c0) {
     using V = typename Prec<T>::vec;
     constexpr int VW = Prec<T>::VW;
-    constexpr int CV = kTX / VW;
-    for (int idx = threadIdx.x; idx < kTY * CV; idx += blockDim.x) {
+    constexpr int CV = C / VW;
+    for (int idx = threadIdx.x; idx < R * CV; idx += blockDim.x) {
         const int rr = idx / CV, cv = idx - rr * CV;
-        const V v = *reinterpret_cast<const V *>(s + (r_s + rr) * SP + c_s + cv * VW);
+        const int gr = (r0 + rr) & (n - 1), gc = (c0 + cv * VW) & (n - 1);
+        const V v = __ldg(reinterpret_cast<const V *>(g + (size_t)gr * n + gc));
+        scatter_vec(red, black, rr, cv * VW, C / 2, v);
+    }
+}
+
+// Store staged rows [r_s, r_s+TY) x cols [c_s, c_s+TX) of a split tile to
+// global rows [gy, gy+TY) x cols [gx, gx+TX).
+template <typename T, int TY, int TX, int C>
+__device__ __forceinline__ void store_split(T *__restrict__ g, const T *red, const T *black, int n,
+                                            int gy, int gx, int r_s, int c_s) {
+    using V = typename Prec<T>::vec;
+    constexpr int VW = Prec<T>::VW;
+    constexpr int CV = TX / VW;
+    for (int idx = threadIdx.x; idx < TY * CV; idx += blockDim.x) {
+        const int rr = idx / CV, cv = idx - rr * CV;
+        const V v = gather_vec(red, black, r_s + rr, c_s + cv * VW, C / 2);
         *reinterpret_cast<V *>(g + (size_t)(gy + rr) * n + gx + cv * VW) = v;
     }
 }
 
-// One colour of Gauss-Seidel on the staged rows [r_lo, r_hi) x cols
-// [c_lo, c_hi) (c_lo and the width even; staged parity equals global parity).
-// x <- (b + ((x_N + x_S) + x_W) + x_E) / 4 for the points with (r+c)%2 == colour.
-template <typename T, int SP>
-__device__ __forceinline__ void half_sweep(T *__restrict__ xs, const T *__restrict__ bs, int r_lo,
-                                           int r_hi, int c_lo, int c_hi, int colour) {
-    const int W = (c_hi - c_lo) >> 1;
-    const int total = (r_hi - r_lo) * W;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int rr = idx / W, k = idx - rr * W;
-        const int r = r_lo + rr;
-        const int c = c_lo + 2 * k + ((r + c_lo + colour) & 1);
-        const int p = r * SP + c;
-        const T nb = ((xs[p - SP] + xs[p + SP]) + xs[p - 1]) + xs[p + 1];
-        xs[p] = (bs[p] + nb) * T(0.25);
+// Visit the points of colour q in staged rows [r_lo, r_hi), split columns
+// [1, CK - 1), as vertical strips: thread (seg, k) walks rows of its segment,
+// keeping N and the centre of the other colour in registers.  body(p, N, S,
+// W, E) gets the split index p = r * CK + k of the point.
+template <int CK, typename T, typename Body>
+__device__ __forceinline__ void colour_strips(const T *__restrict__ P, int r_lo, int r_hi, int q,
+                                              Body body) {
+    constexpr int KW = CK - 2;
+    constexpr int NSEG = kThreads / KW;
+    const int seg = threadIdx.x / KW;
+    if (seg >= NSEG) return;
+    const int k = 1 + (threadIdx.x - seg * KW);
+    const int per = (r_hi - r_lo + NSEG - 1) / NSEG;
+    const int ra = r_lo + seg * per;
+    const int rb = min(r_hi, ra + per);
+    if (ra >= rb) return;
+    T pN = P[(ra - 1) * CK + k];
+    T pC = P[ra * CK + k];
+    for (int r = ra; r < rb; ++r) {
+        const T pS = P[(r + 1) * CK + k];
+        const int o = (r + q) & 1;
+        const T side = P[r * CK + k - 1 + 2 * o];
+        const T W = o ? pC : side;
+        const T E = o ? side : pC;
+        body(r * CK + k, pN, pS, W, E);
+        pN = pC;
+        pC = pS;
     }
+}
+
+// One Gauss-Seidel half-sweep of colour q: x <- (b + (((N + S) + W) + E)) / 4.
+// X and B point at the red arrays; the black ones follow A entries later.
+template <int CK, int A, typename T>
+__device__ __forceinline__ void half_sweep(T *X, const T *B, int r_lo, int r_hi, int q) {
+    T *Xq = X + q * A;
+    const T *Bq = B + q * A;
+    colour_strips<CK>(X + (q ^ 1) * A, r_lo, r_hi, q, [&](int p, T N, T S, T W, T E) {
+        Xq[p] = (Bq[p] + (((N + S) + W) + E)) * T(0.25);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -108,13 +189,15 @@ __device__ __forceinline__ void half_sweep(T *__restrict__ xs, const T *__restri
 // ---------------------------------------------------------------------------
 template <typename T, int NU>
 struct DownCfg {
+    static constexpr int TY = Tile<T>::TY, TX = Tile<T>::TX;
     static constexpr int VW = Prec<T>::VW;
-    static constexpr int H = 2 * NU + 2;             // logical halo (rows and cols)
-    static constexpr int HX = round_up(H, VW);       // staged column halo
-    static constexpr int R = kTY + 2 * H;
-    static constexpr int C = kTX + 2 * HX;
-    static constexpr int SP = C;
-    static constexpr size_t smem = 2ull * R * SP * sizeof(T);
+    static constexpr int H = 2 * NU + 2;           // logical halo (rows and cols)
+    static constexpr int HX = round_up(H + 2, VW);  // staged column halo (>= H + 2: k >= 1)
+    static constexpr int R = TY + 2 * H;
+    static constexpr int C = TX + 2 * HX;
+    static constexpr int CK = C / 2;
+    static constexpr int A = R * CK + 16;  // one colour array (+16 entries: bank offset)
+    static constexpr size_t smem = 4ull * A * sizeof(T);
 };
 
 template <typename T, int NU, bool ZERO>
@@ -122,72 +205,82 @@ __global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *_
                                                    const T *__restrict__ b, int n,
                                                    T *__restrict__ bc) {
     using Cfg = DownCfg<T, NU>;
-    constexpr int H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C, SP = Cfg::SP;
+    constexpr int TY = Cfg::TY, TX = Cfg::TX, H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C,
+                  CK = Cfg::CK, A = Cfg::A;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *xs = reinterpret_cast<T *>(smem_raw);
-    T *bs = xs + R * SP;
-    const int ty0 = blockIdx.y * kTY, tx0 = blockIdx.x * kTX;
+    T *X = reinterpret_cast<T *>(smem_raw);  // red at X, black at X + A
+    T *B = X + 2 * A;                           // red at B, black at B + A
+    const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
 
-    load_tile<T, R, C, SP>(bs, b, n, ty0 - H, tx0 - HX);
+    load_split<T, R, C>(B, B + A, b, n, ty0 - H, tx0 - HX);
     if (ZERO) {
-        for (int i = threadIdx.x; i < R * SP; i += blockDim.x) xs[i] = T(0);
+        for (int i = threadIdx.x; i < 2 * A; i += blockDim.x) X[i] = T(0);
     } else {
-        load_tile<T, R, C, SP>(xs, x, n, ty0 - H, tx0 - HX);
+        load_split<T, R, C>(X, X + A, x, n, ty0 - H, tx0 - HX);
     }
     __syncthreads();
-
-    // staged coordinates: logical (u, v) -> (u + H, v + HX)
-    const int c_off = HX - H;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
 #pragma unroll 1
-        for (int colour = 0; colour < 2; ++colour) {
-            const int k = 2 * s + colour + 1;
-            half_sweep<T, SP>(xs, bs, k, R - k, c_off + k, C - c_off - k, colour);
+        for (int q = 0; q < 2; ++q) {
+            const int j = 2 * s + q + 1;  // valid region shrinks by one per half-sweep
+            half_sweep<CK, A>(X, B, j, R - j, q);
             __syncthreads();
         }
     }
-    // scaled residual s = b - (4x - sum) on logical [-1, T+1), written over b
-    constexpr int RW = kTX + 2;
-    for (int idx = threadIdx.x; idx < (kTY + 2) * RW; idx += blockDim.x) {
-        const int rr = idx / RW, cc = idx - rr * RW;
-        const int p = (H - 1 + rr) * SP + (HX - 1 + cc);
-        const T nb = ((xs[p - SP] + xs[p + SP]) + xs[p - 1]) + xs[p + 1];
-        bs[p] = bs[p] - (T(4) * xs[p] - nb);
+    // scaled residual s = b - (4x - sum) over staged rows [H-1, H+TY+1), written over b
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+        const T *Xq = X + q * A;
+        T *Bq = B + q * A;
+        colour_strips<CK>(X + (q ^ 1) * A, H - 1, H + TY + 1, q, [&](int p, T N, T S, T W, T E) {
+            Bq[p] = Bq[p] - (T(4) * Xq[p] - (((N + S) + W) + E));
+        });
     }
     __syncthreads();
-    // full weighting at coarse (I, J) <-> fine (2I, 2J); times 4 for h_c^2 = 4 h^2
+    // full weighting at coarse (I, J) <-> fine (2I, 2J) (a red point);
+    // times 4 because h_c^2 = 4 h^2
     const int nc = n >> 1;
-    constexpr int CW = kTX / 2;
-    for (int idx = threadIdx.x; idx < (kTY / 2) * CW; idx += blockDim.x) {
+    constexpr int CW = TX / 2;
+    const T *Sr = B, *Sb = B + A;
+    for (int idx = threadIdx.x; idx < (TY / 2) * CW; idx += blockDim.x) {
         const int I = idx / CW, J = idx - I * CW;
-        const int p = (H + 2 * I) * SP + (HX + 2 * J);
-        const T edge = ((bs[p - SP] + bs[p + SP]) + bs[p - 1]) + bs[p + 1];
-        const T corner = ((bs[p - SP - 1] + bs[p - SP + 1]) + bs[p + SP - 1]) + bs[p + SP + 1];
-        bc[(size_t)(ty0 / 2 + I) * nc + tx0 / 2 + J] = (T(4) * bs[p] + T(2) * edge + corner) * T(0.25);
+        const int r = H + 2 * I, k = (HX >> 1) + J;
+        const int p = r * CK + k;
+        const T edge = ((Sb[p - CK] + Sb[p + CK]) + Sb[p - 1]) + Sb[p];
+        const T corner = ((Sr[p - CK - 1] + Sr[p - CK]) + Sr[p + CK - 1]) + Sr[p + CK];
+        bc[(size_t)(ty0 / 2 + I) * nc + tx0 / 2 + J] = (T(4) * Sr[p] + T(2) * edge + corner) * T(0.25);
     }
-    store_tile<T, SP>(xout, xs, n, ty0, tx0, H, HX);
+    store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
 }
 
 // ---------------------------------------------------------------------------
-// k_up: x += P_cubic ec, then NU sweeps, on one tile.
+// k_up: x += P_cubic ec (+ extra), then NU sweeps, on one tile.
 // ---------------------------------------------------------------------------
 template <typename T, int NU>
 struct UpCfg {
+    static constexpr int TY = Tile<T>::TY, TX = Tile<T>::TX, NJ = Tile<T>::NJ;
     static constexpr int VW = Prec<T>::VW;
     static constexpr int L = Prec<T>::L;
     static constexpr int H = 2 * NU;
-    static constexpr int HX = round_up(H, VW);
-    static constexpr int R = kTY + 2 * H;
-    static constexpr int C = kTX + 2 * HX;
-    static constexpr int SP = C;
-    // coarse rows [I0 - CHY, I0 + TY/2 + H/2 + L), cols [J0 - CHX, J0 + TX/2 + CXE)
+    static constexpr int HX = round_up(H + 2, VW);
+    static constexpr int R = TY + 2 * H;
+    static constexpr int C = TX + 2 * HX;
+    static constexpr int CK = C / 2;
+    static constexpr int A = R * CK + 16;
+    // coarse positions refined: J in [-H/2, TX/2 + H/2) (JW of them), I likewise (IW)
+    static constexpr int JW = TX / 2 + H;
+    static constexpr int IW = TY / 2 + H;
+    // coarse tile: rows [I0 - CHY, I0 - CHY + CR), cols [J0 - CHX, J0 - CHX + CC)
     static constexpr int CHY = H / 2 + L - 1;
-    static constexpr int CR = kTY / 2 + CHY + H / 2 + L;
+    static constexpr int CR = IW + 2 * L - 1;
     static constexpr int CHX = round_up(H / 2 + L - 1, VW);
     static constexpr int CXE = round_up(H / 2 + L, VW);
-    static constexpr int CC = kTX / 2 + CHX + CXE;
-    static constexpr size_t smem = (2ull * R * SP + (size_t)CR * CC + (size_t)CR * SP) * sizeof(T);
+    static constexpr int CC = TX / 2 + CHX + CXE;
+    static constexpr int FW = TX + 2 * H;  // fine columns refined, v in [-H, TX + H)
+    static constexpr int U = cmax(2 * A, CR * CC);  // coarse tile, then b (after the row pass)
+    static constexpr size_t smem = (2ull * A + U + (size_t)CR * FW) * sizeof(T);
+    static_assert(JW % NJ == 0 && IW % NJ == 0, "runs must tile the refined range");
 };
 
 template <typename T, int NU>
@@ -195,78 +288,83 @@ __global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__r
                                                  const T *__restrict__ b, const T *__restrict__ ec,
                                                  const T *__restrict__ extra, int n, FirTaps taps) {
     using Cfg = UpCfg<T, NU>;
-    constexpr int H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C, SP = Cfg::SP, L = Cfg::L;
-    constexpr int CHY = Cfg::CHY, CR = Cfg::CR, CHX = Cfg::CHX, CC = Cfg::CC;
+    constexpr int TY = Cfg::TY, TX = Cfg::TX, NJ = Cfg::NJ, H = Cfg::H, HX = Cfg::HX, R = Cfg::R,
+                  C = Cfg::C, CK = Cfg::CK, A = Cfg::A, L = Cfg::L, JW = Cfg::JW, IW = Cfg::IW,
+                  CHY = Cfg::CHY, CR = Cfg::CR, CHX = Cfg::CHX, CC = Cfg::CC, FW = Cfg::FW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *xs = reinterpret_cast<T *>(smem_raw);
-    T *bs = xs + R * SP;
-    T *cs = bs + R * SP;   // coarse tile [CR][CC]
-    T *rs = cs + CR * CC;  // row-refined coarse rows [CR][SP]
-    const int ty0 = blockIdx.y * kTY, tx0 = blockIdx.x * kTX;
+    T *X = reinterpret_cast<T *>(smem_raw);  // red at X, black at X + A
+    T *cs = X + 2 * A;                          // coarse tile [CR][CC] (row pass only)
+    T *B = X + 2 * A;                           // b, loaded over cs after the row pass
+    T *rs = X + 2 * A + Cfg::U;                 // x-refined coarse rows [CR][FW]
+    const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
     const int nc = n >> 1;
 
-    load_tile<T, R, C, SP>(xs, x, n, ty0 - H, tx0 - HX);
-    if (NU > 0) load_tile<T, R, C, SP>(bs, b, n, ty0 - H, tx0 - HX);
+    load_split<T, R, C>(X, X + A, x, n, ty0 - H, tx0 - HX);
     load_tile<T, CR, CC, CC>(cs, ec, nc, ty0 / 2 - CHY, tx0 / 2 - CHX);
     __syncthreads();
 
-    // refine along x: fine logical column v in [-H, TX+H) for every coarse row
-    constexpr int FW = kTX + 2 * H;
-    for (int idx = threadIdx.x; idx < CR * FW; idx += blockDim.x) {
-        const int cr = idx / FW, vv = idx - cr * FW;
-        const int v = vv - H;
-        const T *row = cs + cr * CC;
-        T val;
-        if ((v & 1) == 0) {
-            val = row[CHX + (v >> 1)];
-        } else {
-            const int cb = CHX + ((v - 1) >> 1);
+    // refine along x: coarse row cr, midpoints of J0..J0+NJ-1 (and the nodes)
+    constexpr int NRUN = JW / NJ;
+    for (int item = threadIdx.x; item < CR * NRUN; item += blockDim.x) {
+        const int cr = item / NRUN, jr = item - cr * NRUN;
+        const int J0 = -H / 2 + jr * NJ;
+        const T *w = cs + cr * CC + CHX + J0;  // w[m] = e_c[J0 + m]
+        T *out = rs + cr * FW + 2 * J0 + H;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
             T acc = T(0);
 #pragma unroll
-            for (int k = L; k >= 1; --k) acc += Prec<T>::tap(taps, k) * (row[cb + k] + row[cb + 1 - k]);
-            val = acc;
+            for (int k = L; k >= 1; --k) acc += Prec<T>::tap(taps, k) * (w[j + k] + w[j + 1 - k]);
+            out[2 * j] = w[j];
+            out[2 * j + 1] = acc;
         }
-        rs[cr * SP + HX + v] = val;
     }
     __syncthreads();
-    // refine along y and add: fine logical rows u in [-H, TY+H)
-    constexpr int FH = kTY + 2 * H;
-    for (int idx = threadIdx.x; idx < FH * FW; idx += blockDim.x) {
-        const int uu = idx / FW, vv = idx - uu * FW;
-        const int u = uu - H, v = vv - H;
-        const int col = HX + v;
-        T val;
-        if ((u & 1) == 0) {
-            val = rs[(CHY + (u >> 1)) * SP + col];
-        } else {
-            const int rb = CHY + ((u - 1) >> 1);
+    if (NU > 0) load_split<T, R, C>(B, B + A, b, n, ty0 - H, tx0 - HX);
+    // refine along y and add: fine column v, rows 2I and 2I+1 for I in the run
+    constexpr int NIRUN = IW / NJ;
+    for (int item = threadIdx.x; item < FW * NIRUN; item += blockDim.x) {
+        const int ir = item / FW, vv = item - ir * FW;
+        const int I0 = -H / 2 + ir * NJ;
+        const T *w = rs + (CHY + I0) * FW + vv;  // w[m * FW] = refined row I0 + m
+        const int v = vv - H;
+        const int c = v + HX;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
             T acc = T(0);
 #pragma unroll
             for (int k = L; k >= 1; --k)
-                acc += Prec<T>::tap(taps, k) * (rs[(rb + k) * SP + col] + rs[(rb + 1 - k) * SP + col]);
-            val = acc;
+                acc += Prec<T>::tap(taps, k) * (w[(j + k) * FW] + w[(j + 1 - k) * FW]);
+            const int u = 2 * (I0 + j);
+            T ve = w[j * FW], vo = acc;
+            if (extra) {
+                const size_t gc = (size_t)((tx0 + v) & (n - 1));
+                ve += extra[(size_t)((ty0 + u) & (n - 1)) * n + gc];
+                vo += extra[(size_t)((ty0 + u + 1) & (n - 1)) * n + gc];
+            }
+            const int r = u + H;
+            const int q = (r + c) & 1;  // colour of (r, c); (r + 1, c) has the other
+            X[q * A + r * CK + (c >> 1)] += ve;
+            X[(q ^ 1) * A + (r + 1) * CK + (c >> 1)] += vo;
         }
-        if (extra) val += extra[(size_t)((ty0 + u) & (n - 1)) * n + ((tx0 + v) & (n - 1))];
-        xs[(u + H) * SP + col] += val;
     }
     __syncthreads();
-    const int c_off = HX - H;
 #pragma unroll 1
     for (int s = 0; s < NU; ++s) {
 #pragma unroll 1
-        for (int colour = 0; colour < 2; ++colour) {
-            const int k = 2 * s + colour + 1;
-            half_sweep<T, SP>(xs, bs, k, R - k, c_off + k, C - c_off - k, colour);
+        for (int q = 0; q < 2; ++q) {
+            const int j = 2 * s + q + 1;
+            half_sweep<CK, A>(X, B, j, R - j, q);
             __syncthreads();
         }
     }
-    store_tile<T, SP>(xout, xs, n, ty0, tx0, H, HX);
+    store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
 }
 
 // ---------------------------------------------------------------------------
 // k_bottom: a whole V-cycle on grids <= 64 x 64, one block, shared memory.
 // ---------------------------------------------------------------------------
-constexpr int kBottomThreads = 512;
+constexpr int kBottomThreads = 1024;
 
 template <typename T>
 __device__ __forceinline__ void sweep_periodic(T *X, const T *B, int m, int colour) {
@@ -333,15 +431,19 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ x, co
         }
         __syncthreads();
     }
-    {   // coarsest grid: e = A~^+ b (the pseudo-inverse annihilates the mean)
+    {   // coarsest grid: e = A~^+ b (the pseudo-inverse annihilates the mean).
+        // tpo threads per output row take strided partial dot products (coalesced
+        // loads, all issued in parallel), then a shuffle tree within the group.
         const int mcst = n >> (nlev - 1), Nc = mcst * mcst;
         T *Xc = X[nlev - 1];
         const T *Bc = B[nlev - 1];
-        for (int p = tid; p < Nc; p += nt) {
-            T acc = T(0);
-            for (int q = 0; q < Nc; ++q) acc += ainv[p * Nc + q] * Bc[q];
-            Xc[p] = acc;
-        }
+        const int tpo = min(32, nt / Nc);  // powers of two: groups never straddle a warp
+        const int p = tid / tpo, lane = tid - p * tpo;
+        T acc = T(0);
+        if (p < Nc)
+            for (int q = lane; q < Nc; q += tpo) acc += ainv[p * Nc + q] * Bc[q];
+        for (int o = tpo >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, tpo);
+        if (p < Nc && lane == 0) Xc[p] = acc;
         __syncthreads();
     }
     constexpr int L = Prec<T>::L;
@@ -459,10 +561,50 @@ __global__ void __launch_bounds__(kRedThreads) k_update(double *__restrict__ x,
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_project(double *__restrict__ x, size_t N,
-                                                         const double *__restrict__ sum) {
+                                                         const double *__restrict__ sum,
+                                                         const int *__restrict__ zero_flag) {
+    const bool zero = zero_flag && *zero_flag;
     const double mu = *sum / (double)N;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
-        x[p] -= mu;
+        x[p] = zero ? 0.0 : x[p] - mu;
+}
+
+__global__ void k_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
+                        double n2, double h2, double tol, int step, int max_cycles, int first,
+                        cudaGraphConditionalHandle handle) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (first) {
+        st->fnorm = sqrt(rsum[1]);
+        st->mu = fsum[0] / n2;
+        st->cycles = 0;
+        st->outer = 0;
+        st->status = MG_OK;
+        st->zero_source = 0;
+        st->unorm = 0.0;
+    } else {
+        st->cycles += step;
+        st->outer += 1;
+        if (usum) st->unorm = sqrt(usum[0]);
+    }
+    const double rn = sqrt(rsum[0]) / h2, fn = st->fnorm;
+    unsigned go = 0;
+    if (!isfinite(rn) || !isfinite(fn)) {
+        st->status = MG_ERR_NONFINITE;
+        st->rel = rn / fn;
+    } else if (fn == 0.0) {
+        st->zero_source = 1;
+        st->rel = 0.0;
+    } else {
+        const double rel = rn / fn;
+        st->rel = rel;
+        if (rel > tol) {
+            if (st->cycles + step <= max_cycles)
+                go = 1;
+            else
+                st->status = MG_ERR_NOT_CONVERGED;
+        }
+    }
+    cudaGraphSetConditional(handle, go);
 }
 
 template <typename KernelT>
@@ -471,13 +613,28 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// set_smem once per (kernel instantiation, device): `done` is that
+// instantiation's bit mask of devices already configured.
+template <typename KernelT>
+cudaError_t set_smem_once(KernelT k, size_t bytes, std::atomic<unsigned> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = dev < 32 ? (1u << dev) : 0u;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    e = set_smem(k, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_relaxed);
+    return e;
+}
+
 template <typename T, int NU, bool ZERO>
 cudaError_t down_impl(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_t s) {
     using Cfg = DownCfg<T, NU>;
     auto k = k_down<T, NU, ZERO>;
-    cudaError_t e = set_smem(k, Cfg::smem);
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = set_smem_once(k, Cfg::smem, done);
     if (e != cudaSuccess) return e;
-    dim3 grid(n / kTX, n / kTY);
+    dim3 grid(n / Cfg::TX, n / Cfg::TY);
     k<<<grid, kThreads, Cfg::smem, s>>>(x, xout, b, n, bc);
     count_launches(1);
     return cudaGetLastError();
@@ -488,9 +645,10 @@ cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra
                     const FirTaps &taps, cudaStream_t s) {
     using Cfg = UpCfg<T, NU>;
     auto k = k_up<T, NU>;
-    cudaError_t e = set_smem(k, Cfg::smem);
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = set_smem_once(k, Cfg::smem, done);
     if (e != cudaSuccess) return e;
-    dim3 grid(n / kTX, n / kTY);
+    dim3 grid(n / Cfg::TX, n / Cfg::TY);
     k<<<grid, kThreads, Cfg::smem, s>>>(x, xout, b, ec, extra, n, taps);
     count_launches(1);
     return cudaGetLastError();
@@ -501,7 +659,7 @@ cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra
 template <typename T>
 cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zero_init, T *bc,
                         cudaStream_t s) {
-    if (n < kTX || n % kTX || n % kTY || x == xout) return cudaErrorInvalidValue;
+    if (n < Tile<T>::TY || n < Tile<T>::TX || x == xout) return cudaErrorInvalidValue;
 #define MG_DOWN_CASE(NU)                                                                  \
     case NU:                                                                              \
         return zero_init ? down_impl<T, NU, true>(x, xout, b, n, bc, s)                   \
@@ -520,7 +678,7 @@ cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zer
 template <typename T>
 cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
                       const FirTaps &taps, cudaStream_t s, const T *extra) {
-    if (n < kTX || n % kTX || n % kTY || !ec || x == xout) return cudaErrorInvalidValue;
+    if (n < Tile<T>::TY || n < Tile<T>::TX || !ec || x == xout) return cudaErrorInvalidValue;
     switch (nu) {
         case 0: return up_impl<T, 0>(x, xout, b, ec, extra, n, taps, s);
         case 1: return up_impl<T, 1>(x, xout, b, ec, extra, n, taps, s);
@@ -545,7 +703,11 @@ cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu
     elems += (size_t)n * n;
     const size_t smem = elems * sizeof(T);
     auto k = k_bottom<T>;
-    cudaError_t e = set_smem(k, smem);
+    // configure once for the largest bottom configuration (64^2 down to 4^2)
+    size_t max_elems = (size_t)kBottomMax * kBottomMax;
+    for (int m = kBottomMax; m >= 4; m >>= 1) max_elems += 2ull * m * m;
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = set_smem_once(k, max_elems * sizeof(T), done);
     if (e != cudaSuccess) return e;
     k<<<1, kBottomThreads, smem, s>>>(x, b, n, nlev, nu1, nu2, zero_init ? 1 : 0, ainv, taps);
     count_launches(1);
@@ -601,10 +763,46 @@ cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaS
     count_launches(1);
     return cudaGetLastError();
 }
-cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s) {
-    k_project<<<kRedBlocks, kRedThreads, 0, s>>>(x, (size_t)n * n, sum);
+cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag) {
+    k_project<<<kRedBlocks, kRedThreads, 0, s>>>(x, (size_t)n * n, sum, zero_flag);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
+                         double n2, double h2, double tol, int step, int max_cycles, bool first,
+                         cudaGraphConditionalHandle handle, cudaStream_t s) {
+    k_check<<<1, 32, 0, s>>>(st, rsum, usum, fsum, n2, h2, tol, step, max_cycles, first ? 1 : 0, handle);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T, int NU>
+static cudaError_t prepare_nu() {
+    cudaError_t e = set_smem(k_down<T, NU, true>, DownCfg<T, NU>::smem);
+    if (e == cudaSuccess) e = set_smem(k_down<T, NU, false>, DownCfg<T, NU>::smem);
+    if (e == cudaSuccess) e = set_smem(k_up<T, NU>, UpCfg<T, NU>::smem);
+    return e;
+}
+
+template <typename T>
+static cudaError_t prepare_type() {
+    cudaError_t e = prepare_nu<T, 0>();
+    if (e == cudaSuccess) e = prepare_nu<T, 1>();
+    if (e == cudaSuccess) e = prepare_nu<T, 2>();
+    if (e == cudaSuccess) e = prepare_nu<T, 3>();
+    if (e == cudaSuccess) e = prepare_nu<T, 4>();
+    // the bottom kernel's largest configuration: 64^2 down to 4^2
+    size_t elems = (size_t)kBottomMax * kBottomMax;
+    for (int m = kBottomMax; m >= 4; m >>= 1) elems += 2ull * m * m;
+    if (e == cudaSuccess) e = set_smem(k_bottom<T>, elems * sizeof(T));
+    return e;
+}
+
+cudaError_t prepare_kernels() {
+    cudaError_t e = prepare_type<float>();
+    if (e == cudaSuccess) e = prepare_type<double>();
+    return e;
 }
 
 }  // namespace mg

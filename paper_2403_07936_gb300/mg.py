@@ -38,6 +38,7 @@ SIGNATURES = {
     "mg_setup": (_I, [_I, _I, C.POINTER(_VP)]),
     "mg_set_options": (_I, [_VP, _I, _I, _I, _I, _VP]),
     "mg_set_inner_cycles": (_I, [_VP, _I]),
+    "mg_set_graph_execution": (_I, [_VP, _I]),
     "mg_load_prolong_weights": (_I, [_VP, _VP, _SZ]),
     "mg_solve": (_I, [_VP, _VP, _VP, _D, _I, C.POINTER(SolveInfo)]),
     "mg_vcycle": (_I, [_VP, _VP, _VP, _I]),
@@ -167,6 +168,10 @@ class Context:
         if inner_cycles is not None:
             o.inner_cycles = inner_cycles
             _check(lib.mg_set_inner_cycles(self._h, inner_cycles))
+
+    def set_graph_execution(self, enable: bool):
+        """Run mg_solve as one CUDA graph launch (True, default) or a host loop."""
+        _check(load().mg_set_graph_execution(self._h, int(bool(enable))))
 
     def load_weights(self, blob: bytes):
         buf = C.create_string_buffer(bytes(blob), len(blob))

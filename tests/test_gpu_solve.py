@@ -43,13 +43,15 @@ def _check_solution(f, x, tol=1e-10, err_bound=1e-9, x_ref=None):
     return rel, err
 
 
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("n,coarsest", [(64, 8), (128, 8), (256, 4), (512, 16)])
-def test_solve_matches_oracle(mg, precision, n, coarsest):
+def test_solve_matches_oracle(mg, precision, n, coarsest, graphs):
     f = turbulent_source(n, default_kmax(n), config_seed(0, n))
     ft = torch.tensor(f, device=DEV)
     xt = torch.zeros_like(ft)
     ctx = mg.Context(_levels(n, coarsest), n, precision=precision)
+    ctx.set_graph_execution(graphs)
     info = ctx.solve(ft, xt, tol=1e-10)
     assert info["rel_residual"] <= 1e-10
     x_ref, oinfo = omg.solve(f, tol=1e-10, coarsest=coarsest)
@@ -112,10 +114,12 @@ def test_solve_is_deterministic(mg):
     assert torch.equal(a, b)
 
 
-def test_warm_start_and_nonzero_mean(mg):
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
+def test_warm_start_and_nonzero_mean(mg, graphs):
     n = 256
     f = turbulent_source(n, 32, 5)
     ctx = mg.Context(6, n)
+    ctx.set_graph_execution(graphs)
     ft = torch.tensor(f + 2.5, device=DEV)  # the mean is projected out and reported
     xt = torch.zeros_like(ft)
     info = ctx.solve(ft, xt, tol=1e-10)
@@ -131,9 +135,11 @@ def test_warm_start_and_nonzero_mean(mg):
     _check_solution(g, xt.cpu().numpy())
 
 
-def test_degenerate_sources(mg):
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
+def test_degenerate_sources(mg, graphs):
     n = 128
     ctx = mg.Context(5, n)
+    ctx.set_graph_execution(graphs)
     zt = torch.zeros((n, n), dtype=torch.float64, device=DEV)
     xt = torch.ones_like(zt)
     info = ctx.solve(zt, xt)
@@ -148,12 +154,14 @@ def test_degenerate_sources(mg):
     assert e.value.status == 8  # MG_ERR_NONFINITE
 
 
-def test_not_converged_reports_status(mg):
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
+def test_not_converged_reports_status(mg, graphs):
     n = 256
     f = turbulent_source(n, 32, 9)
     ft = torch.tensor(f, device=DEV)
     xt = torch.zeros_like(ft)
     ctx = mg.Context(6, n, precision="fp64", max_cycles=2)
+    ctx.set_graph_execution(graphs)
     info = ctx.solve(ft, xt, tol=1e-10, check=False)
     assert info["status"] == "MG_ERR_NOT_CONVERGED" and info["vcycles"] == 2
     assert 1e-10 < info["rel_residual"] < 1e-2
@@ -184,3 +192,28 @@ def test_vcycle_entry_point_matches_oracle_cycle(mg):
     for _ in range(2):
         xr = omg.vcycle(xr, f - f.mean(), h)
     assert np.abs(xt.cpu().numpy() - xr).max() <= 1e-11 * np.abs(xr).max()
+
+
+def test_graph_and_host_loop_give_identical_results(mg):
+    """Same kernels in the same order: the two execution modes agree bit for bit,
+    and the launch counter credits every replayed kernel."""
+    n = 1024
+    f = turbulent_source(n, 128, 21)
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(8, n)
+    a = torch.zeros_like(ft)
+    b = torch.zeros_like(ft)
+    ctx.set_graph_execution(False)
+    l0 = mg.kernel_launches()
+    ia = ctx.solve(ft, a)
+    la = mg.kernel_launches() - l0
+    ctx.set_graph_execution(True)
+    ctx.solve(ft, b)  # records the graph
+    b.zero_()
+    l0 = mg.kernel_launches()
+    ib = ctx.solve(ft, b)
+    lb = mg.kernel_launches() - l0
+    assert torch.equal(a, b)
+    assert ia["vcycles"] == ib["vcycles"] and ia["outer_iters"] == ib["outer_iters"]
+    # the graph adds one convergence-test kernel per residual evaluation
+    assert la > 0 and lb == la + ib["outer_iters"] + 1
