@@ -94,8 +94,7 @@ mg_status mg_set_inner_cycles(mg_ctx *ctx, int inner_cycles);
 mg_status mg_set_graph_execution(mg_ctx *ctx, int enable);
 
 /* Load super-resolution generator weights (Sec. 2.3, Fig. 1b).  The blob is
- * copied (the caller keeps ownership).  Blob layout: see mg_sr.h-style
- * description in the library documentation: a 64-byte header
+ * copied (the caller keeps ownership).  Blob layout: a 64-byte header
  * {magic "MGSRW001", u32 n_feat, u32 n_blocks, u32 n_params, 44 bytes 0}
  * followed by n_params little-endian float32 values in the order
  * in.w, in.b, in.a, then per block w1, b1, a, w2, b2, then up.w, up.b, up.a,
@@ -190,6 +189,26 @@ mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, i
  * overlap on the GPU (unordered streams) race.  Asynchronous on `stream`. */
 mg_status mg_op_vcycle_static(int dtype, int n, int coarsest, void *x, const void *b, int nu1,
                               int nu2, int zero_init, void *stream);
+
+/* One 3x3 convolution of the SR generator (Sec. 2.3, Fig. 1b) on the tensor
+ * cores: BF16 operands, FP32 accumulation, BF16 output.  Activations are
+ * channels-last with 64 channels and a one-pixel periodic halo: an H x W grid
+ * is (H+2) x (W+2) x 64 bf16, pixel (y, x) at padded (y+1, x+1), halo entries
+ * holding the wrapped neighbours (the output's halo is written too).  W must
+ * be a multiple of 128.  w_packed: bf16 [groups][9 taps (ky*3+kx)][64 co][64 ci]
+ * (groups = 4 for mode 2).  mode 0: out = PReLU(conv(in) + bias) with prelu[64];
+ * mode 1: out = skip + conv(in) + bias (residual block end); mode 2 (pixel
+ * shuffle): group g computes fine channel c at sub-pixel (g >> 1, g & 1) of a
+ * 2H x 2W padded output, out = PReLU_c(conv(in) + bias[g][c]).  bias holds
+ * groups x 64 floats.  Synchronous; MG_ERR_TIMEOUT if a bounded wait expired. */
+mg_status mg_op_sr_conv(int mode, int H, int W, const void *in, const void *skip, const void *w_packed,
+                        const float *bias, const float *prelu, void *out, void *stream);
+
+/* The SR correction s * G(ec / s), s = max|ec|, for a coarse error ec
+ * (nc x nc floats, device) with the context's loaded weights, written to out
+ * (2nc x 2nc floats, device).  nc a multiple of 128.  Synchronous on the
+ * context's stream. */
+mg_status mg_op_sr_generator(mg_ctx *ctx, const float *ec, int nc, float *out);
 
 /* FP64 outer residual: s = h^2 (f - mu) - (4x - sum nbrs) (so s = h^2 r),
  * written as float to s32 when s32 != NULL; out[0] = sum s^2,

@@ -615,6 +615,8 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     }
     const bool mixed = c->prec == MG_PREC_MIXED;
     MG_TRY(ensure_hierarchy(c, !mixed));
+    if (prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax)
+        MG_TRY(sr_prepare(&c->sr, c->lv[1].n, g_err, sizeof g_err));
     const double *fd;
     double *xd;
     bool staged;
@@ -728,6 +730,8 @@ mg_status mg_vcycle(mg_ctx *c, const double *f, double *x, mg_prolong prolong) {
     MG_TRY(check_common(c, f, x, prolong));
     const bool mixed = c->prec == MG_PREC_MIXED;
     MG_TRY(ensure_hierarchy(c, !mixed));
+    if (prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax)
+        MG_TRY(sr_prepare(&c->sr, c->lv[1].n, g_err, sizeof g_err));
     const double *fd;
     double *xd;
     bool staged;
@@ -906,6 +910,36 @@ mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, i
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d);
     MG_CUDA(e);
+    return MG_OK;
+}
+
+mg_status mg_op_sr_conv(int mode, int H, int W, const void *in, const void *skip, const void *w_packed,
+                        const float *bias, const float *prelu, void *out, void *stream) {
+    if (!in || !w_packed || !bias || !out) {
+        set_err("null pointer");
+        return MG_ERR_INVALID_ARG;
+    }
+    return sr_conv_layer(mode, H, W, in, skip, w_packed, bias, prelu, out, (cudaStream_t)stream, g_err,
+                         sizeof g_err);
+}
+
+mg_status mg_op_sr_generator(mg_ctx *c, const float *ec, int nc, float *out) {
+    if (!c || !ec || !out) {
+        set_err("null pointer");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    MG_TRY(sr_prepare(&c->sr, nc, g_err, sizeof g_err));
+    MG_CUDA(cudaMemsetAsync(c->sr.err, 0, sizeof(int), c->stream));
+    MG_TRY(sr_correction(&c->sr, ec, nc, c->stream, g_err, sizeof g_err));
+    MG_CUDA(cudaMemcpyAsync(out, c->sr.fine_out, sizeof(float) * 4 * nc * nc, cudaMemcpyDeviceToDevice, c->stream));
+    int flag = 0;
+    MG_CUDA(cudaMemcpyAsync(&flag, c->sr.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+    if (flag) {
+        set_err("a bounded wait in the tensor-core convolution timed out");
+        return MG_ERR_TIMEOUT;
+    }
     return MG_OK;
 }
 

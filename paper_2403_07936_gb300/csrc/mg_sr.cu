@@ -1,13 +1,504 @@
-// mg_sr.cu - super-resolution prolongation: weight loading and generator.
-#include <stdint.h>
+// mg_sr.cu - super-resolution prolongation: weight loading and generator
+// kernels (Sec. 2.3, Fig. 1b; Sec. 3.1; Appendix A, Algorithm 5).
+//
+// The 64 -> 64 and 64 -> 256 convolutions run as implicit GEMMs on the
+// tcgen05 tensor cores (BF16 operands, FP32 accumulation in tensor memory):
+// for an output tile of 128 pixels of one row, D[pixel][co] = sum over the 9
+// taps (dy, dx) and 64 input channels of In[row y+dy][pixel+dx][ci] *
+// W[tap][co][ci].  A persistent block walks a vertical strip of tiles: the
+// three input rows a tile needs are TMA-loaded into a ring of four row slots,
+// so each new output row costs one new input row.  A staged row is stored as
+// eight 8-channel planes of [pixel][8 channels] (no swizzle), so the x-shifted
+// tap operands are descriptors offset by 16 * dx bytes into the staged row;
+// the weights use the 128-byte swizzled K-major layout.
+// Thread 0 issues the TMA loads and the 36 MMAs per tile; the tile's
+// accumulator (one of two 64-column TMEM buffers) is drained by all four warps
+// while the next tile's MMAs run.  Every wait on an mbarrier is bounded by a
+// wall-clock limit and reports MG_ERR_TIMEOUT through a device flag.
+// The 1 -> 64 and 64 -> 1 layers are too thin for tensor cores (K = 9 and
+// N = 1) and run on the CUDA cores.
+#include <cuda_bf16.h>
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
+#include "mg_internal.cuh"
 #include "mg_sr.cuh"
 
 namespace mg {
 
 namespace {
+
+constexpr int C = kSrFeat;            // channels
+constexpr int TM = 128;               // pixels per tile (one row segment)
+constexpr int ROWPX = TM + 2;         // staged pixels per input row
+constexpr int ROWBYTES = ROWPX * C * 2;
+// one 8-channel plane of a staged row, [pixel][8 ch] (130 x 16 bytes), padded
+// to a 128-byte multiple so that every TMA destination is 128-byte aligned
+constexpr int PLANE = 2176;
+constexpr int ROWSLOT = 8 * PLANE;    // 17 KiB slots, 1024-byte multiple
+static_assert(PLANE >= ROWPX * 16 && PLANE % 128 == 0, "plane pitch");
+constexpr int NSLOT = 4;              // ring of staged input rows
+constexpr int WBYTES = 9 * C * C * 2;  // one layer's weights, 72 KiB
+constexpr int TAPBYTES = C * C * 2;    // one tap: 64 rows (co) x 128 bytes (ci)
+constexpr int TMEM_COLS = 128;        // two 64-column FP32 accumulators
+constexpr int CONV_THREADS = 128;
+constexpr size_t CONV_SMEM = 1024 + WBYTES + NSLOT * ROWSLOT + 128;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
+
+enum { MODE_PRELU = 0, MODE_RESID = 1, MODE_SHUFFLE = 2 };
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Wait for the phase with the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptors (K-major operands).
+// B (weights): 128-byte swizzle, rows of 128 bytes, 8-row groups 1024 bytes
+// apart, start on a 1024-byte boundary plus the 32-byte step of the K slice.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+// A (activations): no swizzle, core matrices of 8 pixels x 16 bytes.  A staged
+// row is 8 planes (one per 8 channels) of [pixel][8 ch]; consecutive pixels
+// are 16 bytes apart, so 8-pixel core matrices are 128 bytes apart (stride
+// offset) and the next 8 channels are one plane further (leading offset).  A
+// view shifted by dx pixels simply starts 16 * dx bytes later.
+__device__ __forceinline__ uint64_t sdesc_planes(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+    d |= (uint64_t)(PLANE >> 4) << 16;          // leading byte offset: next 8 channels
+    d |= (uint64_t)(128 >> 4) << 32;            // stride byte offset: next 8 pixels
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    return d;                                   // layout type 0: no swizzle
+}
+// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major,
+// M = 128, N = 64.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+// 32 lanes x 32 columns of 32-bit values: thread (lane) gets its row's 32 columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Store one pixel's 64 bf16 channels (8 x 16 bytes) at (y, x) of a padded
+// H x W grid, and at every halo position that wraps onto it.
+__device__ __forceinline__ void store_px(__nv_bfloat16 *out, int H, int W, int y, int x, const uint4 *d) {
+    const int rows[2] = {y + 1, y == 0 ? H + 1 : (y == H - 1 ? 0 : -1)};
+    const int cols[2] = {x + 1, x == 0 ? W + 1 : (x == W - 1 ? 0 : -1)};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        if (rows[a] < 0) continue;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (cols[b] < 0) continue;
+            uint4 *p = reinterpret_cast<uint4 *>(out + ((size_t)rows[a] * (W + 2) + cols[b]) * C);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) p[i] = d[i];
+        }
+    }
+}
+
+struct ConvArgs {
+    const __nv_bfloat16 *skip;  // MODE_RESID: residual input (padded), else null
+    __nv_bfloat16 *out;         // padded output (coarse, or fine for MODE_SHUFFLE)
+    const float *bias;          // [groups][64]
+    const float *prelu;         // [64] (MODE_PRELU, MODE_SHUFFLE)
+    int H, W;                   // coarse grid; W a multiple of 128
+    int layer;                  // weight layer of group 0
+    int chunks;                 // row chunks per (group, column block) strip
+    int rows_per_chunk;
+    int *err;
+};
+
+// ---------------------------------------------------------------------------
+// k_conv_tc: persistent implicit-GEMM 3x3 convolution, 64 -> 64 channels per
+// group, on tcgen05.  Block b handles strip b / chunks = (group, column
+// block) and rows [chunk * rows_per_chunk, ...) of it.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
+              ConvArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *wsm = sm;
+    unsigned char *rows = sm + WBYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(rows + NSLOT * ROWSLOT);
+    uint64_t *wbar = bars, *full = bars + 1, *mdone = bars + 1 + NSLOT;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 8);
+    int *abort_flag = reinterpret_cast<int *>(bars + 9);
+
+    const int NB = a.W / TM;
+    const int strip = blockIdx.x / a.chunks, chunk = blockIdx.x - strip * a.chunks;
+    const int g = strip / NB, cb = strip - g * NB;
+    const int y_a = chunk * a.rows_per_chunk;
+    const int y_b = min(a.H, y_a + a.rows_per_chunk);
+    if (y_a >= y_b) return;  // uniform across the block, before any barrier or TMEM use
+    const int T = y_b - y_a;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(wbar, 1);
+        for (int s = 0; s < NSLOT; ++s) mbar_init(&full[s], 1);
+        mbar_init(&mdone[0], 1);
+        mbar_init(&mdone[1], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // loads in flight per slot (for the bounded drain on abort)
+    int loaded_rows = 0;
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(wbar, WBYTES);
+        tma_load_4d(wsm, &tm_w, wbar, 0, 0, 0, a.layer + g);
+        for (int r = 0; r < NSLOT; ++r) {
+            const int pr = y_a + r;  // padded input row
+            if (pr <= y_b + 1) {
+                const int slot = pr % NSLOT;
+                mbar_expect_tx(&full[slot], ROWBYTES);
+                for (int q = 0; q < 8; ++q)
+                    tma_load_3d(rows + slot * ROWSLOT + q * PLANE, &tm_in, &full[slot], 8 * q, cb * TM, pr);
+                ++loaded_rows;
+            }
+        }
+        if (!mbar_wait(wbar, 0)) *abort_flag = 1;
+    }
+
+    const float *bias = a.bias + g * C;
+    for (int t = 0; t <= T; ++t) {
+        if (threadIdx.x == 0 && t < T && !*abort_flag) {
+            const int y = y_a + t;
+            bool ok = true;
+            for (int dy = 0; dy < 3 && ok; ++dy) {
+                const int pr = y + dy;
+                ok = mbar_wait(&full[pr % NSLOT], ((pr - y_a) / NSLOT) & 1);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+            } else {
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)((t & 1) * C);
+                const uint32_t wbase = smem_u32(wsm), rbase = smem_u32(rows);
+#pragma unroll 1
+                for (int dy = 0; dy < 3; ++dy) {
+                    const uint32_t row = rbase + (uint32_t)(((y + dy) % NSLOT) * ROWSLOT);
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = sdesc_planes(row + 2 * kk * PLANE + dx * 16);
+                            const uint64_t bd = sdesc_sw128(wbase + (dy * 3 + dx) * TAPBYTES + kk * 32);
+                            mma_bf16(d, ad, bd, (dy | dx | kk) ? 1u : 0u);
+                        }
+                }
+                mma_commit(&mdone[t & 1]);
+            }
+        }
+        if (t > 0) {
+            const int tp = t - 1;
+            __syncthreads();  // abort_flag from thread 0 is visible
+            const bool aborted = *abort_flag != 0;
+            bool ok = !aborted && mbar_wait(&mdone[tp & 1], (tp >> 1) & 1);
+            if (!ok) {
+                if (threadIdx.x == 0) *abort_flag = 1;
+            } else {
+                tc_fence_after();
+                if (threadIdx.x == 0) {  // the slot of padded row y_a + tp is free: prefetch
+                    const int pr = y_a + tp + NSLOT;
+                    if (pr <= y_b + 1) {
+                        const int slot = pr % NSLOT;
+                        mbar_expect_tx(&full[slot], ROWBYTES);
+                        for (int q = 0; q < 8; ++q)
+                            tma_load_3d(rows + slot * ROWSLOT + q * PLANE, &tm_in, &full[slot], 8 * q,
+                                        cb * TM, pr);
+                        ++loaded_rows;
+                    }
+                }
+                // epilogue of tile tp: warp w drains TMEM lanes 32w..32w+31
+                const int y = y_a + tp;
+                const int x = cb * TM + warp * 32 + lane;
+                const uint32_t taddr = tmem + (uint32_t)((tp & 1) * C) + ((uint32_t)(warp * 32) << 16);
+                float v[C];
+                tmem_ld32(taddr, v);
+                tmem_ld32(taddr + 32, v + 32);
+                tmem_wait_ld();
+                if (MODE == MODE_RESID) {
+                    const uint4 *sp = reinterpret_cast<const uint4 *>(
+                        a.skip + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint4 q = sp[i];
+                        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
+                            v[i * 8 + 2 * k] += f.x;
+                            v[i * 8 + 2 * k + 1] += f.y;
+                        }
+                    }
+                }
+                uint4 outv[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int c0 = i * 8 + 2 * k;
+                        float v0 = v[c0] + bias[c0], v1 = v[c0 + 1] + bias[c0 + 1];
+                        if (MODE == MODE_RESID) {  // skip already added; bias after the sum
+                        } else {
+                            v0 = v0 > 0.f ? v0 : a.prelu[c0] * v0;
+                            v1 = v1 > 0.f ? v1 : a.prelu[c0 + 1] * v1;
+                        }
+                        const __nv_bfloat162 bb = __floats2bfloat162_rn(v0, v1);
+                        w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
+                    }
+                    outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
+                if (MODE == MODE_SHUFFLE)
+                    store_px(a.out, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), outv);
+                else
+                    store_px(a.out, a.H, a.W, y, x, outv);
+            }
+            tc_fence_before();
+            __syncthreads();  // accumulator tp & 1 drained before it is reused
+            tc_fence_after();
+            if (*abort_flag) break;
+        }
+    }
+    if (*abort_flag && threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        // wait (bounded) for the last row load issued into each slot, so that
+        // no copy is still writing this block's shared memory when it exits
+        for (int r = loaded_rows - 1; r >= 0 && r >= loaded_rows - NSLOT; --r) {
+            const int pr = y_a + r;
+            mbar_wait(&full[pr % NSLOT], ((pr - y_a) / NSLOT) & 1);
+        }
+        mbar_wait(wbar, 0);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core layers and helpers
+// ---------------------------------------------------------------------------
+
+// s = max |ec| (1 when ec = 0), deterministic two-stage reduction
+__global__ void __launch_bounds__(kRedThreads) k_absmax(const float *__restrict__ ec, size_t N,
+                                                        double *partials, unsigned *counter, float *s_out) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    float m = 0.f;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(ec[p]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bm = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) bm = fmaxf(bm, (float)sh[w]);
+        partials[blockIdx.x] = bm;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        float gm = 0.f;
+        for (int b = 0; b < (int)gridDim.x; ++b) gm = fmaxf(gm, (float)((volatile double *)partials)[b]);
+        s_out[0] = gm > 0.f ? gm : 1.f;
+        *counter = 0u;
+    }
+}
+
+// conv3x3 1 -> 64 of q = ec / s, + bias, PReLU, to padded bf16; one thread per pixel.
+__global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ ec, int nc,
+                                                 const float *__restrict__ s_ptr,
+                                                 const float *__restrict__ wpack,  // w[64][9], b[64], a[64]
+                                                 __nv_bfloat16 *__restrict__ out) {
+    __shared__ float w[C * 9 + 2 * C];
+    for (int i = threadIdx.x; i < C * 11; i += blockDim.x) w[i] = wpack[i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nc * nc) return;
+    const int y = p / nc, x = p - y * nc;
+    const float s = *s_ptr;
+    float q[9];
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+            q[ky * 3 + kx] = ec[(size_t)((y + ky - 1 + nc) & (nc - 1)) * nc + ((x + kx - 1 + nc) & (nc - 1))] / s;
+    uint4 outv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = i * 8 + 2 * k + h;
+                float acc = w[C * 9 + c];
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc = fmaf(w[c * 9 + t], q[t], acc);
+                v[h] = acc > 0.f ? acc : w[C * 10 + c] * acc;
+            }
+            const __nv_bfloat162 bb = __floats2bfloat162_rn(v[0], v[1]);
+            w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
+        }
+        outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+    store_px(out, nc, nc, y, x, outv);
+}
+
+// conv3x3 64 -> 1 on the padded fine activation, + bias, times s:
+// fine_out = s * G.  A 16 x 16 tile of pixels stages its 18 x 18 x 64 window.
+constexpr int OUT_T = 16;
+__global__ void __launch_bounds__(OUT_T * OUT_T) k_conv_out(const __nv_bfloat16 *__restrict__ u, int nf,
+                                                            const float *__restrict__ wpack,  // w[9][64], b
+                                                            const float *__restrict__ s_ptr,
+                                                            float *__restrict__ fine_out) {
+    __shared__ uint4 tile[(OUT_T + 2) * (OUT_T + 2) * 8];
+    __shared__ float w[9 * C + 1];
+    for (int i = threadIdx.x; i < 9 * C + 1; i += blockDim.x) w[i] = wpack[i];
+    const int y0 = blockIdx.y * OUT_T, x0 = blockIdx.x * OUT_T;
+    // padded rows y0 .. y0+17, cols x0 .. x0+17 (pixel (y, x) is at padded (y+1, x+1))
+    for (int i = threadIdx.x; i < (OUT_T + 2) * (OUT_T + 2) * 8; i += blockDim.x) {
+        const int px = i >> 3, part = i & 7;
+        const int ry = px / (OUT_T + 2), rx = px - ry * (OUT_T + 2);
+        tile[i] = reinterpret_cast<const uint4 *>(u + ((size_t)(y0 + ry) * (nf + 2) + (x0 + rx)) * C)[part];
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / OUT_T, tx = threadIdx.x - ty * OUT_T;
+    float acc = 0.f;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            const uint4 *pp = tile + ((ty + ky) * (OUT_T + 2) + (tx + kx)) * 8;
+            const float *wt = w + (ky * 3 + kx) * C;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint4 q = pp[i];
+                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
+                    acc = fmaf(wt[i * 8 + 2 * k], f.x, acc);
+                    acc = fmaf(wt[i * 8 + 2 * k + 1], f.y, acc);
+                }
+            }
+        }
+    fine_out[(size_t)(y0 + ty) * nf + x0 + tx] = (*s_ptr) * (acc + w[9 * C]);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
 constexpr char kMagic[8] = {'M', 'G', 'S', 'R', 'W', '0', '0', '1'};
 constexpr size_t kHeader = 64;
 
@@ -18,14 +509,135 @@ size_t expected_params(int nf, int nb) {
     n += (size_t)nf * 9 + 1;                                 // out.w, out.b
     return n;
 }
+
+// bf16 round-to-nearest-even of a float (host)
+uint16_t bf16_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    return (uint16_t)((u + 0x7FFFu + lsb) >> 16);
+}
+float bf16_value(float f) {
+    const uint32_t u = (uint32_t)bf16_bits(f) << 16;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// padded activation [H+2][W+2][64] bf16 as a 3D tensor (c, x, y); a box is
+// one 8-channel plane of a staged row: 8 channels x 130 pixels x 1 row
+bool make_act_map(CUtensorMap *m, void *base, int H, int W) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)(W + 2), (cuuint64_t)(H + 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)(W + 2) * C * 2};
+    cuuint32_t box[3] = {8, (cuuint32_t)ROWPX, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// packed weights [layers][9][64 co][64 ci] bf16 as a 4D tensor; box = one layer
+bool make_w_map(CUtensorMap *m, void *base, int layers) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)C, 9, (cuuint64_t)layers};
+    cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * C * 2, (cuuint64_t)9 * C * C * 2};
+    cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)C, 9, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Opt the convolution kernels into their shared memory (current device).
+cudaError_t prepare_conv() {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<MODE_PRELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CONV_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_tc<MODE_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)CONV_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_tc<MODE_SHUFFLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)CONV_SMEM);
+    return e;
+}
+
+template <int MODE>
+cudaError_t launch_conv(const CUtensorMap &tm_in, const CUtensorMap &tm_w, ConvArgs a, int groups,
+                        cudaStream_t s) {
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int strips = groups * (a.W / TM);
+    int chunks = sms / strips;
+    if (chunks < 1) chunks = 1;
+    if (chunks > a.H) chunks = a.H;
+    a.rows_per_chunk = (a.H + chunks - 1) / chunks;
+    a.chunks = chunks;
+    k_conv_tc<MODE><<<strips * chunks, CONV_THREADS, CONV_SMEM, s>>>(tm_in, tm_w, a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t ensure_buffers(SrState *st, int nc) {
+    if (st->nc == nc && st->act[0]) return cudaSuccess;
+    for (int i = 0; i < 3; ++i) {
+        cudaFree(st->act[i]);
+        st->act[i] = nullptr;
+    }
+    cudaFree(st->fine_act);
+    cudaFree(st->fine_out);
+    st->fine_act = nullptr;
+    st->fine_out = nullptr;
+    st->nc = 0;
+    const size_t coarse = (size_t)(nc + 2) * (nc + 2) * C * 2;
+    const size_t fine = (size_t)(2 * nc + 2) * (2 * nc + 2) * C * 2;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&st->act[i], coarse);
+    if (e == cudaSuccess) e = cudaMalloc(&st->fine_act, fine);
+    if (e == cudaSuccess) e = cudaMalloc(&st->fine_out, sizeof(float) * 4 * nc * nc);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < 3; ++i)
+        if (!make_act_map(&st->tm_act[i], st->act[i], nc, nc)) return cudaErrorInvalidValue;
+    st->nc = nc;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 void sr_free(SrState *st) {
-    cudaFree(st->params);
-    cudaFree(st->packed);
+    cudaFree(st->w_tc);
+    cudaFree(st->bias_tc);
+    cudaFree(st->prelu_blk);
+    cudaFree(st->prelu_up);
+    cudaFree(st->w_in);
+    cudaFree(st->w_out);
+    for (int i = 0; i < 3; ++i) cudaFree(st->act[i]);
+    cudaFree(st->fine_act);
     cudaFree(st->fine_out);
-    cudaFree(st->act);
     cudaFree(st->scal);
+    cudaFree(st->red);
+    cudaFree(st->red_counter);
+    cudaFree(st->err);
     *st = SrState();
 }
 
@@ -38,10 +650,9 @@ mg_status sr_load(SrState *st, const void *blob, size_t bytes, char *err, size_t
     memcpy(hdr, (const char *)blob + 8, sizeof hdr);
     const int nf = (int)hdr[0], nb = (int)hdr[1];
     const size_t np = hdr[2];
-    if (nf != 64 || nb < 1 || nb > 32 || np != expected_params(nf, nb) ||
-        bytes != kHeader + np * sizeof(float)) {
-        snprintf(err, errlen, "weight blob: n_feat=%d n_blocks=%d n_params=%zu bytes=%zu inconsistent",
-                 nf, nb, np, bytes);
+    if (nf != C || nb < 1 || nb > 32 || np != expected_params(nf, nb) || bytes != kHeader + np * sizeof(float)) {
+        snprintf(err, errlen, "weight blob: n_feat=%d n_blocks=%d n_params=%zu bytes=%zu inconsistent", nf, nb, np,
+                 bytes);
         return MG_ERR_BAD_WEIGHTS;
     }
     const float *p = (const float *)((const char *)blob + kHeader);
@@ -52,9 +663,67 @@ mg_status sr_load(SrState *st, const void *blob, size_t bytes, char *err, size_t
             return MG_ERR_BAD_WEIGHTS;
         }
     }
+    // unpack in blob order
+    const float *in_w = p, *in_b = in_w + C * 9, *in_a = in_b + C;
+    const float *q = in_a + C;
+    const int layers = 2 * nb + 4;
+    std::vector<uint16_t> wtc((size_t)layers * 9 * C * C);
+    std::vector<float> btc((size_t)layers * C), ablk((size_t)nb * C), aup(C), win(C * 11), wout(9 * C + 1);
+    auto pack = [&](int layer, const float *w /*[co][ci][3][3]*/, int co_stride, int co_off) {
+        // packed[layer][tap][co][ci] = w[co_src][ci][ky][kx]
+        for (int t = 0; t < 9; ++t)
+            for (int co = 0; co < C; ++co)
+                for (int ci = 0; ci < C; ++ci) {
+                    const int src = co * co_stride + co_off;
+                    wtc[(((size_t)layer * 9 + t) * C + co) * C + ci] = bf16_bits(w[((size_t)src * C + ci) * 9 + t]);
+                }
+    };
+    for (int k = 0; k < nb; ++k) {
+        const float *w1 = q, *b1 = w1 + C * C * 9, *a1 = b1 + C, *w2 = a1 + C, *b2 = w2 + C * C * 9;
+        pack(2 * k, w1, 1, 0);
+        pack(2 * k + 1, w2, 1, 0);
+        memcpy(&btc[(size_t)(2 * k) * C], b1, C * sizeof(float));
+        memcpy(&btc[(size_t)(2 * k + 1) * C], b2, C * sizeof(float));
+        memcpy(&ablk[(size_t)k * C], a1, C * sizeof(float));
+        q = b2 + C;
+    }
+    const float *up_w = q, *up_b = up_w + 4 * C * C * 9, *up_a = up_b + 4 * C;
+    const float *out_w = up_a + C, *out_b = out_w + C * 9;
+    // pixel-shuffle group s holds output channels 4c + s, c = 0..63
+    for (int s = 0; s < 4; ++s) {
+        pack(2 * nb + s, up_w, 4, s);
+        for (int c = 0; c < C; ++c) btc[(size_t)(2 * nb + s) * C + c] = up_b[4 * c + s];
+    }
+    memcpy(aup.data(), up_a, C * sizeof(float));
+    for (int c = 0; c < C; ++c) {
+        for (int t = 0; t < 9; ++t) win[c * 9 + t] = bf16_value(in_w[c * 9 + t]);
+        win[C * 9 + c] = in_b[c];
+        win[C * 10 + c] = in_a[c];
+    }
+    for (int t = 0; t < 9; ++t)
+        for (int c = 0; c < C; ++c) wout[t * C + c] = bf16_value(out_w[c * 9 + t]);
+    wout[9 * C] = out_b[0];
+
     sr_free(st);
-    cudaError_t e = cudaMalloc(&st->params, np * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpy(st->params, p, np * sizeof(float), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc(&st->w_tc, wtc.size() * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMemcpy(st->w_tc, wtc.data(), wtc.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&st->bias_tc, btc.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(st->bias_tc, btc.data(), btc.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&st->prelu_blk, ablk.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(st->prelu_blk, ablk.data(), ablk.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&st->prelu_up, C * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(st->prelu_up, aup.data(), C * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&st->w_in, win.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(st->w_in, win.data(), win.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&st->w_out, wout.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(st->w_out, wout.data(), wout.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&st->scal, 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&st->red, sizeof(double) * kRedBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&st->red_counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(st->red_counter, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&st->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(st->err, 0, sizeof(int));
+    if (e == cudaSuccess && !make_w_map(&st->tm_w, st->w_tc, layers)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         snprintf(err, errlen, "weight upload: %s", cudaGetErrorString(e));
         sr_free(st);
@@ -62,19 +731,111 @@ mg_status sr_load(SrState *st, const void *blob, size_t bytes, char *err, size_t
     }
     st->n_feat = nf;
     st->n_blocks = nb;
-    st->n_params = np;
     st->loaded = true;
     return MG_OK;
 }
 
-mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t stream, char *err,
+mg_status sr_prepare(SrState *st, int nc, char *err, size_t errlen) {
+    if (!st->loaded) {
+        snprintf(err, errlen, "no generator weights loaded");
+        return MG_ERR_NO_WEIGHTS;
+    }
+    if (nc < TM || nc % TM) {
+        snprintf(err, errlen, "SR prolongation needs a coarse grid of at least %d (multiple of %d), got %d", TM, TM, nc);
+        return MG_ERR_INVALID_ARG;
+    }
+    cudaError_t e = prepare_conv();
+    if (e == cudaSuccess) e = ensure_buffers(st, nc);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "SR buffers for %d^2: %s", nc, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t s, char *err, size_t errlen) {
+    if (!st->loaded || st->nc != nc) {
+        snprintf(err, errlen, "SR generator not prepared for a %d^2 coarse grid", nc);
+        return MG_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaSuccess;
+    const size_t N = (size_t)nc * nc;
+    k_absmax<<<kRedBlocks, kRedThreads, 0, s>>>(ec, N, st->red, st->red_counter, st->scal);
+    count_launches(1);
+    k_conv_in<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ec, nc, st->scal, st->w_in,
+                                                        (__nv_bfloat16 *)st->act[0]);
+    count_launches(1);
+    e = cudaGetLastError();
+    int cur = 0;
+    const int nb = st->n_blocks;
+    for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+        const int nxt = (cur + 1) % 3, tmp = (cur + 2) % 3;
+        ConvArgs a1 = {nullptr, (__nv_bfloat16 *)st->act[tmp], st->bias_tc + (size_t)(2 * k) * C,
+                       st->prelu_blk + (size_t)k * C, nc, nc, 2 * k, 0, 0, st->err};
+        e = launch_conv<MODE_PRELU>(st->tm_act[cur], st->tm_w, a1, 1, s);
+        if (e != cudaSuccess) break;
+        ConvArgs a2 = {(const __nv_bfloat16 *)st->act[cur], (__nv_bfloat16 *)st->act[nxt],
+                       st->bias_tc + (size_t)(2 * k + 1) * C, nullptr, nc, nc, 2 * k + 1, 0, 0, st->err};
+        e = launch_conv<MODE_RESID>(st->tm_act[tmp], st->tm_w, a2, 1, s);
+        cur = nxt;
+    }
+    if (e == cudaSuccess) {
+        ConvArgs au = {nullptr, (__nv_bfloat16 *)st->fine_act, st->bias_tc + (size_t)(2 * nb) * C, st->prelu_up,
+                       nc, nc, 2 * nb, 0, 0, st->err};
+        e = launch_conv<MODE_SHUFFLE>(st->tm_act[cur], st->tm_w, au, 4, s);
+    }
+    if (e == cudaSuccess) {
+        const int nf = 2 * nc;
+        dim3 grid(nf / OUT_T, nf / OUT_T);
+        k_conv_out<<<grid, OUT_T * OUT_T, 0, s>>>((const __nv_bfloat16 *)st->fine_act, nf, st->w_out, st->scal,
+                                                  st->fine_out);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "SR generator launch: %s", cudaGetErrorString(e));
+        return MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip, const void *w_packed,
+                        const float *bias, const float *prelu, void *out, cudaStream_t s, char *err,
                         size_t errlen) {
-    (void)st;
-    (void)ec;
-    (void)nc;
-    (void)stream;
-    snprintf(err, errlen, "SR generator kernels are not available in this build");
-    return MG_ERR_INVALID_ARG;
+    if (W < TM || W % TM || H < 1 || (mode != MODE_PRELU && mode != MODE_RESID && mode != MODE_SHUFFLE) ||
+        (mode == MODE_RESID && !skip) || (mode != MODE_RESID && !prelu)) {
+        snprintf(err, errlen, "sr_conv_layer: bad mode %d or size %dx%d (W a multiple of %d)", mode, H, W, TM);
+        return MG_ERR_INVALID_ARG;
+    }
+    CUtensorMap tin, tw;
+    const int groups = mode == MODE_SHUFFLE ? 4 : 1;
+    if (!make_act_map(&tin, const_cast<void *>(in), H, W) || !make_w_map(&tw, const_cast<void *>(w_packed), groups)) {
+        snprintf(err, errlen, "sr_conv_layer: tensor map encoding failed");
+        return MG_ERR_INVALID_ARG;
+    }
+    int *dflag = nullptr;
+    cudaError_t e = prepare_conv();
+    if (e == cudaSuccess) e = cudaMalloc(&dflag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(int), s);
+    ConvArgs a = {(const __nv_bfloat16 *)skip, (__nv_bfloat16 *)out, bias, prelu, H, W, 0, 0, 0, dflag};
+    if (e == cudaSuccess) {
+        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, tw, a, 1, s);
+        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, tw, a, 1, s);
+        else e = launch_conv<MODE_SHUFFLE>(tin, tw, a, 4, s);
+    }
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dflag);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "sr_conv_layer: %s", cudaGetErrorString(e));
+        return MG_ERR_CUDA;
+    }
+    if (flag) {
+        snprintf(err, errlen, "sr_conv_layer: a bounded wait in the tensor-core kernel timed out");
+        return MG_ERR_TIMEOUT;
+    }
+    return MG_OK;
 }
 
 }  // namespace mg

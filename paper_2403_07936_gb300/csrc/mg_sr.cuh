@@ -6,34 +6,64 @@
 // conv3x3 1->64 + PReLU, residual blocks [conv3x3 64->64, PReLU, conv3x3
 // 64->64, + skip], conv3x3 64->256, pixel-shuffle x2, PReLU, conv3x3 64->1,
 // all with circular padding.
+//
+// Activations are bf16, channels-last (64 channels = 128 bytes per pixel),
+// stored with a one-pixel periodic halo: an H x W grid occupies
+// (H + 2) x (W + 2) pixels, pixel (y, x) at padded (y + 1, x + 1), and the
+// halo rows/columns hold the wrapped neighbours.  Every 3x3 window is then a
+// plain rectangle, which is what the TMA tile loads of the tensor-core
+// convolution read.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
 
 #include "../../include/mg.h"
 
 namespace mg {
 
+constexpr int kSrFeat = 64;
+
 struct SrState {
     bool loaded = false;
     int n_feat = 0, n_blocks = 0;
-    size_t n_params = 0;
-    float *params = nullptr;   // all parameters, float, blob order (device)
-    void *packed = nullptr;    // tensor-core weight tiles (device)
-    size_t packed_bytes = 0;
-    float *fine_out = nullptr; // s * G(e_c / s) on the fine grid (device)
-    int fine_n = 0;
-    void *act = nullptr;       // activation buffers (device)
-    size_t act_bytes = 0;
-    double *scal = nullptr;    // device scalars: input scale
+    // weights (device): tensor-core layers packed bf16 [layer][tap][co][ci],
+    // layers = 2 * n_blocks + 4 (the 4 pixel-shuffle groups of conv 64->256)
+    void *w_tc = nullptr;
+    float *bias_tc = nullptr;   // [layers][64]
+    float *prelu_blk = nullptr; // [n_blocks][64]
+    float *prelu_up = nullptr;  // [64]
+    float *w_in = nullptr;      // [64][9], bias [64], prelu [64]  (in one array)
+    float *w_out = nullptr;     // [9][64] then bias [1]
+    // buffers sized for coarse grid nc (reallocated when nc changes)
+    int nc = 0;
+    void *act[3] = {nullptr, nullptr, nullptr};  // padded coarse activations
+    void *fine_act = nullptr;                    // padded fine activation (after shuffle)
+    float *fine_out = nullptr;                   // s * G(e_c / s), fine grid (unpadded)
+    float *scal = nullptr;                       // device scalars: [0] = s
+    double *red = nullptr;                       // reduction partials
+    unsigned *red_counter = nullptr;
+    int *err = nullptr;                          // device error flag (bounded waits)
+    CUtensorMap tm_act[3];
+    CUtensorMap tm_w;
 };
 
 // Parse and copy a weight blob (layout in mg.h).  Errors go to err.
 mg_status sr_load(SrState *st, const void *blob, size_t bytes, char *err, size_t errlen);
-// Compute s * G(e_c / s) for the coarse error ec (nc x nc) into st->fine_out.
+// Allocate the activation buffers and tensor maps for coarse grids of size nc
+// (outside any stream capture).
+mg_status sr_prepare(SrState *st, int nc, char *err, size_t errlen);
+// Compute s * G(e_c / s) for the coarse error ec (nc x nc) into st->fine_out
+// (asynchronous on stream; sr_prepare must have run for nc).
 mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t stream, char *err,
                         size_t errlen);
 void sr_free(SrState *st);
+
+// One tensor-core convolution layer on padded bf16 activations (verification).
+mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip, const void *w_packed,
+                        const float *bias, const float *prelu, void *out, cudaStream_t stream,
+                        char *err, size_t errlen);
 
 }  // namespace mg

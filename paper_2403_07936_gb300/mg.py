@@ -54,6 +54,8 @@ SIGNATURES = {
     "mg_op_up": (_I, [_I, _I, _VP, _VP, _VP, _VP, _I, _VP]),
     "mg_op_vcycle": (_I, [_I, _I, _I, _VP, _VP, _I, _I, _I, _VP]),
     "mg_op_vcycle_static": (_I, [_I, _I, _I, _VP, _VP, _I, _I, _I, _VP]),
+    "mg_op_sr_conv": (_I, [_I, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mg_op_sr_generator": (_I, [_VP, _VP, _I, _VP]),
     "mg_op_outer_residual": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP]),
 }
 
@@ -241,6 +243,15 @@ def op_up(x, x_out, b, ec, nu: int, stream=None):
 def op_vcycle(x, b, coarsest: int, nu1: int, nu2: int, zero_init: bool = False, stream=None):
     _check(load().mg_op_vcycle(_dtype_code(x), x.shape[-1], coarsest, ptr(x), ptr(b), nu1, nu2,
                                int(zero_init), stream_handle(stream)))
+
+
+def op_sr_conv(mode: int, H: int, W: int, inp, skip, w_packed, bias, prelu, out, stream=None):
+    _check(load().mg_op_sr_conv(mode, H, W, ptr(inp), ptr(skip), ptr(w_packed), ptr(bias), ptr(prelu),
+                                ptr(out), stream_handle(stream)))
+
+
+def op_sr_generator(ctx: "Context", ec, out):
+    _check(load().mg_op_sr_generator(ctx.handle, ptr(ec), ec.shape[-1], ptr(out)))
 
 
 def op_outer_residual(f, x, mu: float, s32, out, stream=None):
