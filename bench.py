@@ -195,6 +195,132 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+
+# ---------------------------------------------------------------------------
+# Secondary legs: batched mixed-size solves and the SR prolongation
+# ---------------------------------------------------------------------------
+BATCH_SIZES = [256] * 128 + [512] * 96 + [1024] * 32
+SR_TENSOR_FLOP_PER_COARSE_PX = 2 * 64 * 576 * (16 + 4)  # 16 convs 64->64 and conv 64->256 (as 4 x 64)
+
+
+def _levels(n, coarsest=8):
+    return int(round(np.log2(n // coarsest))) + 1
+
+
+def _events_time(stream, fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def batched_leg(mg, dev, stream, flush, args, rank):
+    import torch
+    from synthetic.sources import config_seed, turbulent_source
+    sizes = BATCH_SIZES
+    fts = [torch.tensor(turbulent_source(n, n // 8, config_seed(3, rank * 1000 + i)), device=dev)
+           for i, n in enumerate(sizes)]
+    ctxs = []
+    for n in sizes:
+        c = mg.Context(_levels(n), n)
+        c.set_options(stream=stream)
+        ctxs.append(c)
+    xs = [torch.zeros_like(f) for f in fts]
+    for _ in range(args.warmup):
+        for x in xs:
+            x.zero_()
+        infos = mg.solve_batched(ctxs, fts, xs)
+    times = []
+    for _ in range(args.steps):
+        for x in xs:
+            x.zero_()
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = mg.solve_batched(ctxs, fts, xs)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = sum(times) / len(times)
+    pts = sum(n * n for n in sizes)
+    vc = max(i["vcycles"] for i in infos)
+    outer = max(i["outer_iters"] for i in infos)
+    # algorithmic bytes of one batch solve: per inner V-cycle ~35 B per finest point (fused
+    # down + up passes, 13 B each, over the 4/3 hierarchy), per outer step 40 B (FP64 residual
+    # 20 B + update 20 B), plus the first residual, the source sum and the projection (44 B)
+    bytes_alg = pts * (vc * 13 * 2 * 4 / 3 + outer * 40 + 44)
+    return {"workload": "256 right-hand sides: 128 x 256^2, 96 x 512^2, 32 x 1024^2 (67.1 M points), "
+                        "independent k^-5/3 sources, FP32 V(2,2) cubic in FP64 defect correction, tol 1e-10, "
+                        "one CUDA graph per batch (one launch per grid size and direction per V-cycle)",
+            "value": len(sizes) / t, "unit": "solves/s", "ms_per_batch": t * 1e3,
+            "vcycles_max": vc, "outer_max": outer,
+            "rel_residual_max": max(i["rel_residual"] for i in infos),
+            "effective_gbs": bytes_alg / t / 1e9,
+            "l2": "flushed between steps (512 MB write); working set 2.2 GB > L2"}
+
+
+def sr_leg(mg, dev, stream, flush, f_dev, x, args):
+    import torch
+    from paper_2403_07936_gb300 import sr
+    from synthetic.sources import turbulent_source
+    from synthetic.weights import random_weights
+    w = random_weights(11, gain=0.5)
+    w["out.w"] = w["out.w"] * 0.1
+    w["out.b"] = w["out.b"] * 0.1
+    ctx = mg.Context(LEVELS, N)
+    ctx.set_options(stream=stream)
+    ctx.load_weights(sr.pack_weights(w))
+    nc = N // 2
+    ec = torch.tensor(turbulent_source(nc, nc // 8, 4242) * 1e-3, dtype=torch.float32, device=dev)
+    out = torch.empty((N, N), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        mg.op_sr_generator(ctx, ec, out)
+    t_gen = _events_time(stream, lambda: mg.op_sr_generator(ctx, ec, out), max(3, args.steps // 2))
+    tflop = SR_TENSOR_FLOP_PER_COARSE_PX * nc * nc / 1e12
+    peak_tf = read_bf16_peak()
+    # whole solves with the SR prolongation at the finest transition
+    for _ in range(2):
+        x.zero_()
+        ctx.solve(f_dev[0], x, prolong="sr")
+    times, infos = [], []
+    for _ in range(max(3, args.steps // 2)):
+        x.zero_()
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(ctx.solve(f_dev[0], x, prolong="sr"))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    ts = sum(times) / len(times)
+    return {"workload": "2048^2, SR prolongation at the finest transition (generator on the 1024^2 coarse "
+                        "error: conv 1->64, 8 residual blocks, conv 64->256 + pixel shuffle, conv 64->1; "
+                        "bf16 operands, fp32 accumulate); seeded random weights (not trained)",
+            "generator_ms": t_gen * 1e3,
+            "tensor_roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05 implicit GEMM)",
+                                "achieved": tflop / t_gen, "peak": peak_tf[0], "unit": "TFLOP/s",
+                                "frac": tflop / t_gen / peak_tf[0], "peak_source": peak_tf[1],
+                                "note": "achieved counts the tensor-core FLOPs of the whole generator call "
+                                        "(which also includes the CUDA-core first/last layers and s = max|e|)"},
+            "solve": {"value": 1.0 / ts, "unit": "solves/s", "ms_per_step": ts * 1e3,
+                      "vcycles": infos[-1]["vcycles"], "outer_iters": infos[-1]["outer_iters"],
+                      "rel_residual": infos[-1]["rel_residual"]}}
+
+
+def read_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    return 1900.0, "fallback"
+
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
@@ -206,6 +332,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-sr", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -351,6 +479,12 @@ def main():
                                 "gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None}
                for k, v in kernel_ms.items()}
 
+    # ---- batched: 256 right-hand sides of mixed sizes in one graph ----------
+    batched = batched_leg(mg, dev, stream, flush, args, rank) if not args.skip_batched else None
+
+    # ---- SR prolongation at 2048^2 (tensor-core generator) ------------------
+    sr_info = sr_leg(mg, dev, stream, flush, f_dev, x, args) if not args.skip_sr else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg(srcs[0])
@@ -380,6 +514,8 @@ def main():
                             "vcycles": info64[-1]["vcycles"], "err_inf_vs_exact_fft": err64},
             "mixed_over_fp64": value / value64,
             "kernels_per_solve": kernels,
+            "batched": batched,
+            "sr": sr_info,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -115,8 +115,17 @@ mg_status mg_solve(mg_ctx *ctx, const double *f, double *x, double tol, mg_prolo
  * one FP32 V-cycle.  x is not projected to zero mean. */
 mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *x, mg_prolong prolong);
 
-/* Solve B independent problems, ctxs[k] with f[k], x[k] (device pointers),
- * each to tol.  Contexts may have different N.  infos may be NULL. */
+/* Solve B independent problems, ctxs[k] with f[k], x[k], each to tol.
+ * Contexts may have different N.  When every context is MG_PREC_MIXED with
+ * the same nu_pre, nu_post, inner_cycles and max_cycles, all buffers are in
+ * device memory and the prolongation is cubic, the whole batch runs as one
+ * CUDA graph: each V-cycle of the batch is one launch per grid size and
+ * direction (every right-hand side with a level of that size takes part) plus
+ * one launch for all coarse levels, the FP64 outer steps are one launch each,
+ * and a right-hand side stops once it has converged.  The graph is kept for
+ * the next call with the same contexts and buffers (the stream is the first
+ * context's).  Otherwise the problems are solved one after another.  Returns
+ * the first non-MG_OK status; infos (may be NULL) get one entry each. */
 mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
                            double tol, mg_prolong prolong, mg_solve_info *infos);
 

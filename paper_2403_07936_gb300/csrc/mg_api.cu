@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -464,6 +465,334 @@ static mg_status get_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_pro
     return MG_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched solves: one graph for B right-hand sides of (possibly) different
+// sizes.  A V-cycle of the whole batch is a down launch per grid size from the
+// largest to 128^2 (every right-hand side with a level of that size takes
+// part), one bottom launch (a block per right-hand side), and an up launch per
+// size back up; the FP64 outer steps, the convergence tests and the projection
+// are one launch each.  Converged right-hand sides drop out through an active
+// mask; the WHILE node runs until none is active.
+// ---------------------------------------------------------------------------
+struct BatchLaunch {
+    int kind;    // 0 down, 1 up, 2 bottom
+    size_t off;  // table offset (entries of TileGrid / BottomGrid)
+    int ngrid;
+    int nblocks;
+};
+
+struct BatchPlan {
+    std::vector<mg_ctx *> ctxs;
+    std::vector<const double *> f;
+    std::vector<double *> x;
+    double tol = 0.0;
+    int B = 0, device = -1;
+    void *dmem = nullptr;
+    RhsDesc *d_rhs = nullptr;
+    TileGrid *d_tiles = nullptr;
+    BottomGrid *d_bottom = nullptr;
+    DevState *d_state = nullptr, *h_state = nullptr;
+    int *d_active = nullptr;
+    double *d_partials = nullptr, *d_out = nullptr;  // out: 4 groups x [B][kMaxSlots]
+    unsigned *d_counters = nullptr;
+    int rhs_blocks = 0;
+    std::vector<BatchLaunch> cyc[2];  // [0] first inner cycle (zero start), [1] the others
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long n_pro = 0, n_body = 0, n_epi = 0;
+    BatchRed red(int g) const { return BatchRed{d_partials, d_counters, d_out + (size_t)g * B * kMaxSlots}; }
+    double *out(int g) const { return d_out + (size_t)g * B * kMaxSlots; }
+};
+
+static std::mutex g_batch_mutex;
+static BatchPlan *g_batch = nullptr;
+
+static void batch_free(BatchPlan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    cudaFree(p->dmem);
+    cudaFreeHost(p->h_state);
+    delete p;
+}
+
+static mg_status batch_build(BatchPlan *p) {
+    mg_ctx *c0 = p->ctxs[0];
+    const int B = p->B;
+    FirTaps taps;
+    fir_taps_host(&taps);
+    // right-hand-side descriptors and the level plan
+    std::vector<RhsDesc> rhs(B);
+    int blk = 0, maxN = 0;
+    for (int r = 0; r < B; ++r) {
+        mg_ctx *c = p->ctxs[r];
+        const int n = c->N;
+        const double h = 2.0 * 3.14159265358979323846 / n;
+        int nblk = (int)(((size_t)n * n) / 16384);
+        nblk = nblk < 1 ? 1 : (nblk > kRedBlocks ? kRedBlocks : nblk);
+        rhs[r] = RhsDesc{p->f[r], p->x[r], c->lv[0].b32, c->lv[0].x32, n, blk, nblk, 0, h * h};
+        blk += nblk;
+        maxN = n > maxN ? n : maxN;
+    }
+    p->rhs_blocks = blk;
+    std::vector<TileGrid> tiles;
+    std::vector<BottomGrid> bottoms;
+    for (int v = 0; v < 2; ++v) {
+        const bool first = v == 0;
+        p->cyc[v].clear();
+        for (int sz = maxN; sz > kBottomMax; sz >>= 1) {  // down sweeps
+            BatchLaunch L{0, tiles.size(), 0, 0};
+            for (int r = 0; r < B; ++r) {
+                mg_ctx *c = p->ctxs[r];
+                for (int l = 0; l + 1 < c->levels; ++l)
+                    if (c->lv[l].n == sz) {
+                        tiles.push_back(TileGrid{c->lv[l].x32, c->lv[l].t32, c->lv[l].b32, c->lv[l + 1].b32, sz,
+                                                 (l > 0 || first) ? 1 : 0, L.nblocks, r});
+                        L.nblocks += (sz / 64) * (sz / 64);
+                        ++L.ngrid;
+                    }
+            }
+            if (L.ngrid) p->cyc[v].push_back(L);
+        }
+        {  // bottom
+            BatchLaunch L{2, bottoms.size(), 0, 0};
+            for (int r = 0; r < B; ++r) {
+                mg_ctx *c = p->ctxs[r];
+                int l = 0;
+                while (c->lv[l].n > kBottomMax) ++l;
+                bottoms.push_back(BottomGrid{c->lv[l].x32, c->lv[l].b32, c->ainv32, c->lv[l].n, c->levels - l,
+                                             (l > 0 || first) ? 1 : 0, r});
+                ++L.ngrid;
+            }
+            L.nblocks = L.ngrid;
+            p->cyc[v].push_back(L);
+        }
+        for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {  // up sweeps
+            BatchLaunch L{1, tiles.size(), 0, 0};
+            for (int r = 0; r < B; ++r) {
+                mg_ctx *c = p->ctxs[r];
+                for (int l = 0; l + 1 < c->levels; ++l)
+                    if (c->lv[l].n == sz) {
+                        tiles.push_back(TileGrid{c->lv[l].t32, c->lv[l].x32, c->lv[l].b32, c->lv[l + 1].x32, sz, 0,
+                                                 L.nblocks, r});
+                        L.nblocks += (sz / 64) * (sz / 64);
+                        ++L.ngrid;
+                    }
+            }
+            if (L.ngrid) p->cyc[v].push_back(L);
+        }
+    }
+    // one device block for every table and buffer
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t o_rhs = 0, o_tiles = o_rhs + al(sizeof(RhsDesc) * B);
+    const size_t o_bot = o_tiles + al(sizeof(TileGrid) * (tiles.size() + 1));
+    const size_t o_state = o_bot + al(sizeof(BottomGrid) * bottoms.size());
+    const size_t o_active = o_state + al(sizeof(DevState) * B);
+    const size_t o_part = o_active + al(sizeof(int) * B);
+    const size_t o_out = o_part + al(sizeof(double) * kMaxSlots * blk);
+    const size_t o_cnt = o_out + al(sizeof(double) * 4 * B * kMaxSlots);
+    const size_t total = o_cnt + al(sizeof(unsigned) * B);
+    MG_CUDA(cudaMalloc(&p->dmem, total));
+    char *d = (char *)p->dmem;
+    p->d_rhs = (RhsDesc *)(d + o_rhs);
+    p->d_tiles = (TileGrid *)(d + o_tiles);
+    p->d_bottom = (BottomGrid *)(d + o_bot);
+    p->d_state = (DevState *)(d + o_state);
+    p->d_active = (int *)(d + o_active);
+    p->d_partials = (double *)(d + o_part);
+    p->d_out = (double *)(d + o_out);
+    p->d_counters = (unsigned *)(d + o_cnt);
+    MG_CUDA(cudaMemset(p->dmem, 0, total));
+    MG_CUDA(cudaMemcpy(p->d_rhs, rhs.data(), sizeof(RhsDesc) * B, cudaMemcpyHostToDevice));
+    if (!tiles.empty())
+        MG_CUDA(cudaMemcpy(p->d_tiles, tiles.data(), sizeof(TileGrid) * tiles.size(), cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(p->d_bottom, bottoms.data(), sizeof(BottomGrid) * bottoms.size(), cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMallocHost(&p->h_state, sizeof(DevState) * B));
+    MG_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+
+    // record: prologue, WHILE(outer step), epilogue
+    cudaStream_t s = p->cap;
+    const int step = c0->inner;
+    cudaGraphConditionalHandle handle;
+    MG_CUDA(cudaGraphCreate(&p->graph, 0));
+    MG_CUDA(cudaGraphConditionalHandleCreate(&handle, p->graph, 0, cudaGraphCondAssignDefault));
+    bool capturing = false;
+    cudaError_t e = cudaSuccess;
+    auto run_cycle = [&](int v) {
+        for (const BatchLaunch &L : p->cyc[v]) {
+            if (e != cudaSuccess) return;
+            if (L.kind == 0)
+                e = launch_down_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu1, p->d_active, s);
+            else if (L.kind == 1)
+                e = launch_up_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu2, p->d_active, taps, s);
+            else
+                e = launch_bottom_batched(p->d_bottom + L.off, L.ngrid, c0->nu1, c0->nu2, p->d_active, taps, s);
+        }
+    };
+    long long l0 = (long long)launches_total();
+    do {
+        e = cudaStreamBeginCaptureToGraph(s, p->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        capturing = true;
+        e = launch_sum_batched(p->d_rhs, B, blk, false, p->red(kGrpF), s);
+        if (e == cudaSuccess)
+            e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), true, nullptr, p->red(kGrpR), s);
+        if (e == cudaSuccess)
+            e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), nullptr, p->out(kGrpF), p->tol, step,
+                                     c0->max_cycles, true, p->d_active, handle, s);
+        if (e != cudaSuccess) break;
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) break;
+        std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+        e = cudaStreamEndCapture(s, &p->graph);
+        capturing = false;
+        if (e != cudaSuccess) break;
+        p->n_pro = (long long)launches_total() - l0;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cond;
+        e = cudaGraphAddNode(&cond, p->graph, tail.data(), nullptr, tail.size(), &cp);
+        if (e != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        l0 = (long long)launches_total();
+        e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        capturing = true;
+        for (int k = 0; k < step; ++k) run_cycle(k == 0 ? 0 : 1);
+        if (e == cudaSuccess) e = launch_update_batched(p->d_rhs, B, blk, p->d_active, p->red(kGrpU), s);
+        if (e == cudaSuccess)
+            e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), false, p->d_active, p->red(kGrpR), s);
+        if (e == cudaSuccess)
+            e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), p->out(kGrpU), p->out(kGrpF), p->tol,
+                                     step, c0->max_cycles, false, p->d_active, handle, s);
+        if (e != cudaSuccess) break;
+        e = cudaStreamEndCapture(s, &body);
+        capturing = false;
+        if (e != cudaSuccess) break;
+        p->n_body = (long long)launches_total() - l0;
+        l0 = (long long)launches_total();
+        e = cudaStreamBeginCaptureToGraph(s, p->graph, &cond, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        capturing = true;
+        e = launch_sum_batched(p->d_rhs, B, blk, true, p->red(kGrpX), s);
+        if (e == cudaSuccess) e = launch_project_batched(p->d_rhs, B, blk, p->out(kGrpX), p->d_state, s);
+        if (e != cudaSuccess) break;
+        e = cudaStreamEndCapture(s, &p->graph);
+        capturing = false;
+        if (e != cudaSuccess) break;
+        p->n_epi = (long long)launches_total() - l0;
+        e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    } while (false);
+    count_launches(-(p->n_pro + p->n_body + p->n_epi));
+    if (capturing) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(s, &junk);
+        if (junk && junk != p->graph) cudaGraphDestroy(junk);
+    }
+    if (e != cudaSuccess) {
+        set_err("batched graph recording failed: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+// Drop the cached batch graph if it refers to context c (destroyed or changed).
+static void batch_forget(mg_ctx *c) {
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    if (!g_batch) return;
+    for (mg_ctx *q : g_batch->ctxs)
+        if (q == c) {
+            batch_free(g_batch);
+            g_batch = nullptr;
+            return;
+        }
+}
+
+// All contexts mixed precision with equal cycle options on one device, all
+// buffers on the device, cubic prolongation: the batched graph applies.
+static bool batch_eligible(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
+                           mg_prolong prolong) {
+    if (B < 1 || prolong != MG_PROLONG_CUBIC) return false;
+    mg_ctx *c0 = ctxs[0];
+    if (!c0 || c0->prec != MG_PREC_MIXED || c0->probe_kind != kProbeNone) return false;
+    for (int r = 0; r < B; ++r) {
+        mg_ctx *c = ctxs[r];
+        if (!c || !f[r] || !x[r] || c->prec != MG_PREC_MIXED || c->nu1 != c0->nu1 || c->nu2 != c0->nu2 ||
+            c->inner != c0->inner || c->max_cycles != c0->max_cycles || c->device != c0->device ||
+            !is_device_pointer(f[r]) || !is_device_pointer(x[r]))
+            return false;
+        for (int q = 0; q < r; ++q)
+            if (ctxs[q] == c || x[q] == x[r]) return false;  // each context and x once
+    }
+    return true;
+}
+
+static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
+                                     double tol, mg_solve_info *infos) {
+    const auto t0 = std::chrono::steady_clock::now();
+    mg_ctx *c0 = ctxs[0];
+    MG_CUDA(cudaSetDevice(c0->device));
+    for (int r = 0; r < B; ++r) MG_TRY(ensure_hierarchy(ctxs[r], false));
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    BatchPlan *p = g_batch;
+    bool same = p && p->B == B && p->tol == tol && p->device == c0->device;
+    for (int r = 0; same && r < B; ++r)
+        same = p->ctxs[r] == ctxs[r] && p->f[r] == f[r] && p->x[r] == x[r];
+    if (!same) {
+        batch_free(g_batch);
+        g_batch = nullptr;
+        p = new BatchPlan();
+        p->B = B;
+        p->tol = tol;
+        p->device = c0->device;
+        p->ctxs.assign(ctxs, ctxs + B);
+        p->f.assign(f, f + B);
+        p->x.assign(x, x + B);
+        mg_status st = batch_build(p);
+        if (st != MG_OK) {
+            batch_free(p);
+            return st;
+        }
+        g_batch = p;
+    }
+    cudaStream_t s = c0->stream;
+    MG_CUDA(cudaGraphLaunch(p->exec, s));
+    MG_CUDA(cudaMemcpyAsync(p->h_state, p->d_state, sizeof(DevState) * B, cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    int outer_max = 0;
+    mg_status worst = MG_OK;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int r = 0; r < B; ++r) {
+        const DevState &ds = p->h_state[r];
+        outer_max = ds.outer > outer_max ? ds.outer : outer_max;
+        if (ds.status != MG_OK && worst == MG_OK) worst = (mg_status)ds.status;
+        if (infos) {
+            infos[r].outer_iters = ds.outer;
+            infos[r].vcycles = ds.cycles;
+            infos[r].rel_residual = ds.rel;
+            infos[r].removed_mean = ds.mu;
+            infos[r].update_norm = ds.unorm;
+            infos[r].time_ms = ms;
+            infos[r].prolong_used = MG_PROLONG_CUBIC;
+            infos[r].sr_fallback = 0;
+        }
+    }
+    count_launches(p->n_pro + (long long)outer_max * p->n_body + p->n_epi);
+    if (worst == MG_ERR_NONFINITE) set_err("non-finite residual in a batched right-hand side");
+    if (worst == MG_ERR_NOT_CONVERGED) set_err("a batched right-hand side did not converge");
+    return worst;
+}
+
 extern "C" {
 
 const char *mg_status_string(mg_status s) {
@@ -486,6 +815,7 @@ const char *mg_last_error(void) { return g_err; }
 void mg_destroy(mg_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    batch_forget(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFree(c->h32_block);
     cudaFree(c->h64_block);
@@ -575,8 +905,10 @@ mg_status mg_set_options(mg_ctx *c, mg_precision prec, int nu_pre, int nu_post, 
                 max_cycles);
         return MG_ERR_INVALID_ARG;
     }
-    if (prec != c->prec || nu_pre != c->nu1 || nu_post != c->nu2 || max_cycles != c->max_cycles)
+    if (prec != c->prec || nu_pre != c->nu1 || nu_post != c->nu2 || max_cycles != c->max_cycles) {
         drop_graphs(c);
+        batch_forget(c);
+    }
     c->prec = prec;
     c->nu1 = nu_pre;
     c->nu2 = nu_post;
@@ -590,7 +922,10 @@ mg_status mg_set_inner_cycles(mg_ctx *c, int inner) {
         set_err("inner_cycles must be in [1, 16]");
         return MG_ERR_INVALID_ARG;
     }
-    if (inner != c->inner) drop_graphs(c);
+    if (inner != c->inner) {
+        drop_graphs(c);
+        batch_forget(c);
+    }
     c->inner = inner;
     return MG_OK;
 }
@@ -756,10 +1091,12 @@ mg_status mg_vcycle(mg_ctx *c, const double *f, double *x, mg_prolong prolong) {
 
 mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
                            double tol, mg_prolong prolong, mg_solve_info *infos) {
-    if (!ctxs || !f || !x || B < 0) {
-        set_err("null batch arrays");
+    if (!ctxs || !f || !x || B < 0 || !(tol >= 0.0)) {
+        set_err("null batch arrays or bad tolerance");
         return MG_ERR_INVALID_ARG;
     }
+    if (B == 0) return MG_OK;
+    if (batch_eligible(ctxs, f, x, B, prolong)) return solve_batched_graph(ctxs, f, x, B, tol, infos);
     mg_status worst = MG_OK;
     for (int k = 0; k < B; ++k) {
         mg_status s = mg_solve(ctxs[k], f[k], x[k], tol, prolong, infos ? &infos[k] : nullptr);

@@ -110,6 +110,42 @@ __device__ __forceinline__ void reduce_finish(const Reduction &red, const double
 }
 
 // ----------------------------------------------------------------------------
+// Batched execution: many right-hand sides of different sizes in one launch.
+// A tile launch covers every grid of its table; block b belongs to the last
+// grid whose first tile is <= b.  Blocks of a right-hand side whose active
+// flag is 0 return at once.
+// ----------------------------------------------------------------------------
+struct TileGrid {
+    const void *x;  // input iterate
+    void *xout;     // output iterate
+    const void *b;  // scaled right-hand side
+    void *aux;      // down: coarse right-hand side (written); up: coarse error (read)
+    int n;          // grid size
+    int zero;       // down: the input iterate is taken as zero
+    int tile0;      // first block of this grid in the launch
+    int rhs;        // right-hand side index
+};
+struct BottomGrid {  // one block each
+    void *x;
+    const void *b;
+    const void *ainv;  // coarsest pseudo-inverse
+    int n, nlev, zero, rhs;
+};
+struct RhsDesc {  // FP64 outer kernels: blocks [blk0, blk0 + nblk) serve this right-hand side
+    const double *f;
+    double *x;
+    float *s32;      // float residual (inner right-hand side)
+    const float *e;  // inner correction
+    int n, blk0, nblk, pad;
+    double h2;
+};
+struct BatchRed {
+    double *partials;   // [blocks][kMaxSlots]
+    unsigned *counters; // [rhs]
+    double *out;        // [rhs][kMaxSlots]
+};
+
+// ----------------------------------------------------------------------------
 // Host-side launchers (defined in mg_kernels.cu); all return cudaError_t.
 // ----------------------------------------------------------------------------
 // xout = nu sweeps of x (x = 0 if zero_init); bc = 4 FW(b - (4 xout - sum)).  x != xout.
@@ -157,6 +193,26 @@ struct DevState {
 cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
                          double n2, double h2, double tol, int step, int max_cycles, bool first,
                          cudaGraphConditionalHandle handle, cudaStream_t s);
+
+// batched forms (float tile kernels; FP64 outer kernels)
+cudaError_t launch_down_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
+                                cudaStream_t s);
+cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
+                              const FirTaps &taps, cudaStream_t s);
+cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int nu2, const int *active,
+                                  const FirTaps &taps, cudaStream_t s);
+// sums of f (of_x = false) or of x (of_x = true) per right-hand side -> red.out[r][0]
+cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of_x, BatchRed red,
+                               cudaStream_t s);
+cudaError_t launch_outer_residual_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *fsum,
+                                          bool want_fnorm, const int *active, BatchRed red, cudaStream_t s);
+cudaError_t launch_update_batched(const RhsDesc *rd, int nrhs, int nblocks, const int *active, BatchRed red,
+                                  cudaStream_t s);
+cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *xsum,
+                                   const DevState *st, cudaStream_t s);
+cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, const double *rsum,
+                                 const double *usum, const double *fsum, double tol, int step, int max_cycles,
+                                 bool first, int *active, cudaGraphConditionalHandle handle, cudaStream_t s);
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,

@@ -200,20 +200,19 @@ struct DownCfg {
     static constexpr size_t smem = 4ull * A * sizeof(T);
 };
 
-template <typename T, int NU, bool ZERO>
-__global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *__restrict__ xout,
-                                                   const T *__restrict__ b, int n,
-                                                   T *__restrict__ bc) {
+template <typename T, int NU>
+__device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict__ xout,
+                                          const T *__restrict__ b, int n, T *__restrict__ bc,
+                                          int ty0, int tx0, bool zero) {
     using Cfg = DownCfg<T, NU>;
     constexpr int TY = Cfg::TY, TX = Cfg::TX, H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C,
                   CK = Cfg::CK, A = Cfg::A;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *X = reinterpret_cast<T *>(smem_raw);  // red at X, black at X + A
     T *B = X + 2 * A;                           // red at B, black at B + A
-    const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
 
     load_split<T, R, C>(B, B + A, b, n, ty0 - H, tx0 - HX);
-    if (ZERO) {
+    if (zero) {
         for (int i = threadIdx.x; i < 2 * A; i += blockDim.x) X[i] = T(0);
     } else {
         load_split<T, R, C>(X, X + A, x, n, ty0 - H, tx0 - HX);
@@ -254,6 +253,35 @@ __global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *_
     store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
 }
 
+template <typename T, int NU, bool ZERO>
+__global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *__restrict__ xout,
+                                                   const T *__restrict__ b, int n,
+                                                   T *__restrict__ bc) {
+    down_tile<T, NU>(x, xout, b, n, bc, blockIdx.y * Tile<T>::TY, blockIdx.x * Tile<T>::TX, ZERO);
+}
+
+// Block of a batched tile launch: locate its grid (the last table entry whose
+// first tile is <= blockIdx.x) and the tile's origin in that grid.
+__device__ __forceinline__ int find_grid(const TileGrid *__restrict__ g, int ngrid) {
+    int lo = 0, hi = ngrid - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g[mid].tile0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int NU>
+__global__ void __launch_bounds__(kThreads) k_down_batched(const TileGrid *__restrict__ tab, int ngrid,
+                                                           const int *__restrict__ active) {
+    const TileGrid t = tab[find_grid(tab, ngrid)];
+    if (active && !active[t.rhs]) return;
+    const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / Tile<T>::TX;
+    down_tile<T, NU>((const T *)t.x, (T *)t.xout, (const T *)t.b, t.n, (T *)t.aux, (lt / tpr) * Tile<T>::TY,
+                     (lt % tpr) * Tile<T>::TX, t.zero != 0);
+}
+
 // ---------------------------------------------------------------------------
 // k_up: x += P_cubic ec (+ extra), then NU sweeps, on one tile.
 // ---------------------------------------------------------------------------
@@ -284,9 +312,10 @@ struct UpCfg {
 };
 
 template <typename T, int NU>
-__global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__restrict__ xout,
-                                                 const T *__restrict__ b, const T *__restrict__ ec,
-                                                 const T *__restrict__ extra, int n, FirTaps taps) {
+__device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__ xout,
+                                        const T *__restrict__ b, const T *__restrict__ ec,
+                                        const T *__restrict__ extra, int n, const FirTaps &taps, int ty0,
+                                        int tx0) {
     using Cfg = UpCfg<T, NU>;
     constexpr int TY = Cfg::TY, TX = Cfg::TX, NJ = Cfg::NJ, H = Cfg::H, HX = Cfg::HX, R = Cfg::R,
                   C = Cfg::C, CK = Cfg::CK, A = Cfg::A, L = Cfg::L, JW = Cfg::JW, IW = Cfg::IW,
@@ -296,7 +325,6 @@ __global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__r
     T *cs = X + 2 * A;                          // coarse tile [CR][CC] (row pass only)
     T *B = X + 2 * A;                           // b, loaded over cs after the row pass
     T *rs = X + 2 * A + Cfg::U;                 // x-refined coarse rows [CR][FW]
-    const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
     const int nc = n >> 1;
 
     load_split<T, R, C>(X, X + A, x, n, ty0 - H, tx0 - HX);
@@ -361,6 +389,23 @@ __global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__r
     store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
 }
 
+template <typename T, int NU>
+__global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__restrict__ xout,
+                                                 const T *__restrict__ b, const T *__restrict__ ec,
+                                                 const T *__restrict__ extra, int n, FirTaps taps) {
+    up_tile<T, NU>(x, xout, b, ec, extra, n, taps, blockIdx.y * Tile<T>::TY, blockIdx.x * Tile<T>::TX);
+}
+
+template <typename T, int NU>
+__global__ void __launch_bounds__(kThreads) k_up_batched(const TileGrid *__restrict__ tab, int ngrid,
+                                                         const int *__restrict__ active, FirTaps taps) {
+    const TileGrid t = tab[find_grid(tab, ngrid)];
+    if (active && !active[t.rhs]) return;
+    const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / Tile<T>::TX;
+    up_tile<T, NU>((const T *)t.x, (T *)t.xout, (const T *)t.b, (const T *)t.aux, nullptr, t.n, taps,
+                   (lt / tpr) * Tile<T>::TY, (lt % tpr) * Tile<T>::TX);
+}
+
 // ---------------------------------------------------------------------------
 // k_bottom: a whole V-cycle on grids <= 64 x 64, one block, shared memory.
 // ---------------------------------------------------------------------------
@@ -380,10 +425,9 @@ __device__ __forceinline__ void sweep_periodic(T *X, const T *B, int m, int colo
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ x, const T *__restrict__ b,
-                                                           int n, int nlev, int nu1, int nu2,
-                                                           int zero_init, const T *__restrict__ ainv,
-                                                           FirTaps taps) {
+__device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restrict__ b, int n, int nlev,
+                                            int nu1, int nu2, int zero_init, const T *__restrict__ ainv,
+                                            const FirTaps &taps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *base = reinterpret_cast<T *>(smem_raw);
     T *X[8], *B[8];
@@ -492,6 +536,25 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ x, co
         }
     }
     for (int p = tid; p < n * n; p += nt) x[p] = X[0][p];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ x, const T *__restrict__ b,
+                                                           int n, int nlev, int nu1, int nu2,
+                                                           int zero_init, const T *__restrict__ ainv,
+                                                           FirTaps taps) {
+    bottom_body<T>(x, b, n, nlev, nu1, nu2, zero_init, ainv, taps);
+}
+
+// one block per grid of the table
+template <typename T>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom_batched(const BottomGrid *__restrict__ tab,
+                                                                   int nu1, int nu2,
+                                                                   const int *__restrict__ active,
+                                                                   FirTaps taps) {
+    const BottomGrid g = tab[blockIdx.x];
+    if (active && !active[g.rhs]) return;
+    bottom_body<T>((T *)g.x, (const T *)g.b, g.n, g.nlev, nu1, nu2, g.zero, (const T *)g.ainv, taps);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,6 +668,163 @@ __global__ void k_check(DevState *st, const double *rsum, const double *usum, co
         }
     }
     cudaGraphSetConditional(handle, go);
+}
+
+// ---------------------------------------------------------------------------
+// Batched FP64 outer kernels: the blocks of right-hand side r are
+// [blk0, blk0 + nblk); each right-hand side's sums finish in its last block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_rhs(const RhsDesc *__restrict__ r, int nrhs) {
+    int lo = 0, hi = nrhs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (r[mid].blk0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int NS>
+__device__ __forceinline__ void batch_finish(const BatchRed &red, int rhs, int blk0, int nblk,
+                                             const double (&vals)[NS], double *sh) {
+    __shared__ bool am_last;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NS; ++k) red.partials[(size_t)blockIdx.x * kMaxSlots + k] = vals[k];
+        __threadfence();
+        const unsigned ticket = atomicAdd(&red.counters[rhs], 1u);
+        am_last = (ticket == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    for (int k = 0; k < NS; ++k) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+            v += ((volatile double *)red.partials)[(size_t)(blk0 + i) * kMaxSlots + k];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) red.out[(size_t)rhs * kMaxSlots + k] = v;
+    }
+    if (threadIdx.x == 0) red.counters[rhs] = 0u;
+}
+
+template <bool OF_X>
+__global__ void __launch_bounds__(kRedThreads) k_sum_b(const RhsDesc *__restrict__ rd, int nrhs, BatchRed red) {
+    __shared__ double sh[32];
+    const int r = find_rhs(rd, nrhs);
+    const RhsDesc d = rd[r];
+    const size_t N = (size_t)d.n * d.n;
+    const double *a = OF_X ? d.x : d.f;
+    double v = 0.0;
+    for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x)
+        v += a[p];
+    double vals[1] = {block_sum(v, sh)};
+    batch_finish<1>(red, r, d.blk0, d.nblk, vals, sh);
+}
+
+template <bool FNORM>
+__global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc *__restrict__ rd, int nrhs,
+                                                                  const double *__restrict__ fsum,
+                                                                  const int *__restrict__ active, BatchRed red) {
+    __shared__ double sh[32];
+    const int r = find_rhs(rd, nrhs);
+    if (active && !active[r]) return;
+    const RhsDesc d = rd[r];
+    const int n = d.n;
+    const size_t N = (size_t)n * n;
+    const double mu = fsum[(size_t)r * kMaxSlots] / (double)N;
+    double ss = 0.0, ff = 0.0;
+    for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x) {
+        const int i = (int)(p / n), j = (int)(p - (size_t)i * n);
+        const int im = (i - 1) & (n - 1), ip = (i + 1) & (n - 1);
+        const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
+        const double *x = d.x;
+        const double nb = ((x[(size_t)im * n + j] + x[(size_t)ip * n + j]) + x[(size_t)i * n + jm]) + x[(size_t)i * n + jp];
+        const double fc = d.f[p] - mu;
+        const double s = d.h2 * fc - (4.0 * x[p] - nb);
+        ss += s * s;
+        if (FNORM) ff += fc * fc;
+        d.s32[p] = (float)s;
+    }
+    double vals[2];
+    vals[0] = block_sum(ss, sh);
+    vals[1] = FNORM ? block_sum(ff, sh) : 0.0;
+    batch_finish<2>(red, r, d.blk0, d.nblk, vals, sh);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restrict__ rd, int nrhs,
+                                                          const int *__restrict__ active, BatchRed red) {
+    __shared__ double sh[32];
+    const int r = find_rhs(rd, nrhs);
+    if (active && !active[r]) return;
+    const RhsDesc d = rd[r];
+    const size_t N = (size_t)d.n * d.n;
+    double ee = 0.0;
+    for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x) {
+        const double e = (double)d.e[p];
+        d.x[p] += e;
+        ee += e * e;
+    }
+    double vals[1] = {block_sum(ee, sh)};
+    batch_finish<1>(red, r, d.blk0, d.nblk, vals, sh);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_project_b(const RhsDesc *__restrict__ rd, int nrhs,
+                                                           const double *__restrict__ xsum,
+                                                           const DevState *__restrict__ st) {
+    const int r = find_rhs(rd, nrhs);
+    const RhsDesc d = rd[r];
+    const size_t N = (size_t)d.n * d.n;
+    const bool zero = st[r].zero_source != 0;
+    const double mu = xsum[(size_t)r * kMaxSlots] / (double)N;
+    for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x)
+        d.x[p] = zero ? 0.0 : d.x[p] - mu;
+}
+
+// Convergence test of every right-hand side still active; the loop continues
+// while any is.  One block.
+__global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs, const double *rsum,
+                          const double *usum, const double *fsum, double tol, int step, int max_cycles,
+                          int first, int *active, cudaGraphConditionalHandle handle) {
+    int any = 0;
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+        if (!first && !active[r]) continue;
+        DevState &s = st[r];
+        const double n2 = (double)rd[r].n * rd[r].n, h2 = rd[r].h2;
+        const double *rs = rsum + (size_t)r * kMaxSlots;
+        if (first) {
+            s.fnorm = sqrt(rs[1]);
+            s.mu = fsum[(size_t)r * kMaxSlots] / n2;
+            s.cycles = 0;
+            s.outer = 0;
+            s.status = MG_OK;
+            s.zero_source = 0;
+            s.unorm = 0.0;
+        } else {
+            s.cycles += step;
+            s.outer += 1;
+            s.unorm = sqrt(usum[(size_t)r * kMaxSlots]);
+        }
+        const double rn = sqrt(rs[0]) / h2, fn = s.fnorm;
+        int go = 0;
+        if (!isfinite(rn) || !isfinite(fn)) {
+            s.status = MG_ERR_NONFINITE;
+            s.rel = rn / fn;
+        } else if (fn == 0.0) {
+            s.zero_source = 1;
+            s.rel = 0.0;
+        } else {
+            const double rel = rn / fn;
+            s.rel = rel;
+            if (rel > tol) {
+                if (s.cycles + step <= max_cycles) go = 1;
+                else s.status = MG_ERR_NOT_CONVERGED;
+            }
+        }
+        active[r] = go;
+        any |= go;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
 }
 
 template <typename KernelT>
@@ -773,6 +993,97 @@ cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, c
                          double n2, double h2, double tol, int step, int max_cycles, bool first,
                          cudaGraphConditionalHandle handle, cudaStream_t s) {
     k_check<<<1, 32, 0, s>>>(st, rsum, usum, fsum, n2, h2, tol, step, max_cycles, first ? 1 : 0, handle);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_down_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
+                                cudaStream_t s) {
+#define MG_DB_CASE(NU)                                                                            \
+    case NU: {                                                                                    \
+        static std::atomic<unsigned> done{0};                                                     \
+        cudaError_t e = set_smem_once(k_down_batched<float, NU>, DownCfg<float, NU>::smem, done); \
+        if (e != cudaSuccess) return e;                                                           \
+        k_down_batched<float, NU><<<nblocks, kThreads, DownCfg<float, NU>::smem, s>>>(tab, ngrid, active); \
+        break;                                                                                    \
+    }
+    switch (nu) {
+        MG_DB_CASE(0) MG_DB_CASE(1) MG_DB_CASE(2) MG_DB_CASE(3) MG_DB_CASE(4)
+        default: return cudaErrorInvalidValue;
+    }
+#undef MG_DB_CASE
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
+                              const FirTaps &taps, cudaStream_t s) {
+#define MG_UB_CASE(NU)                                                                          \
+    case NU: {                                                                                  \
+        static std::atomic<unsigned> done{0};                                                   \
+        cudaError_t e = set_smem_once(k_up_batched<float, NU>, UpCfg<float, NU>::smem, done);   \
+        if (e != cudaSuccess) return e;                                                         \
+        k_up_batched<float, NU><<<nblocks, kThreads, UpCfg<float, NU>::smem, s>>>(tab, ngrid, active, taps); \
+        break;                                                                                  \
+    }
+    switch (nu) {
+        MG_UB_CASE(0) MG_UB_CASE(1) MG_UB_CASE(2) MG_UB_CASE(3) MG_UB_CASE(4)
+        default: return cudaErrorInvalidValue;
+    }
+#undef MG_UB_CASE
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int nu2, const int *active,
+                                  const FirTaps &taps, cudaStream_t s) {
+    size_t max_elems = (size_t)kBottomMax * kBottomMax;
+    for (int m = kBottomMax; m >= 4; m >>= 1) max_elems += 2ull * m * m;
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = set_smem_once(k_bottom_batched<float>, max_elems * sizeof(float), done);
+    if (e != cudaSuccess) return e;
+    k_bottom_batched<float><<<ngrid, kBottomThreads, max_elems * sizeof(float), s>>>(tab, nu1, nu2, active, taps);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of_x, BatchRed red, cudaStream_t s) {
+    if (of_x)
+        k_sum_b<true><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, red);
+    else
+        k_sum_b<false><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, red);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outer_residual_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *fsum,
+                                          bool want_fnorm, const int *active, BatchRed red, cudaStream_t s) {
+    if (want_fnorm)
+        k_outer_residual_b<true><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, fsum, active, red);
+    else
+        k_outer_residual_b<false><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, fsum, active, red);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_batched(const RhsDesc *rd, int nrhs, int nblocks, const int *active, BatchRed red,
+                                  cudaStream_t s) {
+    k_update_b<<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, active, red);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *xsum,
+                                   const DevState *st, cudaStream_t s) {
+    k_project_b<<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, xsum, st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, const double *rsum,
+                                 const double *usum, const double *fsum, double tol, int step, int max_cycles,
+                                 bool first, int *active, cudaGraphConditionalHandle handle, cudaStream_t s) {
+    k_check_b<<<1, 256, 0, s>>>(st, rd, nrhs, rsum, usum, fsum, tol, step, max_cycles, first ? 1 : 0, active, handle);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -59,22 +59,18 @@ def default_kmax(n: int) -> int:
 def _streamfunction_hat(n: int, kmax: int, seed: int) -> np.ndarray:
     if not (1 <= kmax < n // 2):
         raise ValueError(f"k_max={kmax} must lie in [1, n/2) for n={n}")
-    # Half-plane modes in a fixed order: ky outer (0..kmax), kx inner.
-    modes = []
-    for ky in range(0, kmax + 1):
-        for kx in range(-kmax, kmax + 1):
-            if ky == 0 and kx <= 0:
-                continue
-            k2 = kx * kx + ky * ky
-            if 1 <= k2 <= kmax * kmax:
-                modes.append((ky, kx))
-    phases = 2.0 * np.pi * uniform01(seed, len(modes))
+    # Half-plane modes in a fixed order: ky outer (0..kmax), kx inner
+    # (-kmax..kmax), keeping ky > 0 or (ky == 0 and kx > 0), 1 <= |k| <= kmax.
+    ky, kx = np.meshgrid(np.arange(0, kmax + 1), np.arange(-kmax, kmax + 1), indexing="ij")
+    ky, kx = ky.ravel(), kx.ravel()
+    k2 = kx * kx + ky * ky
+    keep = ((ky > 0) | (kx > 0)) & (k2 >= 1) & (k2 <= kmax * kmax)
+    ky, kx, k2 = ky[keep], kx[keep], k2[keep]
+    phases = 2.0 * np.pi * uniform01(seed, ky.size)
+    c = k2.astype(np.float64) ** (-7.0 / 6.0) * np.exp(1j * phases)  # |k|^(-7/3) e^{i phi}
     psi_hat = np.zeros((n, n), dtype=np.complex128)
-    for (ky, kx), phi in zip(modes, phases):
-        amp = (kx * kx + ky * ky) ** (-7.0 / 6.0)  # |k|^(-7/3)
-        c = amp * np.exp(1j * phi)
-        psi_hat[ky % n, kx % n] = c
-        psi_hat[(-ky) % n, (-kx) % n] = np.conj(c)
+    psi_hat[ky % n, kx % n] = c
+    psi_hat[(-ky) % n, (-kx) % n] = np.conj(c)
     return psi_hat
 
 

@@ -1,0 +1,93 @@
+"""Batched solves of many right-hand sides of different sizes (GPU).
+
+The batched graph runs the same tile kernels as a single solve, but its FP64
+sums use a different block split, so results agree with the single solves to
+rounding: the bound is the spec one, |x_batch - x_alone|_inf <=
+1e-9 |x_alone|_inf, with each result also checked against the exact FFT
+solution and for its own relative residual.
+"""
+import numpy as np
+import pytest
+
+from oracle import multigrid as omg
+from synthetic.sources import config_seed, default_kmax, turbulent_source
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mg():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_07936_gb300 import mg as m
+    return m
+
+
+def _levels(n, coarsest=8):
+    return int(np.log2(n // coarsest)) + 1
+
+
+def _case(sizes, seed0):
+    fs = [turbulent_source(n, default_kmax(n), config_seed(3, seed0 + i)) for i, n in enumerate(sizes)]
+    return fs, [torch.tensor(f, device=DEV) for f in fs]
+
+
+@pytest.mark.parametrize("sizes", [[256, 512, 256, 1024, 64, 512, 128],
+                                   [256] * 6 + [512] * 3 + [1024]])
+def test_batch_matches_single_solves_and_exact(mg, sizes):
+    fs, fts = _case(sizes, 10 * len(sizes))
+    ctxs = [mg.Context(_levels(n), n) for n in sizes]
+    xs = [torch.zeros_like(ft) for ft in fts]
+    infos = mg.solve_batched(ctxs, fts, xs, tol=1e-10)
+    for f, ft, x, ctx, info in zip(fs, fts, xs, ctxs, infos):
+        assert info["rel_residual"] <= 1e-10
+        xa = torch.zeros_like(ft)
+        ctx.solve(ft, xa, tol=1e-10)
+        got, alone = x.cpu().numpy(), xa.cpu().numpy()
+        assert np.abs(got - alone).max() <= 1e-9 * np.abs(alone).max()
+        xe = omg.exact_solve_fft(f - f.mean())
+        assert np.abs(got - xe).max() <= 1e-9 * np.abs(xe).max()
+        assert omg.relative_residual(f - f.mean(), got, omg.grid_h(f.shape[0])) <= 1.5e-10
+
+
+def test_batch_graph_is_reused_and_handles_converged_members(mg):
+    sizes = [256, 512, 256]
+    fs, fts = _case(sizes, 77)
+    ctxs = [mg.Context(_levels(n), n) for n in sizes]
+    xs = [torch.zeros_like(ft) for ft in fts]
+    mg.solve_batched(ctxs, fts, xs, tol=1e-10)
+    # x[1] is now converged: it does no cycle, the others (reset) do
+    xs[0].zero_()
+    xs[2].zero_()
+    infos = mg.solve_batched(ctxs, fts, xs, tol=1e-10)
+    assert infos[1]["vcycles"] == 0 and infos[0]["vcycles"] > 0 and infos[2]["vcycles"] > 0
+    for f, x in zip(fs, xs):
+        xe = omg.exact_solve_fft(f - f.mean())
+        assert np.abs(x.cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
+
+
+def test_batch_reports_nonfinite_member_and_solves_the_rest(mg):
+    sizes = [256, 256]
+    fs, fts = _case(sizes, 91)
+    fts[1][5, 7] = float("inf")
+    ctxs = [mg.Context(_levels(n), n) for n in sizes]
+    xs = [torch.zeros_like(ft) for ft in fts]
+    with pytest.raises(mg.MGError) as e:
+        mg.solve_batched(ctxs, fts, xs, tol=1e-10)
+    assert e.value.status == 8
+    xe = omg.exact_solve_fft(fs[0] - fs[0].mean())
+    assert np.abs(xs[0].cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
+
+
+def test_batch_falls_back_for_fp64_contexts(mg):
+    sizes = [128, 256]
+    fs, fts = _case(sizes, 55)
+    ctxs = [mg.Context(_levels(n), n, precision="fp64") for n in sizes]
+    xs = [torch.zeros_like(ft) for ft in fts]
+    infos = mg.solve_batched(ctxs, fts, xs, tol=1e-10)
+    for f, x, info in zip(fs, xs, infos):
+        assert info["rel_residual"] <= 1e-10
+        xe = omg.exact_solve_fft(f - f.mean())
+        assert np.abs(x.cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
