@@ -40,12 +40,13 @@ constexpr int ROWBYTES = ROWPX * C * 2;
 constexpr int PLANE = 2176;
 constexpr int ROWSLOT = 8 * PLANE;    // 17 KiB slots, 1024-byte multiple
 static_assert(PLANE >= ROWPX * 16 && PLANE % 128 == 0, "plane pitch");
-constexpr int NSLOT = 4;              // ring of staged input rows
+constexpr int NSLOT = 6;              // ring of staged input rows (prefetch 3 rows ahead)
 constexpr int WBYTES = 9 * C * C * 2;  // one layer's weights, 72 KiB
 constexpr int TAPBYTES = C * C * 2;    // one tap: 64 rows (co) x 128 bytes (ci)
 constexpr int TMEM_COLS = 128;        // two 64-column FP32 accumulators
-constexpr int CONV_THREADS = 128;
-constexpr size_t CONV_SMEM = 1024 + WBYTES + NSLOT * ROWSLOT + 128;
+constexpr int CONV_THREADS = 256;  // 8 warps drain the accumulator: (lane quarter, column half)
+constexpr int STAGE = TM * C * 2;     // one output tile, 128 px x 128 B (epilogue staging)
+constexpr size_t CONV_SMEM = 1024 + WBYTES + NSLOT * ROWSLOT + 2 * STAGE + 128 + 2 * C * sizeof(float);
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 enum { MODE_PRELU = 0, MODE_RESID = 1, MODE_SHUFFLE = 2 };
@@ -101,6 +102,16 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
         ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
+        ::"l"(map), "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
                  "r"(ncols)
@@ -194,6 +205,27 @@ __device__ __forceinline__ void store_px(__nv_bfloat16 *out, int H, int W, int y
     }
 }
 
+// Store channels [32 half, 32 half + 32) of one pixel (4 x 16 bytes) at (y, x)
+// of a padded H x W grid and at the halo positions that wrap onto it.  With
+// halo_only, the interior position and the halo-row copy in the pixel's own
+// column are skipped (the tile's TMA stores write those).
+__device__ __forceinline__ void store_half_px(__nv_bfloat16 *out, int H, int W, int y, int x, int half,
+                                              const uint4 *d, bool halo_only) {
+    const int rows[2] = {y + 1, y == 0 ? H + 1 : (y == H - 1 ? 0 : -1)};
+    const int cols[2] = {x + 1, x == 0 ? W + 1 : (x == W - 1 ? 0 : -1)};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        if (rows[a] < 0) continue;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (cols[b] < 0 || (halo_only && b == 0)) continue;
+            uint4 *p = reinterpret_cast<uint4 *>(out + ((size_t)rows[a] * (W + 2) + cols[b]) * C + half * 32);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) p[i] = d[i];
+        }
+    }
+}
+
 struct ConvArgs {
     const __nv_bfloat16 *skip;  // MODE_RESID: residual input (padded), else null
     __nv_bfloat16 *out;         // padded output (coarse, or fine for MODE_SHUFFLE)
@@ -214,16 +246,19 @@ struct ConvArgs {
 template <int MODE>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
-              ConvArgs a) {
+              const __grid_constant__ CUtensorMap tm_out, ConvArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *wsm = sm;
     unsigned char *rows = sm + WBYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(rows + NSLOT * ROWSLOT);
+    unsigned char *stage = rows + NSLOT * ROWSLOT;  // 2 x STAGE, 1024-byte aligned
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * STAGE);
     uint64_t *wbar = bars, *full = bars + 1, *mdone = bars + 1 + NSLOT;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 8);
-    int *abort_flag = reinterpret_cast<int *>(bars + 9);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 1 + NSLOT + 2);
+    int *abort_flag = reinterpret_cast<int *>(bars + 2 + NSLOT + 2);
+    float *s_bias = reinterpret_cast<float *>(bars + 16);  // [64] bias, [64] PReLU slopes
+    float *s_prelu = s_bias + C;
 
     const int NB = a.W / TM;
     const int strip = blockIdx.x / a.chunks, chunk = blockIdx.x - strip * a.chunks;
@@ -243,6 +278,10 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+    if (threadIdx.x < C) {
+        s_bias[threadIdx.x] = a.bias[g * C + threadIdx.x];
+        s_prelu[threadIdx.x] = a.prelu ? a.prelu[threadIdx.x] : 0.f;
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -266,7 +305,6 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         if (!mbar_wait(wbar, 0)) *abort_flag = 1;
     }
 
-    const float *bias = a.bias + g * C;
     for (int t = 0; t <= T; ++t) {
         if (threadIdx.x == 0 && t < T && !*abort_flag) {
             const int y = y_a + t;
@@ -298,7 +336,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         }
         if (t > 0) {
             const int tp = t - 1;
-            __syncthreads();  // abort_flag from thread 0 is visible
+            // the staging buffer of tile tp was last read by the TMA store two tiles ago
+            if (MODE != MODE_SHUFFLE && threadIdx.x == 0) bulk_wait_read1();
+            __syncthreads();  // abort_flag from thread 0 is visible; staging buffer free
             const bool aborted = *abort_flag != 0;
             bool ok = !aborted && mbar_wait(&mdone[tp & 1], (tp >> 1) & 1);
             if (!ok) {
@@ -316,19 +356,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                         ++loaded_rows;
                     }
                 }
-                // epilogue of tile tp: warp w drains TMEM lanes 32w..32w+31
+                // epilogue of tile tp: warp w drains TMEM lanes 32 (w & 3) .. +31
+                // (pixels) and accumulator columns 32 (w >> 2) .. +31 (channels)
                 const int y = y_a + tp;
-                const int x = cb * TM + warp * 32 + lane;
-                const uint32_t taddr = tmem + (uint32_t)((tp & 1) * C) + ((uint32_t)(warp * 32) << 16);
-                float v[C];
+                const int j = (warp & 3) * 32 + lane;
+                const int half = warp >> 2;
+                const int x = cb * TM + j;
+                const uint32_t taddr = tmem + (uint32_t)((tp & 1) * C + half * 32) +
+                                       ((uint32_t)((warp & 3) * 32) << 16);
+                float v[32];
                 tmem_ld32(taddr, v);
-                tmem_ld32(taddr + 32, v + 32);
                 tmem_wait_ld();
                 if (MODE == MODE_RESID) {
                     const uint4 *sp = reinterpret_cast<const uint4 *>(
-                        a.skip + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C);
+                        a.skip + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C + half * 32);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < 4; ++i) {
                         const uint4 q = sp[i];
                         const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
@@ -339,28 +382,45 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                         }
                     }
                 }
-                uint4 outv[8];
+                uint4 outv[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 4; ++i) {
                     uint32_t w4[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const int c0 = i * 8 + 2 * k;
-                        float v0 = v[c0] + bias[c0], v1 = v[c0 + 1] + bias[c0 + 1];
-                        if (MODE == MODE_RESID) {  // skip already added; bias after the sum
-                        } else {
-                            v0 = v0 > 0.f ? v0 : a.prelu[c0] * v0;
-                            v1 = v1 > 0.f ? v1 : a.prelu[c0 + 1] * v1;
+                        const int c0 = i * 8 + 2 * k, cc = half * 32 + c0;
+                        float v0 = v[c0] + s_bias[cc], v1 = v[c0 + 1] + s_bias[cc + 1];
+                        if (MODE != MODE_RESID) {
+                            v0 = v0 > 0.f ? v0 : s_prelu[cc] * v0;
+                            v1 = v1 > 0.f ? v1 : s_prelu[cc + 1] * v1;
                         }
                         const __nv_bfloat162 bb = __floats2bfloat162_rn(v0, v1);
                         w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
                     }
                     outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
                 }
-                if (MODE == MODE_SHUFFLE)
-                    store_px(a.out, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), outv);
-                else
-                    store_px(a.out, a.H, a.W, y, x, outv);
+                if (MODE == MODE_SHUFFLE) {
+                    store_half_px(a.out, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), half, outv, false);
+                } else {
+                    // staged in the 128-byte swizzled layout the TMA store expects:
+                    // 16-byte chunk i of pixel j at chunk position i ^ (j & 7)
+                    uint4 *st = reinterpret_cast<uint4 *>(stage + (tp & 1) * STAGE + j * 128);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) st[(half * 4 + i) ^ (j & 7)] = outv[i];
+                    if (x == 0 || x == a.W - 1) store_half_px(a.out, a.H, a.W, y, x, half, outv, true);
+                    fence_proxy_async();
+                }
+            }
+            if (MODE != MODE_SHUFFLE) {
+                __syncthreads();  // the staged tile is complete
+                if (threadIdx.x == 0 && !*abort_flag) {
+                    const unsigned char *src = stage + (tp & 1) * STAGE;
+                    const int y = y_a + tp;
+                    tma_store_3d(&tm_out, src, 0, cb * TM + 1, y + 1);
+                    if (y == 0) tma_store_3d(&tm_out, src, 0, cb * TM + 1, a.H + 1);
+                    if (y == a.H - 1) tma_store_3d(&tm_out, src, 0, cb * TM + 1, 0);
+                    bulk_commit();
+                }
             }
             tc_fence_before();
             __syncthreads();  // accumulator tp & 1 drained before it is reused
@@ -368,6 +428,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             if (*abort_flag) break;
         }
     }
+    if (MODE != MODE_SHUFFLE && threadIdx.x == 0) bulk_wait_all();  // tile stores complete
     if (*abort_flag && threadIdx.x == 0) {
         atomicExch(a.err, 1);
         // wait (bounded) for the last row load issued into each slot, so that
@@ -555,6 +616,20 @@ bool make_act_map(CUtensorMap *m, void *base, int H, int W) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// padded activation as the destination of a tile: box 64 channels x 128 pixels
+// x 1 row, 128-byte swizzle (the epilogue stages the tile in that layout)
+bool make_out_map(CUtensorMap *m, void *base, int H, int W) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)(W + 2), (cuuint64_t)(H + 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)(W + 2) * C * 2};
+    cuuint32_t box[3] = {(cuuint32_t)C, (cuuint32_t)TM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // packed weights [layers][9][64 co][64 ci] bf16 as a 4D tensor; box = one layer
 bool make_w_map(CUtensorMap *m, void *base, int layers) {
     EncodeTiledFn enc = encode_fn();
@@ -582,8 +657,8 @@ cudaError_t prepare_conv() {
 }
 
 template <int MODE>
-cudaError_t launch_conv(const CUtensorMap &tm_in, const CUtensorMap &tm_w, ConvArgs a, int groups,
-                        cudaStream_t s) {
+cudaError_t launch_conv(const CUtensorMap &tm_in, const CUtensorMap &tm_w, const CUtensorMap &tm_out,
+                        ConvArgs a, int groups, cudaStream_t s) {
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -593,7 +668,7 @@ cudaError_t launch_conv(const CUtensorMap &tm_in, const CUtensorMap &tm_w, ConvA
     if (chunks > a.H) chunks = a.H;
     a.rows_per_chunk = (a.H + chunks - 1) / chunks;
     a.chunks = chunks;
-    k_conv_tc<MODE><<<strips * chunks, CONV_THREADS, CONV_SMEM, s>>>(tm_in, tm_w, a);
+    k_conv_tc<MODE><<<strips * chunks, CONV_THREADS, CONV_SMEM, s>>>(tm_in, tm_w, tm_out, a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -617,7 +692,8 @@ cudaError_t ensure_buffers(SrState *st, int nc) {
     if (e == cudaSuccess) e = cudaMalloc(&st->fine_out, sizeof(float) * 4 * nc * nc);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < 3; ++i)
-        if (!make_act_map(&st->tm_act[i], st->act[i], nc, nc)) return cudaErrorInvalidValue;
+        if (!make_act_map(&st->tm_act[i], st->act[i], nc, nc) || !make_out_map(&st->tm_out[i], st->act[i], nc, nc))
+            return cudaErrorInvalidValue;
     st->nc = nc;
     return cudaSuccess;
 }
@@ -772,17 +848,17 @@ mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t s, ch
         const int nxt = (cur + 1) % 3, tmp = (cur + 2) % 3;
         ConvArgs a1 = {nullptr, (__nv_bfloat16 *)st->act[tmp], st->bias_tc + (size_t)(2 * k) * C,
                        st->prelu_blk + (size_t)k * C, nc, nc, 2 * k, 0, 0, st->err};
-        e = launch_conv<MODE_PRELU>(st->tm_act[cur], st->tm_w, a1, 1, s);
+        e = launch_conv<MODE_PRELU>(st->tm_act[cur], st->tm_w, st->tm_out[tmp], a1, 1, s);
         if (e != cudaSuccess) break;
         ConvArgs a2 = {(const __nv_bfloat16 *)st->act[cur], (__nv_bfloat16 *)st->act[nxt],
                        st->bias_tc + (size_t)(2 * k + 1) * C, nullptr, nc, nc, 2 * k + 1, 0, 0, st->err};
-        e = launch_conv<MODE_RESID>(st->tm_act[tmp], st->tm_w, a2, 1, s);
+        e = launch_conv<MODE_RESID>(st->tm_act[tmp], st->tm_w, st->tm_out[nxt], a2, 1, s);
         cur = nxt;
     }
     if (e == cudaSuccess) {
         ConvArgs au = {nullptr, (__nv_bfloat16 *)st->fine_act, st->bias_tc + (size_t)(2 * nb) * C, st->prelu_up,
                        nc, nc, 2 * nb, 0, 0, st->err};
-        e = launch_conv<MODE_SHUFFLE>(st->tm_act[cur], st->tm_w, au, 4, s);
+        e = launch_conv<MODE_SHUFFLE>(st->tm_act[cur], st->tm_w, st->tm_out[cur] /* unused */, au, 4, s);
     }
     if (e == cudaSuccess) {
         const int nf = 2 * nc;
@@ -807,9 +883,10 @@ mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip
         snprintf(err, errlen, "sr_conv_layer: bad mode %d or size %dx%d (W a multiple of %d)", mode, H, W, TM);
         return MG_ERR_INVALID_ARG;
     }
-    CUtensorMap tin, tw;
+    CUtensorMap tin, tw, tout;
     const int groups = mode == MODE_SHUFFLE ? 4 : 1;
-    if (!make_act_map(&tin, const_cast<void *>(in), H, W) || !make_w_map(&tw, const_cast<void *>(w_packed), groups)) {
+    if (!make_act_map(&tin, const_cast<void *>(in), H, W) || !make_w_map(&tw, const_cast<void *>(w_packed), groups) ||
+        !(mode == MODE_SHUFFLE ? make_act_map(&tout, const_cast<void *>(in), H, W) : make_out_map(&tout, out, H, W))) {
         snprintf(err, errlen, "sr_conv_layer: tensor map encoding failed");
         return MG_ERR_INVALID_ARG;
     }
@@ -819,9 +896,9 @@ mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip
     if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(int), s);
     ConvArgs a = {(const __nv_bfloat16 *)skip, (__nv_bfloat16 *)out, bias, prelu, H, W, 0, 0, 0, dflag};
     if (e == cudaSuccess) {
-        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, tw, a, 1, s);
-        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, tw, a, 1, s);
-        else e = launch_conv<MODE_SHUFFLE>(tin, tw, a, 4, s);
+        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, tw, tout, a, 1, s);
+        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, tw, tout, a, 1, s);
+        else e = launch_conv<MODE_SHUFFLE>(tin, tw, tout, a, 4, s);
     }
     int flag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);

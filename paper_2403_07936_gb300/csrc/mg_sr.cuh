@@ -46,7 +46,8 @@ struct SrState {
     double *red = nullptr;                       // reduction partials
     unsigned *red_counter = nullptr;
     int *err = nullptr;                          // device error flag (bounded waits)
-    CUtensorMap tm_act[3];
+    CUtensorMap tm_act[3];  // activation buffers as convolution inputs (row planes)
+    CUtensorMap tm_out[3];  // the same buffers as destinations of output tiles
     CUtensorMap tm_w;
 };
 
