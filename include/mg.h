@@ -129,6 +129,58 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *x, mg_prolong prolong)
 mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
                            double tol, mg_prolong prolong, mg_solve_info *infos);
 
+/* ---------------------------------------------------------------------
+ * Continuous-batching server (mixed precision, cubic prolongation).
+ * Requests wait in a FIFO until a slot - a resident level hierarchy plus f
+ * and x of the request's size - and the device-memory budget allow
+ * admission.  Each mg_server_tick runs one outer step of defect correction
+ * (FP64 residual, inner_cycles FP32 V-cycles, FP64 update) for every admitted
+ * request as batched launches: new requests start with their first residual
+ * while the others continue, and requests that converged are retired (zero-
+ * mean projection, the solution copied to x_out, and kept on the device as the
+ * warm start of the next request of the same stream_id and N).  Requests thus
+ * join and leave between ticks while the rest of the batch keeps running.
+ * ------------------------------------------------------------------- */
+typedef struct mg_server mg_server;
+
+/* Create a server on the current device.  hbm_budget_bytes bounds the device
+ * memory of its slots, warm starts and tables; other arguments as for
+ * mg_set_options.  Work is ordered on cuda_stream. */
+mg_status mg_server_create(size_t hbm_budget_bytes, int nu_pre, int nu_post, int inner_cycles, int max_cycles,
+                           double tol, void *cuda_stream, mg_server **out);
+
+/* Queue a request: N x N source f (host or device, read when the request is
+ * admitted, so it must stay valid until then), solution written to x_out
+ * (host or device, may be NULL) when it retires.  stream_id >= 0 enables warm
+ * starts across requests of one stream; -1 means none.  request_id (may be
+ * NULL) receives the id that mg_server_poll reports. */
+mg_status mg_server_submit(mg_server *srv, int stream_id, int N, const double *f, double *x_out,
+                           long long *request_id);
+
+/* Admit what fits, run one outer step for all admitted requests, retire the
+ * converged ones.  Synchronous.  Outputs (may be NULL): requests in flight,
+ * requests still queued, requests retired by this tick. */
+mg_status mg_server_tick(mg_server *srv, int *n_active, int *n_queued, int *n_done);
+
+/* One retired request.  Times are milliseconds on the server's monotonic
+ * clock (zero at mg_server_create); info.time_ms = t_finish_ms - t_submit_ms. */
+typedef struct mg_server_result {
+    long long request_id;
+    int stream_id;
+    int N;
+    mg_status status;
+    int pad;
+    double t_submit_ms;
+    double t_admit_ms;
+    double t_finish_ms;
+    mg_solve_info info;
+} mg_server_result;
+
+/* Pop the oldest retired request into *result (*got = 1), or set *got = 0. */
+mg_status mg_server_poll(mg_server *srv, mg_server_result *result, int *got);
+
+void mg_server_destroy(mg_server *srv);
+
 void mg_destroy(mg_ctx *ctx);
 const char *mg_status_string(mg_status status);
 const char *mg_last_error(void);

@@ -533,7 +533,7 @@ static mg_status batch_build(BatchPlan *p) {
         const double h = 2.0 * 3.14159265358979323846 / n;
         int nblk = (int)(((size_t)n * n) / 16384);
         nblk = nblk < 1 ? 1 : (nblk > kRedBlocks ? kRedBlocks : nblk);
-        rhs[r] = RhsDesc{p->f[r], p->x[r], c->lv[0].b32, c->lv[0].x32, n, blk, nblk, 0, h * h};
+        rhs[r] = RhsDesc{p->f[r], p->x[r], c->lv[0].b32, c->lv[0].x32, n, blk, nblk, r, 0, 0, h * h};
         blk += nblk;
         maxN = n > maxN ? n : maxN;
     }
@@ -642,7 +642,7 @@ static mg_status batch_build(BatchPlan *p) {
             e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), true, nullptr, p->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), nullptr, p->out(kGrpF), p->tol, step,
-                                     c0->max_cycles, true, p->d_active, handle, s);
+                                     c0->max_cycles, true, p->d_active, handle, true, s);
         if (e != cudaSuccess) break;
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *deps = nullptr;
@@ -673,7 +673,7 @@ static mg_status batch_build(BatchPlan *p) {
             e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), false, p->d_active, p->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), p->out(kGrpU), p->out(kGrpF), p->tol,
-                                     step, c0->max_cycles, false, p->d_active, handle, s);
+                                     step, c0->max_cycles, false, p->d_active, handle, true, s);
         if (e != cudaSuccess) break;
         e = cudaStreamEndCapture(s, &body);
         capturing = false;
@@ -791,6 +791,392 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
     if (worst == MG_ERR_NONFINITE) set_err("non-finite residual in a batched right-hand side");
     if (worst == MG_ERR_NOT_CONVERGED) set_err("a batched right-hand side did not converge");
     return worst;
+}
+
+// ---------------------------------------------------------------------------
+// Continuous-batching server.  Requests wait in a FIFO until a slot (a
+// resident level hierarchy plus FP64 f and x of the request's size) and the
+// device-memory budget allow admission.  Every tick runs one outer step of
+// defect correction for every admitted request as batched launches (new
+// requests start with their first residual, the others continue), then
+// retires the requests that converged: zero-mean projection, the solution
+// copied to the caller's buffer and kept as the warm start of the request's
+// stream.  Requests therefore join and leave the batch between ticks while
+// the others keep going.
+// ---------------------------------------------------------------------------
+constexpr int kServerSlots = 1024;
+
+struct ServerSlot {
+    mg_ctx *ctx = nullptr;
+    int N = 0;
+    double *f = nullptr, *x = nullptr;
+    size_t bytes = 0;
+    bool busy = false, first = false;
+    long long req = -1;
+    int stream_id = -1;
+    double *x_out = nullptr;
+    double t_submit = 0.0, t_admit = 0.0;
+};
+struct ServerRequest {
+    long long id;
+    int stream_id, N;
+    const double *f;
+    double *x_out;
+    double t_submit;
+};
+
+struct mg_server {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0, used = 0;
+    int nu1 = 2, nu2 = 2, inner = 2, max_cycles = 100;
+    double tol = 1e-10;
+    std::vector<ServerSlot> slots;
+    std::vector<ServerRequest> queue;  // FIFO
+    size_t qhead = 0;
+    std::vector<std::pair<long long, double *>> warm;  // key = stream_id * 2^20 + N -> last solution
+    std::vector<mg_server_result> done;
+    size_t dhead = 0;
+    long long next_id = 0;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double now_ms() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    // device state and tables
+    void *dmem = nullptr;
+    DevState *d_state = nullptr;
+    int *d_active = nullptr;
+    double *d_out = nullptr, *d_partials = nullptr;
+    unsigned *d_counters = nullptr;
+    char *d_tab = nullptr, *h_tab = nullptr;  // tables, pinned staging
+    size_t tab_bytes = 0;
+    DevState *h_state = nullptr;
+    int *h_active = nullptr;
+    FirTaps taps;
+    BatchRed red(int g) const { return BatchRed{d_partials, d_counters, d_out + (size_t)g * kServerSlots * kMaxSlots}; }
+    double *out(int g) const { return d_out + (size_t)g * kServerSlots * kMaxSlots; }
+};
+
+static size_t server_slot_bytes(int N) {
+    size_t b = 2ull * N * N * sizeof(double);  // f, x
+    for (int n = N; n >= 8; n >>= 1) b += 3ull * n * n * sizeof(float);
+    return b;
+}
+
+static int server_levels(int N) {
+    int l = 1;
+    for (int n = N; n > 8; n >>= 1) ++l;
+    return l;
+}
+
+static double *server_warm(mg_server *sv, int stream_id, int N, bool create) {
+    const long long key = (long long)stream_id * (1ll << 20) + N;
+    for (auto &w : sv->warm)
+        if (w.first == key) return w.second;
+    if (!create) return nullptr;
+    double *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * N * N) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    sv->used += sizeof(double) * N * N;
+    sv->warm.push_back({key, buf});
+    return buf;
+}
+
+static void server_free_slot(mg_server *sv, size_t k) {
+    ServerSlot &sl = sv->slots[k];
+    cudaFree(sl.f);
+    cudaFree(sl.x);
+    mg_destroy(sl.ctx);
+    sv->used -= sl.bytes;
+    sl = ServerSlot();
+}
+
+// Free idle hierarchies of other sizes, least recently used first, until
+// `need` more bytes fit the budget.  Slot indices never move (the device
+// state is indexed by them); a freed entry is reused by later admissions.
+static bool server_make_room(mg_server *sv, size_t need, int N) {
+    while (sv->used + need > sv->budget) {
+        long long best = -1;
+        double oldest = 0.0;
+        for (size_t k = 0; k < sv->slots.size(); ++k) {
+            const ServerSlot &sl = sv->slots[k];
+            if (sl.ctx && !sl.busy && sl.N != N && (best < 0 || sl.t_admit < oldest)) {
+                best = (long long)k;
+                oldest = sl.t_admit;
+            }
+        }
+        if (best < 0) return false;
+        server_free_slot(sv, (size_t)best);
+    }
+    return true;
+}
+
+// Admit queued requests in FIFO order while a slot and the budget allow.
+static mg_status server_admit(mg_server *sv) {
+    while (sv->qhead < sv->queue.size()) {
+        const ServerRequest &rq = sv->queue[sv->qhead];
+        int sid = -1, empty = -1;
+        for (size_t k = 0; k < sv->slots.size(); ++k) {
+            const ServerSlot &sl = sv->slots[k];
+            if (sl.ctx && !sl.busy && sl.N == rq.N) {
+                sid = (int)k;
+                break;
+            }
+            if (!sl.ctx && empty < 0) empty = (int)k;
+        }
+        if (sid < 0) {
+            const size_t need = server_slot_bytes(rq.N);
+            if (sv->used + need > sv->budget) server_make_room(sv, need, rq.N);
+            if (empty < 0) {  // make_room may have freed an entry
+                for (size_t k = 0; k < sv->slots.size() && empty < 0; ++k)
+                    if (!sv->slots[k].ctx) empty = (int)k;
+            }
+            if (empty < 0 || sv->used + need > sv->budget) break;
+            ServerSlot sl;
+            MG_TRY(mg_setup(server_levels(rq.N), rq.N, &sl.ctx));
+            sl.ctx->nu1 = sv->nu1;
+            sl.ctx->nu2 = sv->nu2;
+            sl.ctx->inner = sv->inner;
+            sl.ctx->max_cycles = sv->max_cycles;
+            sl.ctx->stream = sv->stream;
+            mg_status st = ensure_hierarchy(sl.ctx, false);
+            if (st == MG_OK && cudaMalloc(&sl.f, sizeof(double) * rq.N * rq.N) != cudaSuccess) st = MG_ERR_OOM;
+            if (st == MG_OK && cudaMalloc(&sl.x, sizeof(double) * rq.N * rq.N) != cudaSuccess) st = MG_ERR_OOM;
+            if (st != MG_OK) {
+                cudaGetLastError();
+                cudaFree(sl.f);
+                cudaFree(sl.x);
+                mg_destroy(sl.ctx);
+                if (st == MG_ERR_OOM) break;  // wait for memory to free up
+                return st;
+            }
+            sl.N = rq.N;
+            sl.bytes = need;
+            sv->used += need;
+            sv->slots[empty] = sl;
+            sid = empty;
+        }
+        ServerSlot &sl = sv->slots[sid];
+        const size_t bytes = sizeof(double) * rq.N * rq.N;
+        MG_CUDA(cudaMemcpyAsync(sl.f, rq.f, bytes, cudaMemcpyDefault, sv->stream));
+        const double *w = server_warm(sv, rq.stream_id, rq.N, false);
+        if (w)
+            MG_CUDA(cudaMemcpyAsync(sl.x, w, bytes, cudaMemcpyDeviceToDevice, sv->stream));
+        else
+            MG_CUDA(cudaMemsetAsync(sl.x, 0, bytes, sv->stream));
+        sl.busy = true;
+        sl.first = true;
+        sl.req = rq.id;
+        sl.stream_id = rq.stream_id;
+        sl.x_out = rq.x_out;
+        sl.t_submit = rq.t_submit;
+        sl.t_admit = sv->now_ms();
+        ++sv->qhead;
+    }
+    if (sv->qhead == sv->queue.size()) {
+        sv->queue.clear();
+        sv->qhead = 0;
+    }
+    return MG_OK;
+}
+
+// Tables for one tick live in one staging block: [RhsDesc x n][first-slot
+// RhsDesc x nf][TileGrid ...][BottomGrid ...]; offsets in bytes.
+struct TickPlan {
+    std::vector<RhsDesc> rhs, firsts, dones;
+    std::vector<TileGrid> tiles;
+    std::vector<BottomGrid> bottoms;
+    std::vector<BatchLaunch> cyc[2];
+    int blk = 0, blk_first = 0, blk_done = 0;
+};
+
+static void plan_rhs(std::vector<RhsDesc> &v, int &blk, const ServerSlot &sl, int sid) {
+    const int n = sl.N;
+    const double h = 2.0 * 3.14159265358979323846 / n;
+    int nblk = (int)(((size_t)n * n) / 16384);
+    nblk = nblk < 1 ? 1 : (nblk > kRedBlocks ? kRedBlocks : nblk);
+    v.push_back(RhsDesc{sl.f, sl.x, sl.ctx->lv[0].b32, sl.ctx->lv[0].x32, n, blk, nblk, sid, sl.first ? 1 : 0, 0,
+                        h * h});
+    blk += nblk;
+}
+
+static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sids) {
+    int maxN = 0;
+    for (int sid : sids) maxN = sv->slots[sid].N > maxN ? sv->slots[sid].N : maxN;
+    for (int v = 0; v < 2; ++v) {
+        const bool first = v == 0;
+        for (int sz = maxN; sz > kBottomMax; sz >>= 1) {
+            BatchLaunch L{0, tp.tiles.size(), 0, 0};
+            for (int sid : sids) {
+                mg_ctx *c = sv->slots[sid].ctx;
+                for (int l = 0; l + 1 < c->levels; ++l)
+                    if (c->lv[l].n == sz) {
+                        tp.tiles.push_back(TileGrid{c->lv[l].x32, c->lv[l].t32, c->lv[l].b32, c->lv[l + 1].b32, sz,
+                                                    (l > 0 || first) ? 1 : 0, L.nblocks, sid});
+                        L.nblocks += (sz / 64) * (sz / 64);
+                        ++L.ngrid;
+                    }
+            }
+            if (L.ngrid) tp.cyc[v].push_back(L);
+        }
+        BatchLaunch Lb{2, tp.bottoms.size(), 0, 0};
+        for (int sid : sids) {
+            mg_ctx *c = sv->slots[sid].ctx;
+            int l = 0;
+            while (c->lv[l].n > kBottomMax) ++l;
+            tp.bottoms.push_back(BottomGrid{c->lv[l].x32, c->lv[l].b32, c->ainv32, c->lv[l].n, c->levels - l,
+                                            (l > 0 || first) ? 1 : 0, sid});
+            ++Lb.ngrid;
+        }
+        Lb.nblocks = Lb.ngrid;
+        tp.cyc[v].push_back(Lb);
+        for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {
+            BatchLaunch L{1, tp.tiles.size(), 0, 0};
+            for (int sid : sids) {
+                mg_ctx *c = sv->slots[sid].ctx;
+                for (int l = 0; l + 1 < c->levels; ++l)
+                    if (c->lv[l].n == sz) {
+                        tp.tiles.push_back(TileGrid{c->lv[l].t32, c->lv[l].x32, c->lv[l].b32, c->lv[l + 1].x32, sz, 0,
+                                                    L.nblocks, sid});
+                        L.nblocks += (sz / 64) * (sz / 64);
+                        ++L.ngrid;
+                    }
+            }
+            if (L.ngrid) tp.cyc[v].push_back(L);
+        }
+    }
+}
+
+// Copy the plan's tables to the device in one transfer; returns device pointers.
+static mg_status upload_plan(mg_server *sv, const TickPlan &tp, RhsDesc **d_rhs, RhsDesc **d_first,
+                             TileGrid **d_tiles, BottomGrid **d_bottom) {
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t o1 = al(sizeof(RhsDesc) * tp.rhs.size());
+    const size_t o2 = o1 + al(sizeof(RhsDesc) * (tp.firsts.size() + 1));
+    const size_t o3 = o2 + al(sizeof(TileGrid) * (tp.tiles.size() + 1));
+    const size_t total = o3 + al(sizeof(BottomGrid) * (tp.bottoms.size() + 1));
+    if (total > sv->tab_bytes) {
+        cudaFree(sv->d_tab);
+        cudaFreeHost(sv->h_tab);
+        sv->d_tab = nullptr;
+        sv->h_tab = nullptr;
+        MG_CUDA(cudaMalloc(&sv->d_tab, 2 * total));
+        MG_CUDA(cudaMallocHost(&sv->h_tab, 2 * total));
+        sv->tab_bytes = 2 * total;
+    }
+    memcpy(sv->h_tab, tp.rhs.data(), sizeof(RhsDesc) * tp.rhs.size());
+    memcpy(sv->h_tab + o1, tp.firsts.data(), sizeof(RhsDesc) * tp.firsts.size());
+    memcpy(sv->h_tab + o2, tp.tiles.data(), sizeof(TileGrid) * tp.tiles.size());
+    memcpy(sv->h_tab + o3, tp.bottoms.data(), sizeof(BottomGrid) * tp.bottoms.size());
+    MG_CUDA(cudaMemcpyAsync(sv->d_tab, sv->h_tab, total, cudaMemcpyHostToDevice, sv->stream));
+    *d_rhs = (RhsDesc *)sv->d_tab;
+    *d_first = (RhsDesc *)(sv->d_tab + o1);
+    *d_tiles = (TileGrid *)(sv->d_tab + o2);
+    *d_bottom = (BottomGrid *)(sv->d_tab + o3);
+    return MG_OK;
+}
+
+static mg_status server_tick(mg_server *sv, int *n_active, int *n_queued, int *n_done) {
+    MG_CUDA(cudaSetDevice(sv->device));
+    MG_TRY(server_admit(sv));
+    cudaStream_t s = sv->stream;
+    TickPlan tp;
+    std::vector<int> sids;
+    for (size_t k = 0; k < sv->slots.size(); ++k)
+        if (sv->slots[k].busy) {
+            sids.push_back((int)k);
+            plan_rhs(tp.rhs, tp.blk, sv->slots[k], (int)k);
+            if (sv->slots[k].first) plan_rhs(tp.firsts, tp.blk_first, sv->slots[k], (int)k);
+        }
+    int finished = 0;
+    if (!sids.empty()) {
+        plan_cycles(sv, tp, sids);
+        RhsDesc *d_rhs, *d_first;
+        TileGrid *d_tiles;
+        BottomGrid *d_bottom;
+        MG_TRY(upload_plan(sv, tp, &d_rhs, &d_first, &d_tiles, &d_bottom));
+        const int nr = (int)tp.rhs.size();
+        if (!tp.firsts.empty())
+            MG_CUDA(launch_sum_batched(d_first, (int)tp.firsts.size(), tp.blk_first, false, sv->red(kGrpF), s));
+        MG_CUDA(launch_outer_residual_batched(d_rhs, nr, tp.blk, sv->out(kGrpF), true, nullptr, sv->red(kGrpR), s));
+        MG_CUDA(launch_check_batched(sv->d_state, d_rhs, nr, sv->out(kGrpR), sv->out(kGrpU), sv->out(kGrpF), sv->tol,
+                                     sv->inner, sv->max_cycles, false, sv->d_active, cudaGraphConditionalHandle(), false,
+                                     s));
+        for (int k = 0; k < sv->inner; ++k)
+            for (const BatchLaunch &L : tp.cyc[k == 0 ? 0 : 1]) {
+                if (L.kind == 0)
+                    MG_CUDA(launch_down_batched(d_tiles + L.off, L.ngrid, L.nblocks, sv->nu1, sv->d_active, s));
+                else if (L.kind == 1)
+                    MG_CUDA(launch_up_batched(d_tiles + L.off, L.ngrid, L.nblocks, sv->nu2, sv->d_active, sv->taps, s));
+                else
+                    MG_CUDA(launch_bottom_batched(d_bottom + L.off, L.ngrid, sv->nu1, sv->nu2, sv->d_active, sv->taps, s));
+            }
+        MG_CUDA(launch_update_batched(d_rhs, nr, tp.blk, sv->d_active, sv->red(kGrpU), s));
+        const int ns = sids.back() + 1;
+        MG_CUDA(cudaMemcpyAsync(sv->h_state, sv->d_state, sizeof(DevState) * ns, cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaMemcpyAsync(sv->h_active, sv->d_active, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaStreamSynchronize(s));
+        // retire: projection, result out, warm start kept
+        std::vector<int> retire;
+        for (int sid : sids) {
+            ServerSlot &sl = sv->slots[sid];
+            sl.first = false;
+            if (!sv->h_active[sid]) retire.push_back(sid);
+        }
+        if (!retire.empty()) {
+            TickPlan rp;
+            for (int sid : retire) plan_rhs(rp.rhs, rp.blk, sv->slots[sid], sid);
+            RhsDesc *d_r, *d_f;
+            TileGrid *d_t;
+            BottomGrid *d_b;
+            MG_TRY(upload_plan(sv, rp, &d_r, &d_f, &d_t, &d_b));
+            MG_CUDA(launch_sum_batched(d_r, (int)rp.rhs.size(), rp.blk, true, sv->red(kGrpX), s));
+            MG_CUDA(launch_project_batched(d_r, (int)rp.rhs.size(), rp.blk, sv->out(kGrpX), sv->d_state, s));
+            for (int sid : retire) {
+                ServerSlot &sl = sv->slots[sid];
+                const size_t bytes = sizeof(double) * sl.N * sl.N;
+                if (sl.x_out) MG_CUDA(cudaMemcpyAsync(sl.x_out, sl.x, bytes, cudaMemcpyDefault, s));
+                if (sl.stream_id >= 0) {
+                    double *w = server_warm(sv, sl.stream_id, sl.N, true);
+                    if (w) MG_CUDA(cudaMemcpyAsync(w, sl.x, bytes, cudaMemcpyDeviceToDevice, s));
+                }
+            }
+            MG_CUDA(cudaStreamSynchronize(s));
+            const double t_fin = sv->now_ms();
+            for (int sid : retire) {
+                ServerSlot &sl = sv->slots[sid];
+                const DevState &ds = sv->h_state[sid];
+                mg_server_result d;
+                d.request_id = sl.req;
+                d.stream_id = sl.stream_id;
+                d.N = sl.N;
+                d.status = (mg_status)ds.status;
+                d.t_submit_ms = sl.t_submit;
+                d.t_admit_ms = sl.t_admit;
+                d.t_finish_ms = t_fin;
+                d.info.outer_iters = ds.outer;
+                d.info.vcycles = ds.cycles;
+                d.info.rel_residual = ds.rel;
+                d.info.removed_mean = ds.mu;
+                d.info.update_norm = ds.unorm;
+                d.info.time_ms = t_fin - sl.t_submit;
+                d.info.prolong_used = MG_PROLONG_CUBIC;
+                d.info.sr_fallback = 0;
+                sv->done.push_back(d);
+                sl.busy = false;
+                sl.req = -1;
+                ++finished;
+            }
+        }
+    }
+    int active = 0;
+    for (const ServerSlot &sl : sv->slots) active += sl.busy ? 1 : 0;
+    if (n_active) *n_active = active;
+    if (n_queued) *n_queued = (int)(sv->queue.size() - sv->qhead);
+    if (n_done) *n_done = finished;
+    return MG_OK;
 }
 
 extern "C" {
@@ -1159,6 +1545,110 @@ mg_status mg_probe_read(mg_ctx *c, int *launches, double *total_ms, double *byte
     c->probe_used = 0;
     c->probe_bytes = 0.0;
     return MG_OK;
+}
+
+
+mg_status mg_server_create(size_t hbm_budget_bytes, int nu_pre, int nu_post, int inner_cycles, int max_cycles,
+                           double tol, void *cuda_stream, mg_server **out) {
+    if (out) *out = nullptr;
+    if (!out || nu_pre < 0 || nu_pre > 4 || nu_post < 0 || nu_post > 4 || inner_cycles < 1 || inner_cycles > 16 ||
+        max_cycles < 1 || !(tol >= 0.0)) {
+        set_err("invalid server options");
+        return MG_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    mg_server *sv = new (std::nothrow) mg_server();
+    if (!sv) return MG_ERR_OOM;
+    MG_CUDA(cudaGetDevice(&sv->device));
+    sv->stream = (cudaStream_t)cuda_stream;
+    sv->budget = hbm_budget_bytes;
+    sv->nu1 = nu_pre;
+    sv->nu2 = nu_post;
+    sv->inner = inner_cycles;
+    sv->max_cycles = max_cycles;
+    sv->tol = tol;
+    sv->slots.resize(kServerSlots);
+    fir_taps_host(&sv->taps);
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t o_state = 0, o_act = al(sizeof(DevState) * kServerSlots);
+    const size_t o_out = o_act + al(sizeof(int) * kServerSlots);
+    const size_t o_cnt = o_out + al(sizeof(double) * 4 * kServerSlots * kMaxSlots);
+    const size_t o_part = o_cnt + al(sizeof(unsigned) * kServerSlots);
+    const size_t total = o_part + al(sizeof(double) * kMaxSlots * (size_t)kServerSlots * kRedBlocks);
+    cudaError_t e = cudaMalloc(&sv->dmem, total);
+    if (e == cudaSuccess) e = cudaMemset(sv->dmem, 0, total);
+    if (e == cudaSuccess) e = cudaMallocHost(&sv->h_state, sizeof(DevState) * kServerSlots);
+    if (e == cudaSuccess) e = cudaMallocHost(&sv->h_active, sizeof(int) * kServerSlots);
+    if (e != cudaSuccess) {
+        set_err("server setup: %s", cudaGetErrorString(e));
+        mg_server_destroy(sv);
+        return MG_ERR_OOM;
+    }
+    char *d = (char *)sv->dmem;
+    sv->d_state = (DevState *)(d + o_state);
+    sv->d_active = (int *)(d + o_act);
+    sv->d_out = (double *)(d + o_out);
+    sv->d_counters = (unsigned *)(d + o_cnt);
+    sv->d_partials = (double *)(d + o_part);
+    sv->used = total;
+    *out = sv;
+    return MG_OK;
+}
+
+mg_status mg_server_submit(mg_server *sv, int stream_id, int N, const double *f, double *x_out,
+                           long long *request_id) {
+    if (!sv || !f || !is_pow2(N) || N < 8 || N > 16384) {
+        set_err("invalid request (N a power of two in [8, 16384], f not null)");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (server_slot_bytes(N) > sv->budget) {
+        set_err("a %d^2 request needs more than the server's memory budget", N);
+        return MG_ERR_OOM;
+    }
+    ServerRequest rq{sv->next_id++, stream_id, N, f, x_out, sv->now_ms()};
+    sv->queue.push_back(rq);
+    if (request_id) *request_id = rq.id;
+    return MG_OK;
+}
+
+mg_status mg_server_tick(mg_server *sv, int *n_active, int *n_queued, int *n_done) {
+    if (!sv) {
+        set_err("null server");
+        return MG_ERR_INVALID_ARG;
+    }
+    return server_tick(sv, n_active, n_queued, n_done);
+}
+
+mg_status mg_server_poll(mg_server *sv, mg_server_result *result, int *got) {
+    if (!sv || !got || !result) {
+        set_err("null server or output");
+        return MG_ERR_INVALID_ARG;
+    }
+    *got = 0;
+    if (sv->dhead < sv->done.size()) {
+        *result = sv->done[sv->dhead++];
+        *got = 1;
+        if (sv->dhead == sv->done.size()) {
+            sv->done.clear();
+            sv->dhead = 0;
+        }
+    }
+    return MG_OK;
+}
+
+void mg_server_destroy(mg_server *sv) {
+    if (!sv) return;
+    cudaSetDevice(sv->device);
+    if (sv->stream) cudaStreamSynchronize(sv->stream);
+    for (size_t k = 0; k < sv->slots.size(); ++k)
+        if (sv->slots[k].ctx) server_free_slot(sv, k);
+    for (auto &w : sv->warm) cudaFree(w.second);
+    cudaFree(sv->dmem);
+    cudaFree(sv->d_tab);
+    cudaFreeHost(sv->h_tab);
+    cudaFreeHost(sv->h_state);
+    cudaFreeHost(sv->h_active);
+    delete sv;
 }
 
 // ---------------------------------------------------------------------------

@@ -136,13 +136,16 @@ struct RhsDesc {  // FP64 outer kernels: blocks [blk0, blk0 + nblk) serve this r
     double *x;
     float *s32;      // float residual (inner right-hand side)
     const float *e;  // inner correction
-    int n, blk0, nblk, pad;
+    int n, blk0, nblk;
+    int slot;        // index of its persistent state, sums and active flag
+    int first;       // this step is its first residual evaluation
+    int pad;
     double h2;
 };
 struct BatchRed {
     double *partials;   // [blocks][kMaxSlots]
-    unsigned *counters; // [rhs]
-    double *out;        // [rhs][kMaxSlots]
+    unsigned *counters; // [slots]
+    double *out;        // [slots][kMaxSlots]
 };
 
 // ----------------------------------------------------------------------------
@@ -210,9 +213,12 @@ cudaError_t launch_update_batched(const RhsDesc *rd, int nrhs, int nblocks, cons
                                   cudaStream_t s);
 cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *xsum,
                                    const DevState *st, cudaStream_t s);
+// first: every entry is at its first residual (else each entry's own flag);
+// use_handle: set the graph loop condition (inside a graph only)
 cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, const double *rsum,
                                  const double *usum, const double *fsum, double tol, int step, int max_cycles,
-                                 bool first, int *active, cudaGraphConditionalHandle handle, cudaStream_t s);
+                                 bool first, int *active, cudaGraphConditionalHandle handle, bool use_handle,
+                                 cudaStream_t s);
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,

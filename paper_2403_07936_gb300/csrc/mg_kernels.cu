@@ -685,8 +685,9 @@ __device__ __forceinline__ int find_rhs(const RhsDesc *__restrict__ r, int nrhs)
 }
 
 template <int NS>
-__device__ __forceinline__ void batch_finish(const BatchRed &red, int rhs, int blk0, int nblk,
+__device__ __forceinline__ void batch_finish(const BatchRed &red, int slot, int blk0, int nblk,
                                              const double (&vals)[NS], double *sh) {
+    const int rhs = slot;
     __shared__ bool am_last;
     if (threadIdx.x == 0) {
         for (int k = 0; k < NS; ++k) red.partials[(size_t)blockIdx.x * kMaxSlots + k] = vals[k];
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_b(const RhsDesc *__restrict
     for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x)
         v += a[p];
     double vals[1] = {block_sum(v, sh)};
-    batch_finish<1>(red, r, d.blk0, d.nblk, vals, sh);
+    batch_finish<1>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
 
 template <bool FNORM>
@@ -726,12 +727,11 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc 
                                                                   const double *__restrict__ fsum,
                                                                   const int *__restrict__ active, BatchRed red) {
     __shared__ double sh[32];
-    const int r = find_rhs(rd, nrhs);
-    if (active && !active[r]) return;
-    const RhsDesc d = rd[r];
+    const RhsDesc d = rd[find_rhs(rd, nrhs)];
+    if (active && !active[d.slot]) return;
     const int n = d.n;
     const size_t N = (size_t)n * n;
-    const double mu = fsum[(size_t)r * kMaxSlots] / (double)N;
+    const double mu = fsum[(size_t)d.slot * kMaxSlots] / (double)N;
     double ss = 0.0, ff = 0.0;
     for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x) {
         const int i = (int)(p / n), j = (int)(p - (size_t)i * n);
@@ -748,15 +748,14 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc 
     double vals[2];
     vals[0] = block_sum(ss, sh);
     vals[1] = FNORM ? block_sum(ff, sh) : 0.0;
-    batch_finish<2>(red, r, d.blk0, d.nblk, vals, sh);
+    batch_finish<2>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restrict__ rd, int nrhs,
                                                           const int *__restrict__ active, BatchRed red) {
     __shared__ double sh[32];
-    const int r = find_rhs(rd, nrhs);
-    if (active && !active[r]) return;
-    const RhsDesc d = rd[r];
+    const RhsDesc d = rd[find_rhs(rd, nrhs)];
+    if (active && !active[d.slot]) return;
     const size_t N = (size_t)d.n * d.n;
     double ee = 0.0;
     for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x) {
@@ -765,35 +764,36 @@ __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restr
         ee += e * e;
     }
     double vals[1] = {block_sum(ee, sh)};
-    batch_finish<1>(red, r, d.blk0, d.nblk, vals, sh);
+    batch_finish<1>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_project_b(const RhsDesc *__restrict__ rd, int nrhs,
                                                            const double *__restrict__ xsum,
                                                            const DevState *__restrict__ st) {
-    const int r = find_rhs(rd, nrhs);
-    const RhsDesc d = rd[r];
+    const RhsDesc d = rd[find_rhs(rd, nrhs)];
     const size_t N = (size_t)d.n * d.n;
-    const bool zero = st[r].zero_source != 0;
-    const double mu = xsum[(size_t)r * kMaxSlots] / (double)N;
+    const bool zero = st[d.slot].zero_source != 0;
+    const double mu = xsum[(size_t)d.slot * kMaxSlots] / (double)N;
     for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x)
         d.x[p] = zero ? 0.0 : d.x[p] - mu;
 }
 
-// Convergence test of every right-hand side still active; the loop continues
-// while any is.  One block.
+// Convergence test of every listed right-hand side still active (or at its
+// first residual); a graph loop continues while any is.  One block.
 __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs, const double *rsum,
                           const double *usum, const double *fsum, double tol, int step, int max_cycles,
-                          int first, int *active, cudaGraphConditionalHandle handle) {
+                          int first_all, int *active, cudaGraphConditionalHandle handle, int use_handle) {
     int any = 0;
     for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
-        if (!first && !active[r]) continue;
-        DevState &s = st[r];
+        const int slot = rd[r].slot;
+        const bool first = first_all || rd[r].first;
+        if (!first && !active[slot]) continue;
+        DevState &s = st[slot];
         const double n2 = (double)rd[r].n * rd[r].n, h2 = rd[r].h2;
-        const double *rs = rsum + (size_t)r * kMaxSlots;
+        const double *rs = rsum + (size_t)slot * kMaxSlots;
         if (first) {
             s.fnorm = sqrt(rs[1]);
-            s.mu = fsum[(size_t)r * kMaxSlots] / n2;
+            s.mu = fsum[(size_t)slot * kMaxSlots] / n2;
             s.cycles = 0;
             s.outer = 0;
             s.status = MG_OK;
@@ -802,7 +802,7 @@ __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs
         } else {
             s.cycles += step;
             s.outer += 1;
-            s.unorm = sqrt(usum[(size_t)r * kMaxSlots]);
+            s.unorm = sqrt(usum[(size_t)slot * kMaxSlots]);
         }
         const double rn = sqrt(rs[0]) / h2, fn = s.fnorm;
         int go = 0;
@@ -820,11 +820,11 @@ __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs
                 else s.status = MG_ERR_NOT_CONVERGED;
             }
         }
-        active[r] = go;
+        active[slot] = go;
         any |= go;
     }
     any = __syncthreads_or(any);
-    if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+    if (use_handle && threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
 }
 
 template <typename KernelT>
@@ -1082,8 +1082,10 @@ cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, con
 
 cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, const double *rsum,
                                  const double *usum, const double *fsum, double tol, int step, int max_cycles,
-                                 bool first, int *active, cudaGraphConditionalHandle handle, cudaStream_t s) {
-    k_check_b<<<1, 256, 0, s>>>(st, rd, nrhs, rsum, usum, fsum, tol, step, max_cycles, first ? 1 : 0, active, handle);
+                                 bool first, int *active, cudaGraphConditionalHandle handle, bool use_handle,
+                                 cudaStream_t s) {
+    k_check_b<<<1, 256, 0, s>>>(st, rd, nrhs, rsum, usum, fsum, tol, step, max_cycles, first ? 1 : 0, active, handle,
+                                use_handle ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -34,6 +34,17 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerResult(C.Structure):
+    _fields_ = [("request_id", C.c_longlong), ("stream_id", C.c_int), ("N", C.c_int), ("status", C.c_int),
+                ("pad", C.c_int), ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double),
+                ("t_finish_ms", C.c_double), ("info", SolveInfo)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "info")}
+        d.update(self.info.as_dict())
+        return d
+
+
 SIGNATURES = {
     "mg_setup": (_I, [_I, _I, C.POINTER(_VP)]),
     "mg_set_options": (_I, [_VP, _I, _I, _I, _I, _VP]),
@@ -45,6 +56,11 @@ SIGNATURES = {
     "mg_solve_batched": (_I, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _I, _D, _I,
                               C.POINTER(SolveInfo)]),
     "mg_destroy": (None, [_VP]),
+    "mg_server_create": (_I, [_SZ, _I, _I, _I, _I, _D, _VP, C.POINTER(_VP)]),
+    "mg_server_submit": (_I, [_VP, _I, _I, _VP, _VP, C.POINTER(C.c_longlong)]),
+    "mg_server_tick": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "mg_server_poll": (_I, [_VP, C.POINTER(ServerResult), C.POINTER(_I)]),
+    "mg_server_destroy": (None, [_VP]),
     "mg_status_string": (C.c_char_p, [_I]),
     "mg_last_error": (C.c_char_p, []),
     "mg_kernel_launches": (C.c_ulonglong, []),
@@ -203,6 +219,54 @@ class Context:
     def close(self):
         if self._h:
             load().mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (mg_server_* in include/mg.h).
+
+    submit() queues a request; tick() admits what fits the memory budget, runs
+    one outer defect-correction step for every admitted request and retires
+    the converged ones; poll() returns retired requests.  The caller keeps f
+    (and x_out) alive until the request has retired.
+    """
+
+    def __init__(self, hbm_budget_bytes: int, nu_pre: int = 2, nu_post: int = 2, inner_cycles: int = 2,
+                 max_cycles: int = 100, tol: float = 1e-10, stream=None):
+        h = C.c_void_p()
+        _check(load().mg_server_create(int(hbm_budget_bytes), nu_pre, nu_post, inner_cycles, max_cycles, tol,
+                                       stream_handle(stream), C.byref(h)))
+        self._h = h
+
+    def submit(self, f, x_out=None, stream_id: int = -1) -> int:
+        rid = C.c_longlong()
+        _check(load().mg_server_submit(self._h, stream_id, f.shape[-1], ptr(f), ptr(x_out), C.byref(rid)))
+        return rid.value
+
+    def tick(self):
+        a, q, d = _I(), _I(), _I()
+        _check(load().mg_server_tick(self._h, C.byref(a), C.byref(q), C.byref(d)))
+        return a.value, q.value, d.value
+
+    def poll(self):
+        """All retired requests not yet returned, as dicts."""
+        out = []
+        r, got = ServerResult(), _I()
+        while True:
+            _check(load().mg_server_poll(self._h, C.byref(r), C.byref(got)))
+            if not got.value:
+                return out
+            out.append(r.as_dict())
+
+    def close(self):
+        if self._h:
+            load().mg_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

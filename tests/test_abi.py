@@ -63,3 +63,22 @@ def test_weights_blob_layout_matches_generator_shapes():
     n_params = sum(int(__import__("numpy").prod(s)) for _, s in weight_shapes())
     assert len(blob) == 64 + 4 * n_params
     assert blob[:8] == b"MGSRW001"
+
+
+@pytest.mark.parametrize("args", [(1 << 30, -1, 2, 2, 10, 1e-10), (1 << 30, 2, 5, 2, 10, 1e-10),
+                                  (1 << 30, 2, 2, 0, 10, 1e-10), (1 << 30, 2, 2, 2, 0, 1e-10),
+                                  (1 << 30, 2, 2, 2, 10, float("nan"))])
+def test_server_create_rejects_invalid_options(lib, args):
+    h = C.c_void_p(123)
+    st = lib.mg_server_create(*args, None, C.byref(h))
+    assert st == 1
+    assert h.value is None
+
+
+def test_server_calls_reject_null_server(lib):
+    from paper_2403_07936_gb300 import mg
+    f = (C.c_double * 64)()
+    assert lib.mg_server_submit(None, 0, 8, f, None, None) == 1
+    assert lib.mg_server_tick(None, None, None, None) == 1
+    r, got = mg.ServerResult(), C.c_int()
+    assert lib.mg_server_poll(None, C.byref(r), C.byref(got)) == 1
