@@ -313,6 +313,135 @@ def sr_leg(mg, dev, stream, flush, f_dev, x, args):
                       "rel_residual": infos[-1]["rel_residual"]}}
 
 
+SERVE_SIZES = (128, 256, 512, 1024, 2048)
+SERVE_STREAMS = 16
+SERVE_BUDGET = 160 * (1 << 30)
+SERVE_CHAIN = 4
+
+
+def _serve_sources(dev, rank):
+    """Per stream a chain of SERVE_CHAIN sources, each a 1% perturbation of the last.
+
+    Stream s has grid size SERVE_SIZES[s % 5]; the perturbation fields are
+    drawn once per size and shared by that size's streams.  A stream's
+    requests walk its chain forwards and back (0, 1, 2, 3, 2, 1, 0, 1, ...),
+    so consecutive requests of a stream always differ by one 1% step.
+    """
+    import torch
+    from synthetic.sources import config_seed, default_kmax, perturb_with, turbulent_source
+    gs = {n: [turbulent_source(n, default_kmax(n), config_seed(6, rank * 100000 + 1000 * n + k))
+              for k in range(SERVE_CHAIN - 1)] for n in SERVE_SIZES}
+    chains, sizes = [], []
+    for st in range(SERVE_STREAMS):
+        n = SERVE_SIZES[st % len(SERVE_SIZES)]
+        f = [turbulent_source(n, default_kmax(n), config_seed(5, rank * 100000 + st))]
+        for g in gs[n]:
+            f.append(perturb_with(f[-1], g))
+        chains.append([torch.tensor(a, device=dev) for a in f])
+        sizes.append(n)
+    return chains, sizes
+
+
+def _chain_index(k):
+    period = 2 * (SERVE_CHAIN - 1)
+    k %= period
+    return k if k < SERVE_CHAIN else period - k
+
+
+def serve_leg(mg, dev, stream, args, rank):
+    """Poisson arrivals at each rate against the continuous-batching server.
+
+    Each request draws N uniformly from SERVE_SIZES and one of that size's
+    streams uniformly; its source is the stream's next chain entry and its
+    warm start the stream's last solution (kept by the server).  Latency is
+    the time from the scheduled arrival to the end of the tick that retired
+    the request; requests arriving during the first `warm` seconds of a rate
+    are not counted.  solves/s counts requests retired inside the window.
+    """
+    import torch
+    chains, sizes = _serve_sources(dev, rank)
+    by_size = {n: [s for s in range(SERVE_STREAMS) if sizes[s] == n] for n in SERVE_SIZES}
+    outs = [torch.zeros_like(c[0]) for c in chains]
+    srv = mg.Server(SERVE_BUDGET, stream=stream)
+    step = [0] * SERVE_STREAMS
+    rng = np.random.default_rng(12345 + rank)
+
+    def submit(st):
+        f = chains[st][_chain_index(step[st])]
+        step[st] += 1
+        return srv.submit(f, outs[st], stream_id=st)
+
+    # untimed warm-up: one request per stream, drained
+    for st in range(SERVE_STREAMS):
+        submit(st)
+    while True:
+        a, q, _ = srv.tick()
+        srv.poll()
+        if a == 0 and q == 0:
+            break
+    results = []
+    warm, dur = args.serve_warmup, args.serve_seconds
+    for lam in args.serve_rates:
+        t_arr = np.cumsum(rng.exponential(1.0 / lam, size=int(lam * (warm + dur) * 1.5) + 16))
+        t_arr = t_arr[t_arr < warm + dur]
+        req_n = rng.integers(0, len(SERVE_SIZES), size=t_arr.size)
+        req_s = [by_size[SERVE_SIZES[k]][rng.integers(0, len(by_size[SERVE_SIZES[k]]))] for k in req_n]
+        pending = {}
+        lat, lat_n, cyc, bad, done_in_window = [], {n: [] for n in SERVE_SIZES}, [], 0, 0
+        ticks, max_inflight = 0, 0
+        i = 0
+        t0 = time.perf_counter()
+        deadline = warm + dur + 10.0
+        while True:
+            now = time.perf_counter() - t0
+            while i < t_arr.size and t_arr[i] <= now:
+                rid = submit(req_s[i])
+                pending[rid] = (t_arr[i], sizes[req_s[i]])
+                i += 1
+            if not pending:
+                if i == t_arr.size:
+                    break
+                time.sleep(max(0.0, min(t_arr[i] - now, 0.002)))
+                continue
+            a, q, _ = srv.tick()
+            ticks += 1
+            max_inflight = max(max_inflight, a + q)
+            t_done = time.perf_counter() - t0
+            for r in srv.poll():
+                t_a, n = pending.pop(r["request_id"])
+                if r["status"] != 0:
+                    bad += 1
+                if warm <= t_done < warm + dur:
+                    done_in_window += 1
+                if t_a >= warm:
+                    lat.append(t_done - t_a)
+                    lat_n[n].append(t_done - t_a)
+                    cyc.append(r["vcycles"])
+            if t_done > deadline:
+                break
+        unfinished = len(pending) + (t_arr.size - i)
+        while pending:  # drain what is left before the next rate
+            srv.tick()
+            for r in srv.poll():
+                pending.pop(r["request_id"], None)
+        lat_ms = np.array(lat) * 1e3
+        results.append({
+            "lambda_req_s": lam, "offered": int(np.sum((t_arr >= warm))), "completed": len(lat),
+            "solves_per_s": done_in_window / dur,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None,
+            "p50_ms_by_N": {str(n): float(np.percentile(v, 50) * 1e3) for n, v in lat_n.items() if v},
+            "mean_vcycles": float(np.mean(cyc)) if cyc else None,
+            "ticks": ticks, "max_in_flight": max_inflight, "failed": bad,
+            "saturated": unfinished > 0})
+    srv.close()
+    return {"workload": f"Poisson arrivals; N uniform in {list(SERVE_SIZES)}; {SERVE_STREAMS} streams "
+                        f"(stream s has N = sizes[s mod 5]); each request a 1% perturbation of its stream's "
+                        f"previous source, warm-started from the stream's previous solution; memory budget "
+                        f"160 GiB; tol 1e-10; {dur:g} s measured per rate after {warm:g} s warm-up",
+            "rates": results}
+
+
 def read_bf16_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -334,6 +463,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-sr", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-warmup", type=float, default=0.5)
+    ap.add_argument("--serve-rates", type=lambda v: [float(t) for t in v.split(",")],
+                    default=[50.0, 100.0, 200.0, 500.0, 1000.0, 2000.0])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -485,6 +619,9 @@ def main():
     # ---- SR prolongation at 2048^2 (tensor-core generator) ------------------
     sr_info = sr_leg(mg, dev, stream, flush, f_dev, x, args) if not args.skip_sr else None
 
+    # ---- serving: Poisson arrivals into the continuous-batching server -----
+    serving = serve_leg(mg, dev, stream, args, rank) if not args.skip_serve else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg(srcs[0])
@@ -516,6 +653,7 @@ def main():
             "kernels_per_solve": kernels,
             "batched": batched,
             "sr": sr_info,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

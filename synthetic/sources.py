@@ -112,10 +112,14 @@ def turbulent_source(n: int, kmax: int | None = None, seed: int = 0) -> np.ndarr
     return np.ascontiguousarray(f)
 
 
-def perturbed_source(f_prev: np.ndarray, seed: int, eps: float = 0.01) -> np.ndarray:
-    """Next source of a serving stream: f + eps (|f| / |g|) g, g a fresh source."""
-    n = f_prev.shape[0]
-    g = turbulent_source(n, default_kmax(n), seed)
+def perturb_with(f_prev: np.ndarray, g: np.ndarray, eps: float = 0.01) -> np.ndarray:
+    """f + eps (|f| / |g|) g with the mean removed."""
     f = f_prev + eps * (np.linalg.norm(f_prev) / np.linalg.norm(g)) * g
     f -= f.mean()
     return np.ascontiguousarray(f)
+
+
+def perturbed_source(f_prev: np.ndarray, seed: int, eps: float = 0.01) -> np.ndarray:
+    """Next source of a serving stream: f + eps (|f| / |g|) g, g a fresh source."""
+    n = f_prev.shape[0]
+    return perturb_with(f_prev, turbulent_source(n, default_kmax(n), seed), eps)
