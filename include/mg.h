@@ -181,6 +181,31 @@ mg_status mg_server_poll(mg_server *srv, mg_server_result *result, int *got);
 
 void mg_server_destroy(mg_server *srv);
 
+/* ---------------------------------------------------------------------
+ * Tile-shape autotuning (no counterpart in the paper: an implementation
+ * choice of this library).  The FP32 stencil kernels exist in four tile
+ * variants: bit 0 set = tiles of 32 rows (else 64) by 64 columns; bit 1 set =
+ * two spline midpoints per prolongation work item (else one).  kind 0 is the
+ * down kernel (sweeps, residual, restriction: variants 0 and 1 only), kind 1
+ * the up kernel (prolongation, correction, sweeps).  Every variant computes
+ * the same bits; the choice changes only speed.  The choice is process-wide,
+ * per (kind, grid size n, sweep count nu), starts from built-in defaults, and
+ * applies to every later solve, batched solve and server tick (cached graphs
+ * are re-recorded).
+ * ------------------------------------------------------------------- */
+
+/* Time every variant of both kernels on each tile level of ctx (n >= 128)
+ * with its nu_pre / nu_post, on the context's stream, and keep the fastest.
+ * The context's level buffers are overwritten (not x or f of any solve).  If
+ * cache_path is not NULL, entries recorded there for this GPU model are used
+ * without timing and new measurements are appended (plain text, one entry per
+ * line).  *n_timed (may be NULL) = entries measured.  Synchronous. */
+mg_status mg_autotune(mg_ctx *ctx, const char *cache_path, int *n_timed);
+
+/* Read or set one table entry (n a power of two >= 128, nu 0..4). */
+mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant);
+mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);
+
 void mg_destroy(mg_ctx *ctx);
 const char *mg_status_string(mg_status status);
 const char *mg_last_error(void);

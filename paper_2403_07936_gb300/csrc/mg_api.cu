@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "mg_internal.cuh"
+#include "mg_tune.cuh"
 #include "mg_sr.cuh"
 
 using namespace mg;
@@ -121,6 +122,7 @@ struct SolveGraph {
     cudaGraphExec_t exec = nullptr;
     long long n_pro = 0, n_body = 0, n_epi = 0;  // kernels per part
     unsigned long long stamp = 0;               // last use (LRU)
+    unsigned epoch = 0;                         // tile-variant table at recording
 };
 constexpr int kGraphCache = 4;
 
@@ -449,7 +451,8 @@ static mg_status get_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_pro
                                  SolveGraph **out) {
     SolveGraph *lru = &c->graphs[0];
     for (SolveGraph &g : c->graphs) {
-        if (g.exec && g.f == fd && g.x == xd && g.prolong == (int)prolong && g.tol == tol) {
+        if (g.exec && g.f == fd && g.x == xd && g.prolong == (int)prolong && g.tol == tol &&
+            g.epoch == tune_epoch()) {
             g.stamp = ++c->graph_clock;
             *out = &g;
             return MG_OK;
@@ -459,7 +462,9 @@ static mg_status get_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_pro
     if (lru->exec) cudaGraphExecDestroy(lru->exec);
     if (lru->graph) cudaGraphDestroy(lru->graph);
     *lru = SolveGraph();
+    const unsigned epoch = tune_epoch();
     MG_TRY(record_solve_graph(c, fd, xd, prolong, tol, lru));
+    lru->epoch = epoch;
     lru->stamp = ++c->graph_clock;
     *out = lru;
     return MG_OK;
@@ -480,6 +485,7 @@ struct BatchLaunch {
     size_t off;  // table offset (entries of TileGrid / BottomGrid)
     int ngrid;
     int nblocks;
+    int variant;  // tile variant (down / up)
 };
 
 struct BatchPlan {
@@ -502,6 +508,7 @@ struct BatchPlan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long n_pro = 0, n_body = 0, n_epi = 0;
+    unsigned epoch = 0;
     BatchRed red(int g) const { return BatchRed{d_partials, d_counters, d_out + (size_t)g * B * kMaxSlots}; }
     double *out(int g) const { return d_out + (size_t)g * B * kMaxSlots; }
 };
@@ -544,21 +551,21 @@ static mg_status batch_build(BatchPlan *p) {
         const bool first = v == 0;
         p->cyc[v].clear();
         for (int sz = maxN; sz > kBottomMax; sz >>= 1) {  // down sweeps
-            BatchLaunch L{0, tiles.size(), 0, 0};
+            BatchLaunch L{0, tiles.size(), 0, 0, tile_variant(0, sz, c0->nu1)};
             for (int r = 0; r < B; ++r) {
                 mg_ctx *c = p->ctxs[r];
                 for (int l = 0; l + 1 < c->levels; ++l)
                     if (c->lv[l].n == sz) {
                         tiles.push_back(TileGrid{c->lv[l].x32, c->lv[l].t32, c->lv[l].b32, c->lv[l + 1].b32, sz,
                                                  (l > 0 || first) ? 1 : 0, L.nblocks, r});
-                        L.nblocks += (sz / 64) * (sz / 64);
+                        L.nblocks += variant_tiles(sz, L.variant);
                         ++L.ngrid;
                     }
             }
             if (L.ngrid) p->cyc[v].push_back(L);
         }
         {  // bottom
-            BatchLaunch L{2, bottoms.size(), 0, 0};
+            BatchLaunch L{2, bottoms.size(), 0, 0, 0};
             for (int r = 0; r < B; ++r) {
                 mg_ctx *c = p->ctxs[r];
                 int l = 0;
@@ -571,14 +578,14 @@ static mg_status batch_build(BatchPlan *p) {
             p->cyc[v].push_back(L);
         }
         for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {  // up sweeps
-            BatchLaunch L{1, tiles.size(), 0, 0};
+            BatchLaunch L{1, tiles.size(), 0, 0, tile_variant(1, sz, c0->nu2)};
             for (int r = 0; r < B; ++r) {
                 mg_ctx *c = p->ctxs[r];
                 for (int l = 0; l + 1 < c->levels; ++l)
                     if (c->lv[l].n == sz) {
                         tiles.push_back(TileGrid{c->lv[l].t32, c->lv[l].x32, c->lv[l].b32, c->lv[l + 1].x32, sz, 0,
                                                  L.nblocks, r});
-                        L.nblocks += (sz / 64) * (sz / 64);
+                        L.nblocks += variant_tiles(sz, L.variant);
                         ++L.ngrid;
                     }
             }
@@ -625,9 +632,11 @@ static mg_status batch_build(BatchPlan *p) {
         for (const BatchLaunch &L : p->cyc[v]) {
             if (e != cudaSuccess) return;
             if (L.kind == 0)
-                e = launch_down_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu1, p->d_active, s);
+                e = launch_down_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu1, p->d_active, s,
+                                        L.variant);
             else if (L.kind == 1)
-                e = launch_up_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu2, p->d_active, taps, s);
+                e = launch_up_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu2, p->d_active, taps, s,
+                                      L.variant);
             else
                 e = launch_bottom_batched(p->d_bottom + L.off, L.ngrid, c0->nu1, c0->nu2, p->d_active, taps, s);
         }
@@ -745,7 +754,7 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
     for (int r = 0; r < B; ++r) MG_TRY(ensure_hierarchy(ctxs[r], false));
     std::lock_guard<std::mutex> lock(g_batch_mutex);
     BatchPlan *p = g_batch;
-    bool same = p && p->B == B && p->tol == tol && p->device == c0->device;
+    bool same = p && p->B == B && p->tol == tol && p->device == c0->device && p->epoch == tune_epoch();
     for (int r = 0; same && r < B; ++r)
         same = p->ctxs[r] == ctxs[r] && p->f[r] == f[r] && p->x[r] == x[r];
     if (!same) {
@@ -758,6 +767,7 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
         p->ctxs.assign(ctxs, ctxs + B);
         p->f.assign(f, f + B);
         p->x.assign(x, x + B);
+        p->epoch = tune_epoch();
         mg_status st = batch_build(p);
         if (st != MG_OK) {
             batch_free(p);
@@ -1008,20 +1018,20 @@ static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sid
     for (int v = 0; v < 2; ++v) {
         const bool first = v == 0;
         for (int sz = maxN; sz > kBottomMax; sz >>= 1) {
-            BatchLaunch L{0, tp.tiles.size(), 0, 0};
+            BatchLaunch L{0, tp.tiles.size(), 0, 0, tile_variant(0, sz, sv->nu1)};
             for (int sid : sids) {
                 mg_ctx *c = sv->slots[sid].ctx;
                 for (int l = 0; l + 1 < c->levels; ++l)
                     if (c->lv[l].n == sz) {
                         tp.tiles.push_back(TileGrid{c->lv[l].x32, c->lv[l].t32, c->lv[l].b32, c->lv[l + 1].b32, sz,
                                                     (l > 0 || first) ? 1 : 0, L.nblocks, sid});
-                        L.nblocks += (sz / 64) * (sz / 64);
+                        L.nblocks += variant_tiles(sz, L.variant);
                         ++L.ngrid;
                     }
             }
             if (L.ngrid) tp.cyc[v].push_back(L);
         }
-        BatchLaunch Lb{2, tp.bottoms.size(), 0, 0};
+        BatchLaunch Lb{2, tp.bottoms.size(), 0, 0, 0};
         for (int sid : sids) {
             mg_ctx *c = sv->slots[sid].ctx;
             int l = 0;
@@ -1033,14 +1043,14 @@ static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sid
         Lb.nblocks = Lb.ngrid;
         tp.cyc[v].push_back(Lb);
         for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {
-            BatchLaunch L{1, tp.tiles.size(), 0, 0};
+            BatchLaunch L{1, tp.tiles.size(), 0, 0, tile_variant(1, sz, sv->nu2)};
             for (int sid : sids) {
                 mg_ctx *c = sv->slots[sid].ctx;
                 for (int l = 0; l + 1 < c->levels; ++l)
                     if (c->lv[l].n == sz) {
                         tp.tiles.push_back(TileGrid{c->lv[l].t32, c->lv[l].x32, c->lv[l].b32, c->lv[l + 1].x32, sz, 0,
                                                     L.nblocks, sid});
-                        L.nblocks += (sz / 64) * (sz / 64);
+                        L.nblocks += variant_tiles(sz, L.variant);
                         ++L.ngrid;
                     }
             }
@@ -1107,9 +1117,11 @@ static mg_status server_tick(mg_server *sv, int *n_active, int *n_queued, int *n
         for (int k = 0; k < sv->inner; ++k)
             for (const BatchLaunch &L : tp.cyc[k == 0 ? 0 : 1]) {
                 if (L.kind == 0)
-                    MG_CUDA(launch_down_batched(d_tiles + L.off, L.ngrid, L.nblocks, sv->nu1, sv->d_active, s));
+                    MG_CUDA(launch_down_batched(d_tiles + L.off, L.ngrid, L.nblocks, sv->nu1, sv->d_active, s,
+                                                L.variant));
                 else if (L.kind == 1)
-                    MG_CUDA(launch_up_batched(d_tiles + L.off, L.ngrid, L.nblocks, sv->nu2, sv->d_active, sv->taps, s));
+                    MG_CUDA(launch_up_batched(d_tiles + L.off, L.ngrid, L.nblocks, sv->nu2, sv->d_active, sv->taps,
+                                              s, L.variant));
                 else
                     MG_CUDA(launch_bottom_batched(d_bottom + L.off, L.ngrid, sv->nu1, sv->nu2, sv->d_active, sv->taps, s));
             }
@@ -1500,6 +1512,46 @@ mg_status mg_set_graph_execution(mg_ctx *c, int enable) {
         return MG_ERR_INVALID_ARG;
     }
     c->use_graphs = enable != 0;
+    return MG_OK;
+}
+
+mg_status mg_autotune(mg_ctx *c, const char *cache_path, int *n_timed) {
+    if (n_timed) *n_timed = 0;
+    if (!c) {
+        set_err("null context");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    MG_TRY(ensure_hierarchy(c, false));
+    std::vector<TuneLevel> lv;
+    for (int l = 0; l + 1 < c->levels; ++l)
+        if (c->lv[l].n > kBottomMax)
+            lv.push_back(TuneLevel{c->lv[l].n, c->lv[l].x32, c->lv[l].t32, c->lv[l].b32, c->lv[l + 1].b32,
+                                   c->lv[l + 1].x32});
+    char err[256] = {0};
+    mg_status st = tune_levels(lv.data(), (int)lv.size(), c->nu1, c->nu2, c->taps, c->stream, c->device,
+                               cache_path, n_timed, err, sizeof err);
+    if (st != MG_OK) set_err("%s", err);
+    return st;
+}
+
+mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant) {
+    if (!variant || kind < 0 || kind > 1 || !is_pow2(n) || n < 128 || nu < 0 || nu > 4) {
+        set_err("invalid tile-variant query");
+        return MG_ERR_INVALID_ARG;
+    }
+    *variant = tile_variant(kind, n, nu);
+    return MG_OK;
+}
+
+mg_status mg_set_tile_variant(int kind, int n, int nu, int variant) {
+    if (kind < 0 || kind > 1 || !is_pow2(n) || n < 128 || nu < 0 || nu > 4 || variant < 0 ||
+        variant >= kTileVariants || (kind == 0 && variant_runs(variant) != 1)) {
+        set_err("invalid tile variant (kind 0|1, n a power of two >= 128, nu 0..4, variant 0..3; "
+                "k_down takes 0 or 1)");
+        return MG_ERR_INVALID_ARG;
+    }
+    set_tile_variant(kind, n, nu, variant);
     return MG_OK;
 }
 

@@ -149,17 +149,34 @@ struct BatchRed {
 };
 
 // ----------------------------------------------------------------------------
+// FP32 tile-kernel variants: bit 0 set = 32 rows per tile (else 64), bit 1
+// set = 2 spline midpoints per prolongation work item (else 1).  Tiles are 64
+// columns wide.  All variants give bit-identical results; the process-wide
+// table below (mg_tune.cu) holds the one to use for each (kernel kind: 0 down
+// / 1 up, grid size, sweep count), from built-in defaults or mg_autotune.
+// ----------------------------------------------------------------------------
+constexpr int kTileVariants = 4;
+__host__ __device__ constexpr int variant_rows(int v) { return (v & 1) ? 32 : 64; }
+__host__ __device__ constexpr int variant_runs(int v) { return (v & 2) ? 2 : 1; }
+inline int variant_tiles(int n, int v) { return (n / 64) * (n / variant_rows(v)); }
+int tile_variant(int kind, int n, int nu);
+void set_tile_variant(int kind, int n, int nu, int variant);
+// Incremented whenever a table entry changes (recorded graphs re-record).
+unsigned tune_epoch();
+
+// ----------------------------------------------------------------------------
 // Host-side launchers (defined in mg_kernels.cu); all return cudaError_t.
 // ----------------------------------------------------------------------------
 // xout = nu sweeps of x (x = 0 if zero_init); bc = 4 FW(b - (4 xout - sum)).  x != xout.
+// variant: a tile variant, or -1 for the table's choice (FP64 kernels have one shape).
 template <typename T>
 cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zero_init, T *bc,
-                        cudaStream_t s);
+                        cudaStream_t s, int variant = -1);
 // xout = nu sweeps of (x + P ec + extra); extra is a fine-grid additive
 // correction or null.  x != xout.
 template <typename T>
 cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
-                      const FirTaps &taps, cudaStream_t s, const T *extra = nullptr);
+                      const FirTaps &taps, cudaStream_t s, const T *extra = nullptr, int variant = -1);
 template <typename T>
 cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool zero_init,
                           const T *ainv, const FirTaps &taps, cudaStream_t s);
@@ -198,10 +215,11 @@ cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, c
                          cudaGraphConditionalHandle handle, cudaStream_t s);
 
 // batched forms (float tile kernels; FP64 outer kernels)
+// every grid of one batched launch uses the same variant; nblocks = sum of variant_tiles
 cudaError_t launch_down_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
-                                cudaStream_t s);
+                                cudaStream_t s, int variant);
 cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
-                              const FirTaps &taps, cudaStream_t s);
+                              const FirTaps &taps, cudaStream_t s, int variant);
 cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int nu2, const int *active,
                                   const FirTaps &taps, cudaStream_t s);
 // sums of f (of_x = false) or of x (of_x = true) per right-hand side -> red.out[r][0]

@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "mg_internal.cuh"
 
@@ -53,16 +54,15 @@ constexpr int kThreads = 256;  // threads per tile block
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-// Output tile per precision.  FP32 tiles are taller (less halo per point);
-// FP64 tiles are halved to keep the staged tiles within shared memory.
-// NJ = spline midpoints a thread computes per work item (the window of
-// coarse values they share is loaded once).
-template <typename T> struct Tile;
-template <> struct Tile<float> {
-    static constexpr int TY = 64, TX = 64, NJ = 2;
-};
-template <> struct Tile<double> {
-    static constexpr int TY = 32, TX = 64, NJ = 1;
+// Output tiles are TY x 64 points.  FP32 kernels come in variants (see
+// variant_rows / variant_runs): 64 or 32 rows per tile, and NJ = 1 or 2
+// spline midpoints per work item of the prolongation.  Every variant computes
+// the same values in the same order, so the choice only changes speed.  FP64
+// tiles are 32 x 64 with NJ = 1, to keep the staged tiles within shared memory.
+constexpr int kTX = 64;
+template <typename T> struct Fixed64;  // the FP64 shape
+template <> struct Fixed64<double> {
+    static constexpr int TY = 32, NJ = 1;
 };
 
 // Copy rows [r0, r0+R) x cols [c0, c0+C) of the periodic n x n grid g into
@@ -187,9 +187,9 @@ __device__ __forceinline__ void half_sweep(T *X, const T *B, int r_lo, int r_hi,
 // ---------------------------------------------------------------------------
 // k_down: NU sweeps, residual, full-weighting restriction of one tile.
 // ---------------------------------------------------------------------------
-template <typename T, int NU>
+template <typename T, int NU, int TY_>
 struct DownCfg {
-    static constexpr int TY = Tile<T>::TY, TX = Tile<T>::TX;
+    static constexpr int TY = TY_, TX = kTX;
     static constexpr int VW = Prec<T>::VW;
     static constexpr int H = 2 * NU + 2;           // logical halo (rows and cols)
     static constexpr int HX = round_up(H + 2, VW);  // staged column halo (>= H + 2: k >= 1)
@@ -200,11 +200,11 @@ struct DownCfg {
     static constexpr size_t smem = 4ull * A * sizeof(T);
 };
 
-template <typename T, int NU>
+template <typename T, int NU, int TY_>
 __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict__ xout,
                                           const T *__restrict__ b, int n, T *__restrict__ bc,
                                           int ty0, int tx0, bool zero) {
-    using Cfg = DownCfg<T, NU>;
+    using Cfg = DownCfg<T, NU, TY_>;
     constexpr int TY = Cfg::TY, TX = Cfg::TX, H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C,
                   CK = Cfg::CK, A = Cfg::A;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -253,11 +253,11 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
     store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
 }
 
-template <typename T, int NU, bool ZERO>
+template <typename T, int NU, bool ZERO, int TY>
 __global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *__restrict__ xout,
                                                    const T *__restrict__ b, int n,
                                                    T *__restrict__ bc) {
-    down_tile<T, NU>(x, xout, b, n, bc, blockIdx.y * Tile<T>::TY, blockIdx.x * Tile<T>::TX, ZERO);
+    down_tile<T, NU, TY>(x, xout, b, n, bc, blockIdx.y * TY, blockIdx.x * kTX, ZERO);
 }
 
 // Block of a batched tile launch: locate its grid (the last table entry whose
@@ -272,22 +272,22 @@ __device__ __forceinline__ int find_grid(const TileGrid *__restrict__ g, int ngr
     return lo;
 }
 
-template <typename T, int NU>
+template <typename T, int NU, int TY>
 __global__ void __launch_bounds__(kThreads) k_down_batched(const TileGrid *__restrict__ tab, int ngrid,
                                                            const int *__restrict__ active) {
     const TileGrid t = tab[find_grid(tab, ngrid)];
     if (active && !active[t.rhs]) return;
-    const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / Tile<T>::TX;
-    down_tile<T, NU>((const T *)t.x, (T *)t.xout, (const T *)t.b, t.n, (T *)t.aux, (lt / tpr) * Tile<T>::TY,
-                     (lt % tpr) * Tile<T>::TX, t.zero != 0);
+    const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / kTX;
+    down_tile<T, NU, TY>((const T *)t.x, (T *)t.xout, (const T *)t.b, t.n, (T *)t.aux, (lt / tpr) * TY,
+                         (lt % tpr) * kTX, t.zero != 0);
 }
 
 // ---------------------------------------------------------------------------
 // k_up: x += P_cubic ec (+ extra), then NU sweeps, on one tile.
 // ---------------------------------------------------------------------------
-template <typename T, int NU>
+template <typename T, int NU, int TY_, int NJ_>
 struct UpCfg {
-    static constexpr int TY = Tile<T>::TY, TX = Tile<T>::TX, NJ = Tile<T>::NJ;
+    static constexpr int TY = TY_, TX = kTX, NJ = NJ_;
     static constexpr int VW = Prec<T>::VW;
     static constexpr int L = Prec<T>::L;
     static constexpr int H = 2 * NU;
@@ -311,12 +311,12 @@ struct UpCfg {
     static_assert(JW % NJ == 0 && IW % NJ == 0, "runs must tile the refined range");
 };
 
-template <typename T, int NU>
+template <typename T, int NU, int TY_, int NJ_>
 __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__ xout,
                                         const T *__restrict__ b, const T *__restrict__ ec,
                                         const T *__restrict__ extra, int n, const FirTaps &taps, int ty0,
                                         int tx0) {
-    using Cfg = UpCfg<T, NU>;
+    using Cfg = UpCfg<T, NU, TY_, NJ_>;
     constexpr int TY = Cfg::TY, TX = Cfg::TX, NJ = Cfg::NJ, H = Cfg::H, HX = Cfg::HX, R = Cfg::R,
                   C = Cfg::C, CK = Cfg::CK, A = Cfg::A, L = Cfg::L, JW = Cfg::JW, IW = Cfg::IW,
                   CHY = Cfg::CHY, CR = Cfg::CR, CHX = Cfg::CHX, CC = Cfg::CC, FW = Cfg::FW;
@@ -389,21 +389,21 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
     store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
 }
 
-template <typename T, int NU>
+template <typename T, int NU, int TY, int NJ>
 __global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__restrict__ xout,
                                                  const T *__restrict__ b, const T *__restrict__ ec,
                                                  const T *__restrict__ extra, int n, FirTaps taps) {
-    up_tile<T, NU>(x, xout, b, ec, extra, n, taps, blockIdx.y * Tile<T>::TY, blockIdx.x * Tile<T>::TX);
+    up_tile<T, NU, TY, NJ>(x, xout, b, ec, extra, n, taps, blockIdx.y * TY, blockIdx.x * kTX);
 }
 
-template <typename T, int NU>
+template <typename T, int NU, int TY, int NJ>
 __global__ void __launch_bounds__(kThreads) k_up_batched(const TileGrid *__restrict__ tab, int ngrid,
                                                          const int *__restrict__ active, FirTaps taps) {
     const TileGrid t = tab[find_grid(tab, ngrid)];
     if (active && !active[t.rhs]) return;
-    const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / Tile<T>::TX;
-    up_tile<T, NU>((const T *)t.x, (T *)t.xout, (const T *)t.b, (const T *)t.aux, nullptr, t.n, taps,
-                   (lt / tpr) * Tile<T>::TY, (lt % tpr) * Tile<T>::TX);
+    const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / kTX;
+    up_tile<T, NU, TY, NJ>((const T *)t.x, (T *)t.xout, (const T *)t.b, (const T *)t.aux, nullptr, t.n, taps,
+                           (lt / tpr) * TY, (lt % tpr) * kTX);
 }
 
 // ---------------------------------------------------------------------------
@@ -847,10 +847,10 @@ cudaError_t set_smem_once(KernelT k, size_t bytes, std::atomic<unsigned> &done) 
     return e;
 }
 
-template <typename T, int NU, bool ZERO>
+template <typename T, int NU, bool ZERO, int TY>
 cudaError_t down_impl(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_t s) {
-    using Cfg = DownCfg<T, NU>;
-    auto k = k_down<T, NU, ZERO>;
+    using Cfg = DownCfg<T, NU, TY>;
+    auto k = k_down<T, NU, ZERO, TY>;
     static std::atomic<unsigned> done{0};
     cudaError_t e = set_smem_once(k, Cfg::smem, done);
     if (e != cudaSuccess) return e;
@@ -860,11 +860,11 @@ cudaError_t down_impl(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_
     return cudaGetLastError();
 }
 
-template <typename T, int NU>
+template <typename T, int NU, int TY, int NJ>
 cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra, int n,
                     const FirTaps &taps, cudaStream_t s) {
-    using Cfg = UpCfg<T, NU>;
-    auto k = k_up<T, NU>;
+    using Cfg = UpCfg<T, NU, TY, NJ>;
+    auto k = k_up<T, NU, TY, NJ>;
     static std::atomic<unsigned> done{0};
     cudaError_t e = set_smem_once(k, Cfg::smem, done);
     if (e != cudaSuccess) return e;
@@ -874,16 +874,41 @@ cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra
     return cudaGetLastError();
 }
 
+template <typename T, int NU, bool ZERO>
+cudaError_t down_var(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_t s, int variant) {
+    if constexpr (std::is_same<T, double>::value) {
+        return down_impl<T, NU, ZERO, Fixed64<double>::TY>(x, xout, b, n, bc, s);
+    } else {
+        return variant_rows(variant) == 32 ? down_impl<T, NU, ZERO, 32>(x, xout, b, n, bc, s)
+                                           : down_impl<T, NU, ZERO, 64>(x, xout, b, n, bc, s);
+    }
+}
+
+template <typename T, int NU>
+cudaError_t up_var(const T *x, T *xout, const T *b, const T *ec, const T *extra, int n, const FirTaps &taps,
+                   cudaStream_t s, int variant) {
+    if constexpr (std::is_same<T, double>::value) {
+        return up_impl<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>(x, xout, b, ec, extra, n, taps, s);
+    } else {
+        const bool r32 = variant_rows(variant) == 32, nj2 = variant_runs(variant) == 2;
+        if (r32) return nj2 ? up_impl<T, NU, 32, 2>(x, xout, b, ec, extra, n, taps, s)
+                            : up_impl<T, NU, 32, 1>(x, xout, b, ec, extra, n, taps, s);
+        return nj2 ? up_impl<T, NU, 64, 2>(x, xout, b, ec, extra, n, taps, s)
+                   : up_impl<T, NU, 64, 1>(x, xout, b, ec, extra, n, taps, s);
+    }
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zero_init, T *bc,
-                        cudaStream_t s) {
-    if (n < Tile<T>::TY || n < Tile<T>::TX || x == xout) return cudaErrorInvalidValue;
+                        cudaStream_t s, int variant) {
+    if (n < 64 || x == xout || variant < -1 || variant >= kTileVariants) return cudaErrorInvalidValue;
+    if (variant < 0) variant = tile_variant(0, n, nu);
 #define MG_DOWN_CASE(NU)                                                                  \
     case NU:                                                                              \
-        return zero_init ? down_impl<T, NU, true>(x, xout, b, n, bc, s)                   \
-                         : down_impl<T, NU, false>(x, xout, b, n, bc, s);
+        return zero_init ? down_var<T, NU, true>(x, xout, b, n, bc, s, variant)           \
+                         : down_var<T, NU, false>(x, xout, b, n, bc, s, variant);
     switch (nu) {
         MG_DOWN_CASE(0)
         MG_DOWN_CASE(1)
@@ -897,14 +922,15 @@ cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zer
 
 template <typename T>
 cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
-                      const FirTaps &taps, cudaStream_t s, const T *extra) {
-    if (n < Tile<T>::TY || n < Tile<T>::TX || !ec || x == xout) return cudaErrorInvalidValue;
+                      const FirTaps &taps, cudaStream_t s, const T *extra, int variant) {
+    if (n < 64 || !ec || x == xout || variant < -1 || variant >= kTileVariants) return cudaErrorInvalidValue;
+    if (variant < 0) variant = tile_variant(1, n, nu);
     switch (nu) {
-        case 0: return up_impl<T, 0>(x, xout, b, ec, extra, n, taps, s);
-        case 1: return up_impl<T, 1>(x, xout, b, ec, extra, n, taps, s);
-        case 2: return up_impl<T, 2>(x, xout, b, ec, extra, n, taps, s);
-        case 3: return up_impl<T, 3>(x, xout, b, ec, extra, n, taps, s);
-        case 4: return up_impl<T, 4>(x, xout, b, ec, extra, n, taps, s);
+        case 0: return up_var<T, 0>(x, xout, b, ec, extra, n, taps, s, variant);
+        case 1: return up_var<T, 1>(x, xout, b, ec, extra, n, taps, s, variant);
+        case 2: return up_var<T, 2>(x, xout, b, ec, extra, n, taps, s, variant);
+        case 3: return up_var<T, 3>(x, xout, b, ec, extra, n, taps, s, variant);
+        case 4: return up_var<T, 4>(x, xout, b, ec, extra, n, taps, s, variant);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -935,13 +961,13 @@ cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu
 }
 
 template cudaError_t launch_down<float>(const float *, float *, const float *, int, int, bool, float *,
-                                        cudaStream_t);
+                                        cudaStream_t, int);
 template cudaError_t launch_down<double>(const double *, double *, const double *, int, int, bool,
-                                         double *, cudaStream_t);
+                                         double *, cudaStream_t, int);
 template cudaError_t launch_up<float>(const float *, float *, const float *, const float *, int, int,
-                                      const FirTaps &, cudaStream_t, const float *);
+                                      const FirTaps &, cudaStream_t, const float *, int);
 template cudaError_t launch_up<double>(const double *, double *, const double *, const double *, int,
-                                       int, const FirTaps &, cudaStream_t, const double *);
+                                       int, const FirTaps &, cudaStream_t, const double *, int);
 template cudaError_t launch_bottom<float>(float *, const float *, int, int, int, int, bool, const float *,
                                           const FirTaps &, cudaStream_t);
 template cudaError_t launch_bottom<double>(double *, const double *, int, int, int, int, bool,
@@ -997,42 +1023,69 @@ cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_down_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
-                                cudaStream_t s) {
-#define MG_DB_CASE(NU)                                                                            \
-    case NU: {                                                                                    \
-        static std::atomic<unsigned> done{0};                                                     \
-        cudaError_t e = set_smem_once(k_down_batched<float, NU>, DownCfg<float, NU>::smem, done); \
-        if (e != cudaSuccess) return e;                                                           \
-        k_down_batched<float, NU><<<nblocks, kThreads, DownCfg<float, NU>::smem, s>>>(tab, ngrid, active); \
-        break;                                                                                    \
-    }
-    switch (nu) {
-        MG_DB_CASE(0) MG_DB_CASE(1) MG_DB_CASE(2) MG_DB_CASE(3) MG_DB_CASE(4)
-        default: return cudaErrorInvalidValue;
-    }
-#undef MG_DB_CASE
+namespace {
+template <int NU, int TY>
+cudaError_t down_batched_impl(const TileGrid *tab, int ngrid, int nblocks, const int *active, cudaStream_t s) {
+    auto k = k_down_batched<float, NU, TY>;
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = set_smem_once(k, DownCfg<float, NU, TY>::smem, done);
+    if (e != cudaSuccess) return e;
+    k<<<nblocks, kThreads, DownCfg<float, NU, TY>::smem, s>>>(tab, ngrid, active);
     count_launches(1);
     return cudaGetLastError();
 }
-
-cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
-                              const FirTaps &taps, cudaStream_t s) {
-#define MG_UB_CASE(NU)                                                                          \
-    case NU: {                                                                                  \
-        static std::atomic<unsigned> done{0};                                                   \
-        cudaError_t e = set_smem_once(k_up_batched<float, NU>, UpCfg<float, NU>::smem, done);   \
-        if (e != cudaSuccess) return e;                                                         \
-        k_up_batched<float, NU><<<nblocks, kThreads, UpCfg<float, NU>::smem, s>>>(tab, ngrid, active, taps); \
-        break;                                                                                  \
-    }
-    switch (nu) {
-        MG_UB_CASE(0) MG_UB_CASE(1) MG_UB_CASE(2) MG_UB_CASE(3) MG_UB_CASE(4)
-        default: return cudaErrorInvalidValue;
-    }
-#undef MG_UB_CASE
+template <int NU, int TY, int NJ>
+cudaError_t up_batched_impl(const TileGrid *tab, int ngrid, int nblocks, const int *active, const FirTaps &taps,
+                            cudaStream_t s) {
+    auto k = k_up_batched<float, NU, TY, NJ>;
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = set_smem_once(k, UpCfg<float, NU, TY, NJ>::smem, done);
+    if (e != cudaSuccess) return e;
+    k<<<nblocks, kThreads, UpCfg<float, NU, TY, NJ>::smem, s>>>(tab, ngrid, active, taps);
     count_launches(1);
     return cudaGetLastError();
+}
+template <int NU>
+cudaError_t down_batched_var(const TileGrid *tab, int ngrid, int nblocks, const int *active, cudaStream_t s,
+                             int variant) {
+    return variant_rows(variant) == 32 ? down_batched_impl<NU, 32>(tab, ngrid, nblocks, active, s)
+                                       : down_batched_impl<NU, 64>(tab, ngrid, nblocks, active, s);
+}
+template <int NU>
+cudaError_t up_batched_var(const TileGrid *tab, int ngrid, int nblocks, const int *active, const FirTaps &taps,
+                           cudaStream_t s, int variant) {
+    const bool r32 = variant_rows(variant) == 32, nj2 = variant_runs(variant) == 2;
+    if (r32) return nj2 ? up_batched_impl<NU, 32, 2>(tab, ngrid, nblocks, active, taps, s)
+                        : up_batched_impl<NU, 32, 1>(tab, ngrid, nblocks, active, taps, s);
+    return nj2 ? up_batched_impl<NU, 64, 2>(tab, ngrid, nblocks, active, taps, s)
+               : up_batched_impl<NU, 64, 1>(tab, ngrid, nblocks, active, taps, s);
+}
+}  // namespace
+
+cudaError_t launch_down_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
+                                cudaStream_t s, int variant) {
+    if (variant < 0 || variant >= kTileVariants) return cudaErrorInvalidValue;
+    switch (nu) {
+        case 0: return down_batched_var<0>(tab, ngrid, nblocks, active, s, variant);
+        case 1: return down_batched_var<1>(tab, ngrid, nblocks, active, s, variant);
+        case 2: return down_batched_var<2>(tab, ngrid, nblocks, active, s, variant);
+        case 3: return down_batched_var<3>(tab, ngrid, nblocks, active, s, variant);
+        case 4: return down_batched_var<4>(tab, ngrid, nblocks, active, s, variant);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
+                              const FirTaps &taps, cudaStream_t s, int variant) {
+    if (variant < 0 || variant >= kTileVariants) return cudaErrorInvalidValue;
+    switch (nu) {
+        case 0: return up_batched_var<0>(tab, ngrid, nblocks, active, taps, s, variant);
+        case 1: return up_batched_var<1>(tab, ngrid, nblocks, active, taps, s, variant);
+        case 2: return up_batched_var<2>(tab, ngrid, nblocks, active, taps, s, variant);
+        case 3: return up_batched_var<3>(tab, ngrid, nblocks, active, taps, s, variant);
+        case 4: return up_batched_var<4>(tab, ngrid, nblocks, active, taps, s, variant);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int nu2, const int *active,
@@ -1090,12 +1143,25 @@ cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, cons
     return cudaGetLastError();
 }
 
+template <typename T, int NU, int TY, int NJ>
+static cudaError_t prepare_shape() {
+    cudaError_t e = set_smem(k_down<T, NU, true, TY>, DownCfg<T, NU, TY>::smem);
+    if (e == cudaSuccess) e = set_smem(k_down<T, NU, false, TY>, DownCfg<T, NU, TY>::smem);
+    if (e == cudaSuccess) e = set_smem(k_up<T, NU, TY, NJ>, UpCfg<T, NU, TY, NJ>::smem);
+    return e;
+}
+
 template <typename T, int NU>
 static cudaError_t prepare_nu() {
-    cudaError_t e = set_smem(k_down<T, NU, true>, DownCfg<T, NU>::smem);
-    if (e == cudaSuccess) e = set_smem(k_down<T, NU, false>, DownCfg<T, NU>::smem);
-    if (e == cudaSuccess) e = set_smem(k_up<T, NU>, UpCfg<T, NU>::smem);
-    return e;
+    if constexpr (std::is_same<T, double>::value) {
+        return prepare_shape<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>();
+    } else {
+        cudaError_t e = prepare_shape<T, NU, 64, 1>();
+        if (e == cudaSuccess) e = prepare_shape<T, NU, 64, 2>();
+        if (e == cudaSuccess) e = prepare_shape<T, NU, 32, 1>();
+        if (e == cudaSuccess) e = prepare_shape<T, NU, 32, 2>();
+        return e;
+    }
 }
 
 template <typename T>

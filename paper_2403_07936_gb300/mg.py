@@ -56,6 +56,9 @@ SIGNATURES = {
     "mg_solve_batched": (_I, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _I, _D, _I,
                               C.POINTER(SolveInfo)]),
     "mg_destroy": (None, [_VP]),
+    "mg_autotune": (_I, [_VP, C.c_char_p, C.POINTER(_I)]),
+    "mg_get_tile_variant": (_I, [_I, _I, _I, C.POINTER(_I)]),
+    "mg_set_tile_variant": (_I, [_I, _I, _I, _I]),
     "mg_server_create": (_I, [_SZ, _I, _I, _I, _I, _D, _VP, C.POINTER(_VP)]),
     "mg_server_submit": (_I, [_VP, _I, _I, _VP, _VP, C.POINTER(C.c_longlong)]),
     "mg_server_tick": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
@@ -207,6 +210,13 @@ class Context:
     def vcycle(self, f, x, prolong: str = "cubic"):
         _check(load().mg_vcycle(self._h, ptr(f), ptr(x), PROLONG[prolong]))
 
+    def autotune(self, cache_path: str | None = None) -> int:
+        """Time the tile variants on this context's levels; returns entries measured."""
+        n = _I()
+        path = cache_path.encode() if cache_path else None
+        _check(load().mg_autotune(self._h, path, C.byref(n)))
+        return n.value
+
     def probe(self, kind: int, capacity: int = 256):
         """Time one kernel kind with CUDA events (1 down, 2 up, 3 residual, 4 update)."""
         _check(load().mg_probe_kernel(self._h, kind, capacity))
@@ -274,6 +284,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def get_tile_variant(kind: int, n: int, nu: int) -> int:
+    v = _I()
+    _check(load().mg_get_tile_variant(kind, n, nu, C.byref(v)))
+    return v.value
+
+
+def set_tile_variant(kind: int, n: int, nu: int, variant: int):
+    _check(load().mg_set_tile_variant(kind, n, nu, variant))
 
 
 def kernel_launches() -> int:

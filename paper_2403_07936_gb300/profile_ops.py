@@ -1,0 +1,87 @@
+"""Profiling driver: repeated launches of one library operator on random data.
+
+    python -m paper_2403_07936_gb300.profile_ops --op up --n 2048 --reps 5
+
+Runs `--reps` launches of the chosen operator through the C ABI on cuda:0
+(after building the library) and prints the mean CUDA-event time per launch.
+It exists so that an `ncu` capture of a single kernel (`-k`, `-c 1..3`) has a
+small, self-contained command line; the inputs are random, since only the
+memory traffic and the instruction mix are of interest.
+
+ops:
+  down   finest-level k_down (nu sweeps, residual, full weighting), FP32
+  up     finest-level k_up (cubic prolongation, correction, nu sweeps), FP32
+  outer  FP64 outer residual with norms and FP32 conversion
+  conv   one tensor-core SR convolution layer (mode 0: conv + PReLU) on an
+         n/2 x n/2 coarse grid of 64 channels
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["down", "up", "outer", "conv"], required=True)
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--nu", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+
+    import torch
+
+    from paper_2403_07936_gb300 import build, mg
+    build.build()
+    dev = torch.device("cuda:0")
+    n = args.n
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    if args.op in ("down", "up"):
+        x = torch.randn((n, n), device=dev, generator=g)
+        xo = torch.empty_like(x)
+        b = torch.randn((n, n), device=dev, generator=g)
+        bc = torch.empty((n // 2, n // 2), device=dev)
+        ec = torch.randn((n // 2, n // 2), device=dev, generator=g)
+        if args.op == "down":
+            def run():
+                mg.op_down(x, xo, b, bc, nu=args.nu)
+        else:
+            def run():
+                mg.op_up(x, xo, b, ec, nu=args.nu)
+    elif args.op == "outer":
+        f = torch.randn((n, n), device=dev, dtype=torch.float64, generator=g)
+        x = torch.randn((n, n), device=dev, dtype=torch.float64, generator=g)
+        s32 = torch.empty((n, n), device=dev, dtype=torch.float32)
+        out = torch.empty(4, device=dev, dtype=torch.float64)
+
+        def run():
+            mg.op_outer_residual(f, x, 0.0, s32, out)
+    else:
+        H = W = n // 2
+        xin = torch.randn((H + 2, W + 2, 64), device=dev, generator=g).to(torch.bfloat16)
+        w = (torch.randn((9, 64, 64), device=dev, generator=g) * 0.05).to(torch.bfloat16)
+        bias = torch.zeros(64, device=dev)
+        pre = torch.full((64,), 0.2, device=dev)
+        out = torch.empty((H + 2, W + 2, 64), device=dev, dtype=torch.bfloat16)
+
+        def run():
+            mg.op_sr_conv(0, H, W, xin, None, w, bias, pre, out)
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"{args.op} n={n} reps={args.reps} us_per_launch={e0.elapsed_time(e1) / args.reps * 1e3:.2f}")
+
+
+if __name__ == "__main__":
+    main()

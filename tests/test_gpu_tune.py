@@ -1,0 +1,124 @@
+"""Tile-shape variants and the autotuner (GPU).
+
+The FP32 stencil kernels come in four tile variants (32 or 64 rows per tile;
+one or two spline midpoints per prolongation work item).  Each point's
+arithmetic is the same in all of them, so they must agree bit for bit: the
+operators, a whole solve, and a batched solve.  The autotuner times them,
+keeps the fastest, and round-trips its choices through a cache file.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import multigrid as omg
+from synthetic.sources import config_seed, default_kmax, turbulent_source
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+SIZES = (128, 256, 512, 1024)
+
+
+@pytest.fixture(scope="module")
+def mg():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_07936_gb300 import mg as m
+    return m
+
+
+@pytest.fixture()
+def restore_table(mg):
+    saved = {(k, n, nu): mg.get_tile_variant(k, n, nu) for k in (0, 1) for n in SIZES + (2048,)
+             for nu in (1, 2, 3)}
+    yield
+    for (k, n, nu), v in saved.items():
+        mg.set_tile_variant(k, n, nu, v)
+
+
+def _set_all(mg, vd, vu, nu=2):
+    for n in SIZES + (2048,):
+        mg.set_tile_variant(0, n, nu, vd)
+        mg.set_tile_variant(1, n, nu, vu)
+
+
+@pytest.mark.parametrize("n", [128, 512])
+@pytest.mark.parametrize("nu", [1, 2, 3])
+def test_operator_variants_are_bit_identical(mg, restore_table, n, nu):
+    g = torch.Generator(device=DEV)
+    g.manual_seed(n + nu)
+    x = torch.randn((n, n), device=DEV, generator=g)
+    b = torch.randn((n, n), device=DEV, generator=g)
+    ec = torch.randn((n // 2, n // 2), device=DEV, generator=g)
+    outs_d, outs_u = [], []
+    for v in range(4):
+        if v < 2:
+            mg.set_tile_variant(0, n, nu, v)
+            xo = torch.full_like(x, float("nan"))
+            bc = torch.full_like(ec, float("nan"))
+            mg.op_down(x, xo, b, bc, nu=nu)
+            outs_d.append((xo, bc))
+        mg.set_tile_variant(1, n, nu, v)
+        xu = torch.full_like(x, float("nan"))
+        mg.op_up(x, xu, b, ec, nu=nu)
+        outs_u.append(xu)
+    torch.cuda.synchronize()
+    for xo, bc in outs_d[1:]:
+        assert torch.equal(xo, outs_d[0][0]) and torch.equal(bc, outs_d[0][1])
+    for xu in outs_u[1:]:
+        assert torch.equal(xu, outs_u[0])
+    assert torch.isfinite(outs_u[0]).all()
+
+
+def test_solve_and_batch_are_identical_under_every_variant(mg, restore_table):
+    n = 1024
+    f = turbulent_source(n, default_kmax(n), config_seed(7, 1))
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(8, n)
+    bsizes = [256, 512, 128]
+    bfs = [torch.tensor(turbulent_source(m, default_kmax(m), config_seed(7, 10 + i)), device=DEV)
+           for i, m in enumerate(bsizes)]
+    bctx = [mg.Context(int(np.log2(m // 8)) + 1, m) for m in bsizes]
+    ref = None
+    for vd, vu in [(0, 0), (1, 1), (0, 3), (1, 2)]:
+        _set_all(mg, vd, vu)
+        x = torch.zeros_like(ft)
+        info = ctx.solve(ft, x)
+        xs = [torch.zeros_like(t) for t in bfs]
+        mg.solve_batched(bctx, bfs, xs)
+        got = (x.clone(), [t.clone() for t in xs], info["vcycles"])
+        if ref is None:
+            ref = got
+            assert info["rel_residual"] <= 1e-10
+            xe = omg.exact_solve_fft(f - f.mean())
+            assert np.abs(x.cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
+        else:
+            assert torch.equal(got[0], ref[0]) and got[2] == ref[2]
+            for a, b in zip(got[1], ref[1]):
+                assert torch.equal(a, b)
+
+
+def test_autotune_picks_a_variant_and_round_trips_the_cache(mg, restore_table, tmp_path):
+    n = 1024
+    ctx = mg.Context(8, n)
+    path = str(tmp_path / "tiles.txt")
+    with open(path, "w") as fp:  # an entry for another GPU model is ignored
+        fp.write("Some_Other_GPU/10 1 1024 2 3 1.0\n")
+    timed = ctx.autotune(path)
+    levels = [m for m in (1024, 512, 256, 128)]
+    assert timed == 2 * len(levels)
+    chosen = {(k, m): mg.get_tile_variant(k, m, 2) for k in (0, 1) for m in levels}
+    assert all(v in (0, 1) for (k, m), v in chosen.items() if k == 0)
+    lines = open(path).read().splitlines()
+    assert len(lines) == 1 + 2 * len(levels)
+    # overwrite the table, then load it back from the cache without timing
+    _set_all(mg, 1, 3)
+    assert ctx.autotune(path) == 0
+    assert {(k, m): mg.get_tile_variant(k, m, 2) for k in (0, 1) for m in levels} == chosen
+    # a solve after tuning re-records its graph and still converges
+    f = turbulent_source(n, default_kmax(n), config_seed(7, 2))
+    ft = torch.tensor(f, device=DEV)
+    x = torch.zeros_like(ft)
+    assert ctx.solve(ft, x)["rel_residual"] <= 1e-10
+    assert os.path.getsize(path) > 0
