@@ -302,6 +302,14 @@ mg_status mg_op_sr_generator(mg_ctx *ctx, const float *ec, int nc, float *out);
 mg_status mg_op_outer_residual(int n, const double *f, const double *x, double mu, float *s32,
                                double *out, void *stream);
 
+/* The library's float <-> double conversions on the integer pipe (used by the
+ * FP64 outer kernels in place of the FP64-pipe conversion instructions):
+ * dir 0: out[i] = (float)in[i] rounded to nearest even, in double, out float;
+ * dir 1: out[i] = (double)in[i], in float, out double.  Device arrays of
+ * count elements.  Exposed so that tests can compare them bit for bit with
+ * the hardware conversion.  Synchronous. */
+mg_status mg_op_convert(int dir, size_t count, const void *in, void *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1845,4 +1845,16 @@ mg_status mg_op_outer_residual(int n, const double *f, const double *x, double m
     return MG_OK;
 }
 
+mg_status mg_op_convert(int dir, size_t count, const void *in, void *out, void *stream) {
+    if ((dir != 0 && dir != 1) || (count && (!in || !out))) {
+        set_err("invalid conversion request");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (count == 0) return MG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    MG_CUDA(launch_convert(dir, count, in, out, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
 }  // extern "C"

@@ -54,6 +54,43 @@ template <> struct Prec<double> {
 };
 
 // ----------------------------------------------------------------------------
+// Precision conversions on the integer pipe.  GB300 issues FP64 instructions
+// (which include the hardware conversions between float and double) at a
+// small fraction of its FP32 rate, and the FP64 outer kernels are bound by
+// that pipe; these conversions use integer instructions instead, from the
+// IEEE 754 binary32 / binary64 layouts (1 sign bit; 8 / 11 exponent bits with
+// bias 127 / 1023; 23 / 52 fraction bits).  Normal results are handled here;
+// zeros, subnormals, infinities and NaNs (and results that would be
+// subnormal or overflow) take the hardware conversion, so every input gets
+// the same bits as cvt.rn.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double f32_to_f64(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)v;
+    // exact: re-bias the exponent by 1023 - 127 = 896, widen the fraction by 29 bits
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(ex + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int ex = (int)((hi >> 20) & 0x7ffu) - 896;  // binary32 biased exponent
+    if (ex <= 0 || ex >= 0xff) return (float)v;
+    const unsigned frac = (unsigned)((b >> 29) & 0x7fffffu);  // top 23 of the 52 fraction bits
+    const unsigned rest = (unsigned)(b & 0x1fffffffu);         // the 29 bits dropped
+    unsigned u = (hi & 0x80000000u) | ((unsigned)ex << 23) | frac;
+    // round to nearest, ties to even; a carry out of the fraction bumps the
+    // exponent, which is the correctly rounded result (infinity past the top)
+    const unsigned half = 0x10000000u;
+    u += (rest > half || (rest == half && (frac & 1u))) ? 1u : 0u;
+    return __uint_as_float(u);
+}
+
+// ----------------------------------------------------------------------------
 // Deterministic two-stage reductions: each block writes one partial (fixed
 // order inside the block), the last block to finish sums the partials in
 // index order and resets the arrival counter.  `nslot` independent sums.
@@ -249,5 +286,7 @@ cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaS
 cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s,
                            const int *zero_flag = nullptr);
 cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s);
+// out[i] = the integer-pipe conversion of in[i] (dir 0: double -> float, 1: float -> double)
+cudaError_t launch_convert(int dir, size_t count, const void *in, void *out, cudaStream_t s);
 
 }  // namespace mg

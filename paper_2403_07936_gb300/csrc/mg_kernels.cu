@@ -560,12 +560,25 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom_batched(const BottomG
 // ---------------------------------------------------------------------------
 // FP64 outer kernels
 // ---------------------------------------------------------------------------
+// The outer kernels are grid-stride loops over kRedBlocks x kRedThreads
+// threads with kUnroll independent points per iteration (loads in flight).
+constexpr int kUnroll = 4;
+
 __global__ void __launch_bounds__(kRedThreads) k_sum(const double *__restrict__ a, size_t N,
                                                      Reduction red) {
     __shared__ double sh[32];
     double v = 0.0;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
-        v += a[p];
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < N; p0 += kUnroll * stride) {
+        double t[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const size_t p = p0 + u * stride;
+            t[u] = p < N ? a[p] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) v += t[u];
+    }
     double vals[1] = {block_sum(v, sh)};
     reduce_finish<1>(red, vals, sh);
 }
@@ -579,48 +592,90 @@ __global__ void __launch_bounds__(kRedThreads) k_scaled_rhs(const double *__rest
         b[p] = h2 * (f[p] - mu);
 }
 
+// residual_norm_note: the residual itself is FP64 (it decides the accuracy of
+// the solution), but its norm only decides when to stop and is reported to
+// the user: each thread sums the squares of its float-rounded residuals in
+// FP32 (tens of terms, relative error ~1e-6) and the block and grid sums run
+// in FP64.  A relative residual of 1e-10 is therefore known to ~6 digits.
+//
+// Scaled FP64 residual at point p = i * n + j of the periodic grid (n = 2^lg):
+// s = h^2 (f - mu) - (4 x - (((x_N + x_S) + x_W) + x_E)).  fc = f - mu.
+__device__ __forceinline__ double residual_at(const double *__restrict__ f, const double *__restrict__ x,
+                                              size_t p, int n, int lg, double h2, double mu, double *fc) {
+    const int i = (int)(p >> lg), j = (int)(p & (size_t)(n - 1));
+    const size_t row = p - (size_t)j;
+    const size_t up = (size_t)((i - 1) & (n - 1)) << lg, dn = (size_t)((i + 1) & (n - 1)) << lg;
+    const double nb = ((x[up + j] + x[dn + j]) + x[row + ((j - 1) & (n - 1))]) + x[row + ((j + 1) & (n - 1))];
+    *fc = f[p] - mu;
+    return h2 * *fc - (4.0 * x[p] - nb);
+}
+
 template <bool WRITE32, bool FNORM>
 __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
     const double *__restrict__ f, const double *__restrict__ x, int n, double h2,
     const double *__restrict__ fsum, double mu_host, float *__restrict__ s32, Reduction red) {
     __shared__ double sh[32];
     const size_t N = (size_t)n * n;
+    const int lg = __ffs(n) - 1;
     const double mu = fsum ? *fsum / (double)N : mu_host;
-    double ss = 0.0, ff = 0.0;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(p / n), j = (int)(p - (size_t)i * n);
-        const int im = (i - 1) & (n - 1), ip = (i + 1) & (n - 1);
-        const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
-        const double nb = ((x[(size_t)im * n + j] + x[(size_t)ip * n + j]) + x[(size_t)i * n + jm]) +
-                          x[(size_t)i * n + jp];
-        const double fc = f[p] - mu;
-        const double s = h2 * fc - (4.0 * x[p] - nb);
-        ss += s * s;
-        if (FNORM) ff += fc * fc;
-        if (WRITE32) s32[p] = (float)s;
+    float ss = 0.f;  // squares of the float-rounded residual, FP32 per thread (see residual_norm_note)
+    double ff = 0.0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < N; p0 += 2 * stride) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const size_t p = p0 + u * stride;
+            if (p < N) {
+                double fc;
+                const float sv = f64_to_f32_rn(residual_at(f, x, p, n, lg, h2, mu, &fc));
+                ss = fmaf(sv, sv, ss);
+                if (FNORM) ff += fc * fc;
+                if (WRITE32) s32[p] = sv;
+            }
+        }
     }
     double vals[2];
-    vals[0] = block_sum(ss, sh);
+    vals[0] = block_sum((double)ss, sh);
     vals[1] = FNORM ? block_sum(ff, sh) : 0.0;
     reduce_finish<2>(red, vals, sh);
 }
 
+// x += e (FP64 update by the FP32 correction), sum e^2 -> out[0].  The norm
+// is reported, not used by the iteration, so its squares accumulate in FP32
+// per thread (then in FP64 across threads).
 __global__ void __launch_bounds__(kRedThreads) k_update(double *__restrict__ x,
                                                         const float *__restrict__ e, size_t N,
                                                         Reduction red) {
     __shared__ double sh[32];
-    double ee = 0.0, xs = 0.0;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-        const double d = (double)e[p];
-        const double xn = x[p] + d;
-        x[p] = xn;
-        ee += d * d;
-        xs += xn;
+    float ee = 0.f;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < N; p0 += kUnroll * stride) {
+        float ev[kUnroll];
+        double xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const size_t p = p0 + u * stride;
+            ev[u] = p < N ? e[p] : 0.f;
+            xv[u] = p < N ? x[p] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const size_t p = p0 + u * stride;
+            if (p < N) x[p] = xv[u] + f32_to_f64(ev[u]);
+            ee = fmaf(ev[u], ev[u], ee);
+        }
     }
-    double vals[2];
-    vals[0] = block_sum(ee, sh);
-    vals[1] = block_sum(xs, sh);
-    reduce_finish<2>(red, vals, sh);
+    double vals[1] = {block_sum((double)ee, sh)};
+    reduce_finish<1>(red, vals, sh);
+}
+
+__global__ void k_convert(int dir, size_t count, const void *__restrict__ in, void *__restrict__ out) {
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < count; p += (size_t)gridDim.x * blockDim.x) {
+        if (dir == 0)
+            ((float *)out)[p] = f64_to_f32_rn(((const double *)in)[p]);
+        else
+            ((double *)out)[p] = f32_to_f64(((const float *)in)[p]);
+    }
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_project(double *__restrict__ x, size_t N,
@@ -729,24 +784,27 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc 
     __shared__ double sh[32];
     const RhsDesc d = rd[find_rhs(rd, nrhs)];
     if (active && !active[d.slot]) return;
-    const int n = d.n;
+    const int n = d.n, lg = __ffs(n) - 1;
     const size_t N = (size_t)n * n;
     const double mu = fsum[(size_t)d.slot * kMaxSlots] / (double)N;
-    double ss = 0.0, ff = 0.0;
-    for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x) {
-        const int i = (int)(p / n), j = (int)(p - (size_t)i * n);
-        const int im = (i - 1) & (n - 1), ip = (i + 1) & (n - 1);
-        const int jm = (j - 1) & (n - 1), jp = (j + 1) & (n - 1);
-        const double *x = d.x;
-        const double nb = ((x[(size_t)im * n + j] + x[(size_t)ip * n + j]) + x[(size_t)i * n + jm]) + x[(size_t)i * n + jp];
-        const double fc = d.f[p] - mu;
-        const double s = d.h2 * fc - (4.0 * x[p] - nb);
-        ss += s * s;
-        if (FNORM) ff += fc * fc;
-        d.s32[p] = (float)s;
+    float ss = 0.f;
+    double ff = 0.0;
+    const size_t stride = (size_t)d.nblk * blockDim.x;
+    for (size_t p0 = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p0 < N; p0 += 2 * stride) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const size_t p = p0 + u * stride;
+            if (p < N) {
+                double fc;
+                const float sv = f64_to_f32_rn(residual_at(d.f, d.x, p, n, lg, d.h2, mu, &fc));
+                ss = fmaf(sv, sv, ss);
+                if (FNORM) ff += fc * fc;
+                d.s32[p] = sv;
+            }
+        }
     }
     double vals[2];
-    vals[0] = block_sum(ss, sh);
+    vals[0] = block_sum((double)ss, sh);
     vals[1] = FNORM ? block_sum(ff, sh) : 0.0;
     batch_finish<2>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
@@ -757,13 +815,25 @@ __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restr
     const RhsDesc d = rd[find_rhs(rd, nrhs)];
     if (active && !active[d.slot]) return;
     const size_t N = (size_t)d.n * d.n;
-    double ee = 0.0;
-    for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x) {
-        const double e = (double)d.e[p];
-        d.x[p] += e;
-        ee += e * e;
+    float ee = 0.f;
+    const size_t stride = (size_t)d.nblk * blockDim.x;
+    for (size_t p0 = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p0 < N; p0 += kUnroll * stride) {
+        float ev[kUnroll];
+        double xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const size_t p = p0 + u * stride;
+            ev[u] = p < N ? d.e[p] : 0.f;
+            xv[u] = p < N ? d.x[p] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const size_t p = p0 + u * stride;
+            if (p < N) d.x[p] = xv[u] + f32_to_f64(ev[u]);
+            ee = fmaf(ev[u], ev[u], ee);
+        }
     }
-    double vals[1] = {block_sum(ee, sh)};
+    double vals[1] = {block_sum((double)ee, sh)};
     batch_finish<1>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
 
@@ -1001,6 +1071,11 @@ cudaError_t launch_outer_residual(const double *f, const double *x, int n, doubl
         else
             k_outer_residual<false, false><<<kRedBlocks, kRedThreads, 0, s>>>(f, x, n, h2, mu_sum, mu_host, s32, red);
     }
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_convert(int dir, size_t count, const void *in, void *out, cudaStream_t s) {
+    k_convert<<<kRedBlocks, kRedThreads, 0, s>>>(dir, count, in, out);
     count_launches(1);
     return cudaGetLastError();
 }

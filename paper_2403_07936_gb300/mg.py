@@ -76,6 +76,7 @@ SIGNATURES = {
     "mg_op_sr_conv": (_I, [_I, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mg_op_sr_generator": (_I, [_VP, _VP, _I, _VP]),
     "mg_op_outer_residual": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP]),
+    "mg_op_convert": (_I, [_I, _SZ, _VP, _VP, _VP]),
 }
 
 _lib = None
@@ -341,3 +342,9 @@ def op_sr_generator(ctx: "Context", ec, out):
 def op_outer_residual(f, x, mu: float, s32, out, stream=None):
     _check(load().mg_op_outer_residual(f.shape[-1], ptr(f), ptr(x), mu, ptr(s32), ptr(out),
                                        stream_handle(stream)))
+
+
+def op_convert(inp, out, stream=None):
+    """Integer-pipe conversion: double -> float (round to nearest even) or float -> double."""
+    direction = 0 if "float64" in str(inp.dtype) else 1
+    _check(load().mg_op_convert(direction, inp.numel(), ptr(inp), ptr(out), stream_handle(stream)))
