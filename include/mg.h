@@ -202,6 +202,16 @@ void mg_server_destroy(mg_server *srv);
  * line).  *n_timed (may be NULL) = entries measured.  Synchronous. */
 mg_status mg_autotune(mg_ctx *ctx, const char *cache_path, int *n_timed);
 
+/* Programmatic dependent launch between the library's kernels (process-wide;
+ * off unless the environment variable MG_LAUNCH_OVERLAP=1 was set at first
+ * use).  When on, each kernel is launched with CUDA's programmatic stream
+ * serialization and starts by waiting for its predecessor's completion, so
+ * the next kernel's blocks are scheduled while the previous grid drains.
+ * Results are identical either way; graphs recorded before a change are
+ * re-recorded.  (Measured on GB300: slower for these kernels, hence off.) */
+mg_status mg_set_launch_overlap(int enable);
+int mg_get_launch_overlap(void);
+
 /* Read or set one table entry (n a power of two >= 128, nu 0..4). */
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant);
 mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);

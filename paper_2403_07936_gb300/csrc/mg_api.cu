@@ -228,7 +228,7 @@ template <> const double *ainv<double>(mg_ctx *c) { return c->ainv64; }
 template <typename T>
 static mg_status vcycle_rec(mg_ctx *c, int l, T *x, T *t, const T *b, bool zero) {
     const int n = c->lv[l].n;
-    if (n <= kBottomMax) {
+    if (n <= bottom_max<T>()) {
         MG_CUDA(launch_bottom<T>(x, b, n, c->coarsest, c->nu1, c->nu2, zero, ainv<T>(c), c->taps,
                                  c->stream));
         return MG_OK;
@@ -1525,7 +1525,7 @@ mg_status mg_autotune(mg_ctx *c, const char *cache_path, int *n_timed) {
     MG_TRY(ensure_hierarchy(c, false));
     std::vector<TuneLevel> lv;
     for (int l = 0; l + 1 < c->levels; ++l)
-        if (c->lv[l].n > kBottomMax)
+        if (c->lv[l].n > bottom_max<float>())
             lv.push_back(TuneLevel{c->lv[l].n, c->lv[l].x32, c->lv[l].t32, c->lv[l].b32, c->lv[l + 1].b32,
                                    c->lv[l + 1].x32});
     char err[256] = {0};
@@ -1534,6 +1534,13 @@ mg_status mg_autotune(mg_ctx *c, const char *cache_path, int *n_timed) {
     if (st != MG_OK) set_err("%s", err);
     return st;
 }
+
+mg_status mg_set_launch_overlap(int enable) {
+    set_launch_overlap(enable != 0);
+    return MG_OK;
+}
+
+int mg_get_launch_overlap(void) { return launch_overlap_enabled() ? 1 : 0; }
 
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant) {
     if (!variant || kind < 0 || kind > 1 || !is_pow2(n) || n < 128 || nu < 0 || nu > 4) {
@@ -1753,9 +1760,10 @@ mg_status mg_op_up(int dtype, int n, const void *x, void *x_out, const void *b, 
 mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, int nu1, int nu2,
                        int zero_init, void *stream) {
     MG_TRY(op_check(dtype, n, 4));
-    if (n > kBottomMax || !is_pow2(coarsest) || coarsest < 4 || coarsest > 16 || coarsest > n ||
+    const int nmax = dtype == 0 ? bottom_max<double>() : bottom_max<float>();
+    if (n > nmax || !is_pow2(coarsest) || coarsest < 4 || coarsest > 16 || coarsest > n ||
         !x || !b || nu1 < 0 || nu1 > 4 || nu2 < 0 || nu2 > 4) {
-        set_err("invalid arguments (n <= %d, coarsest 4..16)", kBottomMax);
+        set_err("invalid arguments (n <= %d for this dtype, coarsest 4..16)", nmax);
         return MG_ERR_INVALID_ARG;
     }
     const int Nc = coarsest * coarsest;

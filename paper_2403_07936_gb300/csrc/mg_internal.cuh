@@ -200,6 +200,12 @@ int tile_variant(int kind, int n, int nu);
 void set_tile_variant(int kind, int n, int nu, int variant);
 // Incremented whenever a table entry changes (recorded graphs re-record).
 unsigned tune_epoch();
+// Programmatic dependent launch of the path's kernels (process-wide, off by
+// default; the environment variable MG_LAUNCH_OVERLAP=1 starts it on).  On
+// GB300 it measured slower: a 2048^2 mixed solve took 1.96 ms with it and
+// 1.73 ms without.
+bool launch_overlap_enabled();
+void set_launch_overlap(bool on);
 
 // ----------------------------------------------------------------------------
 // Host-side launchers (defined in mg_kernels.cu); all return cudaError_t.
@@ -217,7 +223,12 @@ cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int n
 template <typename T>
 cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool zero_init,
                           const T *ainv, const FirTaps &taps, cudaStream_t s);
-constexpr int kBottomMax = 64;  // grids up to 64 x 64 run the bottom kernel
+// Grids up to bottom_max<T>() squared run the bottom kernel (one block, the
+// whole V-cycle below in shared memory).  One SM is slower than the tile
+// kernels on the whole GPU from 128^2 up, so the limit is 64 for both types
+// (the kernel itself fits 128^2 in FP32).
+constexpr int kBottomMax = 64;  // the FP32 limit (batched solves and the server are FP32)
+template <typename T> constexpr int bottom_max() { return 64; }
 
 // Set the message mg_last_error() returns on the calling thread.
 void set_last_error(const char *msg);

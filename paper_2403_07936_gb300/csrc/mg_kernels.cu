@@ -27,6 +27,7 @@
 
 #include <atomic>
 #include <type_traits>
+#include <utility>
 
 #include "mg_internal.cuh"
 
@@ -50,6 +51,37 @@ void fir_taps_host(FirTaps *t) {
 namespace {
 
 constexpr int kThreads = 256;  // threads per tile block
+
+// Programmatic dependent launch.  Every kernel of the path starts with
+// pdl_enter(): griddepcontrol.wait blocks until the grids this one depends on
+// have completed and their writes are visible, then launch_dependents lets
+// the next kernel in the stream start launching (its blocks get scheduled on
+// SMs that this grid's tail leaves idle, and wait there in turn).  For a
+// kernel launched without the attribute both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch k with the programmatic-stream-serialization attribute when
+// launch overlap is enabled (launch_overlap_enabled()), else as a plain launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    if (launch_overlap_enabled()) {
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
@@ -257,6 +289,7 @@ template <typename T, int NU, bool ZERO, int TY>
 __global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *__restrict__ xout,
                                                    const T *__restrict__ b, int n,
                                                    T *__restrict__ bc) {
+    pdl_enter();
     down_tile<T, NU, TY>(x, xout, b, n, bc, blockIdx.y * TY, blockIdx.x * kTX, ZERO);
 }
 
@@ -275,6 +308,7 @@ __device__ __forceinline__ int find_grid(const TileGrid *__restrict__ g, int ngr
 template <typename T, int NU, int TY>
 __global__ void __launch_bounds__(kThreads) k_down_batched(const TileGrid *__restrict__ tab, int ngrid,
                                                            const int *__restrict__ active) {
+    pdl_enter();
     const TileGrid t = tab[find_grid(tab, ngrid)];
     if (active && !active[t.rhs]) return;
     const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / kTX;
@@ -393,12 +427,14 @@ template <typename T, int NU, int TY, int NJ>
 __global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__restrict__ xout,
                                                  const T *__restrict__ b, const T *__restrict__ ec,
                                                  const T *__restrict__ extra, int n, FirTaps taps) {
+    pdl_enter();
     up_tile<T, NU, TY, NJ>(x, xout, b, ec, extra, n, taps, blockIdx.y * TY, blockIdx.x * kTX);
 }
 
 template <typename T, int NU, int TY, int NJ>
 __global__ void __launch_bounds__(kThreads) k_up_batched(const TileGrid *__restrict__ tab, int ngrid,
                                                          const int *__restrict__ active, FirTaps taps) {
+    pdl_enter();
     const TileGrid t = tab[find_grid(tab, ngrid)];
     if (active && !active[t.rhs]) return;
     const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / kTX;
@@ -412,16 +448,36 @@ __global__ void __launch_bounds__(kThreads) k_up_batched(const TileGrid *__restr
 constexpr int kBottomThreads = 1024;
 
 template <typename T>
-__device__ __forceinline__ void sweep_periodic(T *X, const T *B, int m, int colour) {
+__device__ __forceinline__ void sweep_periodic(T *X, const T *B, int m, int lg, int colour) {
     const int half = (m * m) >> 1, hm = m >> 1;
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-        const int i = idx / hm, k = idx - i * hm;
+        const int i = idx >> (lg - 1), k = idx & (hm - 1);
         const int j = 2 * k + ((i + colour) & 1);
         const int im = (i - 1) & (m - 1), ip = (i + 1) & (m - 1);
         const int jm = (j - 1) & (m - 1), jp = (j + 1) & (m - 1);
         const T nb = ((X[im * m + j] + X[ip * m + j]) + X[i * m + jm]) + X[i * m + jp];
         X[i * m + j] = (B[i * m + j] + nb) * T(0.25);
     }
+}
+
+// Scaled residual b - (4x - (((N + S) + W) + E)) at (i, j) of an m x m level (indices wrap).
+template <typename T>
+__device__ __forceinline__ T residual_periodic(const T *X, const T *B, int m, int i, int j) {
+    i &= m - 1;
+    j &= m - 1;
+    const int im = (i - 1) & (m - 1), ip = (i + 1) & (m - 1);
+    const int jm = (j - 1) & (m - 1), jp = (j + 1) & (m - 1);
+    const T nb = ((X[im * m + j] + X[ip * m + j]) + X[i * m + jm]) + X[i * m + jp];
+    return B[i * m + j] - (T(4) * X[i * m + j] - nb);
+}
+
+// Shared-memory elements of a bottom solve of an n x n grid with nlev levels:
+// x and b per level, plus n * n / 2 for the row-refined coarse grid of the
+// prolongation.
+__host__ __device__ constexpr size_t bottom_elems(int n, int nlev) {
+    size_t e = (size_t)n * n / 2;
+    for (int l = 0; l < nlev; ++l) e += 2ull * (n >> l) * (n >> l);
+    return e;
 }
 
 template <typename T>
@@ -439,8 +495,9 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
         B[l] = base + off;
         off += m * m;
     }
-    T *S = base + off;  // n*n scratch: residual, then row-refined coarse rows
+    T *S = base + off;  // n * n / 2 scratch: row-refined coarse rows
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lg0 = __ffs(n) - 1;
 
     for (int p = tid; p < n * n; p += nt) {
         X[0][p] = zero_init ? T(0) : x[p];
@@ -448,29 +505,27 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
     }
     __syncthreads();
     for (int l = 0; l + 1 < nlev; ++l) {
-        const int m = n >> l, mc = m >> 1;
+        const int m = n >> l, mc = m >> 1, lg = lg0 - l;
         for (int s = 0; s < nu1; ++s) {
-            sweep_periodic(X[l], B[l], m, 0);
+            sweep_periodic(X[l], B[l], m, lg, 0);
             __syncthreads();
-            sweep_periodic(X[l], B[l], m, 1);
+            sweep_periodic(X[l], B[l], m, lg, 1);
             __syncthreads();
         }
-        for (int p = tid; p < m * m; p += nt) {
-            const int i = p / m, j = p - i * m;
-            const int im = (i - 1) & (m - 1), ip = (i + 1) & (m - 1);
-            const int jm = (j - 1) & (m - 1), jp = (j + 1) & (m - 1);
-            const T nb = ((X[l][im * m + j] + X[l][ip * m + j]) + X[l][i * m + jm]) + X[l][i * m + jp];
-            S[p] = B[l][p] - (T(4) * X[l][p] - nb);
-        }
-        __syncthreads();
+        // full weighting of the residual, evaluated where it is needed
+        // (times 4 because h_c^2 = 4 h^2)
         for (int q = tid; q < mc * mc; q += nt) {
-            const int I = q / mc, J = q - I * mc;
+            const int I = q >> (lg - 1), J = q & (mc - 1);
             const int i = 2 * I, j = 2 * J;
-            const int im = (i - 1) & (m - 1), ip = (i + 1) & (m - 1);
-            const int jm = (j - 1) & (m - 1), jp = (j + 1) & (m - 1);
-            const T edge = ((S[im * m + j] + S[ip * m + j]) + S[i * m + jm]) + S[i * m + jp];
-            const T corner = ((S[im * m + jm] + S[im * m + jp]) + S[ip * m + jm]) + S[ip * m + jp];
-            B[l + 1][q] = (T(4) * S[i * m + j] + T(2) * edge + corner) * T(0.25);
+            const T *Xl = X[l], *Bl = B[l];
+            const T edge = ((residual_periodic(Xl, Bl, m, i - 1, j) + residual_periodic(Xl, Bl, m, i + 1, j)) +
+                            residual_periodic(Xl, Bl, m, i, j - 1)) +
+                           residual_periodic(Xl, Bl, m, i, j + 1);
+            const T corner =
+                ((residual_periodic(Xl, Bl, m, i - 1, j - 1) + residual_periodic(Xl, Bl, m, i - 1, j + 1)) +
+                 residual_periodic(Xl, Bl, m, i + 1, j - 1)) +
+                residual_periodic(Xl, Bl, m, i + 1, j + 1);
+            B[l + 1][q] = (T(4) * residual_periodic(Xl, Bl, m, i, j) + T(2) * edge + corner) * T(0.25);
             X[l + 1][q] = T(0);
         }
         __syncthreads();
@@ -492,10 +547,10 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
     }
     constexpr int L = Prec<T>::L;
     for (int l = nlev - 2; l >= 0; --l) {
-        const int m = n >> l, mc = m >> 1;
+        const int m = n >> l, mc = m >> 1, lg = lg0 - l;
         const T *E = X[l + 1];
         for (int p = tid; p < mc * m; p += nt) {  // refine coarse rows along x
-            const int I = p / m, j = p - I * m;
+            const int I = p >> lg, j = p & (m - 1);
             T val;
             if ((j & 1) == 0) {
                 val = E[I * mc + (j >> 1)];
@@ -512,7 +567,7 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
         }
         __syncthreads();
         for (int p = tid; p < m * m; p += nt) {  // refine along y and add
-            const int i = p / m, j = p - i * m;
+            const int i = p >> lg, j = p & (m - 1);
             T val;
             if ((i & 1) == 0) {
                 val = S[(i >> 1) * m + j];
@@ -529,9 +584,9 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
         }
         __syncthreads();
         for (int s = 0; s < nu2; ++s) {
-            sweep_periodic(X[l], B[l], m, 0);
+            sweep_periodic(X[l], B[l], m, lg, 0);
             __syncthreads();
-            sweep_periodic(X[l], B[l], m, 1);
+            sweep_periodic(X[l], B[l], m, lg, 1);
             __syncthreads();
         }
     }
@@ -543,6 +598,7 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ x, co
                                                            int n, int nlev, int nu1, int nu2,
                                                            int zero_init, const T *__restrict__ ainv,
                                                            FirTaps taps) {
+    pdl_enter();
     bottom_body<T>(x, b, n, nlev, nu1, nu2, zero_init, ainv, taps);
 }
 
@@ -552,6 +608,7 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom_batched(const BottomG
                                                                    int nu1, int nu2,
                                                                    const int *__restrict__ active,
                                                                    FirTaps taps) {
+    pdl_enter();
     const BottomGrid g = tab[blockIdx.x];
     if (active && !active[g.rhs]) return;
     bottom_body<T>((T *)g.x, (const T *)g.b, g.n, g.nlev, nu1, nu2, g.zero, (const T *)g.ainv, taps);
@@ -566,6 +623,7 @@ constexpr int kUnroll = 4;
 
 __global__ void __launch_bounds__(kRedThreads) k_sum(const double *__restrict__ a, size_t N,
                                                      Reduction red) {
+    pdl_enter();
     __shared__ double sh[32];
     double v = 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -586,6 +644,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sum(const double *__restrict__ 
 __global__ void __launch_bounds__(kRedThreads) k_scaled_rhs(const double *__restrict__ f, int n,
                                                             double h2, const double *__restrict__ fsum,
                                                             double *__restrict__ b) {
+    pdl_enter();
     const size_t N = (size_t)n * n;
     const double mu = *fsum / (double)N;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
@@ -614,6 +673,7 @@ template <bool WRITE32, bool FNORM>
 __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
     const double *__restrict__ f, const double *__restrict__ x, int n, double h2,
     const double *__restrict__ fsum, double mu_host, float *__restrict__ s32, Reduction red) {
+    pdl_enter();
     __shared__ double sh[32];
     const size_t N = (size_t)n * n;
     const int lg = __ffs(n) - 1;
@@ -646,6 +706,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
 __global__ void __launch_bounds__(kRedThreads) k_update(double *__restrict__ x,
                                                         const float *__restrict__ e, size_t N,
                                                         Reduction red) {
+    pdl_enter();
     __shared__ double sh[32];
     float ee = 0.f;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -670,6 +731,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update(double *__restrict__ x,
 }
 
 __global__ void k_convert(int dir, size_t count, const void *__restrict__ in, void *__restrict__ out) {
+    pdl_enter();
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < count; p += (size_t)gridDim.x * blockDim.x) {
         if (dir == 0)
             ((float *)out)[p] = f64_to_f32_rn(((const double *)in)[p]);
@@ -681,6 +743,7 @@ __global__ void k_convert(int dir, size_t count, const void *__restrict__ in, vo
 __global__ void __launch_bounds__(kRedThreads) k_project(double *__restrict__ x, size_t N,
                                                          const double *__restrict__ sum,
                                                          const int *__restrict__ zero_flag) {
+    pdl_enter();
     const bool zero = zero_flag && *zero_flag;
     const double mu = *sum / (double)N;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
@@ -690,6 +753,7 @@ __global__ void __launch_bounds__(kRedThreads) k_project(double *__restrict__ x,
 __global__ void k_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
                         double n2, double h2, double tol, int step, int max_cycles, int first,
                         cudaGraphConditionalHandle handle) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (first) {
         st->fnorm = sqrt(rsum[1]);
@@ -765,6 +829,7 @@ __device__ __forceinline__ void batch_finish(const BatchRed &red, int slot, int 
 
 template <bool OF_X>
 __global__ void __launch_bounds__(kRedThreads) k_sum_b(const RhsDesc *__restrict__ rd, int nrhs, BatchRed red) {
+    pdl_enter();
     __shared__ double sh[32];
     const int r = find_rhs(rd, nrhs);
     const RhsDesc d = rd[r];
@@ -781,6 +846,7 @@ template <bool FNORM>
 __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc *__restrict__ rd, int nrhs,
                                                                   const double *__restrict__ fsum,
                                                                   const int *__restrict__ active, BatchRed red) {
+    pdl_enter();
     __shared__ double sh[32];
     const RhsDesc d = rd[find_rhs(rd, nrhs)];
     if (active && !active[d.slot]) return;
@@ -811,6 +877,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc 
 
 __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restrict__ rd, int nrhs,
                                                           const int *__restrict__ active, BatchRed red) {
+    pdl_enter();
     __shared__ double sh[32];
     const RhsDesc d = rd[find_rhs(rd, nrhs)];
     if (active && !active[d.slot]) return;
@@ -840,6 +907,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restr
 __global__ void __launch_bounds__(kRedThreads) k_project_b(const RhsDesc *__restrict__ rd, int nrhs,
                                                            const double *__restrict__ xsum,
                                                            const DevState *__restrict__ st) {
+    pdl_enter();
     const RhsDesc d = rd[find_rhs(rd, nrhs)];
     const size_t N = (size_t)d.n * d.n;
     const bool zero = st[d.slot].zero_source != 0;
@@ -853,6 +921,7 @@ __global__ void __launch_bounds__(kRedThreads) k_project_b(const RhsDesc *__rest
 __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs, const double *rsum,
                           const double *usum, const double *fsum, double tol, int step, int max_cycles,
                           int first_all, int *active, cudaGraphConditionalHandle handle, int use_handle) {
+    pdl_enter();
     int any = 0;
     for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
         const int slot = rd[r].slot;
@@ -925,7 +994,11 @@ cudaError_t down_impl(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_
     cudaError_t e = set_smem_once(k, Cfg::smem, done);
     if (e != cudaSuccess) return e;
     dim3 grid(n / Cfg::TX, n / Cfg::TY);
-    k<<<grid, kThreads, Cfg::smem, s>>>(x, xout, b, n, bc);
+    {
+        cudaError_t le_ = launch_kernel(k, grid, kThreads, Cfg::smem, s,
+                                        x, xout, b, n, bc);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -939,7 +1012,11 @@ cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra
     cudaError_t e = set_smem_once(k, Cfg::smem, done);
     if (e != cudaSuccess) return e;
     dim3 grid(n / Cfg::TX, n / Cfg::TY);
-    k<<<grid, kThreads, Cfg::smem, s>>>(x, xout, b, ec, extra, n, taps);
+    {
+        cudaError_t le_ = launch_kernel(k, grid, kThreads, Cfg::smem, s,
+                                        x, xout, b, ec, extra, n, taps);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1008,24 +1085,20 @@ cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int n
 template <typename T>
 cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool zero_init,
                           const T *ainv, const FirTaps &taps, cudaStream_t s) {
-    if (n > kBottomMax || coarsest < 4 || coarsest > n) return cudaErrorInvalidValue;
+    if (n > bottom_max<T>() || coarsest < 4 || coarsest > n) return cudaErrorInvalidValue;
     int nlev = 0;
-    size_t elems = 0;
-    for (int m = n; m >= coarsest; m >>= 1) {
-        elems += 2ull * m * m;
-        ++nlev;
-    }
+    for (int m = n; m >= coarsest; m >>= 1) ++nlev;
     if ((n >> (nlev - 1)) != coarsest || nlev > 8) return cudaErrorInvalidValue;
-    elems += (size_t)n * n;
-    const size_t smem = elems * sizeof(T);
+    const size_t smem = bottom_elems(n, nlev) * sizeof(T);
     auto k = k_bottom<T>;
-    // configure once for the largest bottom configuration (64^2 down to 4^2)
-    size_t max_elems = (size_t)kBottomMax * kBottomMax;
-    for (int m = kBottomMax; m >= 4; m >>= 1) max_elems += 2ull * m * m;
     static std::atomic<unsigned> done{0};
-    cudaError_t e = set_smem_once(k, max_elems * sizeof(T), done);
+    cudaError_t e = set_smem_once(k, bottom_elems(bottom_max<T>(), 6) * sizeof(T), done);  // largest: down to 4^2
     if (e != cudaSuccess) return e;
-    k<<<1, kBottomThreads, smem, s>>>(x, b, n, nlev, nu1, nu2, zero_init ? 1 : 0, ainv, taps);
+    {
+        cudaError_t le_ = launch_kernel(k, 1, kBottomThreads, smem, s,
+                                        x, b, n, nlev, nu1, nu2, zero_init ? 1 : 0, ainv, taps);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1044,7 +1117,11 @@ template cudaError_t launch_bottom<double>(double *, const double *, int, int, i
                                            const double *, const FirTaps &, cudaStream_t);
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s) {
-    k_sum<<<kRedBlocks, kRedThreads, 0, s>>>(f, (size_t)n * n, red);
+    {
+        cudaError_t le_ = launch_kernel(k_sum, kRedBlocks, kRedThreads, 0, s,
+                                        f, (size_t)n * n, red);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1053,7 +1130,11 @@ cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s) {
 }
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum, double *b,
                               cudaStream_t s) {
-    k_scaled_rhs<<<kRedBlocks, kRedThreads, 0, s>>>(f, n, h2, f_sum, b);
+    {
+        cudaError_t le_ = launch_kernel(k_scaled_rhs, kRedBlocks, kRedThreads, 0, s,
+                                        f, n, h2, f_sum, b);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1062,30 +1143,58 @@ cudaError_t launch_outer_residual(const double *f, const double *x, int n, doubl
                                   bool want_fnorm, Reduction red, cudaStream_t s) {
     if (s32) {
         if (want_fnorm)
-            k_outer_residual<true, true><<<kRedBlocks, kRedThreads, 0, s>>>(f, x, n, h2, mu_sum, mu_host, s32, red);
+            {
+                cudaError_t le_ = launch_kernel(k_outer_residual<true, true>, kRedBlocks, kRedThreads, 0, s,
+                                                f, x, n, h2, mu_sum, mu_host, s32, red);
+                if (le_ != cudaSuccess) return le_;
+            }
         else
-            k_outer_residual<true, false><<<kRedBlocks, kRedThreads, 0, s>>>(f, x, n, h2, mu_sum, mu_host, s32, red);
+            {
+                cudaError_t le_ = launch_kernel(k_outer_residual<true, false>, kRedBlocks, kRedThreads, 0, s,
+                                                f, x, n, h2, mu_sum, mu_host, s32, red);
+                if (le_ != cudaSuccess) return le_;
+            }
     } else {
         if (want_fnorm)
-            k_outer_residual<false, true><<<kRedBlocks, kRedThreads, 0, s>>>(f, x, n, h2, mu_sum, mu_host, s32, red);
+            {
+                cudaError_t le_ = launch_kernel(k_outer_residual<false, true>, kRedBlocks, kRedThreads, 0, s,
+                                                f, x, n, h2, mu_sum, mu_host, s32, red);
+                if (le_ != cudaSuccess) return le_;
+            }
         else
-            k_outer_residual<false, false><<<kRedBlocks, kRedThreads, 0, s>>>(f, x, n, h2, mu_sum, mu_host, s32, red);
+            {
+                cudaError_t le_ = launch_kernel(k_outer_residual<false, false>, kRedBlocks, kRedThreads, 0, s,
+                                                f, x, n, h2, mu_sum, mu_host, s32, red);
+                if (le_ != cudaSuccess) return le_;
+            }
     }
     count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_convert(int dir, size_t count, const void *in, void *out, cudaStream_t s) {
-    k_convert<<<kRedBlocks, kRedThreads, 0, s>>>(dir, count, in, out);
+    {
+        cudaError_t le_ = launch_kernel(k_convert, kRedBlocks, kRedThreads, 0, s,
+                                        dir, count, in, out);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaStream_t s) {
-    k_update<<<kRedBlocks, kRedThreads, 0, s>>>(x, e, (size_t)n * n, red);
+    {
+        cudaError_t le_ = launch_kernel(k_update, kRedBlocks, kRedThreads, 0, s,
+                                        x, e, (size_t)n * n, red);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag) {
-    k_project<<<kRedBlocks, kRedThreads, 0, s>>>(x, (size_t)n * n, sum, zero_flag);
+    {
+        cudaError_t le_ = launch_kernel(k_project, kRedBlocks, kRedThreads, 0, s,
+                                        x, (size_t)n * n, sum, zero_flag);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1093,7 +1202,11 @@ cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, 
 cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
                          double n2, double h2, double tol, int step, int max_cycles, bool first,
                          cudaGraphConditionalHandle handle, cudaStream_t s) {
-    k_check<<<1, 32, 0, s>>>(st, rsum, usum, fsum, n2, h2, tol, step, max_cycles, first ? 1 : 0, handle);
+    {
+        cudaError_t le_ = launch_kernel(k_check, 1, 32, 0, s,
+                                        st, rsum, usum, fsum, n2, h2, tol, step, max_cycles, first ? 1 : 0, handle);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1105,7 +1218,11 @@ cudaError_t down_batched_impl(const TileGrid *tab, int ngrid, int nblocks, const
     static std::atomic<unsigned> done{0};
     cudaError_t e = set_smem_once(k, DownCfg<float, NU, TY>::smem, done);
     if (e != cudaSuccess) return e;
-    k<<<nblocks, kThreads, DownCfg<float, NU, TY>::smem, s>>>(tab, ngrid, active);
+    {
+        cudaError_t le_ = launch_kernel(k, nblocks, kThreads, DownCfg<float, NU, TY>::smem, s,
+                                        tab, ngrid, active);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1116,7 +1233,11 @@ cudaError_t up_batched_impl(const TileGrid *tab, int ngrid, int nblocks, const i
     static std::atomic<unsigned> done{0};
     cudaError_t e = set_smem_once(k, UpCfg<float, NU, TY, NJ>::smem, done);
     if (e != cudaSuccess) return e;
-    k<<<nblocks, kThreads, UpCfg<float, NU, TY, NJ>::smem, s>>>(tab, ngrid, active, taps);
+    {
+        cudaError_t le_ = launch_kernel(k, nblocks, kThreads, UpCfg<float, NU, TY, NJ>::smem, s,
+                                        tab, ngrid, active, taps);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1165,21 +1286,32 @@ cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int n
 
 cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int nu2, const int *active,
                                   const FirTaps &taps, cudaStream_t s) {
-    size_t max_elems = (size_t)kBottomMax * kBottomMax;
-    for (int m = kBottomMax; m >= 4; m >>= 1) max_elems += 2ull * m * m;
+    const size_t bytes = bottom_elems(kBottomMax, 6) * sizeof(float);  // the largest: 128^2 down to 4^2
     static std::atomic<unsigned> done{0};
-    cudaError_t e = set_smem_once(k_bottom_batched<float>, max_elems * sizeof(float), done);
+    cudaError_t e = set_smem_once(k_bottom_batched<float>, bytes, done);
     if (e != cudaSuccess) return e;
-    k_bottom_batched<float><<<ngrid, kBottomThreads, max_elems * sizeof(float), s>>>(tab, nu1, nu2, active, taps);
+    {
+        cudaError_t le_ = launch_kernel(k_bottom_batched<float>, ngrid, kBottomThreads, bytes, s,
+                                        tab, nu1, nu2, active, taps);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of_x, BatchRed red, cudaStream_t s) {
     if (of_x)
-        k_sum_b<true><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, red);
+        {
+            cudaError_t le_ = launch_kernel(k_sum_b<true>, nblocks, kRedThreads, 0, s,
+                                            rd, nrhs, red);
+            if (le_ != cudaSuccess) return le_;
+        }
     else
-        k_sum_b<false><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, red);
+        {
+            cudaError_t le_ = launch_kernel(k_sum_b<false>, nblocks, kRedThreads, 0, s,
+                                            rd, nrhs, red);
+            if (le_ != cudaSuccess) return le_;
+        }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1187,23 +1319,39 @@ cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of
 cudaError_t launch_outer_residual_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *fsum,
                                           bool want_fnorm, const int *active, BatchRed red, cudaStream_t s) {
     if (want_fnorm)
-        k_outer_residual_b<true><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, fsum, active, red);
+        {
+            cudaError_t le_ = launch_kernel(k_outer_residual_b<true>, nblocks, kRedThreads, 0, s,
+                                            rd, nrhs, fsum, active, red);
+            if (le_ != cudaSuccess) return le_;
+        }
     else
-        k_outer_residual_b<false><<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, fsum, active, red);
+        {
+            cudaError_t le_ = launch_kernel(k_outer_residual_b<false>, nblocks, kRedThreads, 0, s,
+                                            rd, nrhs, fsum, active, red);
+            if (le_ != cudaSuccess) return le_;
+        }
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_batched(const RhsDesc *rd, int nrhs, int nblocks, const int *active, BatchRed red,
                                   cudaStream_t s) {
-    k_update_b<<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, active, red);
+    {
+        cudaError_t le_ = launch_kernel(k_update_b, nblocks, kRedThreads, 0, s,
+                                        rd, nrhs, active, red);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *xsum,
                                    const DevState *st, cudaStream_t s) {
-    k_project_b<<<nblocks, kRedThreads, 0, s>>>(rd, nrhs, xsum, st);
+    {
+        cudaError_t le_ = launch_kernel(k_project_b, nblocks, kRedThreads, 0, s,
+                                        rd, nrhs, xsum, st);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1212,8 +1360,11 @@ cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, cons
                                  const double *usum, const double *fsum, double tol, int step, int max_cycles,
                                  bool first, int *active, cudaGraphConditionalHandle handle, bool use_handle,
                                  cudaStream_t s) {
-    k_check_b<<<1, 256, 0, s>>>(st, rd, nrhs, rsum, usum, fsum, tol, step, max_cycles, first ? 1 : 0, active, handle,
-                                use_handle ? 1 : 0);
+    {
+        cudaError_t le_ = launch_kernel(k_check_b, 1, 256, 0, s,
+                                        st, rd, nrhs, rsum, usum, fsum, tol, step, max_cycles, first ? 1 : 0, active, handle, use_handle ? 1 : 0);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1246,10 +1397,8 @@ static cudaError_t prepare_type() {
     if (e == cudaSuccess) e = prepare_nu<T, 2>();
     if (e == cudaSuccess) e = prepare_nu<T, 3>();
     if (e == cudaSuccess) e = prepare_nu<T, 4>();
-    // the bottom kernel's largest configuration: 64^2 down to 4^2
-    size_t elems = (size_t)kBottomMax * kBottomMax;
-    for (int m = kBottomMax; m >= 4; m >>= 1) elems += 2ull * m * m;
-    if (e == cudaSuccess) e = set_smem(k_bottom<T>, elems * sizeof(T));
+    // the bottom kernel's largest configuration: bottom_max<T>()^2 down to 4^2
+    if (e == cudaSuccess) e = set_smem(k_bottom<T>, bottom_elems(bottom_max<T>(), 6) * sizeof(T));
     return e;
 }
 

@@ -96,6 +96,9 @@ cudaError_t run(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool ze
 }  // namespace
 }  // namespace mg
 
+// Largest grid this entry point accepts (both dtypes).
+constexpr int kStaticMax = 64;
+
 extern "C" mg_status mg_op_vcycle_static(int dtype, int n, int coarsest, void *x, const void *b,
                                          int nu1, int nu2, int zero_init, void *stream) {
     thread_local static char err[256];
@@ -103,14 +106,14 @@ extern "C" mg_status mg_op_vcycle_static(int dtype, int n, int coarsest, void *x
         mg::set_last_error(err);
         return st;
     };
-    if ((dtype != 0 && dtype != 1) || n < 4 || n > mg::kBottomMax || (n & (n - 1)) ||
+    if ((dtype != 0 && dtype != 1) || n < 4 || n > kStaticMax || (n & (n - 1)) ||
         coarsest < 4 || coarsest > mg::kStaticCoarsestMax || (coarsest & (coarsest - 1)) ||
         coarsest > n || !x || !b || nu1 < 0 || nu1 > 4 || nu2 < 0 || nu2 > 4) {
         snprintf(err, sizeof err,
                  "mg_op_vcycle_static: need n a power of two in [4, %d], coarsest a power of two in "
                  "[4, min(n, %d)] (static scratch of %d doubles), 0 <= nu <= 4, non-null x and b; "
                  "got n=%d coarsest=%d",
-                 mg::kBottomMax, mg::kStaticCoarsestMax, mg::kStaticPinvEntries, n, coarsest);
+                 kStaticMax, mg::kStaticCoarsestMax, mg::kStaticPinvEntries, n, coarsest);
         return fail(MG_ERR_INVALID_ARG);
     }
     void *pinv = nullptr;

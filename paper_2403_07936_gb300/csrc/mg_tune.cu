@@ -14,6 +14,7 @@
 // mg_autotune (CUDA-event timings of every variant on a context's own level
 // buffers), or from a cache file that earlier autotuning wrote.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -70,6 +71,28 @@ void set_tile_variant(int kind, int n, int nu, int variant) {
 }
 
 unsigned tune_epoch() { return g_epoch.load(); }
+
+namespace {
+std::atomic<int> g_overlap{-1};  // -1: not read from the environment yet
+}
+
+bool launch_overlap_enabled() {
+    int v = g_overlap.load(std::memory_order_relaxed);
+    if (v < 0) {
+        const char *env = getenv("MG_LAUNCH_OVERLAP");
+        v = (env && env[0] == '1') ? 1 : 0;
+        int expect = -1;
+        g_overlap.compare_exchange_strong(expect, v);
+        v = g_overlap.load();
+    }
+    return v != 0;
+}
+
+void set_launch_overlap(bool on) {
+    const bool old = launch_overlap_enabled();
+    g_overlap.store(on ? 1 : 0);
+    if (old != on) g_epoch.fetch_add(1);
+}
 
 namespace {
 

@@ -58,6 +58,8 @@ SIGNATURES = {
     "mg_destroy": (None, [_VP]),
     "mg_autotune": (_I, [_VP, C.c_char_p, C.POINTER(_I)]),
     "mg_get_tile_variant": (_I, [_I, _I, _I, C.POINTER(_I)]),
+    "mg_set_launch_overlap": (_I, [_I]),
+    "mg_get_launch_overlap": (_I, []),
     "mg_set_tile_variant": (_I, [_I, _I, _I, _I]),
     "mg_server_create": (_I, [_SZ, _I, _I, _I, _I, _D, _VP, C.POINTER(_VP)]),
     "mg_server_submit": (_I, [_VP, _I, _I, _VP, _VP, C.POINTER(C.c_longlong)]),
@@ -285,6 +287,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def set_launch_overlap(enable: bool):
+    """Programmatic dependent launch between library kernels (off by default)."""
+    _check(load().mg_set_launch_overlap(int(bool(enable))))
+
+
+def get_launch_overlap() -> bool:
+    return bool(load().mg_get_launch_overlap())
 
 
 def get_tile_variant(kind: int, n: int, nu: int) -> int:

@@ -106,7 +106,7 @@ def test_autotune_picks_a_variant_and_round_trips_the_cache(mg, restore_table, t
     with open(path, "w") as fp:  # an entry for another GPU model is ignored
         fp.write("Some_Other_GPU/10 1 1024 2 3 1.0\n")
     timed = ctx.autotune(path)
-    levels = [m for m in (1024, 512, 256, 128)]
+    levels = [1024, 512, 256, 128]  # tile levels (64^2 and below run in the one-block bottom kernel)
     assert timed == 2 * len(levels)
     chosen = {(k, m): mg.get_tile_variant(k, m, 2) for k in (0, 1) for m in levels}
     assert all(v in (0, 1) for (k, m), v in chosen.items() if k == 0)
@@ -122,3 +122,36 @@ def test_autotune_picks_a_variant_and_round_trips_the_cache(mg, restore_table, t
     x = torch.zeros_like(ft)
     assert ctx.solve(ft, x)["rel_residual"] <= 1e-10
     assert os.path.getsize(path) > 0
+
+
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
+def test_launch_overlap_gives_identical_results(mg, graphs):
+    """Programmatic dependent launch changes scheduling only: same bits on and off."""
+    n = 512
+    f = turbulent_source(n, default_kmax(n), config_seed(7, 3))
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(7, n)
+    ctx.set_graph_execution(graphs)
+    bsizes = [256, 128, 512]
+    bfs = [torch.tensor(turbulent_source(m, default_kmax(m), config_seed(7, 20 + i)), device=DEV)
+           for i, m in enumerate(bsizes)]
+    bctx = [mg.Context(int(np.log2(m // 8)) + 1, m) for m in bsizes]
+    was = mg.get_launch_overlap()
+    outs = []
+    try:
+        for on in (True, False, True):
+            mg.set_launch_overlap(on)
+            assert mg.get_launch_overlap() == on
+            x = torch.zeros_like(ft)
+            info = ctx.solve(ft, x)
+            xs = [torch.zeros_like(t) for t in bfs]
+            mg.solve_batched(bctx, bfs, xs)
+            outs.append((x, xs, info["vcycles"]))
+    finally:
+        mg.set_launch_overlap(was)
+    for x, xs, vc in outs[1:]:
+        assert torch.equal(x, outs[0][0]) and vc == outs[0][2]
+        for a, b in zip(xs, outs[0][1]):
+            assert torch.equal(a, b)
+    xe = omg.exact_solve_fft(f - f.mean())
+    assert np.abs(outs[0][0].cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
