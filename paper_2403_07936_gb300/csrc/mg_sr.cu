@@ -6,14 +6,15 @@
 // for an output tile of 128 pixels of one row, D[pixel][co] = sum over the 9
 // taps (dy, dx) and 64 input channels of In[row y+dy][pixel+dx][ci] *
 // W[tap][co][ci].  A persistent block walks a vertical strip of tiles: the
-// three input rows a tile needs are TMA-loaded into a ring of four row slots,
-// so each new output row costs one new input row.  A staged row is stored as
+// three input rows a tile needs are TMA-loaded into a ring of six row slots
+// (three rows of prefetch), so each new output row costs one new input row.  A staged row is stored as
 // eight 8-channel planes of [pixel][8 channels] (no swizzle), so the x-shifted
 // tap operands are descriptors offset by 16 * dx bytes into the staged row;
 // the weights use the 128-byte swizzled K-major layout.
 // Thread 0 issues the TMA loads and the 36 MMAs per tile; the tile's
-// accumulator (one of two 64-column TMEM buffers) is drained by all four warps
-// while the next tile's MMAs run.  Every wait on an mbarrier is bounded by a
+// accumulator (one of two 64-column TMEM buffers) is drained by all eight
+// warps (lane quarter x column half) while the next tile's MMAs run, and the
+// bf16 results leave through a shared-memory stage and TMA stores.  Every wait on an mbarrier is bounded by a
 // wall-clock limit and reports MG_ERR_TIMEOUT through a device flag.
 // The 1 -> 64 and 64 -> 1 layers are too thin for tensor cores (K = 9 and
 // N = 1) and run on the CUDA cores.
