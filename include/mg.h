@@ -216,6 +216,38 @@ int mg_get_launch_overlap(void);
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant);
 mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);
 
+/* ---------------------------------------------------------------------
+ * Training of the SR generator (Sec. 2.3 and Sec. 3.2: the generator learns
+ * the fine-grid error from the coarse-grid one).  The trainer holds FP32
+ * master weights, Adam moments (beta1 0.9, beta2 0.999, eps 1e-8) and the
+ * activations of one batch of `batch` periodic coarse fields of H x W (powers
+ * of two >= 8; batch * H * W a multiple of 2048, at most 2^24); every
+ * forward and backward convolution runs in the library's own FP32 kernels.
+ * Inputs are device arrays: q [batch][H][W] (the normalised coarse error
+ * e_c / s), target [batch][2H][2W] (the generator's target, e.g.
+ * (e_f - cubic(e_c)) / s), mask [batch][2H][2W] or NULL (per-pixel weights of
+ * the loss).  Loss = sum(mask * (y - target)^2) / (batch * 4 * H * W).
+ * Calls are synchronous on the default stream.
+ * ------------------------------------------------------------------- */
+typedef struct mg_trainer mg_trainer;
+
+/* blob: initial weights in the mg_load_prolong_weights layout; lr: Adam step size. */
+mg_status mg_trainer_create(int H, int W, int batch, const void *blob, size_t bytes, double lr,
+                            mg_trainer **out);
+/* y [batch][2H][2W] (device) = G(q) with the current weights. */
+mg_status mg_trainer_forward(mg_trainer *tr, const float *q, float *y);
+/* Loss (host double, may be NULL) and its gradient with respect to every
+ * parameter, written to grad (device, n_params floats in blob order). */
+mg_status mg_trainer_gradients(mg_trainer *tr, const float *q, const float *target, const float *mask,
+                               float *grad, double *loss);
+/* One Adam step on the batch; *loss (may be NULL) = the loss before the step. */
+mg_status mg_trainer_step(mg_trainer *tr, const float *q, const float *target, const float *mask,
+                          double *loss);
+mg_status mg_trainer_set_lr(mg_trainer *tr, double lr);
+/* Current weights as a blob (bytes = 64 + 4 * n_params). */
+mg_status mg_trainer_get_weights(mg_trainer *tr, void *blob, size_t bytes);
+void mg_trainer_destroy(mg_trainer *tr);
+
 void mg_destroy(mg_ctx *ctx);
 const char *mg_status_string(mg_status status);
 const char *mg_last_error(void);

@@ -66,6 +66,13 @@ SIGNATURES = {
     "mg_server_tick": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "mg_server_poll": (_I, [_VP, C.POINTER(ServerResult), C.POINTER(_I)]),
     "mg_server_destroy": (None, [_VP]),
+    "mg_trainer_create": (_I, [_I, _I, _I, _VP, _SZ, _D, C.POINTER(_VP)]),
+    "mg_trainer_forward": (_I, [_VP, _VP, _VP]),
+    "mg_trainer_gradients": (_I, [_VP, _VP, _VP, _VP, _VP, C.POINTER(_D)]),
+    "mg_trainer_step": (_I, [_VP, _VP, _VP, _VP, C.POINTER(_D)]),
+    "mg_trainer_set_lr": (_I, [_VP, _D]),
+    "mg_trainer_get_weights": (_I, [_VP, _VP, _SZ]),
+    "mg_trainer_destroy": (None, [_VP]),
     "mg_status_string": (C.c_char_p, [_I]),
     "mg_last_error": (C.c_char_p, []),
     "mg_kernel_launches": (C.c_ulonglong, []),
@@ -306,6 +313,48 @@ def get_tile_variant(kind: int, n: int, nu: int) -> int:
 
 def set_tile_variant(kind: int, n: int, nu: int, variant: int):
     _check(load().mg_set_tile_variant(kind, n, nu, variant))
+
+
+class Trainer:
+    """SR generator trainer (mg_trainer_* in include/mg.h); device float32 arrays."""
+
+    def __init__(self, H: int, W: int, batch: int, blob: bytes, lr: float = 1e-4):
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        h = C.c_void_p()
+        _check(load().mg_trainer_create(H, W, batch, C.cast(buf, C.c_void_p), len(blob), lr, C.byref(h)))
+        self._h, self.nbytes = h, len(blob)
+
+    def forward(self, q, y):
+        _check(load().mg_trainer_forward(self._h, ptr(q), ptr(y)))
+
+    def gradients(self, q, target, grad, mask=None) -> float:
+        loss = _D()
+        _check(load().mg_trainer_gradients(self._h, ptr(q), ptr(target), ptr(mask), ptr(grad), C.byref(loss)))
+        return loss.value
+
+    def step(self, q, target, mask=None) -> float:
+        loss = _D()
+        _check(load().mg_trainer_step(self._h, ptr(q), ptr(target), ptr(mask), C.byref(loss)))
+        return loss.value
+
+    def set_lr(self, lr: float):
+        _check(load().mg_trainer_set_lr(self._h, lr))
+
+    def weights(self) -> bytes:
+        buf = C.create_string_buffer(self.nbytes)
+        _check(load().mg_trainer_get_weights(self._h, C.cast(buf, C.c_void_p), self.nbytes))
+        return buf.raw
+
+    def close(self):
+        if self._h:
+            load().mg_trainer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launches() -> int:
