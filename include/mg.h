@@ -66,8 +66,10 @@ typedef struct {
     double removed_mean;  /* mean of f that was projected out */
     double update_norm;   /* ||x_k - x_{k-1}||_2 of the last update */
     double time_ms;       /* wall time of the call (host clock) */
-    int prolong_used;     /* mg_prolong actually applied */
-    int sr_fallback;      /* 1 if SR was replaced by cubic for this solve */
+    int prolong_used;     /* MG_PROLONG_SR if any V-cycle used SR, else MG_PROLONG_CUBIC */
+    int sr_fallback;      /* 1 if SR was dropped for the rest of this solve (an outer
+                             step using it did not halve the relative residual) */
+    int sr_cycles;        /* V-cycles whose top prolongation was SR */
 } mg_solve_info;
 
 /* Create a context for N x N grids with `levels` levels (Fig. 1a hierarchy).
@@ -92,6 +94,19 @@ mg_status mg_set_inner_cycles(mg_ctx *ctx, int inner_cycles);
  * inner_cycles.  0: a host loop with one residual read-back per outer step
  * (also used while a probe is active). */
 mg_status mg_set_graph_execution(mg_ctx *ctx, int enable);
+
+/* Prolongation policy of solves with MG_PROLONG_SR (the hybrid operator
+ * choice of Sec. 4.2 and Algorithm 6).  n_gan >= 1: n_gan V-cycles with SR
+ * per V-cycle with the cubic spline (n_gan = 1 alternates, INFINITY = SR
+ * only); n_gan < 1: 1/n_gan cubic V-cycles per SR V-cycle (>= 1e-6).  V-cycle i
+ * (1-based over the solve) uses the first operator (SR when n_gan >= 1, cubic
+ * otherwise) when i mod (N + 1) != 0, N = n_gan or 1/n_gan rounded, and the
+ * other one otherwise.  s_thres > 0: once the relative residual after an
+ * outer step is <= s_thres, every later V-cycle uses the second operator.
+ * Independently of the policy, an outer step that used SR and did not halve
+ * the relative residual turns SR off for the rest of the solve
+ * (mg_solve_info.sr_fallback).  Default: n_gan = INFINITY, s_thres = 0. */
+mg_status mg_set_prolong_policy(mg_ctx *ctx, double n_gan, double s_thres);
 
 /* Load super-resolution generator weights (Sec. 2.3, Fig. 1b).  The blob is
  * copied (the caller keeps ownership).  Blob layout: a 64-byte header

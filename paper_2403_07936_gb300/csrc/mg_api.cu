@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -121,6 +122,7 @@ struct SolveGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long n_pro = 0, n_body = 0, n_epi = 0;  // kernels per part
+    long long n_sr = 0;                         // kernels of one conditional SR correction
     unsigned long long stamp = 0;               // last use (LRU)
     unsigned epoch = 0;                         // tile-variant table at recording
 };
@@ -145,6 +147,8 @@ struct mg_ctx {
     SrState sr;
     // graph execution
     bool use_graphs = true;
+    ProlongPolicy policy = {1, 0, 0.0};  // SR on every V-cycle
+    int *d_srflag = nullptr;             // device: the current V-cycle uses SR
     cudaStream_t cap_stream = nullptr;  // private stream used only for recording graphs
     DevState *dstate = nullptr, *hstate = nullptr;
     SolveGraph graphs[kGraphCache];
@@ -327,6 +331,45 @@ static void drop_graphs(mg_ctx *c) {
 // Record the solve of A x = f for fixed buffers as one graph.  All launches go
 // to the private capture stream; on any failure the capture is ended and the
 // partial graph destroyed.
+// One FP32 V-cycle whose top prolongation the policy chooses, recorded into
+// the graph `body` that stream s is capturing: down, the coarse levels, the
+// policy kernel, an IF node holding the SR correction, up (which adds the
+// correction only when the policy chose SR).  Capture continues after the IF
+// node on return.  *n_sr = kernels inside the IF body.
+static mg_status record_policy_vcycle(mg_ctx *c, bool zero, int k, cudaGraph_t body, cudaGraphConditionalHandle h,
+                                      cudaStream_t s, long long *n_sr) {
+    const int n = c->lv[0].n;
+    float *x = c->lv[0].x32, *t = c->lv[0].t32, *b = c->lv[0].b32;
+    float *xc = c->lv[1].x32, *tc = c->lv[1].t32, *bc = c->lv[1].b32;
+    MG_CUDA(launch_down<float>(x, t, b, n, c->nu1, zero, bc, s));
+    MG_TRY(vcycle_rec<float>(c, 1, xc, tc, bc, true));
+    MG_CUDA(launch_policy(c->dstate, k, c->policy, c->d_srflag, h, s));
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    MG_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+    MG_CUDA(cudaStreamEndCapture(s, &body));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t ifn;
+    MG_CUDA(cudaGraphAddNode(&ifn, body, tail.data(), nullptr, tail.size(), &cp));
+    cudaGraph_t ifbody = cp.conditional.phGraph_out[0];
+    MG_CUDA(cudaStreamBeginCaptureToGraph(s, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = (long long)launches_total();
+    mg_status st = sr_correction(&c->sr, xc, c->lv[1].n, s, g_err, sizeof g_err);
+    *n_sr = (long long)launches_total() - l0;
+    cudaError_t e = cudaStreamEndCapture(s, &ifbody);
+    MG_TRY(st);
+    MG_CUDA(e);
+    MG_CUDA(cudaStreamBeginCaptureToGraph(s, body, &ifn, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    MG_CUDA(launch_up<float>(t, x, b, xc, n, c->nu2, c->taps, s, c->sr.fine_out, -1, c->d_srflag));
+    return MG_OK;
+}
+
 static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_prolong prolong,
                                     double tol, SolveGraph *out) {
     const bool mixed = c->prec == MG_PREC_MIXED;
@@ -340,7 +383,8 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
     cudaGraphConditionalHandle handle;
     bool capturing = false;
     mg_status st = MG_OK;
-    long long n_pro = 0, n_body = 0, n_epi = 0;
+    long long n_pro = 0, n_body = 0, n_epi = 0, n_sr = 0;
+    const bool use_policy = mixed && prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax;
     auto fail = [&](cudaError_t e, const char *what) {
         set_err("graph recording (%s) failed: %s", what, cudaGetErrorString(e));
         st = MG_ERR_CUDA;
@@ -389,7 +433,18 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
         e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { fail(e, "begin body"); break; }
         capturing = true;
-        if (mixed) {
+        if (use_policy) {
+            // one conditional handle per IF node (a handle serves a single node)
+            for (int k = 0; k < c->inner && st == MG_OK; ++k) {
+                cudaGraphConditionalHandle ih;
+                e = cudaGraphConditionalHandleCreate(&ih, body, 0, cudaGraphCondAssignDefault);
+                if (e != cudaSuccess) break;
+                st = record_policy_vcycle(c, k == 0, k, body, ih, s, &n_sr);
+            }
+            if (e != cudaSuccess) { fail(e, "if handle"); break; }
+            if (st != MG_OK) break;
+            e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
+        } else if (mixed) {
             for (int k = 0; k < c->inner && st == MG_OK; ++k) st = vcycle32_top(c, k == 0, prolong);
             if (st != MG_OK) break;
             e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
@@ -444,6 +499,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
     out->n_pro = n_pro;
     out->n_body = n_body;
     out->n_epi = n_epi;
+    out->n_sr = n_sr;
     return MG_OK;
 }
 
@@ -795,6 +851,7 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
             infos[r].time_ms = ms;
             infos[r].prolong_used = MG_PROLONG_CUBIC;
             infos[r].sr_fallback = 0;
+            infos[r].sr_cycles = 0;
         }
     }
     count_launches(p->n_pro + (long long)outer_max * p->n_body + p->n_epi);
@@ -1176,6 +1233,7 @@ static mg_status server_tick(mg_server *sv, int *n_active, int *n_queued, int *n
                 d.info.time_ms = t_fin - sl.t_submit;
                 d.info.prolong_used = MG_PROLONG_CUBIC;
                 d.info.sr_fallback = 0;
+                d.info.sr_cycles = 0;
                 sv->done.push_back(d);
                 sl.busy = false;
                 sl.req = -1;
@@ -1218,6 +1276,7 @@ void mg_destroy(mg_ctx *c) {
     cudaFree(c->h32_block);
     cudaFree(c->h64_block);
     cudaFree(c->ainv32);
+    cudaFree(c->d_srflag);
     cudaFree(c->ainv64);
     cudaFree(c->red_partials);
     cudaFree(c->red_counter);
@@ -1348,8 +1407,10 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     }
     const bool mixed = c->prec == MG_PREC_MIXED;
     MG_TRY(ensure_hierarchy(c, !mixed));
-    if (prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax)
+    if (prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax) {
         MG_TRY(sr_prepare(&c->sr, c->lv[1].n, g_err, sizeof g_err));
+        if (!c->d_srflag) MG_CUDA(cudaMalloc(&c->d_srflag, sizeof(int)));
+    }
     const double *fd;
     double *xd;
     bool staged;
@@ -1368,7 +1429,9 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
         const DevState &ds = *c->hstate;
-        count_launches(sg->n_pro + (long long)ds.outer * sg->n_body + sg->n_epi);
+        // the SR kernels of a conditional node run only for the V-cycles that used SR
+        count_launches(sg->n_pro + (long long)ds.outer * (sg->n_body - (long long)c->inner * sg->n_sr) +
+                       (long long)ds.sr_used * sg->n_sr + sg->n_epi);
         mg_status gst = (mg_status)ds.status;
         if (gst == MG_ERR_NONFINITE) set_err("non-finite residual (NaN or Inf in f or x)");
         if (gst == MG_ERR_NOT_CONVERGED)
@@ -1379,8 +1442,10 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
             info->rel_residual = ds.rel;
             info->removed_mean = ds.mu;
             info->update_norm = ds.unorm;
-            info->prolong_used = (int)prolong;
-            info->sr_fallback = 0;
+            const bool policy = sg->n_sr > 0;
+            info->sr_cycles = policy ? ds.sr_used : (prolong == MG_PROLONG_SR ? ds.cycles : 0);
+            info->prolong_used = info->sr_cycles > 0 ? MG_PROLONG_SR : MG_PROLONG_CUBIC;
+            info->sr_fallback = policy ? ds.fallback : 0;
             info->time_ms =
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
@@ -1394,6 +1459,11 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     int cycles = 0, outer = 0;
     double fnorm = 0.0, rel = INFINITY, mu = 0.0;
     bool first = true;
+    // the prolongation policy, decided on the host with the same rule as k_policy
+    const bool use_policy = mixed && prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax;
+    int sr_used = 0;
+    bool sr_step = false, fallback = false;
+    double rel_prev = 0.0;
     for (;;) {
         probe_begin(c, kProbeResidual);
         MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
@@ -1419,6 +1489,9 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
             break;
         }
         rel = rnorm / fnorm;
+        if (outer > 0 && sr_step && !(rel <= kSrMinReduction * rel_prev)) fallback = true;
+        sr_step = false;
+        rel_prev = rel;
         if (rel <= tol) break;
         if (cycles >= c->max_cycles) {
             set_err("not converged: rel residual %.3e after %d V-cycles", rel, cycles);
@@ -1426,8 +1499,20 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
             break;
         }
         if (mixed) {
-            for (int k = 0; k < c->inner && cycles < c->max_cycles; ++k, ++cycles)
-                MG_TRY(vcycle32_top(c, k == 0, prolong));
+            for (int k = 0; k < c->inner && cycles < c->max_cycles; ++k, ++cycles) {
+                mg_prolong pk = prolong;
+                if (use_policy) {
+                    const bool sr = policy_use_sr(c->policy, cycles + 1, rel, true, fallback);
+                    pk = sr ? MG_PROLONG_SR : MG_PROLONG_CUBIC;
+                    if (sr) {
+                        ++sr_used;
+                        sr_step = true;
+                    }
+                } else if (prolong == MG_PROLONG_SR) {
+                    ++sr_used;
+                }
+                MG_TRY(vcycle32_top(c, k == 0, pk));
+            }
             probe_begin(c, kProbeUpdate);
             MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
             probe_end(c, kProbeUpdate, N2 * 20.0);
@@ -1451,8 +1536,9 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         info->rel_residual = rel;
         info->removed_mean = mu;
         info->update_norm = mixed && outer > 0 ? sqrt(c->host_out[kGrpU * kMaxSlots]) : 0.0;
-        info->prolong_used = (int)prolong;
-        info->sr_fallback = 0;
+        info->sr_cycles = sr_used;
+        info->prolong_used = sr_used > 0 ? MG_PROLONG_SR : MG_PROLONG_CUBIC;
+        info->sr_fallback = fallback ? 1 : 0;
         info->time_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
@@ -1505,6 +1591,25 @@ mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *
 }
 
 unsigned long long mg_kernel_launches(void) { return launches_total(); }
+
+mg_status mg_set_prolong_policy(mg_ctx *c, double n_gan, double s_thres) {
+    if (!c || !(n_gan > 0.0) || !(s_thres >= 0.0) || (std::isfinite(n_gan) && n_gan < 1.0 && n_gan * 1e6 < 1.0)) {
+        set_err("n_gan must be > 0 (INFINITY: SR only) and >= 1e-6, s_thres >= 0");
+        return MG_ERR_INVALID_ARG;
+    }
+    ProlongPolicy p;
+    if (!std::isfinite(n_gan)) {
+        p = ProlongPolicy{1, 0, s_thres};
+    } else if (n_gan >= 1.0) {
+        p = ProlongPolicy{1, (int)std::lround(n_gan), s_thres};
+    } else {
+        p = ProlongPolicy{0, (int)std::lround(1.0 / n_gan), s_thres};
+    }
+    if (p.first_sr != c->policy.first_sr || p.period != c->policy.period || p.s_thres != c->policy.s_thres)
+        drop_graphs(c);
+    c->policy = p;
+    return MG_OK;
+}
 
 mg_status mg_set_graph_execution(mg_ctx *c, int enable) {
     if (!c) {

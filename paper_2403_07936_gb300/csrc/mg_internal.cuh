@@ -217,9 +217,11 @@ cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zer
                         cudaStream_t s, int variant = -1);
 // xout = nu sweeps of (x + P ec + extra); extra is a fine-grid additive
 // correction or null.  x != xout.
+// extra_flag (device, may be null): extra is added only when *extra_flag != 0.
 template <typename T>
 cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
-                      const FirTaps &taps, cudaStream_t s, const T *extra = nullptr, int variant = -1);
+                      const FirTaps &taps, cudaStream_t s, const T *extra = nullptr, int variant = -1,
+                      const int *extra_flag = nullptr);
 template <typename T>
 cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool zero_init,
                           const T *ainv, const FirTaps &taps, cudaStream_t s);
@@ -254,7 +256,40 @@ struct DevState {
     double rel;       // last relative residual
     double unorm;     // ||e||_2 of the last update
     double mu;        // mean of f
+    int sr_used;      // V-cycles that used the SR prolongation
+    int sr_step;      // the current outer step used it
+    int fallback;     // SR stopped for this solve (an outer step with SR did not halve the residual)
+    int pad;
+    double rel_prev;  // relative residual before the current outer step
 };
+
+// Prolongation policy of a solve with the SR prolongation (the hybrid
+// operator choice of Sec. 4.2 and Algorithm 6).  n_gan >= 1: n_gan SR cycles
+// per cubic cycle (first = SR); n_gan < 1: 1/n_gan cubic cycles per SR cycle
+// (first = cubic); period = 0 means the first operator only.  Once the
+// relative residual of the latest outer step is <= s_thres (> 0), the second
+// operator is used from then on.  V-cycle i (1-based, counted over the solve)
+// uses the first operator when i mod (period + 1) != 0.
+struct ProlongPolicy {
+    int first_sr;   // first operator is SR (1) or cubic (0)
+    int period;     // consecutive first-operator cycles, 0 = no second operator by count
+    double s_thres;
+};
+__host__ __device__ inline bool policy_use_sr(const ProlongPolicy &p, int i, double rel, bool have_rel,
+                                              bool fallback) {
+    if (fallback) return false;
+    const bool switched = p.s_thres > 0.0 && have_rel && rel <= p.s_thres;
+    const bool first = !switched && (p.period == 0 || i % (p.period + 1) != 0);
+    return first ? p.first_sr != 0 : p.first_sr == 0;
+}
+// An outer step that used SR must reduce the relative residual by at least
+// this factor, else SR is dropped for the rest of the solve.
+constexpr double kSrMinReduction = 0.5;
+
+// Decide V-cycle (st->cycles + k + 1) of the running solve on the device:
+// *flag = use SR, the IF node's condition likewise, st->sr_used / sr_step.
+cudaError_t launch_policy(DevState *st, int k, ProlongPolicy p, int *flag, cudaGraphConditionalHandle handle,
+                          cudaStream_t s);
 
 // Convergence test of one outer step: reads the residual sums, updates the
 // state and sets the graph's loop condition (1 = run another step).

@@ -423,12 +423,15 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
     store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
 }
 
+// extra_flag (may be null): the additive term is used only where *extra_flag != 0.
 template <typename T, int NU, int TY, int NJ>
 __global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__restrict__ xout,
                                                  const T *__restrict__ b, const T *__restrict__ ec,
-                                                 const T *__restrict__ extra, int n, FirTaps taps) {
+                                                 const T *__restrict__ extra, const int *__restrict__ extra_flag,
+                                                 int n, FirTaps taps) {
     pdl_enter();
-    up_tile<T, NU, TY, NJ>(x, xout, b, ec, extra, n, taps, blockIdx.y * TY, blockIdx.x * kTX);
+    const T *ex = (extra && (!extra_flag || *extra_flag)) ? extra : nullptr;
+    up_tile<T, NU, TY, NJ>(x, xout, b, ec, ex, n, taps, blockIdx.y * TY, blockIdx.x * kTX);
 }
 
 template <typename T, int NU, int TY, int NJ>
@@ -763,6 +766,9 @@ __global__ void k_check(DevState *st, const double *rsum, const double *usum, co
         st->status = MG_OK;
         st->zero_source = 0;
         st->unorm = 0.0;
+        st->sr_used = 0;
+        st->sr_step = 0;
+        st->fallback = 0;
     } else {
         st->cycles += step;
         st->outer += 1;
@@ -778,6 +784,9 @@ __global__ void k_check(DevState *st, const double *rsum, const double *usum, co
         st->rel = 0.0;
     } else {
         const double rel = rn / fn;
+        if (!first && st->sr_step && !(rel <= kSrMinReduction * st->rel_prev)) st->fallback = 1;
+        st->sr_step = 0;
+        st->rel_prev = rel;
         st->rel = rel;
         if (rel > tol) {
             if (st->cycles + step <= max_cycles)
@@ -787,6 +796,18 @@ __global__ void k_check(DevState *st, const double *rsum, const double *usum, co
         }
     }
     cudaGraphSetConditional(handle, go);
+}
+
+__global__ void k_policy(DevState *st, int k, ProlongPolicy p, int *flag, cudaGraphConditionalHandle handle) {
+    pdl_enter();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool use = policy_use_sr(p, st->cycles + k + 1, st->rel, true, st->fallback != 0);
+    *flag = use ? 1 : 0;
+    if (use) {
+        st->sr_used += 1;
+        st->sr_step = 1;
+    }
+    cudaGraphSetConditional(handle, use ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -938,6 +959,10 @@ __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs
             s.status = MG_OK;
             s.zero_source = 0;
             s.unorm = 0.0;
+            s.sr_used = 0;
+            s.sr_step = 0;
+            s.fallback = 0;
+            s.rel_prev = 0.0;
         } else {
             s.cycles += step;
             s.outer += 1;
@@ -1004,7 +1029,7 @@ cudaError_t down_impl(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_
 }
 
 template <typename T, int NU, int TY, int NJ>
-cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra, int n,
+cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra, const int *eflag, int n,
                     const FirTaps &taps, cudaStream_t s) {
     using Cfg = UpCfg<T, NU, TY, NJ>;
     auto k = k_up<T, NU, TY, NJ>;
@@ -1014,7 +1039,7 @@ cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra
     dim3 grid(n / Cfg::TX, n / Cfg::TY);
     {
         cudaError_t le_ = launch_kernel(k, grid, kThreads, Cfg::smem, s,
-                                        x, xout, b, ec, extra, n, taps);
+                                        x, xout, b, ec, extra, eflag, n, taps);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);
@@ -1032,16 +1057,16 @@ cudaError_t down_var(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_t
 }
 
 template <typename T, int NU>
-cudaError_t up_var(const T *x, T *xout, const T *b, const T *ec, const T *extra, int n, const FirTaps &taps,
-                   cudaStream_t s, int variant) {
+cudaError_t up_var(const T *x, T *xout, const T *b, const T *ec, const T *extra, const int *eflag, int n,
+                   const FirTaps &taps, cudaStream_t s, int variant) {
     if constexpr (std::is_same<T, double>::value) {
-        return up_impl<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>(x, xout, b, ec, extra, n, taps, s);
+        return up_impl<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>(x, xout, b, ec, extra, eflag, n, taps, s);
     } else {
         const bool r32 = variant_rows(variant) == 32, nj2 = variant_runs(variant) == 2;
-        if (r32) return nj2 ? up_impl<T, NU, 32, 2>(x, xout, b, ec, extra, n, taps, s)
-                            : up_impl<T, NU, 32, 1>(x, xout, b, ec, extra, n, taps, s);
-        return nj2 ? up_impl<T, NU, 64, 2>(x, xout, b, ec, extra, n, taps, s)
-                   : up_impl<T, NU, 64, 1>(x, xout, b, ec, extra, n, taps, s);
+        if (r32) return nj2 ? up_impl<T, NU, 32, 2>(x, xout, b, ec, extra, eflag, n, taps, s)
+                            : up_impl<T, NU, 32, 1>(x, xout, b, ec, extra, eflag, n, taps, s);
+        return nj2 ? up_impl<T, NU, 64, 2>(x, xout, b, ec, extra, eflag, n, taps, s)
+                   : up_impl<T, NU, 64, 1>(x, xout, b, ec, extra, eflag, n, taps, s);
     }
 }
 
@@ -1069,15 +1094,15 @@ cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zer
 
 template <typename T>
 cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
-                      const FirTaps &taps, cudaStream_t s, const T *extra, int variant) {
+                      const FirTaps &taps, cudaStream_t s, const T *extra, int variant, const int *extra_flag) {
     if (n < 64 || !ec || x == xout || variant < -1 || variant >= kTileVariants) return cudaErrorInvalidValue;
     if (variant < 0) variant = tile_variant(1, n, nu);
     switch (nu) {
-        case 0: return up_var<T, 0>(x, xout, b, ec, extra, n, taps, s, variant);
-        case 1: return up_var<T, 1>(x, xout, b, ec, extra, n, taps, s, variant);
-        case 2: return up_var<T, 2>(x, xout, b, ec, extra, n, taps, s, variant);
-        case 3: return up_var<T, 3>(x, xout, b, ec, extra, n, taps, s, variant);
-        case 4: return up_var<T, 4>(x, xout, b, ec, extra, n, taps, s, variant);
+        case 0: return up_var<T, 0>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
+        case 1: return up_var<T, 1>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
+        case 2: return up_var<T, 2>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
+        case 3: return up_var<T, 3>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
+        case 4: return up_var<T, 4>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1108,9 +1133,9 @@ template cudaError_t launch_down<float>(const float *, float *, const float *, i
 template cudaError_t launch_down<double>(const double *, double *, const double *, int, int, bool,
                                          double *, cudaStream_t, int);
 template cudaError_t launch_up<float>(const float *, float *, const float *, const float *, int, int,
-                                      const FirTaps &, cudaStream_t, const float *, int);
+                                      const FirTaps &, cudaStream_t, const float *, int, const int *);
 template cudaError_t launch_up<double>(const double *, double *, const double *, const double *, int,
-                                       int, const FirTaps &, cudaStream_t, const double *, int);
+                                       int, const FirTaps &, cudaStream_t, const double *, int, const int *);
 template cudaError_t launch_bottom<float>(float *, const float *, int, int, int, int, bool, const float *,
                                           const FirTaps &, cudaStream_t);
 template cudaError_t launch_bottom<double>(double *, const double *, int, int, int, int, bool,
@@ -1350,6 +1375,16 @@ cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, con
     {
         cudaError_t le_ = launch_kernel(k_project_b, nblocks, kRedThreads, 0, s,
                                         rd, nrhs, xsum, st);
+        if (le_ != cudaSuccess) return le_;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_policy(DevState *st, int k, ProlongPolicy p, int *flag, cudaGraphConditionalHandle handle,
+                          cudaStream_t s) {
+    {
+        cudaError_t le_ = launch_kernel(k_policy, 1, 32, 0, s, st, k, p, flag, handle);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);

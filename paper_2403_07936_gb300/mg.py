@@ -28,7 +28,7 @@ _VP, _I, _D, _SZ = C.c_void_p, C.c_int, C.c_double, C.c_size_t
 class SolveInfo(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("vcycles", C.c_int), ("rel_residual", C.c_double),
                 ("removed_mean", C.c_double), ("update_norm", C.c_double), ("time_ms", C.c_double),
-                ("prolong_used", C.c_int), ("sr_fallback", C.c_int)]
+                ("prolong_used", C.c_int), ("sr_fallback", C.c_int), ("sr_cycles", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -50,6 +50,7 @@ SIGNATURES = {
     "mg_set_options": (_I, [_VP, _I, _I, _I, _I, _VP]),
     "mg_set_inner_cycles": (_I, [_VP, _I]),
     "mg_set_graph_execution": (_I, [_VP, _I]),
+    "mg_set_prolong_policy": (_I, [_VP, _D, _D]),
     "mg_load_prolong_weights": (_I, [_VP, _VP, _SZ]),
     "mg_solve": (_I, [_VP, _VP, _VP, _D, _I, C.POINTER(SolveInfo)]),
     "mg_vcycle": (_I, [_VP, _VP, _VP, _I]),
@@ -199,6 +200,10 @@ class Context:
         if inner_cycles is not None:
             o.inner_cycles = inner_cycles
             _check(lib.mg_set_inner_cycles(self._h, inner_cycles))
+
+    def set_prolong_policy(self, n_gan: float = float("inf"), s_thres: float = 0.0):
+        """Hybrid SR / cubic choice per V-cycle for prolong="sr" solves (mg_set_prolong_policy)."""
+        _check(load().mg_set_prolong_policy(self._h, n_gan, s_thres))
 
     def set_graph_execution(self, enable: bool):
         """Run mg_solve as one CUDA graph launch (True, default) or a host loop."""

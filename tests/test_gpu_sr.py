@@ -160,3 +160,76 @@ def test_sr_requires_weights_and_large_enough_grid(mg):
     with pytest.raises(mg.MGError) as e:
         ctx.solve(ft, torch.zeros_like(ft), prolong="sr")
     assert e.value.status == 6  # MG_ERR_NO_WEIGHTS
+
+
+TRAINED = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.dirname(
+    __import__("os").path.abspath(__file__))), "paper_2403_07936_gb300", "weights", "sr_generator.mgsrw")
+
+
+def _trained_blob(out_scale=1.0):
+    from paper_2403_07936_gb300 import sr
+    blob = open(TRAINED, "rb").read()
+    if out_scale == 1.0:
+        return blob
+    w = sr.unpack_weights(blob)
+    w["out.w"] = w["out.w"] * out_scale
+    w["out.b"] = w["out.b"] * out_scale
+    return sr.pack_weights(w)
+
+
+def _policy_solve(mg, n, blob, graphs, n_gan=float("inf"), s_thres=0.0, prolong="sr", seed=21):
+    f = turbulent_source(n, n // 8, seed)
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(int(np.log2(n // 8)) + 1, n)
+    ctx.set_graph_execution(graphs)
+    ctx.load_weights(blob)
+    ctx.set_prolong_policy(n_gan, s_thres)
+    x = torch.zeros_like(ft)
+    info = ctx.solve(ft, x, prolong=prolong)
+    return f, x, info
+
+
+def _assert_exact(f, x):
+    xe = omg.exact_solve_fft(f - f.mean())
+    assert np.abs(x.cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
+
+
+def test_trained_generator_needs_fewer_vcycles_than_cubic(mg):
+    blob = _trained_blob()
+    f, xc, ic = _policy_solve(mg, 512, blob, True, prolong="cubic")
+    f, xs, isr = _policy_solve(mg, 512, blob, True)
+    assert isr["sr_cycles"] == isr["vcycles"] and isr["sr_fallback"] == 0
+    assert isr["vcycles"] < ic["vcycles"], (isr["vcycles"], ic["vcycles"])
+    _assert_exact(f, xs)
+
+
+@pytest.mark.parametrize("n_gan,s_thres", [(1.0, 0.0), (0.5, 0.0), (float("inf"), 1e-5), (1e-6, 0.0)],
+                         ids=["alternate", "two-cubic-per-sr", "switch-at-1e-5", "cubic-only"])
+def test_prolongation_policies(mg, n_gan, s_thres):
+    blob = _trained_blob()
+    f, xg, ig = _policy_solve(mg, 512, blob, True, n_gan, s_thres)
+    _, xh, ih = _policy_solve(mg, 512, blob, False, n_gan, s_thres)
+    assert torch.equal(xg, xh) and ig["vcycles"] == ih["vcycles"] and ig["sr_cycles"] == ih["sr_cycles"]
+    assert ig["rel_residual"] <= 1e-10 and ig["sr_fallback"] == 0
+    _assert_exact(f, xg)
+    vc, nsr = ig["vcycles"], ig["sr_cycles"]
+    if n_gan == 1.0:
+        assert nsr == (vc + 1) // 2  # odd V-cycles use SR
+    elif n_gan == 0.5:
+        assert nsr == vc // 3  # every third V-cycle uses SR
+    elif n_gan == 1e-6:
+        _, xc, ic = _policy_solve(mg, 512, blob, True, prolong="cubic")
+        assert nsr == 0 and ig["prolong_used"] == 0 and torch.equal(xg, xc)
+    else:
+        assert 0 < nsr < vc
+
+
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
+def test_diverging_generator_falls_back_to_cubic(mg, graphs):
+    """Weights scaled x100 make the SR correction useless: the first outer step
+    does not halve the residual, SR is dropped and the solve still converges."""
+    f, x, info = _policy_solve(mg, 512, _trained_blob(out_scale=100.0), graphs)
+    assert info["sr_fallback"] == 1 and info["status"] == "MG_OK"
+    assert info["sr_cycles"] == 2  # the first outer step's inner V-cycles
+    assert info["rel_residual"] <= 1e-10
+    _assert_exact(f, x)
