@@ -264,17 +264,26 @@ def batched_leg(mg, dev, stream, flush, args, rank):
             "l2": "flushed between steps (512 MB write); working set 2.2 GB > L2"}
 
 
+SR_WEIGHTS = os.path.join(ROOT, "paper_2403_07936_gb300", "weights", "sr_generator.mgsrw")
+
+
 def sr_leg(mg, dev, stream, flush, f_dev, x, args):
+    """SR prolongation (C3): generator throughput, and whole solves at 2048^2
+    and 1024^2 with cubic, SR on every V-cycle, and SR alternated with cubic
+    (N_GAN = 1), using the generator trained by train_sr.py."""
     import torch
     from paper_2403_07936_gb300 import sr
-    from synthetic.sources import turbulent_source
+    from synthetic.sources import config_seed, turbulent_source
     from synthetic.weights import random_weights
-    w = random_weights(11, gain=0.5)
-    w["out.w"] = w["out.w"] * 0.1
-    w["out.b"] = w["out.b"] * 0.1
+    if os.path.exists(SR_WEIGHTS):
+        blob, wdesc = open(SR_WEIGHTS, "rb").read(), "trained (weights/sr_generator.mgsrw)"
+    else:
+        w = random_weights(11, gain=0.5)
+        w["out.w"] = w["out.w"] * 0.1
+        blob, wdesc = sr.pack_weights(w), "seeded random (trained weights not found)"
     ctx = mg.Context(LEVELS, N)
     ctx.set_options(stream=stream)
-    ctx.load_weights(sr.pack_weights(w))
+    ctx.load_weights(blob)
     nc = N // 2
     ec = torch.tensor(turbulent_source(nc, nc // 8, 4242) * 1e-3, dtype=torch.float32, device=dev)
     out = torch.empty((N, N), dtype=torch.float32, device=dev)
@@ -283,34 +292,50 @@ def sr_leg(mg, dev, stream, flush, f_dev, x, args):
     t_gen = _events_time(stream, lambda: mg.op_sr_generator(ctx, ec, out), max(3, args.steps // 2))
     tflop = SR_TENSOR_FLOP_PER_COARSE_PX * nc * nc / 1e12
     peak_tf = read_bf16_peak()
-    # whole solves with the SR prolongation at the finest transition
-    for _ in range(2):
-        x.zero_()
-        ctx.solve(f_dev[0], x, prolong="sr")
-    times, infos = [], []
-    for _ in range(max(3, args.steps // 2)):
-        x.zero_()
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        infos.append(ctx.solve(f_dev[0], x, prolong="sr"))
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        times.append(e0.elapsed_time(e1) / 1e3)
-    ts = sum(times) / len(times)
-    return {"workload": "2048^2, SR prolongation at the finest transition (generator on the 1024^2 coarse "
-                        "error: conv 1->64, 8 residual blocks, conv 64->256 + pixel shuffle, conv 64->1; "
-                        "bf16 operands, fp32 accumulate); seeded random weights (not trained)",
-            "generator_ms": t_gen * 1e3,
+    reps = max(3, args.steps // 4)
+    solves = {}
+    for n in (N, N // 2):
+        c = ctx if n == N else mg.Context(LEVELS - 1, n)
+        if n != N:
+            c.set_options(stream=stream)
+            c.load_weights(blob)
+        f = torch.tensor(turbulent_source(n, n // 8, config_seed(3, 900)), device=dev)
+        xx = torch.zeros_like(f)
+        res = {}
+        for name, prolong, n_gan in (("cubic", "cubic", float("inf")), ("sr", "sr", float("inf")),
+                                     ("alternate", "sr", 1.0)):
+            c.set_prolong_policy(n_gan, 0.0)
+            for _ in range(2):
+                xx.zero_()
+                c.solve(f, xx, prolong=prolong)
+            times, info = [], None
+            for _ in range(reps):
+                xx.zero_()
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = c.solve(f, xx, prolong=prolong)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                times.append(e0.elapsed_time(e1) / 1e3)
+            t = sum(times) / len(times)
+            res[name] = {"solves_per_s": 1.0 / t, "ms_per_solve": t * 1e3, "vcycles": info["vcycles"],
+                         "sr_vcycles": info["sr_cycles"], "outer_iters": info["outer_iters"],
+                         "rel_residual": info["rel_residual"], "sr_fallback": info["sr_fallback"]}
+        c.set_prolong_policy(float("inf"), 0.0)
+        solves[f"{n}^2"] = res
+    return {"workload": "SR prolongation at the finest transition of the 2048^2 and 1024^2 mixed solves "
+                        "(generator on the coarse error: conv 1->64, 8 residual blocks, conv 64->256 + pixel "
+                        "shuffle, conv 64->1; bf16 operands, fp32 accumulate); weights: " + wdesc +
+                        "; policies: cubic only, SR every V-cycle, SR alternated with cubic (N_GAN = 1)",
+            "generator_ms_2048": t_gen * 1e3,
             "tensor_roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05 implicit GEMM)",
                                 "achieved": tflop / t_gen, "peak": peak_tf[0], "unit": "TFLOP/s",
                                 "frac": tflop / t_gen / peak_tf[0], "peak_source": peak_tf[1],
                                 "note": "achieved counts the tensor-core FLOPs of the whole generator call "
                                         "(which also includes the CUDA-core first/last layers and s = max|e|)"},
-            "solve": {"value": 1.0 / ts, "unit": "solves/s", "ms_per_step": ts * 1e3,
-                      "vcycles": infos[-1]["vcycles"], "outer_iters": infos[-1]["outer_iters"],
-                      "rel_residual": infos[-1]["rel_residual"]}}
+            "solves": solves}
 
 
 SERVE_SIZES = (128, 256, 512, 1024, 2048)
