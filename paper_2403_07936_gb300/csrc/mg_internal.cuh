@@ -187,7 +187,9 @@ struct BatchRed {
 
 // ----------------------------------------------------------------------------
 // FP32 tile-kernel variants: bit 0 set = 32 rows per tile (else 64), bit 1
-// set = 2 spline midpoints per prolongation work item (else 1).  Tiles are 64
+// set = the prolongation's spline passes on float2 pairs with packed FP32x2
+// instructions (two rows / two columns per work item; else one midpoint per
+// work item in scalar arithmetic).  Tiles are 64
 // columns wide.  All variants give bit-identical results; the process-wide
 // table below (mg_tune.cu) holds the one to use for each (kernel kind: 0 down
 // / 1 up, grid size, sweep count), from built-in defaults or mg_autotune.

@@ -24,6 +24,7 @@
 // solution update, zero-mean projection.  Sums are deterministic (fixed grid,
 // fixed-order trees, last-block finish).
 #include <math.h>
+#include <string.h>
 
 #include <atomic>
 #include <type_traits>
@@ -63,6 +64,29 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Packed FP32x2 arithmetic (Blackwell): two IEEE round-to-nearest float
+// operations per instruction, lane by lane the same bits as the scalar ones.
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+    unsigned long long u;
+    memcpy(&u, &v, sizeof u);
+    return u;
+}
+__device__ __forceinline__ float2 f2_from(unsigned long long u) {
+    float2 v;
+    memcpy(&v, &u, sizeof v);
+    return v;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_from(r);
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+    return f2_from(r);
+}
+
 // Launch k with the programmatic-stream-serialization attribute when
 // launch overlap is enabled (launch_overlap_enabled()), else as a plain launch.
 template <typename... KArgs, typename... Args>
@@ -87,10 +111,12 @@ __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / 
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 // Output tiles are TY x 64 points.  FP32 kernels come in variants (see
-// variant_rows / variant_runs): 64 or 32 rows per tile, and NJ = 1 or 2
-// spline midpoints per work item of the prolongation.  Every variant computes
-// the same values in the same order, so the choice only changes speed.  FP64
-// tiles are 32 x 64 with NJ = 1, to keep the staged tiles within shared memory.
+// variant_rows / variant_runs): 64 or 32 rows per tile, and NJ = 1 (scalar
+// spline passes, one midpoint per work item) or NJ = 2 (the spline passes on
+// float2 pairs of rows / columns with packed FP32x2 instructions).  Every
+// variant computes the same values in the same order, so the choice only
+// changes speed.  FP64 tiles are 32 x 64 with NJ = 1, to keep the staged tiles
+// within shared memory.
 constexpr int kTX = 64;
 template <typename T> struct Fixed64;  // the FP64 shape
 template <> struct Fixed64<double> {
@@ -159,6 +185,39 @@ __device__ __forceinline__ void load_split(T *red, T *black, const T *__restrict
         scatter_vec(red, black, rr, cv * VW, C / 2, v);
     }
 }
+
+// Two-phase tile loader: issue() starts every 16-byte load of the tile into
+// registers (a thread's share, all independent, so their latencies overlap),
+// scatter() writes them into the colour-split arrays.  Between the two a
+// block can do other work with the loads in flight.
+template <typename T, int R, int C>
+struct SplitLoad {
+    using V = typename Prec<T>::vec;
+    static constexpr int VW = Prec<T>::VW, CV = C / VW, ITEMS = R * CV;
+    static constexpr int PER = (ITEMS + kThreads - 1) / kThreads;
+    V v[PER];
+    __device__ __forceinline__ void issue(const T *__restrict__ g, int n, int r0, int c0) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            if (idx < ITEMS) {
+                const int rr = idx / CV, cv = idx - rr * CV;
+                const int gr = (r0 + rr) & (n - 1), gc = (c0 + cv * VW) & (n - 1);
+                v[i] = __ldg(reinterpret_cast<const V *>(g + (size_t)gr * n + gc));
+            }
+        }
+    }
+    __device__ __forceinline__ void scatter(T *red, T *black) const {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            if (idx < ITEMS) {
+                const int rr = idx / CV, cv = idx - rr * CV;
+                scatter_vec(red, black, rr, cv * VW, C / 2, v[i]);
+            }
+        }
+    }
+};
 
 // Store staged rows [r_s, r_s+TY) x cols [c_s, c_s+TX) of a split tile to
 // global rows [gy, gy+TY) x cols [gx, gx+TX).
@@ -243,11 +302,16 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
     T *X = reinterpret_cast<T *>(smem_raw);  // red at X, black at X + A
     T *B = X + 2 * A;                           // red at B, black at B + A
 
-    load_split<T, R, C>(B, B + A, b, n, ty0 - H, tx0 - HX);
-    if (zero) {
-        for (int i = threadIdx.x; i < 2 * A; i += blockDim.x) X[i] = T(0);
-    } else {
-        load_split<T, R, C>(X, X + A, x, n, ty0 - H, tx0 - HX);
+    {
+        SplitLoad<T, R, C> lb, lx;
+        lb.issue(b, n, ty0 - H, tx0 - HX);
+        if (!zero) lx.issue(x, n, ty0 - H, tx0 - HX);
+        lb.scatter(B, B + A);
+        if (zero) {
+            for (int i = threadIdx.x; i < 2 * A; i += blockDim.x) X[i] = T(0);
+        } else {
+            lx.scatter(X, X + A);
+        }
     }
     __syncthreads();
 #pragma unroll 1
@@ -340,7 +404,8 @@ struct UpCfg {
     static constexpr int CXE = round_up(H / 2 + L, VW);
     static constexpr int CC = TX / 2 + CHX + CXE;
     static constexpr int FW = TX + 2 * H;  // fine columns refined, v in [-H, TX + H)
-    static constexpr int U = cmax(2 * A, CR * CC);  // coarse tile, then b (after the row pass)
+    static constexpr int CRP = (CR + 1) / 2;            // row pairs of the packed coarse tile
+    static constexpr int U = cmax(2 * A, 2 * CRP * CC);  // coarse tile, then b (after the row pass)
     static constexpr size_t smem = (2ull * A + U + (size_t)CR * FW) * sizeof(T);
     static_assert(JW % NJ == 0 && IW % NJ == 0, "runs must tile the refined range");
 };
@@ -361,6 +426,99 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
     T *rs = X + 2 * A + Cfg::U;                 // x-refined coarse rows [CR][FW]
     const int nc = n >> 1;
 
+    if constexpr (std::is_same<T, float>::value && NJ == 2) {
+        // Packed variant: both spline passes on float2 pairs with f32x2
+        // instructions.  Row pass: the coarse tile is stored as row pairs,
+        // cs2[rp][col] = (row 2rp, row 2rp + 1), so one 64-bit load feeds two
+        // rows' midpoints; column pass: two adjacent fine columns of rs.
+        constexpr int CRP = Cfg::CRP;
+        float2 *cs2 = reinterpret_cast<float2 *>(cs);
+        constexpr int CV = CC / 4, CITEMS = CRP * CV, CPER = (CITEMS + kThreads - 1) / kThreads;
+        SplitLoad<T, R, C> lx;
+        lx.issue(x, n, ty0 - H, tx0 - HX);
+        float4 c0v[CPER], c1v[CPER];
+#pragma unroll
+        for (int i = 0; i < CPER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            if (idx < CITEMS) {
+                const int rp = idx / CV, cv = idx - rp * CV;
+                const int gr0 = (ty0 / 2 - CHY + 2 * rp) & (nc - 1), gr1 = (gr0 + 1) & (nc - 1);
+                const int gc = (tx0 / 2 - CHX + 4 * cv) & (nc - 1);
+                c0v[i] = __ldg(reinterpret_cast<const float4 *>(ec + (size_t)gr0 * nc + gc));
+                c1v[i] = __ldg(reinterpret_cast<const float4 *>(ec + (size_t)gr1 * nc + gc));
+            }
+        }
+        lx.scatter(X, X + A);
+#pragma unroll
+        for (int i = 0; i < CPER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            if (idx < CITEMS) {
+                const int rp = idx / CV, cv = idx - rp * CV;
+                float4 *dst = reinterpret_cast<float4 *>(cs2 + rp * CC + 4 * cv);
+                dst[0] = make_float4(c0v[i].x, c1v[i].x, c0v[i].y, c1v[i].y);
+                dst[1] = make_float4(c0v[i].z, c1v[i].z, c0v[i].w, c1v[i].w);
+            }
+        }
+        float2 tp[L];
+#pragma unroll
+        for (int k = 1; k <= L; ++k) tp[k - 1] = make_float2(Prec<float>::tap(taps, k), Prec<float>::tap(taps, k));
+        __syncthreads();
+        SplitLoad<T, R, C> lb;  // b arrives while the row pass runs
+        if (NU > 0) lb.issue(b, n, ty0 - H, tx0 - HX);
+        for (int item = threadIdx.x; item < CRP * JW; item += blockDim.x) {
+            const int rp = item / JW, jr = item - rp * JW;
+            const int J0 = -H / 2 + jr;
+            const float2 *w = cs2 + rp * CC + CHX + J0;  // w[m] = rows (2rp, 2rp+1) at coarse col J0 + m
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = L; k >= 1; --k) acc = f2_fma(tp[k - 1], f2_add(w[k], w[1 - k]), acc);
+            const float2 node = w[0];
+            const int col = 2 * J0 + H;
+            *reinterpret_cast<float2 *>(rs + (2 * rp) * FW + col) = make_float2(node.x, acc.x);
+            if (2 * rp + 1 < CR) *reinterpret_cast<float2 *>(rs + (2 * rp + 1) * FW + col) = make_float2(node.y, acc.y);
+        }
+        __syncthreads();
+        if (NU > 0) lb.scatter(B, B + A);
+        constexpr int CP = FW / 2;
+        for (int item = threadIdx.x; item < IW * CP; item += blockDim.x) {
+            const int ir = item / CP, cp = item - ir * CP;
+            const int I0 = -H / 2 + ir;
+            const float *w = rs + (CHY + I0) * FW + 2 * cp;  // columns 2cp, 2cp + 1
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = L; k >= 1; --k)
+                acc = f2_fma(tp[k - 1], f2_add(*reinterpret_cast<const float2 *>(w + k * FW),
+                                                *reinterpret_cast<const float2 *>(w + (1 - k) * FW)), acc);
+            const float2 node = *reinterpret_cast<const float2 *>(w);
+            const int u = 2 * I0, r = u + H;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int v = 2 * cp + h - H;
+                const int c = v + HX;
+                T ve = h ? node.y : node.x, vo = h ? acc.y : acc.x;
+                if (extra) {
+                    const size_t gc = (size_t)((tx0 + v) & (n - 1));
+                    ve += extra[(size_t)((ty0 + u) & (n - 1)) * n + gc];
+                    vo += extra[(size_t)((ty0 + u + 1) & (n - 1)) * n + gc];
+                }
+                const int q = (r + c) & 1;
+                X[q * A + r * CK + (c >> 1)] += ve;
+                X[(q ^ 1) * A + (r + 1) * CK + (c >> 1)] += vo;
+            }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int s = 0; s < NU; ++s) {
+#pragma unroll 1
+            for (int q = 0; q < 2; ++q) {
+                const int j = 2 * s + q + 1;
+                half_sweep<CK, A>(X, B, j, R - j, q);
+                __syncthreads();
+            }
+        }
+        store_split<T, TY, TX, C>(xout, X, X + A, n, ty0, tx0, H, HX);
+        return;
+    }
     load_split<T, R, C>(X, X + A, x, n, ty0 - H, tx0 - HX);
     load_tile<T, CR, CC, CC>(cs, ec, nc, ty0 / 2 - CHY, tx0 / 2 - CHX);
     __syncthreads();

@@ -10,7 +10,7 @@
 //
 // The table is process-wide, keyed by (kernel kind, grid size, sweep count).
 // Entries come from built-in defaults (op-level timings on GB300: 32-row
-// tiles up to 512^2, 64-row tiles above, one midpoint per work item), from
+// tiles up to 512^2, 64-row tiles above, packed spline passes), from
 // mg_autotune (CUDA-event timings of every variant on a context's own level
 // buffers), or from a cache file that earlier autotuning wrote.
 #include <stdio.h>
@@ -36,9 +36,11 @@ std::map<Key, int> g_table;
 std::atomic<unsigned> g_epoch{1};
 
 int default_variant(int kind, int n, int nu) {
-    (void)kind;
     (void)nu;
-    return n <= 512 ? 1 : 0;  // 32-row tiles up to 512^2; one midpoint per work item
+    // 32-row tiles up to 512^2, 64-row tiles above; the up kernel's packed
+    // FP32x2 spline passes (variant bit 1)
+    const int rows = n <= 512 ? 1 : 0;
+    return kind == 0 ? rows : rows | 2;
 }
 
 std::string gpu_tag(int device) {
