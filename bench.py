@@ -47,6 +47,22 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+def max_over_ranks_of(v, dist=None, device="cpu"):
+    """Max of the local value v over the process group (v itself without one)."""
+    if dist is None or not dist.is_initialized():
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(local_seconds, units_per_rank, world, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: the units all ranks processed over the
+    slowest rank's time (every rank does the same units on its own inputs)."""
+    return world * units_per_rank / max_over_ranks_of(local_seconds, dist, device)
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -554,13 +570,6 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # ---- mixed precision (headline): each solve is one CUDA graph launch -----
     ctx = make_ctx("mixed")
     timed_solves(ctx, args.warmup, f_dev, x)
@@ -572,8 +581,7 @@ def main():
         t_wall = time.perf_counter() - t_wall0
     launches = mg.kernel_launches() - l0
     barrier()
-    total = max_over_ranks(sum(times))
-    value = world * args.steps / total
+    value = weak_scaling_value(sum(times), args.steps, world, dist, dev)
     clocks = clk.summary()
     x_keep = x.clone()
 
@@ -606,7 +614,7 @@ def main():
     timed_solves(ctx64, args.warmup, f_dev, x)
     k64 = max(3, args.steps // 2)
     t64, info64 = timed_solves(ctx64, k64, f_dev, x)
-    value64 = world * k64 / max_over_ranks(sum(t64))
+    value64 = weak_scaling_value(sum(t64), k64, world, dist, dev)
     err64 = float(np.abs(x.cpu().numpy() - omg.exact_solve_fft(srcs[(k64 - 1) % 2])).max()
                   / np.abs(omg.exact_solve_fft(srcs[(k64 - 1) % 2])).max())
 
@@ -615,7 +623,7 @@ def main():
     x_host = torch.zeros_like(f_host[0]).pin_memory()
     timed_solves(ctx, 2, f_host, x_host)
     te2e, _ = timed_solves(ctx, args.steps, f_host, x_host)
-    value_e2e = world * args.steps / max_over_ranks(sum(te2e))
+    value_e2e = weak_scaling_value(sum(te2e), args.steps, world, dist, dev)
     bytes_grid = N * N * 8
 
     # ---- roofline of the dominant kernel -----------------------------------
