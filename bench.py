@@ -63,6 +63,9 @@ def weak_scaling_value(local_seconds, units_per_rank, world, dist=None, device="
     return world * units_per_rank / max_over_ranks_of(local_seconds, dist, device)
 
 
+SIDE_REPS = 20  # repetitions of the secondary measurements (probe, FP64 leg, e2e x4, batched, SR)
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -87,6 +90,36 @@ def kernel_source_sha():
     return h.hexdigest()
 
 
+# FP64 FLOPs per point of the outer residual: 3 adds (neighbour sum), 4x - sum
+# (2), f - mean (1), h^2 (f - mean) - (.) (2); its norm runs in FP32.
+OUTER_FP64_FLOP_PER_POINT = 8
+FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64, nominal
+
+
+def kernel_roofline(kind, n_l, ms, nbytes, peak, peak_src):
+    """Roofline of one probed kernel kind: launches n_l, total ms, algorithmic bytes.
+    The stencils are bounded by memory (HBM peak); the FP64 outer residual by the
+    FP64 pipe (FLOPs against the nominal FP64 peak)."""
+    if not n_l:
+        return None
+    us = ms / n_l * 1e3
+    base = {"kernel": PROBE_NAMES[kind], "avg_launch_us": us, "launches": n_l,
+            "algorithmic_bytes_per_launch": nbytes / n_l, "traffic": read_traffic(kind)}
+    if kind == 3:
+        flops = OUTER_FP64_FLOP_PER_POINT * N * N
+        ach = flops / (us * 1e-6) / 1e12
+        base.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal dense FP64 of GB300 (no measured FP64 peak on this pool)",
+                     "note": "FP64-pipe bound (ncu: 81% of the FP64 pipe busy); 4 of its 6 FP64 "
+                             "instructions per point are adds, counted as 1 FLOP each"})
+    else:
+        ach = (nbytes / n_l) / (us * 1e-6) / 1e9
+        base.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "peak_source": f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if peak_src == 'measured' else 'recipe fallback'})"})
+    return base
+
+
 def read_traffic(kernel_kind):
     """DRAM bytes per launch from a committed ncu capture, if it matches this source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -101,7 +134,7 @@ def read_traffic(kernel_kind):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    """nvidia-smi clock/throttle samples every 50 ms while the timed region runs."""
 
     def __init__(self, gpu_index):
         self.path = tempfile.mktemp(suffix=".csv")
@@ -113,7 +146,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -170,6 +203,15 @@ def oracle_cycle_sample(f, cycles):
 
 
 ORACLE_CYCLES_PER_SOLVE = 7  # FP64 V(2,2) cycles the oracle needs on this workload (tests pin it)
+
+
+def oracle_accuracy(f, x):
+    """|x - x_exact|_inf / |x_exact|_inf and the relative residual of a GPU result,
+    by the oracle (part of the CPU-baseline leg)."""
+    from oracle import multigrid as omg
+    xe = omg.exact_solve_fft(f - f.mean())
+    return (float(np.abs(x - xe).max() / np.abs(xe).max()),
+            float(omg.relative_residual(f - f.mean(), x, omg.grid_h(f.shape[0]))))
 
 
 def cpu_baseline_leg(f, cycles=3):
@@ -251,7 +293,7 @@ def batched_leg(mg, dev, stream, flush, args, rank):
             x.zero_()
         infos = mg.solve_batched(ctxs, fts, xs)
     times = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, SIDE_REPS)):
         for x in xs:
             x.zero_()
         flush.zero_()
@@ -305,10 +347,10 @@ def sr_leg(mg, dev, stream, flush, f_dev, x, args):
     out = torch.empty((N, N), dtype=torch.float32, device=dev)
     for _ in range(2):
         mg.op_sr_generator(ctx, ec, out)
-    t_gen = _events_time(stream, lambda: mg.op_sr_generator(ctx, ec, out), max(3, args.steps // 2))
+    t_gen = _events_time(stream, lambda: mg.op_sr_generator(ctx, ec, out), SIDE_REPS)
     tflop = SR_TENSOR_FLOP_PER_COARSE_PX * nc * nc / 1e12
     peak_tf = read_bf16_peak()
-    reps = max(3, args.steps // 4)
+    reps = 3
     solves = {}
     for n in (N, N // 2):
         c = ctx if n == N else mg.Context(LEVELS - 1, n)
@@ -498,7 +540,7 @@ def read_bf16_peak():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -595,55 +637,46 @@ def main():
         n_l, ms, by = ctx.probe_read()
         kernel_ms[kind] = (n_l, ms, by)
     dom = max(kernel_ms, key=lambda k: kernel_ms[k][1])
-    ctx.probe(dom, 64 * args.steps)
-    tprobe, _ = timed_solves(ctx, args.steps, f_dev, x)
+    n_probe = min(args.steps, SIDE_REPS)
+    ctx.probe(dom, 64 * n_probe)
+    tprobe, _ = timed_solves(ctx, n_probe, f_dev, x)
     n_l, probe_ms, probe_bytes = ctx.probe_read()
     ctx.probe(0, 0)
     x.copy_(x_keep)
 
-    # accuracy of the last solve against the exact FFT solution (plain definition)
-    from oracle import multigrid as omg
+    # the last solve's result, checked by the oracle in the CPU-baseline leg
     f_last = srcs[(args.steps - 1) % len(srcs)]
     x_last = x.cpu().numpy()
-    xe = omg.exact_solve_fft(f_last)
-    err = float(np.abs(x_last - xe).max() / np.abs(xe).max())
-    rel = omg.relative_residual(f_last, x_last, omg.grid_h(N))
 
     # ---- plain FP64 V-cycle on the same GPU ------------------------------
     ctx64 = make_ctx("fp64")
     timed_solves(ctx64, args.warmup, f_dev, x)
-    k64 = max(3, args.steps // 2)
+    k64 = min(max(3, args.steps // 2), SIDE_REPS)
     t64, info64 = timed_solves(ctx64, k64, f_dev, x)
     value64 = weak_scaling_value(sum(t64), k64, world, dist, dev)
-    err64 = float(np.abs(x.cpu().numpy() - omg.exact_solve_fft(srcs[(k64 - 1) % 2])).max()
-                  / np.abs(omg.exact_solve_fft(srcs[(k64 - 1) % 2])).max())
+    f64_last, x64_last = srcs[(k64 - 1) % 2], x.cpu().numpy()
 
     # ---- end to end through host (pinned) buffers --------------------------
     f_host = [torch.tensor(s).pin_memory() for s in srcs]
     x_host = torch.zeros_like(f_host[0]).pin_memory()
     timed_solves(ctx, 2, f_host, x_host)
-    te2e, _ = timed_solves(ctx, args.steps, f_host, x_host)
-    value_e2e = weak_scaling_value(sum(te2e), args.steps, world, dist, dev)
+    n_e2e = min(args.steps, 4 * SIDE_REPS)
+    te2e, _ = timed_solves(ctx, n_e2e, f_host, x_host)
+    value_e2e = weak_scaling_value(sum(te2e), n_e2e, world, dist, dev)
     bytes_grid = N * N * 8
 
     # ---- roofline of the dominant kernel -----------------------------------
     peak, peak_src = read_peaks()
-    achieved = (probe_bytes / n_l) / (probe_ms / n_l / 1e3) / 1e9 if n_l else None
-    roofline = {"bound": "hbm", "kernel": PROBE_NAMES[dom], "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak if achieved else None,
-                "peak_source": f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if peak_src == 'measured' else 'recipe fallback'})",
-                "traffic": read_traffic(dom),
-                "algorithmic_bytes_per_launch": probe_bytes / n_l if n_l else None,
-                "avg_launch_us": probe_ms / n_l * 1e3 if n_l else None, "launches": n_l,
-                "share_of_solve": None}
+    roofline = kernel_roofline(dom, n_l, probe_ms, probe_bytes, peak, peak_src)
     mean_step = sum(times) / len(times)
     mean_probe_step = sum(tprobe) / len(tprobe)
-    roofline["share_of_solve"] = (probe_ms / args.steps / 1e3) / mean_probe_step
-    roofline["measured_over"] = (f"{args.steps} solves of the same workload with CUDA events on the "
+    roofline["share_of_solve"] = (probe_ms / n_probe / 1e3) / mean_probe_step
+    roofline["measured_over"] = (f"{n_probe} solves of the same workload with CUDA events on the "
                                  f"launching stream around each launch of this kernel (host-loop "
                                  f"execution, {mean_probe_step * 1e3:.3f} ms per solve)")
     kernels = {PROBE_NAMES[k]: {"launches_per_solve": v[0], "ms_per_solve": v[1],
-                                "gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None}
+                                "gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None,
+                                "roofline": kernel_roofline(k, v[0], v[1], v[2], peak, peak_src)}
                for k, v in kernel_ms.items()}
 
     # ---- batched: 256 right-hand sides of mixed sizes in one graph ----------
@@ -655,9 +688,11 @@ def main():
     # ---- serving: Poisson arrivals into the continuous-batching server -----
     serving = serve_leg(mg, dev, stream, args, rank) if not args.skip_serve else None
 
-    cpu = None
+    cpu, err, rel, err64 = None, None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg(srcs[0])
+        err, rel = oracle_accuracy(f_last, x_last)
+        err64, _ = oracle_accuracy(f64_last, x64_last)
 
     if rank == 0:
         line = {
@@ -678,7 +713,9 @@ def main():
             "clocks": clocks,
             "wall_s_timed_region": t_wall,
             "solve": {"vcycles": infos[-1]["vcycles"], "outer_iters": infos[-1]["outer_iters"],
-                      "rel_residual": rel, "err_inf_vs_exact_fft": err},
+                      "rel_residual": infos[-1]["rel_residual"], "rel_residual_by_oracle": rel,
+                      "err_inf_vs_exact_fft": err,
+                      "accuracy_check": "by the oracle in the CPU-baseline leg (null when that leg is skipped)"},
             "fp64_vcycle": {"value": value64, "unit": "solves/s", "steps": k64,
                             "ms_per_step": sum(t64) / k64 * 1e3,
                             "vcycles": info64[-1]["vcycles"], "err_inf_vs_exact_fft": err64},
