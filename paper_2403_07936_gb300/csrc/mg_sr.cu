@@ -44,10 +44,16 @@ static_assert(PLANE >= ROWPX * 16 && PLANE % 128 == 0, "plane pitch");
 constexpr int NSLOT = 6;              // ring of staged input rows (prefetch 3 rows ahead)
 constexpr int WBYTES = 9 * C * C * 2;  // one layer's weights, 72 KiB
 constexpr int TAPBYTES = C * C * 2;    // one tap: 64 rows (co) x 128 bytes (ci)
-constexpr int TMEM_COLS = 128;        // two 64-column FP32 accumulators
-constexpr int CONV_THREADS = 256;  // 8 warps drain the accumulator: (lane quarter, column half)
+constexpr int NBUF = 4;               // 64-column FP32 accumulators in TMEM
+constexpr int TMEM_COLS = NBUF * C;
+// warp roles: 0 = TMA producer, 1 = MMA issuer, 2..9 = epilogue (lane quarter
+// warp % 4, column half (warp - 2) / 4 of the 128 x 64 accumulator)
+constexpr int EPI_WARPS = 8;
+constexpr int CONV_THREADS = 32 * (2 + EPI_WARPS);
 constexpr int STAGE = TM * C * 2;     // one output tile, 128 px x 128 B (epilogue staging)
-constexpr size_t CONV_SMEM = 1024 + WBYTES + NSLOT * ROWSLOT + 2 * STAGE + 128 + 2 * C * sizeof(float);
+constexpr int NBARS = 1 + 2 * NSLOT + 2 * NBUF + 1;  // weights, row full/empty, tmem full/empty, mma done
+constexpr size_t CONV_SMEM = 1024 + WBYTES + NSLOT * ROWSLOT + 2 * STAGE + 256 + 2 * C * sizeof(float);
+static_assert(NBARS * 8 + 16 <= 256, "barrier area");
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 enum { MODE_PRELU = 0, MODE_RESID = 1, MODE_SHUFFLE = 2 };
@@ -187,6 +193,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Barrier `id` over `count` threads (the epilogue warps) returning the AND of
+// every participant's predicate: a decision all of them take together.
+__device__ __forceinline__ bool epi_bar_and(bool pred, int id, int count) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void epi_bar(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 // Store one pixel's 64 bf16 channels (8 x 16 bytes) at (y, x) of a padded
 // H x W grid, and at every halo position that wraps onto it.
@@ -255,10 +281,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     unsigned char *rows = sm + WBYTES;
     unsigned char *stage = rows + NSLOT * ROWSLOT;  // 2 x STAGE, 1024-byte aligned
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * STAGE);
-    uint64_t *wbar = bars, *full = bars + 1, *mdone = bars + 1 + NSLOT;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 1 + NSLOT + 2);
-    int *abort_flag = reinterpret_cast<int *>(bars + 2 + NSLOT + 2);
-    float *s_bias = reinterpret_cast<float *>(bars + 16);  // [64] bias, [64] PReLU slopes
+    uint64_t *wbar = bars, *full = bars + 1, *empty = full + NSLOT;
+    uint64_t *tfull = empty + NSLOT, *tempty = tfull + NBUF, *mdone = tempty + NBUF;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NBARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + NBARS) + 1;
+    float *s_bias = reinterpret_cast<float *>(bars + 32);  // [64] bias, [64] PReLU slopes
     float *s_prelu = s_bias + C;
 
     const int NB = a.W / TM;
@@ -267,14 +294,20 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     const int y_a = chunk * a.rows_per_chunk;
     const int y_b = min(a.H, y_a + a.rows_per_chunk);
     if (y_a >= y_b) return;  // uniform across the block, before any barrier or TMEM use
-    const int T = y_b - y_a;
+    const int T = y_b - y_a;  // tiles (output rows); input rows y_a .. y_b + 1 (padded)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         mbar_init(wbar, 1);
-        for (int s = 0; s < NSLOT; ++s) mbar_init(&full[s], 1);
-        mbar_init(&mdone[0], 1);
-        mbar_init(&mdone[1], 1);
+        for (int s2 = 0; s2 < NSLOT; ++s2) {
+            mbar_init(&full[s2], 1);
+            mbar_init(&empty[s2], 1);
+        }
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS);
+        }
+        mbar_init(mdone, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -288,41 +321,48 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // loads in flight per slot (for the bounded drain on abort)
-    int loaded_rows = 0;
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(wbar, WBYTES);
-        tma_load_4d(wsm, &tm_w, wbar, 0, 0, 0, a.layer + g);
-        for (int r = 0; r < NSLOT; ++r) {
-            const int pr = y_a + r;  // padded input row
-            if (pr <= y_b + 1) {
-                const int slot = pr % NSLOT;
+    if (warp == 0) {
+        // ---- producer: the weights, then the ring of input rows ----------------
+        if (lane == 0) {
+            mbar_expect_tx(wbar, WBYTES);
+            tma_load_4d(wsm, &tm_w, wbar, 0, 0, 0, a.layer + g);
+            int issued = 0;
+            for (int i = 0; i < T + 2; ++i) {  // relative input row i = padded row y_a + i
+                const int slot = i % NSLOT;
+                if (i >= NSLOT && !mbar_wait(&empty[slot], ((i / NSLOT) - 1) & 1)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                if (*abort_flag) break;
                 mbar_expect_tx(&full[slot], ROWBYTES);
                 for (int q = 0; q < 8; ++q)
-                    tma_load_3d(rows + slot * ROWSLOT + q * PLANE, &tm_in, &full[slot], 8 * q, cb * TM, pr);
-                ++loaded_rows;
+                    tma_load_3d(rows + slot * ROWSLOT + q * PLANE, &tm_in, &full[slot], 8 * q, cb * TM, y_a + i);
+                issued = i + 1;
+            }
+            if (*abort_flag) {
+                // wait (bounded) for the last load issued into each slot and the
+                // weights, so no copy still writes this block's shared memory
+                for (int i = issued - 1; i >= 0 && i >= issued - NSLOT; --i)
+                    mbar_wait(&full[i % NSLOT], (i / NSLOT) & 1);
+                mbar_wait(wbar, 0);
             }
         }
-        if (!mbar_wait(wbar, 0)) *abort_flag = 1;
-    }
-
-    for (int t = 0; t <= T; ++t) {
-        if (threadIdx.x == 0 && t < T && !*abort_flag) {
-            const int y = y_a + t;
-            bool ok = true;
-            for (int dy = 0; dy < 3 && ok; ++dy) {
-                const int pr = y + dy;
-                ok = mbar_wait(&full[pr % NSLOT], ((pr - y_a) / NSLOT) & 1);
-            }
-            if (!ok) {
-                *abort_flag = 1;
-            } else {
+    } else if (warp == 1) {
+        // ---- MMA issuer ---------------------------------------------------------
+        if (lane == 0) {
+            bool ok = mbar_wait(wbar, 0);
+            int t = 0;
+            for (; ok && t < T; ++t) {
+                const int b = t % NBUF;
+                if (t >= NBUF) ok = mbar_wait(&tempty[b], ((t / NBUF) - 1) & 1);
+                for (int dy = 0; dy < 3 && ok; ++dy) ok = mbar_wait(&full[(t + dy) % NSLOT], ((t + dy) / NSLOT) & 1);
+                if (!ok || *abort_flag) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)((t & 1) * C);
+                const uint32_t d = tmem + (uint32_t)(b * C);
                 const uint32_t wbase = smem_u32(wsm), rbase = smem_u32(rows);
 #pragma unroll 1
                 for (int dy = 0; dy < 3; ++dy) {
-                    const uint32_t row = rbase + (uint32_t)(((y + dy) % NSLOT) * ROWSLOT);
+                    const uint32_t row = rbase + (uint32_t)(((t + dy) % NSLOT) * ROWSLOT);
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
@@ -332,116 +372,101 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                             mma_bf16(d, ad, bd, (dy | dx | kk) ? 1u : 0u);
                         }
                 }
-                mma_commit(&mdone[t & 1]);
+                mma_commit(&tfull[b]);     // accumulator b holds tile t
+                mma_commit(&empty[t % NSLOT]);  // input row t has no later reader
             }
+            if (!ok) *abort_flag = 1;
+            // every issued MMA completes before the block frees its TMEM
+            mma_commit(mdone);
+            mbar_wait(mdone, 0);
         }
-        if (t > 0) {
-            const int tp = t - 1;
-            // the staging buffer of tile tp was last read by the TMA store two tiles ago
-            if (MODE != MODE_SHUFFLE && threadIdx.x == 0) bulk_wait_read1();
-            __syncthreads();  // abort_flag from thread 0 is visible; staging buffer free
-            const bool aborted = *abort_flag != 0;
-            bool ok = !aborted && mbar_wait(&mdone[tp & 1], (tp >> 1) & 1);
-            if (!ok) {
-                if (threadIdx.x == 0) *abort_flag = 1;
-            } else {
-                tc_fence_after();
-                if (threadIdx.x == 0) {  // the slot of padded row y_a + tp is free: prefetch
-                    const int pr = y_a + tp + NSLOT;
-                    if (pr <= y_b + 1) {
-                        const int slot = pr % NSLOT;
-                        mbar_expect_tx(&full[slot], ROWBYTES);
-                        for (int q = 0; q < 8; ++q)
-                            tma_load_3d(rows + slot * ROWSLOT + q * PLANE, &tm_in, &full[slot], 8 * q,
-                                        cb * TM, pr);
-                        ++loaded_rows;
-                    }
-                }
-                // epilogue of tile tp: warp w drains TMEM lanes 32 (w & 3) .. +31
-                // (pixels) and accumulator columns 32 (w >> 2) .. +31 (channels)
-                const int y = y_a + tp;
-                const int j = (warp & 3) * 32 + lane;
-                const int half = warp >> 2;
-                const int x = cb * TM + j;
-                const uint32_t taddr = tmem + (uint32_t)((tp & 1) * C + half * 32) +
-                                       ((uint32_t)((warp & 3) * 32) << 16);
-                float v[32];
-                tmem_ld32(taddr, v);
-                tmem_wait_ld();
-                if (MODE == MODE_RESID) {
-                    const uint4 *sp = reinterpret_cast<const uint4 *>(
-                        a.skip + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C + half * 32);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const uint4 q = sp[i];
-                        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
-                            v[i * 8 + 2 * k] += f.x;
-                            v[i * 8 + 2 * k + 1] += f.y;
-                        }
-                    }
-                }
-                uint4 outv[4];
+    } else {
+        // ---- epilogue: 8 warps drain accumulator b of tile t ----------------------
+        const int e = warp - 2;
+        const int quarter = warp & 3, half = e >> 2;
+        const int j = quarter * 32 + lane;  // pixel of the tile
+        const int x = cb * TM + j;
+        const bool leader = (e == 0 && lane == 0);
+        for (int t = 0; t < T; ++t) {
+            const int b = t % NBUF;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&tfull[b], (t / NBUF) & 1);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!epi_bar_and(ok && !*abort_flag, 1, 32 * EPI_WARPS)) {
+                if (leader) *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            float v[32];
+            tmem_ld32(tmem + (uint32_t)(b * C + half * 32) + ((uint32_t)(quarter * 32) << 16), v);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);  // accumulator b may take tile t + NBUF
+            const int y = y_a + t;
+            if (MODE == MODE_RESID) {
+                const uint4 *sp = reinterpret_cast<const uint4 *>(
+                    a.skip + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C + half * 32);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    uint32_t w4[4];
+                    const uint4 q = sp[i];
+                    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const int c0 = i * 8 + 2 * k, cc = half * 32 + c0;
-                        float v0 = v[c0] + s_bias[cc], v1 = v[c0 + 1] + s_bias[cc + 1];
-                        if (MODE != MODE_RESID) {
-                            v0 = v0 > 0.f ? v0 : s_prelu[cc] * v0;
-                            v1 = v1 > 0.f ? v1 : s_prelu[cc + 1] * v1;
-                        }
-                        const __nv_bfloat162 bb = __floats2bfloat162_rn(v0, v1);
-                        w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
+                        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
+                        v[i * 8 + 2 * k] += f.x;
+                        v[i * 8 + 2 * k + 1] += f.y;
                     }
-                    outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                }
-                if (MODE == MODE_SHUFFLE) {
-                    store_half_px(a.out, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), half, outv, false);
-                } else {
-                    // staged in the 128-byte swizzled layout the TMA store expects:
-                    // 16-byte chunk i of pixel j at chunk position i ^ (j & 7)
-                    uint4 *st = reinterpret_cast<uint4 *>(stage + (tp & 1) * STAGE + j * 128);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) st[(half * 4 + i) ^ (j & 7)] = outv[i];
-                    if (x == 0 || x == a.W - 1) store_half_px(a.out, a.H, a.W, y, x, half, outv, true);
-                    fence_proxy_async();
                 }
             }
-            if (MODE != MODE_SHUFFLE) {
-                __syncthreads();  // the staged tile is complete
-                if (threadIdx.x == 0 && !*abort_flag) {
-                    const unsigned char *src = stage + (tp & 1) * STAGE;
-                    const int y = y_a + tp;
+            uint4 outv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c0 = i * 8 + 2 * k, cc = half * 32 + c0;
+                    float v0 = v[c0] + s_bias[cc], v1 = v[c0 + 1] + s_bias[cc + 1];
+                    if (MODE != MODE_RESID) {
+                        v0 = v0 > 0.f ? v0 : s_prelu[cc] * v0;
+                        v1 = v1 > 0.f ? v1 : s_prelu[cc + 1] * v1;
+                    }
+                    const __nv_bfloat162 bb = __floats2bfloat162_rn(v0, v1);
+                    w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
+                }
+                outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+            if (MODE == MODE_SHUFFLE) {
+                store_half_px(a.out, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), half, outv, false);
+            } else {
+                // stage t & 1 was last read by the TMA store of tile t - 2
+                if (leader) bulk_wait_read1();
+                epi_bar(2, 32 * EPI_WARPS);
+                // 128-byte swizzled staging: 16-byte chunk i of pixel j at position i ^ (j & 7)
+                uint4 *st = reinterpret_cast<uint4 *>(stage + (t & 1) * STAGE + j * 128);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) st[(half * 4 + i) ^ (j & 7)] = outv[i];
+                if (x == 0 || x == a.W - 1) store_half_px(a.out, a.H, a.W, y, x, half, outv, true);
+                fence_proxy_async();
+                epi_bar(2, 32 * EPI_WARPS);
+                if (leader) {
+                    const unsigned char *src = stage + (t & 1) * STAGE;
                     tma_store_3d(&tm_out, src, 0, cb * TM + 1, y + 1);
                     if (y == 0) tma_store_3d(&tm_out, src, 0, cb * TM + 1, a.H + 1);
                     if (y == a.H - 1) tma_store_3d(&tm_out, src, 0, cb * TM + 1, 0);
                     bulk_commit();
                 }
             }
-            tc_fence_before();
-            __syncthreads();  // accumulator tp & 1 drained before it is reused
-            tc_fence_after();
-            if (*abort_flag) break;
         }
+        if (MODE != MODE_SHUFFLE && leader) bulk_wait_all();  // tile stores complete
     }
-    if (MODE != MODE_SHUFFLE && threadIdx.x == 0) bulk_wait_all();  // tile stores complete
-    if (*abort_flag && threadIdx.x == 0) {
-        atomicExch(a.err, 1);
-        // wait (bounded) for the last row load issued into each slot, so that
-        // no copy is still writing this block's shared memory when it exits
-        for (int r = loaded_rows - 1; r >= 0 && r >= loaded_rows - NSLOT; --r) {
-            const int pr = y_a + r;
-            mbar_wait(&full[pr % NSLOT], ((pr - y_a) / NSLOT) & 1);
-        }
-        mbar_wait(wbar, 0);
-    }
+    tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, 1);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
 }
 
 // ---------------------------------------------------------------------------
