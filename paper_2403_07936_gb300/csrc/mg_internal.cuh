@@ -95,7 +95,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double v) {
 // order inside the block), the last block to finish sums the partials in
 // index order and resets the arrival counter.  `nslot` independent sums.
 // ----------------------------------------------------------------------------
-constexpr int kRedBlocks = 304;  // 2 blocks per SM on 152 SMs
+constexpr int kRedBlocks = 304;  // 2 blocks per SM on 152 SMs (4 measured slower)
 constexpr int kRedThreads = 256;
 constexpr int kMaxSlots = 4;
 

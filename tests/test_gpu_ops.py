@@ -126,6 +126,32 @@ def test_bottom_vcycle_matches_oracle(mg, dt, n, coarsest, nu1, nu2, zero):
     assert _relerr(x.double().cpu().numpy(), xr) <= tol
 
 
+RED_BLOCKS, RED_THREADS = 304, 256  # grid of the FP64 outer kernels
+
+
+def test_outer_residual_matches_oracle(mg):
+    n = 256
+    h = omg.grid_h(n)
+    f = _rand(n, 10) + 0.3
+    x = _rand(n, 11)
+    mu = f.mean()
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.tensor(x, device=DEV)
+    s32 = torch.empty((n, n), dtype=torch.float32, device=DEV)
+    out = torch.zeros(2, dtype=torch.float64, device=DEV)
+    mg.op_outer_residual(ft, xt, mu, s32, out)
+    torch.cuda.synchronize()
+    s_ref = h * h * omg.residual(f - mu, x, h)
+    np.testing.assert_allclose(s32.double().cpu().numpy(), s_ref, rtol=1e-6,
+                               atol=1e-6 * np.abs(s_ref).max())
+    o = out.cpu().numpy()
+    # the norm sums squares of float-rounded residuals, FP32 within a thread:
+    # 2^-23 from the rounding plus 2^-24 per term of the longest thread sum
+    terms = -(-(n * n) // (RED_BLOCKS * RED_THREADS))
+    assert abs(o[0] - np.sum(s_ref ** 2)) <= (2.0 ** -23 + terms * 2.0 ** -24) * np.sum(s_ref ** 2)
+    assert abs(o[1] - np.sum((f - mu) ** 2)) <= 1e-12 * np.sum((f - mu) ** 2)
+
+
 def _conversion_inputs_f64():
     rng = np.random.default_rng(5)
     mant = rng.uniform(1.0, 2.0, 200000) * rng.choice([-1.0, 1.0], 200000)
