@@ -84,7 +84,17 @@ mg_status mg_setup(int levels, int N, mg_ctx **out);
  * all work of this context is ordered on it. */
 mg_status mg_set_options(mg_ctx *ctx, mg_precision precision, int nu_pre, int nu_post,
                          int max_cycles, void *cuda_stream);
+/* FP32 V-cycles per FP64 outer step of MIXED solves.  mg_set_inner_cycles
+ * fixes the count (1..16; batched solves and the server always use this
+ * count, default 2).  mg_set_adaptive_cycles (the default for single solves
+ * with the cubic prolongation: m_max = 3, rho = 0.06) lets every outer step
+ * run the smallest m in [1, m_max] with rel * rho^m <= tol, rel the relative
+ * residual before the step and rho the expected contraction per V-cycle
+ * (m_max <= 4; rho = 0 turns it off; mg_set_inner_cycles also turns it off).
+ * The FP32 inner solve cannot reduce the residual by much more than 1e-5 per
+ * outer step, which bounds useful m_max. */
 mg_status mg_set_inner_cycles(mg_ctx *ctx, int inner_cycles);
+mg_status mg_set_adaptive_cycles(mg_ctx *ctx, int m_max, double rho);
 
 /* Execution mode of mg_solve (default 1).  1: the whole solve is one CUDA
  * graph launch - a WHILE conditional node runs the outer steps on the device
@@ -279,8 +289,9 @@ unsigned long long mg_kernel_launches(void);
 /* Record a CUDA event pair around each launch of one kernel kind on the
  * context's stream: 1 = finest-level pre-smoothing/restriction kernel,
  * 2 = finest-level prolongation/post-smoothing kernel, 3 = FP64 outer
- * residual, 4 = FP64 update; 0 disables.  At most `capacity` launches are
- * recorded until mg_probe_read. */
+ * residual, 4 = FP64 update, 5 = the coarse part of an FP32 V-cycle (every
+ * launch below the finest level, as one span); 0 disables.  At most
+ * `capacity` launches (spans) are recorded until mg_probe_read. */
 mg_status mg_probe_kernel(mg_ctx *ctx, int kind, int capacity);
 
 /* Synchronise the context's stream and return the number of recorded

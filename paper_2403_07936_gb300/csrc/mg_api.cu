@@ -123,6 +123,8 @@ struct SolveGraph {
     cudaGraphExec_t exec = nullptr;
     long long n_pro = 0, n_body = 0, n_epi = 0;  // kernels per part
     long long n_sr = 0;                         // kernels of one conditional SR correction
+    long long n_cyc = 0;                        // kernels of one optional (conditional) V-cycle
+    int adapt_max = 0;                          // optional cycles recorded: 2 .. adapt_max
     unsigned long long stamp = 0;               // last use (LRU)
     unsigned epoch = 0;                         // tile-variant table at recording
 };
@@ -132,6 +134,10 @@ struct mg_ctx {
     int N = 0, levels = 0, coarsest = 0, device = 0;
     mg_precision prec = MG_PREC_MIXED;
     int nu1 = 2, nu2 = 2, max_cycles = 100, inner = 2;
+    // adaptive inner cycles of mixed cubic solves: up to adapt_max V-cycles per
+    // outer step, chosen from the residual with contraction rho (0: fixed `inner`)
+    int adapt_max = 3;
+    double rho = 0.06;
     cudaStream_t stream = nullptr;
     Level lv[kMaxLevels];
     void *h32_block = nullptr, *h64_block = nullptr;
@@ -163,7 +169,25 @@ struct mg_ctx {
 };
 
 enum { kGrpF = 0, kGrpR = 1, kGrpU = 2, kGrpX = 3 };
-enum { kProbeNone = 0, kProbeDown = 1, kProbeUp = 2, kProbeResidual = 3, kProbeUpdate = 4 };
+enum { kProbeNone = 0, kProbeDown = 1, kProbeUp = 2, kProbeResidual = 3, kProbeUpdate = 4, kProbeCoarse = 5 };
+
+// Algorithmic bytes of the coarse part of a V-cycle below level l0: 13 B per
+// point for each tile kernel (down and up) of every tiled level, and the
+// bottom kernel's read of b, read and write of x.
+template <typename T>
+static double coarse_bytes(const mg_ctx *c, int l0) {
+    double by = 0.0;
+    for (int l = l0; l < c->levels; ++l) {
+        const double nn = (double)c->lv[l].n * c->lv[l].n;
+        if (c->lv[l].n > bottom_max<T>()) {
+            by += 2.0 * 13.0 * nn * sizeof(T) / 4.0;
+        } else {
+            by += 3.0 * nn * sizeof(T);
+            break;
+        }
+    }
+    return by;
+}
 
 static void probe_begin(mg_ctx *c, int kind) {
     if (c->probe_kind == kind && c->probe_used < c->probe_cap)
@@ -242,7 +266,9 @@ static mg_status vcycle_rec(mg_ctx *c, int l, T *x, T *t, const T *b, bool zero)
     if (l == 0) probe_begin(c, kProbeDown);
     MG_CUDA(launch_down<T>(x, t, b, n, c->nu1, zero, bc, c->stream));
     if (l == 0) probe_end(c, kProbeDown, nn * ((zero ? 0 : 1) + 1 + 1 + 0.25));
+    if (l == 0) probe_begin(c, kProbeCoarse);
     MG_TRY(vcycle_rec<T>(c, l + 1, xc, tc, bc, true));
+    if (l == 0) probe_end(c, kProbeCoarse, coarse_bytes<T>(c, 1));
     if (l == 0) probe_begin(c, kProbeUp);
     MG_CUDA(launch_up<T>(t, x, b, xc, n, c->nu2, c->taps, c->stream));
     if (l == 0) probe_end(c, kProbeUp, nn * (2 + (c->nu2 > 0 ? 1 : 0) + 0.25));
@@ -258,7 +284,9 @@ static mg_status vcycle32_top(mg_ctx *c, bool zero, mg_prolong prolong) {
         probe_begin(c, kProbeDown);
         MG_CUDA(launch_down<float>(x, t, b, c->lv[0].n, c->nu1, zero, bc, c->stream));
         probe_end(c, kProbeDown, nn * ((zero ? 0 : 1) + 1 + 1 + 0.25));
+        probe_begin(c, kProbeCoarse);
         MG_TRY(vcycle_rec<float>(c, 1, xc, tc, bc, true));
+        probe_end(c, kProbeCoarse, coarse_bytes<float>(c, 1));
         // generator correction s * G(e_c / s) on the fine grid, then the cubic
         // part, the correction and the post-smoothing in one up pass
         MG_TRY(sr_correction(&c->sr, xc, c->lv[1].n, c->stream, g_err, sizeof g_err));
@@ -376,7 +404,12 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
     const int N = c->N;
     const double N2 = (double)N * N;
     const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
-    const int step = mixed ? c->inner : 1;
+    const bool use_policy_ = mixed && prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax;
+    const bool adaptive = mixed && !use_policy_ && c->rho > 0.0 && c->adapt_max > 1;
+    const int step = mixed ? (adaptive ? c->adapt_max : c->inner) : 1;
+    const double rho = adaptive ? c->rho : 0.0;
+    CycleHandles ifh{};
+    long long n_cyc = 0;
     cudaStream_t user_stream = c->stream;
     cudaStream_t s = c->cap_stream;
     cudaGraph_t g = nullptr;
@@ -395,6 +428,9 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
         if (e != cudaSuccess) { fail(e, "create"); break; }
         e = cudaGraphConditionalHandleCreate(&handle, g, 0, cudaGraphCondAssignDefault);
         if (e != cudaSuccess) { fail(e, "conditional handle"); break; }
+        for (int k = 2; adaptive && k <= step && e == cudaSuccess; ++k)
+            e = cudaGraphConditionalHandleCreate(&ifh.h[k - 2], g, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { fail(e, "cycle handles"); break; }
         // prologue
         long long l0 = (long long)launches_total();
         e = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
@@ -407,7 +443,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
                                       true, c->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check(c->dstate, c->out(kGrpR), nullptr, c->out(kGrpF), N2, h2, tol, step,
-                             c->max_cycles, true, handle, s);
+                             c->max_cycles, true, handle, s, rho, ifh);
         if (e != cudaSuccess) { fail(e, "prologue"); break; }
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *deps = nullptr;
@@ -444,6 +480,41 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
             if (e != cudaSuccess) { fail(e, "if handle"); break; }
             if (st != MG_OK) break;
             e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
+        } else if (adaptive) {
+            // V-cycle 1 always; V-cycles 2 .. step each behind an IF node
+            st = vcycle32_top(c, true, prolong);
+            for (int k = 2; k <= step && st == MG_OK && e == cudaSuccess; ++k) {
+                cudaStreamCaptureStatus cs2;
+                const cudaGraphNode_t *d2 = nullptr;
+                size_t nd2 = 0;
+                e = cudaStreamGetCaptureInfo(s, &cs2, nullptr, nullptr, &d2, nullptr, &nd2);
+                if (e != cudaSuccess) break;
+                std::vector<cudaGraphNode_t> t2(d2, d2 + nd2);
+                e = cudaStreamEndCapture(s, &body);
+                if (e != cudaSuccess) break;
+                cudaGraphNodeParams ip = {};
+                ip.type = cudaGraphNodeTypeConditional;
+                ip.conditional.handle = ifh.h[k - 2];
+                ip.conditional.type = cudaGraphCondTypeIf;
+                ip.conditional.size = 1;
+                cudaGraphNode_t ifn;
+                e = cudaGraphAddNode(&ifn, body, t2.data(), nullptr, t2.size(), &ip);
+                if (e != cudaSuccess) break;
+                cudaGraph_t ib = ip.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(s, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) break;
+                const long long lc = (long long)launches_total();
+                st = vcycle32_top(c, false, prolong);
+                n_cyc = (long long)launches_total() - lc;
+                cudaError_t e2 = cudaStreamEndCapture(s, &ib);
+                if (st != MG_OK) break;
+                e = e2;
+                if (e != cudaSuccess) break;
+                e = cudaStreamBeginCaptureToGraph(s, body, &ifn, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+            }
+            if (st != MG_OK) break;
+            if (e != cudaSuccess) { fail(e, "optional cycles"); break; }
+            e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
         } else if (mixed) {
             for (int k = 0; k < c->inner && st == MG_OK; ++k) st = vcycle32_top(c, k == 0, prolong);
             if (st != MG_OK) break;
@@ -457,7 +528,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
                                       false, c->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check(c->dstate, c->out(kGrpR), mixed ? c->out(kGrpU) : nullptr, c->out(kGrpF),
-                             N2, h2, tol, step, c->max_cycles, false, handle, s);
+                             N2, h2, tol, step, c->max_cycles, false, handle, s, rho, ifh);
         if (e != cudaSuccess) { fail(e, "body"); break; }
         e = cudaStreamEndCapture(s, &body);
         capturing = false;
@@ -500,6 +571,8 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
     out->n_body = n_body;
     out->n_epi = n_epi;
     out->n_sr = n_sr;
+    out->n_cyc = n_cyc;
+    out->adapt_max = adaptive ? step : 0;
     return MG_OK;
 }
 
@@ -1374,16 +1447,31 @@ mg_status mg_set_options(mg_ctx *c, mg_precision prec, int nu_pre, int nu_post, 
     return MG_OK;
 }
 
+mg_status mg_set_adaptive_cycles(mg_ctx *c, int m_max, double rho) {
+    if (!c || m_max < 1 || m_max > kMaxAdaptive || !(rho >= 0.0 && rho < 1.0)) {
+        set_err("adaptive cycles: m_max in [1, %d], rho in [0, 1)", kMaxAdaptive);
+        return MG_ERR_INVALID_ARG;
+    }
+    if (m_max != c->adapt_max || rho != c->rho) {
+        drop_graphs(c);
+        batch_forget(c);
+    }
+    c->adapt_max = m_max;
+    c->rho = rho;
+    return MG_OK;
+}
+
 mg_status mg_set_inner_cycles(mg_ctx *c, int inner) {
     if (!c || inner < 1 || inner > 16) {
         set_err("inner_cycles must be in [1, 16]");
         return MG_ERR_INVALID_ARG;
     }
-    if (inner != c->inner) {
+    if (inner != c->inner || c->rho != 0.0) {
         drop_graphs(c);
         batch_forget(c);
     }
     c->inner = inner;
+    c->rho = 0.0;  // a fixed count: adaptive inner cycles off
     return MG_OK;
 }
 
@@ -1430,8 +1518,12 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         MG_CUDA(cudaStreamSynchronize(s));
         const DevState &ds = *c->hstate;
         // the SR kernels of a conditional node run only for the V-cycles that used SR
-        count_launches(sg->n_pro + (long long)ds.outer * (sg->n_body - (long long)c->inner * sg->n_sr) +
-                       (long long)ds.sr_used * sg->n_sr + sg->n_epi);
+        if (sg->adapt_max > 0)  // optional V-cycles run only when chosen
+            count_launches(sg->n_pro + (long long)ds.outer * sg->n_body -
+                           ((long long)ds.outer * sg->adapt_max - ds.cycles) * sg->n_cyc + sg->n_epi);
+        else
+            count_launches(sg->n_pro + (long long)ds.outer * (sg->n_body - (long long)c->inner * sg->n_sr) +
+                           (long long)ds.sr_used * sg->n_sr + sg->n_epi);
         mg_status gst = (mg_status)ds.status;
         if (gst == MG_ERR_NONFINITE) set_err("non-finite residual (NaN or Inf in f or x)");
         if (gst == MG_ERR_NOT_CONVERGED)
@@ -1461,6 +1553,7 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     bool first = true;
     // the prolongation policy, decided on the host with the same rule as k_policy
     const bool use_policy = mixed && prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax;
+    const bool adaptive = mixed && !use_policy && c->rho > 0.0 && c->adapt_max > 1;
     int sr_used = 0;
     bool sr_step = false, fallback = false;
     double rel_prev = 0.0;
@@ -1493,13 +1586,20 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         sr_step = false;
         rel_prev = rel;
         if (rel <= tol) break;
-        if (cycles >= c->max_cycles) {
+        // the same rule as k_check: the V-cycles of this outer step
+        const int need = adaptive ? 1 : (mixed ? c->inner : 1);
+        if (cycles + need > c->max_cycles) {
             set_err("not converged: rel residual %.3e after %d V-cycles", rel, cycles);
             st = MG_ERR_NOT_CONVERGED;
             break;
         }
+        int m_step = mixed ? c->inner : 1;
+        if (adaptive) {
+            m_step = adaptive_cycles(rel, tol, c->rho, c->adapt_max);
+            if (m_step > c->max_cycles - cycles) m_step = c->max_cycles - cycles;
+        }
         if (mixed) {
-            for (int k = 0; k < c->inner && cycles < c->max_cycles; ++k, ++cycles) {
+            for (int k = 0; k < m_step; ++k, ++cycles) {
                 mg_prolong pk = prolong;
                 if (use_policy) {
                     const bool sr = policy_use_sr(c->policy, cycles + 1, rel, true, fallback);
@@ -1668,7 +1768,7 @@ mg_status mg_set_tile_variant(int kind, int n, int nu, int variant) {
 }
 
 mg_status mg_probe_kernel(mg_ctx *c, int kind, int capacity) {
-    if (!c || kind < kProbeNone || kind > kProbeUpdate || capacity < 0 || capacity > 4096) {
+    if (!c || kind < kProbeNone || kind > kProbeCoarse || capacity < 0 || capacity > 4096) {
         set_err("invalid probe request");
         return MG_ERR_INVALID_ARG;
     }

@@ -261,7 +261,7 @@ struct DevState {
     int sr_used;      // V-cycles that used the SR prolongation
     int sr_step;      // the current outer step used it
     int fallback;     // SR stopped for this solve (an outer step with SR did not halve the residual)
-    int pad;
+    int m_next;       // V-cycles of the next outer step (adaptive inner cycles)
     double rel_prev;  // relative residual before the current outer step
 };
 
@@ -293,11 +293,34 @@ constexpr double kSrMinReduction = 0.5;
 cudaError_t launch_policy(DevState *st, int k, ProlongPolicy p, int *flag, cudaGraphConditionalHandle handle,
                           cudaStream_t s);
 
+// Adaptive inner cycles: the V-cycles of the next outer step, the smallest
+// m in [1, m_max] with rel * rho^m <= tol, rho the expected contraction per
+// V-cycle.  Multiplications only, so host and device take the same decision.
+__host__ __device__ inline int adaptive_cycles(double rel, double tol, double rho, int m_max) {
+    double r = rel;
+    int m = 0;
+    do {
+        r *= rho;
+        ++m;
+    } while (m < m_max && r > tol);
+    return m;
+}
+constexpr int kMaxAdaptive = 4;  // optional cycles are IF nodes 2 .. kMaxAdaptive of a graph body
+
+// Handles of the IF nodes around the optional V-cycles 2 .. m_max of an outer step.
+struct CycleHandles {
+    cudaGraphConditionalHandle h[kMaxAdaptive - 1];
+};
+
 // Convergence test of one outer step: reads the residual sums, updates the
-// state and sets the graph's loop condition (1 = run another step).
+// state and sets the graph's loop condition (1 = run another step).  With
+// rho > 0 the step just run had st->m_next cycles and the next one gets
+// adaptive_cycles(...) of them (IF handles 2 .. step set accordingly); with
+// rho = 0 every step has `step` cycles.
 cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
                          double n2, double h2, double tol, int step, int max_cycles, bool first,
-                         cudaGraphConditionalHandle handle, cudaStream_t s);
+                         cudaGraphConditionalHandle handle, cudaStream_t s, double rho = 0.0,
+                         CycleHandles ifh = CycleHandles{});
 
 // batched forms (float tile kernels; FP64 outer kernels)
 // every grid of one batched launch uses the same variant; nblocks = sum of variant_tiles

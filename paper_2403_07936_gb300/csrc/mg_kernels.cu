@@ -913,7 +913,7 @@ __global__ void __launch_bounds__(kRedThreads) k_project(double *__restrict__ x,
 
 __global__ void k_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
                         double n2, double h2, double tol, int step, int max_cycles, int first,
-                        cudaGraphConditionalHandle handle) {
+                        cudaGraphConditionalHandle handle, double rho, CycleHandles ifh) {
     pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (first) {
@@ -928,10 +928,11 @@ __global__ void k_check(DevState *st, const double *rsum, const double *usum, co
         st->sr_step = 0;
         st->fallback = 0;
     } else {
-        st->cycles += step;
+        st->cycles += rho > 0.0 ? st->m_next : step;
         st->outer += 1;
         if (usum) st->unorm = sqrt(usum[0]);
     }
+    int m = step;
     const double rn = sqrt(rsum[0]) / h2, fn = st->fnorm;
     unsigned go = 0;
     if (!isfinite(rn) || !isfinite(fn)) {
@@ -947,12 +948,24 @@ __global__ void k_check(DevState *st, const double *rsum, const double *usum, co
         st->rel_prev = rel;
         st->rel = rel;
         if (rel > tol) {
-            if (st->cycles + step <= max_cycles)
+            if (rho > 0.0) {
+                m = adaptive_cycles(rel, tol, rho, step);
+                if (st->cycles + 1 <= max_cycles) {
+                    go = 1;
+                    if (m > max_cycles - st->cycles) m = max_cycles - st->cycles;
+                } else {
+                    st->status = MG_ERR_NOT_CONVERGED;
+                }
+            } else if (st->cycles + step <= max_cycles) {
                 go = 1;
-            else
+            } else {
                 st->status = MG_ERR_NOT_CONVERGED;
+            }
         }
     }
+    st->m_next = m;
+    if (rho > 0.0)
+        for (int k = 2; k <= step && k <= kMaxAdaptive; ++k) cudaGraphSetConditional(ifh.h[k - 2], (go && m >= k) ? 1u : 0u);
     cudaGraphSetConditional(handle, go);
 }
 
@@ -1384,10 +1397,11 @@ cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, 
 
 cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
                          double n2, double h2, double tol, int step, int max_cycles, bool first,
-                         cudaGraphConditionalHandle handle, cudaStream_t s) {
+                         cudaGraphConditionalHandle handle, cudaStream_t s, double rho, CycleHandles ifh) {
     {
         cudaError_t le_ = launch_kernel(k_check, 1, 32, 0, s,
-                                        st, rsum, usum, fsum, n2, h2, tol, step, max_cycles, first ? 1 : 0, handle);
+                                        st, rsum, usum, fsum, n2, h2, tol, step, max_cycles, first ? 1 : 0, handle,
+                                        rho, ifh);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);

@@ -49,6 +49,7 @@ SIGNATURES = {
     "mg_setup": (_I, [_I, _I, C.POINTER(_VP)]),
     "mg_set_options": (_I, [_VP, _I, _I, _I, _I, _VP]),
     "mg_set_inner_cycles": (_I, [_VP, _I]),
+    "mg_set_adaptive_cycles": (_I, [_VP, _I, _D]),
     "mg_set_graph_execution": (_I, [_VP, _I]),
     "mg_set_prolong_policy": (_I, [_VP, _D, _D]),
     "mg_load_prolong_weights": (_I, [_VP, _VP, _SZ]),
@@ -200,6 +201,10 @@ class Context:
         if inner_cycles is not None:
             o.inner_cycles = inner_cycles
             _check(lib.mg_set_inner_cycles(self._h, inner_cycles))
+
+    def set_adaptive_cycles(self, m_max: int = 3, rho: float = 0.06):
+        """Adaptive V-cycles per outer step (mg_set_adaptive_cycles); rho = 0 turns it off."""
+        _check(load().mg_set_adaptive_cycles(self._h, m_max, rho))
 
     def set_prolong_policy(self, n_gan: float = float("inf"), s_thres: float = 0.0):
         """Hybrid SR / cubic choice per V-cycle for prolong="sr" solves (mg_set_prolong_policy)."""

@@ -217,3 +217,40 @@ def test_graph_and_host_loop_give_identical_results(mg):
     assert ia["vcycles"] == ib["vcycles"] and ia["outer_iters"] == ib["outer_iters"]
     # the graph adds one convergence-test kernel per residual evaluation
     assert la > 0 and lb == la + ib["outer_iters"] + 1
+
+
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
+def test_adaptive_inner_cycles(mg, graphs):
+    """Mixed cubic solves choose 1..3 V-cycles per outer step from the residual
+    (contraction 0.06 per V-cycle): the 2048^2 workload takes 3 outer steps
+    (3, 3 and 1 or 2 V-cycles) instead of 4 steps of 2; a fixed count restores
+    the old schedule; the solution meets the same bars."""
+    n = 2048
+    f = turbulent_source(n, 256, config_seed(1, 0))
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(9, n)
+    ctx.set_graph_execution(graphs)
+    xa = torch.zeros_like(ft)
+    ia = ctx.solve(ft, xa)
+    assert ia["outer_iters"] == 3 and ia["vcycles"] <= 8 and ia["rel_residual"] <= 1e-10
+    _check_solution(f, xa.cpu().numpy())
+    ctx.set_options(inner_cycles=2)
+    xf = torch.zeros_like(ft)
+    i2 = ctx.solve(ft, xf)
+    assert i2["outer_iters"] == 4 and i2["vcycles"] == 8 and i2["rel_residual"] <= 1e-10
+    ctx.set_adaptive_cycles(3, 0.06)
+    xb = torch.zeros_like(ft)
+    ib = ctx.solve(ft, xb)
+    assert torch.equal(xa, xb) and ib["vcycles"] == ia["vcycles"]
+
+
+def test_adaptive_cycles_respect_the_cycle_cap(mg):
+    n = 512
+    f = turbulent_source(n, 64, 5)
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(7, n, max_cycles=5)
+    for graphs in (True, False):
+        ctx.set_graph_execution(graphs)
+        x = torch.zeros_like(ft)
+        info = ctx.solve(ft, x, check=False)
+        assert info["status"] == "MG_ERR_NOT_CONVERGED" and info["vcycles"] == 5

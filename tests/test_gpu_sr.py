@@ -127,6 +127,7 @@ def test_sr_solve_with_zero_output_layer_equals_cubic(mg):
     ft = torch.tensor(f, device=DEV)
     ctx = mg.Context(6, n)
     ctx.load_weights(sr.pack_weights(w))
+    ctx.set_options(inner_cycles=2)  # SR solves use a fixed count; the cubic one then uses it too
     a = torch.zeros_like(ft)
     b = torch.zeros_like(ft)
     ia = ctx.solve(ft, a, prolong="cubic")
@@ -182,6 +183,7 @@ def _policy_solve(mg, n, blob, graphs, n_gan=float("inf"), s_thres=0.0, prolong=
     ft = torch.tensor(f, device=DEV)
     ctx = mg.Context(int(np.log2(n // 8)) + 1, n)
     ctx.set_graph_execution(graphs)
+    ctx.set_options(inner_cycles=2)  # the SR schedule, for cubic comparisons too
     ctx.load_weights(blob)
     ctx.set_prolong_policy(n_gan, s_thres)
     x = torch.zeros_like(ft)
