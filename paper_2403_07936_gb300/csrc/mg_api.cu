@@ -637,6 +637,10 @@ struct BatchPlan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long n_pro = 0, n_body = 0, n_epi = 0;
+    long long n_cyc = 0;   // kernels of one optional (conditional) batch V-cycle
+    int adapt_max = 0;     // adaptive inner cycles: optional cycles 2 .. adapt_max recorded
+    int *d_bm = nullptr;   // [0] next step's V-cycles, [1] V-cycles run (adaptive)
+    int h_bm[2] = {0, 0};
     unsigned epoch = 0;
     BatchRed red(int g) const { return BatchRed{d_partials, d_counters, d_out + (size_t)g * B * kMaxSlots}; }
     double *out(int g) const { return d_out + (size_t)g * B * kMaxSlots; }
@@ -730,7 +734,8 @@ static mg_status batch_build(BatchPlan *p) {
     const size_t o_part = o_active + al(sizeof(int) * B);
     const size_t o_out = o_part + al(sizeof(double) * kMaxSlots * blk);
     const size_t o_cnt = o_out + al(sizeof(double) * 4 * B * kMaxSlots);
-    const size_t total = o_cnt + al(sizeof(unsigned) * B);
+    const size_t o_bm = o_cnt + al(sizeof(unsigned) * B);
+    const size_t total = o_bm + al(2 * sizeof(int));
     MG_CUDA(cudaMalloc(&p->dmem, total));
     char *d = (char *)p->dmem;
     p->d_rhs = (RhsDesc *)(d + o_rhs);
@@ -741,6 +746,7 @@ static mg_status batch_build(BatchPlan *p) {
     p->d_partials = (double *)(d + o_part);
     p->d_out = (double *)(d + o_out);
     p->d_counters = (unsigned *)(d + o_cnt);
+    p->d_bm = (int *)(d + o_bm);
     MG_CUDA(cudaMemset(p->dmem, 0, total));
     MG_CUDA(cudaMemcpy(p->d_rhs, rhs.data(), sizeof(RhsDesc) * B, cudaMemcpyHostToDevice));
     if (!tiles.empty())
@@ -751,10 +757,16 @@ static mg_status batch_build(BatchPlan *p) {
 
     // record: prologue, WHILE(outer step), epilogue
     cudaStream_t s = p->cap;
-    const int step = c0->inner;
+    const bool adaptive = c0->rho > 0.0 && c0->adapt_max > 1;
+    const int step = adaptive ? c0->adapt_max : c0->inner;
+    const double rho = adaptive ? c0->rho : 0.0;
+    p->adapt_max = adaptive ? step : 0;
     cudaGraphConditionalHandle handle;
+    CycleHandles ifh{};
     MG_CUDA(cudaGraphCreate(&p->graph, 0));
     MG_CUDA(cudaGraphConditionalHandleCreate(&handle, p->graph, 0, cudaGraphCondAssignDefault));
+    for (int k = 2; adaptive && k <= step; ++k)
+        MG_CUDA(cudaGraphConditionalHandleCreate(&ifh.h[k - 2], p->graph, 0, cudaGraphCondAssignDefault));
     bool capturing = false;
     cudaError_t e = cudaSuccess;
     auto run_cycle = [&](int v) {
@@ -780,7 +792,7 @@ static mg_status batch_build(BatchPlan *p) {
             e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), true, nullptr, p->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), nullptr, p->out(kGrpF), p->tol, step,
-                                     c0->max_cycles, true, p->d_active, handle, true, s);
+                                     c0->max_cycles, true, p->d_active, handle, true, s, rho, ifh, p->d_bm);
         if (e != cudaSuccess) break;
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *deps = nullptr;
@@ -805,13 +817,49 @@ static mg_status batch_build(BatchPlan *p) {
         e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) break;
         capturing = true;
-        for (int k = 0; k < step; ++k) run_cycle(k == 0 ? 0 : 1);
+        if (adaptive) {
+            run_cycle(0);
+            for (int k = 2; k <= step && e == cudaSuccess; ++k) {  // optional cycles behind IF nodes
+                cudaStreamCaptureStatus cs2;
+                const cudaGraphNode_t *d2 = nullptr;
+                size_t nd2 = 0;
+                e = cudaStreamGetCaptureInfo(s, &cs2, nullptr, nullptr, &d2, nullptr, &nd2);
+                if (e != cudaSuccess) break;
+                std::vector<cudaGraphNode_t> t2(d2, d2 + nd2);
+                e = cudaStreamEndCapture(s, &body);
+                capturing = false;
+                if (e != cudaSuccess) break;
+                cudaGraphNodeParams ip = {};
+                ip.type = cudaGraphNodeTypeConditional;
+                ip.conditional.handle = ifh.h[k - 2];
+                ip.conditional.type = cudaGraphCondTypeIf;
+                ip.conditional.size = 1;
+                cudaGraphNode_t ifn;
+                e = cudaGraphAddNode(&ifn, body, t2.data(), nullptr, t2.size(), &ip);
+                if (e != cudaSuccess) break;
+                cudaGraph_t ib = ip.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(s, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) break;
+                capturing = true;
+                const long long lc = (long long)launches_total();
+                run_cycle(1);
+                p->n_cyc = (long long)launches_total() - lc;
+                cudaError_t e2 = cudaStreamEndCapture(s, &ib);
+                capturing = false;
+                if (e == cudaSuccess) e = e2;
+                if (e != cudaSuccess) break;
+                e = cudaStreamBeginCaptureToGraph(s, body, &ifn, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) capturing = true;
+            }
+        } else {
+            for (int k = 0; k < step; ++k) run_cycle(k == 0 ? 0 : 1);
+        }
         if (e == cudaSuccess) e = launch_update_batched(p->d_rhs, B, blk, p->d_active, p->red(kGrpU), s);
         if (e == cudaSuccess)
             e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), false, p->d_active, p->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), p->out(kGrpU), p->out(kGrpF), p->tol,
-                                     step, c0->max_cycles, false, p->d_active, handle, true, s);
+                                     step, c0->max_cycles, false, p->d_active, handle, true, s, rho, ifh, p->d_bm);
         if (e != cudaSuccess) break;
         e = cudaStreamEndCapture(s, &body);
         capturing = false;
@@ -867,6 +915,7 @@ static bool batch_eligible(mg_ctx *const *ctxs, const double *const *f, double *
         mg_ctx *c = ctxs[r];
         if (!c || !f[r] || !x[r] || c->prec != MG_PREC_MIXED || c->nu1 != c0->nu1 || c->nu2 != c0->nu2 ||
             c->inner != c0->inner || c->max_cycles != c0->max_cycles || c->device != c0->device ||
+            c->adapt_max != c0->adapt_max || c->rho != c0->rho ||
             !is_device_pointer(f[r]) || !is_device_pointer(x[r]))
             return false;
         for (int q = 0; q < r; ++q)
@@ -907,6 +956,7 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
     cudaStream_t s = c0->stream;
     MG_CUDA(cudaGraphLaunch(p->exec, s));
     MG_CUDA(cudaMemcpyAsync(p->h_state, p->d_state, sizeof(DevState) * B, cudaMemcpyDeviceToHost, s));
+    if (p->adapt_max > 0) MG_CUDA(cudaMemcpyAsync(p->h_bm, p->d_bm, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
     int outer_max = 0;
     mg_status worst = MG_OK;
@@ -927,7 +977,11 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
             infos[r].sr_cycles = 0;
         }
     }
-    count_launches(p->n_pro + (long long)outer_max * p->n_body + p->n_epi);
+    if (p->adapt_max > 0)  // optional V-cycles ran only in the steps that chose them
+        count_launches(p->n_pro + (long long)outer_max * p->n_body -
+                       ((long long)outer_max * p->adapt_max - p->h_bm[1]) * p->n_cyc + p->n_epi);
+    else
+        count_launches(p->n_pro + (long long)outer_max * p->n_body + p->n_epi);
     if (worst == MG_ERR_NONFINITE) set_err("non-finite residual in a batched right-hand side");
     if (worst == MG_ERR_NOT_CONVERGED) set_err("a batched right-hand side did not converge");
     return worst;

@@ -341,10 +341,12 @@ cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, con
                                    const DevState *st, cudaStream_t s);
 // first: every entry is at its first residual (else each entry's own flag);
 // use_handle: set the graph loop condition (inside a graph only)
+// rho > 0: adaptive inner cycles (batch_m: [0] the next step's V-cycles, [1] total run; ifh: IF handles)
 cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, const double *rsum,
                                  const double *usum, const double *fsum, double tol, int step, int max_cycles,
                                  bool first, int *active, cudaGraphConditionalHandle handle, bool use_handle,
-                                 cudaStream_t s);
+                                 cudaStream_t s, double rho = 0.0, CycleHandles ifh = CycleHandles{},
+                                 int *batch_m = nullptr);
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,

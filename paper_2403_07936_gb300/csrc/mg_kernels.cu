@@ -1110,10 +1110,22 @@ __global__ void __launch_bounds__(kRedThreads) k_project_b(const RhsDesc *__rest
 
 // Convergence test of every listed right-hand side still active (or at its
 // first residual); a graph loop continues while any is.  One block.
+// With rho > 0 (adaptive inner cycles) the batch's next outer step runs m
+// V-cycles, the largest adaptive_cycles(...) of its still-active right-hand
+// sides, capped by the smallest cycle budget left among them; batch_m[0] holds
+// the m of the step just run, batch_m[1] the V-cycles run so far.
 __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs, const double *rsum,
                           const double *usum, const double *fsum, double tol, int step, int max_cycles,
-                          int first_all, int *active, cudaGraphConditionalHandle handle, int use_handle) {
+                          int first_all, int *active, cudaGraphConditionalHandle handle, int use_handle,
+                          double rho, CycleHandles ifh, int *batch_m) {
     pdl_enter();
+    __shared__ int s_m, s_left;
+    if (threadIdx.x == 0) {
+        s_m = 1;
+        s_left = max_cycles;
+    }
+    __syncthreads();
+    const int m_prev = (rho > 0.0 && !first_all) ? batch_m[0] : step;
     int any = 0;
     for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
         const int slot = rd[r].slot;
@@ -1135,7 +1147,7 @@ __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs
             s.fallback = 0;
             s.rel_prev = 0.0;
         } else {
-            s.cycles += step;
+            s.cycles += m_prev;
             s.outer += 1;
             s.unorm = sqrt(usum[(size_t)slot * kMaxSlots]);
         }
@@ -1151,15 +1163,36 @@ __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs
             const double rel = rn / fn;
             s.rel = rel;
             if (rel > tol) {
-                if (s.cycles + step <= max_cycles) go = 1;
-                else s.status = MG_ERR_NOT_CONVERGED;
+                if (rho > 0.0) {
+                    if (s.cycles + 1 <= max_cycles) {
+                        go = 1;
+                        atomicMax(&s_m, adaptive_cycles(rel, tol, rho, step));
+                        atomicMin(&s_left, max_cycles - s.cycles);
+                    } else {
+                        s.status = MG_ERR_NOT_CONVERGED;
+                    }
+                } else if (s.cycles + step <= max_cycles) {
+                    go = 1;
+                } else {
+                    s.status = MG_ERR_NOT_CONVERGED;
+                }
             }
         }
         active[slot] = go;
         any |= go;
     }
     any = __syncthreads_or(any);
-    if (use_handle && threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        if (rho > 0.0) {
+            const int m = s_m < s_left ? s_m : s_left;
+            batch_m[0] = m;
+            if (first_all) batch_m[1] = 0;
+            if (any) batch_m[1] += m;
+            for (int k = 2; k <= step && k <= kMaxAdaptive; ++k)
+                cudaGraphSetConditional(ifh.h[k - 2], (any && m >= k) ? 1u : 0u);
+        }
+        if (use_handle) cudaGraphSetConditional(handle, any ? 1u : 0u);
+    }
 }
 
 template <typename KernelT>
@@ -1566,10 +1599,11 @@ cudaError_t launch_policy(DevState *st, int k, ProlongPolicy p, int *flag, cudaG
 cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, const double *rsum,
                                  const double *usum, const double *fsum, double tol, int step, int max_cycles,
                                  bool first, int *active, cudaGraphConditionalHandle handle, bool use_handle,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, double rho, CycleHandles ifh, int *batch_m) {
     {
         cudaError_t le_ = launch_kernel(k_check_b, 1, 256, 0, s,
-                                        st, rd, nrhs, rsum, usum, fsum, tol, step, max_cycles, first ? 1 : 0, active, handle, use_handle ? 1 : 0);
+                                        st, rd, nrhs, rsum, usum, fsum, tol, step, max_cycles, first ? 1 : 0, active, handle, use_handle ? 1 : 0,
+                                        rho, ifh, batch_m);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);

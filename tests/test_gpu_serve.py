@@ -84,7 +84,9 @@ def test_request_alone_equals_request_in_mix(mg):
         _check_exact(g, x.cpu().numpy())
 
     # the same request as a one-member batched solve: the same kernels and sums
+    # (the server runs a fixed 2 V-cycles per outer step)
     ctx = mg.Context(7, 512)
+    ctx.set_options(inner_cycles=2)
     xb = torch.zeros_like(ft)
     mg.solve_batched([ctx], [ft], [xb], tol=1e-10)
     assert torch.equal(alone, xb)
