@@ -170,7 +170,14 @@ typedef struct mg_server mg_server;
 
 /* Create a server on the current device.  hbm_budget_bytes bounds the device
  * memory of its slots, warm starts and tables; other arguments as for
- * mg_set_options.  Work is ordered on cuda_stream. */
+ * mg_set_options, except that inner_cycles = 0 (0 <= inner_cycles <= 16)
+ * selects adaptive V-cycles per outer step: a request's first step runs 3,
+ * each later one the count mg_set_adaptive_cycles' rule (m_max 3, rho 0.06)
+ * gives for the relative residual the request is predicted to have, i.e. its
+ * last measured one times its own observed contraction per V-cycle to the
+ * power of the V-cycles run since; the count depends only on the request's
+ * own history, never on the rest of the batch.  Work is ordered on
+ * cuda_stream. */
 mg_status mg_server_create(size_t hbm_budget_bytes, int nu_pre, int nu_post, int inner_cycles, int max_cycles,
                            double tol, void *cuda_stream, mg_server **out);
 

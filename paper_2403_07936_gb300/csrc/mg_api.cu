@@ -1010,6 +1010,12 @@ struct ServerSlot {
     int stream_id = -1;
     double *x_out = nullptr;
     double t_submit = 0.0, t_admit = 0.0;
+    // adaptive inner cycles: what the host knows of this request's progress
+    int m_last = 0;          // V-cycles of its last outer step
+    int cycles_run = 0;      // V-cycles scheduled so far
+    int nrel = 0;            // relative residuals seen (start of each of its ticks)
+    double rel1 = 0.0, rel2 = 0.0;  // the last two of them (rel1 newest)
+    int m2 = 0;              // V-cycles between rel2 and rel1
 };
 struct ServerRequest {
     long long id;
@@ -1024,6 +1030,9 @@ struct mg_server {
     cudaStream_t stream = nullptr;
     size_t budget = 0, used = 0;
     int nu1 = 2, nu2 = 2, inner = 2, max_cycles = 100;
+    bool adaptive = false;  // inner_cycles = 0 at creation: per-slot adaptive V-cycles
+    int m_max = 3;
+    double rho = 0.06;
     double tol = 1e-10;
     std::vector<ServerSlot> slots;
     std::vector<ServerRequest> queue;  // FIFO
@@ -1167,6 +1176,8 @@ static mg_status server_admit(mg_server *sv) {
         sl.x_out = rq.x_out;
         sl.t_submit = rq.t_submit;
         sl.t_admit = sv->now_ms();
+        sl.m_last = sl.cycles_run = sl.nrel = sl.m2 = 0;
+        sl.rel1 = sl.rel2 = 0.0;
         ++sv->qhead;
     }
     if (sv->qhead == sv->queue.size()) {
@@ -1182,7 +1193,7 @@ struct TickPlan {
     std::vector<RhsDesc> rhs, firsts, dones;
     std::vector<TileGrid> tiles;
     std::vector<BottomGrid> bottoms;
-    std::vector<BatchLaunch> cyc[2];
+    std::vector<BatchLaunch> cyc[kMaxAdaptive > 2 ? kMaxAdaptive : 2];
     int blk = 0, blk_first = 0, blk_done = 0;
 };
 
@@ -1191,19 +1202,25 @@ static void plan_rhs(std::vector<RhsDesc> &v, int &blk, const ServerSlot &sl, in
     const double h = 2.0 * 3.14159265358979323846 / n;
     int nblk = (int)(((size_t)n * n) / 16384);
     nblk = nblk < 1 ? 1 : (nblk > kRedBlocks ? kRedBlocks : nblk);
-    v.push_back(RhsDesc{sl.f, sl.x, sl.ctx->lv[0].b32, sl.ctx->lv[0].x32, n, blk, nblk, sid, sl.first ? 1 : 0, 0,
-                        h * h});
+    v.push_back(RhsDesc{sl.f, sl.x, sl.ctx->lv[0].b32, sl.ctx->lv[0].x32, n, blk, nblk, sid, sl.first ? 1 : 0,
+                        sl.first ? 0 : sl.m_last, h * h});
     blk += nblk;
 }
 
-static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sids) {
-    int maxN = 0;
-    for (int sid : sids) maxN = sv->slots[sid].N > maxN ? sv->slots[sid].N : maxN;
-    for (int v = 0; v < 2; ++v) {
+// V-cycle k (0-based) of this tick runs for the slots with m[slot] > k; cycle 0
+// starts the finest level from zero.
+static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sids, const std::vector<int> &m) {
+    int maxN = 0, maxm = 0;
+    for (int sid : sids) {
+        maxN = sv->slots[sid].N > maxN ? sv->slots[sid].N : maxN;
+        maxm = m[sid] > maxm ? m[sid] : maxm;
+    }
+    for (int v = 0; v < maxm; ++v) {
         const bool first = v == 0;
         for (int sz = maxN; sz > kBottomMax; sz >>= 1) {
             BatchLaunch L{0, tp.tiles.size(), 0, 0, tile_variant(0, sz, sv->nu1)};
             for (int sid : sids) {
+                if (m[sid] <= v) continue;
                 mg_ctx *c = sv->slots[sid].ctx;
                 for (int l = 0; l + 1 < c->levels; ++l)
                     if (c->lv[l].n == sz) {
@@ -1217,6 +1234,7 @@ static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sid
         }
         BatchLaunch Lb{2, tp.bottoms.size(), 0, 0, 0};
         for (int sid : sids) {
+            if (m[sid] <= v) continue;
             mg_ctx *c = sv->slots[sid].ctx;
             int l = 0;
             while (c->lv[l].n > kBottomMax) ++l;
@@ -1225,10 +1243,11 @@ static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sid
             ++Lb.ngrid;
         }
         Lb.nblocks = Lb.ngrid;
-        tp.cyc[v].push_back(Lb);
+        if (Lb.ngrid) tp.cyc[v].push_back(Lb);
         for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {
             BatchLaunch L{1, tp.tiles.size(), 0, 0, tile_variant(1, sz, sv->nu2)};
             for (int sid : sids) {
+                if (m[sid] <= v) continue;
                 mg_ctx *c = sv->slots[sid].ctx;
                 for (int l = 0; l + 1 < c->levels; ++l)
                     if (c->lv[l].n == sz) {
@@ -1241,6 +1260,27 @@ static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sid
             if (L.ngrid) tp.cyc[v].push_back(L);
         }
     }
+}
+
+// V-cycles of a slot's next outer step.  Fixed: the server's count.  Adaptive:
+// the rule of single solves, applied to the relative residual the slot is
+// predicted to have now (its latest residual times the contraction it showed
+// over its previous step, or rho, to the power of its last step's V-cycles),
+// capped by the cycles it has left.  Only the slot's own history enters, so a
+// request's schedule does not depend on the other requests in flight.
+static int server_cycles(const mg_server *sv, const ServerSlot &sl) {
+    if (!sv->adaptive) return sv->inner;
+    int m = sv->m_max;
+    if (!sl.first && sl.nrel >= 1) {
+        double rho = sv->rho;
+        if (sl.nrel >= 2 && sl.m2 > 0 && sl.rel2 > 0.0 && sl.rel1 > 0.0 && sl.rel1 < sl.rel2)
+            rho = pow(sl.rel1 / sl.rel2, 1.0 / sl.m2);
+        double pred = sl.rel1;
+        for (int k = 0; k < sl.m_last; ++k) pred *= rho;
+        m = adaptive_cycles(pred, sv->tol, sv->rho, sv->m_max);
+    }
+    const int left = sv->max_cycles - sl.cycles_run;
+    return m < left ? (m > 0 ? m : 1) : (left > 0 ? left : 1);
 }
 
 // Copy the plan's tables to the device in one transfer; returns device pointers.
@@ -1286,7 +1326,9 @@ static mg_status server_tick(mg_server *sv, int *n_active, int *n_queued, int *n
         }
     int finished = 0;
     if (!sids.empty()) {
-        plan_cycles(sv, tp, sids);
+        std::vector<int> m(sv->slots.size(), 0);
+        for (int sid : sids) m[sid] = server_cycles(sv, sv->slots[sid]);
+        plan_cycles(sv, tp, sids, m);
         RhsDesc *d_rhs, *d_first;
         TileGrid *d_tiles;
         BottomGrid *d_bottom;
@@ -1296,10 +1338,11 @@ static mg_status server_tick(mg_server *sv, int *n_active, int *n_queued, int *n
             MG_CUDA(launch_sum_batched(d_first, (int)tp.firsts.size(), tp.blk_first, false, sv->red(kGrpF), s));
         MG_CUDA(launch_outer_residual_batched(d_rhs, nr, tp.blk, sv->out(kGrpF), true, nullptr, sv->red(kGrpR), s));
         MG_CUDA(launch_check_batched(sv->d_state, d_rhs, nr, sv->out(kGrpR), sv->out(kGrpU), sv->out(kGrpF), sv->tol,
-                                     sv->inner, sv->max_cycles, false, sv->d_active, cudaGraphConditionalHandle(), false,
-                                     s));
-        for (int k = 0; k < sv->inner; ++k)
-            for (const BatchLaunch &L : tp.cyc[k == 0 ? 0 : 1]) {
+                                     sv->adaptive ? 1 : sv->inner, sv->max_cycles, false, sv->d_active,
+                                     cudaGraphConditionalHandle(), false, s));
+        const int ncyc = sv->adaptive ? sv->m_max : sv->inner;
+        for (int k = 0; k < ncyc; ++k)
+            for (const BatchLaunch &L : tp.cyc[sv->adaptive ? k : (k == 0 ? 0 : 1)]) {
                 if (L.kind == 0)
                     MG_CUDA(launch_down_batched(d_tiles + L.off, L.ngrid, L.nblocks, sv->nu1, sv->d_active, s,
                                                 L.variant));
@@ -1318,6 +1361,13 @@ static mg_status server_tick(mg_server *sv, int *n_active, int *n_queued, int *n
         std::vector<int> retire;
         for (int sid : sids) {
             ServerSlot &sl = sv->slots[sid];
+            // bookkeeping of the adaptive rule: the residual at this tick's start
+            sl.rel2 = sl.rel1;
+            sl.m2 = sl.m_last;
+            sl.rel1 = sv->h_state[sid].rel;
+            sl.nrel += 1;
+            sl.m_last = m[sid];
+            sl.cycles_run += m[sid];
             sl.first = false;
             if (!sv->h_active[sid]) retire.push_back(sid);
         }
@@ -1869,7 +1919,7 @@ mg_status mg_probe_read(mg_ctx *c, int *launches, double *total_ms, double *byte
 mg_status mg_server_create(size_t hbm_budget_bytes, int nu_pre, int nu_post, int inner_cycles, int max_cycles,
                            double tol, void *cuda_stream, mg_server **out) {
     if (out) *out = nullptr;
-    if (!out || nu_pre < 0 || nu_pre > 4 || nu_post < 0 || nu_post > 4 || inner_cycles < 1 || inner_cycles > 16 ||
+    if (!out || nu_pre < 0 || nu_pre > 4 || nu_post < 0 || nu_post > 4 || inner_cycles < 0 || inner_cycles > 16 ||
         max_cycles < 1 || !(tol >= 0.0)) {
         set_err("invalid server options");
         return MG_ERR_INVALID_ARG;
@@ -1882,7 +1932,8 @@ mg_status mg_server_create(size_t hbm_budget_bytes, int nu_pre, int nu_post, int
     sv->budget = hbm_budget_bytes;
     sv->nu1 = nu_pre;
     sv->nu2 = nu_post;
-    sv->inner = inner_cycles;
+    sv->inner = inner_cycles > 0 ? inner_cycles : 2;
+    sv->adaptive = inner_cycles == 0;
     sv->max_cycles = max_cycles;
     sv->tol = tol;
     sv->slots.resize(kServerSlots);

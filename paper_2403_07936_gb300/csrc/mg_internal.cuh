@@ -176,7 +176,7 @@ struct RhsDesc {  // FP64 outer kernels: blocks [blk0, blk0 + nblk) serve this r
     int n, blk0, nblk;
     int slot;        // index of its persistent state, sums and active flag
     int first;       // this step is its first residual evaluation
-    int pad;
+    int m_prev;      // V-cycles it ran in the previous outer step (0: the launch's common count)
     double h2;
 };
 struct BatchRed {

@@ -1147,7 +1147,7 @@ __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs
             s.fallback = 0;
             s.rel_prev = 0.0;
         } else {
-            s.cycles += m_prev;
+            s.cycles += rd[r].m_prev > 0 ? rd[r].m_prev : m_prev;
             s.outer += 1;
             s.unorm = sqrt(usum[(size_t)slot * kMaxSlots]);
         }

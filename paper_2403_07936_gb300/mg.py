@@ -264,10 +264,12 @@ class Server:
     submit() queues a request; tick() admits what fits the memory budget, runs
     one outer defect-correction step for every admitted request and retires
     the converged ones; poll() returns retired requests.  The caller keeps f
-    (and x_out) alive until the request has retired.
+    (and x_out) alive until the request has retired.  inner_cycles = 0 (the
+    default) picks each request's V-cycles per step adaptively from its own
+    residual history.
     """
 
-    def __init__(self, hbm_budget_bytes: int, nu_pre: int = 2, nu_post: int = 2, inner_cycles: int = 2,
+    def __init__(self, hbm_budget_bytes: int, nu_pre: int = 2, nu_post: int = 2, inner_cycles: int = 0,
                  max_cycles: int = 100, tol: float = 1e-10, stream=None):
         h = C.c_void_p()
         _check(load().mg_server_create(int(hbm_budget_bytes), nu_pre, nu_post, inner_cycles, max_cycles, tol,

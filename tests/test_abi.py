@@ -66,7 +66,8 @@ def test_weights_blob_layout_matches_generator_shapes():
 
 
 @pytest.mark.parametrize("args", [(1 << 30, -1, 2, 2, 10, 1e-10), (1 << 30, 2, 5, 2, 10, 1e-10),
-                                  (1 << 30, 2, 2, 0, 10, 1e-10), (1 << 30, 2, 2, 2, 0, 1e-10),
+                                  (1 << 30, 2, 2, -1, 10, 1e-10), (1 << 30, 2, 2, 17, 10, 1e-10),
+                                  (1 << 30, 2, 2, 2, 0, 1e-10),
                                   (1 << 30, 2, 2, 2, 10, float("nan"))])
 def test_server_create_rejects_invalid_options(lib, args):
     h = C.c_void_p(123)

@@ -1,12 +1,13 @@
 """Continuous-batching server (GPU).
 
 Requests of mixed sizes join and leave the running batch between ticks.  Each
-request runs the same batched kernels with its own reduction layout, so its
-result does not depend on what else is in flight: a request served alone and
-the same request served inside a mix of arrivals give identical bits, and both
-equal a one-request batched solve.  Every result is also checked against the
-exact FFT solution (|x - x_exact|_inf <= 1e-9 |x_exact|_inf) and for its own
-relative residual.
+request runs the same batched kernels with its own reduction layout, and with
+adaptive V-cycles a count chosen from its own residuals alone, so its result
+does not depend on what else is in flight: a request served alone and the
+same request served inside a mix of arrivals give identical bits, and with a
+fixed count both equal a one-request batched solve.  Every result is also
+checked against the exact FFT solution (|x - x_exact|_inf <= 1e-9
+|x_exact|_inf) and for its own relative residual.
 """
 import numpy as np
 import pytest
@@ -48,11 +49,12 @@ def _check_exact(f, x):
     assert omg.relative_residual(f - f.mean(), x, omg.grid_h(f.shape[0])) <= 1.5e-10
 
 
-def test_request_alone_equals_request_in_mix(mg):
+@pytest.mark.parametrize("inner", [0, 2])  # adaptive, fixed V-cycles per outer step
+def test_request_alone_equals_request_in_mix(mg, inner):
     f = _src(512, 0)
     ft = torch.tensor(f, device=DEV)
     alone = torch.zeros_like(ft)
-    srv = mg.Server(8 * GB)
+    srv = mg.Server(8 * GB, inner_cycles=inner)
     srv.submit(ft, alone)
     res = _drain(srv)
     assert len(res) == 1 and res[0]["status"] == 0
@@ -62,7 +64,7 @@ def test_request_alone_equals_request_in_mix(mg):
     ots = [torch.tensor(g, device=DEV) for g in others]
     oxs = [torch.zeros_like(t) for t in ots]
     mixed = torch.full_like(ft, float("nan"))
-    srv = mg.Server(8 * GB)
+    srv = mg.Server(8 * GB, inner_cycles=inner)
     srv.submit(ots[0], oxs[0])
     srv.submit(ots[1], oxs[1])
     srv.tick()
@@ -83,8 +85,9 @@ def test_request_alone_equals_request_in_mix(mg):
     for g, x in zip(others, oxs):
         _check_exact(g, x.cpu().numpy())
 
+    if inner == 0:
+        return
     # the same request as a one-member batched solve: the same kernels and sums
-    # (the server runs a fixed 2 V-cycles per outer step)
     ctx = mg.Context(7, 512)
     ctx.set_options(inner_cycles=2)
     xb = torch.zeros_like(ft)
@@ -151,7 +154,8 @@ def test_failures_retire_with_status_and_do_not_disturb_others(mg):
     assert res[ig]["status"] == 0 and res[ib]["status"] == 8  # MG_ERR_NONFINITE
     _check_exact(good, gx.cpu().numpy())
     srv.close()
-    # a cycle cap below what the tolerance needs: MG_ERR_NOT_CONVERGED with the best x so far
+    # a cycle cap below what the tolerance needs: MG_ERR_NOT_CONVERGED with the
+    # best x so far (adaptive: 3 V-cycles, then the 1 left)
     srv = mg.Server(4 * GB, max_cycles=4)
     x = torch.zeros_like(gt)
     srv.submit(gt, x)
