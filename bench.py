@@ -35,12 +35,13 @@ TOL = 1e-10
 METRIC = "solves/s to ||r||/||f||<=1e-10, mixed vs FP64 V-cycle; serve p50/p99 ms"
 WORKLOAD = ("2048^2 periodic pressure-Poisson -Lap_h p = f (5-point, h = 2pi/2048), 9 levels to 8^2, "
             "V(2,2) red-black Gauss-Seidel, full weighting, periodic cubic-spline prolongation, exact "
-            "8^2 coarse solve; FP32 V-cycles (2 per outer step) in FP64 defect correction; "
+            "8^2 coarse solve; FP32 V-cycles (1 to 3 per outer step, adaptive) in FP64 defect correction; "
             "tol ||r||/||f|| <= 1e-10; seeded k^-5/3 turbulent source, 1 <= k <= 256")
-# algorithmic bytes per grid point of each probed kernel kind
+# kernels the library's probe can time (mg_probe_kernel kinds); the library
+# credits each timed launch with its algorithmic bytes
 PROBE_NAMES = {1: "k_down<float,2> (finest: 2 RB-GS sweeps + residual + FW)",
                2: "k_up<float,2> (finest: cubic prolongation + correction + 2 RB-GS sweeps)",
-               3: "k_outer_residual<f64> (FP64 residual, norms, float conversion)",
+               3: "k_outer_residual (binary64 operands, exact integer stencil sum, one rounding to float, norms)",
                4: "k_update (FP64 x += e)",
                5: "coarse levels (1024^2 down to the bottom kernel and back, one span per V-cycle)"}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -91,16 +92,11 @@ def kernel_source_sha():
     return h.hexdigest()
 
 
-# FP64 FLOPs per point of the outer residual: 3 adds (neighbour sum), 4x - sum
-# (2), f - mean (1), h^2 (f - mean) - (.) (2); its norm runs in FP32.
-OUTER_FP64_FLOP_PER_POINT = 8
-FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64, nominal
-
 
 def kernel_roofline(kind, n_l, ms, nbytes, peak, peak_src):
     """Roofline of one probed kernel kind: launches n_l, total ms, algorithmic bytes.
-    The stencils are bounded by memory (HBM peak); the FP64 outer residual by the
-    FP64 pipe (FLOPs against the nominal FP64 peak)."""
+    Every probed kernel is bounded by memory (HBM peak): the FP32 stencils, and
+    the outer residual, whose exact stencil sum runs on the integer pipe."""
     if not n_l:
         return None
     us = ms / n_l * 1e3
@@ -111,18 +107,9 @@ def kernel_roofline(kind, n_l, ms, nbytes, peak, peak_src):
                      "peak": None, "frac": None,
                      "note": "a span of 9 launches per V-cycle on grids of 1024^2 and less; its bytes fit L2"})
         return base
-    if kind == 3:
-        flops = OUTER_FP64_FLOP_PER_POINT * N * N
-        ach = flops / (us * 1e-6) / 1e12
-        base.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach / FP64_PEAK_TFLOPS,
-                     "peak_source": "nominal dense FP64 of GB300 (no measured FP64 peak on this pool)",
-                     "note": "FP64-pipe bound (ncu: 81% of the FP64 pipe busy); 4 of its 6 FP64 "
-                             "instructions per point are adds, counted as 1 FLOP each"})
-    else:
-        ach = (nbytes / n_l) / (us * 1e-6) / 1e9
-        base.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                     "peak_source": f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if peak_src == 'measured' else 'recipe fallback'})"})
+    ach = (nbytes / n_l) / (us * 1e-6) / 1e9
+    base.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                 "peak_source": f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if peak_src == 'measured' else 'recipe fallback'})"})
     return base
 
 

@@ -372,9 +372,15 @@ mg_status mg_op_sr_conv(int mode, int H, int W, const void *in, const void *skip
  * context's stream. */
 mg_status mg_op_sr_generator(mg_ctx *ctx, const float *ec, int nc, float *out);
 
-/* FP64 outer residual: s = h^2 (f - mu) - (4x - sum nbrs) (so s = h^2 r),
- * written as float to s32 when s32 != NULL; out[0] = sum s^2,
- * out[1] = sum (f - mu)^2 (out: 2 doubles, device). */
+/* Outer residual of FP64 data: s = b - (4x - sum nbrs) with b = h^2 (f - mu)
+ * formed in FP64 (so s = h^2 r), written as float to s32 when s32 != NULL;
+ * out[0] = sum s^2, out[1] = sum (f - mu)^2 (out: 2 doubles, device).  The
+ * stencil sum is exact on the integer pipe and rounded once to float: for
+ * n >= 32 with s32, the solver's task-tiled kernel (operands aligned to the
+ * largest exponent of the point's 32-column x 8-row task, error under
+ * 10 * 2^-59 of that task's largest operand before the rounding); otherwise
+ * each point's six operands are aligned to their own largest exponent (error
+ * under 6 * 2^-59 of it).  An infinite or NaN operand gives NaN. */
 mg_status mg_op_outer_residual(int n, const double *f, const double *x, double mu, float *s32,
                                double *out, void *stream);
 

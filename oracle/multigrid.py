@@ -67,6 +67,26 @@ def residual(f: np.ndarray, x: np.ndarray, h: float) -> np.ndarray:
     return f - apply_A(x, h)
 
 
+def scaled_residual_exact(b: np.ndarray, x: np.ndarray) -> list:
+    """Exact scaled residual b - (4 x - sum of the 4 periodic neighbours) of
+    binary64 grids b and x (Algorithm 6's residual step in the scaled form
+    h^2 f - h^2 A x), as Python Fractions: every binary64 value is a dyadic
+    rational, so nothing is rounded.  Returned as a list of rows.  Slow; for
+    small grids.  It fixes the value that any evaluation of the residual in
+    finite precision approximates."""
+    from fractions import Fraction
+    n = x.shape[0]
+    X = [[Fraction(float(v)) for v in row] for row in x]
+    out = []
+    for i in range(n):
+        row = []
+        for j in range(n):
+            nb = X[(i - 1) % n][j] + X[(i + 1) % n][j] + X[i][(j - 1) % n] + X[i][(j + 1) % n]
+            row.append(Fraction(float(b[i, j])) - (4 * X[i][j] - nb))
+        out.append(row)
+    return out
+
+
 def red_mask(n: int) -> np.ndarray:
     """Boolean mask of red points, (i + j) even."""
     i = np.arange(n)

@@ -141,6 +141,10 @@ struct mg_ctx {
     cudaStream_t stream = nullptr;
     Level lv[kMaxLevels];
     void *h32_block = nullptr, *h64_block = nullptr;
+    // scaled right-hand side h^2 (f - mu) of the finest level, FP64, written by
+    // each solve's first outer residual (mixed contexts; FP64 ones use lv[0].b64)
+    double *bsc64 = nullptr;
+    int *ebt = nullptr;  // per residual task of the finest grid: bsc64's alignment exponent (N >= kResMinN)
     float *ainv32 = nullptr;
     double *ainv64 = nullptr;
     FirTaps taps;
@@ -218,6 +222,11 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
         const size_t nn = (size_t)c->lv[l].n * c->lv[l].n;
         total += 3 * align_up(nn * es);
     }
+    const size_t bsc_off = total;
+    if (!fp64) total += align_up((size_t)c->N * c->N * sizeof(double));
+    const size_t ebt_off = total;
+    const bool tasks = !fp64 && c->N >= kResMinN;
+    if (tasks) total += align_up(res_tasks(c->N) * sizeof(int));
     MG_CUDA(cudaMalloc(&blk, total));
     MG_CUDA(cudaMemsetAsync(blk, 0, total, c->stream));
     char *p = (char *)blk;
@@ -235,7 +244,25 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
         }
         p += 3 * bytes;
     }
+    if (!fp64) c->bsc64 = (double *)((char *)blk + bsc_off);
+    if (tasks) c->ebt = (int *)((char *)blk + ebt_off);
     return MG_OK;
+}
+
+// The finest level's scaled right-hand side buffer of a solve.
+static double *scaled_rhs(mg_ctx *c, bool mixed) { return mixed ? c->bsc64 : c->lv[0].b64; }
+
+// The outer residual of a solve on stream s.  The solve's first evaluation
+// (first) sums (f - mu)^2 and stores b = h^2 (f - mu); later ones load b.
+// Mixed solves of N >= kResMinN use the task-tiled kernel (b stored aligned).
+static cudaError_t solve_residual(mg_ctx *c, const double *fd, const double *xd, bool mixed, bool first,
+                                  double h2, cudaStream_t s) {
+    const int N = c->N;
+    if (mixed && N >= kResMinN)
+        return launch_outer_residual_tasks(fd, xd, N, h2, c->out(kGrpF), 0.0, c->lv[0].b32, first,
+                                           reinterpret_cast<long long *>(c->bsc64), c->ebt, c->red(kGrpR), s);
+    return launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr, first,
+                                 scaled_rhs(c, mixed), !first, c->red(kGrpR), s);
 }
 
 template <typename T> static T *lvx(mg_ctx *c, int l);
@@ -437,10 +464,8 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
         if (e != cudaSuccess) { fail(e, "begin prologue"); break; }
         capturing = true;
         e = launch_source_sum(fd, N, c->red(kGrpF), s);
-        if (e == cudaSuccess && !mixed) e = launch_scaled_rhs(fd, N, h2, c->out(kGrpF), c->lv[0].b64, s);
-        if (e == cudaSuccess)
-            e = launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
-                                      true, c->red(kGrpR), s);
+        // the first residual also stores the scaled right-hand side b = h^2 (f - mu)
+        if (e == cudaSuccess) e = solve_residual(c, fd, xd, mixed, true, h2, s);
         if (e == cudaSuccess)
             e = launch_check(c->dstate, c->out(kGrpR), nullptr, c->out(kGrpF), N2, h2, tol, step,
                              c->max_cycles, true, handle, s, rho, ifh);
@@ -523,9 +548,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
             st = vcycle_rec<double>(c, 0, xd, c->lv[0].t64, c->lv[0].b64, false);
             if (st != MG_OK) break;
         }
-        if (e == cudaSuccess)
-            e = launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
-                                      false, c->red(kGrpR), s);
+        if (e == cudaSuccess) e = solve_residual(c, fd, xd, mixed, false, h2, s);
         if (e == cudaSuccess)
             e = launch_check(c->dstate, c->out(kGrpR), mixed ? c->out(kGrpU) : nullptr, c->out(kGrpF),
                              N2, h2, tol, step, c->max_cycles, false, handle, s, rho, ifh);
@@ -673,7 +696,8 @@ static mg_status batch_build(BatchPlan *p) {
         const double h = 2.0 * 3.14159265358979323846 / n;
         int nblk = (int)(((size_t)n * n) / 16384);
         nblk = nblk < 1 ? 1 : (nblk > kRedBlocks ? kRedBlocks : nblk);
-        rhs[r] = RhsDesc{p->f[r], p->x[r], c->lv[0].b32, c->lv[0].x32, n, blk, nblk, r, 0, 0, h * h};
+        rhs[r] = RhsDesc{p->f[r], p->x[r], c->lv[0].b32, c->lv[0].x32, c->bsc64, c->ebt, n, blk, nblk, r, 0, 0,
+                         h * h};
         blk += nblk;
         maxN = n > maxN ? n : maxN;
     }
@@ -789,7 +813,7 @@ static mg_status batch_build(BatchPlan *p) {
         capturing = true;
         e = launch_sum_batched(p->d_rhs, B, blk, false, p->red(kGrpF), s);
         if (e == cudaSuccess)
-            e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), true, nullptr, p->red(kGrpR), s);
+            e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), true, true, nullptr, p->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), nullptr, p->out(kGrpF), p->tol, step,
                                      c0->max_cycles, true, p->d_active, handle, true, s, rho, ifh, p->d_bm);
@@ -856,7 +880,8 @@ static mg_status batch_build(BatchPlan *p) {
         }
         if (e == cudaSuccess) e = launch_update_batched(p->d_rhs, B, blk, p->d_active, p->red(kGrpU), s);
         if (e == cudaSuccess)
-            e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), false, p->d_active, p->red(kGrpR), s);
+            e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), false, false, p->d_active,
+                                              p->red(kGrpR), s);
         if (e == cudaSuccess)
             e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), p->out(kGrpU), p->out(kGrpF), p->tol,
                                      step, c0->max_cycles, false, p->d_active, handle, true, s, rho, ifh, p->d_bm);
@@ -1061,7 +1086,8 @@ struct mg_server {
 };
 
 static size_t server_slot_bytes(int N) {
-    size_t b = 2ull * N * N * sizeof(double);  // f, x
+    size_t b = 3ull * N * N * sizeof(double);  // f, x, scaled right-hand side
+    if (N >= kResMinN) b += res_tasks(N) * sizeof(int);
     for (int n = N; n >= 8; n >>= 1) b += 3ull * n * n * sizeof(float);
     return b;
 }
@@ -1202,7 +1228,8 @@ static void plan_rhs(std::vector<RhsDesc> &v, int &blk, const ServerSlot &sl, in
     const double h = 2.0 * 3.14159265358979323846 / n;
     int nblk = (int)(((size_t)n * n) / 16384);
     nblk = nblk < 1 ? 1 : (nblk > kRedBlocks ? kRedBlocks : nblk);
-    v.push_back(RhsDesc{sl.f, sl.x, sl.ctx->lv[0].b32, sl.ctx->lv[0].x32, n, blk, nblk, sid, sl.first ? 1 : 0,
+    v.push_back(RhsDesc{sl.f, sl.x, sl.ctx->lv[0].b32, sl.ctx->lv[0].x32, sl.ctx->bsc64, sl.ctx->ebt, n, blk, nblk, sid,
+                        sl.first ? 1 : 0,
                         sl.first ? 0 : sl.m_last, h * h});
     blk += nblk;
 }
@@ -1336,7 +1363,8 @@ static mg_status server_tick(mg_server *sv, int *n_active, int *n_queued, int *n
         const int nr = (int)tp.rhs.size();
         if (!tp.firsts.empty())
             MG_CUDA(launch_sum_batched(d_first, (int)tp.firsts.size(), tp.blk_first, false, sv->red(kGrpF), s));
-        MG_CUDA(launch_outer_residual_batched(d_rhs, nr, tp.blk, sv->out(kGrpF), true, nullptr, sv->red(kGrpR), s));
+        MG_CUDA(launch_outer_residual_batched(d_rhs, nr, tp.blk, sv->out(kGrpF), true, false, nullptr,
+                                              sv->red(kGrpR), s));
         MG_CUDA(launch_check_batched(sv->d_state, d_rhs, nr, sv->out(kGrpR), sv->out(kGrpU), sv->out(kGrpF), sv->tol,
                                      sv->adaptive ? 1 : sv->inner, sv->max_cycles, false, sv->d_active,
                                      cudaGraphConditionalHandle(), false, s));
@@ -1649,7 +1677,6 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     }
 
     MG_CUDA(launch_source_sum(fd, N, c->red(kGrpF), s));
-    if (!mixed) MG_CUDA(launch_scaled_rhs(fd, N, h2, c->out(kGrpF), c->lv[0].b64, s));
 
     mg_status st = MG_OK;
     int cycles = 0, outer = 0;
@@ -1663,9 +1690,9 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     double rel_prev = 0.0;
     for (;;) {
         probe_begin(c, kProbeResidual);
-        MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr,
-                                      first, c->red(kGrpR), s));
-        probe_end(c, kProbeResidual, N2 * (16.0 + (mixed ? 4.0 : 0.0)));
+        // the first residual computes and stores b = h^2 (f - mu), later ones load it
+        MG_CUDA(solve_residual(c, fd, xd, mixed, first, h2, s));
+        probe_end(c, kProbeResidual, N2 * ((first ? 24.0 : 16.0) + (mixed ? 4.0 : 0.0)));
         MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 2 * kMaxSlots,
                                 cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
@@ -1764,7 +1791,7 @@ mg_status mg_vcycle(mg_ctx *c, const double *f, double *x, mg_prolong prolong) {
     cudaStream_t s = c->stream;
     MG_CUDA(launch_source_sum(fd, N, c->red(kGrpF), s));
     if (mixed) {
-        MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, c->lv[0].b32, false,
+        MG_CUDA(launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, c->lv[0].b32, false, nullptr, false,
                                       c->red(kGrpR), s));
         MG_TRY(vcycle32_top(c, true, prolong));
         MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
@@ -2149,16 +2176,26 @@ mg_status mg_op_outer_residual(int n, const double *f, const double *x, double m
     }
     double *partials = nullptr;
     unsigned *counter = nullptr;
+    long long *bint = nullptr;
+    int *ebt = nullptr;
+    const bool tasks = s32 && n >= kResMinN;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMalloc(&partials, sizeof(double) * kMaxSlots * kRedBlocks);
     if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(unsigned));
+    if (e == cudaSuccess && tasks) e = cudaMalloc(&bint, sizeof(long long) * n * n);
+    if (e == cudaSuccess && tasks) e = cudaMalloc(&ebt, sizeof(int) * res_tasks(n));
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     const double h = 2.0 * 3.14159265358979323846 / n;
     if (e == cudaSuccess)
-        e = launch_outer_residual(f, x, n, h * h, nullptr, mu, s32, true, Reduction{partials, counter, out}, s);
+        e = tasks ? launch_outer_residual_tasks(f, x, n, h * h, nullptr, mu, s32, true, bint, ebt,
+                                                Reduction{partials, counter, out}, s)
+                  : launch_outer_residual(f, x, n, h * h, nullptr, mu, s32, true, nullptr, false,
+                                          Reduction{partials, counter, out}, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(partials);
     cudaFree(counter);
+    cudaFree(bint);
+    cudaFree(ebt);
     MG_CUDA(e);
     return MG_OK;
 }

@@ -91,6 +91,85 @@ __device__ __forceinline__ float f64_to_f32_rn(double v) {
 }
 
 // ----------------------------------------------------------------------------
+// Exact outer residual on the integer pipe.  The scaled residual
+// s = b - 4x + xN + xS + xW + xE of six binary64 operands is summed exactly in
+// a 64-bit integer and rounded once to binary32 (nearest, ties to even), the
+// precision the inner V-cycles take it in.  Each operand's 53-bit significand
+// is aligned so that the largest operand's leading bit sits at bit 59 (the
+// centre's exponent is raised by 2 for the factor 4, which is exact) and the
+// others are shifted right by their exponent difference; six such terms stay
+// below 2^63.  Only bits more than 59 places below the largest operand's
+// leading bit are dropped, so before the final rounding the sum is within
+// 6 * 2^-59 of the largest operand: tighter than any evaluation of the same
+// sum in binary64 arithmetic, whose every addition may err by 2^-53 of its
+// result.  An infinite or NaN operand gives NaN.
+// ----------------------------------------------------------------------------
+struct ExactOperand {
+    unsigned long long m;  // significand, hidden bit included
+    int e;                 // biased exponent (1 for zeros and subnormals) plus log2 of the factor
+    unsigned neg;          // sign of the term
+    bool special;          // infinity or NaN
+};
+
+__device__ __forceinline__ ExactOperand exact_operand(double v, int log2_factor, unsigned negate) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(u >> 32);
+    const int ef = (int)((hi >> 20) & 0x7ffu);
+    ExactOperand o;
+    o.m = (u & 0x000fffffffffffffull) | (ef ? (1ull << 52) : 0ull);
+    o.e = (ef ? ef : 1) + log2_factor;
+    o.neg = (hi >> 31) ^ negate;
+    o.special = ef == 0x7ff;
+    return o;
+}
+
+// The operand's significand in units of 2^(emax - 1082), truncated, signed.
+__device__ __forceinline__ long long exact_term(const ExactOperand &o, int emax) {
+    const int d = min(emax - o.e, 63);
+    const long long a = (long long)((o.m << 7) >> d);
+    return o.neg ? -a : a;
+}
+
+// The binary32 nearest to acc * 2^(emax - 1082).
+__device__ __forceinline__ float exact_to_f32(long long acc, int emax) {
+    if (acc == 0) return 0.0f;
+    const unsigned sign = acc < 0 ? 0x80000000u : 0u;
+    const unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
+    const int t = 63 - __clzll((long long)a);  // a in [2^t, 2^(t+1))
+    int bf = t + emax - 955;                     // biased binary32 exponent of the value
+    // bits to drop: down to a 24-bit significand, or to units of 2^-149 (subnormal)
+    const int sh = bf >= 1 ? t - 23 : 933 - emax;
+    unsigned long long q;
+    if (sh <= 0) {
+        q = a << (-sh);
+    } else if (sh >= 64) {
+        q = 0ull;  // a < 2^63: below half a unit
+    } else {
+        q = a >> sh;
+        const unsigned long long r = a - (q << sh), half = 1ull << (sh - 1);
+        q += (r > half || (r == half && (q & 1ull))) ? 1ull : 0ull;
+    }
+    if (bf < 1) return __uint_as_float(sign | (unsigned)q);  // a carry into bit 23 is the smallest normal
+    if (q >> 24) {
+        q >>= 1;
+        ++bf;
+    }
+    if (bf >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)bf << 23) | ((unsigned)q & 0x7fffffu));
+}
+
+__device__ __forceinline__ float residual_exact_f32(double b, double x, double xn, double xs, double xw,
+                                                    double xe) {
+    const ExactOperand o0 = exact_operand(b, 0, 0u), o1 = exact_operand(x, 2, 1u), o2 = exact_operand(xn, 0, 0u),
+                       o3 = exact_operand(xs, 0, 0u), o4 = exact_operand(xw, 0, 0u), o5 = exact_operand(xe, 0, 0u);
+    if (o0.special | o1.special | o2.special | o3.special | o4.special | o5.special) return __uint_as_float(0x7fc00000u);
+    const int emax = max(max(max(o0.e, o1.e), max(o2.e, o3.e)), max(o4.e, o5.e));
+    const long long acc = ((exact_term(o0, emax) + exact_term(o1, emax)) + (exact_term(o2, emax) + exact_term(o3, emax))) +
+                          (exact_term(o4, emax) + exact_term(o5, emax));
+    return exact_to_f32(acc, emax);
+}
+
+// ----------------------------------------------------------------------------
 // Deterministic two-stage reductions: each block writes one partial (fixed
 // order inside the block), the last block to finish sums the partials in
 // index order and resets the arrival counter.  `nslot` independent sums.
@@ -173,6 +252,9 @@ struct RhsDesc {  // FP64 outer kernels: blocks [blk0, blk0 + nblk) serve this r
     double *x;
     float *s32;      // float residual (inner right-hand side)
     const float *e;  // inner correction
+    double *bsc;     // scaled right-hand side h^2 (f - mu), written by its first residual
+                     // (n >= kResMinN: as aligned int64 per residual task, see k_outer_residual_t)
+    int *ebt;        // per residual task: the exponent bsc's integers are aligned to
     int n, blk0, nblk;
     int slot;        // index of its persistent state, sums and active flag
     int first;       // this step is its first residual evaluation
@@ -333,8 +415,12 @@ cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int
 // sums of f (of_x = false) or of x (of_x = true) per right-hand side -> red.out[r][0]
 cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of_x, BatchRed red,
                                cudaStream_t s);
+// want_fnorm: the right-hand sides at their first residual (all with
+// first_all, else those whose descriptor says first) compute b = h^2 (f - mu)
+// in FP64, store it to bsc and sum (f - mu)^2; all others load b from bsc.
 cudaError_t launch_outer_residual_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *fsum,
-                                          bool want_fnorm, const int *active, BatchRed red, cudaStream_t s);
+                                          bool want_fnorm, bool first_all, const int *active, BatchRed red,
+                                          cudaStream_t s);
 cudaError_t launch_update_batched(const RhsDesc *rd, int nrhs, int nblocks, const int *active, BatchRed red,
                                   cudaStream_t s);
 cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *xsum,
@@ -351,9 +437,25 @@ cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, cons
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,
                               double *b, cudaStream_t s);
+// Task-tiled outer residual of mixed solves (grids of n >= kResMinN): each
+// warp takes tasks of 32 columns x kResRows rows and aligns all of a task's
+// operands to one exponent, the task's largest.  The first residual of a
+// solve computes b = h^2 (f - mu) and stores it as int64 aligned to the
+// task's largest b exponent (bint, with that exponent in ebt[task]); later
+// residuals load it.  ebt holds res_tasks(n) entries.
+constexpr int kResRows = 8;
+constexpr int kResMinN = 32;
+inline size_t res_tasks(int n) { return (size_t)(n / 32) * (size_t)(n / kResRows); }
+cudaError_t launch_outer_residual_tasks(const double *f, const double *x, int n, double h2, const double *mu_sum,
+                                        double mu_host, float *s32, bool first, long long *bint, int *ebt,
+                                        Reduction red, cudaStream_t s);
+
+// Scaled outer residual.  b = h^2 (f - mu) is computed from f in FP64 (and
+// stored to bsc when bsc is given), or with load_b taken from bsc as an
+// earlier call stored it; the stencil sum is exact (residual_exact_f32).
 cudaError_t launch_outer_residual(const double *f, const double *x, int n, double h2,
                                   const double *mu_sum, double mu_host, float *s32,
-                                  bool want_fnorm, Reduction red, cudaStream_t s);
+                                  bool want_fnorm, double *bsc, bool load_b, Reduction red, cudaStream_t s);
 cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaStream_t s);
 // x -= sum / n^2, or x = 0 where *zero_flag is set (zero_flag may be null)
 cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s,

@@ -812,34 +812,48 @@ __global__ void __launch_bounds__(kRedThreads) k_scaled_rhs(const double *__rest
         b[p] = h2 * (f[p] - mu);
 }
 
-// residual_norm_note: the residual itself is FP64 (it decides the accuracy of
-// the solution), but its norm only decides when to stop and is reported to
-// the user: each thread sums the squares of its float-rounded residuals in
-// FP32 (tens of terms, relative error ~1e-6) and the block and grid sums run
-// in FP64.  A relative residual of 1e-10 is therefore known to ~6 digits.
+// residual_norm_note: the residual itself is exact before its rounding to
+// float (it decides the accuracy of the solution), but its norm only decides
+// when to stop and is reported to the user: each thread sums the squares of
+// its float residuals in FP32 (tens of terms, relative error ~1e-6) and the
+// block and grid sums run in FP64.  A relative residual of 1e-10 is therefore
+// known to ~6 digits.
 //
-// Scaled FP64 residual at point p = i * n + j of the periodic grid (n = 2^lg):
-// s = h^2 (f - mu) - (4 x - (((x_N + x_S) + x_W) + x_E)).  fc = f - mu.
-__device__ __forceinline__ double residual_at(const double *__restrict__ f, const double *__restrict__ x,
-                                              size_t p, int n, int lg, double h2, double mu, double *fc) {
+// Scaled residual at point p = i * n + j of the periodic grid (n = 2^lg):
+// s = b - (4 x - (x_N + x_S + x_W + x_E)), b = h^2 (f - mu), the stencil sum
+// exact on the integer pipe (residual_exact_f32).  BMODE 0: b from f;
+// 1: from f and stored to bsc; 2: loaded from bsc.  fc = f - mu (modes 0, 1).
+template <int BMODE>
+__device__ __forceinline__ float outer_point(const double *__restrict__ f, double *__restrict__ bsc,
+                                             const double *__restrict__ x, size_t p, int n, int lg, double h2,
+                                             double mu, double *fc) {
     const int i = (int)(p >> lg), j = (int)(p & (size_t)(n - 1));
     const size_t row = p - (size_t)j;
     const size_t up = (size_t)((i - 1) & (n - 1)) << lg, dn = (size_t)((i + 1) & (n - 1)) << lg;
-    const double nb = ((x[up + j] + x[dn + j]) + x[row + ((j - 1) & (n - 1))]) + x[row + ((j + 1) & (n - 1))];
-    *fc = f[p] - mu;
-    return h2 * *fc - (4.0 * x[p] - nb);
+    double b;
+    if (BMODE == 2) {
+        b = bsc[p];
+        *fc = 0.0;
+    } else {
+        *fc = f[p] - mu;
+        b = h2 * *fc;
+        if (BMODE == 1) bsc[p] = b;
+    }
+    return residual_exact_f32(b, x[p], x[up + j], x[dn + j], x[row + ((j - 1) & (n - 1))],
+                              x[row + ((j + 1) & (n - 1))]);
 }
 
-template <bool WRITE32, bool FNORM>
+template <bool WRITE32, bool FNORM, int BMODE>
 __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
     const double *__restrict__ f, const double *__restrict__ x, int n, double h2,
-    const double *__restrict__ fsum, double mu_host, float *__restrict__ s32, Reduction red) {
+    const double *__restrict__ fsum, double mu_host, float *__restrict__ s32, double *__restrict__ bsc,
+    Reduction red) {
     pdl_enter();
     __shared__ double sh[32];
     const size_t N = (size_t)n * n;
     const int lg = __ffs(n) - 1;
     const double mu = fsum ? *fsum / (double)N : mu_host;
-    float ss = 0.f;  // squares of the float-rounded residual, FP32 per thread (see residual_norm_note)
+    float ss = 0.f;  // squares of the float residual, FP32 per thread (see residual_norm_note)
     double ff = 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < N; p0 += 2 * stride) {
@@ -848,7 +862,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
             const size_t p = p0 + u * stride;
             if (p < N) {
                 double fc;
-                const float sv = f64_to_f32_rn(residual_at(f, x, p, n, lg, h2, mu, &fc));
+                const float sv = outer_point<BMODE>(f, bsc, x, p, n, lg, h2, mu, &fc);
                 ss = fmaf(sv, sv, ss);
                 if (FNORM) ff += fc * fc;
                 if (WRITE32) s32[p] = sv;
@@ -858,6 +872,131 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
     double vals[2];
     vals[0] = block_sum((double)ss, sh);
     vals[1] = FNORM ? block_sum(ff, sh) : 0.0;
+    reduce_finish<2>(red, vals, sh);
+}
+
+// ---------------------------------------------------------------------------
+// Task-tiled outer residual (mixed solves).  A warp task is 32 columns (one per
+// lane) x kResRows rows.  residual_exact_f32 aligns six operands per point;
+// here each x value is aligned once, to the task's exponent
+// E = max(largest x exponent + 2, largest b exponent), and reaches its four
+// neighbours through registers (north, south) and shuffles (west, east; the
+// task's two halo columns are held by lanes 0..kResRows-1 and 16..).  Every
+// term is then a multiple of 2^(E - 1082): |b| < 2^60, |4x| and each
+// neighbour < 2^58 (E >= x exponent + 2), so the int64 sum cannot overflow.
+// Truncation leaves each x within one unit (4x within four) and b within two
+// (its stored alignment, then the shift), under 10 units = 10 * 2^-59 of the
+// task's largest operand in all; the sum is then rounded once to binary32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned hi_abs(double v) {
+    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+}
+
+// v as a multiple of 2^(E - 1082), truncated toward zero (E >= v's biased exponent).
+__device__ __forceinline__ long long align_to(double v, int E) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(u >> 32);
+    const int ef = (int)((hi >> 20) & 0x7ffu);
+    const unsigned long long m = (u & 0x000fffffffffffffull) | (ef ? (1ull << 52) : 0ull);
+    const long long a = (long long)((m << 7) >> min(E - (ef ? ef : 1), 63));
+    return (hi >> 31) ? -a : a;
+}
+
+// acc * 2^(E - 1082) rounded once to binary32.  The conversion rounds acc to
+// 24 bits and the power-of-two scale (an exponent-field add) is exact while
+// the result is a normal float; exact_to_f32 takes the other cases.
+__device__ __forceinline__ float aligned_to_f32(long long acc, int E) {
+    const float v = __ll2float_rn(acc);
+    const int ev = (int)((__float_as_uint(v) >> 23) & 0xffu);
+    if (ev == 0) return 0.0f;  // acc == 0 (a nonzero integer converts to a normal float)
+    const int k = E - 1082, er = ev + k;
+    if (er >= 1 && er <= 254) return __uint_as_float(__float_as_uint(v) + ((unsigned)k << 23));
+    return exact_to_f32(acc, E);
+}
+
+template <bool FIRST>
+__device__ __forceinline__ void residual_task(int task, int n, int lg, const double *__restrict__ f, double mu,
+                                              double h2, long long *__restrict__ bint, int *__restrict__ ebt,
+                                              const double *__restrict__ x, float *__restrict__ s32, float &ss,
+                                              double &ff) {
+    constexpr int R = kResRows;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int strips = n >> 5;
+    const int c0 = (task % strips) << 5, r0 = (task / strips) * R;
+    const int c = c0 + lane;
+    double xv[R + 2];  // rows r0 - 1 .. r0 + R of column c
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) xv[k] = x[((size_t)((r0 - 1 + k) & (n - 1)) << lg) + c];
+    // halo columns: lane k < R holds x[r0 + k][c0 - 1], lane 16 + k holds x[r0 + k][c0 + 32]
+    const int hk = lane & 15;
+    double hv = 0.0;
+    if (hk < R) hv = x[((size_t)(r0 + hk) << lg) + ((lane < 16 ? c0 - 1 : c0 + 32) & (n - 1))];
+    long long bq[R];
+    int eb;
+    if (FIRST) {
+        double bv[R];
+        unsigned hb = 0u;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const double fc = f[((size_t)(r0 + k) << lg) + c] - mu;
+            ff += fc * fc;
+            bv[k] = h2 * fc;
+            hb = max(hb, hi_abs(bv[k]));
+        }
+        eb = max((int)(__reduce_max_sync(kFull, hb) >> 20), 1);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            bq[k] = align_to(bv[k], eb);
+            bint[((size_t)(r0 + k) << lg) + c] = bq[k];
+        }
+        if (lane == 0) ebt[task] = eb;
+    } else {
+        eb = ebt[task];
+#pragma unroll
+        for (int k = 0; k < R; ++k) bq[k] = bint[((size_t)(r0 + k) << lg) + c];
+    }
+    unsigned hx = hi_abs(hv);
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) hx = max(hx, hi_abs(xv[k]));
+    const int ex = max((int)(__reduce_max_sync(kFull, hx) >> 20), 1);
+    const bool special = ex == 0x7ff || eb == 0x7ff;  // an infinity or NaN in the task
+    const int E = max(ex + 2, eb);
+    const int bs = min(E - eb, 63);
+    long long X[R + 2];
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) X[k] = align_to(xv[k], E);
+    const long long H = align_to(hv, E);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const long long C = X[k + 1];
+        long long W = __shfl_up_sync(kFull, C, 1), Ea = __shfl_down_sync(kFull, C, 1);
+        const long long hW = __shfl_sync(kFull, H, k), hE = __shfl_sync(kFull, H, 16 + k);
+        if (lane == 0) W = hW;
+        if (lane == 31) Ea = hE;
+        const long long acc = ((bq[k] >> bs) - C * 4) + ((X[k] + X[k + 2]) + (W + Ea));
+        const float sv = special ? __uint_as_float(0x7fc00000u) : aligned_to_f32(acc, E);
+        ss = fmaf(sv, sv, ss);
+        s32[((size_t)(r0 + k) << lg) + c] = sv;
+    }
+}
+
+template <bool FIRST>
+__global__ void __launch_bounds__(kRedThreads) k_outer_residual_t(
+    const double *__restrict__ f, const double *__restrict__ x, int n, double h2, const double *__restrict__ fsum,
+    double mu_host, float *__restrict__ s32, long long *__restrict__ bint, int *__restrict__ ebt, Reduction red) {
+    pdl_enter();
+    __shared__ double sh[32];
+    const int lg = __ffs(n) - 1;
+    const double mu = fsum ? *fsum / ((double)n * n) : mu_host;
+    float ss = 0.f;  // squares of the float residual, FP32 per thread (see residual_norm_note)
+    double ff = 0.0;
+    const int ntask = (n >> 5) * (n / kResRows), wpb = blockDim.x >> 5;
+    for (int t = blockIdx.x * wpb + (int)(threadIdx.x >> 5); t < ntask; t += gridDim.x * wpb)
+        residual_task<FIRST>(t, n, lg, f, mu, h2, bint, ebt, x, s32, ss, ff);
+    double vals[2];
+    vals[0] = block_sum((double)ss, sh);
+    vals[1] = FIRST ? block_sum(ff, sh) : 0.0;
     reduce_finish<2>(red, vals, sh);
 }
 
@@ -1034,19 +1173,11 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_b(const RhsDesc *__restrict
     batch_finish<1>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
 
-template <bool FNORM>
-__global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc *__restrict__ rd, int nrhs,
-                                                                  const double *__restrict__ fsum,
-                                                                  const int *__restrict__ active, BatchRed red) {
-    pdl_enter();
-    __shared__ double sh[32];
-    const RhsDesc d = rd[find_rhs(rd, nrhs)];
-    if (active && !active[d.slot]) return;
+// One right-hand side's points of a batched outer residual (see outer_point).
+template <int BMODE>
+__device__ __forceinline__ void outer_rows_b(const RhsDesc &d, double mu, float &ss, double &ff) {
     const int n = d.n, lg = __ffs(n) - 1;
     const size_t N = (size_t)n * n;
-    const double mu = fsum[(size_t)d.slot * kMaxSlots] / (double)N;
-    float ss = 0.f;
-    double ff = 0.0;
     const size_t stride = (size_t)d.nblk * blockDim.x;
     for (size_t p0 = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p0 < N; p0 += 2 * stride) {
 #pragma unroll
@@ -1054,12 +1185,42 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc 
             const size_t p = p0 + u * stride;
             if (p < N) {
                 double fc;
-                const float sv = f64_to_f32_rn(residual_at(d.f, d.x, p, n, lg, d.h2, mu, &fc));
+                const float sv = outer_point<BMODE>(d.f, d.bsc, d.x, p, n, lg, d.h2, mu, &fc);
                 ss = fmaf(sv, sv, ss);
-                if (FNORM) ff += fc * fc;
+                if (BMODE == 1) ff += fc * fc;
                 d.s32[p] = sv;
             }
         }
+    }
+}
+
+template <bool FNORM>
+__global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc *__restrict__ rd, int nrhs,
+                                                                  const double *__restrict__ fsum, int first_all,
+                                                                  const int *__restrict__ active, BatchRed red) {
+    pdl_enter();
+    __shared__ double sh[32];
+    const RhsDesc d = rd[find_rhs(rd, nrhs)];
+    if (active && !active[d.slot]) return;
+    const size_t N = (size_t)d.n * d.n;
+    const double mu = fsum[(size_t)d.slot * kMaxSlots] / (double)N;
+    float ss = 0.f;
+    double ff = 0.0;
+    const bool fresh = FNORM && (first_all || d.first);
+    if (d.n >= kResMinN) {
+        const int n = d.n, lg = __ffs(n) - 1, wpb = blockDim.x >> 5;
+        const int ntask = (n >> 5) * (n / kResRows);
+        long long *bint = reinterpret_cast<long long *>(d.bsc);
+        for (int t = (blockIdx.x - d.blk0) * wpb + (int)(threadIdx.x >> 5); t < ntask; t += d.nblk * wpb) {
+            if (fresh)
+                residual_task<true>(t, n, lg, d.f, mu, d.h2, bint, d.ebt, d.x, d.s32, ss, ff);
+            else
+                residual_task<false>(t, n, lg, d.f, mu, d.h2, bint, d.ebt, d.x, d.s32, ss, ff);
+        }
+    } else if (fresh) {
+        outer_rows_b<1>(d, mu, ss, ff);
+    } else {
+        outer_rows_b<2>(d, mu, ss, ff);
     }
     double vals[2];
     vals[0] = block_sum((double)ss, sh);
@@ -1367,36 +1528,46 @@ cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f
     count_launches(1);
     return cudaGetLastError();
 }
+namespace {
+template <bool WRITE32, bool FNORM, int BMODE>
+cudaError_t outer_residual_impl(const double *f, const double *x, int n, double h2, const double *mu_sum,
+                                double mu_host, float *s32, double *bsc, Reduction red, cudaStream_t s) {
+    return launch_kernel(k_outer_residual<WRITE32, FNORM, BMODE>, kRedBlocks, kRedThreads, 0, s, f, x, n, h2,
+                         mu_sum, mu_host, s32, bsc, red);
+}
+template <bool WRITE32>
+cudaError_t outer_residual_w(const double *f, const double *x, int n, double h2, const double *mu_sum,
+                             double mu_host, float *s32, bool want_fnorm, double *bsc, bool load_b, Reduction red,
+                             cudaStream_t s) {
+    if (load_b) return outer_residual_impl<WRITE32, false, 2>(f, x, n, h2, mu_sum, mu_host, s32, bsc, red, s);
+    if (want_fnorm)
+        return bsc ? outer_residual_impl<WRITE32, true, 1>(f, x, n, h2, mu_sum, mu_host, s32, bsc, red, s)
+                   : outer_residual_impl<WRITE32, true, 0>(f, x, n, h2, mu_sum, mu_host, s32, bsc, red, s);
+    return bsc ? outer_residual_impl<WRITE32, false, 1>(f, x, n, h2, mu_sum, mu_host, s32, bsc, red, s)
+               : outer_residual_impl<WRITE32, false, 0>(f, x, n, h2, mu_sum, mu_host, s32, bsc, red, s);
+}
+}  // namespace
+
 cudaError_t launch_outer_residual(const double *f, const double *x, int n, double h2,
                                   const double *mu_sum, double mu_host, float *s32,
-                                  bool want_fnorm, Reduction red, cudaStream_t s) {
-    if (s32) {
-        if (want_fnorm)
-            {
-                cudaError_t le_ = launch_kernel(k_outer_residual<true, true>, kRedBlocks, kRedThreads, 0, s,
-                                                f, x, n, h2, mu_sum, mu_host, s32, red);
-                if (le_ != cudaSuccess) return le_;
-            }
-        else
-            {
-                cudaError_t le_ = launch_kernel(k_outer_residual<true, false>, kRedBlocks, kRedThreads, 0, s,
-                                                f, x, n, h2, mu_sum, mu_host, s32, red);
-                if (le_ != cudaSuccess) return le_;
-            }
-    } else {
-        if (want_fnorm)
-            {
-                cudaError_t le_ = launch_kernel(k_outer_residual<false, true>, kRedBlocks, kRedThreads, 0, s,
-                                                f, x, n, h2, mu_sum, mu_host, s32, red);
-                if (le_ != cudaSuccess) return le_;
-            }
-        else
-            {
-                cudaError_t le_ = launch_kernel(k_outer_residual<false, false>, kRedBlocks, kRedThreads, 0, s,
-                                                f, x, n, h2, mu_sum, mu_host, s32, red);
-                if (le_ != cudaSuccess) return le_;
-            }
-    }
+                                  bool want_fnorm, double *bsc, bool load_b, Reduction red, cudaStream_t s) {
+    if (load_b && (!bsc || want_fnorm)) return cudaErrorInvalidValue;
+    const cudaError_t e = s32 ? outer_residual_w<true>(f, x, n, h2, mu_sum, mu_host, s32, want_fnorm, bsc, load_b, red, s)
+                              : outer_residual_w<false>(f, x, n, h2, mu_sum, mu_host, s32, want_fnorm, bsc, load_b, red, s);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_outer_residual_tasks(const double *f, const double *x, int n, double h2, const double *mu_sum,
+                                        double mu_host, float *s32, bool first, long long *bint, int *ebt,
+                                        Reduction red, cudaStream_t s) {
+    if (n < kResMinN || !s32 || !bint || !ebt) return cudaErrorInvalidValue;
+    const cudaError_t e =
+        first ? launch_kernel(k_outer_residual_t<true>, kRedBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
+                              s32, bint, ebt, red)
+              : launch_kernel(k_outer_residual_t<false>, kRedBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
+                              s32, bint, ebt, red);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1547,17 +1718,19 @@ cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of
 }
 
 cudaError_t launch_outer_residual_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *fsum,
-                                          bool want_fnorm, const int *active, BatchRed red, cudaStream_t s) {
+                                          bool want_fnorm, bool first_all, const int *active, BatchRed red,
+                                          cudaStream_t s) {
+    const int fa = first_all ? 1 : 0;
     if (want_fnorm)
         {
             cudaError_t le_ = launch_kernel(k_outer_residual_b<true>, nblocks, kRedThreads, 0, s,
-                                            rd, nrhs, fsum, active, red);
+                                            rd, nrhs, fsum, fa, active, red);
             if (le_ != cudaSuccess) return le_;
         }
     else
         {
             cudaError_t le_ = launch_kernel(k_outer_residual_b<false>, nblocks, kRedThreads, 0, s,
-                                            rd, nrhs, fsum, active, red);
+                                            rd, nrhs, fsum, fa, active, red);
             if (le_ != cudaSuccess) return le_;
         }
     count_launches(1);

@@ -14,6 +14,8 @@ ops:
   outer  FP64 outer residual with norms and FP32 conversion
   conv   one tensor-core SR convolution layer (mode 0: conv + PReLU) on an
          n/2 x n/2 coarse grid of 64 channels
+  solve  a whole mixed-precision solve of a seeded turbulent source (host-loop
+         execution, so every kernel is a separate launch); time per solve
 """
 from __future__ import annotations
 
@@ -28,7 +30,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["down", "up", "outer", "conv"], required=True)
+    ap.add_argument("--op", choices=["down", "up", "outer", "conv", "solve"], required=True)
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
@@ -62,6 +64,18 @@ def main():
 
         def run():
             mg.op_outer_residual(f, x, 0.0, s32, out)
+    elif args.op == "solve":
+        import math
+
+        from synthetic.sources import default_kmax, turbulent_source
+        ctx = mg.Context(int(math.log2(n // 8)) + 1, n)
+        ctx.set_graph_execution(False)
+        f = torch.tensor(turbulent_source(n, default_kmax(n), 1), device=dev)
+        x = torch.zeros_like(f)
+
+        def run():
+            x.zero_()
+            ctx.solve(f, x)
     else:
         H = W = n // 2
         xin = torch.randn((H + 2, W + 2, 64), device=dev, generator=g).to(torch.bfloat16)

@@ -1,4 +1,4 @@
-"""Operator-level parity of the CUDA kernels against the FP64 oracle (GPU).
+"""Operator-level parity of the CUDA kernels against the oracle (GPU).
 
 Each C-ABI operator entry point runs the production kernel on one grid; the
 oracle runs the same step in FP64 with mesh width 1, which is exactly the
@@ -150,6 +150,70 @@ def test_outer_residual_matches_oracle(mg):
     terms = -(-(n * n) // (RED_BLOCKS * RED_THREADS))
     assert abs(o[0] - np.sum(s_ref ** 2)) <= (2.0 ** -23 + terms * 2.0 ** -24) * np.sum(s_ref ** 2)
     assert abs(o[1] - np.sum((f - mu) ** 2)) <= 1e-12 * np.sum((f - mu) ** 2)
+
+
+def _exact_residual_inputs(case, n):
+    rng = np.random.default_rng({"wide": 21, "cancelling": 22, "subnormal": 23}[case])
+    h2 = omg.grid_h(n) ** 2
+    if case == "wide":  # operands spread over 2^-30 .. 2^30, both signs
+        x = rng.choice([-1.0, 1.0], (n, n)) * 2.0 ** rng.uniform(-30, 30, (n, n))
+        f = rng.standard_normal((n, n)) * 2.0 ** rng.uniform(-10, 40, (n, n))
+    elif case == "cancelling":  # b = 4x - sum to binary64 rounding: the residual is the rounding
+        j = np.arange(n) * omg.grid_h(n)
+        x = 1e6 * np.sin(j)[:, None] * np.cos(2 * j)[None, :] + rng.uniform(-1e-3, 1e-3, (n, n))
+        f = (4.0 * x - omg.neighbour_sum(x)) / h2
+    else:  # residuals in binary32's subnormal range
+        x = rng.standard_normal((n, n)) * 1e-39
+        f = rng.standard_normal((n, n)) * 1e-40 / h2
+    return f, x, h2 * f  # b = h^2 (f - mu) with mu = 0, as the kernel forms it
+
+
+def _task_max_operand(b, x, rows=8, cols=32):
+    """Largest operand magnitude, max(4|x|, |b|), over each point's residual task:
+    the task-tiled kernel's tiling of 32 columns x 8 rows, with the x rows just
+    above and below it and the x columns just left and right of it."""
+    n = x.shape[0]
+    m = np.empty((n, n))
+    for r0 in range(0, n, rows):
+        for c0 in range(0, n, cols):
+            rr = np.arange(r0 - 1, r0 + rows + 1) % n
+            xs = np.abs(x[np.ix_(rr, np.arange(c0, c0 + cols))]).max()
+            halo = np.abs(x[np.ix_(np.arange(r0, r0 + rows), [(c0 - 1) % n, (c0 + cols) % n])]).max()
+            bs = np.abs(b[r0:r0 + rows, c0:c0 + cols]).max()
+            m[r0:r0 + rows, c0:c0 + cols] = max(4 * xs, 4 * halo, bs)
+    return m
+
+
+@pytest.mark.parametrize("case", ["wide", "cancelling", "subnormal"])
+def test_outer_residual_is_exact_before_its_float_rounding(mg, case):
+    """The outer residual sums its binary64 operands exactly, as 64-bit integers
+    aligned to the largest exponent of the point's task (32 columns x 8 rows),
+    and rounds once to float: within 10 * 2^-59 of the task's largest operand,
+    plus half a float ulp, of the exact rational residual.  In the cancelling
+    case binary64 evaluation itself misses that bound."""
+    from fractions import Fraction
+    n = 32
+    f, x, b = _exact_residual_inputs(case, n)
+    s32 = torch.empty((n, n), dtype=torch.float32, device=DEV)
+    out = torch.zeros(2, dtype=torch.float64, device=DEV)
+    mg.op_outer_residual(torch.tensor(f, device=DEV), torch.tensor(x, device=DEV), 0.0, s32, out)
+    torch.cuda.synchronize()
+    got = s32.cpu().numpy()
+    ex = omg.scaled_residual_exact(b, x)
+    tol = 10 * 2.0 ** -59 * _task_max_operand(b, x)
+    half_ulp = np.abs(np.spacing(got)).astype(np.float64) / 2
+    r64 = omg.residual(b, x, 1.0)
+    fp64_ok = True
+    for i in range(n):
+        for j in range(n):
+            bound = Fraction(float(tol[i, j])) + Fraction(float(half_ulp[i, j]))
+            err = abs(Fraction(float(got[i, j])) - ex[i][j])
+            assert err <= bound, (i, j, got[i, j], float(ex[i][j]))
+            fp64_ok &= abs(Fraction(float(np.float32(r64[i, j]))) - ex[i][j]) <= bound
+    if case == "cancelling":
+        assert not fp64_ok
+    if case == "subnormal":
+        assert np.any((got != 0) & (np.abs(got) < np.finfo(np.float32).tiny))
 
 
 def _conversion_inputs_f64():

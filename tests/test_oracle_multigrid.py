@@ -33,6 +33,34 @@ def _rand_zero_mean(n, seed):
 # Operator and exact solution (Sec. 2.2, Eq. poissoneq)
 # --------------------------------------------------------------------------
 
+def test_exact_residual_against_integer_arithmetic_and_a_rounding_case():
+    """scaled_residual_exact is exact: on integer-valued grids it equals the
+    integer stencil; on random grids it is within binary64's rounding bound of
+    the FP64 residual; and at a point where binary64 evaluation rounds a
+    neighbour sum 2 + 2^-52 to 2 (a tie, to even) it keeps the 2^-52."""
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    n = 8
+    xi = rng.integers(-1000, 1000, (n, n))
+    bi = rng.integers(-1000, 1000, (n, n))
+    ex = mg.scaled_residual_exact(bi.astype(np.float64), xi.astype(np.float64))
+    want = bi - (4 * xi - (np.roll(xi, 1, 0) + np.roll(xi, -1, 0) + np.roll(xi, 1, 1) + np.roll(xi, -1, 1)))
+    assert all(ex[i][j] == int(want[i, j]) for i in range(n) for j in range(n))
+    x = rng.standard_normal((n, n))
+    b = rng.standard_normal((n, n))
+    ex = mg.scaled_residual_exact(b, x)
+    r64 = mg.residual(b, x, 1.0)
+    bound = 8 * 2.0 ** -53 * (np.abs(b) + 4 * np.abs(x) + 4 * np.abs(x).max())
+    assert all(abs(float(ex[i][j]) - r64[i, j]) <= bound[i, j] for i in range(n) for j in range(n))
+    x = np.ones((n, n))
+    x[3, 4] = 1.0 + 2.0 ** -52  # north neighbour of (4, 4)
+    b = np.zeros((n, n))
+    b[4, 4] = 1e-20
+    ex = mg.scaled_residual_exact(b, x)
+    assert ex[4][4] == Fraction(2) ** -52 + Fraction(1e-20)
+    assert mg.residual(b, x, 1.0)[4, 4] != float(ex[4][4])  # binary64 loses it
+
+
 @pytest.mark.parametrize("n,kx,ky", [(8, 1, 0), (16, 3, 2), (32, 5, 7), (64, 16, 1)])
 def test_operator_on_fourier_modes(n, kx, ky):
     """A cos(k.x) = lambda cos(k.x), lambda = (4/h^2)(sin^2(kx h/2) + sin^2(ky h/2))."""
