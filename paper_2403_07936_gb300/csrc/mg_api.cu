@@ -1872,11 +1872,16 @@ mg_status mg_autotune(mg_ctx *c, const char *cache_path, int *n_timed) {
 }
 
 mg_status mg_set_launch_overlap(int enable) {
-    set_launch_overlap(enable != 0);
+    if (enable < 0 || enable > 2) {
+        set_err("launch overlap mode %d: 0 (off), 1 (every kernel) or 2 (grids of <= %d blocks)", enable,
+                kOverlapMaxBlocks);
+        return MG_ERR_INVALID_ARG;
+    }
+    set_launch_overlap(enable);
     return MG_OK;
 }
 
-int mg_get_launch_overlap(void) { return launch_overlap_enabled() ? 1 : 0; }
+int mg_get_launch_overlap(void) { return launch_overlap_mode(); }
 
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant) {
     if (!variant || kind < 0 || kind > 1 || !is_pow2(n) || n < 128 || nu < 0 || nu > 4) {

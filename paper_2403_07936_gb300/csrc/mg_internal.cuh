@@ -288,8 +288,14 @@ unsigned tune_epoch();
 // default; the environment variable MG_LAUNCH_OVERLAP=1 starts it on).  On
 // GB300 it measured slower: a 2048^2 mixed solve took 1.96 ms with it and
 // 1.73 ms without.
+// Programmatic dependent launch: 0 off, 1 every kernel, 2 the kernels whose
+// grid has at most kOverlapMaxBlocks blocks (at most about one wave: the
+// coarse levels, the bottom solve, the outer and convergence kernels), where
+// launch latency is a large part of a kernel's time.
+constexpr int kOverlapMaxBlocks = 304;
+int launch_overlap_mode();
 bool launch_overlap_enabled();
-void set_launch_overlap(bool on);
+void set_launch_overlap(int mode);
 
 // ----------------------------------------------------------------------------
 // Host-side launchers (defined in mg_kernels.cu); all return cudaError_t.

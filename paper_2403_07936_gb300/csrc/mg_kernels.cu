@@ -87,8 +87,9 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
     return f2_from(r);
 }
 
-// Launch k with the programmatic-stream-serialization attribute when
-// launch overlap is enabled (launch_overlap_enabled()), else as a plain launch.
+// Launch k with the programmatic-stream-serialization attribute when launch
+// overlap applies to it (mode 1, or mode 2 and a grid of at most
+// kOverlapMaxBlocks blocks), else as a plain launch.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                           Args &&...args) {
@@ -100,12 +101,14 @@ cudaError_t launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sme
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
-    if (launch_overlap_enabled()) {
+    const int mode = launch_overlap_mode();
+    if (mode == 1 || (mode == 2 && (size_t)grid.x * grid.y * grid.z <= (size_t)kOverlapMaxBlocks)) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
     }
     return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
+
 
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
@@ -608,35 +611,121 @@ __global__ void __launch_bounds__(kThreads) k_up_batched(const TileGrid *__restr
 // ---------------------------------------------------------------------------
 constexpr int kBottomThreads = 1024;
 
-template <typename T>
-__device__ __forceinline__ void sweep_periodic(T *X, const T *B, int m, int lg, int colour) {
-    const int half = (m * m) >> 1, hm = m >> 1;
-    for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-        const int i = idx >> (lg - 1), k = idx & (hm - 1);
-        const int j = 2 * k + ((i + colour) & 1);
-        const int im = (i - 1) & (m - 1), ip = (i + 1) & (m - 1);
-        const int jm = (j - 1) & (m - 1), jp = (j + 1) & (m - 1);
-        const T nb = ((X[im * m + j] + X[ip * m + j]) + X[i * m + jm]) + X[i * m + jp];
-        X[i * m + j] = (B[i * m + j] + nb) * T(0.25);
+// Runs.  On a level of m x m points (4 <= m <= 64) a thread holds a run: 4
+// consecutive points of one row, m / 4 runs per row.  For m >= 16 the
+// m^2 / 4 runs fill w = m^2 / 128 whole warps, warp g taking rows
+// g, g + w, g + 2w, ...: w is even, so the rows of a warp share their parity
+// and a half-sweep's colour choice is warp-uniform.  Smaller levels use
+// lanes of warp 0.  The lanes of one row are adjacent, so the west and east
+// neighbours of a run's end points come from the neighbouring lanes.
+struct RunMap {
+    int row, c0;         // the run's row and first column
+    int lane_w, lane_e;  // lanes holding the runs to the west and east (periodic)
+    bool warp_on, on;    // the warp takes part; this lane holds a run
+};
+
+__device__ __forceinline__ RunMap run_map(int m) {
+    const int tpr = m >> 2, runs = (m * m) >> 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    RunMap r;
+    if (runs >= 64) {
+        const int w = runs >> 5;
+        r.warp_on = warp < w;
+        r.on = r.warp_on;
+        r.row = warp + (lane / tpr) * w;
+    } else {
+        r.warp_on = warp == 0;
+        r.on = warp == 0 && lane < runs;
+        r.row = lane / tpr;
     }
+    r.c0 = (lane & (tpr - 1)) << 2;
+    const int base = lane & ~(tpr - 1);
+    r.lane_w = base | ((lane - 1) & (tpr - 1));
+    r.lane_e = base | ((lane + 1) & (tpr - 1));
+    return r;
 }
 
-// Scaled residual b - (4x - (((N + S) + W) + E)) at (i, j) of an m x m level (indices wrap).
+template <typename T> struct RunIO;
+template <> struct RunIO<float> {
+    static __device__ __forceinline__ void ld(const float *p, float (&v)[4]) {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+        v[3] = a.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&v)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct RunIO<double> {
+    static __device__ __forceinline__ void ld(const double *p, double (&v)[4]) {
+        const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&v)[4]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+    }
+};
+
+// The other-colour neighbours of a run: north and south runs from shared
+// memory, the points west and east of its ends from the neighbouring lanes.
+// Called by whole warps (warp_on); lanes without a run get zeros.
 template <typename T>
-__device__ __forceinline__ T residual_periodic(const T *X, const T *B, int m, int i, int j) {
-    i &= m - 1;
-    j &= m - 1;
-    const int im = (i - 1) & (m - 1), ip = (i + 1) & (m - 1);
-    const int jm = (j - 1) & (m - 1), jp = (j + 1) & (m - 1);
-    const T nb = ((X[im * m + j] + X[ip * m + j]) + X[i * m + jm]) + X[i * m + jp];
-    return B[i * m + j] - (T(4) * X[i * m + j] - nb);
+__device__ __forceinline__ void run_neighbours(const T *X, const T (&xr)[4], const RunMap &r, int m, T (&nr)[4],
+                                               T (&sr)[4], T &wn, T &en) {
+    if (r.on) {
+        RunIO<T>::ld(X + ((r.row - 1) & (m - 1)) * m + r.c0, nr);
+        RunIO<T>::ld(X + ((r.row + 1) & (m - 1)) * m + r.c0, sr);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) nr[a] = sr[a] = T(0);
+    }
+    wn = __shfl_sync(0xffffffffu, xr[3], r.lane_w);
+    en = __shfl_sync(0xffffffffu, xr[0], r.lane_e);
+}
+
+// One Gauss-Seidel half-sweep of colour q over the level's runs,
+// x <- (b + (((N + S) + W) + E)) / 4; the run (xr) stays in registers and is
+// stored for the neighbours' next half-sweep.
+template <typename T>
+__device__ __forceinline__ void run_half_sweep(T *X, const T (&br)[4], T (&xr)[4], const RunMap &r, int m, int q) {
+    if (r.warp_on) {
+        T nr[4], sr[4], wn, en;
+        run_neighbours(X, xr, r, m, nr, sr, wn, en);
+        if (((r.row + q) & 1) == 0) {  // colour q at run positions 0 and 2
+            xr[0] = (br[0] + (((nr[0] + sr[0]) + wn) + xr[1])) * T(0.25);
+            xr[2] = (br[2] + (((nr[2] + sr[2]) + xr[1]) + xr[3])) * T(0.25);
+        } else {  // at positions 1 and 3
+            xr[1] = (br[1] + (((nr[1] + sr[1]) + xr[0]) + xr[2])) * T(0.25);
+            xr[3] = (br[3] + (((nr[3] + sr[3]) + xr[2]) + en)) * T(0.25);
+        }
+        if (r.on) RunIO<T>::st(X + r.row * m + r.c0, xr);
+    }
+    __syncthreads();
+}
+
+// Midpoint J + 1/2 of a periodic coarse row E (mc points) by the cubic
+// spline's FIR taps.
+template <typename T>
+__device__ __forceinline__ T spline_mid_row(const T *E, int J, int mc, const FirTaps &taps) {
+    constexpr int L = Prec<T>::L;
+    T acc = T(0);
+#pragma unroll
+    for (int k = L; k >= 1; --k)
+        acc += Prec<T>::tap(taps, k) * (E[(J + k) & (mc - 1)] + E[(J + 1 - k) & (mc - 1)]);
+    return acc;
 }
 
 // Shared-memory elements of a bottom solve of an n x n grid with nlev levels:
-// x and b per level, plus n * n / 2 for the row-refined coarse grid of the
-// prolongation.
+// x and b per level, n * n / 2 for the row-refined coarse grid of the
+// prolongation and n * n for the residual that full weighting reads.
 __host__ __device__ constexpr size_t bottom_elems(int n, int nlev) {
-    size_t e = (size_t)n * n / 2;
+    size_t e = (size_t)n * n / 2 + (size_t)n * n;
     for (int l = 0; l < nlev; ++l) e += 2ull * (n >> l) * (n >> l);
     return e;
 }
@@ -647,47 +736,74 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
                                             const FirTaps &taps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *base = reinterpret_cast<T *>(smem_raw);
-    T *X[8], *B[8];
-    int off = 0;
-    for (int l = 0; l < nlev; ++l) {
-        const int m = n >> l;
-        X[l] = base + off;
-        off += m * m;
-        B[l] = base + off;
-        off += m * m;
-    }
-    T *S = base + off;  // n * n / 2 scratch: row-refined coarse rows
+    // level l (m = n >> l points a side): x at X(l), b at X(l) + m^2; the levels
+    // above it take 2 (n^2 + (n/2)^2 + ... + (2m)^2) = 8 (n^2 - m^2) / 3 elements
+    auto X = [&](int l) { const int m = n >> l; return base + 8 * (n * n - m * m) / 3; };
+    auto B = [&](int l) { const int m = n >> l; return base + 8 * (n * n - m * m) / 3 + m * m; };
+    const int mlast = n >> (nlev - 1);
+    T *S = base + 8 * (n * n - mlast * mlast) / 3 + 2 * mlast * mlast;  // n * n / 2: row-refined coarse rows
+    T *R = S + n * n / 2;  // n * n: residual of the level being restricted
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lg0 = __ffs(n) - 1;
 
     for (int p = tid; p < n * n; p += nt) {
-        X[0][p] = zero_init ? T(0) : x[p];
-        B[0][p] = b[p];
+        X(0)[p] = zero_init ? T(0) : x[p];
+        B(0)[p] = b[p];
     }
     __syncthreads();
     for (int l = 0; l + 1 < nlev; ++l) {
-        const int m = n >> l, mc = m >> 1, lg = lg0 - l;
-        for (int s = 0; s < nu1; ++s) {
-            sweep_periodic(X[l], B[l], m, lg, 0);
-            __syncthreads();
-            sweep_periodic(X[l], B[l], m, lg, 1);
-            __syncthreads();
+        const int m = n >> l, mc = m >> 1;
+        const RunMap r = run_map(m);
+        T xr[4] = {}, br[4] = {};
+        if (r.on) {
+            RunIO<T>::ld(X(l) + r.row * m + r.c0, xr);
+            RunIO<T>::ld(B(l) + r.row * m + r.c0, br);
         }
-        // full weighting of the residual, evaluated where it is needed
-        // (times 4 because h_c^2 = 4 h^2)
-        for (int q = tid; q < mc * mc; q += nt) {
-            const int I = q >> (lg - 1), J = q & (mc - 1);
-            const int i = 2 * I, j = 2 * J;
-            const T *Xl = X[l], *Bl = B[l];
-            const T edge = ((residual_periodic(Xl, Bl, m, i - 1, j) + residual_periodic(Xl, Bl, m, i + 1, j)) +
-                            residual_periodic(Xl, Bl, m, i, j - 1)) +
-                           residual_periodic(Xl, Bl, m, i, j + 1);
-            const T corner =
-                ((residual_periodic(Xl, Bl, m, i - 1, j - 1) + residual_periodic(Xl, Bl, m, i - 1, j + 1)) +
-                 residual_periodic(Xl, Bl, m, i + 1, j - 1)) +
-                residual_periodic(Xl, Bl, m, i + 1, j + 1);
-            B[l + 1][q] = (T(4) * residual_periodic(Xl, Bl, m, i, j) + T(2) * edge + corner) * T(0.25);
-            X[l + 1][q] = T(0);
+        for (int s = 0; s < nu1; ++s) {
+            run_half_sweep(X(l), br, xr, r, m, 0);
+            run_half_sweep(X(l), br, xr, r, m, 1);
+        }
+        // scaled residual b - (4x - (((N + S) + W) + E))
+        if (r.warp_on) {
+            T nr[4], sr[4], wn, en;
+            run_neighbours(X(l), xr, r, m, nr, sr, wn, en);
+            const T w[4] = {wn, xr[0], xr[1], xr[2]}, e[4] = {xr[1], xr[2], xr[3], en};
+            T rr[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) rr[a] = br[a] - (T(4) * xr[a] - (((nr[a] + sr[a]) + w[a]) + e[a]));
+            if (r.on) RunIO<T>::st(R + r.row * m + r.c0, rr);
+        }
+        __syncthreads();
+        // full weighting at coarse (I, J) <-> fine (2I, 2J), times 4 because
+        // h_c^2 = 4 h^2; each coarse run reads fine rows 2I - 1 .. 2I + 1,
+        // columns 2J0 - 1 .. 2J0 + 7
+        const RunMap rc = run_map(mc);
+        if (rc.on) {
+            const int i = 2 * rc.row, j0 = 2 * rc.c0;
+            T v[3][9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const T *Rw = R + ((i - 1 + k) & (m - 1)) * m;
+                T lo[4], hi[4];
+                RunIO<T>::ld(Rw + j0, lo);
+                RunIO<T>::ld(Rw + j0 + 4, hi);
+                v[k][0] = Rw[(j0 - 1) & (m - 1)];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    v[k][1 + a] = lo[a];
+                    v[k][5 + a] = hi[a];
+                }
+            }
+            T bc[4];
+            const T zero[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int jj = 1 + 2 * a;
+                const T edge = ((v[0][jj] + v[2][jj]) + v[1][jj - 1]) + v[1][jj + 1];
+                const T corner = ((v[0][jj - 1] + v[0][jj + 1]) + v[2][jj - 1]) + v[2][jj + 1];
+                bc[a] = (T(4) * v[1][jj] + T(2) * edge + corner) * T(0.25);
+            }
+            RunIO<T>::st(B(l + 1) + rc.row * mc + rc.c0, bc);
+            RunIO<T>::st(X(l + 1) + rc.row * mc + rc.c0, zero);
         }
         __syncthreads();
     }
@@ -695,8 +811,8 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
         // tpo threads per output row take strided partial dot products (coalesced
         // loads, all issued in parallel), then a shuffle tree within the group.
         const int mcst = n >> (nlev - 1), Nc = mcst * mcst;
-        T *Xc = X[nlev - 1];
-        const T *Bc = B[nlev - 1];
+        T *Xc = X(nlev - 1);
+        const T *Bc = B(nlev - 1);
         const int tpo = min(32, nt / Nc);  // powers of two: groups never straddle a warp
         const int p = tid / tpo, lane = tid - p * tpo;
         T acc = T(0);
@@ -708,50 +824,54 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
     }
     constexpr int L = Prec<T>::L;
     for (int l = nlev - 2; l >= 0; --l) {
-        const int m = n >> l, mc = m >> 1, lg = lg0 - l;
-        const T *E = X[l + 1];
-        for (int p = tid; p < mc * m; p += nt) {  // refine coarse rows along x
-            const int I = p >> lg, j = p & (m - 1);
-            T val;
-            if ((j & 1) == 0) {
-                val = E[I * mc + (j >> 1)];
-            } else {
-                const int J = j >> 1;
-                T acc = T(0);
-#pragma unroll 4
-                for (int k = L; k >= 1; --k)
-                    acc += Prec<T>::tap(taps, k) *
-                           (E[I * mc + ((J + k) & (mc - 1))] + E[I * mc + ((J + 1 - k) & (mc - 1))]);
-                val = acc;
-            }
-            S[p] = val;
+        const int m = n >> l, mc = m >> 1;
+        const T *E = X(l + 1);
+        // refine coarse rows along x: runs of 4 fine columns j0 .. j0 + 3 of
+        // coarse row I (coarse values at j0, j0 + 2, midpoints between)
+        for (int t = tid; t < (m * m) >> 3; t += nt) {
+            const int I = t / (m >> 2), j0 = (t - I * (m >> 2)) << 2, J0 = j0 >> 1;
+            const T *Er = E + I * mc;
+            T o[4];
+            o[0] = Er[J0];
+            o[1] = spline_mid_row(Er, J0, mc, taps);
+            o[2] = Er[J0 + 1];
+            o[3] = spline_mid_row(Er, J0 + 1, mc, taps);
+            RunIO<T>::st(S + I * m + j0, o);
         }
         __syncthreads();
-        for (int p = tid; p < m * m; p += nt) {  // refine along y and add
-            const int i = p >> lg, j = p & (m - 1);
-            T val;
-            if ((i & 1) == 0) {
-                val = S[(i >> 1) * m + j];
+        // refine along y and add to the level's x, in the level's runs
+        const RunMap r = run_map(m);
+        T xr[4] = {}, br[4] = {};
+        if (r.on) {
+            T val[4];
+            if ((r.row & 1) == 0) {
+                RunIO<T>::ld(S + (r.row >> 1) * m + r.c0, val);
             } else {
-                const int I = i >> 1;
-                T acc = T(0);
-#pragma unroll 4
-                for (int k = L; k >= 1; --k)
-                    acc += Prec<T>::tap(taps, k) *
-                           (S[((I + k) & (mc - 1)) * m + j] + S[((I + 1 - k) & (mc - 1)) * m + j]);
-                val = acc;
+                const int I = r.row >> 1;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) val[a] = T(0);
+#pragma unroll
+                for (int k = L; k >= 1; --k) {
+                    T u[4], w[4];
+                    RunIO<T>::ld(S + ((I + k) & (mc - 1)) * m + r.c0, u);
+                    RunIO<T>::ld(S + ((I + 1 - k) & (mc - 1)) * m + r.c0, w);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) val[a] += Prec<T>::tap(taps, k) * (u[a] + w[a]);
+                }
             }
-            X[l][p] += val;
+            RunIO<T>::ld(X(l) + r.row * m + r.c0, xr);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xr[a] += val[a];
+            RunIO<T>::st(X(l) + r.row * m + r.c0, xr);
+            RunIO<T>::ld(B(l) + r.row * m + r.c0, br);
         }
         __syncthreads();
         for (int s = 0; s < nu2; ++s) {
-            sweep_periodic(X[l], B[l], m, lg, 0);
-            __syncthreads();
-            sweep_periodic(X[l], B[l], m, lg, 1);
-            __syncthreads();
+            run_half_sweep(X(l), br, xr, r, m, 0);
+            run_half_sweep(X(l), br, xr, r, m, 1);
         }
     }
-    for (int p = tid; p < n * n; p += nt) x[p] = X[0][p];
+    for (int p = tid; p < n * n; p += nt) x[p] = X(0)[p];
 }
 
 template <typename T>

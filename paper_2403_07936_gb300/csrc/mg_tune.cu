@@ -78,22 +78,24 @@ namespace {
 std::atomic<int> g_overlap{-1};  // -1: not read from the environment yet
 }
 
-bool launch_overlap_enabled() {
+int launch_overlap_mode() {
     int v = g_overlap.load(std::memory_order_relaxed);
     if (v < 0) {
         const char *env = getenv("MG_LAUNCH_OVERLAP");
-        v = (env && env[0] == '1') ? 1 : 0;
+        v = (env && (env[0] == '1' || env[0] == '2')) ? env[0] - '0' : 0;
         int expect = -1;
         g_overlap.compare_exchange_strong(expect, v);
         v = g_overlap.load();
     }
-    return v != 0;
+    return v;
 }
 
-void set_launch_overlap(bool on) {
-    const bool old = launch_overlap_enabled();
-    g_overlap.store(on ? 1 : 0);
-    if (old != on) g_epoch.fetch_add(1);
+bool launch_overlap_enabled() { return launch_overlap_mode() != 0; }
+
+void set_launch_overlap(int mode) {
+    const int old = launch_overlap_mode();
+    g_overlap.store(mode);
+    if (old != mode) g_epoch.fetch_add(1);
 }
 
 namespace {

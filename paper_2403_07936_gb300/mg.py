@@ -308,13 +308,14 @@ class Server:
             pass
 
 
-def set_launch_overlap(enable: bool):
-    """Programmatic dependent launch between library kernels (off by default)."""
-    _check(load().mg_set_launch_overlap(int(bool(enable))))
+def set_launch_overlap(mode):
+    """Programmatic dependent launch between library kernels: 0 / False off,
+    1 / True every kernel, 2 kernels of grids of at most one wave."""
+    _check(load().mg_set_launch_overlap(int(mode)))
 
 
-def get_launch_overlap() -> bool:
-    return bool(load().mg_get_launch_overlap())
+def get_launch_overlap() -> int:
+    return int(load().mg_get_launch_overlap())
 
 
 def get_tile_variant(kind: int, n: int, nu: int) -> int:
