@@ -215,11 +215,11 @@ void mg_server_destroy(mg_server *srv);
 
 /* ---------------------------------------------------------------------
  * Tile-shape autotuning (no counterpart in the paper: an implementation
- * choice of this library).  The FP32 stencil kernels exist in four tile
- * variants: bit 0 set = tiles of 32 rows (else 64) by 64 columns; bit 1 set =
- * the prolongation's spline passes on pairs of rows / columns with packed
- * FP32x2 instructions (else scalar, one midpoint per work item).  kind 0 is the
- * down kernel (sweeps, residual, restriction: variants 0 and 1 only), kind 1
+ * choice of this library).  The FP32 stencil kernels exist in eight tile
+ * variants: tiles of 64 >> (v & 3) rows (64, 32, 16 or 8) by 64 columns; bit 2
+ * set = the prolongation's spline passes on pairs of rows / columns with
+ * packed FP32x2 instructions (else scalar, one midpoint per work item).  kind 0
+ * is the down kernel (sweeps, residual, restriction: variants 0-3 only), kind 1
  * the up kernel (prolongation, correction, sweeps).  Every variant computes
  * the same bits; the choice changes only speed.  The choice is process-wide,
  * per (kind, grid size n, sweep count nu), starts from built-in defaults, and

@@ -14,6 +14,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <mutex>
@@ -247,6 +248,32 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
     if (!fp64) c->bsc64 = (double *)((char *)blk + bsc_off);
     if (tasks) c->ebt = (int *)((char *)blk + ebt_off);
     return MG_OK;
+}
+
+// Streaming multiprocessors of the current device (queried once).
+static int num_sms() {
+    static std::atomic<int> sms{0};
+    int v = sms.load(std::memory_order_relaxed);
+    if (v == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        sms.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// Variant of a batched tile launch over ngrid grids of size sz: the table's
+// choice while the launch's 32-row tiles would not fill the GPU once (small
+// tiles shorten a lone grid's chain of dependent phases); beyond that the GPU
+// is full and smaller tiles only add halo work, so at least 32 rows.
+static int batch_variant(int kind, int sz, int nu, int ngrid) {
+    int v = tile_variant(kind, sz, nu);
+    if (variant_rows(v) < 32 && (long long)ngrid * variant_tiles(sz, 1) >= num_sms()) v = (v & kVariantPacked) | 1;
+    return v;
 }
 
 // The finest level's scaled right-hand side buffer of a solve.
@@ -707,8 +734,14 @@ static mg_status batch_build(BatchPlan *p) {
     for (int v = 0; v < 2; ++v) {
         const bool first = v == 0;
         p->cyc[v].clear();
+        auto grids_of = [&](int sz) {
+            int g = 0;
+            for (int r = 0; r < B; ++r)
+                for (int l = 0; l + 1 < p->ctxs[r]->levels; ++l) g += p->ctxs[r]->lv[l].n == sz;
+            return g;
+        };
         for (int sz = maxN; sz > kBottomMax; sz >>= 1) {  // down sweeps
-            BatchLaunch L{0, tiles.size(), 0, 0, tile_variant(0, sz, c0->nu1)};
+            BatchLaunch L{0, tiles.size(), 0, 0, batch_variant(0, sz, c0->nu1, grids_of(sz))};
             for (int r = 0; r < B; ++r) {
                 mg_ctx *c = p->ctxs[r];
                 for (int l = 0; l + 1 < c->levels; ++l)
@@ -735,7 +768,7 @@ static mg_status batch_build(BatchPlan *p) {
             p->cyc[v].push_back(L);
         }
         for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {  // up sweeps
-            BatchLaunch L{1, tiles.size(), 0, 0, tile_variant(1, sz, c0->nu2)};
+            BatchLaunch L{1, tiles.size(), 0, 0, batch_variant(1, sz, c0->nu2, grids_of(sz))};
             for (int r = 0; r < B; ++r) {
                 mg_ctx *c = p->ctxs[r];
                 for (int l = 0; l + 1 < c->levels; ++l)
@@ -1244,8 +1277,17 @@ static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sid
     }
     for (int v = 0; v < maxm; ++v) {
         const bool first = v == 0;
+        auto grids_of = [&](int sz) {
+            int g = 0;
+            for (int sid : sids) {
+                if (m[sid] <= v) continue;
+                const mg_ctx *c = sv->slots[sid].ctx;
+                for (int l = 0; l + 1 < c->levels; ++l) g += c->lv[l].n == sz;
+            }
+            return g;
+        };
         for (int sz = maxN; sz > kBottomMax; sz >>= 1) {
-            BatchLaunch L{0, tp.tiles.size(), 0, 0, tile_variant(0, sz, sv->nu1)};
+            BatchLaunch L{0, tp.tiles.size(), 0, 0, batch_variant(0, sz, sv->nu1, grids_of(sz))};
             for (int sid : sids) {
                 if (m[sid] <= v) continue;
                 mg_ctx *c = sv->slots[sid].ctx;
@@ -1272,7 +1314,7 @@ static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sid
         Lb.nblocks = Lb.ngrid;
         if (Lb.ngrid) tp.cyc[v].push_back(Lb);
         for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {
-            BatchLaunch L{1, tp.tiles.size(), 0, 0, tile_variant(1, sz, sv->nu2)};
+            BatchLaunch L{1, tp.tiles.size(), 0, 0, batch_variant(1, sz, sv->nu2, grids_of(sz))};
             for (int sid : sids) {
                 if (m[sid] <= v) continue;
                 mg_ctx *c = sv->slots[sid].ctx;
@@ -1895,8 +1937,8 @@ mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant) {
 mg_status mg_set_tile_variant(int kind, int n, int nu, int variant) {
     if (kind < 0 || kind > 1 || !is_pow2(n) || n < 128 || nu < 0 || nu > 4 || variant < 0 ||
         variant >= kTileVariants || (kind == 0 && variant_runs(variant) != 1)) {
-        set_err("invalid tile variant (kind 0|1, n a power of two >= 128, nu 0..4, variant 0..3; "
-                "k_down takes 0 or 1)");
+        set_err("invalid tile variant (kind 0|1, n a power of two >= 128, nu 0..4, variant 0..%d; "
+                "k_down takes 0..%d)", kTileVariants - 1, kVariantPacked - 1);
         return MG_ERR_INVALID_ARG;
     }
     set_tile_variant(kind, n, nu, variant);

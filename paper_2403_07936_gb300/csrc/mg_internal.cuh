@@ -276,9 +276,12 @@ struct BatchRed {
 // table below (mg_tune.cu) holds the one to use for each (kernel kind: 0 down
 // / 1 up, grid size, sweep count), from built-in defaults or mg_autotune.
 // ----------------------------------------------------------------------------
-constexpr int kTileVariants = 4;
-__host__ __device__ constexpr int variant_rows(int v) { return (v & 1) ? 32 : 64; }
-__host__ __device__ constexpr int variant_runs(int v) { return (v & 2) ? 2 : 1; }
+// Tile variant v: tiles of 64 >> (v & 3) rows (64, 32, 16 or 8) by 64 columns;
+// bit 2 set: the spline passes on pairs of rows / columns (packed FP32x2).
+constexpr int kTileVariants = 8;
+constexpr int kVariantPacked = 4;
+__host__ __device__ constexpr int variant_rows(int v) { return 64 >> (v & 3); }
+__host__ __device__ constexpr int variant_runs(int v) { return (v & kVariantPacked) ? 2 : 1; }
 inline int variant_tiles(int n, int v) { return (n / 64) * (n / variant_rows(v)); }
 int tile_variant(int kind, int n, int nu);
 void set_tile_variant(int kind, int n, int nu, int variant);

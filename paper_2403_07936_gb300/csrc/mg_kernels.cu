@@ -114,7 +114,7 @@ __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / 
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 // Output tiles are TY x 64 points.  FP32 kernels come in variants (see
-// variant_rows / variant_runs): 64 or 32 rows per tile, and NJ = 1 (scalar
+// variant_rows / variant_runs): 64, 32, 16 or 8 rows per tile, and NJ = 1 (scalar
 // spline passes, one midpoint per work item) or NJ = 2 (the spline passes on
 // float2 pairs of rows / columns with packed FP32x2 instructions).  Every
 // variant computes the same values in the same order, so the choice only
@@ -1536,8 +1536,12 @@ cudaError_t down_var(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_t
     if constexpr (std::is_same<T, double>::value) {
         return down_impl<T, NU, ZERO, Fixed64<double>::TY>(x, xout, b, n, bc, s);
     } else {
-        return variant_rows(variant) == 32 ? down_impl<T, NU, ZERO, 32>(x, xout, b, n, bc, s)
-                                           : down_impl<T, NU, ZERO, 64>(x, xout, b, n, bc, s);
+        switch (variant_rows(variant)) {
+            case 8: return down_impl<T, NU, ZERO, 8>(x, xout, b, n, bc, s);
+            case 16: return down_impl<T, NU, ZERO, 16>(x, xout, b, n, bc, s);
+            case 32: return down_impl<T, NU, ZERO, 32>(x, xout, b, n, bc, s);
+            default: return down_impl<T, NU, ZERO, 64>(x, xout, b, n, bc, s);
+        }
     }
 }
 
@@ -1547,11 +1551,20 @@ cudaError_t up_var(const T *x, T *xout, const T *b, const T *ec, const T *extra,
     if constexpr (std::is_same<T, double>::value) {
         return up_impl<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>(x, xout, b, ec, extra, eflag, n, taps, s);
     } else {
-        const bool r32 = variant_rows(variant) == 32, nj2 = variant_runs(variant) == 2;
-        if (r32) return nj2 ? up_impl<T, NU, 32, 2>(x, xout, b, ec, extra, eflag, n, taps, s)
-                            : up_impl<T, NU, 32, 1>(x, xout, b, ec, extra, eflag, n, taps, s);
-        return nj2 ? up_impl<T, NU, 64, 2>(x, xout, b, ec, extra, eflag, n, taps, s)
-                   : up_impl<T, NU, 64, 1>(x, xout, b, ec, extra, eflag, n, taps, s);
+#define MG_UP_ROWS(TYV)                                                                                  \
+    case TYV:                                                                                            \
+        return nj2 ? up_impl<T, NU, TYV, 2>(x, xout, b, ec, extra, eflag, n, taps, s)                   \
+                   : up_impl<T, NU, TYV, 1>(x, xout, b, ec, extra, eflag, n, taps, s);
+        const bool nj2 = variant_runs(variant) == 2;
+        switch (variant_rows(variant)) {
+            MG_UP_ROWS(8)
+            MG_UP_ROWS(16)
+            MG_UP_ROWS(32)
+            default:
+                return nj2 ? up_impl<T, NU, 64, 2>(x, xout, b, ec, extra, eflag, n, taps, s)
+                           : up_impl<T, NU, 64, 1>(x, xout, b, ec, extra, eflag, n, taps, s);
+        }
+#undef MG_UP_ROWS
     }
 }
 
@@ -1765,17 +1778,27 @@ cudaError_t up_batched_impl(const TileGrid *tab, int ngrid, int nblocks, const i
 template <int NU>
 cudaError_t down_batched_var(const TileGrid *tab, int ngrid, int nblocks, const int *active, cudaStream_t s,
                              int variant) {
-    return variant_rows(variant) == 32 ? down_batched_impl<NU, 32>(tab, ngrid, nblocks, active, s)
-                                       : down_batched_impl<NU, 64>(tab, ngrid, nblocks, active, s);
+    switch (variant_rows(variant)) {
+        case 8: return down_batched_impl<NU, 8>(tab, ngrid, nblocks, active, s);
+        case 16: return down_batched_impl<NU, 16>(tab, ngrid, nblocks, active, s);
+        case 32: return down_batched_impl<NU, 32>(tab, ngrid, nblocks, active, s);
+        default: return down_batched_impl<NU, 64>(tab, ngrid, nblocks, active, s);
+    }
 }
 template <int NU>
 cudaError_t up_batched_var(const TileGrid *tab, int ngrid, int nblocks, const int *active, const FirTaps &taps,
                            cudaStream_t s, int variant) {
-    const bool r32 = variant_rows(variant) == 32, nj2 = variant_runs(variant) == 2;
-    if (r32) return nj2 ? up_batched_impl<NU, 32, 2>(tab, ngrid, nblocks, active, taps, s)
-                        : up_batched_impl<NU, 32, 1>(tab, ngrid, nblocks, active, taps, s);
-    return nj2 ? up_batched_impl<NU, 64, 2>(tab, ngrid, nblocks, active, taps, s)
-               : up_batched_impl<NU, 64, 1>(tab, ngrid, nblocks, active, taps, s);
+    const bool nj2 = variant_runs(variant) == 2;
+    switch (variant_rows(variant)) {
+        case 8: return nj2 ? up_batched_impl<NU, 8, 2>(tab, ngrid, nblocks, active, taps, s)
+                           : up_batched_impl<NU, 8, 1>(tab, ngrid, nblocks, active, taps, s);
+        case 16: return nj2 ? up_batched_impl<NU, 16, 2>(tab, ngrid, nblocks, active, taps, s)
+                            : up_batched_impl<NU, 16, 1>(tab, ngrid, nblocks, active, taps, s);
+        case 32: return nj2 ? up_batched_impl<NU, 32, 2>(tab, ngrid, nblocks, active, taps, s)
+                            : up_batched_impl<NU, 32, 1>(tab, ngrid, nblocks, active, taps, s);
+        default: return nj2 ? up_batched_impl<NU, 64, 2>(tab, ngrid, nblocks, active, taps, s)
+                            : up_batched_impl<NU, 64, 1>(tab, ngrid, nblocks, active, taps, s);
+    }
 }
 }  // namespace
 
@@ -1916,10 +1939,16 @@ static cudaError_t prepare_nu() {
     if constexpr (std::is_same<T, double>::value) {
         return prepare_shape<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>();
     } else {
-        cudaError_t e = prepare_shape<T, NU, 64, 1>();
-        if (e == cudaSuccess) e = prepare_shape<T, NU, 64, 2>();
-        if (e == cudaSuccess) e = prepare_shape<T, NU, 32, 1>();
-        if (e == cudaSuccess) e = prepare_shape<T, NU, 32, 2>();
+        cudaError_t e = cudaSuccess;
+        for (int v = 0; v < kTileVariants && e == cudaSuccess; ++v) {
+            const int nj = variant_runs(v);
+            switch (variant_rows(v)) {
+                case 8: e = nj == 2 ? prepare_shape<T, NU, 8, 2>() : prepare_shape<T, NU, 8, 1>(); break;
+                case 16: e = nj == 2 ? prepare_shape<T, NU, 16, 2>() : prepare_shape<T, NU, 16, 1>(); break;
+                case 32: e = nj == 2 ? prepare_shape<T, NU, 32, 2>() : prepare_shape<T, NU, 32, 1>(); break;
+                default: e = nj == 2 ? prepare_shape<T, NU, 64, 2>() : prepare_shape<T, NU, 64, 1>(); break;
+            }
+        }
         return e;
     }
 }

@@ -2,15 +2,16 @@
 //
 // The FP32 stencil kernels (k_down: sweeps + residual + full weighting, k_up:
 // cubic prolongation + correction + sweeps) are compiled in several tile
-// shapes (32 or 64 rows of 64 points; one or two spline midpoints per
+// shapes (64, 32, 16 or 8 rows of 64 points; one or two spline midpoints per
 // prolongation work item).  Which one is fastest depends on the grid size:
 // a 2048^2 level has enough 64-row tiles to fill 152 SMs, while a 256^2 level
-// has 16 of them and is better served by 32 smaller ones.  All variants give
+// has 16 of them; there smaller tiles shorten each block's chain of
+// dependent phases, which bounds the kernel's time when SMs sit idle.  All variants give
 // bit-identical results, so the table only decides speed.
 //
 // The table is process-wide, keyed by (kernel kind, grid size, sweep count).
-// Entries come from built-in defaults (op-level timings on GB300: 32-row
-// tiles up to 512^2, 64-row tiles above, packed spline passes), from
+// Entries come from built-in defaults (op-level timings on GB300, see
+// default_variant), from
 // mg_autotune (CUDA-event timings of every variant on a context's own level
 // buffers), or from a cache file that earlier autotuning wrote.
 #include <stdio.h>
@@ -37,10 +38,12 @@ std::atomic<unsigned> g_epoch{1};
 
 int default_variant(int kind, int n, int nu) {
     (void)nu;
-    // 32-row tiles up to 512^2, 64-row tiles above; the up kernel's packed
-    // FP32x2 spline passes (variant bit 1)
-    const int rows = n <= 512 ? 1 : 0;
-    return kind == 0 ? rows : rows | 2;
+    // op-level timings on GB300 (nu = 2): 64-row tiles from 1024^2, 32-row
+    // tiles at 512^2, and below that 8-row tiles for the down kernel and
+    // 16-row tiles for the up kernel, whose spline halo makes 8 rows dearer;
+    // the up kernel's packed FP32x2 spline passes throughout
+    if (kind == 0) return n >= 1024 ? 0 : (n == 512 ? 1 : 3);
+    return kVariantPacked | (n >= 1024 ? 0 : (n == 512 ? 1 : 2));
 }
 
 std::string gpu_tag(int device) {
@@ -52,7 +55,8 @@ std::string gpu_tag(int device) {
     std::string name(prop.name);
     for (char &ch : name)
         if (ch == ' ' || ch == '\t') ch = '_';
-    return name + "/" + std::to_string(prop.multiProcessorCount);
+    // the trailing tag names the variant numbering (rows 64 >> (v & 3), bit 2 packed)
+    return name + "/" + std::to_string(prop.multiProcessorCount) + "/v8";
 }
 
 }  // namespace

@@ -1,7 +1,7 @@
 """Tile-shape variants and the autotuner (GPU).
 
-The FP32 stencil kernels come in four tile variants (32 or 64 rows per tile;
-one or two spline midpoints per prolongation work item).  Each point's
+The FP32 stencil kernels come in eight tile variants (64, 32, 16 or 8 rows
+per tile; one or two spline midpoints per prolongation work item).  Each point's
 arithmetic is the same in all of them, so they must agree bit for bit: the
 operators, a whole solve, and a batched solve.  The autotuner times them,
 keeps the fastest, and round-trips its choices through a cache file.
@@ -52,8 +52,8 @@ def test_operator_variants_are_bit_identical(mg, restore_table, n, nu):
     b = torch.randn((n, n), device=DEV, generator=g)
     ec = torch.randn((n // 2, n // 2), device=DEV, generator=g)
     outs_d, outs_u = [], []
-    for v in range(4):
-        if v < 2:
+    for v in range(8):
+        if v < 4:  # the down kernel has no spline pass
             mg.set_tile_variant(0, n, nu, v)
             xo = torch.full_like(x, float("nan"))
             bc = torch.full_like(ec, float("nan"))
@@ -81,7 +81,7 @@ def test_solve_and_batch_are_identical_under_every_variant(mg, restore_table):
            for i, m in enumerate(bsizes)]
     bctx = [mg.Context(int(np.log2(m // 8)) + 1, m) for m in bsizes]
     ref = None
-    for vd, vu in [(0, 0), (1, 1), (0, 3), (1, 2)]:
+    for vd, vu in [(0, 0), (1, 5), (3, 6), (2, 7), (1, 3)]:
         _set_all(mg, vd, vu)
         x = torch.zeros_like(ft)
         info = ctx.solve(ft, x)
@@ -109,7 +109,7 @@ def test_autotune_picks_a_variant_and_round_trips_the_cache(mg, restore_table, t
     levels = [1024, 512, 256, 128]  # tile levels (64^2 and below run in the one-block bottom kernel)
     assert timed == 2 * len(levels)
     chosen = {(k, m): mg.get_tile_variant(k, m, 2) for k in (0, 1) for m in levels}
-    assert all(v in (0, 1) for (k, m), v in chosen.items() if k == 0)
+    assert all(v in range(4) if k == 0 else v in range(8) for (k, m), v in chosen.items())
     lines = open(path).read().splitlines()
     assert len(lines) == 1 + 2 * len(levels)
     # overwrite the table, then load it back from the cache without timing
