@@ -1582,7 +1582,7 @@ mg_status mg_setup(int levels, int N, mg_ctx **out) {
     if (e == cudaSuccess) e = cudaMemcpy(c->ainv32, hf, sizeof(float) * Nc * Nc, cudaMemcpyHostToDevice);
     delete[] h;
     delete[] hf;
-    if (e == cudaSuccess) e = cudaMalloc(&c->red_partials, sizeof(double) * kMaxSlots * kRedBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->red_partials, sizeof(double) * kMaxSlots * kRedStride);
     if (e == cudaSuccess) e = cudaMalloc(&c->red_counter, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->red_counter, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(double) * 4 * kMaxSlots);
@@ -2227,7 +2227,7 @@ mg_status mg_op_outer_residual(int n, const double *f, const double *x, double m
     int *ebt = nullptr;
     const bool tasks = s32 && n >= kResMinN;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMalloc(&partials, sizeof(double) * kMaxSlots * kRedBlocks);
+    cudaError_t e = cudaMalloc(&partials, sizeof(double) * kMaxSlots * kRedStride);
     if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(unsigned));
     if (e == cudaSuccess && tasks) e = cudaMalloc(&bint, sizeof(long long) * n * n);
     if (e == cudaSuccess && tasks) e = cudaMalloc(&ebt, sizeof(int) * res_tasks(n));

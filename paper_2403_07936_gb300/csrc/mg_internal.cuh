@@ -174,12 +174,15 @@ __device__ __forceinline__ float residual_exact_f32(double b, double x, double x
 // order inside the block), the last block to finish sums the partials in
 // index order and resets the arrival counter.  `nslot` independent sums.
 // ----------------------------------------------------------------------------
-constexpr int kRedBlocks = 304;  // 2 blocks per SM on 152 SMs (4 measured slower)
+constexpr int kRedBlocks = 304;  // 2 blocks per SM on 152 SMs (4 measured slower for the FP64 kernels)
+constexpr int kRedStride = 1216;  // capacity of a Reduction's partials: blocks of one launch
+constexpr int kWideBlocks = 608;  // 4 blocks per SM: the update (latency-bound)
+constexpr int kResBlocks = 456;   // 3 blocks per SM: the steady task-tiled residual (<= 85 registers)
 constexpr int kRedThreads = 256;
 constexpr int kMaxSlots = 4;
 
 struct Reduction {
-    double *partials;   // [kMaxSlots][kRedBlocks]
+    double *partials;   // [kMaxSlots][kRedStride]
     unsigned *counter;  // 1 arrival counter
     double *out;        // [kMaxSlots] final sums
 };
@@ -206,7 +209,7 @@ __device__ __forceinline__ void reduce_finish(const Reduction &red, const double
                                               double *sh) {
     __shared__ bool am_last;
     if (threadIdx.x == 0) {
-        for (int k = 0; k < NS; ++k) red.partials[k * kRedBlocks + blockIdx.x] = vals[k];
+        for (int k = 0; k < NS; ++k) red.partials[k * kRedStride + blockIdx.x] = vals[k];
         __threadfence();
         const unsigned ticket = atomicAdd(red.counter, 1u);
         am_last = (ticket == gridDim.x - 1);
@@ -218,7 +221,7 @@ __device__ __forceinline__ void reduce_finish(const Reduction &red, const double
         double v = 0.0;
         // fixed assignment of partials to threads, then a fixed-order tree
         for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
-            v += ((volatile double *)red.partials)[k * kRedBlocks + i];
+            v += ((volatile double *)red.partials)[k * kRedStride + i];
         v = block_sum(v, sh);
         if (threadIdx.x == 0) red.out[k] = v;
     }

@@ -1102,7 +1102,7 @@ __device__ __forceinline__ void residual_task(int task, int n, int lg, const dou
 }
 
 template <bool FIRST>
-__global__ void __launch_bounds__(kRedThreads) k_outer_residual_t(
+__global__ void __launch_bounds__(kRedThreads, FIRST ? 2 : 3) k_outer_residual_t(
     const double *__restrict__ f, const double *__restrict__ x, int n, double h2, const double *__restrict__ fsum,
     double mu_host, float *__restrict__ s32, long long *__restrict__ bint, int *__restrict__ ebt, Reduction red) {
     pdl_enter();
@@ -1144,6 +1144,45 @@ __global__ void __launch_bounds__(kRedThreads) k_update(double *__restrict__ x,
             const size_t p = p0 + u * stride;
             if (p < N) x[p] = xv[u] + f32_to_f64(ev[u]);
             ee = fmaf(ev[u], ev[u], ee);
+        }
+    }
+    double vals[1] = {block_sum((double)ee, sh)};
+    reduce_finish<1>(red, vals, sh);
+}
+
+// The same update on 16-byte-aligned x and e, four points per 16-byte load of
+// e (two loads of x), two groups in flight per thread.  N is a multiple of 4.
+__global__ void __launch_bounds__(kRedThreads) k_update_v(double *__restrict__ x, const float *__restrict__ e,
+                                                          size_t N, Reduction red) {
+    pdl_enter();
+    __shared__ double sh[32];
+    float ee = 0.f;
+    const size_t G = N >> 2, stride = (size_t)gridDim.x * blockDim.x;
+    const float4 *e4 = reinterpret_cast<const float4 *>(e);
+    double2 *x2 = reinterpret_cast<double2 *>(x);
+    for (size_t g0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g0 < G; g0 += 2 * stride) {
+        float4 ev[2];
+        double2 xa[2], xb[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const size_t g = g0 + u * stride;
+            if (g < G) {
+                ev[u] = e4[g];
+                xa[u] = x2[2 * g];
+                xb[u] = x2[2 * g + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const size_t g = g0 + u * stride;
+            if (g < G) {
+                x2[2 * g] = make_double2(xa[u].x + f32_to_f64(ev[u].x), xa[u].y + f32_to_f64(ev[u].y));
+                x2[2 * g + 1] = make_double2(xb[u].x + f32_to_f64(ev[u].z), xb[u].y + f32_to_f64(ev[u].w));
+                ee = fmaf(ev[u].x, ev[u].x, ee);
+                ee = fmaf(ev[u].y, ev[u].y, ee);
+                ee = fmaf(ev[u].z, ev[u].z, ee);
+                ee = fmaf(ev[u].w, ev[u].w, ee);
+            }
         }
     }
     double vals[1] = {block_sum((double)ee, sh)};
@@ -1698,7 +1737,7 @@ cudaError_t launch_outer_residual_tasks(const double *f, const double *x, int n,
     const cudaError_t e =
         first ? launch_kernel(k_outer_residual_t<true>, kRedBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
                               s32, bint, ebt, red)
-              : launch_kernel(k_outer_residual_t<false>, kRedBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
+              : launch_kernel(k_outer_residual_t<false>, kResBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
                               s32, bint, ebt, red);
     if (e != cudaSuccess) return e;
     count_launches(1);
@@ -1714,9 +1753,11 @@ cudaError_t launch_convert(int dir, size_t count, const void *in, void *out, cud
     return cudaGetLastError();
 }
 cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaStream_t s) {
+    const size_t N = (size_t)n * n;
+    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(e)) & 15u) == 0 && (N & 3u) == 0;
     {
-        cudaError_t le_ = launch_kernel(k_update, kRedBlocks, kRedThreads, 0, s,
-                                        x, e, (size_t)n * n, red);
+        cudaError_t le_ = vec ? launch_kernel(k_update_v, kWideBlocks, kRedThreads, 0, s, x, e, N, red)
+                              : launch_kernel(k_update, kRedBlocks, kRedThreads, 0, s, x, e, N, red);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);
