@@ -540,6 +540,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-sr", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-smoothing", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-warmup", type=float, default=0.5)
     ap.add_argument("--serve-rates", type=lambda v: [float(t) for t in v.split(",")],
@@ -681,6 +682,27 @@ def main():
     # ---- serving: Poisson arrivals into the continuous-batching server -----
     serving = serve_leg(mg, dev, stream, args, rank) if not args.skip_serve else None
 
+    # ---- smoothing-count sweep: V(nu, nu) for nu = 1..4 on the same workload --
+    smoothing = None
+    if not args.skip_smoothing:
+        smoothing = {"workload": "the 2048^2 headline solve with V(nu, nu), nu = 1..4 (cubic, mixed, adaptive "
+                                 "V-cycles per outer step with the contraction estimate 0.06 of V(2,2))",
+                     "runs": []}
+        for nu in (1, 2, 3, 4):
+            cs = make_ctx("mixed")
+            cs.set_options(nu_pre=nu, nu_post=nu)
+            timed_solves(cs, 3, f_dev, x)  # warm-up (records the graph)
+            ts, inf = timed_solves(cs, SIDE_REPS, f_dev, x)
+            ms = sum(ts) / len(ts) * 1e3
+            vc = inf[-1]["vcycles"]
+            smoothing["runs"].append({
+                "nu": nu, "vcycles": vc, "outer_iters": inf[-1]["outer_iters"], "ms_per_solve": ms,
+                "solves_per_s": 1e3 / ms, "rel_residual": inf[-1]["rel_residual"],
+                # smoothing sweeps per V-cycle on the finest level, times V-cycles: the paper's
+                # iteration count weighted by the smoothing work it carries
+                "finest_sweeps_per_solve": 2 * nu * vc})
+            cs.close()
+
     cpu, err, rel, err64 = None, None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg(srcs[0])
@@ -717,6 +739,7 @@ def main():
             "batched": batched,
             "sr": sr_info,
             "serving": serving,
+            "smoothing_sweep": smoothing,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
