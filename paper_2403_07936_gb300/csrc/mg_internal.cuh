@@ -59,20 +59,31 @@ template <> struct Prec<double> {
 // small fraction of its FP32 rate, and the FP64 outer kernels are bound by
 // that pipe; these conversions use integer instructions instead, from the
 // IEEE 754 binary32 / binary64 layouts (1 sign bit; 8 / 11 exponent bits with
-// bias 127 / 1023; 23 / 52 fraction bits).  Normal results are handled here;
-// zeros, subnormals, infinities and NaNs (and results that would be
-// subnormal or overflow) take the hardware conversion, so every input gets
-// the same bits as cvt.rn.
+// bias 127 / 1023; 23 / 52 fraction bits).  f32_to_f64 handles every input;
+// f64_to_f32_rn handles normal results, and zeros, subnormals, infinities and
+// NaNs (and results that would be subnormal or overflow) take the hardware
+// conversion, so every input gets the same bits as cvt.rn.
 // ----------------------------------------------------------------------------
+// float -> double is exact for every input, so all classes are handled here
+// (a fallback to the hardware conversion would be evaluated by every lane and
+// occupy the FP64 pipe).  Normal: re-bias the exponent by 1023 - 127 = 896 and
+// widen the fraction by 29 bits.  Subnormal m * 2^-149 with leading bit p:
+// exponent field p + 874, fraction m shifted so that bit p lands on bit 52.
+// Infinity and NaN: exponent field 0x7ff, NaNs quieted (fraction bit 51).
 __device__ __forceinline__ double f32_to_f64(float v) {
     const unsigned u = __float_as_uint(v);
-    const unsigned ex = (u >> 23) & 0xffu;
-    if (ex == 0u || ex == 0xffu) return (double)v;
-    // exact: re-bias the exponent by 1023 - 127 = 896, widen the fraction by 29 bits
-    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                    ((unsigned long long)(ex + 896u) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
+    const unsigned ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    unsigned long long body = ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)m << 29);
+    if (ex == 0u) {
+        const int lz = __clz(m);  // m == 0: lz = 32 and the result is a signed zero
+        body = m ? (((unsigned long long)(905 - lz) << 52) |
+                    (((unsigned long long)m << (21 + lz)) & 0x000fffffffffffffull))
+                 : 0ull;
+    } else if (ex == 0xffu) {
+        body = (0x7ffull << 52) | ((unsigned long long)m << 29) | (m ? (1ull << 51) : 0ull);
+    }
+    return __longlong_as_double((long long)(sign | body));
 }
 
 __device__ __forceinline__ float f64_to_f32_rn(double v) {
