@@ -237,13 +237,40 @@ __device__ __forceinline__ void store_split(T *__restrict__ g, const T *red, con
     }
 }
 
+// Rows of the remainder columns that one warp instruction can cover without
+// shared-memory bank conflicts: the largest g <= 32 / kr for which the g rows'
+// runs of kr elements (a row is ck elements of wb 4-byte words further on)
+// fall into disjoint banks.
+__host__ __device__ constexpr int strip_rem_rows(int ck, int kr, int wb) {
+    int best = 1;
+    for (int g = 2; g * kr <= 32; ++g) {
+        bool ok = true;
+        for (int a = 0; a < g && ok; ++a)
+            for (int c = a + 1; c < g && ok; ++c) {
+                const int d = ((c - a) * ck * wb) % 32;  // bank offset of row c against row a
+                const int w = kr * wb;                   // banks a run of kr elements covers
+                ok = d >= w && 32 - d >= w;
+            }
+        if (ok) best = g;
+    }
+    return best;
+}
+
 // Visit the points of colour q in staged rows [r_lo, r_hi), split columns
-// [1, CK - 1), as vertical strips: thread (seg, k) walks rows of its segment,
-// keeping N and the centre of the other colour in registers.  body(p, N, S,
-// W, E) gets the split index p = r * CK + k of the point.
+// [1, CK - 1), and call body(p, N, S, W, E) with the split index p = r * CK + k
+// of each and its four neighbours (the other colour).  Columns 1 .. 32 go as
+// vertical strips, one warp per block of consecutive rows, lane k - 1 walking
+// down column k with N and the centre kept in registers: a warp's 32 lanes
+// read 32 consecutive elements of one row, so no bank conflicts.  The
+// remaining columns 33 .. CK - 2 go in groups of rows chosen so that one warp
+// instruction's rows fall into disjoint banks (strip_rem_rows).
+// Small tiles (a few rows per thread) are latency-bound rather than bound by
+// shared-memory bandwidth; there the rows go as NSEG segments of KW = CK - 2
+// consecutive threads each (warps may straddle two segments), which keeps the
+// chain of dependent rows per thread shortest.
 template <int CK, typename T, typename Body>
-__device__ __forceinline__ void colour_strips(const T *__restrict__ P, int r_lo, int r_hi, int q,
-                                              Body body) {
+__device__ __forceinline__ void colour_segments(const T *__restrict__ P, int r_lo, int r_hi, int q,
+                                                Body body) {
     constexpr int KW = CK - 2;
     constexpr int NSEG = kThreads / KW;
     const int seg = threadIdx.x / KW;
@@ -267,13 +294,61 @@ __device__ __forceinline__ void colour_strips(const T *__restrict__ P, int r_lo,
     }
 }
 
+template <int CK, bool STRIPS, typename T, typename Body>
+__device__ __forceinline__ void colour_strips(const T *__restrict__ P, int r_lo, int r_hi, int q,
+                                              Body body) {
+    if constexpr (!STRIPS) {
+        colour_segments<CK>(P, r_lo, r_hi, q, body);
+        return;
+    }
+    constexpr int KW = CK - 2;
+    constexpr int KM = KW < 32 ? KW : 32;  // columns of the strips
+    constexpr int KR = KW - KM;            // remainder columns
+    constexpr int NW = kThreads / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows = r_hi - r_lo;
+    if (lane < KM) {
+        const int per = (rows + NW - 1) / NW;
+        const int ra = r_lo + warp * per;
+        const int rb = min(r_hi, ra + per);
+        const int k = 1 + lane;
+        if (ra < rb) {
+            T pN = P[(ra - 1) * CK + k];
+            T pC = P[ra * CK + k];
+            for (int r = ra; r < rb; ++r) {
+                const T pS = P[(r + 1) * CK + k];
+                const int o = (r + q) & 1;
+                const T side = P[r * CK + k - 1 + 2 * o];
+                const T W = o ? pC : side;
+                const T E = o ? side : pC;
+                body(r * CK + k, pN, pS, W, E);
+                pN = pC;
+                pC = pS;
+            }
+        }
+    }
+    if constexpr (KR > 0) {
+        constexpr int RG = strip_rem_rows(CK, KR, (int)(sizeof(T) / 4));
+        const int dr = lane / KR, k = KM + 1 + (lane - dr * KR);
+        if (dr < RG) {
+            for (int r = r_lo + warp * RG + dr; r < r_hi; r += NW * RG) {
+                const T pN = P[(r - 1) * CK + k], pS = P[(r + 1) * CK + k], pC = P[r * CK + k];
+                const int o = (r + q) & 1;
+                const T side = P[r * CK + k - 1 + 2 * o];
+                body(r * CK + k, pN, pS, o ? pC : side, o ? side : pC);
+            }
+        }
+    }
+}
+
 // One Gauss-Seidel half-sweep of colour q: x <- (b + (((N + S) + W) + E)) / 4.
 // X and B point at the red arrays; the black ones follow A entries later.
-template <int CK, int A, typename T>
+// STRIPS: the conflict-free strip mapping (tiles of >= 32 rows), else segments.
+template <int CK, int A, bool STRIPS, typename T>
 __device__ __forceinline__ void half_sweep(T *X, const T *B, int r_lo, int r_hi, int q) {
     T *Xq = X + q * A;
     const T *Bq = B + q * A;
-    colour_strips<CK>(X + (q ^ 1) * A, r_lo, r_hi, q, [&](int p, T N, T S, T W, T E) {
+    colour_strips<CK, STRIPS>(X + (q ^ 1) * A, r_lo, r_hi, q, [&](int p, T N, T S, T W, T E) {
         Xq[p] = (Bq[p] + (((N + S) + W) + E)) * T(0.25);
     });
 }
@@ -322,7 +397,7 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
 #pragma unroll 1
         for (int q = 0; q < 2; ++q) {
             const int j = 2 * s + q + 1;  // valid region shrinks by one per half-sweep
-            half_sweep<CK, A>(X, B, j, R - j, q);
+            half_sweep<CK, A, (TY >= 32)>(X, B, j, R - j, q);
             __syncthreads();
         }
     }
@@ -331,7 +406,7 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
     for (int q = 0; q < 2; ++q) {
         const T *Xq = X + q * A;
         T *Bq = B + q * A;
-        colour_strips<CK>(X + (q ^ 1) * A, H - 1, H + TY + 1, q, [&](int p, T N, T S, T W, T E) {
+        colour_strips<CK, (TY >= 32)>(X + (q ^ 1) * A, H - 1, H + TY + 1, q, [&](int p, T N, T S, T W, T E) {
             Bq[p] = Bq[p] - (T(4) * Xq[p] - (((N + S) + W) + E));
         });
     }
@@ -515,7 +590,7 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
 #pragma unroll 1
             for (int q = 0; q < 2; ++q) {
                 const int j = 2 * s + q + 1;
-                half_sweep<CK, A>(X, B, j, R - j, q);
+                half_sweep<CK, A, (TY >= 32)>(X, B, j, R - j, q);
                 __syncthreads();
             }
         }
@@ -577,7 +652,7 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
 #pragma unroll 1
         for (int q = 0; q < 2; ++q) {
             const int j = 2 * s + q + 1;
-            half_sweep<CK, A>(X, B, j, R - j, q);
+            half_sweep<CK, A, (TY >= 32)>(X, B, j, R - j, q);
             __syncthreads();
         }
     }
