@@ -483,7 +483,10 @@ struct UpCfg {
     static constexpr int CC = TX / 2 + CHX + CXE;
     static constexpr int FW = TX + 2 * H;  // fine columns refined, v in [-H, TX + H)
     static constexpr int CRP = (CR + 1) / 2;            // row pairs of the packed coarse tile
-    static constexpr int U = cmax(2 * A, 2 * CRP * CC);  // coarse tile, then b (after the row pass)
+    // row pitch of the packed coarse tile in float2: 2 CCP = 8 (mod 32) 4-byte words,
+    // so the row pass's remainder groups of rows fall into disjoint banks
+    static constexpr int CCP = (CC + 15) / 16 * 16 + 4;
+    static constexpr int U = cmax(2 * A, 2 * CRP * CCP);  // coarse tile, then b (after the row pass)
     static constexpr size_t smem = (2ull * A + U + (size_t)CR * FW) * sizeof(T);
     static_assert(JW % NJ == 0 && IW % NJ == 0, "runs must tile the refined range");
 };
@@ -532,7 +535,7 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
             const int idx = threadIdx.x + i * kThreads;
             if (idx < CITEMS) {
                 const int rp = idx / CV, cv = idx - rp * CV;
-                float4 *dst = reinterpret_cast<float4 *>(cs2 + rp * CC + 4 * cv);
+                float4 *dst = reinterpret_cast<float4 *>(cs2 + rp * Cfg::CCP + 4 * cv);
                 dst[0] = make_float4(c0v[i].x, c1v[i].x, c0v[i].y, c1v[i].y);
                 dst[1] = make_float4(c0v[i].z, c1v[i].z, c0v[i].w, c1v[i].w);
             }
@@ -543,10 +546,14 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
         __syncthreads();
         SplitLoad<T, R, C> lb;  // b arrives while the row pass runs
         if (NU > 0) lb.issue(b, n, ty0 - H, tx0 - HX);
-        for (int item = threadIdx.x; item < CRP * JW; item += blockDim.x) {
-            const int rp = item / JW, jr = item - rp * JW;
+        // Both spline passes map one warp instruction to one row of items (32
+        // consecutive, conflict-free) and take each row's remaining items in
+        // groups of rows whose runs fall into disjoint banks (strip_rem_rows).
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        constexpr int NWARP = kThreads / 32;
+        auto row_item = [&](int rp, int jr) {
             const int J0 = -H / 2 + jr;
-            const float2 *w = cs2 + rp * CC + CHX + J0;  // w[m] = rows (2rp, 2rp+1) at coarse col J0 + m
+            const float2 *w = cs2 + rp * Cfg::CCP + CHX + J0;  // w[m] = rows (2rp, 2rp+1) at coarse col J0 + m
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = L; k >= 1; --k) acc = f2_fma(tp[k - 1], f2_add(w[k], w[1 - k]), acc);
@@ -554,12 +561,22 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
             const int col = 2 * J0 + H;
             *reinterpret_cast<float2 *>(rs + (2 * rp) * FW + col) = make_float2(node.x, acc.x);
             if (2 * rp + 1 < CR) *reinterpret_cast<float2 *>(rs + (2 * rp + 1) * FW + col) = make_float2(node.y, acc.y);
+        };
+        {
+            constexpr int JM = JW < 32 ? JW : 32, JR = JW - JM;
+            if (lane < JM)
+                for (int rp = warp; rp < CRP; rp += NWARP) row_item(rp, lane);
+            if constexpr (JR > 0) {
+                constexpr int RG = strip_rem_rows(Cfg::CCP, JR, 2);
+                const int dr = lane / JR, jr = JM + (lane - dr * JR);
+                if (dr < RG)
+                    for (int rp = warp * RG + dr; rp < CRP; rp += NWARP * RG) row_item(rp, jr);
+            }
         }
         __syncthreads();
         if (NU > 0) lb.scatter(B, B + A);
         constexpr int CP = FW / 2;
-        for (int item = threadIdx.x; item < IW * CP; item += blockDim.x) {
-            const int ir = item / CP, cp = item - ir * CP;
+        auto col_item = [&](int ir, int cp) {
             const int I0 = -H / 2 + ir;
             const float *w = rs + (CHY + I0) * FW + 2 * cp;  // columns 2cp, 2cp + 1
             float2 acc = make_float2(0.f, 0.f);
@@ -582,6 +599,17 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
                 const int q = (r + c) & 1;
                 X[q * A + r * CK + (c >> 1)] += ve;
                 X[(q ^ 1) * A + (r + 1) * CK + (c >> 1)] += vo;
+            }
+        };
+        {
+            constexpr int CM = CP < 32 ? CP : 32, CRM = CP - CM;
+            if (lane < CM)
+                for (int ir = warp; ir < IW; ir += NWARP) col_item(ir, lane);
+            if constexpr (CRM > 0) {
+                constexpr int RG = strip_rem_rows(FW / 2, CRM, 2);
+                const int dr = lane / CRM, cp = CM + (lane - dr * CRM);
+                if (dr < RG)
+                    for (int ir = warp * RG + dr; ir < IW; ir += NWARP * RG) col_item(ir, cp);
             }
         }
         __syncthreads();
