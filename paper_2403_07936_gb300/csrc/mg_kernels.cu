@@ -264,6 +264,42 @@ __host__ __device__ constexpr int strip_rem_rows(int ck, int kr, int wb) {
 // read 32 consecutive elements of one row, so no bank conflicts.  The
 // remaining columns 33 .. CK - 2 go in groups of rows chosen so that one warp
 // instruction's rows fall into disjoint banks (strip_rem_rows).
+// Walk split column k down rows [ra, rb) (ra < rb), calling body for each
+// point of colour q with N and the centre carried in registers.  Rows
+// alternate which neighbour (west or east) sits in the same split column; the
+// walk takes two rows per step with that alternation fixed at compile time,
+// after one branch on the first row's parity.
+template <int CK, typename T, typename Body>
+__device__ __forceinline__ void strip_walk(const T *__restrict__ P, int ra, int rb, int k, int q, Body &body) {
+    T pN = P[(ra - 1) * CK + k];
+    T pC = P[ra * CK + k];
+    auto row = [&](int r, auto odd) {
+        constexpr int o = decltype(odd)::value;
+        const T pS = P[(r + 1) * CK + k];
+        const T side = P[r * CK + k - 1 + 2 * o];
+        if constexpr (o) body(r * CK + k, pN, pS, pC, side);
+        else body(r * CK + k, pN, pS, side, pC);
+        pN = pC;
+        pC = pS;
+    };
+    using O0 = std::integral_constant<int, 0>;
+    using O1 = std::integral_constant<int, 1>;
+    int r = ra;
+    if (((ra + q) & 1) == 0) {
+        for (; r + 1 < rb; r += 2) {
+            row(r, O0{});
+            row(r + 1, O1{});
+        }
+        if (r < rb) row(r, O0{});
+    } else {
+        for (; r + 1 < rb; r += 2) {
+            row(r, O1{});
+            row(r + 1, O0{});
+        }
+        if (r < rb) row(r, O1{});
+    }
+}
+
 // Small tiles (a few rows per thread) are latency-bound rather than bound by
 // shared-memory bandwidth; there the rows go as NSEG segments of KW = CK - 2
 // consecutive threads each (warps may straddle two segments), which keeps the
@@ -280,6 +316,8 @@ __device__ __forceinline__ void colour_segments(const T *__restrict__ P, int r_l
     const int ra = r_lo + seg * per;
     const int rb = min(r_hi, ra + per);
     if (ra >= rb) return;
+    // per row parity (segments of one warp may start on rows of either parity,
+    // so a parity branch would diverge)
     T pN = P[(ra - 1) * CK + k];
     T pC = P[ra * CK + k];
     for (int r = ra; r < rb; ++r) {
@@ -312,20 +350,7 @@ __device__ __forceinline__ void colour_strips(const T *__restrict__ P, int r_lo,
         const int ra = r_lo + warp * per;
         const int rb = min(r_hi, ra + per);
         const int k = 1 + lane;
-        if (ra < rb) {
-            T pN = P[(ra - 1) * CK + k];
-            T pC = P[ra * CK + k];
-            for (int r = ra; r < rb; ++r) {
-                const T pS = P[(r + 1) * CK + k];
-                const int o = (r + q) & 1;
-                const T side = P[r * CK + k - 1 + 2 * o];
-                const T W = o ? pC : side;
-                const T E = o ? side : pC;
-                body(r * CK + k, pN, pS, W, E);
-                pN = pC;
-                pC = pS;
-            }
-        }
+        if (ra < rb) strip_walk<CK>(P, ra, rb, k, q, body);
     }
     if constexpr (KR > 0) {
         constexpr int RG = strip_rem_rows(CK, KR, (int)(sizeof(T) / 4));
