@@ -1252,7 +1252,7 @@ struct TickPlan {
     std::vector<RhsDesc> rhs, firsts, dones;
     std::vector<TileGrid> tiles;
     std::vector<BottomGrid> bottoms;
-    std::vector<BatchLaunch> cyc[kMaxAdaptive > 2 ? kMaxAdaptive : 2];
+    std::vector<BatchLaunch> cyc[kMaxAdaptive > 2 ? kMaxAdaptive : 2];  // see plan_cycles
     int blk = 0, blk_first = 0, blk_done = 0;
 };
 
@@ -1267,15 +1267,18 @@ static void plan_rhs(std::vector<RhsDesc> &v, int &blk, const ServerSlot &sl, in
     blk += nblk;
 }
 
-// V-cycle k (0-based) of this tick runs for the slots with m[slot] > k; cycle 0
-// starts the finest level from zero.
+// Tables of the tick's V-cycles.  Adaptive: table k serves V-cycle k (0-based)
+// and holds the slots with m[slot] > k.  Fixed count: table 0 serves the first
+// V-cycle and table 1 all later ones (every slot runs all of them).  The first
+// V-cycle starts the finest level from zero.
 static void plan_cycles(mg_server *sv, TickPlan &tp, const std::vector<int> &sids, const std::vector<int> &m) {
     int maxN = 0, maxm = 0;
     for (int sid : sids) {
         maxN = sv->slots[sid].N > maxN ? sv->slots[sid].N : maxN;
         maxm = m[sid] > maxm ? m[sid] : maxm;
     }
-    for (int v = 0; v < maxm; ++v) {
+    const int ntab = sv->adaptive ? maxm : (maxm > 1 ? 2 : 1);
+    for (int v = 0; v < ntab; ++v) {
         const bool first = v == 0;
         auto grids_of = [&](int sz) {
             int g = 0;

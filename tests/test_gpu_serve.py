@@ -49,7 +49,7 @@ def _check_exact(f, x):
     assert omg.relative_residual(f - f.mean(), x, omg.grid_h(f.shape[0])) <= 1.5e-10
 
 
-@pytest.mark.parametrize("inner", [0, 2])  # adaptive, fixed V-cycles per outer step
+@pytest.mark.parametrize("inner", [0, 2, 5])  # adaptive; fixed V-cycles per outer step
 def test_request_alone_equals_request_in_mix(mg, inner):
     f = _src(512, 0)
     ft = torch.tensor(f, device=DEV)
@@ -89,7 +89,7 @@ def test_request_alone_equals_request_in_mix(mg, inner):
         return
     # the same request as a one-member batched solve: the same kernels and sums
     ctx = mg.Context(7, 512)
-    ctx.set_options(inner_cycles=2)
+    ctx.set_options(inner_cycles=inner)
     xb = torch.zeros_like(ft)
     mg.solve_batched([ctx], [ft], [xb], tol=1e-10)
     assert torch.equal(alone, xb)
