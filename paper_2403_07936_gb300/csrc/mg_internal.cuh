@@ -59,10 +59,10 @@ template <> struct Prec<double> {
 // small fraction of its FP32 rate, and the FP64 outer kernels are bound by
 // that pipe; these conversions use integer instructions instead, from the
 // IEEE 754 binary32 / binary64 layouts (1 sign bit; 8 / 11 exponent bits with
-// bias 127 / 1023; 23 / 52 fraction bits).  f32_to_f64 handles every input;
-// f64_to_f32_rn handles normal results, and zeros, subnormals, infinities and
-// NaNs (and results that would be subnormal or overflow) take the hardware
-// conversion, so every input gets the same bits as cvt.rn.
+// bias 127 / 1023; 23 / 52 fraction bits).  Both handle every input on the
+// integer pipe (a fallback to the hardware conversion would be evaluated by
+// every lane of a warp and occupy the FP64 pipe); a GPU test compares them
+// bit for bit with the hardware conversions.
 // ----------------------------------------------------------------------------
 // float -> double is exact for every input, so all classes are handled here
 // (a fallback to the hardware conversion would be evaluated by every lane and
@@ -86,19 +86,40 @@ __device__ __forceinline__ double f32_to_f64(float v) {
     return __longlong_as_double((long long)(sign | body));
 }
 
+// double -> float, round to nearest even, for every input on the integer pipe.
+// Normal results: keep the top 23 of the 52 fraction bits and round on the 29
+// dropped; a carry out of the fraction bumps the exponent, which is the
+// correctly rounded result (infinity past the top).  Subnormal results (value
+// below 2^-126): the 53-bit significand scaled to units of 2^-149 and rounded
+// (a carry into bit 23 is the smallest normal).  Infinity and NaN keep their
+// class (NaNs quieted).
 __device__ __forceinline__ float f64_to_f32_rn(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned hi = (unsigned)(b >> 32);
-    const int ex = (int)((hi >> 20) & 0x7ffu) - 896;  // binary32 biased exponent
-    if (ex <= 0 || ex >= 0xff) return (float)v;
-    const unsigned frac = (unsigned)((b >> 29) & 0x7fffffu);  // top 23 of the 52 fraction bits
-    const unsigned rest = (unsigned)(b & 0x1fffffffu);         // the 29 bits dropped
-    unsigned u = (hi & 0x80000000u) | ((unsigned)ex << 23) | frac;
-    // round to nearest, ties to even; a carry out of the fraction bumps the
-    // exponent, which is the correctly rounded result (infinity past the top)
-    const unsigned half = 0x10000000u;
-    u += (rest > half || (rest == half && (frac & 1u))) ? 1u : 0u;
-    return __uint_as_float(u);
+    const unsigned sign = hi & 0x80000000u;
+    const int e64 = (int)((hi >> 20) & 0x7ffu);
+    const int ex = e64 - 896;  // binary32 biased exponent of a normal result
+    if (ex >= 1 && ex < 0xff) {
+        const unsigned frac = (unsigned)((b >> 29) & 0x7fffffu);  // top 23 of the 52 fraction bits
+        const unsigned rest = (unsigned)(b & 0x1fffffffu);         // the 29 bits dropped
+        unsigned u = sign | ((unsigned)ex << 23) | frac;
+        const unsigned half = 0x10000000u;
+        u += (rest > half || (rest == half && (frac & 1u))) ? 1u : 0u;
+        return __uint_as_float(u);
+    }
+    const unsigned long long m52 = b & 0x000fffffffffffffull;
+    if (e64 == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m52 ? (0x00400000u | (unsigned)(m52 >> 29)) : 0u));
+    if (ex >= 0xff) return __uint_as_float(sign | 0x7f800000u);  // overflow
+    if (e64 == 0) return __uint_as_float(sign);                  // binary64 subnormals round to zero
+    const unsigned long long mant = (1ull << 52) | m52;
+    const int sh = 926 - e64;  // >= 30
+    unsigned long long q = 0ull;
+    if (sh < 64) {
+        q = mant >> sh;
+        const unsigned long long r = mant - (q << sh), half = 1ull << (sh - 1);
+        q += (r > half || (r == half && (q & 1ull))) ? 1ull : 0ull;
+    }
+    return __uint_as_float(sign | (unsigned)q);
 }
 
 // ----------------------------------------------------------------------------
