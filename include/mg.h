@@ -236,12 +236,15 @@ void mg_server_destroy(mg_server *srv);
 mg_status mg_autotune(mg_ctx *ctx, const char *cache_path, int *n_timed);
 
 /* Programmatic dependent launch between the library's kernels (process-wide;
- * off unless the environment variable MG_LAUNCH_OVERLAP=1 was set at first
- * use).  When on, each kernel is launched with CUDA's programmatic stream
- * serialization and starts by waiting for its predecessor's completion, so
- * the next kernel's blocks are scheduled while the previous grid drains.
- * Results are identical either way; graphs recorded before a change are
- * re-recorded.  (Measured on GB300: slower for these kernels, hence off.) */
+ * mode 0 = off, the default unless the environment variable MG_LAUNCH_OVERLAP
+ * was 1 or 2 at first use).  Mode 1: every kernel is launched with CUDA's
+ * programmatic stream serialization and starts by waiting for its
+ * predecessor's completion, so the next kernel's blocks are scheduled while
+ * the previous grid drains; mode 2: only kernels whose grid has at most 304
+ * blocks (about one wave: the coarse levels, the bottom solve, the outer and
+ * convergence kernels).  Results are identical in every mode; graphs recorded
+ * before a change are re-recorded.  Returns MG_ERR_INVALID_ARG for other
+ * modes.  (Measured on GB300: both modes slower for these graphs, hence off.) */
 mg_status mg_set_launch_overlap(int enable);
 int mg_get_launch_overlap(void);
 
@@ -295,8 +298,9 @@ unsigned long long mg_kernel_launches(void);
 
 /* Record a CUDA event pair around each launch of one kernel kind on the
  * context's stream: 1 = finest-level pre-smoothing/restriction kernel,
- * 2 = finest-level prolongation/post-smoothing kernel, 3 = FP64 outer
- * residual, 4 = FP64 update, 5 = the coarse part of an FP32 V-cycle (every
+ * 2 = finest-level prolongation/post-smoothing kernel, 3 = outer residual
+ * (the exact sum of the FP64 iterate's residual), 4 = FP64 update, 5 = the
+ * coarse part of an FP32 V-cycle (every
  * launch below the finest level, as one span); 0 disables.  At most
  * `capacity` launches (spans) are recorded until mg_probe_read. */
 mg_status mg_probe_kernel(mg_ctx *ctx, int kind, int capacity);
@@ -385,7 +389,7 @@ mg_status mg_op_outer_residual(int n, const double *f, const double *x, double m
                                double *out, void *stream);
 
 /* The library's float <-> double conversions on the integer pipe (used by the
- * FP64 outer kernels in place of the FP64-pipe conversion instructions):
+ * outer kernels in place of the FP64-pipe conversion instructions):
  * dir 0: out[i] = (float)in[i] rounded to nearest even, in double, out float;
  * dir 1: out[i] = (double)in[i], in float, out double.  Device arrays of
  * count elements.  Exposed so that tests can compare them bit for bit with

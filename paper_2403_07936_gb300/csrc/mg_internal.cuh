@@ -56,8 +56,8 @@ template <> struct Prec<double> {
 // ----------------------------------------------------------------------------
 // Precision conversions on the integer pipe.  GB300 issues FP64 instructions
 // (which include the hardware conversions between float and double) at a
-// small fraction of its FP32 rate, and the FP64 outer kernels are bound by
-// that pipe; these conversions use integer instructions instead, from the
+// small fraction of its FP32 rate, and the outer kernels' few FP64 operations
+// are their bottleneck; these conversions use integer instructions instead, from the
 // IEEE 754 binary32 / binary64 layouts (1 sign bit; 8 / 11 exponent bits with
 // bias 127 / 1023; 23 / 52 fraction bits).  Both handle every input on the
 // integer pipe (a fallback to the hardware conversion would be evaluated by
@@ -282,7 +282,7 @@ struct BottomGrid {  // one block each
     const void *ainv;  // coarsest pseudo-inverse
     int n, nlev, zero, rhs;
 };
-struct RhsDesc {  // FP64 outer kernels: blocks [blk0, blk0 + nblk) serve this right-hand side
+struct RhsDesc {  // outer kernels: blocks [blk0, blk0 + nblk) serve this right-hand side
     const double *f;
     double *x;
     float *s32;      // float residual (inner right-hand side)
@@ -448,7 +448,7 @@ cudaError_t launch_check(DevState *st, const double *rsum, const double *usum, c
                          cudaGraphConditionalHandle handle, cudaStream_t s, double rho = 0.0,
                          CycleHandles ifh = CycleHandles{});
 
-// batched forms (float tile kernels; FP64 outer kernels)
+// batched forms (float tile kernels; outer kernels)
 // every grid of one batched launch uses the same variant; nblocks = sum of variant_tiles
 cudaError_t launch_down_batched(const TileGrid *tab, int ngrid, int nblocks, int nu, const int *active,
                                 cudaStream_t s, int variant);

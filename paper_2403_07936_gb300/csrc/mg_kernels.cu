@@ -19,10 +19,11 @@
 // Within one colour every update reads only the other colour, so the fused
 // sweeps give exactly the values of separate half-sweeps.
 //
-// FP64 outer kernels (defect correction around FP32 V-cycles): source sum,
-// scaled right-hand side, FP64 residual with norms and float conversion,
-// solution update, zero-mean projection.  Sums are deterministic (fixed grid,
-// fixed-order trees, last-block finish).
+// Outer kernels (FP64 defect correction around FP32 V-cycles): source sum,
+// scaled right-hand side, the residual of the FP64 iterate (summed exactly on
+// the integer pipe) with norms and float conversion, FP64 solution update,
+// zero-mean projection.  Sums are deterministic (fixed grid, fixed-order
+// trees, last-block finish).
 #include <math.h>
 #include <string.h>
 
@@ -1024,7 +1025,7 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom_batched(const BottomG
 }
 
 // ---------------------------------------------------------------------------
-// FP64 outer kernels
+// Outer kernels (FP64 data)
 // ---------------------------------------------------------------------------
 // The outer kernels are grid-stride loops over kRedBlocks x kRedThreads
 // threads with kUnroll independent points per iteration (loads in flight).
@@ -1411,7 +1412,7 @@ __global__ void k_policy(DevState *st, int k, ProlongPolicy p, int *flag, cudaGr
 }
 
 // ---------------------------------------------------------------------------
-// Batched FP64 outer kernels: the blocks of right-hand side r are
+// Batched outer kernels: the blocks of right-hand side r are
 // [blk0, blk0 + nblk); each right-hand side's sums finish in its last block.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_rhs(const RhsDesc *__restrict__ r, int nrhs) {

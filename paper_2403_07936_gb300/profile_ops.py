@@ -11,7 +11,7 @@ memory traffic and the instruction mix are of interest.
 ops:
   down   finest-level k_down (nu sweeps, residual, full weighting), FP32
   up     finest-level k_up (cubic prolongation, correction, nu sweeps), FP32
-  outer  FP64 outer residual with norms and FP32 conversion
+  outer  outer residual of FP64 data (exact stencil sum) with norms, float output
   conv   one tensor-core SR convolution layer (mode 0: conv + PReLU) on an
          n/2 x n/2 coarse grid of 64 channels
   solve  a whole mixed-precision solve of a seeded turbulent source (host-loop
