@@ -220,6 +220,43 @@ def prolong_cubic(ec: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(prolong_cubic_1d(rows, H))  # along y: (2 nc, 2 nc)
 
 
+def spline_values(v: np.ndarray, H: float, factor: int) -> np.ndarray:
+    """Periodic cubic interpolating splines along axis 0 (columns of v, node
+    spacing H) evaluated at the points k + j / factor, j = 0 .. factor - 1, of
+    every interval [k, k + 1]: with the nodes' second derivatives M (the
+    periodic system of spline_midpoints) and t = j / factor,
+    s = (1 - t) v_k + t v_{k+1} + (H^2 / 6) [((1 - t)^3 - (1 - t)) M_k + (t^3 - t) M_{k+1}]."""
+    rhs = (6.0 / (H * H)) * (np.roll(v, -1, 0) - 2.0 * v + np.roll(v, 1, 0))
+    M = _solve_cyclic_tridiagonal(1.0, 4.0, 1.0, rhs)
+    vn, Mn = np.roll(v, -1, 0), np.roll(M, -1, 0)
+    out = np.empty((factor * v.shape[0],) + v.shape[1:])
+    for j in range(factor):
+        t = j / factor
+        out[j::factor] = ((1.0 - t) * v + t * vn
+                          + (H * H / 6.0) * (((1.0 - t) ** 3 - (1.0 - t)) * M + (t ** 3 - t) * Mn))
+    return out
+
+
+def prolong_cubic_factor(ec: np.ndarray, factor: int) -> np.ndarray:
+    """Tensor-product periodic cubic spline prolongation by `factor` (a power
+    of two), (n / factor)^2 -> n^2: coarse node I -> fine factor * I, the spline
+    evaluated at every fine point, rows (along x) then columns (along y).  The
+    paper's two-level cycle interpolates the coarse correction by 16 in one
+    step with a bivariate spline (Sec. 4.1; Table 1 N_step = 4)."""
+    nc = ec.shape[0]
+    H = grid_h(nc)
+    rows = spline_values(ec.T, H, factor).T
+    return np.ascontiguousarray(spline_values(rows, H, factor))
+
+
+def restrict_fw_factor(r: np.ndarray, factor: int) -> np.ndarray:
+    """Restriction by `factor` (a power of two) as repeated full weighting."""
+    while factor > 1:
+        r = restrict_fw(r)
+        factor //= 2
+    return r
+
+
 def prolong_linear(ec: np.ndarray) -> np.ndarray:
     """Bilinear prolongation (textbook special case used to pin the V-cycle)."""
     nc = ec.shape[0]
@@ -343,6 +380,27 @@ def vcycle(x: np.ndarray, f: np.ndarray, h: float, nu1: int = 2, nu2: int = 2,
     x += prolong(ec)
     rbgs(x, f, h, nu2)
     return x
+
+
+def two_level_cycle(x: np.ndarray, f: np.ndarray, h: float, factor: int = 16, nu: int = 20,
+                    coarse_sweeps: int = 10) -> np.ndarray:
+    """One cycle of the paper's two-level scheme (Sec. 4.1; Algorithm 6 with a
+    single coarse level): relax nu times (red-black Gauss-Seidel), restrict the
+    residual by `factor`, relax the coarse correction equation coarse_sweeps
+    times from zero (Algorithm 6's coarsest-level relaxation; 0 = the exact
+    coarse solve), interpolate the correction back by `factor` with the cubic
+    spline and add it.  No post-smoothing (Algorithm 6 relaxes before the
+    coarse correction only)."""
+    x = x.copy()
+    rbgs(x, f, h, nu)
+    rc = restrict_fw_factor(residual(f, x, h), factor)
+    hc = h * factor
+    if coarse_sweeps > 0:
+        ec = np.zeros_like(rc)
+        rbgs(ec, rc, hc, coarse_sweeps)
+    else:
+        ec = coarse_solve(rc, hc)
+    return x + prolong_cubic_factor(ec, factor)
 
 
 def relative_residual(f: np.ndarray, x: np.ndarray, h: float) -> float:

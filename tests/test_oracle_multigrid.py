@@ -236,6 +236,64 @@ def test_spline_midpoint_symbol(m, k):
                                atol=1e-14)
 
 
+@pytest.mark.parametrize("factor", [2, 4, 16])
+def test_spline_values_match_scipy_periodic_cubicspline(factor):
+    """Evaluation of the periodic cubic spline at every fine point of a
+    refinement by `factor` equals SciPy's periodic CubicSpline."""
+    from scipy.interpolate import CubicSpline
+    rng = np.random.default_rng(factor)
+    m = 12
+    H = 2 * np.pi / m
+    v = rng.standard_normal((m, 3))
+    got = mg.spline_values(v, H, factor)
+    xs = np.arange(m + 1) * H
+    fine = np.arange(m * factor) * H / factor
+    for c in range(3):
+        cs = CubicSpline(xs, np.append(v[:, c], v[0, c]), bc_type="periodic")
+        np.testing.assert_allclose(got[:, c], cs(fine), rtol=0, atol=1e-13)
+
+
+def test_prolong_cubic_factor_invariants_and_factor_two():
+    """P_k 1 = 1, exact at coarse nodes, a tensor product of the 1-D splines,
+    and for factor 2 it is the midpoint prolongation."""
+    rng = np.random.default_rng(3)
+    ec = rng.standard_normal((8, 8))
+    p16 = mg.prolong_cubic_factor(ec, 16)
+    assert p16.shape == (128, 128)
+    np.testing.assert_allclose(p16[::16, ::16], ec, atol=1e-13)
+    np.testing.assert_allclose(mg.prolong_cubic_factor(np.full((8, 8), 2.5), 16), 2.5, atol=1e-13)
+    np.testing.assert_allclose(mg.prolong_cubic_factor(ec, 2), mg.prolong_cubic(ec), atol=1e-13)
+    # separable: a product of a row profile and a column profile stays one
+    a, b = rng.standard_normal(8), rng.standard_normal(8)
+    pa = mg.spline_values(a[:, None], mg.grid_h(8), 4)[:, 0]
+    pb = mg.spline_values(b[:, None], mg.grid_h(8), 4)[:, 0]
+    np.testing.assert_allclose(mg.prolong_cubic_factor(np.outer(a, b), 4), np.outer(pa, pb), atol=1e-12)
+
+
+def test_two_level_cycle_with_factor_two_is_a_v_cycle():
+    """With coarsening by 2 and an exact coarse solve the two-level cycle is the
+    V(nu, 0) cycle whose coarsest grid is n / 2; with factor 16 and 10 coarse
+    relaxations it still reduces the error (contraction < 1)."""
+    n = 32
+    h = mg.grid_h(n)
+    f = _rand_zero_mean(n, 7)
+    x0 = np.random.default_rng(8).standard_normal((n, n))
+    a = mg.two_level_cycle(x0, f, h, factor=2, nu=3, coarse_sweeps=0)
+    b = mg.vcycle(x0, f, h, nu1=3, nu2=0, coarsest=n // 2)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+    n = 64
+    h = mg.grid_h(n)
+    f = _rand_zero_mean(n, 9)
+    xe = mg.exact_solve_fft(f, h)
+    x = np.zeros((n, n))
+    errs = []
+    for _ in range(4):
+        x = mg.two_level_cycle(x, f, h, factor=16, nu=20, coarse_sweeps=10)
+        d = x - xe
+        errs.append(np.linalg.norm(d - d.mean()))
+    assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:]))
+
+
 def test_prolong_cubic_invariants():
     ec = np.random.default_rng(12).standard_normal((8, 8))
     p = mg.prolong_cubic(ec)
