@@ -541,6 +541,7 @@ def main():
     ap.add_argument("--skip-sr", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-smoothing", action="store_true")
+    ap.add_argument("--skip-two-level", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-warmup", type=float, default=0.5)
     ap.add_argument("--serve-rates", type=lambda v: [float(t) for t in v.split(",")],
@@ -709,6 +710,39 @@ def main():
         err, rel = oracle_accuracy(f_last, x_last)
         err64, _ = oracle_accuracy(f64_last, x64_last)
 
+    # ---- the paper's two-level x16 configuration (cubic spline prolongation) --
+    two_level = None
+    if not args.skip_two_level:
+        two_level = {"workload": "two-level cycles (Sec. 4.1): one coarse level 16x coarser, N_smooth red-black "
+                                 "sweeps on the finest grid, 10 coarse sweeps, cubic spline prolongation by 16 in "
+                                 "one step, FP32 cycles in FP64 defect correction, tol 1e-10, x from 0",
+                     "runs": []}
+        for n2, lev2 in ((1024, 8), (2048, 9)):
+            f2 = torch.tensor(turbulent_source(n2, n2 // 8, config_seed(1, rank * 100 + 50)), device=dev)
+            x2 = torch.zeros_like(f2)
+            c2 = mg.Context(lev2, n2)
+            c2.set_options(stream=stream)
+            for nus in (15, 20):
+                c2.two_level_solve(f2, x2, max_cycles=400, nu_smooth=nus, check=False)  # warm-up
+                ts2, inf2 = [], None
+                for _ in range(3):
+                    x2.zero_()
+                    torch.cuda.synchronize(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    inf2 = c2.two_level_solve(f2, x2, max_cycles=400, nu_smooth=nus, check=False)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ts2.append(e0.elapsed_time(e1))
+                xm = torch.zeros_like(f2)
+                vm = c2.solve(f2, xm)["vcycles"]
+                two_level["runs"].append({"n": n2, "nu_smooth": nus, "coarse_sweeps": 10, "status": inf2["status"],
+                                          "cycles": inf2["vcycles"], "rel_residual": inf2["rel_residual"],
+                                          "ms_per_solve": sum(ts2) / len(ts2),
+                                          "multilevel_vcycles_same_source": vm})
+            c2.close()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -740,6 +774,7 @@ def main():
             "sr": sr_info,
             "serving": serving,
             "smoothing_sweep": smoothing,
+            "two_level_x16": two_level,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -140,6 +140,22 @@ mg_status mg_solve(mg_ctx *ctx, const double *f, double *x, double tol, mg_prolo
  * one FP32 V-cycle.  x is not projected to zero mean. */
 mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *x, mg_prolong prolong);
 
+/* The paper's two-level configuration (Sec. 4.1; Table 1: N_step = 4, one
+ * coarse level 16 times coarser): FP64 defect correction as in mg_solve, each
+ * outer step running one FP32 two-level cycle from e = 0 - nu_smooth
+ * red-black Gauss-Seidel sweeps on the finest grid, the residual restricted by
+ * 2^coarsen_log2 (full weighting applied coarsen_log2 times), coarse_sweeps
+ * red-black sweeps of the coarse correction equation from zero (Algorithm 6's
+ * coarsest-level relaxation), the coarse correction interpolated back by
+ * 2^coarsen_log2 in one step with the periodic cubic spline (B-spline
+ * coefficients by a truncated exact inverse filter, then the tensor cubic
+ * B-spline at every fine point) and added; no post-smoothing.  MIXED contexts
+ * with levels >= coarsen_log2 + 2 and N >> coarsen_log2 >= 64; 0 <= nu_smooth
+ * <= 64; 1 <= coarse_sweeps <= 64.  info->vcycles and info->outer_iters count
+ * two-level cycles; MG_ERR_NOT_CONVERGED after max_cycles with the best x. */
+mg_status mg_two_level_solve(mg_ctx *ctx, const double *f, double *x, double tol, int coarsen_log2, int nu_smooth,
+                             int coarse_sweeps, int max_cycles, mg_solve_info *info);
+
 /* Solve B independent problems, ctxs[k] with f[k], x[k], each to tol.
  * Contexts may have different N.  When every context is MG_PREC_MIXED with
  * the same nu_pre, nu_post, inner_cycles and max_cycles, all buffers are in

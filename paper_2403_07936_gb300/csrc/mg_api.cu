@@ -19,6 +19,7 @@
 #include <cmath>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "mg_internal.cuh"
@@ -1817,6 +1818,122 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         info->sr_fallback = fallback ? 1 : 0;
         info->time_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return st;
+}
+
+// One FP32 two-level cycle on A e = s (s in the finest level's b32, e from
+// zero): nu red-black sweeps, the residual restricted by 2^k (full weighting
+// k times), ncs sweeps of the coarse correction equation from zero, the
+// coarse correction interpolated back by 2^k with the cubic spline and added.
+// Returns the buffer holding e.
+static mg_status two_level_cycle32(mg_ctx *c, int k, int nu, int ncs, float **e_out) {
+    cudaStream_t s = c->stream;
+    float *src = c->lv[0].x32, *dst = c->lv[0].t32;
+    int left = nu;
+    bool first = true;
+    do {  // fine sweeps in passes of <= 4; the last pass restricts its residual to level 1
+        const int m = left < 4 ? left : 4;
+        MG_CUDA(launch_down<float>(src, dst, c->lv[0].b32, c->lv[0].n, m, first, c->lv[1].b32, s));
+        std::swap(src, dst);
+        left -= m;
+        first = false;
+    } while (left > 0);
+    for (int l = 1; l < k; ++l)  // restrict the residual on down to level k (e = 0 there)
+        MG_CUDA(launch_down<float>(c->lv[l].x32, c->lv[l].t32, c->lv[l].b32, c->lv[l].n, 0, true,
+                                   c->lv[l + 1].b32, s));
+    float *cs = c->lv[k].x32, *cd = c->lv[k].t32;
+    left = ncs;
+    first = true;
+    do {  // coarse sweeps from zero (their restriction to level k + 1 is not used)
+        const int m = left < 4 ? left : 4;
+        MG_CUDA(launch_down<float>(cs, cd, c->lv[k].b32, c->lv[k].n, m, first, c->lv[k + 1].b32, s));
+        std::swap(cs, cd);
+        left -= m;
+        first = false;
+    } while (left > 0);
+    // B-spline coefficients of the coarse correction (rows into cd, then columns back into cs)
+    MG_CUDA(launch_bspline_coef(cs, cd, c->lv[k].n, 0, s));
+    MG_CUDA(launch_bspline_coef(cd, cs, c->lv[k].n, 1, s));
+    MG_CUDA(launch_prolong_factor(src, cs, c->lv[0].n, k, s));
+    *e_out = src;
+    return MG_OK;
+}
+
+mg_status mg_two_level_solve(mg_ctx *c, const double *f, double *x, double tol, int coarsen_log2, int nu_smooth,
+                             int coarse_sweeps, int max_cycles, mg_solve_info *info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    MG_TRY(check_common(c, f, x, MG_PROLONG_CUBIC));
+    const int k = coarsen_log2;
+    if (c->prec != MG_PREC_MIXED || k < 1 || k + 2 > c->levels || (c->N >> k) < 64 || nu_smooth < 0 ||
+        nu_smooth > 64 || coarse_sweeps < 1 || coarse_sweeps > 64 || max_cycles < 1 || !(tol > 0.0)) {
+        set_err("two-level solve: mixed precision; 1 <= coarsen_log2 with levels >= coarsen_log2 + 2 and "
+                "N >> coarsen_log2 >= 64; 0 <= nu_smooth <= 64; 1 <= coarse_sweeps <= 64; max_cycles >= 1; tol > 0");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_TRY(ensure_hierarchy(c, false));
+    const double *fd;
+    double *xd;
+    bool staged;
+    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged));
+    const int N = c->N;
+    const double N2 = (double)N * N;
+    const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
+    cudaStream_t s = c->stream;
+    MG_CUDA(launch_source_sum(fd, N, c->red(kGrpF), s));
+    mg_status st = MG_OK;
+    int cycles = 0;
+    double fnorm = 0.0, rel = INFINITY, mu = 0.0;
+    bool first = true;
+    for (;;) {  // FP64 defect correction, one FP32 two-level cycle per outer step
+        MG_CUDA(solve_residual(c, fd, xd, true, first, h2, s));
+        MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 2 * kMaxSlots, cudaMemcpyDeviceToHost, s));
+        MG_CUDA(cudaStreamSynchronize(s));
+        if (first) {
+            mu = c->host_out[kGrpF * kMaxSlots] / N2;
+            fnorm = sqrt(c->host_out[kGrpR * kMaxSlots + 1]);
+            first = false;
+        }
+        const double rnorm = sqrt(c->host_out[kGrpR * kMaxSlots]) / h2;
+        if (!isfinite(rnorm) || !isfinite(fnorm)) {
+            set_err("non-finite residual (NaN or Inf in f or x)");
+            st = MG_ERR_NONFINITE;
+            break;
+        }
+        if (fnorm == 0.0) {
+            MG_CUDA(cudaMemsetAsync(xd, 0, sizeof(double) * N * N, s));
+            rel = 0.0;
+            break;
+        }
+        rel = rnorm / fnorm;
+        if (rel <= tol) break;
+        if (cycles >= max_cycles) {
+            set_err("not converged: rel residual %.3e after %d two-level cycles", rel, cycles);
+            st = MG_ERR_NOT_CONVERGED;
+            break;
+        }
+        float *e = nullptr;
+        MG_TRY(two_level_cycle32(c, k, nu_smooth, coarse_sweeps, &e));
+        MG_CUDA(launch_update(xd, e, N, c->red(kGrpU), s));
+        ++cycles;
+    }
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
+        MG_CUDA(launch_sum(xd, N, c->red(kGrpX), s));
+        MG_CUDA(launch_project(xd, N, c->out(kGrpX), s));
+    }
+    if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 4 * kMaxSlots, cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        info->outer_iters = cycles;
+        info->vcycles = cycles;
+        info->rel_residual = rel;
+        info->removed_mean = mu;
+        info->update_norm = cycles > 0 ? sqrt(c->host_out[kGrpU * kMaxSlots]) : 0.0;
+        info->sr_cycles = 0;
+        info->prolong_used = MG_PROLONG_CUBIC;
+        info->sr_fallback = 0;
+        info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     return st;
 }

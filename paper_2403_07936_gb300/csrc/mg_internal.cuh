@@ -481,6 +481,17 @@ cudaError_t launch_check_batched(DevState *st, const RhsDesc *rd, int nrhs, cons
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s);
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum,
                               double *b, cudaStream_t s);
+// Cubic spline prolongation by 2^lgf in one step (the paper's two-level
+// configuration).  Coefficients: c = the periodic cubic B-spline coefficients
+// of the nc x nc coarse grid e, a truncated exact inverse of the B-spline
+// collocation filter (1, 4, 1) / 6 along one axis (dir 0 rows, 1 columns):
+// c_J = a_0 e_J + sum_{k=1..kBspTaps} a_k (e_{J+k} + e_{J-k}),
+// a_k = sqrt(3) (sqrt(3) - 2)^k.  Prolongation: e_f(i, j) += the tensor
+// cubic B-spline sum over the 4 x 4 coefficients around (i, j) / 2^lgf.
+constexpr int kBspTaps = 14;  // |sqrt(3) - 2|^15 < 3e-9: below FP32 rounding
+cudaError_t launch_bspline_coef(const float *e, float *c, int nc, int dir, cudaStream_t s);
+cudaError_t launch_prolong_factor(float *ef, const float *c, int n, int lgf, cudaStream_t s);
+
 // Task-tiled outer residual of mixed solves (grids of n >= kResMinN): each
 // warp takes tasks of 32 columns x kResRows rows and aligns all of a task's
 // operands to one exponent, the task's largest.  The first residual of a

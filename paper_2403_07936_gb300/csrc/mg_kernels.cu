@@ -1321,6 +1321,66 @@ __global__ void __launch_bounds__(kRedThreads) k_update_v(double *__restrict__ x
     reduce_finish<1>(red, vals, sh);
 }
 
+// ---------------------------------------------------------------------------
+// Cubic spline prolongation by 2^lgf (two-level configuration)
+// ---------------------------------------------------------------------------
+struct BspTaps {
+    float a[kBspTaps + 1];
+};
+
+// One axis of the B-spline coefficient filter (see launch_bspline_coef).
+__global__ void __launch_bounds__(kRedThreads) k_bspline_coef(const float *__restrict__ e, float *__restrict__ c,
+                                                              int nc, int dir, BspTaps taps) {
+    pdl_enter();
+    const int npt = nc * nc;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npt; p += gridDim.x * blockDim.x) {
+        const int I = p / nc, J = p - I * nc;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = kBspTaps; k >= 1; --k) {
+            const float u = dir == 0 ? e[I * nc + ((J + k) % nc)] : e[((I + k) % nc) * nc + J];
+            const float w = dir == 0 ? e[I * nc + ((J - k) % nc + nc) % nc] : e[(((I - k) % nc + nc) % nc) * nc + J];
+            acc = fmaf(taps.a[k], u + w, acc);
+        }
+        c[p] = fmaf(taps.a[0], e[p], acc);
+    }
+}
+
+// ef(i, j) += sum_{a,b = 0..3} wy_a wx_b c(I - 1 + a, J - 1 + b), (I, J) = (i, j) >> lgf,
+// w the uniform cubic B-spline weights at t = ((i, j) mod 2^lgf) / 2^lgf.
+__global__ void __launch_bounds__(kRedThreads) k_prolong_factor(float *__restrict__ ef, const float *__restrict__ c,
+                                                                int n, int lgf) {
+    pdl_enter();
+    const int nc = n >> lgf, lg = __ffs(n) - 1;
+    const float inv = 1.0f / (float)(1 << lgf);
+    const size_t npt = (size_t)n * n;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npt; p += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p >> lg), j = (int)(p & (size_t)(n - 1));
+        const int I = i >> lgf, J = j >> lgf;
+        float wy[4], wx[4];
+        const float ty = (float)(i & ((1 << lgf) - 1)) * inv, tx = (float)(j & ((1 << lgf) - 1)) * inv;
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            const float t = d ? tx : ty, u = 1.f - t;
+            float *w = d ? wx : wy;
+            w[0] = u * u * u * (1.f / 6.f);
+            w[1] = ((3.f * t - 6.f) * t * t + 4.f) * (1.f / 6.f);
+            w[2] = (((-3.f * t + 3.f) * t + 3.f) * t + 1.f) * (1.f / 6.f);
+            w[3] = t * t * t * (1.f / 6.f);
+        }
+        float v = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float *row = c + (size_t)((I - 1 + a + nc) % nc) * nc;
+            float r = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) r = fmaf(wx[b], row[(J - 1 + b + nc) % nc], r);
+            v = fmaf(wy[a], r, v);
+        }
+        ef[p] += v;
+    }
+}
+
 __global__ void k_convert(int dir, size_t count, const void *__restrict__ in, void *__restrict__ out) {
     pdl_enter();
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < count; p += (size_t)gridDim.x * blockDim.x) {
@@ -1872,6 +1932,30 @@ cudaError_t launch_outer_residual_tasks(const double *f, const double *x, int n,
               : launch_kernel(k_outer_residual_t<false>, kResBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
                               s32, bint, ebt, red);
     if (e != cudaSuccess) return e;
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_bspline_coef(const float *e, float *c, int nc, int dir, cudaStream_t s) {
+    if (nc < 4 || (dir != 0 && dir != 1) || e == c) return cudaErrorInvalidValue;
+    BspTaps t;
+    const double z = 1.7320508075688772 - 2.0;  // sqrt(3) - 2, the B-spline filter's pole
+    double a = 1.7320508075688772;
+    for (int k = 0; k <= kBspTaps; ++k, a *= z) t.a[k] = (float)a;
+    const int blocks = (nc * nc + kRedThreads - 1) / kRedThreads;
+    {
+        cudaError_t le_ = launch_kernel(k_bspline_coef, blocks < kRedBlocks ? blocks : kRedBlocks, kRedThreads, 0, s,
+                                        e, c, nc, dir, t);
+        if (le_ != cudaSuccess) return le_;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_prolong_factor(float *ef, const float *c, int n, int lgf, cudaStream_t s) {
+    if (lgf < 1 || (n >> lgf) < 4) return cudaErrorInvalidValue;
+    {
+        cudaError_t le_ = launch_kernel(k_prolong_factor, kWideBlocks, kRedThreads, 0, s, ef, c, n, lgf);
+        if (le_ != cudaSuccess) return le_;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
