@@ -15,6 +15,7 @@ weak scaling, no collective on the data path); the time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -438,6 +439,10 @@ def serve_leg(mg, dev, stream, args, rank):
     chains, sizes = _serve_sources(dev, rank)
     by_size = {n: [s for s in range(SERVE_STREAMS) if sizes[s] == n] for n in SERVE_SIZES}
     outs = [torch.zeros_like(c[0]) for c in chains]
+    # buffers of earlier legs are released here, not by the collector in the middle of a
+    # timed arrival process (a release synchronises the device)
+    gc.collect()
+    torch.cuda.synchronize(dev)
     srv = mg.Server(SERVE_BUDGET, stream=stream)
     step = [0] * SERVE_STREAMS
     rng = np.random.default_rng(12345 + rank)
@@ -464,6 +469,8 @@ def serve_leg(mg, dev, stream, args, rank):
         req_s = [by_size[SERVE_SIZES[k]][rng.integers(0, len(by_size[SERVE_SIZES[k]]))] for k in req_n]
         pending = {}
         lat, lat_n, cyc, bad, done_in_window = [], {n: [] for n in SERVE_SIZES}, [], 0, 0
+        gc.collect()
+        gc.disable()  # no collector pauses inside the arrival process (re-enabled after it)
         ticks, max_inflight = 0, 0
         i = 0
         t0 = time.perf_counter()
@@ -495,6 +502,7 @@ def serve_leg(mg, dev, stream, args, rank):
                     cyc.append(r["vcycles"])
             if t_done > deadline:
                 break
+        gc.enable()
         unfinished = len(pending) + (t_arr.size - i)
         while pending:  # drain what is left before the next rate
             srv.tick()
