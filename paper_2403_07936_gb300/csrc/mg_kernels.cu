@@ -747,6 +747,10 @@ constexpr int kBottomThreads = 1024;
 // and a half-sweep's colour choice is warp-uniform.  Smaller levels use
 // lanes of warp 0.  The lanes of one row are adjacent, so the west and east
 // neighbours of a run's end points come from the neighbouring lanes.
+// log2 of a power of two (shifts instead of integer division by sizes
+// known only at run time)
+__device__ __forceinline__ int ilog2(int v) { return __ffs(v) - 1; }
+
 struct RunMap {
     int row, c0;         // the run's row and first column
     int lane_w, lane_e;  // lanes holding the runs to the west and east (periodic)
@@ -761,11 +765,11 @@ __device__ __forceinline__ RunMap run_map(int m) {
         const int w = runs >> 5;
         r.warp_on = warp < w;
         r.on = r.warp_on;
-        r.row = warp + (lane / tpr) * w;
+        r.row = warp + (lane >> ilog2(tpr)) * w;
     } else {
         r.warp_on = warp == 0;
         r.on = warp == 0 && lane < runs;
-        r.row = lane / tpr;
+        r.row = lane >> ilog2(tpr);
     }
     r.c0 = (lane & (tpr - 1)) << 2;
     const int base = lane & ~(tpr - 1);
@@ -850,6 +854,76 @@ __device__ __forceinline__ T spline_mid_row(const T *E, int J, int mc, const Fir
     return acc;
 }
 
+// FP32 prolongation and correction of one bottom level: x (m x m) +=
+// spline(E), E the coarse error (mc = m / 2 a side), S the m x mc scratch of
+// row-refined coarse rows.  Each midpoint sums its taps in the same order as
+// spline_mid_row (k = L down to 1), but a thread computes several midpoints
+// from one window of loaded values: along x, 4 midpoints of a coarse row from
+// 9 aligned 16-byte loads; along y, 4 odd fine rows of one column from
+// 2L + 3 loads.  Ends with the level's x updated and a barrier.
+__device__ __forceinline__ void bottom_prolong_f32(float *X, const float *E, float *S, int m,
+                                                   const FirTaps &taps) {
+    constexpr int L = Prec<float>::L;
+    static_assert(L <= 16, "the x window holds 16 + 4 + 16 coarse values");
+    const int mc = m >> 1, tid = threadIdx.x, nt = blockDim.x;
+    // along x: item (I, J0), J0 a multiple of 4: coarse row I, midpoints
+    // J0 + 1/2 .. J0 + 7/2; window w[p] = E[I][J0 - 16 + p], p < 36
+    for (int t = tid; t < mc * (mc >> 2); t += nt) {
+        const int I = t >> ilog2(mc >> 2), J0 = (t - I * (mc >> 2)) << 2;
+        const float *Er = E + I * mc;
+        float w[36];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float4 v = *reinterpret_cast<const float4 *>(Er + ((J0 - 16 + 4 * q) & (mc - 1)));
+            w[4 * q] = v.x;
+            w[4 * q + 1] = v.y;
+            w[4 * q + 2] = v.z;
+            w[4 * q + 3] = v.w;
+        }
+        float o[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = L; k >= 1; --k) acc += Prec<float>::tap(taps, k) * (w[16 + i + k] + w[17 + i - k]);
+            o[2 * i] = w[16 + i];
+            o[2 * i + 1] = acc;
+        }
+        float *Sr = S + I * m + 2 * J0;
+        *reinterpret_cast<float4 *>(Sr) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(Sr + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    __syncthreads();
+    // along y: odd fine rows 2I + 1 (I = I0 .. I0 + 3) of column c from the
+    // window v[q] = S[I0 + 1 - L + q][c]; even fine rows 2I take S row I
+    const int nodd = m * (mc >> 2), neven = (m * m) >> 3;
+    for (int t = tid; t < nodd + neven; t += nt) {
+        if (t < nodd) {
+            const int c = t & (m - 1), I0 = (t >> ilog2(m)) << 2;
+            float v[2 * L + 3];
+#pragma unroll
+            for (int q = 0; q < 2 * L + 3; ++q) v[q] = S[((I0 + 1 - L + q) & (mc - 1)) * m + c];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = L; k >= 1; --k) acc += Prec<float>::tap(taps, k) * (v[i + k + L - 1] + v[i - k + L]);
+                float *xp = X + (2 * (I0 + i) + 1) * m + c;
+                *xp = *xp + acc;
+            }
+        } else {
+            const int e = t - nodd, row = (e >> ilog2(m >> 2)) << 1, c0 = (e - (row >> 1) * (m >> 2)) << 2;
+            float xv[4], sv[4];
+            RunIO<float>::ld(X + row * m + c0, xv);
+            RunIO<float>::ld(S + (row >> 1) * m + c0, sv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xv[a] += sv[a];
+            RunIO<float>::st(X + row * m + c0, xv);
+        }
+    }
+    __syncthreads();
+}
+
 // Shared-memory elements of a bottom solve of an n x n grid with nlev levels:
 // x and b per level, n * n / 2 for the row-refined coarse grid of the
 // prolongation and n * n for the residual that full weighting reads.
@@ -858,6 +932,25 @@ __host__ __device__ constexpr size_t bottom_elems(int n, int nlev) {
     for (int l = 0; l < nlev; ++l) e += 2ull * (n >> l) * (n >> l);
     return e;
 }
+
+// A coarsest grid of at most this many points keeps its pseudo-inverse
+// (Nc^2 entries) in shared memory, staged together with the finest level.
+constexpr int kBottomAinvShared = 64;
+
+__host__ __device__ constexpr size_t bottom_smem_elems(int n, int nlev) {
+    const size_t nc = (size_t)(n >> (nlev - 1)) * (n >> (nlev - 1));
+    return bottom_elems(n, nlev) + (nc <= (size_t)kBottomAinvShared ? nc * nc : 0);
+}
+
+// The largest bottom configuration: kBottomMax^2 over any level count that
+// ends at a coarsest grid of at least 4^2.
+constexpr size_t bottom_smem_max() {
+    size_t best = 0;
+    for (int l = 1; (kBottomMax >> (l - 1)) >= 4; ++l)
+        best = bottom_smem_elems(kBottomMax, l) > best ? bottom_smem_elems(kBottomMax, l) : best;
+    return best;
+}
+
 
 template <typename T>
 __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restrict__ b, int n, int nlev,
@@ -869,14 +962,42 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
     // above it take 2 (n^2 + (n/2)^2 + ... + (2m)^2) = 8 (n^2 - m^2) / 3 elements
     auto X = [&](int l) { const int m = n >> l; return base + 8 * (n * n - m * m) / 3; };
     auto B = [&](int l) { const int m = n >> l; return base + 8 * (n * n - m * m) / 3 + m * m; };
-    const int mlast = n >> (nlev - 1);
+    const int mlast = n >> (nlev - 1), Nc = mlast * mlast;
     T *S = base + 8 * (n * n - mlast * mlast) / 3 + 2 * mlast * mlast;  // n * n / 2: row-refined coarse rows
     T *R = S + n * n / 2;  // n * n: residual of the level being restricted
+    T *Ash = R + n * n;    // Nc * Nc: the coarsest grid's pseudo-inverse (small coarsest grids)
+    const bool a_sh = Nc <= kBottomAinvShared;
     const int tid = threadIdx.x, nt = blockDim.x;
 
-    for (int p = tid; p < n * n; p += nt) {
-        X(0)[p] = zero_init ? T(0) : x[p];
-        B(0)[p] = b[p];
+    // Stage x, b and the pseudo-inverse with 16-byte loads, every load of a
+    // thread issued before its stores; element by element when a pointer is
+    // unaligned.
+    constexpr int VW = Prec<T>::VW;
+    using V = typename Prec<T>::vec;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(b) |
+                           reinterpret_cast<uintptr_t>(ainv)) & 15) == 0;
+    if (aligned) {
+        const int nx = (n * n) / VW, na = a_sh ? (Nc * Nc) / VW : 0;
+        for (int i = tid; i < max(nx, na); i += nt) {
+            V vx{}, vb{}, va{};
+            if (i < nx) {
+                if (!zero_init) vx = reinterpret_cast<const V *>(x)[i];
+                vb = reinterpret_cast<const V *>(b)[i];
+            }
+            if (i < na) va = reinterpret_cast<const V *>(ainv)[i];
+            if (i < nx) {
+                reinterpret_cast<V *>(X(0))[i] = vx;
+                reinterpret_cast<V *>(B(0))[i] = vb;
+            }
+            if (i < na) reinterpret_cast<V *>(Ash)[i] = va;
+        }
+    } else {
+        for (int p = tid; p < n * n; p += nt) {
+            X(0)[p] = zero_init ? T(0) : x[p];
+            B(0)[p] = b[p];
+        }
+        if (a_sh)
+            for (int p = tid; p < Nc * Nc; p += nt) Ash[p] = ainv[p];
     }
     __syncthreads();
     for (int l = 0; l + 1 < nlev; ++l) {
@@ -939,14 +1060,22 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
     {   // coarsest grid: e = A~^+ b (the pseudo-inverse annihilates the mean).
         // tpo threads per output row take strided partial dot products (coalesced
         // loads, all issued in parallel), then a shuffle tree within the group.
-        const int mcst = n >> (nlev - 1), Nc = mcst * mcst;
         T *Xc = X(nlev - 1);
         const T *Bc = B(nlev - 1);
-        const int tpo = min(32, nt / Nc);  // powers of two: groups never straddle a warp
-        const int p = tid / tpo, lane = tid - p * tpo;
+        const int tpo = min(32, nt >> ilog2(Nc));  // powers of two: groups never straddle a warp
+        const int p = tid >> ilog2(tpo), lane = tid - p * tpo;
         T acc = T(0);
-        if (p < Nc)
-            for (int q = lane; q < Nc; q += tpo) acc += ainv[p * Nc + q] * Bc[q];
+        if (p < Nc) {
+            if (a_sh) {  // Nc <= 64 and tpo >= 16: at most 4 terms, from shared memory
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int q = lane + k * tpo;
+                    if (q < Nc) acc += Ash[p * Nc + q] * Bc[q];
+                }
+            } else {
+                for (int q = lane; q < Nc; q += tpo) acc += ainv[p * Nc + q] * Bc[q];
+            }
+        }
         for (int o = tpo >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, tpo);
         if (p < Nc && lane == 0) Xc[p] = acc;
         __syncthreads();
@@ -955,52 +1084,65 @@ __device__ __forceinline__ void bottom_body(T *__restrict__ x, const T *__restri
     for (int l = nlev - 2; l >= 0; --l) {
         const int m = n >> l, mc = m >> 1;
         const T *E = X(l + 1);
-        // refine coarse rows along x: runs of 4 fine columns j0 .. j0 + 3 of
-        // coarse row I (coarse values at j0, j0 + 2, midpoints between)
-        for (int t = tid; t < (m * m) >> 3; t += nt) {
-            const int I = t / (m >> 2), j0 = (t - I * (m >> 2)) << 2, J0 = j0 >> 1;
-            const T *Er = E + I * mc;
-            T o[4];
-            o[0] = Er[J0];
-            o[1] = spline_mid_row(Er, J0, mc, taps);
-            o[2] = Er[J0 + 1];
-            o[3] = spline_mid_row(Er, J0 + 1, mc, taps);
-            RunIO<T>::st(S + I * m + j0, o);
-        }
-        __syncthreads();
-        // refine along y and add to the level's x, in the level's runs
-        const RunMap r = run_map(m);
         T xr[4] = {}, br[4] = {};
-        if (r.on) {
-            T val[4];
-            if ((r.row & 1) == 0) {
-                RunIO<T>::ld(S + (r.row >> 1) * m + r.c0, val);
-            } else {
-                const int I = r.row >> 1;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) val[a] = T(0);
-#pragma unroll
-                for (int k = L; k >= 1; --k) {
-                    T u[4], w[4];
-                    RunIO<T>::ld(S + ((I + k) & (mc - 1)) * m + r.c0, u);
-                    RunIO<T>::ld(S + ((I + 1 - k) & (mc - 1)) * m + r.c0, w);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) val[a] += Prec<T>::tap(taps, k) * (u[a] + w[a]);
-                }
+        const RunMap r = run_map(m);
+        if constexpr (sizeof(T) == 4) {
+            bottom_prolong_f32(X(l), E, S, m, taps);
+            if (r.on) {
+                RunIO<T>::ld(X(l) + r.row * m + r.c0, xr);
+                RunIO<T>::ld(B(l) + r.row * m + r.c0, br);
             }
-            RunIO<T>::ld(X(l) + r.row * m + r.c0, xr);
+        } else {
+            // refine coarse rows along x: runs of 4 fine columns j0 .. j0 + 3 of
+            // coarse row I (coarse values at j0, j0 + 2, midpoints between)
+            for (int t = tid; t < (m * m) >> 3; t += nt) {
+                const int I = t >> ilog2(m >> 2), j0 = (t - I * (m >> 2)) << 2, J0 = j0 >> 1;
+                const T *Er = E + I * mc;
+                T o[4];
+                o[0] = Er[J0];
+                o[1] = spline_mid_row(Er, J0, mc, taps);
+                o[2] = Er[J0 + 1];
+                o[3] = spline_mid_row(Er, J0 + 1, mc, taps);
+                RunIO<T>::st(S + I * m + j0, o);
+            }
+            __syncthreads();
+            // refine along y and add to the level's x, in the level's runs
+            if (r.on) {
+                T val[4];
+                if ((r.row & 1) == 0) {
+                    RunIO<T>::ld(S + (r.row >> 1) * m + r.c0, val);
+                } else {
+                    const int I = r.row >> 1;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) xr[a] += val[a];
-            RunIO<T>::st(X(l) + r.row * m + r.c0, xr);
-            RunIO<T>::ld(B(l) + r.row * m + r.c0, br);
+                    for (int a = 0; a < 4; ++a) val[a] = T(0);
+#pragma unroll
+                    for (int k = L; k >= 1; --k) {
+                        T u[4], w[4];
+                        RunIO<T>::ld(S + ((I + k) & (mc - 1)) * m + r.c0, u);
+                        RunIO<T>::ld(S + ((I + 1 - k) & (mc - 1)) * m + r.c0, w);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) val[a] += Prec<T>::tap(taps, k) * (u[a] + w[a]);
+                    }
+                }
+                RunIO<T>::ld(X(l) + r.row * m + r.c0, xr);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xr[a] += val[a];
+                RunIO<T>::st(X(l) + r.row * m + r.c0, xr);
+                RunIO<T>::ld(B(l) + r.row * m + r.c0, br);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         for (int s = 0; s < nu2; ++s) {
             run_half_sweep(X(l), br, xr, r, m, 0);
             run_half_sweep(X(l), br, xr, r, m, 1);
         }
     }
-    for (int p = tid; p < n * n; p += nt) x[p] = X(0)[p];
+    if (aligned) {
+        for (int p = VW * tid; p < n * n; p += VW * nt)
+            *reinterpret_cast<V *>(x + p) = *reinterpret_cast<const V *>(X(0) + p);
+    } else {
+        for (int p = tid; p < n * n; p += nt) x[p] = X(0)[p];
+    }
 }
 
 template <typename T>
@@ -1843,10 +1985,10 @@ cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu
     int nlev = 0;
     for (int m = n; m >= coarsest; m >>= 1) ++nlev;
     if ((n >> (nlev - 1)) != coarsest || nlev > 8) return cudaErrorInvalidValue;
-    const size_t smem = bottom_elems(n, nlev) * sizeof(T);
+    const size_t smem = bottom_smem_elems(n, nlev) * sizeof(T);
     auto k = k_bottom<T>;
     static std::atomic<unsigned> done{0};
-    cudaError_t e = set_smem_once(k, bottom_elems(bottom_max<T>(), 6) * sizeof(T), done);  // largest: down to 4^2
+    cudaError_t e = set_smem_once(k, bottom_smem_max() * sizeof(T), done);
     if (e != cudaSuccess) return e;
     {
         cudaError_t le_ = launch_kernel(k, 1, kBottomThreads, smem, s,
@@ -2087,7 +2229,7 @@ cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int n
 
 cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int nu2, const int *active,
                                   const FirTaps &taps, cudaStream_t s) {
-    const size_t bytes = bottom_elems(kBottomMax, 6) * sizeof(float);  // the largest: 128^2 down to 4^2
+    const size_t bytes = bottom_smem_max() * sizeof(float);  // every grid of the table fits
     static std::atomic<unsigned> done{0};
     cudaError_t e = set_smem_once(k_bottom_batched<float>, bytes, done);
     if (e != cudaSuccess) return e;
@@ -2217,8 +2359,8 @@ static cudaError_t prepare_type() {
     if (e == cudaSuccess) e = prepare_nu<T, 2>();
     if (e == cudaSuccess) e = prepare_nu<T, 3>();
     if (e == cudaSuccess) e = prepare_nu<T, 4>();
-    // the bottom kernel's largest configuration: bottom_max<T>()^2 down to 4^2
-    if (e == cudaSuccess) e = set_smem(k_bottom<T>, bottom_elems(bottom_max<T>(), 6) * sizeof(T));
+    // the bottom kernel's largest configuration
+    if (e == cudaSuccess) e = set_smem(k_bottom<T>, bottom_smem_max() * sizeof(T));
     return e;
 }
 

@@ -102,3 +102,12 @@ def test_tile_variant_table_host_logic(lib):
     finally:
         mg.set_tile_variant(0, 4096, 3, old_d)
         mg.set_tile_variant(1, 4096, 3, old_u)
+
+
+def test_empty_batch_is_a_no_op(lib):
+    """A batch of zero right-hand sides succeeds without touching a device."""
+    from paper_2403_07936_gb300 import mg
+    H, F, X = (C.c_void_p * 1)(), (C.c_void_p * 1)(), (C.c_void_p * 1)()
+    infos = (mg.SolveInfo * 1)()
+    assert lib.mg_solve_batched(H, F, X, 0, 1e-10, 0, infos) == 0
+    assert lib.mg_solve_batched(H, F, X, -1, 1e-10, 0, infos) == 1

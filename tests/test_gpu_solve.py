@@ -75,6 +75,53 @@ def test_solve_2048_full_size(mg, precision):
     assert info["vcycles"] <= 12
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_solve_maximum_size(mg, precision):
+    """The largest grid the library accepts, 16384^2 with 12 levels down to 8^2.
+    The source is a sum of Fourier modes cos(2 pi (kx j + ky i) / n + phase); each
+    is an eigenvector of the periodic 5-point operator with eigenvalue
+    (4 sin^2(pi kx / n) + 4 sin^2(pi ky / n)) / h^2, so the exact discrete
+    solution is the same sum with every amplitude divided by its eigenvalue.
+    Fields are built on the device in FP64 from outer products of 1-D cosines
+    and sines (the oracle's dense FFT would need minutes at this size)."""
+    n = 16384
+    h = 2 * np.pi / n
+    rng = np.random.default_rng(config_seed(3, 0))
+    kmax = n // 8
+    ks = [(1, 0), (0, 3)] + [tuple(int(v) for v in rng.integers(-kmax, kmax + 1, 2)) for _ in range(22)]
+    ks = [k for k in ks if k != (0, 0)]
+    # amplitudes growing like |k| (most of the source's norm at high wavenumbers,
+    # as in the turbulent source): with a source dominated by its lowest mode,
+    # rounding x to binary64 alone leaves a relative residual of about
+    # 1e-16 / h^2 ~ 1e-9 at this size, above the tolerance
+    amp = np.array([1.0] + [rng.standard_normal() * np.hypot(*k) for k in ks[1:]])
+    phase = rng.uniform(0.0, 2 * np.pi, len(ks))
+    idx = torch.arange(n, device=DEV, dtype=torch.int64)
+    f = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+    xe = torch.zeros_like(f)
+    for (kx, ky), a, ph in zip(ks, amp, phase):
+        th = 2 * np.pi * ((kx * idx) % n).double() / n + ph  # column j
+        ps = 2 * np.pi * ((ky * idx) % n).double() / n  # row i
+        lam = (4 * np.sin(np.pi * kx / n) ** 2 + 4 * np.sin(np.pi * ky / n) ** 2) / h ** 2
+        mode = torch.outer(torch.cos(ps), torch.cos(th))
+        mode -= torch.outer(torch.sin(ps), torch.sin(th))
+        f.add_(mode, alpha=float(a))
+        xe.add_(mode, alpha=float(a / lam))
+        del mode
+    ctx = mg.Context(12, n, precision=precision)
+    x = torch.zeros_like(f)
+    info = ctx.solve(f, x, tol=1e-10)
+    assert info["rel_residual"] <= 1e-10
+    # residual recomputed here with the 5-point stencil on the device
+    fz = f - f.mean()
+    r = fz - (4 * x - x.roll(1, 0) - x.roll(-1, 0) - x.roll(1, 1) - x.roll(-1, 1)) / h ** 2
+    assert (r.norm() / fz.norm()).item() <= 1.5e-10
+    del r, fz
+    err = (x - xe).abs().max().item() / xe.abs().max().item()
+    assert err <= 1e-8, err
+    assert abs(x.mean().item()) <= 1e-12 * x.abs().max().item()
+
+
 def test_solve_64_config_batch_of_seeds(mg):
     """64^2, 4 levels, FP64 V(2,2): several independent seeds."""
     ctx = mg.Context(4, 64, precision="fp64")
