@@ -668,6 +668,30 @@ def main():
     value_e2e = weak_scaling_value(sum(te2e), n_e2e, world, dist, dev)
     bytes_grid = N * N * 8
 
+    # the host link's copy bandwidth, for the end-to-end bound: a solve from
+    # host buffers copies f and x in and x out around the device solve
+    def link_ms(fn, reps=10):
+        with torch.cuda.stream(stream):
+            fn()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    def h2d():
+        f_dev[0].copy_(f_host[0], non_blocking=True)
+        x.copy_(x_host, non_blocking=True)
+
+    def d2h():
+        x_host.copy_(x, non_blocking=True)
+
+    h2d_gbs = 2 * bytes_grid / (link_ms(h2d) * 1e-3) / 1e9
+    d2h_gbs = bytes_grid / (link_ms(d2h) * 1e-3) / 1e9  # (f_host[0] holds f_dev[0]'s source)
+
     # ---- roofline of the dominant kernel -----------------------------------
     peak, peak_src = read_peaks()
     roofline = kernel_roofline(dom, n_l, probe_ms, probe_bytes, peak, peak_src)
@@ -765,7 +789,11 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": value_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * bytes_grid,
                     "d2h_bytes_per_step": bytes_grid,
-                    "path": "mg_solve with pinned host f and x (copies inside the call)"},
+                    "path": "mg_solve with pinned host f and x (copies inside the call)",
+                    "link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs},
+                    "bound": 1.0 / (mean_step + 2 * bytes_grid / (h2d_gbs * 1e9) + bytes_grid / (d2h_gbs * 1e9)),
+                    "bound_note": "1 / (device solve time + copies at the measured host-link bandwidths): "
+                                  "the copies cannot overlap the solve, which needs all of f and x first"},
             "gpu_launches": launches,
             "clocks": clocks,
             "wall_s_timed_region": t_wall,

@@ -602,40 +602,62 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
         __syncthreads();
         if (NU > 0) lb.scatter(B, B + A);
         constexpr int CP = FW / 2;
-        auto col_item = [&](int ir, int cp) {
-            const int I0 = -H / 2 + ir;
-            const float *w = rs + (CHY + I0) * FW + 2 * cp;  // columns 2cp, 2cp + 1
-            float2 acc = make_float2(0.f, 0.f);
+        // Column pass: an item refines two adjacent fine columns (2cp, 2cp + 1)
+        // at the midpoints of coarse rows I0 and I0 + 1 (rows 2 I0 + 1 and
+        // 2 I0 + 3).  Each midpoint sums its taps k = L .. 1 in the order of the
+        // one-midpoint form; the two share a rolling window, w[k] and w[2 - k]
+        // of one step being the next step's w[k] and w[1 - k] of the other
+        // midpoint, so an item loads 2L + 2 rows instead of 4L.
+        auto col_item = [&](int ip, int cp) {
+            const int I0 = -H / 2 + 2 * ip;
+            const float *w = rs + (CHY + I0) * FW + 2 * cp;  // w[m * FW]: refined row I0 + m
+            auto ld = [&](int m) { return *reinterpret_cast<const float2 *>(w + m * FW); };
+            float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+            float2 hi0 = ld(L), lo0 = ld(1 - L), hi1 = ld(L + 1), lo1 = ld(2 - L);
 #pragma unroll
-            for (int k = L; k >= 1; --k)
-                acc = f2_fma(tp[k - 1], f2_add(*reinterpret_cast<const float2 *>(w + k * FW),
-                                                *reinterpret_cast<const float2 *>(w + (1 - k) * FW)), acc);
-            const float2 node = *reinterpret_cast<const float2 *>(w);
-            const int u = 2 * I0, r = u + H;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int v = 2 * cp + h - H;
-                const int c = v + HX;
-                T ve = h ? node.y : node.x, vo = h ? acc.y : acc.x;
-                if (extra) {
-                    const size_t gc = (size_t)((tx0 + v) & (n - 1));
-                    ve += extra[(size_t)((ty0 + u) & (n - 1)) * n + gc];
-                    vo += extra[(size_t)((ty0 + u + 1) & (n - 1)) * n + gc];
+            for (int k = L; k >= 1; --k) {
+                a0 = f2_fma(tp[k - 1], f2_add(hi0, lo0), a0);  // w[k] + w[1 - k]
+                a1 = f2_fma(tp[k - 1], f2_add(hi1, lo1), a1);  // w[k + 1] + w[2 - k]
+                if (k > 1) {
+                    hi1 = hi0;
+                    hi0 = ld(k - 1);
+                    lo0 = lo1;
+                    lo1 = ld(3 - k);
                 }
-                const int q = (r + c) & 1;
-                X[q * A + r * CK + (c >> 1)] += ve;
-                X[(q ^ 1) * A + (r + 1) * CK + (c >> 1)] += vo;
+            }
+            // after the last step lo0 = w[0] and lo1 = w[1]: the rows' nodes
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float2 node = i ? lo1 : lo0, acc = i ? a1 : a0;
+                const int u = 2 * (I0 + i), r = u + H;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int v = 2 * cp + h - H;
+                    const int c = v + HX;
+                    T ve = h ? node.y : node.x, vo = h ? acc.y : acc.x;
+                    if (extra) {
+                        const size_t gc = (size_t)((tx0 + v) & (n - 1));
+                        ve += extra[(size_t)((ty0 + u) & (n - 1)) * n + gc];
+                        vo += extra[(size_t)((ty0 + u + 1) & (n - 1)) * n + gc];
+                    }
+                    const int q = (r + c) & 1;
+                    X[q * A + r * CK + (c >> 1)] += ve;
+                    X[(q ^ 1) * A + (r + 1) * CK + (c >> 1)] += vo;
+                }
             }
         };
         {
+            static_assert(IW % 2 == 0, "column-pass items take two coarse rows");
+            constexpr int IP = IW / 2;
             constexpr int CM = CP < 32 ? CP : 32, CRM = CP - CM;
             if (lane < CM)
-                for (int ir = warp; ir < IW; ir += NWARP) col_item(ir, lane);
+                for (int ip = warp; ip < IP; ip += NWARP) col_item(ip, lane);
             if constexpr (CRM > 0) {
-                constexpr int RG = strip_rem_rows(FW / 2, CRM, 2);
+                // consecutive items are two refined rows (FW float2) apart
+                constexpr int RG = strip_rem_rows(FW, CRM, 2);
                 const int dr = lane / CRM, cp = CM + (lane - dr * CRM);
                 if (dr < RG)
-                    for (int ir = warp * RG + dr; ir < IW; ir += NWARP * RG) col_item(ir, cp);
+                    for (int ip = warp * RG + dr; ip < IP; ip += NWARP * RG) col_item(ip, cp);
             }
         }
         __syncthreads();

@@ -16,6 +16,10 @@ ops:
          n/2 x n/2 coarse grid of 64 channels
   solve  a whole mixed-precision solve of a seeded turbulent source (host-loop
          execution, so every kernel is a separate launch); time per solve
+  link   the host link: copies of n x n FP64 arrays between pinned host memory
+         and the device with cudaMemcpyAsync - host to device (f and x, as a
+         solve from host buffers stages them), device to host (x), and both
+         directions at once on two streams; GB/s of each (no library kernel)
 """
 from __future__ import annotations
 
@@ -30,7 +34,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["down", "up", "outer", "conv", "solve"], required=True)
+    ap.add_argument("--op", choices=["down", "up", "outer", "conv", "solve", "link"], required=True)
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
@@ -44,6 +48,9 @@ def main():
     n = args.n
     g = torch.Generator(device=dev)
     g.manual_seed(0)
+    if args.op == "link":
+        link_bandwidth(n, max(args.reps, 10))
+        return
     if args.op in ("down", "up"):
         x = torch.randn((n, n), device=dev, generator=g)
         xo = torch.empty_like(x)
@@ -95,6 +102,44 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     print(f"{args.op} n={n} reps={args.reps} us_per_launch={e0.elapsed_time(e1) / args.reps * 1e3:.2f}")
+
+
+def link_bandwidth(n: int, reps: int):
+    import torch
+    dev = torch.device("cuda:0")
+    hf = torch.ones((n, n), dtype=torch.float64).pin_memory()
+    hx = torch.ones((n, n), dtype=torch.float64).pin_memory()
+    df = torch.empty((n, n), dtype=torch.float64, device=dev)
+    dx = torch.empty((n, n), dtype=torch.float64, device=dev)
+    nbytes = hf.numel() * 8
+    side = torch.cuda.Stream()
+
+    def h2d():
+        df.copy_(hf, non_blocking=True)
+        dx.copy_(hx, non_blocking=True)
+
+    def d2h():
+        hx.copy_(dx, non_blocking=True)
+
+    def duplex():
+        cur = torch.cuda.current_stream()
+        side.wait_stream(cur)
+        df.copy_(hf, non_blocking=True)
+        with torch.cuda.stream(side):
+            hx.copy_(dx, non_blocking=True)
+        cur.wait_stream(side)
+
+    for name, fn, moved in (("h2d f+x", h2d, 2 * nbytes), ("d2h x", d2h, nbytes), ("h2d f || d2h x", duplex, 2 * nbytes)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        print(f"link {name}: {moved / 1e6:.1f} MB in {ms * 1e3:.1f} us = {moved / (ms * 1e-3) / 1e9:.1f} GB/s")
 
 
 if __name__ == "__main__":
