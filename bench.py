@@ -94,15 +94,27 @@ def kernel_source_sha():
 
 
 
-def kernel_roofline(kind, n_l, ms, nbytes, peak, peak_src):
+def kernel_roofline(kind, n_l, ms, nbytes, peak, peak_src, sms=None, sm_mhz=None):
     """Roofline of one probed kernel kind: launches n_l, total ms, algorithmic bytes.
     Every probed kernel is bounded by memory (HBM peak): the FP32 stencils, and
-    the outer residual, whose exact stencil sum runs on the integer pipe."""
+    the outer residual, whose exact stencil sum runs on the integer pipe.  With
+    a committed capture of the kernel's shared-memory wavefronts, the line also
+    carries its shared-memory roofline: one 128-byte wavefront per cycle per
+    SM at the SM clock."""
     if not n_l:
         return None
     us = ms / n_l * 1e3
+    cap = read_capture(kind)
     base = {"kernel": PROBE_NAMES[kind], "avg_launch_us": us, "launches": n_l,
-            "algorithmic_bytes_per_launch": nbytes / n_l, "traffic": read_traffic(kind)}
+            "algorithmic_bytes_per_launch": nbytes / n_l,
+            "traffic": cap.get("dram_bytes_per_launch") if cap else None}
+    wf = cap.get("smem_wavefronts_per_launch") if cap else None
+    if wf and sms and sm_mhz:
+        speak = sms * sm_mhz * 1e6
+        base["smem"] = {"wavefronts_per_launch": wf, "achieved_per_s": wf / (us * 1e-6), "peak_per_s": speak,
+                        "frac": wf / (us * 1e-6) / speak,
+                        "note": f"128-byte shared-memory wavefronts (ncu, {cap.get('profile')}) per second of the "
+                                f"live launch time, against one per cycle on each of {sms} SMs at {sm_mhz:.0f} MHz"}
     if kind == 5:
         base.update({"bound": "launch/latency", "achieved": (nbytes / n_l) / (us * 1e-6) / 1e9, "unit": "GB/s",
                      "peak": None, "frac": None,
@@ -114,8 +126,9 @@ def kernel_roofline(kind, n_l, ms, nbytes, peak, peak_src):
     return base
 
 
-def read_traffic(kernel_kind):
-    """DRAM bytes per launch from a committed ncu capture, if it matches this source."""
+def read_capture(kernel_kind):
+    """Per-launch counters (DRAM bytes, shared-memory wavefronts) from a committed
+    ncu capture, if it was taken of this kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -124,7 +137,7 @@ def read_traffic(kernel_kind):
     ent = d.get(str(kernel_kind))
     if not ent or ent.get("source_sha1") != kernel_source_sha():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent
 
 
 class ClockSampler:
@@ -694,7 +707,9 @@ def main():
 
     # ---- roofline of the dominant kernel -----------------------------------
     peak, peak_src = read_peaks()
-    roofline = kernel_roofline(dom, n_l, probe_ms, probe_bytes, peak, peak_src)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (clocks or {}).get("sm_max_mhz")
+    roofline = kernel_roofline(dom, n_l, probe_ms, probe_bytes, peak, peak_src, sms, sm_mhz)
     mean_step = sum(times) / len(times)
     mean_probe_step = sum(tprobe) / len(tprobe)
     roofline["share_of_solve"] = (probe_ms / n_probe / 1e3) / mean_probe_step
@@ -703,7 +718,7 @@ def main():
                                  f"execution, {mean_probe_step * 1e3:.3f} ms per solve)")
     kernels = {PROBE_NAMES[k]: {"launches_per_solve": v[0], "ms_per_solve": v[1],
                                 "gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None,
-                                "roofline": kernel_roofline(k, v[0], v[1], v[2], peak, peak_src)}
+                                "roofline": kernel_roofline(k, v[0], v[1], v[2], peak, peak_src, sms, sm_mhz)}
                for k, v in kernel_ms.items()}
 
     # ---- batched: 256 right-hand sides of mixed sizes in one graph ----------
