@@ -762,7 +762,9 @@ def main():
     if not args.skip_two_level:
         two_level = {"workload": "two-level cycles (Sec. 4.1): one coarse level 16x coarser, N_smooth red-black "
                                  "sweeps on the finest grid, 10 coarse sweeps, cubic spline prolongation by 16 in "
-                                 "one step, FP32 cycles in FP64 defect correction, tol 1e-10, x from 0",
+                                 "one step (runs with 'prolong': SR by 16 as four stages of the cubic spline by 2 "
+                                 "plus the trained generator's correction, every cycle or alternated with cubic), "
+                                 "FP32 cycles in FP64 defect correction, tol 1e-10, x from 0",
                      "runs": []}
         for n2, lev2 in ((1024, 8), (2048, 9)):
             f2 = torch.tensor(turbulent_source(n2, n2 // 8, config_seed(1, rank * 100 + 50)), device=dev)
@@ -788,6 +790,27 @@ def main():
                                           "cycles": inf2["vcycles"], "rel_residual": inf2["rel_residual"],
                                           "ms_per_solve": sum(ts2) / len(ts2),
                                           "multilevel_vcycles_same_source": vm})
+            if n2 == 2048 and os.path.exists(SR_WEIGHTS):
+                # SR x16: four stages of (cubic by 2 + the trained generator's correction)
+                with open(SR_WEIGHTS, "rb") as fh:
+                    c2.load_weights(fh.read())
+                for label, n_gan in (("sr", float("inf")), ("alternate", 1.0)):
+                    c2.set_prolong_policy(n_gan, 0.0)
+                    c2.two_level_solve(f2, x2, max_cycles=2, nu_smooth=20, prolong="sr", check=False)  # buffers
+                    x2.zero_()
+                    torch.cuda.synchronize(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    inf2 = c2.two_level_solve(f2, x2, max_cycles=400, nu_smooth=20, prolong="sr", check=False)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    two_level["runs"].append({"n": n2, "nu_smooth": 20, "coarse_sweeps": 10, "prolong": label,
+                                              "status": inf2["status"], "cycles": inf2["vcycles"],
+                                              "sr_cycles": inf2["sr_cycles"], "sr_fallback": inf2["sr_fallback"],
+                                              "rel_residual": inf2["rel_residual"],
+                                              "ms_per_solve": e0.elapsed_time(e1)})
+                c2.set_prolong_policy(float("inf"), 0.0)
             c2.close()
 
     if rank == 0:

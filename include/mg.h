@@ -151,10 +151,18 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *x, mg_prolong prolong)
  * coefficients by a truncated exact inverse filter, then the tensor cubic
  * B-spline at every fine point) and added; no post-smoothing.  MIXED contexts
  * with levels >= coarsen_log2 + 2 and N >> coarsen_log2 >= 64; 0 <= nu_smooth
- * <= 64; 1 <= coarse_sweeps <= 64.  info->vcycles and info->outer_iters count
- * two-level cycles; MG_ERR_NOT_CONVERGED after max_cycles with the best x. */
+ * <= 64; 1 <= coarse_sweeps <= 64.  prolong = MG_PROLONG_SR interpolates the
+ * correction with the loaded generator instead (Sec. 2.3, Algorithm 5, which
+ * applies the generator repeatedly): coarsen_log2 stages, each the cubic
+ * spline by 2 plus the generator's correction s G(e / s), s = max|e|; it needs
+ * weights (MG_ERR_NO_WEIGHTS), coarsen_log2 <= 8 and N >> coarsen_log2 >= 128;
+ * the context's policy (mg_set_prolong_policy) picks SR or cubic per cycle,
+ * and an SR cycle that does not reduce the relative residual turns SR off for
+ * the rest of the solve (info->sr_fallback).  info->vcycles and
+ * info->outer_iters count two-level cycles, info->sr_cycles those with SR;
+ * MG_ERR_NOT_CONVERGED after max_cycles with the best x. */
 mg_status mg_two_level_solve(mg_ctx *ctx, const double *f, double *x, double tol, int coarsen_log2, int nu_smooth,
-                             int coarse_sweeps, int max_cycles, mg_solve_info *info);
+                             int coarse_sweeps, int max_cycles, mg_prolong prolong, mg_solve_info *info);
 
 /* Solve B independent problems, ctxs[k] with f[k], x[k], each to tol.
  * Contexts may have different N.  When every context is MG_PREC_MIXED with

@@ -383,14 +383,16 @@ def vcycle(x: np.ndarray, f: np.ndarray, h: float, nu1: int = 2, nu2: int = 2,
 
 
 def two_level_cycle(x: np.ndarray, f: np.ndarray, h: float, factor: int = 16, nu: int = 20,
-                    coarse_sweeps: int = 10) -> np.ndarray:
+                    coarse_sweeps: int = 10, prolong=None) -> np.ndarray:
     """One cycle of the paper's two-level scheme (Sec. 4.1; Algorithm 6 with a
     single coarse level): relax nu times (red-black Gauss-Seidel), restrict the
     residual by `factor`, relax the coarse correction equation coarse_sweeps
     times from zero (Algorithm 6's coarsest-level relaxation; 0 = the exact
     coarse solve), interpolate the correction back by `factor` with the cubic
     spline and add it.  No post-smoothing (Algorithm 6 relaxes before the
-    coarse correction only)."""
+    coarse correction only).  `prolong`, when given, maps the coarse
+    correction to the fine grid in place of the cubic spline by `factor` (the
+    SR operator of Algorithm 5, for example)."""
     x = x.copy()
     rbgs(x, f, h, nu)
     rc = restrict_fw_factor(residual(f, x, h), factor)
@@ -400,7 +402,7 @@ def two_level_cycle(x: np.ndarray, f: np.ndarray, h: float, factor: int = 16, nu
         rbgs(ec, rc, hc, coarse_sweeps)
     else:
         ec = coarse_solve(rc, hc)
-    return x + prolong_cubic_factor(ec, factor)
+    return x + (prolong_cubic_factor(ec, factor) if prolong is None else prolong(ec))
 
 
 def relative_residual(f: np.ndarray, x: np.ndarray, h: float) -> float:

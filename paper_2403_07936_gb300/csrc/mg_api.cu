@@ -157,6 +157,10 @@ struct mg_ctx {
     double *host_out = nullptr;  // pinned mirror of red_out
     double *f_stage = nullptr, *x_stage = nullptr;
     SrState sr;
+    // views of sr's generator for the stages of the two-level SR prolongation
+    // (stage j refines level j + 1 to level j)
+    static constexpr int kSrStages = 8;
+    SrState sr_stage[kSrStages];
     // graph execution
     bool use_graphs = true;
     ProlongPolicy policy = {1, 0, 0.0};  // SR on every V-cycle
@@ -1535,6 +1539,7 @@ void mg_destroy(mg_ctx *c) {
     cudaFreeHost(c->host_out);
     cudaFree(c->f_stage);
     cudaFree(c->x_stage);
+    for (SrState &v : c->sr_stage) sr_free(&v);
     sr_free(&c->sr);
     probe_free(c);
     drop_graphs(c);
@@ -1827,7 +1832,7 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
 // k times), ncs sweeps of the coarse correction equation from zero, the
 // coarse correction interpolated back by 2^k with the cubic spline and added.
 // Returns the buffer holding e.
-static mg_status two_level_cycle32(mg_ctx *c, int k, int nu, int ncs, float **e_out) {
+static mg_status two_level_cycle32(mg_ctx *c, int k, int nu, int ncs, bool sr, float **e_out) {
     cudaStream_t s = c->stream;
     float *src = c->lv[0].x32, *dst = c->lv[0].t32;
     int left = nu;
@@ -1852,18 +1857,39 @@ static mg_status two_level_cycle32(mg_ctx *c, int k, int nu, int ncs, float **e_
         left -= m;
         first = false;
     } while (left > 0);
-    // B-spline coefficients of the coarse correction (rows into cd, then columns back into cs)
-    MG_CUDA(launch_bspline_coef(cs, cd, c->lv[k].n, 0, s));
-    MG_CUDA(launch_bspline_coef(cd, cs, c->lv[k].n, 1, s));
-    MG_CUDA(launch_prolong_factor(src, cs, c->lv[0].n, k, s));
-    *e_out = src;
+    if (!sr) {
+        // B-spline coefficients of the coarse correction (rows into cd, then columns back into cs)
+        MG_CUDA(launch_bspline_coef(cs, cd, c->lv[k].n, 0, s));
+        MG_CUDA(launch_bspline_coef(cd, cs, c->lv[k].n, 1, s));
+        MG_CUDA(launch_prolong_factor(src, cs, c->lv[0].n, k, s));
+        *e_out = src;
+        return MG_OK;
+    }
+    // SR prolongation by 2^k: k stages, each the cubic spline by 2 plus the
+    // generator's correction s G(e / s) (the generator applied repeatedly, as
+    // Algorithm 5 applies it twice); levels k - 1 .. 1 hold the intermediate
+    // corrections, the last stage adds to the smoothed fine iterate
+    const float *e = cs;
+    for (int j = k - 1; j >= 0; --j) {
+        SrState *v = &c->sr_stage[j];
+        MG_TRY(sr_correction(v, e, c->lv[j + 1].n, s, g_err, sizeof g_err));
+        const int nj = c->lv[j].n;
+        if (j > 0) {
+            MG_CUDA(cudaMemsetAsync(c->lv[j].x32, 0, sizeof(float) * nj * nj, s));
+            MG_CUDA(launch_up<float>(c->lv[j].x32, c->lv[j].t32, c->lv[j].b32, e, nj, 0, c->taps, s, v->fine_out));
+            e = c->lv[j].t32;
+        } else {
+            MG_CUDA(launch_up<float>(src, dst, c->lv[0].b32, e, nj, 0, c->taps, s, v->fine_out));
+        }
+    }
+    *e_out = dst;
     return MG_OK;
 }
 
 mg_status mg_two_level_solve(mg_ctx *c, const double *f, double *x, double tol, int coarsen_log2, int nu_smooth,
-                             int coarse_sweeps, int max_cycles, mg_solve_info *info) {
+                             int coarse_sweeps, int max_cycles, mg_prolong prolong, mg_solve_info *info) {
     const auto t0 = std::chrono::steady_clock::now();
-    MG_TRY(check_common(c, f, x, MG_PROLONG_CUBIC));
+    MG_TRY(check_common(c, f, x, prolong));
     const int k = coarsen_log2;
     if (c->prec != MG_PREC_MIXED || k < 1 || k + 2 > c->levels || (c->N >> k) < 64 || nu_smooth < 0 ||
         nu_smooth > 64 || coarse_sweeps < 1 || coarse_sweeps > 64 || max_cycles < 1 || !(tol > 0.0)) {
@@ -1871,7 +1897,17 @@ mg_status mg_two_level_solve(mg_ctx *c, const double *f, double *x, double tol, 
                 "N >> coarsen_log2 >= 64; 0 <= nu_smooth <= 64; 1 <= coarse_sweeps <= 64; max_cycles >= 1; tol > 0");
         return MG_ERR_INVALID_ARG;
     }
+    const bool sr_on = prolong == MG_PROLONG_SR;
+    if (sr_on && (k > mg_ctx::kSrStages || (c->N >> k) < 128)) {
+        set_err("two-level SR prolongation: coarsen_log2 <= %d and N >> coarsen_log2 >= 128 (the generator's "
+                "smallest grid)", mg_ctx::kSrStages);
+        return MG_ERR_INVALID_ARG;
+    }
     MG_TRY(ensure_hierarchy(c, false));
+    if (sr_on) {
+        for (int j = 0; j < k; ++j) MG_TRY(sr_view(&c->sr_stage[j], &c->sr, c->lv[j + 1].n, g_err, sizeof g_err));
+        MG_CUDA(cudaMemsetAsync(c->sr.err, 0, sizeof(int), c->stream));  // the convolutions' bounded waits
+    }
     const double *fd;
     double *xd;
     bool staged;
@@ -1882,9 +1918,9 @@ mg_status mg_two_level_solve(mg_ctx *c, const double *f, double *x, double tol, 
     cudaStream_t s = c->stream;
     MG_CUDA(launch_source_sum(fd, N, c->red(kGrpF), s));
     mg_status st = MG_OK;
-    int cycles = 0;
-    double fnorm = 0.0, rel = INFINITY, mu = 0.0;
-    bool first = true;
+    int cycles = 0, sr_used = 0;
+    double fnorm = 0.0, rel = INFINITY, rel_prev = INFINITY, mu = 0.0;
+    bool first = true, sr_last = false, fallback = false;
     for (;;) {  // FP64 defect correction, one FP32 two-level cycle per outer step
         MG_CUDA(solve_residual(c, fd, xd, true, first, h2, s));
         MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 2 * kMaxSlots, cudaMemcpyDeviceToHost, s));
@@ -1906,14 +1942,20 @@ mg_status mg_two_level_solve(mg_ctx *c, const double *f, double *x, double tol, 
             break;
         }
         rel = rnorm / fnorm;
+        // an SR cycle that did not reduce the residual turns SR off for the rest
+        if (sr_last && !(rel < rel_prev)) fallback = true;
         if (rel <= tol) break;
         if (cycles >= max_cycles) {
             set_err("not converged: rel residual %.3e after %d two-level cycles", rel, cycles);
             st = MG_ERR_NOT_CONVERGED;
             break;
         }
+        // the context's policy (N_GAN alternation, S_thres switch) picks the operator
+        sr_last = sr_on && policy_use_sr(c->policy, cycles + 1, rel, true, fallback);
+        sr_used += sr_last ? 1 : 0;
+        rel_prev = rel;
         float *e = nullptr;
-        MG_TRY(two_level_cycle32(c, k, nu_smooth, coarse_sweeps, &e));
+        MG_TRY(two_level_cycle32(c, k, nu_smooth, coarse_sweeps, sr_last, &e));
         MG_CUDA(launch_update(xd, e, N, c->red(kGrpU), s));
         ++cycles;
     }
@@ -1924,15 +1966,23 @@ mg_status mg_two_level_solve(mg_ctx *c, const double *f, double *x, double tol, 
     if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 4 * kMaxSlots, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
+    if (sr_on) {
+        int flag = 0;
+        MG_CUDA(cudaMemcpy(&flag, c->sr.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            set_err("SR generator: a bounded wait in the tensor-core convolution expired");
+            st = MG_ERR_TIMEOUT;
+        }
+    }
     if (info) {
         info->outer_iters = cycles;
         info->vcycles = cycles;
         info->rel_residual = rel;
         info->removed_mean = mu;
         info->update_norm = cycles > 0 ? sqrt(c->host_out[kGrpU * kMaxSlots]) : 0.0;
-        info->sr_cycles = 0;
-        info->prolong_used = MG_PROLONG_CUBIC;
-        info->sr_fallback = 0;
+        info->sr_cycles = sr_used;
+        info->prolong_used = sr_used > 0 ? MG_PROLONG_SR : MG_PROLONG_CUBIC;
+        info->sr_fallback = fallback ? 1 : 0;
         info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     return st;

@@ -727,6 +727,13 @@ cudaError_t ensure_buffers(SrState *st, int nc) {
 }  // namespace
 
 void sr_free(SrState *st) {
+    if (st->view) {
+        for (int i = 0; i < 3; ++i) cudaFree(st->act[i]);
+        cudaFree(st->fine_act);
+        cudaFree(st->fine_out);
+        *st = SrState();
+        return;
+    }
     cudaFree(st->w_tc);
     cudaFree(st->bias_tc);
     cudaFree(st->prelu_blk);
@@ -848,6 +855,37 @@ mg_status sr_prepare(SrState *st, int nc, char *err, size_t errlen) {
     }
     cudaError_t e = prepare_conv();
     if (e == cudaSuccess) e = ensure_buffers(st, nc);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "SR buffers for %d^2: %s", nc, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+mg_status sr_view(SrState *view, const SrState *st, int nc, char *err, size_t errlen) {
+    if (!st->loaded || st->view) {
+        snprintf(err, errlen, "no generator weights loaded");
+        return MG_ERR_NO_WEIGHTS;
+    }
+    if (nc < TM || nc % TM) {
+        snprintf(err, errlen, "SR prolongation needs a coarse grid of at least %d (multiple of %d), got %d", TM, TM, nc);
+        return MG_ERR_INVALID_ARG;
+    }
+    // the view's own buffers survive; everything else is st's (refreshed on
+    // every call, so reloaded weights are picked up)
+    SrState v = *st;
+    v.view = true;
+    for (int i = 0; i < 3; ++i) {
+        v.act[i] = view->act[i];
+        v.tm_act[i] = view->tm_act[i];
+        v.tm_out[i] = view->tm_out[i];
+    }
+    v.fine_act = view->fine_act;
+    v.fine_out = view->fine_out;
+    v.nc = view->view ? view->nc : 0;
+    cudaError_t e = prepare_conv();
+    if (e == cudaSuccess) e = ensure_buffers(&v, nc);
+    *view = v;
     if (e != cudaSuccess) {
         snprintf(err, errlen, "SR buffers for %d^2: %s", nc, cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;

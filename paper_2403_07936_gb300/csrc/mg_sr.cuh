@@ -28,6 +28,7 @@ constexpr int kSrFeat = 64;
 
 struct SrState {
     bool loaded = false;
+    bool view = false;  // shares another state's weights and scratch scalars (sr_view)
     int n_feat = 0, n_blocks = 0;
     // weights (device): tensor-core layers packed bf16 [layer][tap][co][ci],
     // layers = 2 * n_blocks + 4 (the 4 pixel-shuffle groups of conv 64->256)
@@ -60,6 +61,12 @@ mg_status sr_prepare(SrState *st, int nc, char *err, size_t errlen);
 // (asynchronous on stream; sr_prepare must have run for nc).
 mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t stream, char *err,
                         size_t errlen);
+// Point view at st's weights and scratch scalars, with activation and output
+// buffers of its own for coarse grids of size nc (kept while nc is unchanged),
+// so that one generator runs at several grid sizes without reallocating.
+// Outside any stream capture; a view is used on st's stream only.
+mg_status sr_view(SrState *view, const SrState *st, int nc, char *err, size_t errlen);
+// Free a state; a view frees only its own buffers.
 void sr_free(SrState *st);
 
 // One tensor-core convolution layer on padded bf16 activations (verification).

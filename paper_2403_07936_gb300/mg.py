@@ -55,7 +55,7 @@ SIGNATURES = {
     "mg_load_prolong_weights": (_I, [_VP, _VP, _SZ]),
     "mg_solve": (_I, [_VP, _VP, _VP, _D, _I, C.POINTER(SolveInfo)]),
     "mg_vcycle": (_I, [_VP, _VP, _VP, _I]),
-    "mg_two_level_solve": (_I, [_VP, _VP, _VP, _D, _I, _I, _I, _I, C.POINTER(SolveInfo)]),
+    "mg_two_level_solve": (_I, [_VP, _VP, _VP, _D, _I, _I, _I, _I, _I, C.POINTER(SolveInfo)]),
     "mg_solve_batched": (_I, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _I, _D, _I,
                               C.POINTER(SolveInfo)]),
     "mg_destroy": (None, [_VP]),
@@ -232,13 +232,15 @@ class Context:
         _check(load().mg_vcycle(self._h, ptr(f), ptr(x), PROLONG[prolong]))
 
     def two_level_solve(self, f, x, tol: float = 1e-10, coarsen_log2: int = 4, nu_smooth: int = 20,
-                        coarse_sweeps: int = 10, max_cycles: int = 300, check: bool = True) -> dict:
+                        coarse_sweeps: int = 10, max_cycles: int = 300, prolong: str = "cubic",
+                        check: bool = True) -> dict:
         """The paper's two-level configuration (mg_two_level_solve): one coarse
         level 2^coarsen_log2 times coarser, nu_smooth fine sweeps, coarse_sweeps
-        coarse sweeps, cubic spline prolongation by 2^coarsen_log2."""
+        coarse sweeps, prolongation by 2^coarsen_log2 with the cubic spline or
+        ("sr") the generator applied once per factor 2."""
         info = SolveInfo()
         st = load().mg_two_level_solve(self._h, ptr(f), ptr(x), tol, coarsen_log2, nu_smooth, coarse_sweeps,
-                                       max_cycles, C.byref(info))
+                                       max_cycles, PROLONG[prolong], C.byref(info))
         d = info.as_dict()
         d["status"] = STATUS_NAMES.get(st, st)
         if check and st not in (MG_OK,):

@@ -270,6 +270,22 @@ def test_prolong_cubic_factor_invariants_and_factor_two():
     np.testing.assert_allclose(mg.prolong_cubic_factor(np.outer(a, b), 4), np.outer(pa, pb), atol=1e-12)
 
 
+def test_nested_spline_refinements_compose():
+    """Refining by 2 four times gives the spline by 16: the periodic cubic
+    spline through the coarse nodes is a cubic spline on every finer set of
+    nodes too, so the interpolating spline through its values there is itself
+    (uniqueness of periodic spline interpolation).  Pins the midpoint filter
+    against the direct evaluation at any factor (two independent codes)."""
+    rng = np.random.default_rng(5)
+    ec = rng.standard_normal((16, 16))
+    e = ec
+    for _ in range(4):
+        e = mg.prolong_cubic(e)
+    np.testing.assert_allclose(e, mg.prolong_cubic_factor(ec, 16), atol=1e-12)
+    e2 = mg.prolong_cubic_factor(mg.prolong_cubic_factor(ec, 4), 2)
+    np.testing.assert_allclose(e2, mg.prolong_cubic_factor(ec, 8), atol=1e-12)
+
+
 def test_two_level_cycle_with_factor_two_is_a_v_cycle():
     """With coarsening by 2 and an exact coarse solve the two-level cycle is the
     V(nu, 0) cycle whose coarsest grid is n / 2; with factor 16 and 10 coarse
