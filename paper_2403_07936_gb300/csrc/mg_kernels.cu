@@ -603,38 +603,47 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
         if (NU > 0) lb.scatter(B, B + A);
         constexpr int CP = FW / 2;
         // Column pass: an item refines two adjacent fine columns (2cp, 2cp + 1)
-        // at the midpoints of coarse rows I0 and I0 + 1 (rows 2 I0 + 1 and
-        // 2 I0 + 3).  Each midpoint sums its taps k = L .. 1 in the order of the
-        // one-midpoint form; the two share a rolling window, w[k] and w[2 - k]
-        // of one step being the next step's w[k] and w[1 - k] of the other
-        // midpoint, so an item loads 2L + 2 rows instead of 4L.
+        // at the midpoints of RPI consecutive coarse rows I0 .. I0 + RPI - 1.
+        // Each midpoint sums its taps k = L .. 1 in the order of the
+        // one-midpoint form, w[k + i] + w[1 - k + i] for row I0 + i; the rows
+        // share a rolling window (one step's w[k + i] is the next step's
+        // w[k - 1 + (i + 1)], its w[2 - k + i] the next step's w[1 - (k - 1) + (i - 1)]),
+        // so an item loads 2L + 2 RPI - 2 rows instead of 2L RPI.
+        constexpr int RPI = IW % 4 == 0 ? 4 : 2;
+        static_assert(IW % RPI == 0, "column-pass items take RPI coarse rows");
         auto col_item = [&](int ip, int cp) {
-            const int I0 = -H / 2 + 2 * ip;
+            const int I0 = -H / 2 + RPI * ip;
             const float *w = rs + (CHY + I0) * FW + 2 * cp;  // w[m * FW]: refined row I0 + m
             auto ld = [&](int m) { return *reinterpret_cast<const float2 *>(w + m * FW); };
-            float2 a0 = make_float2(0.f, 0.f), a1 = a0;
-            float2 hi0 = ld(L), lo0 = ld(1 - L), hi1 = ld(L + 1), lo1 = ld(2 - L);
+            float2 hi[RPI], lo[RPI], acc[RPI];
+#pragma unroll
+            for (int i = 0; i < RPI; ++i) {
+                hi[i] = ld(L + i);
+                lo[i] = ld(1 - L + i);
+                acc[i] = make_float2(0.f, 0.f);
+            }
 #pragma unroll
             for (int k = L; k >= 1; --k) {
-                a0 = f2_fma(tp[k - 1], f2_add(hi0, lo0), a0);  // w[k] + w[1 - k]
-                a1 = f2_fma(tp[k - 1], f2_add(hi1, lo1), a1);  // w[k + 1] + w[2 - k]
+#pragma unroll
+                for (int i = 0; i < RPI; ++i) acc[i] = f2_fma(tp[k - 1], f2_add(hi[i], lo[i]), acc[i]);
                 if (k > 1) {
-                    hi1 = hi0;
-                    hi0 = ld(k - 1);
-                    lo0 = lo1;
-                    lo1 = ld(3 - k);
+#pragma unroll
+                    for (int i = RPI - 1; i >= 1; --i) hi[i] = hi[i - 1];
+                    hi[0] = ld(k - 1);
+#pragma unroll
+                    for (int i = 0; i + 1 < RPI; ++i) lo[i] = lo[i + 1];
+                    lo[RPI - 1] = ld(RPI + 1 - k);
                 }
             }
-            // after the last step lo0 = w[0] and lo1 = w[1]: the rows' nodes
+            // after the last step lo[i] = w[i]: the rows' nodes
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const float2 node = i ? lo1 : lo0, acc = i ? a1 : a0;
+            for (int i = 0; i < RPI; ++i) {
                 const int u = 2 * (I0 + i), r = u + H;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int v = 2 * cp + h - H;
                     const int c = v + HX;
-                    T ve = h ? node.y : node.x, vo = h ? acc.y : acc.x;
+                    T ve = h ? lo[i].y : lo[i].x, vo = h ? acc[i].y : acc[i].x;
                     if (extra) {
                         const size_t gc = (size_t)((tx0 + v) & (n - 1));
                         ve += extra[(size_t)((ty0 + u) & (n - 1)) * n + gc];
@@ -647,14 +656,13 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
             }
         };
         {
-            static_assert(IW % 2 == 0, "column-pass items take two coarse rows");
-            constexpr int IP = IW / 2;
+            constexpr int IP = IW / RPI;
             constexpr int CM = CP < 32 ? CP : 32, CRM = CP - CM;
             if (lane < CM)
                 for (int ip = warp; ip < IP; ip += NWARP) col_item(ip, lane);
             if constexpr (CRM > 0) {
-                // consecutive items are two refined rows (FW float2) apart
-                constexpr int RG = strip_rem_rows(FW, CRM, 2);
+                // consecutive items are RPI refined rows (RPI FW / 2 float2) apart
+                constexpr int RG = strip_rem_rows(RPI * FW / 2, CRM, 2);
                 const int dr = lane / CRM, cp = CM + (lane - dr * CRM);
                 if (dr < RG)
                     for (int ip = warp * RG + dr; ip < IP; ip += NWARP * RG) col_item(ip, cp);
