@@ -609,7 +609,9 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
         // share a rolling window (one step's w[k + i] is the next step's
         // w[k - 1 + (i + 1)], its w[2 - k + i] the next step's w[1 - (k - 1) + (i - 1)]),
         // so an item loads 2L + 2 RPI - 2 rows instead of 2L RPI.
-        constexpr int RPI = IW % 4 == 0 ? 4 : 2;
+        // four rows per item only where two-row items would need a second pass
+        // of the block's threads (small tiles: the longer chain would cost more)
+        constexpr int RPI = (IW % 4 == 0 && (IW / 2) * CP > kThreads) ? 4 : 2;
         static_assert(IW % RPI == 0, "column-pass items take RPI coarse rows");
         auto col_item = [&](int ip, int cp) {
             const int I0 = -H / 2 + RPI * ip;

@@ -122,6 +122,46 @@ def test_solve_maximum_size(mg, precision):
     assert abs(x.mean().item()) <= 1e-12 * x.abs().max().item()
 
 
+def test_distinct_contexts_in_threads_match_sequential_solves(mg):
+    """Distinct contexts may be used from different threads at once (graph
+    capture is thread-local, error text per thread): four threads, each with
+    its own context, give the bits of the same solves run one after another."""
+    import threading
+    sizes = [256, 512, 1024, 512]
+    fs = [torch.tensor(turbulent_source(n, n // 8, config_seed(11, i)), device=DEV) for i, n in enumerate(sizes)]
+    ref = []
+    for n, f in zip(sizes, fs):
+        c = mg.Context(_levels(n), n)
+        x = torch.zeros_like(f)
+        c.solve(f, x)
+        ref.append(x)
+        c.close()
+    outs, infos, errs = [None] * len(sizes), [None] * len(sizes), []
+
+    def work(i):
+        try:
+            c = mg.Context(_levels(sizes[i]), sizes[i])
+            x = torch.zeros_like(fs[i])
+            for _ in range(3):
+                x.zero_()
+                infos[i] = c.solve(fs[i], x)
+            outs[i] = x
+            c.close()
+        except Exception as e:  # reported below
+            errs.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(sizes))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errs, errs
+    torch.cuda.synchronize()
+    for i in range(len(sizes)):
+        assert infos[i]["rel_residual"] <= 1e-10
+        assert torch.equal(outs[i], ref[i])
+
+
 def test_solve_64_config_batch_of_seeds(mg):
     """64^2, 4 levels, FP64 V(2,2): several independent seeds."""
     ctx = mg.Context(4, 64, precision="fp64")
