@@ -63,17 +63,31 @@ def weight_shapes(n_feat: int = N_FEAT, n_blocks: int = N_BLOCKS):
     return shapes
 
 
-def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+def shift2d(x: np.ndarray, dy: int, dx: int, padding: str = "circular") -> np.ndarray:
+    """out[c, y, x] = in[c, y - dy, x - dx]: indices wrap ("circular") or read
+    zero outside the field ("zero")."""
+    if padding == "circular":
+        return np.roll(x, (dy, dx), axis=(1, 2))
+    out = np.zeros_like(x)
+    H, W = x.shape[1:]
+    ys, yd = (slice(0, H - dy), slice(dy, H)) if dy >= 0 else (slice(-dy, H), slice(0, H + dy))
+    xs, xd = (slice(0, W - dx), slice(dx, W)) if dx >= 0 else (slice(-dx, W), slice(0, W + dx))
+    out[:, yd, xd] = x[:, ys, xs]
+    return out
+
+
+def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray, padding: str = "circular") -> np.ndarray:
     """out[o, y, x] = b[o] + sum_{c, ky, kx} w[o, c, ky, kx] in[c, y+ky-1, x+kx-1].
 
-    Indices wrap (circular padding).  Each of the nine taps is a shifted copy
+    Indices wrap (circular padding), or read zero outside the field (zero
+    padding, for windows of a field).  Each of the nine taps is a shifted copy
     of the input contracted over channels.
     """
     cout = w.shape[0]
     out = np.broadcast_to(b[:, None, None], (cout,) + x.shape[1:]).astype(np.float64).copy()
     for ky in range(3):
         for kx in range(3):
-            shifted = np.roll(x, (1 - ky, 1 - kx), axis=(1, 2))
+            shifted = shift2d(x, 1 - ky, 1 - kx, padding)
             out += np.einsum("oc,chw->ohw", w[:, :, ky, kx], shifted)
     return out
 
@@ -95,19 +109,20 @@ def pixel_shuffle2(x: np.ndarray) -> np.ndarray:
 
 
 def generator_forward(q: np.ndarray, weights: dict, n_blocks: int = N_BLOCKS,
-                      emulate_bf16: bool = False) -> np.ndarray:
-    """G(q) for a normalised coarse field q (H, W) -> fine field (2H, 2W)."""
+                      emulate_bf16: bool = False, padding: str = "circular") -> np.ndarray:
+    """G(q) for a normalised coarse field q (H, W) -> fine field (2H, 2W);
+    padding "zero" treats q as a window cut out of a larger field."""
     rnd = bf16_round if emulate_bf16 else (lambda a: a)
     W = {k: (rnd(v) if (emulate_bf16 and k.endswith(("w", "w1", "w2"))) else v)
          for k, v in weights.items()}
     x = q[None, :, :].astype(np.float64)
-    x = rnd(prelu(conv3x3(x, W["in.w"], W["in.b"]), W["in.a"]))
+    x = rnd(prelu(conv3x3(x, W["in.w"], W["in.b"], padding), W["in.a"]))
     for k in range(n_blocks):
-        t = rnd(prelu(conv3x3(x, W[f"b{k}.w1"], W[f"b{k}.b1"]), W[f"b{k}.a"]))
-        x = rnd(x + conv3x3(t, W[f"b{k}.w2"], W[f"b{k}.b2"]))
-    u = conv3x3(x, W["up.w"], W["up.b"])
+        t = rnd(prelu(conv3x3(x, W[f"b{k}.w1"], W[f"b{k}.b1"], padding), W[f"b{k}.a"]))
+        x = rnd(x + conv3x3(t, W[f"b{k}.w2"], W[f"b{k}.b2"], padding))
+    u = conv3x3(x, W["up.w"], W["up.b"], padding)
     u = rnd(prelu(pixel_shuffle2(u), W["up.a"]))
-    return conv3x3(u, W["out.w"], W["out.b"])[0]
+    return conv3x3(u, W["out.w"], W["out.b"], padding)[0]
 
 
 def sr_scale(ec: np.ndarray) -> float:
