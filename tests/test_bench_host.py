@@ -57,3 +57,28 @@ def test_reference_arm_prints_one_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["e2e"]["value"] == line["value"]
+
+
+def test_profile_commands_name_committed_entry_points():
+    """Every ncu summary under profiles/ gives its command; the commands run
+    committed entry points with options those entry points accept, and every
+    command line has --clock-control none on its ncu invocation."""
+    import glob
+    import re
+    ops = set(re.findall(r'"(\w+)"', open(os.path.join(ROOT, "paper_2403_07936_gb300", "profile_ops.py")).read()
+                         .split('choices=[', 1)[1].split(']', 1)[0]))
+    bench_flags = set(re.findall(r'add_argument\("(--[\w-]+)"', open(os.path.join(ROOT, "bench.py")).read()))
+    md = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+    assert md
+    for path in md:
+        text = open(path).read()
+        cmd = text.split("Command", 1)[1].split("\n\n", 2)[1]  # the indented block after the heading line
+        cmd = cmd.replace("\\\n", " ")
+        assert "ncu " in cmd and "--clock-control none" in cmd, path
+        for op in re.findall(r"profile_ops --op (\w+)", cmd):
+            assert op in ops, (path, op)
+        if "bench.py" in cmd:
+            for flag in re.findall(r"(--[\w-]+)", cmd.split("bench.py", 1)[1]):
+                if flag.startswith(("--metrics", "--clock-control", "--csv", "--log-file", "--set")):
+                    continue
+                assert flag in bench_flags, (path, flag)
