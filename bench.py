@@ -229,7 +229,76 @@ def cpu_baseline_leg(f, cycles=3):
             "sample": f"{cycles} FP64 oracle V(2,2) cycles + residuals on the 2048^2 source "
                       f"({dt:.1f} s, {per_cycle:.2f} s/cycle), scaled by the oracle's "
                       f"{ORACLE_CYCLES_PER_SOLVE} cycles per solve; numpy, single thread, "
-                      f"host {os.uname().machine} x{os.cpu_count()}"}
+                      f"host {os.uname().machine} x{os.cpu_count()}",
+            "all_cores": cpu_all_cores()}
+
+
+# The multi-core CPU figure: independent solves, one per core (the oracle
+# itself stays single-threaded), each process timing one oracle V-cycle on its
+# own 2048^2 source; the processes start the cycle together at a barrier.
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+_CYCLE_BARRIER = None
+
+
+def _cycle_pool_init(barrier):
+    global _CYCLE_BARRIER
+    _CYCLE_BARRIER = barrier
+
+
+def _oracle_cycle_worker(seed):
+    global np
+    import numpy as np
+    from synthetic.sources import turbulent_source
+    f = turbulent_source(N, KMAX, seed)
+    _CYCLE_BARRIER.wait(timeout=600)
+    dt, _ = oracle_cycle_sample(f, 1)
+    return dt
+
+
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def cpu_all_cores(per_process_bytes=1 << 30):
+    """Aggregate oracle solves/s with one independent solve per core (spawned
+    processes: this runs after the device has been used).  Processes are
+    limited to what the available memory holds at about 1 GiB each."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    procs = os.cpu_count() or 1
+    avail = _mem_available_bytes()
+    if avail is not None:
+        procs = max(1, min(procs, avail // (2 * per_process_bytes)))
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    try:
+        for k in _THREAD_VARS:
+            os.environ[k] = "1"
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(procs)
+        with cf.ProcessPoolExecutor(max_workers=procs, mp_context=ctx, initializer=_cycle_pool_init,
+                                    initargs=(barrier,)) as ex:
+            futs = [ex.submit(_oracle_cycle_worker, 1000 + i) for i in range(procs)]
+            dts = [fu.result(timeout=900) for fu in futs]
+    except Exception as e:  # reported, never fatal to the benchmark
+        return {"value": None, "error": f"{type(e).__name__}: {e}"}
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    value = sum(1.0 / (dt * ORACLE_CYCLES_PER_SOLVE) for dt in dts)
+    return {"value": value, "unit": "solves/s", "cores": procs, "kind": "oracle",
+            "sample": f"{procs} processes, each one FP64 oracle V(2,2) cycle + residual on its own "
+                      f"2048^2 source, started together ({min(dts):.2f}-{max(dts):.2f} s per cycle); "
+                      f"sum over processes of 1 / ({ORACLE_CYCLES_PER_SOLVE} x cycle time)"}
 
 
 def run_reference(args, rank):

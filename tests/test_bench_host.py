@@ -82,3 +82,11 @@ def test_profile_commands_name_committed_entry_points():
                 if flag.startswith(("--metrics", "--clock-control", "--csv", "--log-file", "--set")):
                     continue
                 assert flag in bench_flags, (path, flag)
+
+
+def test_all_cores_cpu_figure_runs_one_solve_per_process():
+    import numpy
+    bench.np = numpy  # bench.main() binds it; the legs use the module global
+    r = bench.cpu_all_cores()
+    assert r.get("error") is None, r
+    assert r["cores"] >= 1 and r["value"] > 0 and r["kind"] == "oracle"
