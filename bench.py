@@ -250,7 +250,7 @@ def _oracle_cycle_worker(seed):
     import numpy as np
     from synthetic.sources import turbulent_source
     f = turbulent_source(N, KMAX, seed)
-    _CYCLE_BARRIER.wait(timeout=600)
+    _CYCLE_BARRIER.wait(timeout=120)
     dt, _ = oracle_cycle_sample(f, 1)
     return dt
 
@@ -285,7 +285,7 @@ def cpu_all_cores(per_process_bytes=1 << 30):
         with cf.ProcessPoolExecutor(max_workers=procs, mp_context=ctx, initializer=_cycle_pool_init,
                                     initargs=(barrier,)) as ex:
             futs = [ex.submit(_oracle_cycle_worker, 1000 + i) for i in range(procs)]
-            dts = [fu.result(timeout=900) for fu in futs]
+            dts = [fu.result(timeout=300) for fu in futs]
     except Exception as e:  # reported, never fatal to the benchmark
         return {"value": None, "error": f"{type(e).__name__}: {e}"}
     finally:
