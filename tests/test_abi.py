@@ -111,3 +111,14 @@ def test_empty_batch_is_a_no_op(lib):
     infos = (mg.SolveInfo * 1)()
     assert lib.mg_solve_batched(H, F, X, 0, 1e-10, 0, infos) == 0
     assert lib.mg_solve_batched(H, F, X, -1, 1e-10, 0, infos) == 1
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU fallback: a missing libmg.so is an ImportError naming the build step."""
+    import subprocess
+    import sys
+    code = ("from paper_2403_07936_gb300 import mg\n"
+            "mg.load('" + os.path.join(ROOT, "no_such_dir", "libmg.so") + "')\n")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=120)
+    assert p.returncode != 0
+    assert "ImportError" in p.stderr and "no CPU fallback" in p.stderr
