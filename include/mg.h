@@ -303,13 +303,21 @@ mg_status mg_trainer_gradients(mg_trainer *tr, const float *q, const float *targ
 /* One Adam step on the batch; *loss (may be NULL) = the loss before the step. */
 mg_status mg_trainer_step(mg_trainer *tr, const float *q, const float *target, const float *mask,
                           double *loss);
+/* Set the Adam learning rate (lr > 0) for the following steps. */
 mg_status mg_trainer_set_lr(mg_trainer *tr, double lr);
 /* Current weights as a blob (bytes = 64 + 4 * n_params). */
 mg_status mg_trainer_get_weights(mg_trainer *tr, void *blob, size_t bytes);
+/* Free the trainer and its device memory; NULL is ignored. */
 void mg_trainer_destroy(mg_trainer *tr);
 
+/* Free a context: its level hierarchy, graphs, staging buffers, generator
+ * weights and streams it created (not a caller's stream); waits for its work
+ * first.  NULL is ignored. */
 void mg_destroy(mg_ctx *ctx);
+/* Name of a status code ("MG_OK", ...); a static string, never NULL. */
 const char *mg_status_string(mg_status status);
+/* Text of the last error raised on the calling thread (thread-local; empty
+ * when none); valid until the thread's next failing call. */
 const char *mg_last_error(void);
 
 /* ---------------------------------------------------------------------
