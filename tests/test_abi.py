@@ -122,3 +122,13 @@ def test_binding_fails_loudly_without_the_library():
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=120)
     assert p.returncode != 0
     assert "ImportError" in p.stderr and "no CPU fallback" in p.stderr
+
+
+def test_every_declared_function_is_documented():
+    """Each entry point of include/mg.h is preceded by its comment block."""
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        lines = open(h).read().split("\n")
+        for i, line in enumerate(lines):
+            m = re.match(r"^(?:mg_status|const char \*|void|unsigned long long|int)\s+\**(mg_\w+)\s*\(", line)
+            if m:
+                assert "*/" in "\n".join(lines[max(0, i - 3):i]), f"{m.group(1)} has no comment block"
