@@ -125,6 +125,56 @@ def generator_forward(q: np.ndarray, weights: dict, n_blocks: int = N_BLOCKS,
     return conv3x3(u, W["out.w"], W["out.b"], padding)[0]
 
 
+def _conv3x3_valid(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """conv3x3 without padding: the output is 2 smaller in each direction and
+    every value is the full 3x3 sum (no wrap, no zeros)."""
+    cout = w.shape[0]
+    H, W = x.shape[1] - 2, x.shape[2] - 2
+    out = np.broadcast_to(b[:, None, None], (cout, H, W)).astype(np.float64).copy()
+    for ky in range(3):
+        for kx in range(3):
+            out += np.einsum("oc,chw->ohw", w[:, :, ky, kx], x[:, ky:ky + H, kx:kx + W])
+    return out
+
+
+def generator_reach(n_blocks: int = N_BLOCKS) -> int:
+    """Coarse cells around a fine point's coarse cell that its G value depends
+    on: the first conv, two per residual block and the up conv at coarse
+    resolution, plus one coarse cell for the last (fine) conv."""
+    return 2 * n_blocks + 3
+
+
+def generator_at(q: np.ndarray, weights: dict, points, n_blocks: int = N_BLOCKS,
+                 emulate_bf16: bool = False) -> np.ndarray:
+    """G(q) of a periodic coarse field q at the fine points [(Y, X), ...], each
+    computed from its own neighbourhood of coarse cells (generator_reach
+    around (Y // 2, X // 2), indices wrapped) with unpadded convolutions, so the
+    cost per point does not depend on the grid size.  Same layers, order and
+    bf16 rounding points as generator_forward."""
+    rnd = bf16_round if emulate_bf16 else (lambda a: a)
+    W = {k: (rnd(v) if (emulate_bf16 and k.endswith(("w", "w1", "w2"))) else v)
+         for k, v in weights.items()}
+    n = q.shape[0]
+    R = generator_reach(n_blocks)
+    if 2 * R + 1 > n:
+        raise ValueError(f"grid {n} smaller than the generator's reach {2 * R + 1}")
+    out = []
+    for Y, X in points:
+        cy, cx = Y // 2, X // 2
+        rows = (cy - R + np.arange(2 * R + 1)) % n
+        cols = (cx - R + np.arange(2 * R + 1)) % n
+        x = q[np.ix_(rows, cols)][None, :, :].astype(np.float64)
+        x = rnd(prelu(_conv3x3_valid(x, W["in.w"], W["in.b"]), W["in.a"]))
+        for k in range(n_blocks):
+            t = rnd(prelu(_conv3x3_valid(x, W[f"b{k}.w1"], W[f"b{k}.b1"]), W[f"b{k}.a"]))
+            x = rnd(x[:, 2:-2, 2:-2] + _conv3x3_valid(t, W[f"b{k}.w2"], W[f"b{k}.b2"]))
+        u = _conv3x3_valid(x, W["up.w"], W["up.b"])  # 3 x 3 coarse cells: cy - 1 .. cy + 1
+        u = rnd(prelu(pixel_shuffle2(u), W["up.a"]))  # fine rows 2 cy - 2 .. 2 cy + 3
+        g = _conv3x3_valid(u, W["out.w"], W["out.b"])[0]  # fine rows 2 cy - 1 .. 2 cy + 2
+        out.append(g[Y - (2 * cy - 1), X - (2 * cx - 1)])
+    return np.array(out)
+
+
 def sr_scale(ec: np.ndarray) -> float:
     """Input scale s = max |e_c|, or 1 for a zero field."""
     s = float(np.max(np.abs(ec)))

@@ -74,3 +74,40 @@ def test_sr_prolong_scale_equivariance():
     b = g.sr_prolong(1e-6 * ec, w, n_blocks=1)
     np.testing.assert_allclose(b, 1e-6 * a, rtol=1e-10, atol=1e-20)
     assert g.sr_scale(np.zeros((4, 4))) == 1.0
+
+
+def test_sampled_generator_equals_the_whole_grid_forward_pass():
+    """generator_at (unpadded convolutions on each point's neighbourhood) gives
+    the whole-grid circular forward pass's values at those points, plain and
+    with bf16 emulation, including points whose neighbourhood wraps."""
+    from oracle import generator as og
+    from synthetic.weights import random_weights
+    w = random_weights(3)
+    q = np.random.default_rng(0).standard_normal((48, 48))
+    pts = [(0, 0), (95, 95), (1, 94), (47, 50), (10, 3), (60, 91), (33, 0)]
+    for bf16 in (False, True):
+        full = og.generator_forward(q, w, emulate_bf16=bf16)
+        got = og.generator_at(q, w, pts, emulate_bf16=bf16)
+        np.testing.assert_array_equal(got, np.array([full[y, x] for y, x in pts]))
+
+
+def test_generator_reach_is_tight():
+    """A fine point's value depends on coarse cells up to generator_reach away
+    (on the side its fine-grid parity faces) and on none further."""
+    from oracle import generator as og
+    from synthetic.weights import random_weights
+    nb, n = 2, 32
+    w = random_weights(3, n_blocks=nb)
+    q = np.random.default_rng(0).standard_normal((n, n))
+    R = og.generator_reach(nb)
+    for Y, side in ((20, -1), (21, +1)):  # even fine rows reach further up, odd ones further down
+        cy, cx = Y // 2, 21 // 2
+        base = og.generator_forward(q, w, n_blocks=nb)[Y, 21]
+
+        def bumped(d):
+            q2 = q.copy()
+            q2[(cy + d) % n, cx] += 1.0
+            return og.generator_forward(q2, w, n_blocks=nb)[Y, 21]
+
+        assert bumped(side * R) != base
+        assert bumped(side * (R + 1)) == base and bumped(-side * R) == base
