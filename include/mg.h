@@ -383,8 +383,10 @@ mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, i
  * larger sizes return MG_ERR_INVALID_ARG.  No cudaMalloc/cudaFree or other
  * allocating call is made.  The first call on a device looks up the array's
  * address there (cudaGetSymbolAddress) - make that first call before any
- * stream capture.  All calls share the array and rewrite it, so calls that
- * overlap on the GPU (unordered streams) race.  Asynchronous on `stream`. */
+ * stream capture - and keeps it for the process, so the entry point must not
+ * be used across a cudaDeviceReset.  All calls share the array and rewrite
+ * it, so calls that overlap on the GPU (unordered streams) race.
+ * Asynchronous on `stream`. */
 mg_status mg_op_vcycle_static(int dtype, int n, int coarsest, void *x, const void *b, int nu1,
                               int nu2, int zero_init, void *stream);
 
@@ -407,6 +409,27 @@ mg_status mg_op_sr_conv(int mode, int H, int W, const void *in, const void *skip
  * (2nc x 2nc floats, device).  nc a multiple of 128.  Synchronous on the
  * context's stream. */
 mg_status mg_op_sr_generator(mg_ctx *ctx, const float *ec, int nc, float *out);
+
+/* One layer of the context's loaded SR generator (Sec. 2.3, Fig. 1b;
+ * Appendix A, Algorithm 5) on caller buffers: the production kernels and
+ * packed weights of mg_op_sr_generator, which runs layers 0 .. 2 n_blocks + 2
+ * in order, for layer-by-layer verification.  Buffers are device memory,
+ * activations padded bf16 in the layout of mg_op_sr_conv (halo written).
+ *   layer 0: in = ec (nc x nc floats); *s (device float) receives
+ *            s = max|ec| (1 when ec = 0); out = PReLU(conv 1 -> 64 of ec / s),
+ *            padded coarse.
+ *   layers 1 .. 2 n_blocks: residual block k = (layer - 1) / 2; odd layers
+ *            out = PReLU(conv(in)), even layers out = skip + conv(in) (skip
+ *            the block's input); in, skip, out padded coarse.
+ *   layer 2 n_blocks + 1: out = PReLU(pixel_shuffle(conv 64 -> 256 of in)),
+ *            in padded coarse, out padded fine ((2nc + 2)^2 x 64).
+ *   layer 2 n_blocks + 2: out = s * (conv 64 -> 1 of in), in padded fine,
+ *            *s read, out 2nc x 2nc floats.
+ * nc a multiple of 128 (the coarse grid).  MG_ERR_INVALID_ARG for a layer
+ * out of range or a missing buffer, MG_ERR_NO_WEIGHTS without weights,
+ * MG_ERR_TIMEOUT if a bounded wait expired.  Synchronous on the context's
+ * stream. */
+mg_status mg_op_sr_layer(mg_ctx *ctx, int layer, int nc, const void *in, const void *skip, float *s, void *out);
 
 /* Outer residual of FP64 data: s = b - (4x - sum nbrs) with b = h^2 (f - mu)
  * formed in FP64 (so s = h^2 r), written as float to s32 when s32 != NULL;

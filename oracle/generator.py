@@ -125,6 +125,34 @@ def generator_forward(q: np.ndarray, weights: dict, n_blocks: int = N_BLOCKS,
     return conv3x3(u, W["out.w"], W["out.b"], padding)[0]
 
 
+def generator_stages(q: np.ndarray, weights: dict, n_blocks: int = N_BLOCKS,
+                     emulate_bf16: bool = False, padding: str = "circular") -> list:
+    """The layers of generator_forward one by one: a list of (v, a) per stage,
+    v the stage's value before its output is stored and a the stored value
+    (v rounded to bf16 with emulate_bf16, else v).  Stages: the 1 -> 64 layer
+    with PReLU; for each residual block its first convolution with PReLU and
+    its second convolution plus the skip; the 64 -> 256 layer with the pixel
+    shuffle and PReLU; the 64 -> 1 layer (its a is v: the output is not
+    stored as bf16).  Each stage reads the previous stage's a."""
+    rnd = bf16_round if emulate_bf16 else (lambda a: a)
+    W = {k: (rnd(v) if (emulate_bf16 and k.endswith(("w", "w1", "w2"))) else v)
+         for k, v in weights.items()}
+    out = []
+    v = prelu(conv3x3(q[None, :, :].astype(np.float64), W["in.w"], W["in.b"], padding), W["in.a"])
+    out.append((v, rnd(v)))
+    for k in range(n_blocks):
+        x = out[-1][1]
+        v = prelu(conv3x3(x, W[f"b{k}.w1"], W[f"b{k}.b1"], padding), W[f"b{k}.a"])
+        out.append((v, rnd(v)))
+        v = x + conv3x3(out[-1][1], W[f"b{k}.w2"], W[f"b{k}.b2"], padding)
+        out.append((v, rnd(v)))
+    v = prelu(pixel_shuffle2(conv3x3(out[-1][1], W["up.w"], W["up.b"], padding)), W["up.a"])
+    out.append((v, rnd(v)))
+    v = conv3x3(out[-1][1], W["out.w"], W["out.b"], padding)[0]
+    out.append((v, v))
+    return out
+
+
 def _conv3x3_valid(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
     """conv3x3 without padding: the output is 2 smaller in each direction and
     every value is the full 3x3 sum (no wrap, no zeros)."""
@@ -173,6 +201,36 @@ def generator_at(q: np.ndarray, weights: dict, points, n_blocks: int = N_BLOCKS,
         g = _conv3x3_valid(u, W["out.w"], W["out.b"])[0]  # fine rows 2 cy - 1 .. 2 cy + 2
         out.append(g[Y - (2 * cy - 1), X - (2 * cx - 1)])
     return np.array(out)
+
+
+def generator_block(q: np.ndarray, weights: dict, y0: int, x0: int, rows: int, cols: int,
+                    n_blocks: int = N_BLOCKS, emulate_bf16: bool = False) -> np.ndarray:
+    """G(q) of a periodic coarse field q on the block of fine points
+    [y0, y0 + rows) x [x0, x0 + cols) (all even; the block may wrap around the
+    grid), from the block's own neighbourhood of coarse cells (generator_reach
+    beyond the block's coarse cells, indices wrapped) with unpadded
+    convolutions.  The same computation as generator_at for every point of
+    the block, sharing the layers' work between neighbouring points."""
+    if y0 % 2 or x0 % 2 or rows % 2 or cols % 2 or rows <= 0 or cols <= 0:
+        raise ValueError("block origin and size must be even and positive")
+    rnd = bf16_round if emulate_bf16 else (lambda a: a)
+    W = {k: (rnd(v) if (emulate_bf16 and k.endswith(("w", "w1", "w2"))) else v)
+         for k, v in weights.items()}
+    n = q.shape[0]
+    R = generator_reach(n_blocks)
+    if rows // 2 + 2 * R > n or cols // 2 + 2 * R > n:
+        raise ValueError("block and the generator's reach exceed the grid")
+    ridx = (y0 // 2 - R + np.arange(rows // 2 + 2 * R)) % n
+    cidx = (x0 // 2 - R + np.arange(cols // 2 + 2 * R)) % n
+    x = q[np.ix_(ridx, cidx)][None, :, :].astype(np.float64)
+    x = rnd(prelu(_conv3x3_valid(x, W["in.w"], W["in.b"]), W["in.a"]))
+    for k in range(n_blocks):
+        t = rnd(prelu(_conv3x3_valid(x, W[f"b{k}.w1"], W[f"b{k}.b1"]), W[f"b{k}.a"]))
+        x = rnd(x[:, 2:-2, 2:-2] + _conv3x3_valid(t, W[f"b{k}.w2"], W[f"b{k}.b2"]))
+    u = _conv3x3_valid(x, W["up.w"], W["up.b"])  # coarse cells y0/2 - 1 .. (y0 + rows)/2
+    u = rnd(prelu(pixel_shuffle2(u), W["up.a"]))  # fine rows y0 - 2 .. y0 + rows + 1
+    g = _conv3x3_valid(u, W["out.w"], W["out.b"])[0]  # fine rows y0 - 1 .. y0 + rows
+    return g[1:rows + 1, 1:cols + 1]
 
 
 def sr_scale(ec: np.ndarray) -> float:

@@ -2384,6 +2384,15 @@ mg_status mg_op_sr_generator(mg_ctx *c, const float *ec, int nc, float *out) {
     return MG_OK;
 }
 
+mg_status mg_op_sr_layer(mg_ctx *c, int layer, int nc, const void *in, const void *skip, float *s, void *out) {
+    if (!c) {
+        set_err("null context");
+        return MG_ERR_INVALID_ARG;
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    return sr_layer(&c->sr, layer, nc, in, skip, s, out, c->stream, g_err, sizeof g_err);
+}
+
 mg_status mg_op_outer_residual(int n, const double *f, const double *x, double mu, float *s32,
                                double *out, void *stream) {
     MG_TRY(op_check(0, n, 4));

@@ -206,6 +206,27 @@ __device__ __forceinline__ float residual_exact_f32(double b, double x, double x
 // order inside the block), the last block to finish sums the partials in
 // index order and resets the arrival counter.  `nslot` independent sums.
 // ----------------------------------------------------------------------------
+// Sum of squares of float values, kept per thread as an unevaluated pair
+// hi + lo of floats: each square is split exactly (v * v = p + e, e from an
+// FMA) and each addition to hi is made exact by Knuth's TwoSum, its rounding
+// error going to lo with e.  hi + lo equals the exact sum up to the roundings
+// of the lo additions (relative error below n^2 2^-48 for n terms): an FP64-
+// grade sum at FP32 instruction cost (the FP64 pipe runs at 1/64 of the FP32
+// rate).  The _rn intrinsics keep the compiler from contracting p into an FMA.
+struct SqSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float p = __fmul_rn(v, v);
+        const float e = __fmaf_rn(v, v, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 constexpr int kRedBlocks = 304;  // 2 blocks per SM on 152 SMs (4 measured slower for the FP64 kernels)
 constexpr int kRedStride = 1216;  // capacity of a Reduction's partials: blocks of one launch
 constexpr int kWideBlocks = 608;  // 4 blocks per SM: the update (latency-bound)

@@ -1235,12 +1235,12 @@ __global__ void __launch_bounds__(kRedThreads) k_scaled_rhs(const double *__rest
         b[p] = h2 * (f[p] - mu);
 }
 
-// residual_norm_note: the residual itself is exact before its rounding to
-// float (it decides the accuracy of the solution), but its norm only decides
-// when to stop and is reported to the user: each thread sums the squares of
-// its float residuals in FP32 (tens of terms, relative error ~1e-6) and the
-// block and grid sums run in FP64.  A relative residual of 1e-10 is therefore
-// known to ~6 digits.
+// residual_norm_note: the residual is exact before its rounding to float (the
+// inner solve's input); its norm, which decides when to stop, is the 2-norm
+// of those float values: each thread sums their squares exactly as a float
+// pair (SqSum) and the block and grid sums run in FP64, so the norm carries
+// the floats' rounding only (relative error <= 2^-24) and a relative residual
+// of 1e-10 is known to ~7 digits.
 //
 // Scaled residual at point p = i * n + j of the periodic grid (n = 2^lg):
 // s = b - (4 x - (x_N + x_S + x_W + x_E)), b = h^2 (f - mu), the stencil sum
@@ -1276,7 +1276,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
     const size_t N = (size_t)n * n;
     const int lg = __ffs(n) - 1;
     const double mu = fsum ? *fsum / (double)N : mu_host;
-    float ss = 0.f;  // squares of the float residual, FP32 per thread (see residual_norm_note)
+    SqSum ss;  // squares of the float residual (see residual_norm_note)
     double ff = 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < N; p0 += 2 * stride) {
@@ -1286,14 +1286,14 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(
             if (p < N) {
                 double fc;
                 const float sv = outer_point<BMODE>(f, bsc, x, p, n, lg, h2, mu, &fc);
-                ss = fmaf(sv, sv, ss);
+                ss.add(sv);
                 if (FNORM) ff += fc * fc;
                 if (WRITE32) s32[p] = sv;
             }
         }
     }
     double vals[2];
-    vals[0] = block_sum((double)ss, sh);
+    vals[0] = block_sum(ss.value(), sh);
     vals[1] = FNORM ? block_sum(ff, sh) : 0.0;
     reduce_finish<2>(red, vals, sh);
 }
@@ -1343,7 +1343,7 @@ __device__ __forceinline__ float aligned_to_f32(long long acc, int E) {
 template <bool FIRST>
 __device__ __forceinline__ void residual_task(int task, int n, int lg, const double *__restrict__ f, double mu,
                                               double h2, long long *__restrict__ bint, int *__restrict__ ebt,
-                                              const double *__restrict__ x, float *__restrict__ s32, float &ss,
+                                              const double *__restrict__ x, float *__restrict__ s32, SqSum &ss,
                                               double &ff) {
     constexpr int R = kResRows;
     constexpr unsigned kFull = 0xffffffffu;
@@ -1402,7 +1402,7 @@ __device__ __forceinline__ void residual_task(int task, int n, int lg, const dou
         if (lane == 31) Ea = hE;
         const long long acc = ((bq[k] >> bs) - C * 4) + ((X[k] + X[k + 2]) + (W + Ea));
         const float sv = special ? __uint_as_float(0x7fc00000u) : aligned_to_f32(acc, E);
-        ss = fmaf(sv, sv, ss);
+        ss.add(sv);
         s32[((size_t)(r0 + k) << lg) + c] = sv;
     }
 }
@@ -1415,26 +1415,25 @@ __global__ void __launch_bounds__(kRedThreads, FIRST ? 2 : 3) k_outer_residual_t
     __shared__ double sh[32];
     const int lg = __ffs(n) - 1;
     const double mu = fsum ? *fsum / ((double)n * n) : mu_host;
-    float ss = 0.f;  // squares of the float residual, FP32 per thread (see residual_norm_note)
+    SqSum ss;  // squares of the float residual (see residual_norm_note)
     double ff = 0.0;
     const int ntask = (n >> 5) * (n / kResRows), wpb = blockDim.x >> 5;
     for (int t = blockIdx.x * wpb + (int)(threadIdx.x >> 5); t < ntask; t += gridDim.x * wpb)
         residual_task<FIRST>(t, n, lg, f, mu, h2, bint, ebt, x, s32, ss, ff);
     double vals[2];
-    vals[0] = block_sum((double)ss, sh);
+    vals[0] = block_sum(ss.value(), sh);
     vals[1] = FIRST ? block_sum(ff, sh) : 0.0;
     reduce_finish<2>(red, vals, sh);
 }
 
-// x += e (FP64 update by the FP32 correction), sum e^2 -> out[0].  The norm
-// is reported, not used by the iteration, so its squares accumulate in FP32
-// per thread (then in FP64 across threads).
+// x += e (FP64 update by the FP32 correction), sum e^2 -> out[0] (squares
+// summed exactly per thread as a float pair, then in FP64 across threads).
 __global__ void __launch_bounds__(kRedThreads) k_update(double *__restrict__ x,
                                                         const float *__restrict__ e, size_t N,
                                                         Reduction red) {
     pdl_enter();
     __shared__ double sh[32];
-    float ee = 0.f;
+    SqSum ee;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t p0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p0 < N; p0 += kUnroll * stride) {
         float ev[kUnroll];
@@ -1449,10 +1448,10 @@ __global__ void __launch_bounds__(kRedThreads) k_update(double *__restrict__ x,
         for (int u = 0; u < kUnroll; ++u) {
             const size_t p = p0 + u * stride;
             if (p < N) x[p] = xv[u] + f32_to_f64(ev[u]);
-            ee = fmaf(ev[u], ev[u], ee);
+            ee.add(ev[u]);
         }
     }
-    double vals[1] = {block_sum((double)ee, sh)};
+    double vals[1] = {block_sum(ee.value(), sh)};
     reduce_finish<1>(red, vals, sh);
 }
 
@@ -1462,7 +1461,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_v(double *__restrict__ x
                                                           size_t N, Reduction red) {
     pdl_enter();
     __shared__ double sh[32];
-    float ee = 0.f;
+    SqSum ee;
     const size_t G = N >> 2, stride = (size_t)gridDim.x * blockDim.x;
     const float4 *e4 = reinterpret_cast<const float4 *>(e);
     double2 *x2 = reinterpret_cast<double2 *>(x);
@@ -1484,14 +1483,14 @@ __global__ void __launch_bounds__(kRedThreads) k_update_v(double *__restrict__ x
             if (g < G) {
                 x2[2 * g] = make_double2(xa[u].x + f32_to_f64(ev[u].x), xa[u].y + f32_to_f64(ev[u].y));
                 x2[2 * g + 1] = make_double2(xb[u].x + f32_to_f64(ev[u].z), xb[u].y + f32_to_f64(ev[u].w));
-                ee = fmaf(ev[u].x, ev[u].x, ee);
-                ee = fmaf(ev[u].y, ev[u].y, ee);
-                ee = fmaf(ev[u].z, ev[u].z, ee);
-                ee = fmaf(ev[u].w, ev[u].w, ee);
+                ee.add(ev[u].x);
+                ee.add(ev[u].y);
+                ee.add(ev[u].z);
+                ee.add(ev[u].w);
             }
         }
     }
-    double vals[1] = {block_sum((double)ee, sh)};
+    double vals[1] = {block_sum(ee.value(), sh)};
     reduce_finish<1>(red, vals, sh);
 }
 
@@ -1700,7 +1699,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_b(const RhsDesc *__restrict
 
 // One right-hand side's points of a batched outer residual (see outer_point).
 template <int BMODE>
-__device__ __forceinline__ void outer_rows_b(const RhsDesc &d, double mu, float &ss, double &ff) {
+__device__ __forceinline__ void outer_rows_b(const RhsDesc &d, double mu, SqSum &ss, double &ff) {
     const int n = d.n, lg = __ffs(n) - 1;
     const size_t N = (size_t)n * n;
     const size_t stride = (size_t)d.nblk * blockDim.x;
@@ -1711,7 +1710,7 @@ __device__ __forceinline__ void outer_rows_b(const RhsDesc &d, double mu, float 
             if (p < N) {
                 double fc;
                 const float sv = outer_point<BMODE>(d.f, d.bsc, d.x, p, n, lg, d.h2, mu, &fc);
-                ss = fmaf(sv, sv, ss);
+                ss.add(sv);
                 if (BMODE == 1) ff += fc * fc;
                 d.s32[p] = sv;
             }
@@ -1729,7 +1728,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc 
     if (active && !active[d.slot]) return;
     const size_t N = (size_t)d.n * d.n;
     const double mu = fsum[(size_t)d.slot * kMaxSlots] / (double)N;
-    float ss = 0.f;
+    SqSum ss;
     double ff = 0.0;
     const bool fresh = FNORM && (first_all || d.first);
     if (d.n >= kResMinN) {
@@ -1748,7 +1747,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual_b(const RhsDesc 
         outer_rows_b<2>(d, mu, ss, ff);
     }
     double vals[2];
-    vals[0] = block_sum((double)ss, sh);
+    vals[0] = block_sum(ss.value(), sh);
     vals[1] = FNORM ? block_sum(ff, sh) : 0.0;
     batch_finish<2>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
@@ -1760,7 +1759,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restr
     const RhsDesc d = rd[find_rhs(rd, nrhs)];
     if (active && !active[d.slot]) return;
     const size_t N = (size_t)d.n * d.n;
-    float ee = 0.f;
+    SqSum ee;
     const size_t stride = (size_t)d.nblk * blockDim.x;
     for (size_t p0 = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p0 < N; p0 += kUnroll * stride) {
         float ev[kUnroll];
@@ -1775,10 +1774,10 @@ __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restr
         for (int u = 0; u < kUnroll; ++u) {
             const size_t p = p0 + u * stride;
             if (p < N) d.x[p] = xv[u] + f32_to_f64(ev[u]);
-            ee = fmaf(ev[u], ev[u], ee);
+            ee.add(ev[u]);
         }
     }
-    double vals[1] = {block_sum((double)ee, sh)};
+    double vals[1] = {block_sum(ee.value(), sh)};
     batch_finish<1>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
 

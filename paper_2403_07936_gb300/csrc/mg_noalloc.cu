@@ -14,6 +14,9 @@
 // up to 16 x 16 points (a 256 x 256 matrix); larger grids are rejected.  All
 // calls share the one array and each call rewrites it on the caller's stream,
 // so calls that overlap on the GPU (different streams, no ordering) race.
+// The array's address is looked up once per device and kept for the process;
+// after a cudaDeviceReset the module is loaded anew and that address is stale,
+// so this entry point must not be used across a device reset.
 #include <stdio.h>
 
 #include <mutex>
@@ -37,9 +40,21 @@ void *g_pinv_addr[kMaxDevices] = {};
 // Closed-form pseudo-inverse of the scaled periodic operator 4I - shifts on an
 // m x m grid: entry (p, q) = (1/m^2) sum_{k != 0} cos(2 pi k.(p - q) / m) / lam(k),
 // lam(k) = 4 sin^2(pi kx / m) + 4 sin^2(pi ky / m).  One thread per entry.
+// Each block first tabulates lam(k) (m^2 <= 256 values) and cos(2 pi j / m)
+// (m <= 16 values) in shared memory, so an entry costs table reads, FP64
+// divisions and additions instead of three transcendental calls per term.
 template <typename T>
 __global__ void k_build_pinv(T *__restrict__ out, int m) {
+    __shared__ double lam[kStaticCoarsestMax * kStaticCoarsestMax];
+    __shared__ double cosv[kStaticCoarsestMax];
     const int Nc = m * m;
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
+        const int ky = k / m, kx = k - ky * m;
+        const double sx = sinpi((double)kx / m), sy = sinpi((double)ky / m);
+        lam[k] = 4.0 * (sx * sx + sy * sy);
+    }
+    for (int j = threadIdx.x; j < m; j += blockDim.x) cosv[j] = cospi(2.0 * j / m);
+    __syncthreads();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Nc * Nc) return;
     const int P = e / Nc, Q = e - P * Nc;
@@ -49,9 +64,7 @@ __global__ void k_build_pinv(T *__restrict__ out, int m) {
     for (int ky = 0; ky < m; ++ky)
         for (int kx = 0; kx < m; ++kx) {
             if (kx == 0 && ky == 0) continue;
-            const double sx = sinpi((double)kx / m), sy = sinpi((double)ky / m);
-            const int ph = (kx * dj + ky * di) % m;
-            acc += cospi(2.0 * ph / m) / (4.0 * (sx * sx + sy * sy));
+            acc += cosv[(kx * dj + ky * di) % m] / lam[ky * m + kx];
         }
     out[e] = (T)(acc / Nc);
 }

@@ -939,6 +939,66 @@ mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t s, ch
     return MG_OK;
 }
 
+mg_status sr_layer(SrState *st, int layer, int nc, const void *in, const void *skip, float *s, void *out,
+                   cudaStream_t strm, char *err, size_t errlen) {
+    if (!st->loaded) {
+        snprintf(err, errlen, "no generator weights loaded");
+        return MG_ERR_NO_WEIGHTS;
+    }
+    const int nb = st->n_blocks;
+    if (layer < 0 || layer > 2 * nb + 2 || nc < TM || nc % TM || !in || !out || !s ||
+        (layer >= 1 && layer <= 2 * nb && layer % 2 == 0 && !skip)) {
+        snprintf(err, errlen, "sr_layer: bad layer %d (0..%d), size %d (a multiple of %d) or null buffer", layer,
+                 2 * nb + 2, nc, TM);
+        return MG_ERR_INVALID_ARG;
+    }
+    cudaError_t e = prepare_conv();
+    if (e == cudaSuccess) e = cudaMemsetAsync(st->err, 0, sizeof(int), strm);
+    if (e == cudaSuccess && layer == 0) {
+        const size_t N = (size_t)nc * nc;
+        k_absmax<<<kRedBlocks, kRedThreads, 0, strm>>>((const float *)in, N, st->red, st->red_counter, s);
+        count_launches(1);
+        k_conv_in<<<(unsigned)((N + 255) / 256), 256, 0, strm>>>((const float *)in, nc, s, st->w_in,
+                                                               (__nv_bfloat16 *)out);
+        count_launches(1);
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess && layer <= 2 * nb + 1) {
+        const int l = layer - 1;  // weight layer (the pixel-shuffle groups follow the blocks)
+        const int mode = layer == 2 * nb + 1 ? MODE_SHUFFLE : (l % 2 ? MODE_RESID : MODE_PRELU);
+        CUtensorMap tin, tout;
+        if (!make_act_map(&tin, const_cast<void *>(in), nc, nc) ||
+            !(mode == MODE_SHUFFLE ? make_act_map(&tout, const_cast<void *>(in), nc, nc)
+                                   : make_out_map(&tout, out, nc, nc))) {
+            snprintf(err, errlen, "sr_layer: tensor map encoding failed");
+            return MG_ERR_INVALID_ARG;
+        }
+        const float *prelu = mode == MODE_SHUFFLE ? st->prelu_up : st->prelu_blk + (size_t)(l / 2) * C;
+        ConvArgs a = {mode == MODE_RESID ? (const __nv_bfloat16 *)skip : nullptr, (__nv_bfloat16 *)out,
+                      st->bias_tc + (size_t)l * C, mode == MODE_RESID ? nullptr : prelu, nc, nc, l, 0, 0, st->err};
+        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, st->tm_w, tout, a, 1, strm);
+        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, st->tm_w, tout, a, 1, strm);
+        else e = launch_conv<MODE_SHUFFLE>(tin, st->tm_w, tout, a, 4, strm);
+    } else if (e == cudaSuccess) {
+        const int nf = 2 * nc;
+        dim3 grid(nf / OUT_T, nf / OUT_T);
+        k_conv_out<<<grid, OUT_T * OUT_T, 0, strm>>>((const __nv_bfloat16 *)in, nf, st->w_out, s, (float *)out);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, st->err, sizeof(int), cudaMemcpyDeviceToHost, strm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "sr_layer: %s", cudaGetErrorString(e));
+        return MG_ERR_CUDA;
+    }
+    if (flag) {
+        snprintf(err, errlen, "sr_layer: a bounded wait in the tensor-core kernel timed out");
+        return MG_ERR_TIMEOUT;
+    }
+    return MG_OK;
+}
+
 mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip, const void *w_packed,
                         const float *bias, const float *prelu, void *out, cudaStream_t s, char *err,
                         size_t errlen) {

@@ -69,6 +69,15 @@ mg_status sr_view(SrState *view, const SrState *st, int nc, char *err, size_t er
 // Free a state; a view frees only its own buffers.
 void sr_free(SrState *st);
 
+// One layer of the loaded generator on caller buffers (verification; the
+// kernels and weights of sr_correction): layer 0 = s = max|ec| into *s, then
+// conv 1 -> 64 + PReLU of ec / s; 1 .. 2 n_blocks = the block convolutions
+// (odd: + PReLU; even: + skip); 2 n_blocks + 1 = conv 64 -> 256, shuffle,
+// PReLU; 2 n_blocks + 2 = s * conv 64 -> 1 of the padded fine activation.
+// Synchronous on stream.
+mg_status sr_layer(SrState *st, int layer, int nc, const void *in, const void *skip, float *s, void *out,
+                   cudaStream_t stream, char *err, size_t errlen);
+
 // One tensor-core convolution layer on padded bf16 activations (verification).
 mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip, const void *w_packed,
                         const float *bias, const float *prelu, void *out, cudaStream_t stream,

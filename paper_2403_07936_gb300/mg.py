@@ -87,6 +87,7 @@ SIGNATURES = {
     "mg_op_vcycle_static": (_I, [_I, _I, _I, _VP, _VP, _I, _I, _I, _VP]),
     "mg_op_sr_conv": (_I, [_I, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mg_op_sr_generator": (_I, [_VP, _VP, _I, _VP]),
+    "mg_op_sr_layer": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP]),
     "mg_op_outer_residual": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP]),
     "mg_op_convert": (_I, [_I, _SZ, _VP, _VP, _VP]),
 }
@@ -427,6 +428,11 @@ def op_sr_conv(mode: int, H: int, W: int, inp, skip, w_packed, bias, prelu, out,
 
 def op_sr_generator(ctx: "Context", ec, out):
     _check(load().mg_op_sr_generator(ctx.handle, ptr(ec), ec.shape[-1], ptr(out)))
+
+
+def op_sr_layer(ctx: "Context", layer: int, nc: int, inp, out, s, skip=None):
+    """One layer of the context's generator on caller buffers (see mg_op_sr_layer)."""
+    _check(load().mg_op_sr_layer(ctx.handle, layer, nc, ptr(inp), ptr(skip), ptr(s), ptr(out)))
 
 
 def op_outer_residual(f, x, mu: float, s32, out, stream=None):

@@ -1,6 +1,6 @@
 """Profiling driver: repeated launches of one library operator on random data.
 
-    python -m paper_2403_07936_gb300.profile_ops --op up --n 2048 --reps 5
+    python profile_ops.py --op up --n 2048 --reps 5
 
 Runs `--reps` launches of the chosen operator through the C ABI on cuda:0
 (after building the library) and prints the mean CUDA-event time per launch.
@@ -27,7 +27,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

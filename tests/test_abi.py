@@ -132,3 +132,11 @@ def test_every_declared_function_is_documented():
             m = re.match(r"^(?:mg_status|const char \*|void|unsigned long long|int)\s+\**(mg_\w+)\s*\(", line)
             if m:
                 assert "*/" in "\n".join(lines[max(0, i - 3):i]), f"{m.group(1)} has no comment block"
+
+
+def test_allocation_free_entry_point_source_calls_no_allocator():
+    """The translation unit of mg_op_vcycle_static names no CUDA allocation call."""
+    import re
+    src = open(os.path.join(ROOT, "paper_2403_07936_gb300", "csrc", "mg_noalloc.cu")).read()
+    code = "\n".join(line.split("//")[0] for line in src.splitlines())
+    assert not re.search(r"cuda(Malloc|Free|MallocAsync|FreeAsync|MallocHost|HostAlloc|MallocManaged)\s*\(", code)

@@ -65,7 +65,7 @@ def test_profile_commands_name_committed_entry_points():
     command line has --clock-control none on its ncu invocation."""
     import glob
     import re
-    ops = set(re.findall(r'"(\w+)"', open(os.path.join(ROOT, "paper_2403_07936_gb300", "profile_ops.py")).read()
+    ops = set(re.findall(r'"(\w+)"', open(os.path.join(ROOT, "profile_ops.py")).read()
                          .split('choices=[', 1)[1].split(']', 1)[0]))
     bench_flags = set(re.findall(r'add_argument\("(--[\w-]+)"', open(os.path.join(ROOT, "bench.py")).read()))
     md = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
@@ -75,7 +75,7 @@ def test_profile_commands_name_committed_entry_points():
         cmd = text.split("Command", 1)[1].split("\n\n", 2)[1]  # the indented block after the heading line
         cmd = cmd.replace("\\\n", " ")
         assert "ncu " in cmd and "--clock-control none" in cmd, path
-        for op in re.findall(r"profile_ops --op (\w+)", cmd):
+        for op in re.findall(r"profile_ops(?:\.py)? --op (\w+)", cmd):
             assert op in ops, (path, op)
         if "bench.py" in cmd:
             for flag in re.findall(r"(--[\w-]+)", cmd.split("bench.py", 1)[1]):

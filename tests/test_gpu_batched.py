@@ -49,7 +49,8 @@ def test_batch_matches_single_solves_and_exact(mg, sizes):
         assert np.abs(got - alone).max() <= 1e-9 * np.abs(alone).max()
         xe = omg.exact_solve_fft(f - f.mean())
         assert np.abs(got - xe).max() <= 1e-9 * np.abs(xe).max()
-        assert omg.relative_residual(f - f.mean(), got, omg.grid_h(f.shape[0])) <= 1.5e-10
+        h = omg.grid_h(f.shape[0])
+        assert omg.relative_residual(f - f.mean(), got, h) <= 1e-10 + 2e-16 * 8 / h ** 2  # FP64 recomputation margin
 
 
 def test_batch_graph_is_reused_and_handles_converged_members(mg):
@@ -91,3 +92,24 @@ def test_batch_falls_back_for_fp64_contexts(mg):
         assert info["rel_residual"] <= 1e-10
         xe = omg.exact_solve_fft(f - f.mean())
         assert np.abs(x.cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
+
+
+def test_batch_of_the_full_mixed_size_workload(mg):
+    """The batched workload itself: 256 right-hand sides, 128 at 256^2, 96 at
+    512^2 and 32 at 1024^2 (67.1 M points), independent k^-5/3 sources (the
+    benchmark's seeds), one batched graph.  Every member reports a relative
+    residual <= 1e-10; every eighth member (16 + 12 + 4: all three sizes) is
+    checked against the exact FFT solution to 1e-9."""
+    sizes = [256] * 128 + [512] * 96 + [1024] * 32
+    fs = [turbulent_source(n, n // 8, config_seed(3, i)) for i, n in enumerate(sizes)]
+    fts = [torch.tensor(f, device=DEV) for f in fs]
+    ctxs = [mg.Context(_levels(n), n) for n in sizes]
+    xs = [torch.zeros_like(ft) for ft in fts]
+    infos = mg.solve_batched(ctxs, fts, xs, tol=1e-10)
+    assert all(i["rel_residual"] <= 1e-10 for i in infos)  # (a failing member raises)
+    for k in range(0, len(sizes), 8):
+        f = fs[k]
+        xe = omg.exact_solve_fft(f - f.mean())
+        got = xs[k].cpu().numpy()
+        assert np.abs(got - xe).max() <= 1e-9 * np.abs(xe).max(), (k, sizes[k])
+        assert abs(got.mean()) <= 1e-12 * np.abs(got).max()

@@ -46,7 +46,8 @@ def _drain(srv, max_ticks=500):
 def _check_exact(f, x):
     xe = omg.exact_solve_fft(f - f.mean())
     assert np.abs(x - xe).max() <= 1e-9 * np.abs(xe).max()
-    assert omg.relative_residual(f - f.mean(), x, omg.grid_h(f.shape[0])) <= 1.5e-10
+    h = omg.grid_h(f.shape[0])
+    assert omg.relative_residual(f - f.mean(), x, h) <= 1e-10 + 2e-16 * 8 / h ** 2  # FP64 recomputation margin
 
 
 @pytest.mark.parametrize("inner", [0, 2, 5])  # adaptive; fixed V-cycles per outer step

@@ -55,7 +55,7 @@ def test_two_level_solve_converges_to_the_exact_solution(mg):
     assert info["status"] == "MG_OK" and info["rel_residual"] <= 1e-10
     fc = f - f.mean()
     xg = x.cpu().numpy()
-    assert omg.relative_residual(fc, xg, omg.grid_h(n)) <= 1.5e-10
+    assert omg.relative_residual(fc, xg, omg.grid_h(n)) <= 1e-10 + 2e-16 * 8 / omg.grid_h(n) ** 2
     # the error left at that residual is smooth (the weak coarse relaxation is
     # last to reduce the smooth modes, whose residual is small against their
     # size), so it is larger than after the multilevel V-cycle's 1e-9

@@ -111,3 +111,48 @@ def test_generator_reach_is_tight():
 
         assert bumped(side * R) != base
         assert bumped(side * (R + 1)) == base and bumped(-side * R) == base
+
+
+def test_block_generator_equals_the_whole_grid_forward_pass():
+    """generator_block (one unpadded neighbourhood for a block of fine points)
+    gives the whole-grid circular forward pass's values on the block, plain and
+    with bf16 emulation, for blocks inside the grid and blocks that wrap
+    around its edges and corner."""
+    from oracle import generator as og
+    from synthetic.weights import random_weights
+    w = random_weights(3)
+    q = np.random.default_rng(0).standard_normal((48, 48))
+    nf = 96
+    for bf16 in (False, True):
+        full = og.generator_forward(q, w, emulate_bf16=bf16)
+        for y0, x0, rows, cols in ((0, 0, 8, 8), (40, 12, 6, 10), (92, 90, 8, 10), (94, 0, 4, 6)):
+            got = og.generator_block(q, w, y0, x0, rows, cols, emulate_bf16=bf16)
+            ref = full[np.ix_((y0 + np.arange(rows)) % nf, (x0 + np.arange(cols)) % nf)]
+            np.testing.assert_array_equal(got, ref)
+    with pytest.raises(ValueError):
+        og.generator_block(q, w, 1, 0, 4, 4)
+
+
+def test_generator_stages_compose_to_the_forward_pass():
+    """generator_stages: each stage is the stated layer of the previous
+    stage's stored output (checked against torch's conv2d, prelu and
+    pixel_shuffle for the first and the shuffle stage), the stored values are
+    the bf16 roundings, and the last stage is generator_forward bit for bit."""
+    from oracle import generator as og
+    w = random_weights(5)
+    q = np.random.default_rng(1).standard_normal((16, 16))
+    for bf16 in (False, True):
+        st = og.generator_stages(q, w, emulate_bf16=bf16)
+        assert len(st) == 2 * og.N_BLOCKS + 3
+        np.testing.assert_array_equal(st[-1][0], og.generator_forward(q, w, emulate_bf16=bf16))
+        for v, a in st[:-1]:
+            np.testing.assert_array_equal(a, g.bf16_round(v) if bf16 else v)
+    st = og.generator_stages(q, w)
+    x = torch.from_numpy(np.pad(q, 1, mode="wrap"))[None, None]
+    ref = F.prelu(F.conv2d(x, torch.from_numpy(w["in.w"]), torch.from_numpy(w["in.b"])),
+                  torch.from_numpy(w["in.a"]))[0].numpy()
+    np.testing.assert_allclose(st[0][0], ref, rtol=1e-12, atol=1e-12)
+    a = torch.from_numpy(np.pad(st[-3][1], ((0, 0), (1, 1), (1, 1)), mode="wrap"))[None]
+    u = F.conv2d(a, torch.from_numpy(w["up.w"]), torch.from_numpy(w["up.b"]))
+    ref = F.prelu(F.pixel_shuffle(u, 2), torch.from_numpy(w["up.a"]))[0].numpy()
+    np.testing.assert_allclose(st[-2][0], ref, rtol=1e-12, atol=1e-12)

@@ -68,3 +68,26 @@ def test_static_vcycle_rejects_sizes_beyond_its_scratch(lib):
                                      C.c_void_p(x.data_ptr()), 2, 2, 1, None)
         assert st == 1  # MG_ERR_INVALID_ARG
         assert b"static scratch" in lib.mg_last_error()
+
+
+def test_static_vcycle_neither_waits_nor_holds_memory(lib):
+    """The call is asynchronous (it returns while earlier work on its stream
+    is still running: no allocation or other device-wide synchronisation
+    inside it) and leaves the device's free memory unchanged."""
+    stream = torch.cuda.current_stream()
+    x0, b = _case(64, torch.float64, 7)
+    x = x0.clone()
+    st = lib.mg_op_vcycle_static(0, 64, 8, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()), 2, 2, 0,
+                                 C.c_void_p(stream.cuda_stream))
+    assert st == 0, lib.mg_last_error()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    torch.cuda._sleep(200_000_000)  # ~0.1 s of spinning on the stream
+    st = lib.mg_op_vcycle_static(0, 64, 8, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()), 2, 2, 0,
+                                 C.c_void_p(stream.cuda_stream))
+    busy = not stream.query()
+    assert st == 0, lib.mg_last_error()
+    assert busy  # returned before the sleep ahead of it finished
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
