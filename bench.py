@@ -352,31 +352,34 @@ def _events_time(stream, fn, reps):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def batched_leg(mg, dev, stream, flush, args, rank):
+def batched_leg(mg, dev, stream, flush, args, rank, prolong="cubic"):
     import torch
     from synthetic.sources import config_seed, turbulent_source
     sizes = BATCH_SIZES
     fts = [torch.tensor(turbulent_source(n, n // 8, config_seed(3, rank * 1000 + i)), device=dev)
            for i, n in enumerate(sizes)]
+    blob = open(SR_WEIGHTS, "rb").read() if prolong == "sr" else None
     ctxs = []
     for n in sizes:
         c = mg.Context(_levels(n), n)
         c.set_options(stream=stream)
+        if blob is not None:
+            c.load_weights(blob)
         ctxs.append(c)
     xs = [torch.zeros_like(f) for f in fts]
-    for _ in range(args.warmup):
+    for _ in range(args.warmup if prolong == "cubic" else 2):
         for x in xs:
             x.zero_()
-        infos = mg.solve_batched(ctxs, fts, xs)
+        infos = mg.solve_batched(ctxs, fts, xs, prolong=prolong)
     times = []
-    for _ in range(min(args.steps, SIDE_REPS)):
+    for _ in range(min(args.steps, SIDE_REPS if prolong == "cubic" else 3)):
         for x in xs:
             x.zero_()
         flush.zero_()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        infos = mg.solve_batched(ctxs, fts, xs)
+        infos = mg.solve_batched(ctxs, fts, xs, prolong=prolong)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -388,6 +391,20 @@ def batched_leg(mg, dev, stream, flush, args, rank):
     # down + up passes, 13 B each, over the 4/3 hierarchy), per outer step 40 B (FP64 residual
     # 20 B + update 20 B), plus the first residual, the source sum and the projection (44 B)
     bytes_alg = pts * (vc * 13 * 2 * 4 / 3 + outer * 40 + 44)
+    if prolong == "sr":
+        coarse_px = sum((n // 2) ** 2 for n in sizes)
+        sr_cyc = [i["sr_cycles"] for i in infos]
+        return {"workload": "256 right-hand sides: 128 x 256^2, 96 x 512^2, 32 x 1024^2, independent k^-5/3 "
+                            "sources, FP32 V(2,2) in FP64 defect correction (2 V-cycles per outer step), SR "
+                            "prolongation at every right-hand side's finest transition on every V-cycle "
+                            "(trained generator; one launch per layer and grid size for the whole batch), tol 1e-10",
+                "value": len(sizes) / t, "unit": "solves/s", "ms_per_batch": t * 1e3,
+                "vcycles_max": max(i["vcycles"] for i in infos), "outer_max": outer,
+                "sr_vcycles_min": min(sr_cyc), "sr_vcycles_max": max(sr_cyc),
+                "sr_fallbacks": sum(i["sr_fallback"] for i in infos),
+                "rel_residual_max": max(i["rel_residual"] for i in infos),
+                "generator_tflop_per_vcycle": SR_TENSOR_FLOP_PER_COARSE_PX * coarse_px / 1e12,
+                "reps": len(times), "l2": "flushed between steps (512 MB write)"}
     return {"workload": "256 right-hand sides: 128 x 256^2, 96 x 512^2, 32 x 1024^2 (67.1 M points), "
                         "independent k^-5/3 sources, FP32 V(2,2) cubic in FP64 defect correction, tol 1e-10, "
                         "one CUDA graph per batch (one launch per grid size and direction per V-cycle)",
@@ -792,6 +809,8 @@ def main():
 
     # ---- batched: 256 right-hand sides of mixed sizes in one graph ----------
     batched = batched_leg(mg, dev, stream, flush, args, rank) if not args.skip_batched else None
+    batched_sr = (batched_leg(mg, dev, stream, flush, args, rank, prolong="sr")
+                  if not args.skip_batched and os.path.exists(SR_WEIGHTS) else None)
 
     # ---- SR prolongation at 2048^2 (tensor-core generator) ------------------
     sr_info = sr_leg(mg, dev, stream, flush, f_dev, x, args) if not args.skip_sr else None
@@ -914,6 +933,7 @@ def main():
             "mixed_over_fp64": value / value64,
             "kernels_per_solve": kernels,
             "batched": batched,
+            "batched_sr": batched_sr,
             "sr": sr_info,
             "serving": serving,
             "smoothing_sweep": smoothing,

@@ -164,17 +164,27 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *x, mg_prolong prolong)
 mg_status mg_two_level_solve(mg_ctx *ctx, const double *f, double *x, double tol, int coarsen_log2, int nu_smooth,
                              int coarse_sweeps, int max_cycles, mg_prolong prolong, mg_solve_info *info);
 
-/* Solve B independent problems, ctxs[k] with f[k], x[k], each to tol.
- * Contexts may have different N.  When every context is MG_PREC_MIXED with
- * the same nu_pre, nu_post, inner_cycles and max_cycles, all buffers are in
- * device memory and the prolongation is cubic, the whole batch runs as one
- * CUDA graph: each V-cycle of the batch is one launch per grid size and
+/* Solve B independent problems, ctxs[k] with f[k], x[k], each to tol (the
+ * batched form of Algorithm 6 over many right-hand sides; the paper solves
+ * grids one at a time).  Contexts may have different N.  When every context
+ * is MG_PREC_MIXED with the same nu_pre, nu_post, inner_cycles and
+ * max_cycles and all buffers are in device memory, the whole batch runs as
+ * one CUDA graph: each V-cycle of the batch is one launch per grid size and
  * direction (every right-hand side with a level of that size takes part) plus
  * one launch for all coarse levels, the FP64 outer steps are one launch each,
- * and a right-hand side stops once it has converged.  The graph is kept for
- * the next call with the same contexts and buffers (the stream is the first
- * context's).  Otherwise the problems are solved one after another.  Returns
- * the first non-MG_OK status; infos (may be NULL) get one entry each. */
+ * and a right-hand side stops once it has converged.  With MG_PROLONG_SR
+ * (every context loaded with the same weights) the finest transition of each
+ * right-hand side whose coarse grid is >= 128 (a multiple of 128) adds the
+ * generator's correction (Algorithm 5): one generator launch per layer and
+ * grid size serves all right-hand sides of that size, SR on every V-cycle,
+ * inner_cycles V-cycles per outer step, and a right-hand side whose outer
+ * step did not halve its relative residual drops SR for the rest of its
+ * solve (infos[k].sr_fallback); smaller grids use the cubic spline.  The
+ * graph is kept for the next call with the same contexts, buffers and
+ * prolongation (the stream is the first context's).  Otherwise the problems
+ * are solved one after another.  Returns the first non-MG_OK status
+ * (MG_ERR_TIMEOUT if a bounded wait of the generator expired); infos (may be
+ * NULL) get one entry each. */
 mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
                            double tol, mg_prolong prolong, mg_solve_info *infos);
 

@@ -670,6 +670,7 @@ struct BatchLaunch {
     int ngrid;
     int nblocks;
     int variant;  // tile variant (down / up)
+    int size = 0;  // grid size (down / up)
 };
 
 struct BatchPlan {
@@ -678,6 +679,12 @@ struct BatchPlan {
     std::vector<double *> x;
     double tol = 0.0;
     int B = 0, device = -1;
+    mg_prolong prolong = MG_PROLONG_CUBIC;
+    // SR prolongation: one generator batch per grid size whose right-hand
+    // sides end in an SR transition (their finest coarse grid >= 128)
+    std::vector<SrBatch> srb;
+    std::vector<int> sr_size;  // fine grid size of srb[i]
+    uint64_t srb_hash = 0;     // weights the plan was recorded with
     void *dmem = nullptr;
     RhsDesc *d_rhs = nullptr;
     TileGrid *d_tiles = nullptr;
@@ -711,6 +718,7 @@ static void batch_free(BatchPlan *p) {
     if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->dmem);
     cudaFreeHost(p->h_state);
+    for (SrBatch &b : p->srb) sr_batch_free(&b);
     delete p;
 }
 
@@ -734,6 +742,27 @@ static mg_status batch_build(BatchPlan *p) {
         maxN = n > maxN ? n : maxN;
     }
     p->rhs_blocks = blk;
+    // SR groups: right-hand sides of one fine size whose coarse grid the
+    // generator takes (>= 128, a multiple of 128); smaller ones stay cubic
+    std::vector<int> sr_group(B, -1), sr_index(B, -1);
+    if (p->prolong == MG_PROLONG_SR) {
+        for (int sz = maxN; sz >= 2 * kSrMinCoarse; sz >>= 1) {
+            std::vector<const float *> ecs;
+            for (int r = 0; r < B; ++r) {
+                mg_ctx *c = p->ctxs[r];
+                if (c->N == sz && c->levels > 1 && c->lv[0].n > kBottomMax) {
+                    sr_group[r] = (int)p->srb.size();
+                    sr_index[r] = (int)ecs.size();
+                    ecs.push_back(c->lv[1].x32);
+                    rhs[r].sr = 1;
+                }
+            }
+            if (ecs.empty()) continue;
+            p->srb.emplace_back();
+            p->sr_size.push_back(sz);
+            MG_TRY(sr_batch_prepare(&p->srb.back(), (int)ecs.size(), sz / 2, ecs.data(), g_err, sizeof g_err));
+        }
+    }
     std::vector<TileGrid> tiles;
     std::vector<BottomGrid> bottoms;
     for (int v = 0; v < 2; ++v) {
@@ -746,7 +775,7 @@ static mg_status batch_build(BatchPlan *p) {
             return g;
         };
         for (int sz = maxN; sz > kBottomMax; sz >>= 1) {  // down sweeps
-            BatchLaunch L{0, tiles.size(), 0, 0, batch_variant(0, sz, c0->nu1, grids_of(sz))};
+            BatchLaunch L{0, tiles.size(), 0, 0, batch_variant(0, sz, c0->nu1, grids_of(sz)), sz};
             for (int r = 0; r < B; ++r) {
                 mg_ctx *c = p->ctxs[r];
                 for (int l = 0; l + 1 < c->levels; ++l)
@@ -773,13 +802,15 @@ static mg_status batch_build(BatchPlan *p) {
             p->cyc[v].push_back(L);
         }
         for (int sz = 2 * kBottomMax; sz <= maxN; sz <<= 1) {  // up sweeps
-            BatchLaunch L{1, tiles.size(), 0, 0, batch_variant(1, sz, c0->nu2, grids_of(sz))};
+            BatchLaunch L{1, tiles.size(), 0, 0, batch_variant(1, sz, c0->nu2, grids_of(sz)), sz};
             for (int r = 0; r < B; ++r) {
                 mg_ctx *c = p->ctxs[r];
                 for (int l = 0; l + 1 < c->levels; ++l)
                     if (c->lv[l].n == sz) {
-                        tiles.push_back(TileGrid{c->lv[l].t32, c->lv[l].x32, c->lv[l].b32, c->lv[l + 1].x32, sz, 0,
-                                                 L.nblocks, r});
+                        TileGrid t{c->lv[l].t32, c->lv[l].x32, c->lv[l].b32, c->lv[l + 1].x32, sz, 0, L.nblocks, r};
+                        if (l == 0 && sr_group[r] >= 0)
+                            t.extra = p->srb[sr_group[r]].fine_out + (size_t)sr_index[r] * sz * sz;
+                        tiles.push_back(t);
                         L.nblocks += variant_tiles(sz, L.variant);
                         ++L.ngrid;
                     }
@@ -809,6 +840,8 @@ static mg_status batch_build(BatchPlan *p) {
     p->d_out = (double *)(d + o_out);
     p->d_counters = (unsigned *)(d + o_cnt);
     p->d_bm = (int *)(d + o_bm);
+    for (TileGrid &t : tiles)  // SR is skipped for a right-hand side once it has fallen back
+        if (t.extra) t.extra_off = &p->d_state[t.rhs].fallback;
     MG_CUDA(cudaMemset(p->dmem, 0, total));
     MG_CUDA(cudaMemcpy(p->d_rhs, rhs.data(), sizeof(RhsDesc) * B, cudaMemcpyHostToDevice));
     if (!tiles.empty())
@@ -819,7 +852,8 @@ static mg_status batch_build(BatchPlan *p) {
 
     // record: prologue, WHILE(outer step), epilogue
     cudaStream_t s = p->cap;
-    const bool adaptive = c0->rho > 0.0 && c0->adapt_max > 1;
+    // SR batches keep the fixed count of V-cycles per outer step (as SR solves do)
+    const bool adaptive = p->prolong == MG_PROLONG_CUBIC && c0->rho > 0.0 && c0->adapt_max > 1;
     const int step = adaptive ? c0->adapt_max : c0->inner;
     const double rho = adaptive ? c0->rho : 0.0;
     p->adapt_max = adaptive ? step : 0;
@@ -837,9 +871,16 @@ static mg_status batch_build(BatchPlan *p) {
             if (L.kind == 0)
                 e = launch_down_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu1, p->d_active, s,
                                         L.variant);
-            else if (L.kind == 1)
-                e = launch_up_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu2, p->d_active, taps, s,
-                                      L.variant);
+            else if (L.kind == 1) {
+                // the generator's correction for the right-hand sides whose finest grid is this size
+                for (size_t g = 0; g < p->srb.size() && e == cudaSuccess; ++g)
+                    if (p->sr_size[g] == L.size &&
+                        sr_batch_correction(&p->srb[g], &c0->sr, s, g_err, sizeof g_err) != MG_OK)
+                        e = cudaErrorLaunchFailure;
+                if (e == cudaSuccess)
+                    e = launch_up_batched(p->d_tiles + L.off, L.ngrid, L.nblocks, c0->nu2, p->d_active, taps, s,
+                                          L.variant);
+            }
             else
                 e = launch_bottom_batched(p->d_bottom + L.off, L.ngrid, c0->nu1, c0->nu2, p->d_active, taps, s);
         }
@@ -968,12 +1009,17 @@ static void batch_forget(mg_ctx *c) {
 }
 
 // All contexts mixed precision with equal cycle options on one device, all
-// buffers on the device, cubic prolongation: the batched graph applies.
+// buffers on the device, and the cubic prolongation or the SR one with the
+// same generator weights in every context: the batched graph applies.
 static bool batch_eligible(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
                            mg_prolong prolong) {
-    if (B < 1 || prolong != MG_PROLONG_CUBIC) return false;
+    if (B < 1 || (prolong != MG_PROLONG_CUBIC && prolong != MG_PROLONG_SR)) return false;
     mg_ctx *c0 = ctxs[0];
     if (!c0 || c0->prec != MG_PREC_MIXED || c0->probe_kind != kProbeNone) return false;
+    if (prolong == MG_PROLONG_SR) {  // every context holds the same generator weights
+        for (int r = 0; r < B; ++r)
+            if (!ctxs[r] || !ctxs[r]->sr.loaded || ctxs[r]->sr.hash != c0->sr.hash) return false;
+    }
     for (int r = 0; r < B; ++r) {
         mg_ctx *c = ctxs[r];
         if (!c || !f[r] || !x[r] || c->prec != MG_PREC_MIXED || c->nu1 != c0->nu1 || c->nu2 != c0->nu2 ||
@@ -988,14 +1034,15 @@ static bool batch_eligible(mg_ctx *const *ctxs, const double *const *f, double *
 }
 
 static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f, double *const *x, int B,
-                                     double tol, mg_solve_info *infos) {
+                                     double tol, mg_prolong prolong, mg_solve_info *infos) {
     const auto t0 = std::chrono::steady_clock::now();
     mg_ctx *c0 = ctxs[0];
     MG_CUDA(cudaSetDevice(c0->device));
     for (int r = 0; r < B; ++r) MG_TRY(ensure_hierarchy(ctxs[r], false));
     std::lock_guard<std::mutex> lock(g_batch_mutex);
     BatchPlan *p = g_batch;
-    bool same = p && p->B == B && p->tol == tol && p->device == c0->device && p->epoch == tune_epoch();
+    bool same = p && p->B == B && p->tol == tol && p->device == c0->device && p->epoch == tune_epoch() &&
+                p->prolong == prolong && (prolong == MG_PROLONG_CUBIC || p->srb_hash == c0->sr.hash);
     for (int r = 0; same && r < B; ++r)
         same = p->ctxs[r] == ctxs[r] && p->f[r] == f[r] && p->x[r] == x[r];
     if (!same) {
@@ -1005,6 +1052,8 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
         p->B = B;
         p->tol = tol;
         p->device = c0->device;
+        p->prolong = prolong;
+        p->srb_hash = prolong == MG_PROLONG_SR ? c0->sr.hash : 0;
         p->ctxs.assign(ctxs, ctxs + B);
         p->f.assign(f, f + B);
         p->x.assign(x, x + B);
@@ -1017,8 +1066,12 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
         g_batch = p;
     }
     cudaStream_t s = c0->stream;
+    const bool sr = !p->srb.empty();
+    int sr_flag = 0;
+    if (sr) MG_CUDA(cudaMemsetAsync(c0->sr.err, 0, sizeof(int), s));
     MG_CUDA(cudaGraphLaunch(p->exec, s));
     MG_CUDA(cudaMemcpyAsync(p->h_state, p->d_state, sizeof(DevState) * B, cudaMemcpyDeviceToHost, s));
+    if (sr) MG_CUDA(cudaMemcpyAsync(&sr_flag, c0->sr.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (p->adapt_max > 0) MG_CUDA(cudaMemcpyAsync(p->h_bm, p->d_bm, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
     int outer_max = 0;
@@ -1035,9 +1088,9 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
             infos[r].removed_mean = ds.mu;
             infos[r].update_norm = ds.unorm;
             infos[r].time_ms = ms;
-            infos[r].prolong_used = MG_PROLONG_CUBIC;
-            infos[r].sr_fallback = 0;
-            infos[r].sr_cycles = 0;
+            infos[r].prolong_used = ds.sr_used > 0 ? MG_PROLONG_SR : MG_PROLONG_CUBIC;
+            infos[r].sr_fallback = ds.fallback;
+            infos[r].sr_cycles = ds.sr_used;
         }
     }
     if (p->adapt_max > 0)  // optional V-cycles ran only in the steps that chose them
@@ -1045,6 +1098,10 @@ static mg_status solve_batched_graph(mg_ctx *const *ctxs, const double *const *f
                        ((long long)outer_max * p->adapt_max - p->h_bm[1]) * p->n_cyc + p->n_epi);
     else
         count_launches(p->n_pro + (long long)outer_max * p->n_body + p->n_epi);
+    if (sr_flag) {
+        set_err("a bounded wait in the tensor-core convolution timed out (batched SR)");
+        return MG_ERR_TIMEOUT;
+    }
     if (worst == MG_ERR_NONFINITE) set_err("non-finite residual in a batched right-hand side");
     if (worst == MG_ERR_NOT_CONVERGED) set_err("a batched right-hand side did not converge");
     return worst;
@@ -2023,7 +2080,7 @@ mg_status mg_solve_batched(mg_ctx *const *ctxs, const double *const *f, double *
         return MG_ERR_INVALID_ARG;
     }
     if (B == 0) return MG_OK;
-    if (batch_eligible(ctxs, f, x, B, prolong)) return solve_batched_graph(ctxs, f, x, B, tol, infos);
+    if (batch_eligible(ctxs, f, x, B, prolong)) return solve_batched_graph(ctxs, f, x, B, tol, prolong, infos);
     mg_status worst = MG_OK;
     for (int k = 0; k < B; ++k) {
         mg_status s = mg_solve(ctxs[k], f[k], x[k], tol, prolong, infos ? &infos[k] : nullptr);

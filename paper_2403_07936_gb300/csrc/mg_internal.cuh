@@ -296,6 +296,8 @@ struct TileGrid {
     int zero;       // down: the input iterate is taken as zero
     int tile0;      // first block of this grid in the launch
     int rhs;        // right-hand side index
+    const void *extra = nullptr;     // up: fine-grid additive correction (the SR term) or null
+    const int *extra_off = nullptr;  // up: the correction is skipped while *extra_off != 0 (SR dropped)
 };
 struct BottomGrid {  // one block each
     void *x;
@@ -316,6 +318,7 @@ struct RhsDesc {  // outer kernels: blocks [blk0, blk0 + nblk) serve this right-
     int first;       // this step is its first residual evaluation
     int m_prev;      // V-cycles it ran in the previous outer step (0: the launch's common count)
     double h2;
+    int sr = 0;      // its finest transition adds the SR correction (batched SR solves)
 };
 struct BatchRed {
     double *partials;   // [blocks][kMaxSlots]

@@ -763,7 +763,8 @@ __global__ void __launch_bounds__(kThreads) k_up_batched(const TileGrid *__restr
     const TileGrid t = tab[find_grid(tab, ngrid)];
     if (active && !active[t.rhs]) return;
     const int lt = (int)blockIdx.x - t.tile0, tpr = t.n / kTX;
-    up_tile<T, NU, TY, NJ>((const T *)t.x, (T *)t.xout, (const T *)t.b, (const T *)t.aux, nullptr, t.n, taps,
+    const T *ex = (t.extra && !(t.extra_off && *t.extra_off)) ? (const T *)t.extra : nullptr;
+    up_tile<T, NU, TY, NJ>((const T *)t.x, (T *)t.xout, (const T *)t.b, (const T *)t.aux, ex, t.n, taps,
                            (lt / tpr) * TY, (lt % tpr) * kTX);
 }
 
@@ -1846,6 +1847,15 @@ __global__ void k_check_b(DevState *st, const RhsDesc *__restrict__ rd, int nrhs
             s.rel = 0.0;
         } else {
             const double rel = rn / fn;
+            // SR bookkeeping (batched SR solves; rd.sr = 0 otherwise): a step
+            // that used SR and did not reduce the relative residual by
+            // kSrMinReduction drops SR for the rest of this solve
+            if (!first && s.sr_step) {
+                s.sr_used += rd[r].m_prev > 0 ? rd[r].m_prev : m_prev;
+                if (!(rel <= kSrMinReduction * s.rel_prev)) s.fallback = 1;
+            }
+            s.sr_step = (rd[r].sr && !s.fallback) ? 1 : 0;
+            s.rel_prev = rel;
             s.rel = rel;
             if (rel > tol) {
                 if (rho > 0.0) {

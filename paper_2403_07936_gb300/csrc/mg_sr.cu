@@ -263,12 +263,15 @@ struct ConvArgs {
     int chunks;                 // row chunks per (group, column block) strip
     int rows_per_chunk;
     int *err;
+    int imgs = 1;               // images stacked along y, each with its own halo
 };
 
 // ---------------------------------------------------------------------------
 // k_conv_tc: persistent implicit-GEMM 3x3 convolution, 64 -> 64 channels per
-// group, on tcgen05.  Block b handles strip b / chunks = (group, column
-// block) and rows [chunk * rows_per_chunk, ...) of it.
+// group, on tcgen05.  Block b handles strip b / chunks = (image, group,
+// column block) and rows [chunk * rows_per_chunk, ...) of it.  A batch of
+// equal-size images is stacked along y, each padded image (H + 2 rows, or
+// 2H + 2 for the shuffle layer's output) after the previous one.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
@@ -290,7 +293,12 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
 
     const int NB = a.W / TM;
     const int strip = blockIdx.x / a.chunks, chunk = blockIdx.x - strip * a.chunks;
-    const int g = strip / NB, cb = strip - g * NB;
+    const int per_img = (MODE == MODE_SHUFFLE ? 4 : 1) * NB;
+    const int img = strip / per_img, gs = strip - img * per_img;
+    const int g = gs / NB, cb = gs - g * NB;
+    const int yin0 = img * (a.H + 2);  // first padded row of this image in the stacked input
+    const size_t in_img = (size_t)img * (a.H + 2) * (a.W + 2) * C;
+    const size_t out_img = MODE == MODE_SHUFFLE ? (size_t)img * (2 * a.H + 2) * (2 * a.W + 2) * C : in_img;
     const int y_a = chunk * a.rows_per_chunk;
     const int y_b = min(a.H, y_a + a.rows_per_chunk);
     if (y_a >= y_b) return;  // uniform across the block, before any barrier or TMEM use
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 if (*abort_flag) break;
                 mbar_expect_tx(&full[slot], ROWBYTES);
                 for (int q = 0; q < 8; ++q)
-                    tma_load_3d(rows + slot * ROWSLOT + q * PLANE, &tm_in, &full[slot], 8 * q, cb * TM, y_a + i);
+                    tma_load_3d(rows + slot * ROWSLOT + q * PLANE, &tm_in, &full[slot], 8 * q, cb * TM, yin0 + y_a + i);
                 issued = i + 1;
             }
             if (*abort_flag) {
@@ -406,7 +414,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             const int y = y_a + t;
             if (MODE == MODE_RESID) {
                 const uint4 *sp = reinterpret_cast<const uint4 *>(
-                    a.skip + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C + half * 32);
+                    a.skip + in_img + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C + half * 32);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const uint4 q = sp[i];
@@ -437,7 +445,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
             }
             if (MODE == MODE_SHUFFLE) {
-                store_half_px(a.out, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), half, outv, false);
+                store_half_px(a.out + out_img, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), half, outv, false);
             } else {
                 // stage t & 1 was last read by the TMA store of tile t - 2
                 if (leader) bulk_wait_read1();
@@ -446,14 +454,14 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 uint4 *st = reinterpret_cast<uint4 *>(stage + (t & 1) * STAGE + j * 128);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) st[(half * 4 + i) ^ (j & 7)] = outv[i];
-                if (x == 0 || x == a.W - 1) store_half_px(a.out, a.H, a.W, y, x, half, outv, true);
+                if (x == 0 || x == a.W - 1) store_half_px(a.out + out_img, a.H, a.W, y, x, half, outv, true);
                 fence_proxy_async();
                 epi_bar(2, 32 * EPI_WARPS);
                 if (leader) {
                     const unsigned char *src = stage + (t & 1) * STAGE;
-                    tma_store_3d(&tm_out, src, 0, cb * TM + 1, y + 1);
-                    if (y == 0) tma_store_3d(&tm_out, src, 0, cb * TM + 1, a.H + 1);
-                    if (y == a.H - 1) tma_store_3d(&tm_out, src, 0, cb * TM + 1, 0);
+                    tma_store_3d(&tm_out, src, 0, cb * TM + 1, yin0 + y + 1);
+                    if (y == 0) tma_store_3d(&tm_out, src, 0, cb * TM + 1, yin0 + a.H + 1);
+                    if (y == a.H - 1) tma_store_3d(&tm_out, src, 0, cb * TM + 1, yin0);
                     bulk_commit();
                 }
             }
@@ -583,6 +591,107 @@ __global__ void __launch_bounds__(OUT_T * OUT_T) k_conv_out(const __nv_bfloat16 
     fine_out[(size_t)(y0 + ty) * nf + x0 + tx] = (*s_ptr) * (acc + w[9 * C]);
 }
 
+// Batched forms for a stack of equal-size images (image = blockIdx.y, or
+// blockIdx.z for k_conv_out_b): the same per-pixel arithmetic as k_absmax,
+// k_conv_in and k_conv_out, with each image's coarse error read through a
+// pointer table and its own scale s[image].
+__global__ void __launch_bounds__(1024) k_absmax_b(const float *const *__restrict__ ecs, int nc,
+                                                   float *__restrict__ s_out) {
+    __shared__ float sh[32];
+    const float *ec = ecs[blockIdx.x];
+    const size_t N = (size_t)nc * nc;
+    float m = 0.f;
+    for (size_t p = threadIdx.x; p < N; p += blockDim.x) m = fmaxf(m, fabsf(ec[p]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bm = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) bm = fmaxf(bm, sh[w]);
+        s_out[blockIdx.x] = bm > 0.f ? bm : 1.f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_conv_in_b(const float *const *__restrict__ ecs, int nc,
+                                                   const float *__restrict__ s_all,
+                                                   const float *__restrict__ wpack, __nv_bfloat16 *__restrict__ out) {
+    __shared__ float w[C * 9 + 2 * C];
+    for (int i = threadIdx.x; i < C * 11; i += blockDim.x) w[i] = wpack[i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nc * nc) return;
+    const float *ec = ecs[blockIdx.y];
+    __nv_bfloat16 *o = out + (size_t)blockIdx.y * (nc + 2) * (nc + 2) * C;
+    const int y = p / nc, x = p - y * nc;
+    const float s = s_all[blockIdx.y];
+    float q[9];
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+            q[ky * 3 + kx] = ec[(size_t)((y + ky - 1 + nc) & (nc - 1)) * nc + ((x + kx - 1 + nc) & (nc - 1))] / s;
+    uint4 outv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = i * 8 + 2 * k + h;
+                float acc = w[C * 9 + c];
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc = fmaf(w[c * 9 + t], q[t], acc);
+                v[h] = acc > 0.f ? acc : w[C * 10 + c] * acc;
+            }
+            const __nv_bfloat162 bb = __floats2bfloat162_rn(v[0], v[1]);
+            w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
+        }
+        outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+    store_px(o, nc, nc, y, x, outv);
+}
+
+__global__ void __launch_bounds__(OUT_T * OUT_T) k_conv_out_b(const __nv_bfloat16 *__restrict__ u_all, int nf,
+                                                              const float *__restrict__ wpack,
+                                                              const float *__restrict__ s_all,
+                                                              float *__restrict__ out_all) {
+    __shared__ uint4 tile[(OUT_T + 2) * (OUT_T + 2) * 8];
+    __shared__ float w[9 * C + 1];
+    const __nv_bfloat16 *u = u_all + (size_t)blockIdx.z * (nf + 2) * (nf + 2) * C;
+    float *fine_out = out_all + (size_t)blockIdx.z * nf * nf;
+    for (int i = threadIdx.x; i < 9 * C + 1; i += blockDim.x) w[i] = wpack[i];
+    const int y0 = blockIdx.y * OUT_T, x0 = blockIdx.x * OUT_T;
+    for (int i = threadIdx.x; i < (OUT_T + 2) * (OUT_T + 2) * 8; i += blockDim.x) {
+        const int px = i >> 3, part = i & 7;
+        const int ry = px / (OUT_T + 2), rx = px - ry * (OUT_T + 2);
+        tile[i] = reinterpret_cast<const uint4 *>(u + ((size_t)(y0 + ry) * (nf + 2) + (x0 + rx)) * C)[part];
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / OUT_T, tx = threadIdx.x - ty * OUT_T;
+    float acc = 0.f;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            const uint4 *pp = tile + ((ty + ky) * (OUT_T + 2) + (tx + kx)) * 8;
+            const float *wt = w + (ky * 3 + kx) * C;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint4 q = pp[i];
+                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
+                    acc = fmaf(wt[i * 8 + 2 * k], f.x, acc);
+                    acc = fmaf(wt[i * 8 + 2 * k + 1], f.y, acc);
+                }
+            }
+        }
+    fine_out[(size_t)(y0 + ty) * nf + x0 + tx] = s_all[blockIdx.z] * (acc + w[9 * C]);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -688,9 +797,21 @@ cudaError_t launch_conv(const CUtensorMap &tm_in, const CUtensorMap &tm_w, const
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int strips = groups * (a.W / TM);
+    const int strips = a.imgs * groups * (a.W / TM);
     int chunks = sms / strips;
     if (chunks < 1) chunks = 1;
+    if (a.imgs > 1) {
+        // many strips: the row split with the fewest waves x (rows + 2 halo rows) per block
+        long long best = -1;
+        for (int c = 1; c <= a.H; ++c) {
+            const long long waves = ((long long)strips * c + sms - 1) / sms;
+            const long long cost = waves * ((a.H + c - 1) / c + 2);
+            if (best < 0 || cost < best) {
+                best = cost;
+                chunks = c;
+            }
+        }
+    }
     if (chunks > a.H) chunks = a.H;
     a.rows_per_chunk = (a.H + chunks - 1) / chunks;
     a.chunks = chunks;
@@ -840,6 +961,9 @@ mg_status sr_load(SrState *st, const void *blob, size_t bytes, char *err, size_t
     }
     st->n_feat = nf;
     st->n_blocks = nb;
+    uint64_t hsh = 1469598103934665603ull;
+    for (size_t i = 0; i < bytes; ++i) hsh = (hsh ^ ((const unsigned char *)blob)[i]) * 1099511628211ull;
+    st->hash = hsh;
     st->loaded = true;
     return MG_OK;
 }
@@ -995,6 +1119,87 @@ mg_status sr_layer(SrState *st, int layer, int nc, const void *in, const void *s
     if (flag) {
         snprintf(err, errlen, "sr_layer: a bounded wait in the tensor-core kernel timed out");
         return MG_ERR_TIMEOUT;
+    }
+    return MG_OK;
+}
+
+void sr_batch_free(SrBatch *b) {
+    for (int i = 0; i < 3; ++i) cudaFree(b->act[i]);
+    cudaFree(b->fine_act);
+    cudaFree(b->fine_out);
+    cudaFree(b->s);
+    cudaFree(b->ecs);
+    *b = SrBatch();
+}
+
+mg_status sr_batch_prepare(SrBatch *b, int imgs, int nc, const float *const *ecs, char *err, size_t errlen) {
+    sr_batch_free(b);
+    if (imgs < 1 || nc < TM || nc % TM) {
+        snprintf(err, errlen, "batched SR: %d images of %d^2 (a multiple of %d) not supported", imgs, nc, TM);
+        return MG_ERR_INVALID_ARG;
+    }
+    const size_t coarse = (size_t)imgs * (nc + 2) * (nc + 2) * C * 2;
+    const size_t fine = (size_t)imgs * (2 * nc + 2) * (2 * nc + 2) * C * 2;
+    cudaError_t e = prepare_conv();
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&b->act[i], coarse);
+    if (e == cudaSuccess) e = cudaMalloc(&b->fine_act, fine);
+    if (e == cudaSuccess) e = cudaMalloc(&b->fine_out, sizeof(float) * imgs * 4 * (size_t)nc * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&b->s, sizeof(float) * imgs);
+    if (e == cudaSuccess) e = cudaMalloc(&b->ecs, sizeof(float *) * imgs);
+    if (e == cudaSuccess) e = cudaMemcpy(b->ecs, ecs, sizeof(float *) * imgs, cudaMemcpyHostToDevice);
+    const int Hs = imgs * (nc + 2) - 2;  // the stack as one padded grid of Hs + 2 rows
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        if (!make_act_map(&b->tm_act[i], b->act[i], Hs, nc) || !make_out_map(&b->tm_out[i], b->act[i], Hs, nc))
+            e = cudaErrorInvalidValue;
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "batched SR buffers (%d x %d^2): %s", imgs, nc, cudaGetErrorString(e));
+        sr_batch_free(b);
+        return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+    }
+    b->imgs = imgs;
+    b->nc = nc;
+    return MG_OK;
+}
+
+mg_status sr_batch_correction(SrBatch *b, const SrState *st, cudaStream_t s, char *err, size_t errlen) {
+    if (!st->loaded || !b->imgs) {
+        snprintf(err, errlen, "batched SR: no weights or no prepared batch");
+        return MG_ERR_INVALID_ARG;
+    }
+    const int nc = b->nc, imgs = b->imgs, nb = st->n_blocks;
+    k_absmax_b<<<imgs, 1024, 0, s>>>(b->ecs, nc, b->s);
+    count_launches(1);
+    k_conv_in_b<<<dim3((unsigned)(((size_t)nc * nc + 255) / 256), imgs), 256, 0, s>>>(b->ecs, nc, b->s, st->w_in,
+                                                                                      (__nv_bfloat16 *)b->act[0]);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    int cur = 0;
+    for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+        const int nxt = (cur + 1) % 3, tmp = (cur + 2) % 3;
+        ConvArgs a1 = {nullptr, (__nv_bfloat16 *)b->act[tmp], st->bias_tc + (size_t)(2 * k) * C,
+                       st->prelu_blk + (size_t)k * C, nc, nc, 2 * k, 0, 0, st->err, imgs};
+        e = launch_conv<MODE_PRELU>(b->tm_act[cur], st->tm_w, b->tm_out[tmp], a1, 1, s);
+        if (e != cudaSuccess) break;
+        ConvArgs a2 = {(const __nv_bfloat16 *)b->act[cur], (__nv_bfloat16 *)b->act[nxt],
+                       st->bias_tc + (size_t)(2 * k + 1) * C, nullptr, nc, nc, 2 * k + 1, 0, 0, st->err, imgs};
+        e = launch_conv<MODE_RESID>(b->tm_act[tmp], st->tm_w, b->tm_out[nxt], a2, 1, s);
+        cur = nxt;
+    }
+    if (e == cudaSuccess) {
+        ConvArgs au = {nullptr, (__nv_bfloat16 *)b->fine_act, st->bias_tc + (size_t)(2 * nb) * C, st->prelu_up,
+                       nc, nc, 2 * nb, 0, 0, st->err, imgs};
+        e = launch_conv<MODE_SHUFFLE>(b->tm_act[cur], st->tm_w, b->tm_out[cur] /* unused */, au, 4, s);
+    }
+    if (e == cudaSuccess) {
+        const int nf = 2 * nc;
+        k_conv_out_b<<<dim3(nf / OUT_T, nf / OUT_T, imgs), OUT_T * OUT_T, 0, s>>>(
+            (const __nv_bfloat16 *)b->fine_act, nf, st->w_out, b->s, b->fine_out);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "batched SR generator launch: %s", cudaGetErrorString(e));
+        return MG_ERR_CUDA;
     }
     return MG_OK;
 }

@@ -25,11 +25,13 @@
 namespace mg {
 
 constexpr int kSrFeat = 64;
+constexpr int kSrMinCoarse = 128;  // coarse grids the generator takes: multiples of 128
 
 struct SrState {
     bool loaded = false;
     bool view = false;  // shares another state's weights and scratch scalars (sr_view)
     int n_feat = 0, n_blocks = 0;
+    uint64_t hash = 0;  // FNV-1a of the loaded blob (equal weights in a batch)
     // weights (device): tensor-core layers packed bf16 [layer][tap][co][ci],
     // layers = 2 * n_blocks + 4 (the 4 pixel-shuffle groups of conv 64->256)
     void *w_tc = nullptr;
@@ -51,6 +53,29 @@ struct SrState {
     CUtensorMap tm_out[3];  // the same buffers as destinations of output tiles
     CUtensorMap tm_w;
 };
+
+// SR generator buffers for a batch of `imgs` equal-size coarse errors (the
+// finest transitions of several right-hand sides of one size): activations of
+// all images stacked along y, each padded image after the previous one, so a
+// single launch per layer serves the whole batch.  Weights come from an
+// SrState at run time.
+struct SrBatch {
+    int imgs = 0, nc = 0;
+    void *act[3] = {nullptr, nullptr, nullptr};
+    void *fine_act = nullptr;
+    float *fine_out = nullptr;  // [imgs][2nc][2nc]: s_i G(e_i / s_i)
+    float *s = nullptr;         // [imgs]
+    const float **ecs = nullptr;  // [imgs] device pointers to the coarse errors (device table)
+    CUtensorMap tm_act[3];
+    CUtensorMap tm_out[3];
+};
+// Allocate for imgs coarse errors of nc x nc at the device addresses ecs[]
+// (host array of device pointers; copied).  Outside any stream capture.
+mg_status sr_batch_prepare(SrBatch *b, int imgs, int nc, const float *const *ecs, char *err, size_t errlen);
+// b->fine_out[i] = s_i G(e_i / s_i), s_i = max|e_i|, with st's weights
+// (asynchronous on stream; capturable).
+mg_status sr_batch_correction(SrBatch *b, const SrState *st, cudaStream_t stream, char *err, size_t errlen);
+void sr_batch_free(SrBatch *b);
 
 // Parse and copy a weight blob (layout in mg.h).  Errors go to err.
 mg_status sr_load(SrState *st, const void *blob, size_t bytes, char *err, size_t errlen);

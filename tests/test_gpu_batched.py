@@ -6,6 +6,8 @@ rounding: the bound is the spec one, |x_batch - x_alone|_inf <=
 1e-9 |x_alone|_inf, with each result also checked against the exact FFT
 solution and for its own relative residual.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -113,3 +115,74 @@ def test_batch_of_the_full_mixed_size_workload(mg):
         got = xs[k].cpu().numpy()
         assert np.abs(got - xe).max() <= 1e-9 * np.abs(xe).max(), (k, sizes[k])
         assert abs(got.mean()) <= 1e-12 * np.abs(got).max()
+
+
+TRAINED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2403_07936_gb300",
+                       "weights", "sr_generator.mgsrw")
+
+
+@pytest.mark.parametrize("graphs", [True, False], ids=["single-graph", "single-hostloop"])
+def test_sr_batch_matches_single_sr_solves_and_exact(mg, graphs):
+    """The SR prolongation inside the batched graph (Algorithm 5 inside
+    Algorithm 6 for every right-hand side): members of all three sizes of the
+    batched workload (reduced counts) and one 128^2 member, whose 64^2 coarse
+    grid the generator does not take, so it stays cubic.  Each member equals
+    its own single SR solve (same V-cycle and SR-cycle counts, solution within
+    1e-9; the generator kernels are the same, the FP64 sums use another block
+    split) and the exact FFT solution to 1e-9."""
+    blob = open(TRAINED, "rb").read()
+    sizes = [256, 512, 256, 1024, 512, 256, 1024, 128]
+    fs, fts = _case(sizes, 500)
+    ctxs = []
+    for n in sizes:
+        c = mg.Context(_levels(n), n)
+        c.load_weights(blob)
+        c.set_options(inner_cycles=2)
+        ctxs.append(c)
+    xs = [torch.zeros_like(ft) for ft in fts]
+    infos = mg.solve_batched(ctxs, fts, xs, tol=1e-10, prolong="sr")
+    for n, f, ft, x, ctx, info in zip(sizes, fs, fts, xs, ctxs, infos):
+        assert info["rel_residual"] <= 1e-10
+        got = x.cpu().numpy()
+        xe = omg.exact_solve_fft(f - f.mean())
+        assert np.abs(got - xe).max() <= 1e-9 * np.abs(xe).max(), n
+        if n == 128:
+            assert info["sr_cycles"] == 0 and info["prolong_used"] == 0
+            continue
+        assert info["prolong_used"] == 1 and info["sr_cycles"] > 0
+        ctx.set_graph_execution(graphs)
+        xa = torch.zeros_like(ft)
+        ia = ctx.solve(ft, xa, tol=1e-10, prolong="sr")
+        assert (ia["vcycles"], ia["sr_cycles"], ia["sr_fallback"]) == \
+            (info["vcycles"], info["sr_cycles"], info["sr_fallback"]), (n, ia, info)
+        alone = xa.cpu().numpy()
+        assert np.abs(got - alone).max() <= 1e-9 * np.abs(alone).max()
+
+
+def test_sr_batch_falls_back_per_member(mg):
+    """A generator whose output is scaled x100 makes the SR correction useless:
+    every member drops SR after its first outer step (two SR V-cycles) and
+    still converges to the exact solution; the cubic members are unaffected."""
+    from paper_2403_07936_gb300 import sr
+    w = sr.unpack_weights(open(TRAINED, "rb").read())
+    w["out.w"] = w["out.w"] * 100.0
+    w["out.b"] = w["out.b"] * 100.0
+    blob = sr.pack_weights(w)
+    sizes = [256, 512, 128]
+    fs, fts = _case(sizes, 600)
+    ctxs = []
+    for n in sizes:
+        c = mg.Context(_levels(n), n)
+        c.load_weights(blob)
+        c.set_options(inner_cycles=2)
+        ctxs.append(c)
+    xs = [torch.zeros_like(ft) for ft in fts]
+    infos = mg.solve_batched(ctxs, fts, xs, tol=1e-10, prolong="sr")
+    for n, f, x, info in zip(sizes, fs, xs, infos):
+        assert info["rel_residual"] <= 1e-10
+        xe = omg.exact_solve_fft(f - f.mean())
+        assert np.abs(x.cpu().numpy() - xe).max() <= 1e-9 * np.abs(xe).max()
+        if n == 128:
+            assert info["sr_fallback"] == 0 and info["sr_cycles"] == 0
+        else:
+            assert info["sr_fallback"] == 1 and info["sr_cycles"] == 2
