@@ -441,6 +441,23 @@ mg_status mg_op_sr_generator(mg_ctx *ctx, const float *ec, int nc, float *out);
  * stream. */
 mg_status mg_op_sr_layer(mg_ctx *ctx, int layer, int nc, const void *in, const void *skip, float *s, void *out);
 
+/* The windowed SR prolongation of Sec. 3.1 and Fig. 2 (Appendix A,
+ * Algorithms 1-5) with the context's loaded generator: the coarse field ec
+ * (nc x nc floats, device) is normalised by the symmetric logarithm
+ * (Algorithm 3: q = sgn(p) (log10|p| - log10 p_min) / (log10 p_max -
+ * log10 p_min), magnitudes clamped to [p_min, p_max], 0 kept), cut into
+ * 6 x 6 windows whose origins step by 2 (window (a, b) covers rows 2a - 2 ..
+ * 2a + 3 and columns 2b - 2 .. 2b + 3, wrapped around the periodic grid),
+ * each window goes through the generator alone with zero padding, the
+ * central 2 x 2 coarse cells of each (4 x 4 fine points) are kept and
+ * stitched, and each kept value g is mapped back (Algorithm 4: sgn(g)
+ * 10^(log10 p_min + |g| (log10 p_max - log10 p_min))).  out: 2nc x 2nc
+ * floats (device), the prolongation itself (Algorithm 5 has no spline term).
+ * nc a power of two >= 32; 0 < p_min < p_max (the paper's interval is
+ * [1e-10, 1e-3]).  MG_ERR_NO_WEIGHTS without weights; synchronous on the
+ * context's stream. */
+mg_status mg_op_sr_windowed(mg_ctx *ctx, const float *ec, int nc, double p_min, double p_max, float *out);
+
 /* Outer residual of FP64 data: s = b - (4x - sum nbrs) with b = h^2 (f - mu)
  * formed in FP64 (so s = h^2 r), written as float to s32 when s32 != NULL;
  * out[0] = sum s^2, out[1] = sum (f - mu)^2 (out: 2 doubles, device).  The

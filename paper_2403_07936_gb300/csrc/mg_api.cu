@@ -157,6 +157,7 @@ struct mg_ctx {
     double *host_out = nullptr;  // pinned mirror of red_out
     double *f_stage = nullptr, *x_stage = nullptr;
     SrState sr;
+    SrWindows srw;  // windowed SR mosaic buffers (mg_op_sr_windowed)
     // views of sr's generator for the stages of the two-level SR prolongation
     // (stage j refines level j + 1 to level j)
     static constexpr int kSrStages = 8;
@@ -1598,6 +1599,7 @@ void mg_destroy(mg_ctx *c) {
     cudaFree(c->x_stage);
     for (SrState &v : c->sr_stage) sr_free(&v);
     sr_free(&c->sr);
+    sr_windows_free(&c->srw);
     probe_free(c);
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -2448,6 +2450,33 @@ mg_status mg_op_sr_layer(mg_ctx *c, int layer, int nc, const void *in, const voi
     }
     MG_CUDA(cudaSetDevice(c->device));
     return sr_layer(&c->sr, layer, nc, in, skip, s, out, c->stream, g_err, sizeof g_err);
+}
+
+mg_status mg_op_sr_windowed(mg_ctx *c, const float *ec, int nc, double p_min, double p_max, float *out) {
+    if (!c || !ec || !out) {
+        set_err("null pointer");
+        return MG_ERR_INVALID_ARG;
+    }
+    if (!(p_min > 0.0) || !(p_max > p_min) || !std::isfinite(p_max)) {
+        set_err("normalisation interval [%g, %g] must satisfy 0 < p_min < p_max", p_min, p_max);
+        return MG_ERR_INVALID_ARG;
+    }
+    if (!c->sr.loaded) {
+        set_err("no generator weights loaded");
+        return MG_ERR_NO_WEIGHTS;
+    }
+    MG_CUDA(cudaSetDevice(c->device));
+    MG_TRY(sr_windows_prepare(&c->srw, nc, g_err, sizeof g_err));
+    MG_CUDA(cudaMemsetAsync(c->sr.err, 0, sizeof(int), c->stream));
+    MG_TRY(sr_windowed(&c->srw, &c->sr, ec, nc, p_min, p_max, out, c->stream, g_err, sizeof g_err));
+    int flag = 0;
+    MG_CUDA(cudaMemcpyAsync(&flag, c->sr.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+    if (flag) {
+        set_err("a bounded wait in the tensor-core convolution timed out");
+        return MG_ERR_TIMEOUT;
+    }
+    return MG_OK;
 }
 
 mg_status mg_op_outer_residual(int n, const double *f, const double *x, double mu, float *s32,

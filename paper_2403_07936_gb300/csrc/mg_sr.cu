@@ -264,6 +264,8 @@ struct ConvArgs {
     int rows_per_chunk;
     int *err;
     int imgs = 1;               // images stacked along y, each with its own halo
+    int mosaic = 0;             // > 0: pixels with y or x = mosaic - 1 (mod mosaic) are window
+                                // separators and their outputs are forced to zero
 };
 
 // ---------------------------------------------------------------------------
@@ -427,6 +429,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     }
                 }
             }
+            // a window separator of a mosaic stays zero (the windows' zero padding)
+            const bool sep = a.mosaic > 0 && ((y % a.mosaic) == a.mosaic - 1 || (x % a.mosaic) == a.mosaic - 1);
             uint4 outv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -439,6 +443,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                         v0 = v0 > 0.f ? v0 : s_prelu[cc] * v0;
                         v1 = v1 > 0.f ? v1 : s_prelu[cc + 1] * v1;
                     }
+                    if (sep) v0 = v1 = 0.f;
                     const __nv_bfloat162 bb = __floats2bfloat162_rn(v0, v1);
                     w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
                 }
@@ -690,6 +695,119 @@ __global__ void __launch_bounds__(OUT_T * OUT_T) k_conv_out_b(const __nv_bfloat1
             }
         }
     fine_out[(size_t)(y0 + ty) * nf + x0 + tx] = s_all[blockIdx.z] * (acc + w[9 * C]);
+}
+
+// ---------------------------------------------------------------------------
+// Windowed SR (Sec. 3.1, Fig. 2; Appendix A, Algorithms 1-5).  The coarse
+// field is normalised by the symmetric logarithm, cut into n_s x n_s = 6 x 6
+// windows whose origins step by 2 (window (a, b) covers coarse rows
+// 2a - 2 .. 2a + 3 and columns 2b - 2 .. 2b + 3, wrapped), each window is
+// super-resolved on its own with zero padding, the central 2 x 2 coarse
+// cells of each (4 x 4 fine points) are kept and stitched, and the result is
+// mapped back through the inverse normalisation.  The windows are laid out
+// as a mosaic: a 7 x 7 cell per window (6 x 6 values, one zero separator row
+// and column), kWinPerRow windows per mosaic row.  The mosaic is periodic and
+// ends in a separator, so its periodic halo and the separators give every
+// window exactly the zero padding it would have alone, as long as every
+// layer keeps the separators zero (ConvArgs::mosaic).
+// ---------------------------------------------------------------------------
+constexpr int kWinNs = 6, kWinCell = 7, kWinPerRow = 128;  // mosaic width 896, a multiple of TM
+
+__device__ __forceinline__ float symlog_f(float p, float pmin, float pmax, float lmin, float inv_span) {
+    if (p == 0.f) return 0.f;
+    const float m = fminf(fmaxf(fabsf(p), pmin), pmax);
+    return copysignf((log10f(m) - lmin) * inv_span, p);
+}
+
+// conv 1 -> 64 + PReLU of the normalised windows, one thread per mosaic pixel.
+__global__ void __launch_bounds__(256) k_win_in(const float *__restrict__ ec, int nc, float pmin, float pmax,
+                                                float lmin, float inv_span, const float *__restrict__ wpack,
+                                                __nv_bfloat16 *__restrict__ out, int Hm, int Wm) {
+    __shared__ float w[C * 9 + 2 * C];
+    for (int i = threadIdx.x; i < C * 11; i += blockDim.x) w[i] = wpack[i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Hm * Wm) return;
+    const int y = p / Wm, x = p - y * Wm;
+    const int r = y / kWinCell, i = y - r * kWinCell, k = x / kWinCell, j = x - k * kWinCell;
+    uint4 outv[8];
+    if (i < kWinNs && j < kWinNs) {
+        const int half = nc >> 1;
+        const int wi = r * kWinPerRow + k;
+        const int a = wi / half, b = wi - a * half;
+        float q[9];
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                const int li = i + ky - 1, lj = j + kx - 1;
+                float v = 0.f;
+                if (li >= 0 && li < kWinNs && lj >= 0 && lj < kWinNs)
+                    v = symlog_f(ec[(size_t)((2 * a - 2 + li) & (nc - 1)) * nc + ((2 * b - 2 + lj) & (nc - 1))], pmin,
+                                 pmax, lmin, inv_span);
+                q[ky * 3 + kx] = v;
+            }
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                float v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = ii * 8 + 2 * kk + h;
+                    float acc = w[C * 9 + c];
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) acc = fmaf(w[c * 9 + t], q[t], acc);
+                    v[h] = acc > 0.f ? acc : w[C * 10 + c] * acc;
+                }
+                const __nv_bfloat162 bb = __floats2bfloat162_rn(v[0], v[1]);
+                w4[kk] = *reinterpret_cast<const uint32_t *>(&bb);
+            }
+            outv[ii] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+    } else {
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) outv[ii] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    store_px(out, Hm, Wm, y, x, outv);
+}
+
+// conv 64 -> 1 at the kept 4 x 4 fine points of every window, then the
+// inverse normalisation: out[Y][X] (fine grid 2nc) for Y, X in window
+// (Y / 4, X / 4)'s kept block.  One thread per fine point, 16 per window.
+__global__ void __launch_bounds__(256) k_win_out(const __nv_bfloat16 *__restrict__ u, int Wmf,
+                                                 const float *__restrict__ wpack, int nc, float lmin, float span,
+                                                 float *__restrict__ out) {
+    const int half = nc >> 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= half * half * 16) return;
+    const int wi = t >> 4, o = t & 15, oy = o >> 2, ox = o & 3;
+    const int a = wi / half, b = wi - a * half;
+    const int r = wi / kWinPerRow, k = wi - r * kWinPerRow;
+    const int yf = 2 * kWinCell * r + 4 + oy, xf = 2 * kWinCell * k + 4 + ox;  // mosaic fine pixel
+    float acc = 0.f;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            const uint4 *pp = reinterpret_cast<const uint4 *>(u + ((size_t)(yf + ky) * (Wmf + 2) + (xf + kx)) * C);
+            const float *wt = wpack + (ky * 3 + kx) * C;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint4 q = pp[i];
+                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[kk]));
+                    acc = fmaf(wt[i * 8 + 2 * kk], f.x, acc);
+                    acc = fmaf(wt[i * 8 + 2 * kk + 1], f.y, acc);
+                }
+            }
+        }
+    const float g = acc + wpack[9 * C];
+    const float mag = exp10f(lmin + fabsf(g) * span);
+    out[(size_t)(4 * a + oy) * (2 * nc) + 4 * b + ox] = g > 0.f ? mag : (g < 0.f ? -mag : 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -1199,6 +1317,85 @@ mg_status sr_batch_correction(SrBatch *b, const SrState *st, cudaStream_t s, cha
     }
     if (e != cudaSuccess) {
         snprintf(err, errlen, "batched SR generator launch: %s", cudaGetErrorString(e));
+        return MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+void sr_windows_free(SrWindows *w) {
+    for (int i = 0; i < 3; ++i) cudaFree(w->act[i]);
+    cudaFree(w->fine_act);
+    *w = SrWindows();
+}
+
+static int win_rows(int nc) { return (nc / 2) * (nc / 2) / kWinPerRow * kWinCell; }
+
+mg_status sr_windows_prepare(SrWindows *w, int nc, char *err, size_t errlen) {
+    if (nc < 32 || (nc & (nc - 1))) {
+        snprintf(err, errlen, "windowed SR needs a power-of-two coarse grid of at least 32, got %d", nc);
+        return MG_ERR_INVALID_ARG;
+    }
+    if (w->nc == nc && w->act[0]) return MG_OK;
+    sr_windows_free(w);
+    const int Hm = win_rows(nc), Wm = kWinPerRow * kWinCell;
+    const size_t coarse = (size_t)(Hm + 2) * (Wm + 2) * C * 2;
+    const size_t fine = (size_t)(2 * Hm + 2) * (2 * Wm + 2) * C * 2;
+    cudaError_t e = prepare_conv();
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&w->act[i], coarse);
+    if (e == cudaSuccess) e = cudaMalloc(&w->fine_act, fine);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        if (!make_act_map(&w->tm_act[i], w->act[i], Hm, Wm) || !make_out_map(&w->tm_out[i], w->act[i], Hm, Wm))
+            e = cudaErrorInvalidValue;
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "windowed SR buffers for %d^2: %s", nc, cudaGetErrorString(e));
+        sr_windows_free(w);
+        return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+    }
+    w->nc = nc;
+    w->Hm = Hm;
+    w->Wm = Wm;
+    return MG_OK;
+}
+
+mg_status sr_windowed(SrWindows *w, const SrState *st, const float *ec, int nc, double p_min, double p_max,
+                      float *out, cudaStream_t s, char *err, size_t errlen) {
+    if (!st->loaded || w->nc != nc) {
+        snprintf(err, errlen, "windowed SR not prepared for a %d^2 coarse grid", nc);
+        return MG_ERR_INVALID_ARG;
+    }
+    const double lmin = log10(p_min), lmax = log10(p_max);
+    const int Hm = w->Hm, Wm = w->Wm, nb = st->n_blocks;
+    k_win_in<<<(unsigned)(((size_t)Hm * Wm + 255) / 256), 256, 0, s>>>(
+        ec, nc, (float)p_min, (float)p_max, (float)lmin, (float)(1.0 / (lmax - lmin)), st->w_in,
+        (__nv_bfloat16 *)w->act[0], Hm, Wm);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    int cur = 0;
+    for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+        const int nxt = (cur + 1) % 3, tmp = (cur + 2) % 3;
+        ConvArgs a1 = {nullptr, (__nv_bfloat16 *)w->act[tmp], st->bias_tc + (size_t)(2 * k) * C,
+                       st->prelu_blk + (size_t)k * C, Hm, Wm, 2 * k, 0, 0, st->err, 1, kWinCell};
+        e = launch_conv<MODE_PRELU>(w->tm_act[cur], st->tm_w, w->tm_out[tmp], a1, 1, s);
+        if (e != cudaSuccess) break;
+        ConvArgs a2 = {(const __nv_bfloat16 *)w->act[cur], (__nv_bfloat16 *)w->act[nxt],
+                       st->bias_tc + (size_t)(2 * k + 1) * C, nullptr, Hm, Wm, 2 * k + 1, 0, 0, st->err, 1, kWinCell};
+        e = launch_conv<MODE_RESID>(w->tm_act[tmp], st->tm_w, w->tm_out[nxt], a2, 1, s);
+        cur = nxt;
+    }
+    if (e == cudaSuccess) {
+        ConvArgs au = {nullptr, (__nv_bfloat16 *)w->fine_act, st->bias_tc + (size_t)(2 * nb) * C, st->prelu_up,
+                       Hm, Wm, 2 * nb, 0, 0, st->err, 1, kWinCell};
+        e = launch_conv<MODE_SHUFFLE>(w->tm_act[cur], st->tm_w, w->tm_out[cur] /* unused */, au, 4, s);
+    }
+    if (e == cudaSuccess) {
+        const size_t pts = (size_t)(nc / 2) * (nc / 2) * 16;
+        k_win_out<<<(unsigned)((pts + 255) / 256), 256, 0, s>>>((const __nv_bfloat16 *)w->fine_act, 2 * Wm,
+                                                               st->w_out, nc, (float)lmin, (float)(lmax - lmin), out);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "windowed SR launch: %s", cudaGetErrorString(e));
         return MG_ERR_CUDA;
     }
     return MG_OK;

@@ -77,6 +77,23 @@ mg_status sr_batch_prepare(SrBatch *b, int imgs, int nc, const float *const *ecs
 mg_status sr_batch_correction(SrBatch *b, const SrState *st, cudaStream_t stream, char *err, size_t errlen);
 void sr_batch_free(SrBatch *b);
 
+// Windowed SR (Sec. 3.1, Fig. 2; Algorithms 1-5): mosaic buffers for the
+// (nc/2)^2 windows of an nc x nc coarse field (see mg_sr.cu).
+struct SrWindows {
+    int nc = 0, Hm = 0, Wm = 0;  // coarse grid; mosaic rows and columns
+    void *act[3] = {nullptr, nullptr, nullptr};
+    void *fine_act = nullptr;
+    CUtensorMap tm_act[3];
+    CUtensorMap tm_out[3];
+};
+// Allocate for coarse grids of nc (a power of two >= 32); outside capture.
+mg_status sr_windows_prepare(SrWindows *w, int nc, char *err, size_t errlen);
+// out (2nc x 2nc, device) = the windowed SR prolongation of ec with st's
+// weights and the normalisation interval [p_min, p_max] (asynchronous).
+mg_status sr_windowed(SrWindows *w, const SrState *st, const float *ec, int nc, double p_min, double p_max,
+                      float *out, cudaStream_t stream, char *err, size_t errlen);
+void sr_windows_free(SrWindows *w);
+
 // Parse and copy a weight blob (layout in mg.h).  Errors go to err.
 mg_status sr_load(SrState *st, const void *blob, size_t bytes, char *err, size_t errlen);
 // Allocate the activation buffers and tensor maps for coarse grids of size nc

@@ -88,6 +88,7 @@ SIGNATURES = {
     "mg_op_sr_conv": (_I, [_I, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mg_op_sr_generator": (_I, [_VP, _VP, _I, _VP]),
     "mg_op_sr_layer": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP]),
+    "mg_op_sr_windowed": (_I, [_VP, _VP, _I, _D, _D, _VP]),
     "mg_op_outer_residual": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP]),
     "mg_op_convert": (_I, [_I, _SZ, _VP, _VP, _VP]),
 }
@@ -433,6 +434,11 @@ def op_sr_generator(ctx: "Context", ec, out):
 def op_sr_layer(ctx: "Context", layer: int, nc: int, inp, out, s, skip=None):
     """One layer of the context's generator on caller buffers (see mg_op_sr_layer)."""
     _check(load().mg_op_sr_layer(ctx.handle, layer, nc, ptr(inp), ptr(skip), ptr(s), ptr(out)))
+
+
+def op_sr_windowed(ctx: "Context", ec, out, p_min: float = 1e-10, p_max: float = 1e-3):
+    """Windowed SR prolongation with symmetric-log normalisation (see mg_op_sr_windowed)."""
+    _check(load().mg_op_sr_windowed(ctx.handle, ptr(ec), ec.shape[-1], p_min, p_max, ptr(out)))
 
 
 def op_outer_residual(f, x, mu: float, s32, out, stream=None):
