@@ -45,6 +45,12 @@ PROBE_NAMES = {1: "k_down<float,2> (finest: 2 RB-GS sweeps + residual + FW)",
                3: "k_outer_residual (binary64 operands, exact integer stencil sum, one rounding to float, norms)",
                4: "k_update (FP64 x += e)",
                5: "coarse levels (1024^2 down to the bottom kernel and back, one span per V-cycle)"}
+# FP32 finest-level stencils (V(2,2)): the per-point algorithmic bytes of the
+# unfused steps a launch performs, 4 B x (2 sweeps x 3 words + 2.25 words of
+# residual + restriction, or of prolongation + correction) = 33 B, against the
+# fused kernel's compulsory 13 B the library's probe credits
+SURVEY_BYTES_PER_POINT = 33
+SURVEY_BYTES_RATIO = {1: 33 / 13, 2: 33 / 13}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -120,9 +126,24 @@ def kernel_roofline(kind, n_l, ms, nbytes, peak, peak_src, sms=None, sm_mhz=None
                      "peak": None, "frac": None,
                      "note": "a span of 9 launches per V-cycle on grids of 1024^2 and less; its bytes fit L2"})
         return base
-    ach = (nbytes / n_l) / (us * 1e-6) / 1e9
-    base.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                 "peak_source": f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if peak_src == 'measured' else 'recipe fallback'})"})
+    ach_c = (nbytes / n_l) / (us * 1e-6) / 1e9
+    psrc = f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if peak_src == 'measured' else 'recipe fallback'})"
+    if kind in SURVEY_BYTES_RATIO:
+        # the per-point count of the unfused steps (each sweep reads x and b and
+        # writes x; prolongation + correction and residual + restriction 2.25
+        # words each), over the same points as the fused kernel's compulsory count
+        sb = nbytes / n_l * SURVEY_BYTES_RATIO[kind]
+        ach = sb / (us * 1e-6) / 1e9
+        base.update({"bound": "hbm", "algorithmic_bytes_per_launch": sb,
+                     "bytes_per_point": SURVEY_BYTES_PER_POINT,
+                     "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": psrc,
+                     "compulsory": {"bytes_per_launch": nbytes / n_l, "bytes_per_point": 13, "achieved": ach_c,
+                                    "frac": ach_c / peak,
+                                    "note": "the fused kernel's own minimum traffic (read x, b and 1/4 of the "
+                                            "coarse grid, write x): the stricter figure"}})
+        return base
+    base.update({"bound": "hbm", "achieved": ach_c, "peak": peak, "unit": "GB/s", "frac": ach_c / peak,
+                 "peak_source": psrc})
     return base
 
 
@@ -301,6 +322,13 @@ def cpu_all_cores(per_process_bytes=1 << 30):
                       f"sum over processes of 1 / ({ORACLE_CYCLES_PER_SOLVE} x cycle time)"}
 
 
+def bench_config(world):
+    """The workload both arms time (the same dict in both JSON lines)."""
+    return {"workload": WORKLOAD, "grid": N, "levels": LEVELS, "rhs_per_step": 1, "prolongation": "cubic",
+            "l2": "GPU arm: flushed between steps (512 MB write), x reset to 0; CPU arm: n/a",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -321,7 +349,7 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_cycle * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "config": bench_config(args.gpus),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -572,8 +600,10 @@ def serve_leg(mg, dev, stream, args, rank):
         if a == 0 and q == 0:
             break
     results = []
-    warm, dur = args.serve_warmup, args.serve_seconds
+    warm = args.serve_warmup
     for lam in args.serve_rates:
+        # long enough for serve_min_completions requests (p99 from >= 2000 samples)
+        dur = max(args.serve_seconds, args.serve_min_completions / lam)
         t_arr = np.cumsum(rng.exponential(1.0 / lam, size=int(lam * (warm + dur) * 1.5) + 16))
         t_arr = t_arr[t_arr < warm + dur]
         req_n = rng.integers(0, len(SERVE_SIZES), size=t_arr.size)
@@ -621,7 +651,8 @@ def serve_leg(mg, dev, stream, args, rank):
                 pending.pop(r["request_id"], None)
         lat_ms = np.array(lat) * 1e3
         results.append({
-            "lambda_req_s": lam, "offered": int(np.sum((t_arr >= warm))), "completed": len(lat),
+            "lambda_req_s": lam, "window_s": dur, "offered": int(np.sum((t_arr >= warm))), "completed": len(lat),
+            "p99_samples": len(lat),
             "solves_per_s": done_in_window / dur,
             "p50_ms": float(np.percentile(lat_ms, 50)) if lat else None,
             "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None,
@@ -633,7 +664,8 @@ def serve_leg(mg, dev, stream, args, rank):
     return {"workload": f"Poisson arrivals; N uniform in {list(SERVE_SIZES)}; {SERVE_STREAMS} streams "
                         f"(stream s has N = sizes[s mod 5]); each request a 1% perturbation of its stream's "
                         f"previous source, warm-started from the stream's previous solution; memory budget "
-                        f"160 GiB; tol 1e-10; {dur:g} s measured per rate after {warm:g} s warm-up",
+                        f"160 GiB; tol 1e-10; per rate max({args.serve_seconds:g} s, "
+                        f"{args.serve_min_completions} / rate) measured after {warm:g} s warm-up",
             "rates": results}
 
 
@@ -662,6 +694,7 @@ def main():
     ap.add_argument("--skip-smoothing", action="store_true")
     ap.add_argument("--skip-two-level", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-min-completions", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=float, default=0.5)
     ap.add_argument("--serve-rates", type=lambda v: [float(t) for t in v.split(",")],
                     default=[50.0, 100.0, 200.0, 500.0, 1000.0, 2000.0])
@@ -919,10 +952,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (V-cycles) + f64 (outer residual, update, norms)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": N, "levels": LEVELS, "rhs_per_step": 1,
-                       "precision": "mixed", "prolongation": "cubic",
-                       "l2": "flushed between steps (512 MB write), x reset to 0",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": bench_config(world),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": value_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * bytes_grid,

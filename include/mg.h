@@ -79,7 +79,10 @@ typedef struct {
 mg_status mg_setup(int levels, int N, mg_ctx **out);
 
 /* Options (defaults: MG_PREC_MIXED, nu_pre = nu_post = 2, max_cycles = 100,
- * inner_cycles = 2, stream 0).  0 <= nu <= 4.  max_cycles bounds the V-cycles
+ * inner_cycles = 2, stream 0).  nu_pre / nu_post are the relaxation counts
+ * before and after the coarse correction (Algorithm 6's relaxation step; the
+ * smoothing count N_smooth of Sec. 4.2 and Table 1); max_cycles is the
+ * iteration cap (Table 1's N_iter).  0 <= nu <= 4.  max_cycles bounds the V-cycles
  * of one mg_solve.  `cuda_stream` is a cudaStream_t (NULL = legacy stream);
  * all work of this context is ordered on it. */
 mg_status mg_set_options(mg_ctx *ctx, mg_precision precision, int nu_pre, int nu_post,
@@ -322,9 +325,11 @@ void mg_trainer_destroy(mg_trainer *tr);
 
 /* Free a context: its level hierarchy, graphs, staging buffers, generator
  * weights and streams it created (not a caller's stream); waits for its work
- * first.  NULL is ignored. */
+ * first.  NULL is ignored.  (Resource management of this library; the paper
+ * has no counterpart.) */
 void mg_destroy(mg_ctx *ctx);
-/* Name of a status code ("MG_OK", ...); a static string, never NULL. */
+/* Name of a status code ("MG_OK", ...); a static string, never NULL.  (Error
+ * reporting of this library; the paper has no counterpart.) */
 const char *mg_status_string(mg_status status);
 /* Text of the last error raised on the calling thread (thread-local; empty
  * when none); valid until the thread's next failing call. */

@@ -18,8 +18,13 @@ def test_roofline_is_algorithmic_bytes_over_launch_time():
     nbytes = 7 * 13 * 2048 * 2048
     r = bench.kernel_roofline(2, 7, 0.2625, nbytes, 6776.6, "measured", 152, 2070.0)
     assert r["avg_launch_us"] == pytest.approx(37.5)
-    assert r["achieved"] == pytest.approx(13 * 2048 * 2048 / 37.5e-6 / 1e9)
+    # the unfused steps' 33 B per point (two sweeps of 3 words, prolongation +
+    # correction 2.25 words); the fused kernel's compulsory 13 B beside it
+    assert r["achieved"] == pytest.approx(33 * 2048 * 2048 / 37.5e-6 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6776.6)
+    assert r["compulsory"]["achieved"] == pytest.approx(13 * 2048 * 2048 / 37.5e-6 / 1e9)
+    outer = bench.kernel_roofline(3, 4, 0.12, 4 * 20 * 2048 * 2048, 6776.6, "measured")
+    assert outer["achieved"] == pytest.approx(20 * 2048 * 2048 / 30e-6 / 1e9) and "compulsory" not in outer
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     cap = bench.read_capture(2)
     if cap is not None:  # the committed capture matches this source
