@@ -5,16 +5,16 @@
 // tcgen05 tensor cores (BF16 operands, FP32 accumulation in tensor memory):
 // for an output tile of 128 pixels of one row, D[pixel][co] = sum over the 9
 // taps (dy, dx) and 64 input channels of In[row y+dy][pixel+dx][ci] *
-// W[tap][co][ci].  A persistent block walks a vertical strip of tiles: the
-// three input rows a tile needs are TMA-loaded into a ring of six row slots
-// (three rows of prefetch), so each new output row costs one new input row.  A staged row is stored as
-// eight 8-channel planes of [pixel][8 channels] (no swizzle), so the x-shifted
-// tap operands are descriptors offset by 16 * dx bytes into the staged row;
-// the weights use the 128-byte swizzled K-major layout.
-// Thread 0 issues the TMA loads and the 36 MMAs per tile; the tile's
-// accumulator (one of two 64-column TMEM buffers) is drained by all eight
-// warps (lane quarter x column half) while the next tile's MMAs run, and the
-// bf16 results leave through a shared-memory stage and TMA stores.  Every wait on an mbarrier is bounded by a
+// W[tap][co][ci].  A persistent block walks a vertical strip of rows: each
+// input row is TMA-loaded once into a ring of six row slots and multiplied by
+// the three dy taps at once (N = 192), accumulating into the TMEM slots of
+// the three output rows it feeds (k_conv_tc below).  A staged row is stored
+// as eight 8-channel planes of [pixel][8 channels] (no swizzle), so the
+// x-shifted tap operands are descriptors offset by 16 * dx bytes into the
+// staged row; the weights use the 128-byte swizzled K-major layout.  One
+// warp issues the TMA loads, one thread the MMAs, and eight warps drain the
+// finished accumulators (lane quarter x column half), and the bf16 results
+// leave through a shared-memory stage and TMA stores.  Every wait on an mbarrier is bounded by a
 // wall-clock limit and reports MG_ERR_TIMEOUT through a device flag.
 // The 1 -> 64 and 64 -> 1 layers are too thin for tensor cores (K = 9 and
 // N = 1) and run on the CUDA cores.
@@ -41,19 +41,25 @@ constexpr int ROWBYTES = ROWPX * C * 2;
 constexpr int PLANE = 2176;
 constexpr int ROWSLOT = 8 * PLANE;    // 17 KiB slots, 1024-byte multiple
 static_assert(PLANE >= ROWPX * 16 && PLANE % 128 == 0, "plane pitch");
-constexpr int NSLOT = 6;              // ring of staged input rows (prefetch 3 rows ahead)
+constexpr int NSLOT = 4;              // ring of staged input rows (prefetch up to 4 rows ahead)
 constexpr int WBYTES = 9 * C * C * 2;  // one layer's weights, 72 KiB
 constexpr int TAPBYTES = C * C * 2;    // one tap: 64 rows (co) x 128 bytes (ci)
-constexpr int NBUF = 4;               // 64-column FP32 accumulators in TMEM
-constexpr int TMEM_COLS = NBUF * C;
+constexpr int DXBYTES = 3 * TAPBYTES;  // the three dy taps of one dx, 192 rows (dy, co) x 128 bytes
+constexpr int TSLOTS = 8;              // 64-column FP32 accumulators in TMEM (one per output row)
+constexpr int TMEM_COLS = TSLOTS * C;  // all 512 columns
 // warp roles: 0 = TMA producer, 1 = MMA issuer, 2..9 = epilogue (lane quarter
 // warp % 4, column half (warp - 2) / 4 of the 128 x 64 accumulator)
 constexpr int EPI_WARPS = 8;
 constexpr int CONV_THREADS = 32 * (2 + EPI_WARPS);
 constexpr int STAGE = TM * C * 2;     // one output tile, 128 px x 128 B (epilogue staging)
-constexpr int NBARS = 1 + 2 * NSLOT + 2 * NBUF + 1;  // weights, row full/empty, tmem full/empty, mma done
-constexpr size_t CONV_SMEM = 1024 + WBYTES + NSLOT * ROWSLOT + 2 * STAGE + 256 + 2 * C * sizeof(float);
-static_assert(NBARS * 8 + 16 <= 256, "barrier area");
+constexpr int SKIPBUF = 3;            // residual-input tiles in flight (rows o .. o + 2)
+// weights, row full / empty, accumulator full / empty, accumulators zeroed, MMAs done, skip tiles
+constexpr int NBARS = 1 + 2 * NSLOT + 2 * TSLOTS + 1 + 1 + SKIPBUF;
+constexpr int BAR_AREA = 512;
+constexpr size_t CONV_SMEM =
+    1024 + WBYTES + NSLOT * ROWSLOT + (2 + SKIPBUF) * STAGE + BAR_AREA + 2 * C * sizeof(float);
+static_assert(NBARS * 8 + 16 <= BAR_AREA, "barrier area");
+static_assert(CONV_SMEM <= 232448, "shared memory per block");
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 enum { MODE_PRELU = 0, MODE_RESID = 1, MODE_SHUFFLE = 2 };
@@ -79,19 +85,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
 // Wait for the phase with the given parity to complete; false after kWaitNs.
+// The clock is read only once the first try has failed.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(bar, parity)) return true;
         if (global_ns() - t0 > kWaitNs) return false;
     }
 }
@@ -102,17 +113,24 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
 }
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
-                                            int c1, int c2, int c3) {
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
         : "memory");
 }
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int c0, int c1, int c2) {
     asm volatile(
         "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
         ::"l"(map), "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void *src, int c0, int c1, int c2,
+                                             int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];"
+        ::"l"(map), "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -160,15 +178,19 @@ __device__ __forceinline__ uint64_t sdesc_planes(uint32_t saddr) {
     return d;                                   // layout type 0: no swizzle
 }
 // Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major,
-// M = 128, N = 64.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// M = 128, N = n (a multiple of 16 up to 256).
+__host__ __device__ constexpr uint32_t idesc_n(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+// D = A B + (ACC ? D : 0).
+template <uint32_t N, int ACC>
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "n"(idesc_n(N)), "n"(ACC)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -193,6 +215,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 lanes x 32 columns of zeros (the accumulator slot is reset for its next row).
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+        ::"r"(taddr), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // Barrier `id` over `count` threads (the epilogue warps) returning the AND of
 // every participant's predicate: a decision all of them take together.
 __device__ __forceinline__ bool epi_bar_and(bool pred, int id, int count) {
@@ -216,7 +249,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // Store one pixel's 64 bf16 channels (8 x 16 bytes) at (y, x) of a padded
 // H x W grid, and at every halo position that wraps onto it.
-__device__ __forceinline__ void store_px(__nv_bfloat16 *out, int H, int W, int y, int x, const uint4 *d) {
+// With halo_only, the interior position is skipped.
+__device__ __forceinline__ void store_px(__nv_bfloat16 *out, int H, int W, int y, int x, const uint4 *d,
+                                         bool halo_only = false) {
     const int rows[2] = {y + 1, y == 0 ? H + 1 : (y == H - 1 ? 0 : -1)};
     const int cols[2] = {x + 1, x == 0 ? W + 1 : (x == W - 1 ? 0 : -1)};
 #pragma unroll
@@ -224,7 +259,7 @@ __device__ __forceinline__ void store_px(__nv_bfloat16 *out, int H, int W, int y
         if (rows[a] < 0) continue;
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            if (cols[b] < 0) continue;
+            if (cols[b] < 0 || (halo_only && a == 0 && b == 0)) continue;
             uint4 *p = reinterpret_cast<uint4 *>(out + ((size_t)rows[a] * (W + 2) + cols[b]) * C);
 #pragma unroll
             for (int i = 0; i < 8; ++i) p[i] = d[i];
@@ -274,24 +309,42 @@ struct ConvArgs {
 // column block) and rows [chunk * rows_per_chunk, ...) of it.  A batch of
 // equal-size images is stacked along y, each padded image (H + 2 rows, or
 // 2H + 2 for the shuffle layer's output) after the previous one.
+//
+// The block walks its input rows once.  Input row i (padded row y_a + i)
+// feeds output rows i, i - 1 and i - 2 through the taps dy = 0, 1, 2, so for
+// each dx and each 16-channel slice one MMA with N = 192 multiplies the
+// row's x-shifted pixels by the three dy taps' weights side by side (the
+// weights are staged [dx][dy][co][ci]) into the accumulators of those three
+// output rows, which sit side by side in TMEM: output row o owns the 64
+// columns of slot (-o) mod 8, so rows i, i - 1, i - 2 own slots s, s + 1,
+// s + 2.  Where that run wraps past slot 7 (two input rows of eight) the MMA
+// splits into N = 128 + 64 or 64 + 128.  12 to 24 MMAs per input row instead
+// of 36 of N = 64.  The epilogue drains a slot once its row's last input
+// (dy = 2) is in, writes zeros back (every MMA accumulates: splitting off the
+// first product of each row to overwrite its slot costs one more MMA per
+// input row, which measured slower than the zero stores) and frees it; the
+// two rows before the block's first output row (o = -2, -1) only collect
+// partial sums and are drained without a store.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
-              const __grid_constant__ CUtensorMap tm_out, ConvArgs a) {
+              const __grid_constant__ CUtensorMap tm_out, const __grid_constant__ CUtensorMap tm_skip, ConvArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *wsm = sm;
     unsigned char *rows = sm + WBYTES;
     unsigned char *stage = rows + NSLOT * ROWSLOT;  // 2 x STAGE, 1024-byte aligned
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * STAGE);
+    unsigned char *skipbuf = stage + 2 * STAGE;     // SKIPBUF x STAGE (residual layer)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(skipbuf + SKIPBUF * STAGE);
     uint64_t *wbar = bars, *full = bars + 1, *empty = full + NSLOT;
-    uint64_t *tfull = empty + NSLOT, *tempty = tfull + NBUF, *mdone = tempty + NBUF;
+    uint64_t *tfull = empty + NSLOT, *tempty = tfull + TSLOTS, *tzero = tempty + TSLOTS, *mdone = tzero + 1;
+    uint64_t *skipbar = mdone + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + NBARS) + 1;
-    float *s_bias = reinterpret_cast<float *>(bars + 32);  // [64] bias, [64] PReLU slopes
-    float *s_prelu = s_bias + C;
+    float *s_bias = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(bars) + BAR_AREA);  // [64] bias
+    float *s_prelu = s_bias + C;                                                                     // [64] slopes
 
     const int NB = a.W / TM;
     const int strip = blockIdx.x / a.chunks, chunk = blockIdx.x - strip * a.chunks;
@@ -304,7 +357,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     const int y_a = chunk * a.rows_per_chunk;
     const int y_b = min(a.H, y_a + a.rows_per_chunk);
     if (y_a >= y_b) return;  // uniform across the block, before any barrier or TMEM use
-    const int T = y_b - y_a;  // tiles (output rows); input rows y_a .. y_b + 1 (padded)
+    const int T = y_b - y_a;  // output rows; input rows y_a .. y_b + 1 (padded), i = 0 .. T + 1
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -313,11 +366,13 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             mbar_init(&full[s2], 1);
             mbar_init(&empty[s2], 1);
         }
-        for (int b = 0; b < NBUF; ++b) {
+        for (int b = 0; b < TSLOTS; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], EPI_WARPS);
         }
+        mbar_init(tzero, EPI_WARPS);
         mbar_init(mdone, 1);
+        for (int k = 0; k < SKIPBUF; ++k) mbar_init(&skipbar[k], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -332,10 +387,10 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ---- producer: the weights, then the ring of input rows ----------------
+        // ---- producer: the weights ([dx][dy][co][ci]), then the ring of input rows
         if (lane == 0) {
             mbar_expect_tx(wbar, WBYTES);
-            tma_load_4d(wsm, &tm_w, wbar, 0, 0, 0, a.layer + g);
+            for (int dx = 0; dx < 3; ++dx) tma_load_5d(wsm + dx * DXBYTES, &tm_w, wbar, 0, 0, dx, 0, a.layer + g);
             int issued = 0;
             for (int i = 0; i < T + 2; ++i) {  // relative input row i = padded row y_a + i
                 const int slot = i % NSLOT;
@@ -359,31 +414,45 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         }
     } else if (warp == 1) {
         // ---- MMA issuer ---------------------------------------------------------
+        // Descriptors are formed once: every operand is a fixed byte offset from
+        // the weight base or from the staged row, and the start address field of
+        // a descriptor is that address / 16 (no carry: shared addresses stay
+        // below 2^18), so each MMA costs two 64-bit adds.
         if (lane == 0) {
-            bool ok = mbar_wait(wbar, 0);
-            int t = 0;
-            for (; ok && t < T; ++t) {
-                const int b = t % NBUF;
-                if (t >= NBUF) ok = mbar_wait(&tempty[b], ((t / NBUF) - 1) & 1);
-                for (int dy = 0; dy < 3 && ok; ++dy) ok = mbar_wait(&full[(t + dy) % NSLOT], ((t + dy) / NSLOT) & 1);
+            bool ok = mbar_wait(tzero, 0) && mbar_wait(wbar, 0);
+            const uint32_t rbase = smem_u32(rows);
+            const uint64_t bd0 = sdesc_sw128(smem_u32(wsm));
+            int si = 0;  // ring slot of input row i
+            int i = 0;
+            for (; ok && i < T + 2; ++i) {
+                const int ts = (-i) & (TSLOTS - 1);  // accumulator slot of output row i
+                // the slot's previous row (i - 8) must be drained and zeroed
+                if (i >= TSLOTS - 2) ok = mbar_wait(&tempty[ts], ((i - (TSLOTS - 2)) >> 3) & 1);
+                if (ok) ok = mbar_wait(&full[si], (i / NSLOT) & 1);
                 if (!ok || *abort_flag) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * C);
-                const uint32_t wbase = smem_u32(wsm), rbase = smem_u32(rows);
-#pragma unroll 1
-                for (int dy = 0; dy < 3; ++dy) {
-                    const uint32_t row = rbase + (uint32_t)(((t + dy) % NSLOT) * ROWSLOT);
+                const uint64_t ad0 = sdesc_planes(rbase + (uint32_t)(si * ROWSLOT));
+                const uint32_t d = tmem + (uint32_t)(ts * C);
 #pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
+                for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ad = sdesc_planes(row + 2 * kk * PLANE + dx * 16);
-                            const uint64_t bd = sdesc_sw128(wbase + (dy * 3 + dx) * TAPBYTES + kk * 32);
-                            mma_bf16(d, ad, bd, (dy | dx | kk) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = ad0 + (uint64_t)(kk * (2 * PLANE / 16) + dx);
+                        const uint64_t bd = bd0 + (uint64_t)(dx * (DXBYTES / 16) + kk * 2);
+                        constexpr uint64_t B1 = TAPBYTES / 16, B2 = 2 * TAPBYTES / 16;  // dy = 1, 2 rows of B
+                        if (ts <= TSLOTS - 3) {
+                            mma_bf16<192, 1>(d, ad, bd);
+                        } else if (ts == TSLOTS - 2) {  // rows i, i - 1 in slots 6, 7; row i - 2 in slot 0
+                            mma_bf16<128, 1>(d, ad, bd);
+                            mma_bf16<64, 1>(tmem, ad, bd + B2);
+                        } else {  // row i in slot 7; rows i - 1, i - 2 in slots 0, 1
+                            mma_bf16<64, 1>(d, ad, bd);
+                            mma_bf16<128, 1>(tmem, ad, bd + B1);
                         }
-                }
-                mma_commit(&tfull[b]);     // accumulator b holds tile t
-                mma_commit(&empty[t % NSLOT]);  // input row t has no later reader
+                    }
+                mma_commit(&tfull[(2 - i) & (TSLOTS - 1)]);  // output row i - 2 is complete
+                mma_commit(&empty[si]);                      // input row i has no later reader
+                si = si + 1 == NSLOT ? 0 : si + 1;
             }
             if (!ok) *abort_flag = 1;
             // every issued MMA completes before the block frees its TMEM
@@ -391,36 +460,65 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             mbar_wait(mdone, 0);
         }
     } else {
-        // ---- epilogue: 8 warps drain accumulator b of tile t ----------------------
+        // ---- epilogue: 8 warps drain the slot of output row o ----------------------
         const int e = warp - 2;
         const int quarter = warp & 3, half = e >> 2;
         const int j = quarter * 32 + lane;  // pixel of the tile
         const int x = cb * TM + j;
         const bool leader = (e == 0 && lane == 0);
-        for (int t = 0; t < T; ++t) {
-            const int b = t % NBUF;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        // every slot starts at zero
+        for (int b = 0; b < TSLOTS; ++b) tmem_zero32(tmem + (uint32_t)(b * C + half * 32) + lane_base);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tzero);
+        // the residual layer's skip input (this block's output rows of the block
+        // input) arrives by TMA, two rows ahead, in the output tile's swizzled layout
+        if (MODE == MODE_RESID && leader)
+            for (int k = 0; k < 2 && k < T; ++k) {
+                mbar_expect_tx(&skipbar[k], STAGE);
+                tma_load_3d(skipbuf + k * STAGE, &tm_skip, &skipbar[k], 0, cb * TM + 1, yin0 + y_a + k + 1);
+            }
+        for (int q = 0; q < T + 2; ++q) {  // output row o = q - 2 (o < 0: partial sums only)
+            const int o = q - 2;
+            const int ts = (2 - q) & (TSLOTS - 1);
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(&tfull[b], (t / NBUF) & 1);
+            if (lane == 0) {
+                ok = mbar_wait(&tfull[ts], (q >> 3) & 1);
+                if (MODE == MODE_RESID && o >= 0 && ok) ok = mbar_wait(&skipbar[o % SKIPBUF], (o / SKIPBUF) & 1);
+            }
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!epi_bar_and(ok && !*abort_flag, 1, 32 * EPI_WARPS)) {
                 if (leader) *abort_flag = 1;
                 break;
             }
             tc_fence_after();
+            if (MODE == MODE_RESID && leader && o >= 0 && o + 2 < T) {
+                // buffer (o + 2) % 3 last held row o - 1, whose readers are past the barrier above
+                const int k = (o + 2) % SKIPBUF;
+                mbar_expect_tx(&skipbar[k], STAGE);
+                tma_load_3d(skipbuf + k * STAGE, &tm_skip, &skipbar[k], 0, cb * TM + 1, yin0 + y_a + o + 3);
+            }
+            const uint32_t taddr = tmem + (uint32_t)(ts * C + half * 32) + lane_base;
             float v[32];
-            tmem_ld32(tmem + (uint32_t)(b * C + half * 32) + ((uint32_t)(quarter * 32) << 16), v);
-            tmem_wait_ld();
+            if (o >= 0) {
+                tmem_ld32(taddr, v);
+                tmem_wait_ld();
+            }
+            tmem_zero32(taddr);
+            tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);  // accumulator b may take tile t + NBUF
-            const int y = y_a + t;
+            if (lane == 0) mbar_arrive(&tempty[ts]);  // the slot may take row o + 8
+            if (o < 0) continue;
+            const int y = y_a + o;
             if (MODE == MODE_RESID) {
-                const uint4 *sp = reinterpret_cast<const uint4 *>(
-                    a.skip + in_img + ((size_t)(y + 1) * (a.W + 2) + (x + 1)) * C + half * 32);
+                const uint4 *sp = reinterpret_cast<const uint4 *>(skipbuf + (o % SKIPBUF) * STAGE + j * 128);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const uint4 q = sp[i];
-                    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+                    const uint4 qv = sp[(half * 4 + i) ^ (j & 7)];
+                    const uint32_t w4[4] = {qv.x, qv.y, qv.z, qv.w};
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
@@ -428,6 +526,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                         v[i * 8 + 2 * k + 1] += f.y;
                     }
                 }
+                fence_proxy_async();  // these reads come before the buffer's next TMA write
             }
             // a window separator of a mosaic stays zero (the windows' zero padding)
             const bool sep = a.mosaic > 0 && ((y % a.mosaic) == a.mosaic - 1 || (x % a.mosaic) == a.mosaic - 1);
@@ -449,29 +548,38 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 }
                 outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
             }
-            if (MODE == MODE_SHUFFLE) {
-                store_half_px(a.out + out_img, 2 * a.H, 2 * a.W, 2 * y + (g >> 1), 2 * x + (g & 1), half, outv, false);
-            } else {
-                // stage t & 1 was last read by the TMA store of tile t - 2
-                if (leader) bulk_wait_read1();
-                epi_bar(2, 32 * EPI_WARPS);
-                // 128-byte swizzled staging: 16-byte chunk i of pixel j at position i ^ (j & 7)
-                uint4 *st = reinterpret_cast<uint4 *>(stage + (t & 1) * STAGE + j * 128);
+            // output geometry: the coarse grid, or for the pixel shuffle the fine
+            // grid, where group g's pixel x lands at (2y + g / 2, 2x + g % 2)
+            const int OH = MODE == MODE_SHUFFLE ? 2 * a.H : a.H, OW = MODE == MODE_SHUFFLE ? 2 * a.W : a.W;
+            const int oy = MODE == MODE_SHUFFLE ? 2 * y + (g >> 1) : y;
+            const int ox = MODE == MODE_SHUFFLE ? 2 * x + (g & 1) : x;
+            const int yout0 = MODE == MODE_SHUFFLE ? img * (2 * a.H + 2) : yin0;
+            // stage o & 1 was last read by the TMA store of row o - 2
+            if (leader) bulk_wait_read1();
+            epi_bar(2, 32 * EPI_WARPS);
+            // 128-byte swizzled staging: 16-byte chunk i of pixel j at position i ^ (j & 7)
+            uint4 *st = reinterpret_cast<uint4 *>(stage + (o & 1) * STAGE + j * 128);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) st[(half * 4 + i) ^ (j & 7)] = outv[i];
-                if (x == 0 || x == a.W - 1) store_half_px(a.out + out_img, a.H, a.W, y, x, half, outv, true);
-                fence_proxy_async();
-                epi_bar(2, 32 * EPI_WARPS);
-                if (leader) {
-                    const unsigned char *src = stage + (t & 1) * STAGE;
-                    tma_store_3d(&tm_out, src, 0, cb * TM + 1, yin0 + y + 1);
-                    if (y == 0) tma_store_3d(&tm_out, src, 0, cb * TM + 1, yin0 + a.H + 1);
-                    if (y == a.H - 1) tma_store_3d(&tm_out, src, 0, cb * TM + 1, yin0);
-                    bulk_commit();
+            for (int i = 0; i < 4; ++i) st[(half * 4 + i) ^ (j & 7)] = outv[i];
+            if (ox == 0 || ox == OW - 1) store_half_px(a.out + out_img, OH, OW, oy, ox, half, outv, true);
+            fence_proxy_async();
+            epi_bar(2, 32 * EPI_WARPS);
+            if (leader) {
+                const unsigned char *src = stage + (o & 1) * STAGE;
+                if (MODE == MODE_SHUFFLE) {
+                    // fine map (channels, x parity, x / 2, padded row) from padded column 1
+                    tma_store_4d(&tm_out, src, 0, g & 1, cb * TM, yout0 + oy + 1);
+                    if (oy == 0) tma_store_4d(&tm_out, src, 0, g & 1, cb * TM, yout0 + OH + 1);
+                    if (oy == OH - 1) tma_store_4d(&tm_out, src, 0, g & 1, cb * TM, yout0);
+                } else {
+                    tma_store_3d(&tm_out, src, 0, cb * TM + 1, yout0 + oy + 1);
+                    if (oy == 0) tma_store_3d(&tm_out, src, 0, cb * TM + 1, yout0 + OH + 1);
+                    if (oy == OH - 1) tma_store_3d(&tm_out, src, 0, cb * TM + 1, yout0);
                 }
+                bulk_commit();
             }
         }
-        if (MODE != MODE_SHUFFLE && leader) bulk_wait_all();  // tile stores complete
+        if (leader) bulk_wait_all();  // tile stores complete
     }
     tc_fence_before();
     __syncthreads();
@@ -505,95 +613,198 @@ __global__ void __launch_bounds__(kRedThreads) k_absmax(const float *__restrict_
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {  // the last block takes the max of the partials, all threads at once
         __threadfence();
         float gm = 0.f;
-        for (int b = 0; b < (int)gridDim.x; ++b) gm = fmaxf(gm, (float)((volatile double *)partials)[b]);
-        s_out[0] = gm > 0.f ? gm : 1.f;
-        *counter = 0u;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            gm = fmaxf(gm, (float)((volatile double *)partials)[b]);
+        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_down_sync(0xffffffffu, gm, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = gm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float bm = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) bm = fmaxf(bm, (float)sh[w]);
+            s_out[0] = bm > 0.f ? bm : 1.f;
+            *counter = 0u;
+        }
     }
 }
 
-// conv3x3 1 -> 64 of q = ec / s, + bias, PReLU, to padded bf16; one thread per pixel.
-__global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ ec, int nc,
-                                                 const float *__restrict__ s_ptr,
-                                                 const float *__restrict__ wpack,  // w[64][9], b[64], a[64]
-                                                 __nv_bfloat16 *__restrict__ out) {
-    __shared__ float w[C * 9 + 2 * C];
-    for (int i = threadIdx.x; i < C * 11; i += blockDim.x) w[i] = wpack[i];
-    __syncthreads();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nc * nc) return;
-    const int y = p / nc, x = p - y * nc;
-    const float s = *s_ptr;
+// conv3x3 1 -> 64 of q = ec / s, + bias, PReLU, to padded bf16; one thread per
+// pixel.  The block's 256 pixels (consecutive along rows) go through shared
+// memory so that the interior stores are 16-byte words written by consecutive
+// threads; the halo copies of edge pixels are written directly.
+// wt: the layer's weights staged as [tap][64 channels] (tap 9 = bias, 10 =
+// PReLU slope), read four channels per 16-byte broadcast load.
+__device__ __forceinline__ void conv_in_px(const float *__restrict__ ec, int nc, float s, const float4 *wt, int y,
+                                           int x, uint4 *outv) {
     float q[9];
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx)
             q[ky * 3 + kx] = ec[(size_t)((y + ky - 1 + nc) & (nc - 1)) * nc + ((x + kx - 1 + nc) & (nc - 1))] / s;
-    uint4 outv[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
+        float v[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // channels 8i + 4h .. + 3
+            const float4 b4 = wt[9 * (C / 4) + 2 * i + h];
+            float acc[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float4 w4 = wt[t * (C / 4) + 2 * i + h];
+                acc[0] = fmaf(w4.x, q[t], acc[0]);
+                acc[1] = fmaf(w4.y, q[t], acc[1]);
+                acc[2] = fmaf(w4.z, q[t], acc[2]);
+                acc[3] = fmaf(w4.w, q[t], acc[3]);
+            }
+            const float4 a4 = wt[10 * (C / 4) + 2 * i + h];
+            v[4 * h + 0] = acc[0] > 0.f ? acc[0] : a4.x * acc[0];
+            v[4 * h + 1] = acc[1] > 0.f ? acc[1] : a4.y * acc[1];
+            v[4 * h + 2] = acc[2] > 0.f ? acc[2] : a4.z * acc[2];
+            v[4 * h + 3] = acc[3] > 0.f ? acc[3] : a4.w * acc[3];
+        }
         uint32_t w4[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float v[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = i * 8 + 2 * k + h;
-                float acc = w[C * 9 + c];
-#pragma unroll
-                for (int t = 0; t < 9; ++t) acc = fmaf(w[c * 9 + t], q[t], acc);
-                v[h] = acc > 0.f ? acc : w[C * 10 + c] * acc;
-            }
-            const __nv_bfloat162 bb = __floats2bfloat162_rn(v[0], v[1]);
+            const __nv_bfloat162 bb = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
             w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
         }
         outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
-    store_px(out, nc, nc, y, x, outv);
+}
+
+// Stage wpack (w[64][9], b[64], a[64]) as [tap][64] with the bias and the
+// slopes as rows 9 and 10.
+__device__ __forceinline__ void stage_in_weights(float *w, const float *__restrict__ wpack) {
+    for (int i = threadIdx.x; i < C * 11; i += blockDim.x) {
+        const int t = i / C, c = i - t * C;
+        w[i] = t < 9 ? wpack[c * 9 + t] : wpack[C * 9 + (t - 9) * C + c];
+    }
+}
+
+// Write the block's 256 staged pixels (p0 .. p0 + 255 of an nc x nc grid, all
+// valid) to their interior positions: 16-byte word k of the block = chunk
+// k & 7 of pixel k >> 3 (staged with the chunk index XOR the pixel's low bits).
+__device__ __forceinline__ void conv_in_flush(const uint4 *st, __nv_bfloat16 *__restrict__ out, int nc, int p0) {
+    for (int k = threadIdx.x; k < 256 * 8; k += 256) {
+        const int px = k >> 3, ch = k & 7;
+        const int p = p0 + px, y = p / nc, x = p - y * nc;
+        reinterpret_cast<uint4 *>(out + ((size_t)(y + 1) * (nc + 2) + (x + 1)) * C)[ch] = st[px * 8 + (ch ^ (px & 7))];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ ec, int nc,
+                                                 const float *__restrict__ s_ptr,
+                                                 const float *__restrict__ wpack,  // w[64][9], b[64], a[64]
+                                                 __nv_bfloat16 *__restrict__ out) {
+    __shared__ __align__(16) float w[C * 11];
+    __shared__ uint4 st[256 * 8];
+    stage_in_weights(w, wpack);
+    __syncthreads();
+    const int p0 = blockIdx.x * 256, p = p0 + threadIdx.x;  // nc * nc is a multiple of 256
+    const int y = p / nc, x = p - y * nc;
+    uint4 outv[8];
+    conv_in_px(ec, nc, *s_ptr, reinterpret_cast<const float4 *>(w), y, x, outv);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) st[threadIdx.x * 8 + (i ^ (threadIdx.x & 7))] = outv[i];
+    if (x == 0 || x == nc - 1 || y == 0 || y == nc - 1) store_px(out, nc, nc, y, x, outv, true);
+    __syncthreads();
+    conv_in_flush(st, out, nc, p0);
 }
 
 // conv3x3 64 -> 1 on the padded fine activation, + bias, times s:
-// fine_out = s * G.  A 16 x 16 tile of pixels stages its 18 x 18 x 64 window.
+// fine_out = s * G.  A 16 x 16 tile of outputs stages its 18 x 18 x 64 window
+// in shared memory; warp w computes the 32 outputs of tile rows 2w, 2w + 1
+// with its lanes split over pixels and channels (conv_out_warp), each
+// accumulating the even and odd channel sums of an output as one packed
+// FP32 pair.
 constexpr int OUT_T = 16;
-__global__ void __launch_bounds__(OUT_T * OUT_T) k_conv_out(const __nv_bfloat16 *__restrict__ u, int nf,
-                                                            const float *__restrict__ wpack,  // w[9][64], b
-                                                            const float *__restrict__ s_ptr,
-                                                            float *__restrict__ fine_out) {
-    __shared__ uint4 tile[(OUT_T + 2) * (OUT_T + 2) * 8];
-    __shared__ float w[9 * C + 1];
-    for (int i = threadIdx.x; i < 9 * C + 1; i += blockDim.x) w[i] = wpack[i];
-    const int y0 = blockIdx.y * OUT_T, x0 = blockIdx.x * OUT_T;
-    // padded rows y0 .. y0+17, cols x0 .. x0+17 (pixel (y, x) is at padded (y+1, x+1))
-    for (int i = threadIdx.x; i < (OUT_T + 2) * (OUT_T + 2) * 8; i += blockDim.x) {
+constexpr int OUT_TP = OUT_T + 2;
+
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+
+// Stage padded pixels [y0, y0 + 18) x [x0, x0 + 18) of u (row pitch nf + 2) into tile.
+__device__ __forceinline__ void stage_out_tile(uint4 *tile, const __nv_bfloat16 *__restrict__ u, int nf, int y0,
+                                               int x0) {
+    for (int i = threadIdx.x; i < OUT_TP * OUT_TP * 8; i += blockDim.x) {
         const int px = i >> 3, part = i & 7;
-        const int ry = px / (OUT_T + 2), rx = px - ry * (OUT_T + 2);
+        const int ry = px / OUT_TP, rx = px - ry * OUT_TP;
         tile[i] = reinterpret_cast<const uint4 *>(u + ((size_t)(y0 + ry) * (nf + 2) + (x0 + rx)) * C)[part];
     }
-    __syncthreads();
-    const int ty = threadIdx.x / OUT_T, tx = threadIdx.x - ty * OUT_T;
-    float acc = 0.f;
+}
+
+// The 32 outputs of warp w's two tile rows (tile row 2w + j / 16, column
+// j % 16, before bias and scale).  Lane l holds channels 2l, 2l + 1: a
+// pixel's 128 bytes are one conflict-free 32-word shared load.  Each staged
+// pixel of the three input rows of an output row is loaded once and feeds
+// the three outputs it is a horizontal tap of (54 loads per output row
+// instead of 144), each output accumulating its even and odd channel sums as
+// one packed FP32 pair; a transposing butterfly over the lanes then leaves
+// output j's total in lane j, which is returned with its index.
+__device__ __forceinline__ float conv_out_warp(const uint4 *tile, const float *__restrict__ wpack, int w, int lane,
+                                               int *jout) {
+    const uint32_t *t32 = reinterpret_cast<const uint32_t *>(tile);
+    unsigned long long wp[9];
 #pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
+    for (int t = 0; t < 9; ++t) wp[t] = pack2(wpack[t * C + 2 * lane], wpack[t * C + 2 * lane + 1]);
+    unsigned long long acc[32];
 #pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-            const uint4 *pp = tile + ((ty + ky) * (OUT_T + 2) + (tx + kx)) * 8;
-            const float *wt = w + (ky * 3 + kx) * C;
+    for (int j = 0; j < 32; ++j) acc[j] = 0ull;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const uint4 q = pp[i];
-                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
-                    acc = fmaf(wt[i * 8 + 2 * k], f.x, acc);
-                    acc = fmaf(wt[i * 8 + 2 * k + 1], f.y, acc);
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int xp = 0; xp < OUT_TP; ++xp) {
+                const uint32_t v = t32[((2 * w + r + dy) * OUT_TP + xp) * 32 + lane];
+                const unsigned long long vv =
+                    (unsigned long long)(v << 16) | ((unsigned long long)(v & 0xffff0000u) << 32);
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int tx = xp - kx;
+                    if (tx >= 0 && tx < OUT_T) acc[r * 16 + tx] = ffma2(wp[dy * 3 + kx], vv, acc[r * 16 + tx]);
                 }
             }
+    float a[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = __uint_as_float((uint32_t)acc[j]) + __uint_as_float((uint32_t)(acc[j] >> 32));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const float send = upper ? a[i] : a[i + off];
+            const float keep = upper ? a[i + off] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
-    fine_out[(size_t)(y0 + ty) * nf + x0 + tx] = (*s_ptr) * (acc + w[9 * C]);
+    }
+    *jout = lane;
+    return a[0];
+}
+
+__global__ void __launch_bounds__(256) k_conv_out(const __nv_bfloat16 *__restrict__ u, int nf,
+                                                  const float *__restrict__ wpack,  // w[9][64], b
+                                                  const float *__restrict__ s_ptr,
+                                                  float *__restrict__ fine_out) {
+    __shared__ uint4 tile[OUT_TP * OUT_TP * 8];
+    const int y0 = blockIdx.y * OUT_T, x0 = blockIdx.x * OUT_T;
+    stage_out_tile(tile, u, nf, y0, x0);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int j;
+    const float g = conv_out_warp(tile, wpack, w, lane, &j);
+    fine_out[(size_t)(y0 + 2 * w + (j >> 4)) * nf + x0 + (j & 15)] = (*s_ptr) * (g + wpack[9 * C]);
 }
 
 // Batched forms for a stack of equal-size images (image = blockIdx.y, or
@@ -620,81 +831,37 @@ __global__ void __launch_bounds__(1024) k_absmax_b(const float *const *__restric
 __global__ void __launch_bounds__(256) k_conv_in_b(const float *const *__restrict__ ecs, int nc,
                                                    const float *__restrict__ s_all,
                                                    const float *__restrict__ wpack, __nv_bfloat16 *__restrict__ out) {
-    __shared__ float w[C * 9 + 2 * C];
-    for (int i = threadIdx.x; i < C * 11; i += blockDim.x) w[i] = wpack[i];
+    __shared__ __align__(16) float w[C * 11];
+    __shared__ uint4 st[256 * 8];
+    stage_in_weights(w, wpack);
     __syncthreads();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nc * nc) return;
     const float *ec = ecs[blockIdx.y];
     __nv_bfloat16 *o = out + (size_t)blockIdx.y * (nc + 2) * (nc + 2) * C;
+    const int p0 = blockIdx.x * 256, p = p0 + threadIdx.x;
     const int y = p / nc, x = p - y * nc;
-    const float s = s_all[blockIdx.y];
-    float q[9];
-#pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx)
-            q[ky * 3 + kx] = ec[(size_t)((y + ky - 1 + nc) & (nc - 1)) * nc + ((x + kx - 1 + nc) & (nc - 1))] / s;
     uint4 outv[8];
+    conv_in_px(ec, nc, s_all[blockIdx.y], reinterpret_cast<const float4 *>(w), y, x, outv);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        uint32_t w4[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float v[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = i * 8 + 2 * k + h;
-                float acc = w[C * 9 + c];
-#pragma unroll
-                for (int t = 0; t < 9; ++t) acc = fmaf(w[c * 9 + t], q[t], acc);
-                v[h] = acc > 0.f ? acc : w[C * 10 + c] * acc;
-            }
-            const __nv_bfloat162 bb = __floats2bfloat162_rn(v[0], v[1]);
-            w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
-        }
-        outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-    }
-    store_px(o, nc, nc, y, x, outv);
+    for (int i = 0; i < 8; ++i) st[threadIdx.x * 8 + (i ^ (threadIdx.x & 7))] = outv[i];
+    if (x == 0 || x == nc - 1 || y == 0 || y == nc - 1) store_px(o, nc, nc, y, x, outv, true);
+    __syncthreads();
+    conv_in_flush(st, o, nc, p0);
 }
 
-__global__ void __launch_bounds__(OUT_T * OUT_T) k_conv_out_b(const __nv_bfloat16 *__restrict__ u_all, int nf,
-                                                              const float *__restrict__ wpack,
-                                                              const float *__restrict__ s_all,
-                                                              float *__restrict__ out_all) {
-    __shared__ uint4 tile[(OUT_T + 2) * (OUT_T + 2) * 8];
-    __shared__ float w[9 * C + 1];
+__global__ void __launch_bounds__(256) k_conv_out_b(const __nv_bfloat16 *__restrict__ u_all, int nf,
+                                                    const float *__restrict__ wpack,
+                                                    const float *__restrict__ s_all,
+                                                    float *__restrict__ out_all) {
+    __shared__ uint4 tile[OUT_TP * OUT_TP * 8];
     const __nv_bfloat16 *u = u_all + (size_t)blockIdx.z * (nf + 2) * (nf + 2) * C;
     float *fine_out = out_all + (size_t)blockIdx.z * nf * nf;
-    for (int i = threadIdx.x; i < 9 * C + 1; i += blockDim.x) w[i] = wpack[i];
     const int y0 = blockIdx.y * OUT_T, x0 = blockIdx.x * OUT_T;
-    for (int i = threadIdx.x; i < (OUT_T + 2) * (OUT_T + 2) * 8; i += blockDim.x) {
-        const int px = i >> 3, part = i & 7;
-        const int ry = px / (OUT_T + 2), rx = px - ry * (OUT_T + 2);
-        tile[i] = reinterpret_cast<const uint4 *>(u + ((size_t)(y0 + ry) * (nf + 2) + (x0 + rx)) * C)[part];
-    }
+    stage_out_tile(tile, u, nf, y0, x0);
     __syncthreads();
-    const int ty = threadIdx.x / OUT_T, tx = threadIdx.x - ty * OUT_T;
-    float acc = 0.f;
-#pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-            const uint4 *pp = tile + ((ty + ky) * (OUT_T + 2) + (tx + kx)) * 8;
-            const float *wt = w + (ky * 3 + kx) * C;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const uint4 q = pp[i];
-                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[k]));
-                    acc = fmaf(wt[i * 8 + 2 * k], f.x, acc);
-                    acc = fmaf(wt[i * 8 + 2 * k + 1], f.y, acc);
-                }
-            }
-        }
-    fine_out[(size_t)(y0 + ty) * nf + x0 + tx] = s_all[blockIdx.z] * (acc + w[9 * C]);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int j;
+    const float g = conv_out_warp(tile, wpack, w, lane, &j);
+    fine_out[(size_t)(y0 + 2 * w + (j >> 4)) * nf + x0 + (j & 15)] = s_all[blockIdx.z] * (g + wpack[9 * C]);
 }
 
 // ---------------------------------------------------------------------------
@@ -884,14 +1051,35 @@ bool make_out_map(CUtensorMap *m, void *base, int H, int W) {
 }
 
 // packed weights [layers][9][64 co][64 ci] bf16 as a 4D tensor; box = one layer
+// the padded fine activation of the pixel-shuffle layer as the destination of
+// a tile: fine pixel X = 2 x2 + p of a row sits at padded column X + 1, so
+// from padded column 1 the map is (64 channels, parity p, x2, padded row) and
+// a box of 64 x 1 x 128 x 1 is the 128 pixels of one parity of one row,
+// 128-byte swizzled; rows = padded fine rows of all stacked images
+bool make_fine_map(CUtensorMap *m, void *base, int rows, int W) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)C, 2, (cuuint64_t)W, (cuuint64_t)rows};
+    cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)2 * C * 2, (cuuint64_t)(2 * W + 2) * C * 2};
+    cuuint32_t box[4] = {(cuuint32_t)C, 1, (cuuint32_t)TM, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (char *)base + C * 2, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// packed weights [layers][9 taps = dy * 3 + dx][64 co][64 ci] bf16 as a 5D
+// tensor (ci, co, dx, dy, layer); a box is one dx of one layer, all three dy:
+// [dy][co][ci] = 192 rows of 128 bytes, 128-byte swizzled
 bool make_w_map(CUtensorMap *m, void *base, int layers) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
-    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)C, 9, (cuuint64_t)layers};
-    cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * C * 2, (cuuint64_t)9 * C * C * 2};
-    cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)C, 9, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)C, 3, 3, (cuuint64_t)layers};
+    cuuint64_t strides[4] = {(cuuint64_t)C * 2, (cuuint64_t)TAPBYTES, (cuuint64_t)3 * TAPBYTES,
+                             (cuuint64_t)9 * TAPBYTES};
+    cuuint32_t box[5] = {(cuuint32_t)C, (cuuint32_t)C, 1, 3, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -910,8 +1098,11 @@ cudaError_t prepare_conv() {
 }
 
 template <int MODE>
+// tm_out: the output activation map (make_out_map), or for MODE_SHUFFLE the
+// fine map (make_fine_map); tm_skip: the residual input (make_out_map of the
+// skip buffer) for MODE_RESID, any map otherwise (not read).
 cudaError_t launch_conv(const CUtensorMap &tm_in, const CUtensorMap &tm_w, const CUtensorMap &tm_out,
-                        ConvArgs a, int groups, cudaStream_t s) {
+                        const CUtensorMap &tm_skip, ConvArgs a, int groups, cudaStream_t s) {
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -933,7 +1124,7 @@ cudaError_t launch_conv(const CUtensorMap &tm_in, const CUtensorMap &tm_w, const
     if (chunks > a.H) chunks = a.H;
     a.rows_per_chunk = (a.H + chunks - 1) / chunks;
     a.chunks = chunks;
-    k_conv_tc<MODE><<<strips * chunks, CONV_THREADS, CONV_SMEM, s>>>(tm_in, tm_w, tm_out, a);
+    k_conv_tc<MODE><<<strips * chunks, CONV_THREADS, CONV_SMEM, s>>>(tm_in, tm_w, tm_out, tm_skip, a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -959,6 +1150,7 @@ cudaError_t ensure_buffers(SrState *st, int nc) {
     for (int i = 0; i < 3; ++i)
         if (!make_act_map(&st->tm_act[i], st->act[i], nc, nc) || !make_out_map(&st->tm_out[i], st->act[i], nc, nc))
             return cudaErrorInvalidValue;
+    if (!make_fine_map(&st->tm_fine, st->fine_act, 2 * nc + 2, nc)) return cudaErrorInvalidValue;
     st->nc = nc;
     return cudaSuccess;
 }
@@ -1154,22 +1346,22 @@ mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t s, ch
         const int nxt = (cur + 1) % 3, tmp = (cur + 2) % 3;
         ConvArgs a1 = {nullptr, (__nv_bfloat16 *)st->act[tmp], st->bias_tc + (size_t)(2 * k) * C,
                        st->prelu_blk + (size_t)k * C, nc, nc, 2 * k, 0, 0, st->err};
-        e = launch_conv<MODE_PRELU>(st->tm_act[cur], st->tm_w, st->tm_out[tmp], a1, 1, s);
+        e = launch_conv<MODE_PRELU>(st->tm_act[cur], st->tm_w, st->tm_out[tmp], st->tm_out[cur], a1, 1, s);
         if (e != cudaSuccess) break;
         ConvArgs a2 = {(const __nv_bfloat16 *)st->act[cur], (__nv_bfloat16 *)st->act[nxt],
                        st->bias_tc + (size_t)(2 * k + 1) * C, nullptr, nc, nc, 2 * k + 1, 0, 0, st->err};
-        e = launch_conv<MODE_RESID>(st->tm_act[tmp], st->tm_w, st->tm_out[nxt], a2, 1, s);
+        e = launch_conv<MODE_RESID>(st->tm_act[tmp], st->tm_w, st->tm_out[nxt], st->tm_out[cur], a2, 1, s);
         cur = nxt;
     }
     if (e == cudaSuccess) {
         ConvArgs au = {nullptr, (__nv_bfloat16 *)st->fine_act, st->bias_tc + (size_t)(2 * nb) * C, st->prelu_up,
                        nc, nc, 2 * nb, 0, 0, st->err};
-        e = launch_conv<MODE_SHUFFLE>(st->tm_act[cur], st->tm_w, st->tm_out[cur] /* unused */, au, 4, s);
+        e = launch_conv<MODE_SHUFFLE>(st->tm_act[cur], st->tm_w, st->tm_fine, st->tm_out[cur], au, 4, s);
     }
     if (e == cudaSuccess) {
         const int nf = 2 * nc;
         dim3 grid(nf / OUT_T, nf / OUT_T);
-        k_conv_out<<<grid, OUT_T * OUT_T, 0, s>>>((const __nv_bfloat16 *)st->fine_act, nf, st->w_out, st->scal,
+        k_conv_out<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)st->fine_act, nf, st->w_out, st->scal,
                                                   st->fine_out);
         count_launches(1);
         e = cudaGetLastError();
@@ -1207,23 +1399,23 @@ mg_status sr_layer(SrState *st, int layer, int nc, const void *in, const void *s
     } else if (e == cudaSuccess && layer <= 2 * nb + 1) {
         const int l = layer - 1;  // weight layer (the pixel-shuffle groups follow the blocks)
         const int mode = layer == 2 * nb + 1 ? MODE_SHUFFLE : (l % 2 ? MODE_RESID : MODE_PRELU);
-        CUtensorMap tin, tout;
+        CUtensorMap tin, tout, tskip;
         if (!make_act_map(&tin, const_cast<void *>(in), nc, nc) ||
-            !(mode == MODE_SHUFFLE ? make_act_map(&tout, const_cast<void *>(in), nc, nc)
-                                   : make_out_map(&tout, out, nc, nc))) {
+            !(mode == MODE_SHUFFLE ? make_fine_map(&tout, out, 2 * nc + 2, nc) : make_out_map(&tout, out, nc, nc)) ||
+            !make_out_map(&tskip, const_cast<void *>(mode == MODE_RESID ? skip : in), nc, nc)) {
             snprintf(err, errlen, "sr_layer: tensor map encoding failed");
             return MG_ERR_INVALID_ARG;
         }
         const float *prelu = mode == MODE_SHUFFLE ? st->prelu_up : st->prelu_blk + (size_t)(l / 2) * C;
         ConvArgs a = {mode == MODE_RESID ? (const __nv_bfloat16 *)skip : nullptr, (__nv_bfloat16 *)out,
                       st->bias_tc + (size_t)l * C, mode == MODE_RESID ? nullptr : prelu, nc, nc, l, 0, 0, st->err};
-        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, st->tm_w, tout, a, 1, strm);
-        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, st->tm_w, tout, a, 1, strm);
-        else e = launch_conv<MODE_SHUFFLE>(tin, st->tm_w, tout, a, 4, strm);
+        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, st->tm_w, tout, tskip, a, 1, strm);
+        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, st->tm_w, tout, tskip, a, 1, strm);
+        else e = launch_conv<MODE_SHUFFLE>(tin, st->tm_w, tout, tskip, a, 4, strm);
     } else if (e == cudaSuccess) {
         const int nf = 2 * nc;
         dim3 grid(nf / OUT_T, nf / OUT_T);
-        k_conv_out<<<grid, OUT_T * OUT_T, 0, strm>>>((const __nv_bfloat16 *)in, nf, st->w_out, s, (float *)out);
+        k_conv_out<<<grid, 256, 0, strm>>>((const __nv_bfloat16 *)in, nf, st->w_out, s, (float *)out);
         count_launches(1);
         e = cudaGetLastError();
     }
@@ -1269,6 +1461,7 @@ mg_status sr_batch_prepare(SrBatch *b, int imgs, int nc, const float *const *ecs
     for (int i = 0; i < 3 && e == cudaSuccess; ++i)
         if (!make_act_map(&b->tm_act[i], b->act[i], Hs, nc) || !make_out_map(&b->tm_out[i], b->act[i], Hs, nc))
             e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && !make_fine_map(&b->tm_fine, b->fine_act, imgs * (2 * nc + 2), nc)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         snprintf(err, errlen, "batched SR buffers (%d x %d^2): %s", imgs, nc, cudaGetErrorString(e));
         sr_batch_free(b);
@@ -1296,21 +1489,21 @@ mg_status sr_batch_correction(SrBatch *b, const SrState *st, cudaStream_t s, cha
         const int nxt = (cur + 1) % 3, tmp = (cur + 2) % 3;
         ConvArgs a1 = {nullptr, (__nv_bfloat16 *)b->act[tmp], st->bias_tc + (size_t)(2 * k) * C,
                        st->prelu_blk + (size_t)k * C, nc, nc, 2 * k, 0, 0, st->err, imgs};
-        e = launch_conv<MODE_PRELU>(b->tm_act[cur], st->tm_w, b->tm_out[tmp], a1, 1, s);
+        e = launch_conv<MODE_PRELU>(b->tm_act[cur], st->tm_w, b->tm_out[tmp], b->tm_out[cur], a1, 1, s);
         if (e != cudaSuccess) break;
         ConvArgs a2 = {(const __nv_bfloat16 *)b->act[cur], (__nv_bfloat16 *)b->act[nxt],
                        st->bias_tc + (size_t)(2 * k + 1) * C, nullptr, nc, nc, 2 * k + 1, 0, 0, st->err, imgs};
-        e = launch_conv<MODE_RESID>(b->tm_act[tmp], st->tm_w, b->tm_out[nxt], a2, 1, s);
+        e = launch_conv<MODE_RESID>(b->tm_act[tmp], st->tm_w, b->tm_out[nxt], b->tm_out[cur], a2, 1, s);
         cur = nxt;
     }
     if (e == cudaSuccess) {
         ConvArgs au = {nullptr, (__nv_bfloat16 *)b->fine_act, st->bias_tc + (size_t)(2 * nb) * C, st->prelu_up,
                        nc, nc, 2 * nb, 0, 0, st->err, imgs};
-        e = launch_conv<MODE_SHUFFLE>(b->tm_act[cur], st->tm_w, b->tm_out[cur] /* unused */, au, 4, s);
+        e = launch_conv<MODE_SHUFFLE>(b->tm_act[cur], st->tm_w, b->tm_fine, b->tm_out[cur], au, 4, s);
     }
     if (e == cudaSuccess) {
         const int nf = 2 * nc;
-        k_conv_out_b<<<dim3(nf / OUT_T, nf / OUT_T, imgs), OUT_T * OUT_T, 0, s>>>(
+        k_conv_out_b<<<dim3(nf / OUT_T, nf / OUT_T, imgs), 256, 0, s>>>(
             (const __nv_bfloat16 *)b->fine_act, nf, st->w_out, b->s, b->fine_out);
         count_launches(1);
         e = cudaGetLastError();
@@ -1346,6 +1539,7 @@ mg_status sr_windows_prepare(SrWindows *w, int nc, char *err, size_t errlen) {
     for (int i = 0; i < 3 && e == cudaSuccess; ++i)
         if (!make_act_map(&w->tm_act[i], w->act[i], Hm, Wm) || !make_out_map(&w->tm_out[i], w->act[i], Hm, Wm))
             e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && !make_fine_map(&w->tm_fine, w->fine_act, 2 * Hm + 2, Wm)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         snprintf(err, errlen, "windowed SR buffers for %d^2: %s", nc, cudaGetErrorString(e));
         sr_windows_free(w);
@@ -1375,17 +1569,17 @@ mg_status sr_windowed(SrWindows *w, const SrState *st, const float *ec, int nc, 
         const int nxt = (cur + 1) % 3, tmp = (cur + 2) % 3;
         ConvArgs a1 = {nullptr, (__nv_bfloat16 *)w->act[tmp], st->bias_tc + (size_t)(2 * k) * C,
                        st->prelu_blk + (size_t)k * C, Hm, Wm, 2 * k, 0, 0, st->err, 1, kWinCell};
-        e = launch_conv<MODE_PRELU>(w->tm_act[cur], st->tm_w, w->tm_out[tmp], a1, 1, s);
+        e = launch_conv<MODE_PRELU>(w->tm_act[cur], st->tm_w, w->tm_out[tmp], w->tm_out[cur], a1, 1, s);
         if (e != cudaSuccess) break;
         ConvArgs a2 = {(const __nv_bfloat16 *)w->act[cur], (__nv_bfloat16 *)w->act[nxt],
                        st->bias_tc + (size_t)(2 * k + 1) * C, nullptr, Hm, Wm, 2 * k + 1, 0, 0, st->err, 1, kWinCell};
-        e = launch_conv<MODE_RESID>(w->tm_act[tmp], st->tm_w, w->tm_out[nxt], a2, 1, s);
+        e = launch_conv<MODE_RESID>(w->tm_act[tmp], st->tm_w, w->tm_out[nxt], w->tm_out[cur], a2, 1, s);
         cur = nxt;
     }
     if (e == cudaSuccess) {
         ConvArgs au = {nullptr, (__nv_bfloat16 *)w->fine_act, st->bias_tc + (size_t)(2 * nb) * C, st->prelu_up,
                        Hm, Wm, 2 * nb, 0, 0, st->err, 1, kWinCell};
-        e = launch_conv<MODE_SHUFFLE>(w->tm_act[cur], st->tm_w, w->tm_out[cur] /* unused */, au, 4, s);
+        e = launch_conv<MODE_SHUFFLE>(w->tm_act[cur], st->tm_w, w->tm_fine, w->tm_out[cur], au, 4, s);
     }
     if (e == cudaSuccess) {
         const size_t pts = (size_t)(nc / 2) * (nc / 2) * 16;
@@ -1409,10 +1603,11 @@ mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip
         snprintf(err, errlen, "sr_conv_layer: bad mode %d or size %dx%d (W a multiple of %d)", mode, H, W, TM);
         return MG_ERR_INVALID_ARG;
     }
-    CUtensorMap tin, tw, tout;
+    CUtensorMap tin, tw, tout, tskip;
     const int groups = mode == MODE_SHUFFLE ? 4 : 1;
     if (!make_act_map(&tin, const_cast<void *>(in), H, W) || !make_w_map(&tw, const_cast<void *>(w_packed), groups) ||
-        !(mode == MODE_SHUFFLE ? make_act_map(&tout, const_cast<void *>(in), H, W) : make_out_map(&tout, out, H, W))) {
+        !(mode == MODE_SHUFFLE ? make_fine_map(&tout, out, 2 * H + 2, W) : make_out_map(&tout, out, H, W)) ||
+        !make_out_map(&tskip, const_cast<void *>(mode == MODE_RESID ? skip : in), H, W)) {
         snprintf(err, errlen, "sr_conv_layer: tensor map encoding failed");
         return MG_ERR_INVALID_ARG;
     }
@@ -1422,9 +1617,9 @@ mg_status sr_conv_layer(int mode, int H, int W, const void *in, const void *skip
     if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(int), s);
     ConvArgs a = {(const __nv_bfloat16 *)skip, (__nv_bfloat16 *)out, bias, prelu, H, W, 0, 0, 0, dflag};
     if (e == cudaSuccess) {
-        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, tw, tout, a, 1, s);
-        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, tw, tout, a, 1, s);
-        else e = launch_conv<MODE_SHUFFLE>(tin, tw, tout, a, 4, s);
+        if (mode == MODE_PRELU) e = launch_conv<MODE_PRELU>(tin, tw, tout, tskip, a, 1, s);
+        else if (mode == MODE_RESID) e = launch_conv<MODE_RESID>(tin, tw, tout, tskip, a, 1, s);
+        else e = launch_conv<MODE_SHUFFLE>(tin, tw, tout, tskip, a, 4, s);
     }
     int flag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);

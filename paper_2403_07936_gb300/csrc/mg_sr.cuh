@@ -51,6 +51,7 @@ struct SrState {
     int *err = nullptr;                          // device error flag (bounded waits)
     CUtensorMap tm_act[3];  // activation buffers as convolution inputs (row planes)
     CUtensorMap tm_out[3];  // the same buffers as destinations of output tiles
+    CUtensorMap tm_fine;    // fine_act as the destination of the pixel-shuffle layer
     CUtensorMap tm_w;
 };
 
@@ -68,6 +69,7 @@ struct SrBatch {
     const float **ecs = nullptr;  // [imgs] device pointers to the coarse errors (device table)
     CUtensorMap tm_act[3];
     CUtensorMap tm_out[3];
+    CUtensorMap tm_fine;
 };
 // Allocate for imgs coarse errors of nc x nc at the device addresses ecs[]
 // (host array of device pointers; copied).  Outside any stream capture.
@@ -85,6 +87,7 @@ struct SrWindows {
     void *fine_act = nullptr;
     CUtensorMap tm_act[3];
     CUtensorMap tm_out[3];
+    CUtensorMap tm_fine;
 };
 // Allocate for coarse grids of nc (a power of two >= 32); outside capture.
 mg_status sr_windows_prepare(SrWindows *w, int nc, char *err, size_t errlen);
