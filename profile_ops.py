@@ -9,13 +9,16 @@ small, self-contained command line; the inputs are random, since only the
 memory traffic and the instruction mix are of interest.
 
 ops:
-  down   finest-level k_down (nu sweeps, residual, full weighting), FP32
+  down   finest-level k_down (nu sweeps, residual, full weighting), FP32 or
+         FP64 (--dtype)
   up     finest-level k_up (cubic prolongation, correction, nu sweeps), FP32
+         or FP64 (--dtype)
   outer  outer residual of FP64 data (exact stencil sum) with norms, float output
   conv   one tensor-core SR convolution layer (mode 0: conv + PReLU) on an
          n/2 x n/2 coarse grid of 64 channels
-  solve  a whole mixed-precision solve of a seeded turbulent source (host-loop
-         execution, so every kernel is a separate launch); time per solve
+  solve  a whole solve of a seeded turbulent source (host-loop execution, so
+         every kernel is a separate launch), mixed or FP64 (--precision);
+         time per solve
   link   the host link: copies of n x n FP64 arrays between pinned host memory
          and the device with cudaMemcpyAsync - host to device (f and x, as a
          solve from host buffers stages them), device to host (x), and both
@@ -38,6 +41,8 @@ def main():
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32", help="down / up: element type")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="solve: precision")
     args = ap.parse_args()
 
     import torch
@@ -52,11 +57,12 @@ def main():
         link_bandwidth(n, max(args.reps, 10))
         return
     if args.op in ("down", "up"):
-        x = torch.randn((n, n), device=dev, generator=g)
+        dt = torch.float64 if args.dtype == "f64" else torch.float32
+        x = torch.randn((n, n), device=dev, generator=g, dtype=dt)
         xo = torch.empty_like(x)
-        b = torch.randn((n, n), device=dev, generator=g)
-        bc = torch.empty((n // 2, n // 2), device=dev)
-        ec = torch.randn((n // 2, n // 2), device=dev, generator=g)
+        b = torch.randn((n, n), device=dev, generator=g, dtype=dt)
+        bc = torch.empty((n // 2, n // 2), device=dev, dtype=dt)
+        ec = torch.randn((n // 2, n // 2), device=dev, generator=g, dtype=dt)
         if args.op == "down":
             def run():
                 mg.op_down(x, xo, b, bc, nu=args.nu)
@@ -75,7 +81,7 @@ def main():
         import math
 
         from synthetic.sources import default_kmax, turbulent_source
-        ctx = mg.Context(int(math.log2(n // 8)) + 1, n)
+        ctx = mg.Context(int(math.log2(n // 8)) + 1, n, precision=args.precision)
         ctx.set_graph_execution(False)
         f = torch.tensor(turbulent_source(n, default_kmax(n), 1), device=dev)
         x = torch.zeros_like(f)
