@@ -1226,6 +1226,29 @@ __global__ void __launch_bounds__(kRedThreads) k_sum(const double *__restrict__ 
     reduce_finish<1>(red, vals, sh);
 }
 
+// The same sum on 16-byte-aligned data (N a multiple of 4): two 16-byte loads
+// per thread and iteration, four groups in flight, so that enough loads are
+// outstanding to cover the memory latency (the scalar form is latency-bound).
+__global__ void __launch_bounds__(kRedThreads) k_sum_v(const double *__restrict__ a, size_t N, Reduction red) {
+    pdl_enter();
+    __shared__ double sh[32];
+    double v = 0.0;
+    const size_t G = N >> 1, stride = (size_t)gridDim.x * blockDim.x;
+    const double2 *a2 = reinterpret_cast<const double2 *>(a);
+    for (size_t g0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g0 < G; g0 += kUnroll * stride) {
+        double2 t[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const size_t g = g0 + u * stride;
+            t[u] = g < G ? a2[g] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) v += t[u].x + t[u].y;
+    }
+    double vals[1] = {block_sum(v, sh)};
+    reduce_finish<1>(red, vals, sh);
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_scaled_rhs(const double *__restrict__ f, int n,
                                                             double h2, const double *__restrict__ fsum,
                                                             double *__restrict__ b) {
@@ -1573,6 +1596,31 @@ __global__ void __launch_bounds__(kRedThreads) k_project(double *__restrict__ x,
     const double mu = *sum / (double)N;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
         x[p] = zero ? 0.0 : x[p] - mu;
+}
+
+// The same projection on 16-byte-aligned x (N a multiple of 4), two 16-byte
+// words per thread and iteration.
+__global__ void __launch_bounds__(kRedThreads) k_project_v(double *__restrict__ x, size_t N,
+                                                           const double *__restrict__ sum,
+                                                           const int *__restrict__ zero_flag) {
+    pdl_enter();
+    const bool zero = zero_flag && *zero_flag;
+    const double mu = *sum / (double)N;
+    double2 *x2 = reinterpret_cast<double2 *>(x);
+    const size_t G = N >> 1, stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t g0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g0 < G; g0 += 2 * stride) {
+        double2 t[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const size_t g = g0 + u * stride;
+            if (g < G) t[u] = x2[g];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const size_t g = g0 + u * stride;
+            if (g < G) x2[g] = zero ? make_double2(0.0, 0.0) : make_double2(t[u].x - mu, t[u].y - mu);
+        }
+    }
 }
 
 __global__ void k_check(DevState *st, const double *rsum, const double *usum, const double *fsum,
@@ -2055,8 +2103,10 @@ template cudaError_t launch_bottom<double>(double *, const double *, int, int, i
 
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s) {
     {
-        cudaError_t le_ = launch_kernel(k_sum, kRedBlocks, kRedThreads, 0, s,
-                                        f, (size_t)n * n, red);
+        const size_t N = (size_t)n * n;
+        const bool vec = (reinterpret_cast<uintptr_t>(f) & 15) == 0 && N % 4 == 0;
+        cudaError_t le_ = vec ? launch_kernel(k_sum_v, kWideBlocks, kRedThreads, 0, s, f, N, red)
+                              : launch_kernel(k_sum, kRedBlocks, kRedThreads, 0, s, f, N, red);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);
@@ -2164,8 +2214,10 @@ cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaS
 }
 cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag) {
     {
-        cudaError_t le_ = launch_kernel(k_project, kRedBlocks, kRedThreads, 0, s,
-                                        x, (size_t)n * n, sum, zero_flag);
+        const size_t N = (size_t)n * n;
+        const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0 && N % 4 == 0;
+        cudaError_t le_ = vec ? launch_kernel(k_project_v, kWideBlocks, kRedThreads, 0, s, x, N, sum, zero_flag)
+                              : launch_kernel(k_project, kRedBlocks, kRedThreads, 0, s, x, N, sum, zero_flag);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);

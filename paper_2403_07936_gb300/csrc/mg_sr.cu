@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(kRedThreads) k_absmax(const float *__restrict_
 // wt: the layer's weights staged as [tap][64 channels] (tap 9 = bias, 10 =
 // PReLU slope), read four channels per 16-byte broadcast load.
 __device__ __forceinline__ void conv_in_px(const float *__restrict__ ec, int nc, float s, const float4 *wt, int y,
-                                           int x, uint4 *outv) {
+                                           int x, uint4 *outv, int swz) {
     float q[9];
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky)
@@ -672,7 +672,7 @@ __device__ __forceinline__ void conv_in_px(const float *__restrict__ ec, int nc,
             const __nv_bfloat162 bb = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
             w4[k] = *reinterpret_cast<const uint32_t *>(&bb);
         }
-        outv[i] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        outv[i ^ swz] = make_uint4(w4[0], w4[1], w4[2], w4[3]);  // straight to the staging row
     }
 }
 
@@ -683,6 +683,15 @@ __device__ __forceinline__ void stage_in_weights(float *w, const float *__restri
         const int t = i / C, c = i - t * C;
         w[i] = t < 9 ? wpack[c * 9 + t] : wpack[C * 9 + (t - 9) * C + c];
     }
+}
+
+// The halo copies of this thread's edge pixel, read back from its staging row.
+__device__ __forceinline__ void conv_in_halo(const uint4 *st, __nv_bfloat16 *__restrict__ out, int nc, int y,
+                                             int x) {
+    uint4 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = st[threadIdx.x * 8 + (i ^ (threadIdx.x & 7))];
+    store_px(out, nc, nc, y, x, v, true);
 }
 
 // Write the block's 256 staged pixels (p0 .. p0 + 255 of an nc x nc grid, all
@@ -706,23 +715,30 @@ __global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ ec, i
     __syncthreads();
     const int p0 = blockIdx.x * 256, p = p0 + threadIdx.x;  // nc * nc is a multiple of 256
     const int y = p / nc, x = p - y * nc;
-    uint4 outv[8];
-    conv_in_px(ec, nc, *s_ptr, reinterpret_cast<const float4 *>(w), y, x, outv);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) st[threadIdx.x * 8 + (i ^ (threadIdx.x & 7))] = outv[i];
-    if (x == 0 || x == nc - 1 || y == 0 || y == nc - 1) store_px(out, nc, nc, y, x, outv, true);
+    conv_in_px(ec, nc, *s_ptr, reinterpret_cast<const float4 *>(w), y, x, st + threadIdx.x * 8, threadIdx.x & 7);
+    if (x == 0 || x == nc - 1 || y == 0 || y == nc - 1) conv_in_halo(st, out, nc, y, x);
     __syncthreads();
     conv_in_flush(st, out, nc, p0);
 }
 
 // conv3x3 64 -> 1 on the padded fine activation, + bias, times s:
-// fine_out = s * G.  A 16 x 16 tile of outputs stages its 18 x 18 x 64 window
-// in shared memory; warp w computes the 32 outputs of tile rows 2w, 2w + 1
-// with its lanes split over pixels and channels (conv_out_warp), each
-// accumulating the even and odd channel sums of an output as one packed
-// FP32 pair.
-constexpr int OUT_T = 16;
-constexpr int OUT_TP = OUT_T + 2;
+// fine_out = s * G.  A block walks a strip of 32 output columns down
+// OUT_ROWS rows with four warps, two output rows per step; the 34-pixel input
+// rows it needs stream through a ring of six shared-memory rows (cp.async),
+// the next step's two rows loading while the current step computes, so every
+// input pixel is read from memory about once (1.06 times with the strip's
+// halo columns).  A warp takes 16 outputs of one row with its lanes split over
+// the channels (lane l holds channels 2l, 2l + 1: a pixel's 128 bytes are one
+// conflict-free 32-word shared load); each staged pixel of the output row's
+// three input rows is loaded once and feeds the three outputs it is a
+// horizontal tap of, each output accumulating its even and odd channel sums
+// as one packed FP32 pair; a transposing butterfly over the lanes then gives
+// lanes 2j and 2j + 1 output j.
+constexpr int OUT_W = 32;             // strip width (output columns)
+constexpr int OUT_ROWS = 32;          // output rows per block
+constexpr int OUT_RING = 6;           // staged input rows
+constexpr int OUT_PX = OUT_W + 2;     // staged pixels per row
+constexpr int OUT_THREADS = 128;
 
 __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
                                                     unsigned long long c) {
@@ -733,78 +749,96 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Stage padded pixels [y0, y0 + 18) x [x0, x0 + 18) of u (row pitch nf + 2) into tile.
-__device__ __forceinline__ void stage_out_tile(uint4 *tile, const __nv_bfloat16 *__restrict__ u, int nf, int y0,
-                                               int x0) {
-    for (int i = threadIdx.x; i < OUT_TP * OUT_TP * 8; i += blockDim.x) {
-        const int px = i >> 3, part = i & 7;
-        const int ry = px / OUT_TP, rx = px - ry * OUT_TP;
-        tile[i] = reinterpret_cast<const uint4 *>(u + ((size_t)(y0 + ry) * (nf + 2) + (x0 + rx)) * C)[part];
-    }
+// Stage padded input row py (pixels x0 .. x0 + 33 of a row of nf + 2) into ring slot py % OUT_RING.
+__device__ __forceinline__ void out_stage_row(uint4 *ring, const __nv_bfloat16 *__restrict__ u, int nf, int py,
+                                              int x0) {
+    uint4 *dst = ring + (py % OUT_RING) * OUT_PX * 8;
+    const uint4 *src = reinterpret_cast<const uint4 *>(u + ((size_t)py * (nf + 2) + x0) * C);
+    for (int i = threadIdx.x; i < OUT_PX * 8; i += OUT_THREADS) cp_async16(dst + i, src + i);
 }
 
-// The 32 outputs of warp w's two tile rows (tile row 2w + j / 16, column
-// j % 16, before bias and scale).  Lane l holds channels 2l, 2l + 1: a
-// pixel's 128 bytes are one conflict-free 32-word shared load.  Each staged
-// pixel of the three input rows of an output row is loaded once and feeds
-// the three outputs it is a horizontal tap of (54 loads per output row
-// instead of 144), each output accumulating its even and odd channel sums as
-// one packed FP32 pair; a transposing butterfly over the lanes then leaves
-// output j's total in lane j, which is returned with its index.
-__device__ __forceinline__ float conv_out_warp(const uint4 *tile, const float *__restrict__ wpack, int w, int lane,
-                                               int *jout) {
-    const uint32_t *t32 = reinterpret_cast<const uint32_t *>(tile);
-    unsigned long long wp[9];
+// The 16 outputs (before bias and scale) of one output row segment: staged
+// rows py .. py + 2 (ring), pixels c0 .. c0 + 17 of the staged rows.  Lanes
+// 2j and 2j + 1 return output j.
+__device__ __forceinline__ float out_row16(const uint4 *ring, int py, int c0, const unsigned long long (&wp)[9],
+                                           int lane) {
+    const uint32_t *t32 = reinterpret_cast<const uint32_t *>(ring);
+    unsigned long long acc[16];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) wp[t] = pack2(wpack[t * C + 2 * lane], wpack[t * C + 2 * lane + 1]);
-    unsigned long long acc[32];
+    for (int j = 0; j < 16; ++j) acc[j] = 0ull;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0ull;
+    for (int dy = 0; dy < 3; ++dy) {
+        const uint32_t *row = t32 + ((py + dy) % OUT_RING) * OUT_PX * 32;
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+        for (int xp = 0; xp < 18; ++xp) {
+            const uint32_t v = row[(c0 + xp) * 32 + lane];
+            const unsigned long long vv = (unsigned long long)(v << 16) | ((unsigned long long)(v & 0xffff0000u) << 32);
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int xp = 0; xp < OUT_TP; ++xp) {
-                const uint32_t v = t32[((2 * w + r + dy) * OUT_TP + xp) * 32 + lane];
-                const unsigned long long vv =
-                    (unsigned long long)(v << 16) | ((unsigned long long)(v & 0xffff0000u) << 32);
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const int tx = xp - kx;
-                    if (tx >= 0 && tx < OUT_T) acc[r * 16 + tx] = ffma2(wp[dy * 3 + kx], vv, acc[r * 16 + tx]);
-                }
+            for (int kx = 0; kx < 3; ++kx) {
+                const int tx = xp - kx;
+                if (tx >= 0 && tx < 16) acc[tx] = ffma2(wp[dy * 3 + kx], vv, acc[tx]);
             }
-    float a[32];
+        }
+    }
+    float a[16];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) a[j] = __uint_as_float((uint32_t)acc[j]) + __uint_as_float((uint32_t)(acc[j] >> 32));
+    for (int j = 0; j < 16; ++j) a[j] = __uint_as_float((uint32_t)acc[j]) + __uint_as_float((uint32_t)(acc[j] >> 32));
+    // lanes' bits 4 .. 1 select the output bits 3 .. 0; bit 0 pairs two lanes
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
+    for (int off = 16, half = 8; off >= 2; off >>= 1, half >>= 1) {
         const bool upper = (lane & off) != 0;
 #pragma unroll
-        for (int i = 0; i < off; ++i) {
-            const float send = upper ? a[i] : a[i + off];
-            const float keep = upper ? a[i + off] : a[i];
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? a[i] : a[i + half];
+            const float keep = upper ? a[i + half] : a[i];
             a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
-    *jout = lane;
-    return a[0];
+    return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
-__global__ void __launch_bounds__(256) k_conv_out(const __nv_bfloat16 *__restrict__ u, int nf,
-                                                  const float *__restrict__ wpack,  // w[9][64], b
-                                                  const float *__restrict__ s_ptr,
-                                                  float *__restrict__ fine_out) {
-    __shared__ uint4 tile[OUT_TP * OUT_TP * 8];
-    const int y0 = blockIdx.y * OUT_T, x0 = blockIdx.x * OUT_T;
-    stage_out_tile(tile, u, nf, y0, x0);
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int j;
-    const float g = conv_out_warp(tile, wpack, w, lane, &j);
-    fine_out[(size_t)(y0 + 2 * w + (j >> 4)) * nf + x0 + (j & 15)] = (*s_ptr) * (g + wpack[9 * C]);
+// Block (bx, by [, image bz]): output columns bx * 32 .., rows by * OUT_ROWS ..
+__device__ __forceinline__ void conv_out_strip(const __nv_bfloat16 *__restrict__ u, int nf,
+                                               const float *__restrict__ wpack, float s,
+                                               float *__restrict__ fine_out, uint4 *ring) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * OUT_W, y0 = blockIdx.y * OUT_ROWS;
+    unsigned long long wp[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) wp[t] = pack2(wpack[t * C + 2 * lane], wpack[t * C + 2 * lane + 1]);
+    const float bias = wpack[9 * C];
+    // output row y needs padded rows y .. y + 2; a step computes rows r, r + 1
+    for (int p = 0; p < 4; ++p) out_stage_row(ring, u, nf, y0 + p, x0);
+    cp_async_commit();
+    for (int r = 0; r < OUT_ROWS; r += 2) {
+        if (r + 2 < OUT_ROWS) {  // the next step's two new rows
+            out_stage_row(ring, u, nf, y0 + r + 4, x0);
+            out_stage_row(ring, u, nf, y0 + r + 5, x0);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();  // everything but the group just issued
+        __syncthreads();
+        const int ry = r + (w >> 1), c0 = (w & 1) * 16;
+        const float g = out_row16(ring, y0 + ry, c0, wp, lane);
+        if ((lane & 1) == 0) fine_out[(size_t)(y0 + ry) * nf + x0 + c0 + (lane >> 1)] = s * (g + bias);
+        __syncthreads();  // the ring slots of rows r, r + 1 are free for the step after next
+    }
+    cp_async_wait<0>();
+}
+
+__global__ void __launch_bounds__(OUT_THREADS) k_conv_out(const __nv_bfloat16 *__restrict__ u, int nf,
+                                                          const float *__restrict__ wpack,  // w[9][64], b
+                                                          const float *__restrict__ s_ptr,
+                                                          float *__restrict__ fine_out) {
+    __shared__ uint4 ring[OUT_RING * OUT_PX * 8];
+    conv_out_strip(u, nf, wpack, *s_ptr, fine_out, ring);
 }
 
 // Batched forms for a stack of equal-size images (image = blockIdx.y, or
@@ -839,29 +873,20 @@ __global__ void __launch_bounds__(256) k_conv_in_b(const float *const *__restric
     __nv_bfloat16 *o = out + (size_t)blockIdx.y * (nc + 2) * (nc + 2) * C;
     const int p0 = blockIdx.x * 256, p = p0 + threadIdx.x;
     const int y = p / nc, x = p - y * nc;
-    uint4 outv[8];
-    conv_in_px(ec, nc, s_all[blockIdx.y], reinterpret_cast<const float4 *>(w), y, x, outv);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) st[threadIdx.x * 8 + (i ^ (threadIdx.x & 7))] = outv[i];
-    if (x == 0 || x == nc - 1 || y == 0 || y == nc - 1) store_px(o, nc, nc, y, x, outv, true);
+    conv_in_px(ec, nc, s_all[blockIdx.y], reinterpret_cast<const float4 *>(w), y, x, st + threadIdx.x * 8,
+               threadIdx.x & 7);
+    if (x == 0 || x == nc - 1 || y == 0 || y == nc - 1) conv_in_halo(st, o, nc, y, x);
     __syncthreads();
     conv_in_flush(st, o, nc, p0);
 }
 
-__global__ void __launch_bounds__(256) k_conv_out_b(const __nv_bfloat16 *__restrict__ u_all, int nf,
-                                                    const float *__restrict__ wpack,
-                                                    const float *__restrict__ s_all,
-                                                    float *__restrict__ out_all) {
-    __shared__ uint4 tile[OUT_TP * OUT_TP * 8];
-    const __nv_bfloat16 *u = u_all + (size_t)blockIdx.z * (nf + 2) * (nf + 2) * C;
-    float *fine_out = out_all + (size_t)blockIdx.z * nf * nf;
-    const int y0 = blockIdx.y * OUT_T, x0 = blockIdx.x * OUT_T;
-    stage_out_tile(tile, u, nf, y0, x0);
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int j;
-    const float g = conv_out_warp(tile, wpack, w, lane, &j);
-    fine_out[(size_t)(y0 + 2 * w + (j >> 4)) * nf + x0 + (j & 15)] = s_all[blockIdx.z] * (g + wpack[9 * C]);
+__global__ void __launch_bounds__(OUT_THREADS) k_conv_out_b(const __nv_bfloat16 *__restrict__ u_all, int nf,
+                                                            const float *__restrict__ wpack,
+                                                            const float *__restrict__ s_all,
+                                                            float *__restrict__ out_all) {
+    __shared__ uint4 ring[OUT_RING * OUT_PX * 8];
+    conv_out_strip(u_all + (size_t)blockIdx.z * (nf + 2) * (nf + 2) * C, nf, wpack, s_all[blockIdx.z],
+                   out_all + (size_t)blockIdx.z * nf * nf, ring);
 }
 
 // ---------------------------------------------------------------------------
@@ -1360,8 +1385,8 @@ mg_status sr_correction(SrState *st, const float *ec, int nc, cudaStream_t s, ch
     }
     if (e == cudaSuccess) {
         const int nf = 2 * nc;
-        dim3 grid(nf / OUT_T, nf / OUT_T);
-        k_conv_out<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)st->fine_act, nf, st->w_out, st->scal,
+        dim3 grid(nf / OUT_W, nf / OUT_ROWS);
+        k_conv_out<<<grid, OUT_THREADS, 0, s>>>((const __nv_bfloat16 *)st->fine_act, nf, st->w_out, st->scal,
                                                   st->fine_out);
         count_launches(1);
         e = cudaGetLastError();
@@ -1414,8 +1439,8 @@ mg_status sr_layer(SrState *st, int layer, int nc, const void *in, const void *s
         else e = launch_conv<MODE_SHUFFLE>(tin, st->tm_w, tout, tskip, a, 4, strm);
     } else if (e == cudaSuccess) {
         const int nf = 2 * nc;
-        dim3 grid(nf / OUT_T, nf / OUT_T);
-        k_conv_out<<<grid, 256, 0, strm>>>((const __nv_bfloat16 *)in, nf, st->w_out, s, (float *)out);
+        dim3 grid(nf / OUT_W, nf / OUT_ROWS);
+        k_conv_out<<<grid, OUT_THREADS, 0, strm>>>((const __nv_bfloat16 *)in, nf, st->w_out, s, (float *)out);
         count_launches(1);
         e = cudaGetLastError();
     }
@@ -1503,7 +1528,7 @@ mg_status sr_batch_correction(SrBatch *b, const SrState *st, cudaStream_t s, cha
     }
     if (e == cudaSuccess) {
         const int nf = 2 * nc;
-        k_conv_out_b<<<dim3(nf / OUT_T, nf / OUT_T, imgs), 256, 0, s>>>(
+        k_conv_out_b<<<dim3(nf / OUT_W, nf / OUT_ROWS, imgs), OUT_THREADS, 0, s>>>(
             (const __nv_bfloat16 *)b->fine_act, nf, st->w_out, b->s, b->fine_out);
         count_launches(1);
         e = cudaGetLastError();

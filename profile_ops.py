@@ -16,6 +16,8 @@ ops:
   outer  outer residual of FP64 data (exact stencil sum) with norms, float output
   conv   one tensor-core SR convolution layer (mode 0: conv + PReLU) on an
          n/2 x n/2 coarse grid of 64 channels
+  generator  the whole SR generator (seeded weights) on an n/2 x n/2 coarse
+         error: s = max|e|, conv 1->64, the tensor-core layers, conv 64->1
   solve  a whole solve of a seeded turbulent source (host-loop execution, so
          every kernel is a separate launch), mixed or FP64 (--precision);
          time per solve
@@ -37,7 +39,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["down", "up", "outer", "conv", "solve", "link"], required=True)
+    ap.add_argument("--op", choices=["down", "up", "outer", "conv", "generator", "solve", "link"], required=True)
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
@@ -89,6 +91,18 @@ def main():
         def run():
             x.zero_()
             ctx.solve(f, x)
+    elif args.op == "generator":
+        import math
+
+        from paper_2403_07936_gb300 import sr
+        from synthetic.weights import random_weights
+        ctx = mg.Context(int(math.log2(n // 8)) + 1, n)
+        ctx.load_weights(sr.pack_weights(random_weights(3, gain=0.5)))
+        ec = torch.randn((n // 2, n // 2), device=dev, generator=g) * 1e-3
+        out = torch.empty((n, n), device=dev)
+
+        def run():
+            mg.op_sr_generator(ctx, ec, out)
     else:
         H = W = n // 2
         xin = torch.randn((H + 2, W + 2, 64), device=dev, generator=g).to(torch.bfloat16)
