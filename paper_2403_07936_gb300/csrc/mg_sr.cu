@@ -1341,6 +1341,7 @@ mg_status sr_view(SrState *view, const SrState *st, int nc, char *err, size_t er
     }
     v.fine_act = view->fine_act;
     v.fine_out = view->fine_out;
+    v.tm_fine = view->tm_fine;  // the view's own fine map (st's maps describe st's buffers)
     v.nc = view->view ? view->nc : 0;
     cudaError_t e = prepare_conv();
     if (e == cudaSuccess) e = ensure_buffers(&v, nc);

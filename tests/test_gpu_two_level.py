@@ -131,6 +131,11 @@ def test_sr_x16_solve_with_trained_generator(mg, n_gan):
     if not isr["sr_fallback"]:
         assert isr["sr_cycles"] == (cyc if n_gan == float("inf") else (cyc + 1) // 2)
     assert omg.relative_residual(f - f.mean(), xs.cpu().numpy(), omg.grid_h(n)) <= 1.5 * isr["rel_residual"]
+    # a second SR solve on the same context reuses the stages' generator
+    # buffers (and their tensor maps): the same bits
+    xs2 = torch.zeros_like(ft)
+    isr2 = ctx.two_level_solve(ft, xs2, max_cycles=cyc, prolong="sr", check=False)
+    assert torch.equal(xs, xs2) and isr2["sr_cycles"] == isr["sr_cycles"]
 
 
 def test_sr_x16_needs_weights_and_a_coarse_grid_of_128(mg):
