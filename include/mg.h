@@ -295,7 +295,14 @@ mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);
  * master weights, Adam moments (beta1 0.9, beta2 0.999, eps 1e-8) and the
  * activations of one batch of `batch` periodic coarse fields of H x W (powers
  * of two >= 8; batch * H * W a multiple of 2048, at most 2^24); every
- * forward and backward convolution runs in the library's own FP32 kernels.
+ * forward and backward convolution runs in the library's own kernels.  When
+ * W is a multiple of 128 the 64- and 256-channel convolutions (forward, data
+ * gradient, weight gradient) run on the tcgen05 tensor cores by default, with
+ * BF16 operands (activations and the FP32 master weights rounded to nearest
+ * even) and FP32 accumulation; the thin first and last layers, PReLU, the
+ * loss and Adam stay in FP32.  Otherwise, or after
+ * mg_trainer_set_tensor_cores(tr, 0), every convolution runs in FP32 on the
+ * CUDA cores.
  * Inputs are device arrays: q [batch][H][W] (the normalised coarse error
  * e_c / s), target [batch][2H][2W] (the generator's target, e.g.
  * (e_f - cubic(e_c)) / s), mask [batch][2H][2W] or NULL (per-pixel weights of
@@ -318,6 +325,15 @@ mg_status mg_trainer_step(mg_trainer *tr, const float *q, const float *target, c
                           double *loss);
 /* Set the Adam learning rate (lr > 0) for the following steps. */
 mg_status mg_trainer_set_lr(mg_trainer *tr, double lr);
+/* Choose the convolution arithmetic of the following passes (Sec. 3.2 trains
+ * the generator; the precision is this library's choice): on != 0 = BF16
+ * operands on the tcgen05 tensor cores (MG_ERR_INVALID_ARG unless W is a
+ * multiple of 128), 0 = FP32 on the CUDA cores.  A tensor-core pass whose
+ * bounded wait on its MMAs runs out makes the call that ran it return
+ * MG_ERR_TIMEOUT. */
+mg_status mg_trainer_set_tensor_cores(mg_trainer *tr, int on);
+/* *on = 1 if the trainer's convolutions run on the tensor cores, else 0. */
+mg_status mg_trainer_get_tensor_cores(mg_trainer *tr, int *on);
 /* Current weights as a blob (bytes = 64 + 4 * n_params). */
 mg_status mg_trainer_get_weights(mg_trainer *tr, void *blob, size_t bytes);
 /* Free the trainer and its device memory; NULL is ignored. */

@@ -74,6 +74,8 @@ SIGNATURES = {
     "mg_trainer_gradients": (_I, [_VP, _VP, _VP, _VP, _VP, C.POINTER(_D)]),
     "mg_trainer_step": (_I, [_VP, _VP, _VP, _VP, C.POINTER(_D)]),
     "mg_trainer_set_lr": (_I, [_VP, _D]),
+    "mg_trainer_set_tensor_cores": (_I, [_VP, _I]),
+    "mg_trainer_get_tensor_cores": (_I, [_VP, C.POINTER(_I)]),
     "mg_trainer_get_weights": (_I, [_VP, _VP, _SZ]),
     "mg_trainer_destroy": (None, [_VP]),
     "mg_status_string": (C.c_char_p, [_I]),
@@ -371,6 +373,17 @@ class Trainer:
 
     def set_lr(self, lr: float):
         _check(load().mg_trainer_set_lr(self._h, lr))
+
+    @property
+    def tensor_cores(self) -> bool:
+        """True if the 64/256-channel convolutions run on the tcgen05 tensor cores (BF16 operands)."""
+        v = _I()
+        _check(load().mg_trainer_get_tensor_cores(self._h, C.byref(v)))
+        return bool(v.value)
+
+    @tensor_cores.setter
+    def tensor_cores(self, on: bool):
+        _check(load().mg_trainer_set_tensor_cores(self._h, int(bool(on))))
 
     def weights(self) -> bytes:
         buf = C.create_string_buffer(self.nbytes)
