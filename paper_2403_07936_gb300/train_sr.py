@@ -23,7 +23,9 @@ so the loss mask keeps only the fine pixels whose receptive field (the
 generator's reach, 2 n_blocks + 3 coarse cells) stays inside the crop.
 
 Every step of the pair generation runs in the library (mg_solve, mg_vcycle,
-mg_op_down, mg_op_up), and the training in its trainer kernels; torch only
+mg_op_down, mg_op_up), and the training in its trainer kernels (the
+convolutions on the tcgen05 tensor cores with bf16 operands, the trainer's
+default for 128-pixel crops); torch only
 holds device memory and does casts, crops and the symmetry augmentation (the
 eight rotations / reflections of the square and even shifts, which map red
 points to red points and coarse node I to fine node 2I, so they are
@@ -224,7 +226,9 @@ def train(args):
                "pairs_val": int(q_va.shape[0]), "pairs_val_by_size": {str(k): v for k, v in n_va.items()},
                "cycles_per_source": args.cycles, "steps": args.steps, "batch": args.batch, "lr": args.lr,
                "pair_generation_s": t_pairs, "train_s": train_s,
-               "train_tflops": flop_step * args.steps / train_s / 1e12,
+               "train_tflops": flop_step * args.steps / train_s / 1e12, "tensor_cores": tr.tensor_cores,
+               "gemm_arithmetic": ("tcgen05 tensor cores, bf16 operands, fp32 accumulation" if tr.tensor_cores
+                                   else "fp32 on the CUDA cores"),
                "val_ratio_initial": log[0]["val_ratio"], "val_ratio_final": log[-1]["val_ratio"], "log": log}
     with open(args.out + ".json", "w") as fp:
         json.dump(summary, fp, indent=1)
