@@ -285,6 +285,19 @@ mg_status mg_autotune(mg_ctx *ctx, const char *cache_path, int *n_timed);
 mg_status mg_set_launch_overlap(int enable);
 int mg_get_launch_overlap(void);
 
+/* Staging of the smoother's tiles (Algorithm 6, relax / residual / restrict:
+ * the down pass of a level, red-black sweeps, residual and full weighting on
+ * one shared-memory tile with its halo).  on = 1: single solves stage every
+ * interior 64-row tile of an FP32 level with V(2, .) by TMA (tiled 2D copies
+ * of the x and b tiles with their halo into shared memory, split there into
+ * the red and black arrays); tiles whose halo wraps around the periodic grid
+ * keep the 16-byte vector loads.  on = 0 (the default): vector loads for
+ * every tile.  Results are identical bit for bit; graphs recorded before a
+ * change are re-recorded.  A TMA wait that runs out makes the solve return
+ * MG_ERR_TIMEOUT.  MG_ERR_INVALID_ARG for other values. */
+mg_status mg_set_tma_tiles(int on);
+int mg_get_tma_tiles(void);
+
 /* Read or set one table entry (n a power of two >= 128, nu 0..4). */
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant);
 mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);

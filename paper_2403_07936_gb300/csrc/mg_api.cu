@@ -168,6 +168,10 @@ struct mg_ctx {
     int *d_srflag = nullptr;             // device: the current V-cycle uses SR
     cudaStream_t cap_stream = nullptr;  // private stream used only for recording graphs
     DevState *dstate = nullptr, *hstate = nullptr;
+    // 2D tensor maps of each FP32 level's x and b with the TMA-staged k_down
+    // tile as box (levels of >= 128 points a side; tm_ok when encoded)
+    CUtensorMap tm_x32[kMaxLevels], tm_b32[kMaxLevels];
+    bool tm_ok[kMaxLevels] = {};
     SolveGraph graphs[kGraphCache];
     unsigned long long graph_clock = 0;
     // optional CUDA-event probe around one kernel kind (instrumentation)
@@ -253,6 +257,13 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
     }
     if (!fp64) c->bsc64 = (double *)((char *)blk + bsc_off);
     if (tasks) c->ebt = (int *)((char *)blk + ebt_off);
+    if (!fp64) {
+        int bc = 0, br = 0;
+        down_tma_box(2, &bc, &br);
+        for (int l = 0; l < c->levels; ++l)
+            c->tm_ok[l] = c->lv[l].n >= 128 && make_grid_map_f32(&c->tm_x32[l], c->lv[l].x32, c->lv[l].n, bc, br) &&
+                          make_grid_map_f32(&c->tm_b32[l], c->lv[l].b32, c->lv[l].n, bc, br);
+    }
     return MG_OK;
 }
 
@@ -311,6 +322,23 @@ template <typename T> static const T *ainv(mg_ctx *c);
 template <> const float *ainv<float>(mg_ctx *c) { return c->ainv32; }
 template <> const double *ainv<double>(mg_ctx *c) { return c->ainv64; }
 
+// The down pass of level l (x -> t, restricted residual -> bc).  FP32 levels
+// on 64-row tiles with V(2, .) take the TMA-staged kernel when TMA tiles are
+// on (mg_set_tma_tiles) and the level's maps describe these buffers.
+template <typename T>
+static cudaError_t down_level(mg_ctx *c, int l, const T *x, T *t, const T *b, bool zero, T *bc, cudaStream_t s) {
+    return launch_down<T>(x, t, b, c->lv[l].n, c->nu1, zero, bc, s);
+}
+template <>
+cudaError_t down_level<float>(mg_ctx *c, int l, const float *x, float *t, const float *b, bool zero, float *bc,
+                              cudaStream_t s) {
+    const int n = c->lv[l].n;
+    if (tma_tiles_mode() && c->tm_ok[l] && c->nu1 == 2 && x == c->lv[l].x32 && b == c->lv[l].b32 &&
+        variant_rows(tile_variant(0, n, c->nu1)) == 64)
+        return launch_down_tma(x, t, b, n, c->nu1, zero, bc, &c->tm_x32[l], &c->tm_b32[l], &c->dstate->tile_err, s);
+    return launch_down<float>(x, t, b, n, c->nu1, zero, bc, s);
+}
+
 // One V(nu1, nu2) cycle on 4x - sum = b at level l (x = 0 on entry if zero);
 // t is the level's second buffer, the result is left in x.
 template <typename T>
@@ -324,7 +352,7 @@ static mg_status vcycle_rec(mg_ctx *c, int l, T *x, T *t, const T *b, bool zero)
     T *xc = lvx<T>(c, l + 1), *tc = lvt<T>(c, l + 1), *bc = lvb<T>(c, l + 1);
     const double nn = (double)n * n * sizeof(T);
     if (l == 0) probe_begin(c, kProbeDown);
-    MG_CUDA(launch_down<T>(x, t, b, n, c->nu1, zero, bc, c->stream));
+    MG_CUDA(down_level<T>(c, l, x, t, b, zero, bc, c->stream));
     if (l == 0) probe_end(c, kProbeDown, nn * ((zero ? 0 : 1) + 1 + 1 + 0.25));
     if (l == 0) probe_begin(c, kProbeCoarse);
     MG_TRY(vcycle_rec<T>(c, l + 1, xc, tc, bc, true));
@@ -342,7 +370,7 @@ static mg_status vcycle32_top(mg_ctx *c, bool zero, mg_prolong prolong) {
         float *xc = c->lv[1].x32, *tc = c->lv[1].t32, *bc = c->lv[1].b32;
         const double nn = (double)c->lv[0].n * c->lv[0].n * sizeof(float);
         probe_begin(c, kProbeDown);
-        MG_CUDA(launch_down<float>(x, t, b, c->lv[0].n, c->nu1, zero, bc, c->stream));
+        MG_CUDA(down_level<float>(c, 0, x, t, b, zero, bc, c->stream));
         probe_end(c, kProbeDown, nn * ((zero ? 0 : 1) + 1 + 1 + 0.25));
         probe_begin(c, kProbeCoarse);
         MG_TRY(vcycle_rec<float>(c, 1, xc, tc, bc, true));
@@ -429,7 +457,7 @@ static mg_status record_policy_vcycle(mg_ctx *c, bool zero, int k, cudaGraph_t b
     const int n = c->lv[0].n;
     float *x = c->lv[0].x32, *t = c->lv[0].t32, *b = c->lv[0].b32;
     float *xc = c->lv[1].x32, *tc = c->lv[1].t32, *bc = c->lv[1].b32;
-    MG_CUDA(launch_down<float>(x, t, b, n, c->nu1, zero, bc, s));
+    MG_CUDA(down_level<float>(c, 0, x, t, b, zero, bc, s));
     MG_TRY(vcycle_rec<float>(c, 1, xc, tc, bc, true));
     MG_CUDA(launch_policy(c->dstate, k, c->policy, c->d_srflag, h, s));
     cudaStreamCaptureStatus cs;
@@ -1766,6 +1794,11 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         else
             count_launches(sg->n_pro + (long long)ds.outer * (sg->n_body - (long long)c->inner * sg->n_sr) +
                            (long long)ds.sr_used * sg->n_sr + sg->n_epi);
+        if (ds.tile_err) {
+            MG_CUDA(cudaMemsetAsync(&c->dstate->tile_err, 0, sizeof(int), s));
+            set_err("a TMA tile load of k_down timed out");
+            return MG_ERR_TIMEOUT;
+        }
         mg_status gst = (mg_status)ds.status;
         if (gst == MG_ERR_NONFINITE) set_err("non-finite residual (NaN or Inf in f or x)");
         if (gst == MG_ERR_NOT_CONVERGED)
@@ -1870,7 +1903,14 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 4 * kMaxSlots,
                             cudaMemcpyDeviceToHost, s));
+    int tile_err = 0;
+    if (tma_tiles_mode()) MG_CUDA(cudaMemcpyAsync(&tile_err, &c->dstate->tile_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaStreamSynchronize(s));
+    if (tile_err) {
+        MG_CUDA(cudaMemsetAsync(&c->dstate->tile_err, 0, sizeof(int), s));
+        set_err("a TMA tile load of k_down timed out");
+        return MG_ERR_TIMEOUT;
+    }
     if (info) {
         info->outer_iters = outer;
         info->vcycles = cycles;
@@ -2153,6 +2193,17 @@ mg_status mg_set_launch_overlap(int enable) {
 }
 
 int mg_get_launch_overlap(void) { return launch_overlap_mode(); }
+
+mg_status mg_set_tma_tiles(int on) {
+    if (on != 0 && on != 1) {
+        set_err("TMA tiles: 0 (vector loads) or 1 (TMA-staged interior tiles)");
+        return MG_ERR_INVALID_ARG;
+    }
+    set_tma_tiles(on);
+    return MG_OK;
+}
+
+int mg_get_tma_tiles(void) { return tma_tiles_mode(); }
 
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant) {
     if (!variant || kind < 0 || kind > 1 || !is_pow2(n) || n < 128 || nu < 0 || nu > 4) {

@@ -8,6 +8,7 @@
 // h_c^2 = 4 h^2.  The inner V-cycle therefore carries no mesh width at all.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -356,6 +357,19 @@ unsigned tune_epoch();
 // launch latency is a large part of a kernel's time.
 constexpr int kOverlapMaxBlocks = 304;
 int launch_overlap_mode();
+// 1: single-solve FP32 k_down launches on 64-row tiles stage interior tiles by TMA
+int tma_tiles_mode();
+void set_tma_tiles(int on);
+// box (columns, rows) of a TMA-staged k_down tile with nu sweeps
+void down_tma_box(int nu, int *cols, int *rows);
+// k_down (nu = 2, 64-row tiles) with interior tiles staged by TMA from the 2D
+// maps tmx (of x; may be null with zero_init) and tmb (of b), boxes down_tma_box;
+// err: device flag set when a bounded wait runs out
+cudaError_t launch_down_tma(const float *x, float *xout, const float *b, int n, int nu, bool zero_init, float *bc,
+                            const CUtensorMap *tmx, const CUtensorMap *tmb, int *err, cudaStream_t s);
+// 2D tensor map of an n x n FP32 grid with boxes of cols x rows (false if the
+// driver's encoder is unavailable or rejects the map)
+bool make_grid_map_f32(CUtensorMap *m, void *base, int n, int cols, int rows);
 bool launch_overlap_enabled();
 void set_launch_overlap(int mode);
 
@@ -413,6 +427,7 @@ struct DevState {
     int fallback;     // SR stopped for this solve (an outer step with SR did not halve the residual)
     int m_next;       // V-cycles of the next outer step (adaptive inner cycles)
     double rel_prev;  // relative residual before the current outer step
+    int tile_err;     // a TMA tile load's bounded wait ran out (set by k_down_tma)
 };
 
 // Prolongation policy of a solve with the SR prolongation (the hybrid

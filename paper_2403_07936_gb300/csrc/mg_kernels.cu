@@ -32,6 +32,7 @@
 #include <utility>
 
 #include "mg_internal.cuh"
+#include "mg_tc.cuh"
 
 namespace mg {
 
@@ -395,10 +396,69 @@ struct DownCfg {
     static constexpr size_t smem = 4ull * A * sizeof(T);
 };
 
-template <typename T, int NU, int TY_>
+// TMA staging of an interior k_down tile (FP32): one thread issues the tiled
+// 2D copies of the b and x tiles (rows ty0 - H .., columns tx0 - HX .., the
+// innermost coordinate a multiple of 4 floats) straight into the tile's
+// colour-split regions, which a raw tile fits; every thread then reads its
+// share of the raw rows into registers and, after a barrier, scatters them
+// into the red and black arrays in place, as the vector-load path does from
+// global memory.  The mbarrier sits just past the four arrays (the launch
+// adds 16 bytes).  Tiles whose halo wraps around the periodic grid (a tiled
+// copy does not wrap) and unaligned buffers return false and take the vector
+// loads.  The wait is bounded; when it runs out, *err is set.
+template <int NU, int TY_>
+__device__ __forceinline__ bool tma_stage_tile(float *X, float *B, const void *tmx, const void *tmb, int n,
+                                               int ty0, int tx0, bool zero, int *err) {
+    using Cfg = DownCfg<float, NU, TY_>;
+    constexpr int R = Cfg::R, C = Cfg::C, A = Cfg::A, H = Cfg::H, HX = Cfg::HX;
+    static_assert(R * C <= 2 * A && (C * 4) % 16 == 0 && C <= 256 && R <= 256, "raw TMA tile");
+    const bool interior = ty0 >= H && ty0 + TY_ + H <= n && tx0 >= HX && tx0 + Cfg::TX + HX <= n;
+    const bool aligned = ((smem_u32(X) | smem_u32(B)) & 127u) == 0;
+    if (!interior || !aligned || !tmb || (!zero && !tmx)) return false;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(X + 4 * A);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(bar, (zero ? 1u : 2u) * (uint32_t)(R * C * 4));
+        tma_load_2d(B, tmb, bar, tx0 - HX, ty0 - H);
+        if (!zero) tma_load_2d(X, tmx, bar, tx0 - HX, ty0 - H);
+    }
+    __syncthreads();
+    if (!mbar_wait(bar, 0)) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        mbar_wait(bar, 0);  // once more, so no copy is left writing this block's tile
+    }
+    constexpr int CV = C / 4, ITEMS = R * CV, PER = (ITEMS + kThreads - 1) / kThreads;
+    float4 vb[PER], vx[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        if (idx < ITEMS) {
+            const int rr = idx / CV, cv = idx - rr * CV;
+            vb[i] = *reinterpret_cast<const float4 *>(B + rr * C + cv * 4);
+            if (!zero) vx[i] = *reinterpret_cast<const float4 *>(X + rr * C + cv * 4);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        if (idx < ITEMS) {
+            const int rr = idx / CV, cv = idx - rr * CV;
+            scatter_vec(B, B + A, rr, cv * 4, C / 2, vb[i]);
+            if (!zero) scatter_vec(X, X + A, rr, cv * 4, C / 2, vx[i]);
+        }
+    }
+    if (zero)
+        for (int i = threadIdx.x; i < 2 * A; i += blockDim.x) X[i] = 0.f;
+    return true;
+}
+
+template <typename T, int NU, int TY_, bool TMA = false>
 __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict__ xout,
                                           const T *__restrict__ b, int n, T *__restrict__ bc,
-                                          int ty0, int tx0, bool zero) {
+                                          int ty0, int tx0, bool zero, const void *tmx = nullptr,
+                                          const void *tmb = nullptr, int *err = nullptr) {
     using Cfg = DownCfg<T, NU, TY_>;
     constexpr int TY = Cfg::TY, TX = Cfg::TX, H = Cfg::H, HX = Cfg::HX, R = Cfg::R, C = Cfg::C,
                   CK = Cfg::CK, A = Cfg::A;
@@ -406,7 +466,9 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
     T *X = reinterpret_cast<T *>(smem_raw);  // red at X, black at X + A
     T *B = X + 2 * A;                           // red at B, black at B + A
 
-    {
+    bool staged = false;
+    if constexpr (TMA) staged = tma_stage_tile<NU, TY_>(X, B, tmx, tmb, n, ty0, tx0, zero, err);
+    if (!staged) {
         SplitLoad<T, R, C> lb, lx;
         lb.issue(b, n, ty0 - H, tx0 - HX);
         if (!zero) lx.issue(x, n, ty0 - H, tx0 - HX);
@@ -459,6 +521,18 @@ __global__ void __launch_bounds__(kThreads) k_down(const T *__restrict__ x, T *_
                                                    T *__restrict__ bc) {
     pdl_enter();
     down_tile<T, NU, TY>(x, xout, b, n, bc, blockIdx.y * TY, blockIdx.x * kTX, ZERO);
+}
+
+// k_down on 64-row FP32 tiles with the interior tiles staged by TMA (tmx, tmb:
+// 2D maps of x and b with boxes of the staged tile, C x R floats).
+template <int NU, bool ZERO>
+__global__ void __launch_bounds__(kThreads) k_down_tma(const __grid_constant__ CUtensorMap tmx,
+                                                       const __grid_constant__ CUtensorMap tmb,
+                                                       const float *__restrict__ x, float *__restrict__ xout,
+                                                       const float *__restrict__ b, int n, float *__restrict__ bc,
+                                                       int *err) {
+    pdl_enter();
+    down_tile<float, NU, 64, true>(x, xout, b, n, bc, blockIdx.y * 64, blockIdx.x * kTX, ZERO, &tmx, &tmb, err);
 }
 
 // Block of a batched tile launch: locate its grid (the last table entry whose
@@ -2050,6 +2124,28 @@ cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zer
         default: return cudaErrorInvalidValue;
     }
 #undef MG_DOWN_CASE
+}
+
+// Box of the TMA-staged k_down tile (columns, rows) for sweeps nu.
+void down_tma_box(int nu, int *cols, int *rows) {
+    *cols = kTX + 2 * round_up(2 * nu + 4, 4);
+    *rows = 64 + 2 * (2 * nu + 2);
+}
+
+cudaError_t launch_down_tma(const float *x, float *xout, const float *b, int n, int nu, bool zero_init, float *bc,
+                            const CUtensorMap *tmx, const CUtensorMap *tmb, int *err, cudaStream_t s) {
+    if (nu != 2 || n < 128 || x == xout || !tmb || !err) return cudaErrorInvalidValue;
+    using Cfg = DownCfg<float, 2, 64>;
+    const size_t smem = Cfg::smem + 16;
+    auto k = zero_init ? k_down_tma<2, true> : k_down_tma<2, false>;
+    static std::atomic<unsigned> done0{0}, done1{0};
+    cudaError_t e = set_smem_once(k, smem, zero_init ? done1 : done0);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap &mx = tmx ? *tmx : *tmb;  // x is not read with zero_init
+    e = launch_kernel(k, dim3(n / kTX, n / 64), kThreads, smem, s, mx, *tmb, x, xout, b, n, bc, err);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 template <typename T>

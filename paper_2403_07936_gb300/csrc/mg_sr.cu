@@ -67,10 +67,6 @@ enum { MODE_PRELU = 0, MODE_RESID = 1, MODE_SHUFFLE = 2 };
 // ---------------------------------------------------------------------------
 // PTX wrappers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
                                             int c1, int c2) {
     asm volatile(
@@ -958,6 +954,22 @@ EncodeTiledFn encode_fn() {
     }
     return fn;
 }
+
+}  // namespace
+
+bool make_grid_map_f32(CUtensorMap *m, void *base, int n, int cols, int rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || n < cols || n < rows) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)n * 4};
+    cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
 
 // padded activation [H+2][W+2][64] bf16 as a 3D tensor (c, x, y); a box is
 // one 8-channel plane of a staged row: 8 channels x 130 pixels x 1 row

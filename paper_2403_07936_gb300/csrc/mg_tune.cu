@@ -96,6 +96,17 @@ int launch_overlap_mode() {
 
 bool launch_overlap_enabled() { return launch_overlap_mode() != 0; }
 
+namespace {
+std::atomic<int> g_tma_tiles{0};
+}
+
+int tma_tiles_mode() { return g_tma_tiles.load(std::memory_order_relaxed); }
+
+void set_tma_tiles(int on) {
+    const int old = g_tma_tiles.exchange(on ? 1 : 0);
+    if (old != (on ? 1 : 0)) g_epoch.fetch_add(1);
+}
+
 void set_launch_overlap(int mode) {
     const int old = launch_overlap_mode();
     g_overlap.store(mode);

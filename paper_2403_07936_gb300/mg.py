@@ -75,6 +75,8 @@ SIGNATURES = {
     "mg_trainer_step": (_I, [_VP, _VP, _VP, _VP, C.POINTER(_D)]),
     "mg_trainer_set_lr": (_I, [_VP, _D]),
     "mg_trainer_set_tensor_cores": (_I, [_VP, _I]),
+    "mg_set_tma_tiles": (_I, [_I]),
+    "mg_get_tma_tiles": (_I, []),
     "mg_trainer_get_tensor_cores": (_I, [_VP, C.POINTER(_I)]),
     "mg_trainer_get_weights": (_I, [_VP, _VP, _SZ]),
     "mg_trainer_destroy": (None, [_VP]),
@@ -333,6 +335,15 @@ def set_launch_overlap(mode):
     """Programmatic dependent launch between library kernels: 0 / False off,
     1 / True every kernel, 2 kernels of grids of at most one wave."""
     _check(load().mg_set_launch_overlap(int(mode)))
+
+
+def set_tma_tiles(on: bool):
+    """Stage the smoother's interior 64-row FP32 tiles by TMA (True) or 16-byte vector loads."""
+    _check(load().mg_set_tma_tiles(int(bool(on))))
+
+
+def get_tma_tiles() -> bool:
+    return bool(load().mg_get_tma_tiles())
 
 
 def get_launch_overlap() -> int:
