@@ -187,15 +187,16 @@ __global__ void __launch_bounds__(GT) k_conv_wgrad(const float *__restrict__ in,
 // Tensor-core (tcgen05) forms of the two GEMM kernels above: the same
 // products and epilogues, with BF16 operands (the FP32 activations and the
 // FP32 master weights rounded to nearest even) and FP32 accumulation in
-// tensor memory.  Four warps per block: all gather operands into shared
+// tensor memory.  Eight warps per block: all gather operands into shared
 // memory, one thread issues the MMAs, and warp w drains TMEM lanes
-// 32 w .. 32 w + 31 (the hardware's lane quarter of warp w).  Operands use the
+// 32 (w mod 4) .. + 31 (the hardware's lane quarter of warp w), columns
+// 32 (w / 4) .. + 31 of the 64-column accumulator.  Operands use the
 // no-swizzle K-major layout (core matrices of 8 rows x 16 bytes).  Every
 // mbarrier wait is bounded (kWaitNs) and reports through a device flag.
 // ---------------------------------------------------------------------------
 constexpr int TCM = 128;                 // pixels per block: one row segment (W a multiple of 128)
 constexpr int TCN = 64;                  // output channels per block
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr int TC_ROWPX = TCM + 2;        // staged pixels of an input row: x0 - 1 .. x0 + 128 (periodic)
 constexpr int TC_PLANE = 2176;           // one 8-channel plane of a staged row, [pixel][8 ch], 128-B multiple
 constexpr int TC_ABYTES = 8 * TC_PLANE;  // a staged row: 64 channels
@@ -303,44 +304,44 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_gemm_tc(const float *__rest
     ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
     if (ok) {
-        float v[TCN];
-        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
-        tmem_ld32(ta, v);
-        tmem_ld32(ta + 32, v + 32);
+        constexpr int NH = TCN / 2;  // columns per warp
+        float v[NH];
+        const int quarter = warp & 3, nh = n0 + NH * (warp >> 2);  // this warp's pixels and first channel
+        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(NH * (warp >> 2)), v);
         tmem_wait_ld();
-        const int p = p0 + 32 * warp + lane;
+        const int p = p0 + 32 * quarter + lane;
 #pragma unroll
-        for (int j = 0; j < TCN; ++j) v[j] += bias ? bias[n0 + j] : 0.f;
+        for (int j = 0; j < NH; ++j) v[j] += bias ? bias[nh + j] : 0.f;
         if (EPI == EPI_SHUFFLE) {
             const int Wc = W, Hc = H;
             const int x = p & (Wc - 1), yy = (p >> g.lgW) & (Hc - 1), b = p >> (g.lgW + g.lgH);
 #pragma unroll
-            for (int j = 0; j < TCN; j += 4)
-                *reinterpret_cast<float4 *>(out + (size_t)p * CN + n0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            for (int j = 0; j < NH; j += 4)
+                *reinterpret_cast<float4 *>(out + (size_t)p * CN + nh + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
 #pragma unroll
-            for (int j = 0; j < TCN; ++j) {
-                const int n = n0 + j, c = n >> 2, sy = (n >> 1) & 1, sx = n & 1;
+            for (int j = 0; j < NH; ++j) {
+                const int n = nh + j, c = n >> 2, sy = (n >> 1) & 1, sx = n & 1;
                 const size_t pf = ((size_t)(b * 2 * Hc + 2 * yy + sy) * (2 * Wc)) + 2 * x + sx;
                 out2[pf * F + c] = v[j] > 0.f ? v[j] : slope[c] * v[j];
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < TCN; j += 4) {
+            for (int j = 0; j < NH; j += 4) {
                 float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 if (EPI == EPI_ADD) {
-                    const float4 k4 = *reinterpret_cast<const float4 *>(skip + (size_t)p * CN + n0 + j);
+                    const float4 k4 = *reinterpret_cast<const float4 *>(skip + (size_t)p * CN + nh + j);
                     o.x += k4.x;
                     o.y += k4.y;
                     o.z += k4.z;
                     o.w += k4.w;
                 }
-                *reinterpret_cast<float4 *>(out + (size_t)p * CN + n0 + j) = o;
+                *reinterpret_cast<float4 *>(out + (size_t)p * CN + nh + j) = o;
                 if (EPI == EPI_PRELU) {
-                    const float4 a4 = make_float4(o.x > 0.f ? o.x : slope[n0 + j] * o.x,
-                                                  o.y > 0.f ? o.y : slope[n0 + j + 1] * o.y,
-                                                  o.z > 0.f ? o.z : slope[n0 + j + 2] * o.z,
-                                                  o.w > 0.f ? o.w : slope[n0 + j + 3] * o.w);
-                    *reinterpret_cast<float4 *>(out2 + (size_t)p * CN + n0 + j) = a4;
+                    const float4 a4 = make_float4(o.x > 0.f ? o.x : slope[nh + j] * o.x,
+                                                  o.y > 0.f ? o.y : slope[nh + j + 1] * o.y,
+                                                  o.z > 0.f ? o.z : slope[nh + j + 2] * o.z,
+                                                  o.w > 0.f ? o.w : slope[nh + j + 3] * o.w);
+                    *reinterpret_cast<float4 *>(out2 + (size_t)p * CN + nh + j) = a4;
                 }
             }
         }
@@ -383,8 +384,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_wgrad_tc(const float *__res
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    // this thread's A row: (tap of the pair, k); B rows n = tid & 63, planes q = (tid >> 6) + 2 i
-    const int tap = t0 + (tid >> 6), ka = tid & 63, nb = tid & 63, qb = tid >> 6;
+    // this thread's A row m = tid & 127 = (tap of the pair, k), planes 4 (tid >> 7) .. + 3;
+    // B row n = tid & 63, planes (tid >> 6) and (tid >> 6) + 4
+    const int ma = tid & 127, qa = 4 * (tid >> 7);
+    const int tap = t0 + (ma >> 6), ka = ma & 63, nb = tid & 63, qb = tid >> 6;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     constexpr int S = WCHUNK_TC / 64;
     bool ok = true;
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_wgrad_tc(const float *__res
             if (tap < 9) {
                 const float *rowp = in + ((size_t)smp + ((size_t)((yr + dy) & (H - 1)) << g.lgW)) * CK + ka;
 #pragma unroll 2
-                for (int q = 0; q < 8; ++q) {
+                for (int q = qa; q < qa + 4; ++q) {
                     float v[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) v[i] = rowp[(size_t)((xs + 8 * q + i + dx) & (W - 1)) * CK];
@@ -409,16 +412,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_wgrad_tc(const float *__res
                     o.y = pack_bf16x2(v[2], v[3]);
                     o.z = pack_bf16x2(v[4], v[5]);
                     o.w = pack_bf16x2(v[6], v[7]);
-                    *reinterpret_cast<uint4 *>(A + q * TCW_APLANE + tid * 16) = o;
+                    *reinterpret_cast<uint4 *>(A + q * TCW_APLANE + ma * 16) = o;
                 }
             } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) *reinterpret_cast<uint4 *>(A + q * TCW_APLANE + tid * 16) = make_uint4(0, 0, 0, 0);
+                for (int q = qa; q < qa + 4; ++q)
+                    *reinterpret_cast<uint4 *>(A + q * TCW_APLANE + ma * 16) = make_uint4(0, 0, 0, 0);
             }
             const float *dp = dout + (size_t)pst * CN + n0 + nb;
 #pragma unroll
-            for (int i2 = 0; i2 < 4; ++i2) {
-                const int q = qb + 2 * i2;
+            for (int i2 = 0; i2 < 2; ++i2) {
+                const int q = qb + 4 * i2;
                 float v[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) v[i] = dp[(size_t)(8 * q + i) * CN];
@@ -451,16 +455,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_wgrad_tc(const float *__res
     ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
     if (ok) {
-        float v[64];
-        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
-        tmem_ld32(ta, v);
-        tmem_ld32(ta + 32, v + 32);
+        float v[32];
+        const int quarter = warp & 3, nh = 32 * (warp >> 2);
+        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)nh, v);
         tmem_wait_ld();
-        const int m = 32 * warp + lane, tr = t0 + (m >> 6), k = m & 63;
+        const int m = 32 * quarter + lane, tr = t0 + (m >> 6), k = m & 63;
         if (tr < 9) {
-            float *dst = part + (((size_t)chunk * 9 + tr) * CN + n0) * CK + k;
+            float *dst = part + (((size_t)chunk * 9 + tr) * CN + n0 + nh) * CK + k;
 #pragma unroll
-            for (int n = 0; n < 64; ++n) dst[(size_t)n * CK] = v[n];
+            for (int n = 0; n < 32; ++n) dst[(size_t)n * CK] = v[n];
         }
     } else if (tid == 0) {
         atomicExch(err, 1);

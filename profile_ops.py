@@ -21,6 +21,10 @@ ops:
   solve  a whole solve of a seeded turbulent source (host-loop execution, so
          every kernel is a separate launch), mixed or FP64 (--precision);
          time per solve
+  train  one Adam step of the SR generator trainer on a batch of 4 periodic
+         crops of 128^2 coarse pixels (the training configuration; the
+         tensor-core GEMMs, or the FP32 CUDA-core GEMMs with --fp32-gemm); time
+         per step
   link   the host link: copies of n x n FP64 arrays between pinned host memory
          and the device with cudaMemcpyAsync - host to device (f and x, as a
          solve from host buffers stages them), device to host (x), and both
@@ -39,12 +43,14 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["down", "up", "outer", "conv", "generator", "solve", "link"], required=True)
+    ap.add_argument("--op", choices=["down", "up", "outer", "conv", "generator", "solve", "link", "train"],
+                    required=True)
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--nu", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32", help="down / up: element type")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="solve: precision")
+    ap.add_argument("--fp32-gemm", action="store_true", help="train: FP32 CUDA-core GEMMs instead of tensor cores")
     args = ap.parse_args()
 
     import torch
@@ -91,6 +97,17 @@ def main():
         def run():
             x.zero_()
             ctx.solve(f, x)
+    elif args.op == "train":
+        from paper_2403_07936_gb300 import sr
+        from synthetic.weights import random_weights
+        crop, batch = 128, 4
+        tr = mg.Trainer(crop, crop, batch, sr.pack_weights(random_weights(5, gain=0.5)), lr=1e-5)
+        tr.tensor_cores = not args.fp32_gemm
+        q = torch.randn((batch, crop, crop), device=dev, generator=g)
+        tgt = torch.randn((batch, 2 * crop, 2 * crop), device=dev, generator=g) * 0.1
+
+        def run():
+            tr.step(q, tgt)
     elif args.op == "generator":
         import math
 
