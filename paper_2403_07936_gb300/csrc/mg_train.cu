@@ -198,9 +198,11 @@ constexpr int TCM = 128;                 // pixels per block: one row segment (W
 constexpr int TCN = 64;                  // output channels per block
 constexpr int TC_THREADS = 256;
 constexpr int TC_ROWPX = TCM + 2;        // staged pixels of an input row: x0 - 1 .. x0 + 128 (periodic)
-constexpr int TC_PLANE = 2176;           // one 8-channel plane of a staged row, [pixel][8 ch], 128-B multiple
+// one 8-channel plane of a staged row, [pixel][8 ch]: 130 x 16 bytes padded to
+// 2192 (548 words), so the 8 planes of one pixel fall into distinct banks
+constexpr int TC_PLANE = 2192;
 constexpr int TC_ABYTES = 8 * TC_PLANE;  // a staged row: 64 channels
-constexpr int TC_BPLANE = TCN * 16;      // 8 K values of the 64 weight rows
+constexpr int TC_BPLANE = TCN * 16 + 16; // 8 K values of the 64 weight rows (+16 bytes: distinct banks per plane)
 constexpr int TC_BTAP = 8 * TC_BPLANE;   // one tap: 64 rows (n) x 64 k
 constexpr int TC_STAGE = TC_ABYTES + 3 * TC_BTAP;
 constexpr size_t TC_GEMM_SMEM = 128 + 2 * TC_STAGE + 64;
@@ -208,7 +210,8 @@ constexpr int TCW_APLANE = 128 * 16;     // weight gradient: 8 pixels of the 128
 constexpr int TCW_BPLANE = 64 * 16;      // 8 pixels of the 64 rows n
 constexpr int TCW_STAGE = 8 * TCW_APLANE + 8 * TCW_BPLANE;
 constexpr size_t TC_WGRAD_SMEM = 128 + 2 * TCW_STAGE + 64;
-static_assert(TC_STAGE % 128 == 0 && TCW_STAGE % 128 == 0, "stage alignment");
+static_assert(TC_STAGE % 128 == 0 && TCW_STAGE % 128 == 0 && TC_PLANE % 16 == 0 && TC_BPLANE % 16 == 0,
+              "stage and plane alignment");
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
@@ -261,8 +264,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_gemm_tc(const float *__rest
         if (ok) {
             const int ry = (y + r - 1) & (H - 1);
             const float *rowp = in + ((size_t)sample0 + ((size_t)ry << g.lgW)) * CK + ks * 64;
+            // item (pixel j, plane q), q fastest: 8 lanes read one pixel's 256 contiguous bytes
             for (int i = tid; i < 8 * TC_ROWPX; i += TC_THREADS) {
-                const int q = i / TC_ROWPX, j = i - q * TC_ROWPX;
+                const int j = i >> 3, q = i & 7;
                 const int x = (x0 - 1 + j) & (W - 1);
                 const float4 *src = reinterpret_cast<const float4 *>(rowp + (size_t)x * CK + 8 * q);
                 const float4 u = src[0], v = src[1];
@@ -273,8 +277,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_gemm_tc(const float *__rest
                 o.w = pack_bf16x2(v.z, v.w);
                 *reinterpret_cast<uint4 *>(A + q * TC_PLANE + j * 16) = o;
             }
+            // item (tap c, row n, plane q), q fastest: 8 lanes read one weight row's 128 bytes
             for (int i = tid; i < 3 * 8 * TCN; i += TC_THREADS) {
-                const int c = i / (8 * TCN), rem = i - c * (8 * TCN), q = rem / TCN, n = rem - q * TCN;
+                const int q = i & 7, rest = i >> 3, n = rest % TCN, c = rest / TCN;
                 const int tap = DGRAD ? (2 - r) * 3 + (2 - c) : r * 3 + c;
                 const uint4 v = *reinterpret_cast<const uint4 *>(wp + ((size_t)(tap * CN + n0 + n) * CK + ks * 64 + 8 * q));
                 *reinterpret_cast<uint4 *>(Bm + c * TC_BTAP + q * TC_BPLANE + n * 16) = v;
