@@ -298,6 +298,17 @@ int mg_get_launch_overlap(void);
 mg_status mg_set_tma_tiles(int on);
 int mg_get_tma_tiles(void);
 
+/* Launch form of the coarse tail of a single solve's V(2,2) cycle
+ * (Algorithm 6's recursion below the 128^2 level: its down pass, the levels
+ * <= 64^2 down to the exact coarsest solve and back, its up pass).  on = 1
+ * (the default): one launch of a thread-block cluster of 8 CTAs, CTA r taking
+ * tile r of the 128^2 level, CTA 0 the bottom V-cycle, the phases ordered by
+ * the cluster's hardware barrier; on = 0: three launches.  Results are
+ * identical bit for bit; graphs recorded before a change are re-recorded.
+ * MG_ERR_INVALID_ARG for other values. */
+mg_status mg_set_coarse_cluster(int on);
+int mg_get_coarse_cluster(void);
+
 /* Read or set one table entry (n a power of two >= 128, nu 0..4). */
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant);
 mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);

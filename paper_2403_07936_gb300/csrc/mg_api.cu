@@ -20,6 +20,7 @@
 #include <mutex>
 #include <new>
 #include <utility>
+#include <type_traits>
 #include <vector>
 
 #include "mg_internal.cuh"
@@ -350,6 +351,14 @@ static mg_status vcycle_rec(mg_ctx *c, int l, T *x, T *t, const T *b, bool zero)
         return MG_OK;
     }
     T *xc = lvx<T>(c, l + 1), *tc = lvt<T>(c, l + 1), *bc = lvb<T>(c, l + 1);
+    if constexpr (std::is_same<T, float>::value) {
+        // the 128^2 level and the bottom solve below it as one cluster launch
+        if (coarse_cluster_mode() && l > 0 && zero && n == 128 && c->lv[l + 1].n <= bottom_max<T>() &&
+            c->nu1 == 2 && c->nu2 == 2) {
+            MG_CUDA(launch_coarse_cluster(x, t, b, xc, bc, c->coarsest, 2, 2, ainv<T>(c), c->taps, c->stream));
+            return MG_OK;
+        }
+    }
     const double nn = (double)n * n * sizeof(T);
     if (l == 0) probe_begin(c, kProbeDown);
     MG_CUDA(down_level<T>(c, l, x, t, b, zero, bc, c->stream));
@@ -2193,6 +2202,17 @@ mg_status mg_set_launch_overlap(int enable) {
 }
 
 int mg_get_launch_overlap(void) { return launch_overlap_mode(); }
+
+mg_status mg_set_coarse_cluster(int on) {
+    if (on != 0 && on != 1) {
+        set_err("coarse cluster: 0 (separate launches) or 1 (one cluster launch)");
+        return MG_ERR_INVALID_ARG;
+    }
+    set_coarse_cluster(on);
+    return MG_OK;
+}
+
+int mg_get_coarse_cluster(void) { return coarse_cluster_mode(); }
 
 mg_status mg_set_tma_tiles(int on) {
     if (on != 0 && on != 1) {

@@ -367,6 +367,14 @@ void down_tma_box(int nu, int *cols, int *rows);
 // err: device flag set when a bounded wait runs out
 cudaError_t launch_down_tma(const float *x, float *xout, const float *b, int n, int nu, bool zero_init, float *bc,
                             const CUtensorMap *tmx, const CUtensorMap *tmb, int *err, cudaStream_t s);
+// the 128^2 level's down pass, the bottom V-cycle (levels <= 64^2 to the
+// coarsest) and the 128^2 level's up pass in one 8-CTA cluster launch
+// (V(2,2), the level's x = 0 on entry); bits of the three separate launches
+cudaError_t launch_coarse_cluster(float *x, float *t, const float *b, float *xb, float *bb, int coarsest, int nu1,
+                                  int nu2, const float *ainv, const FirTaps &taps, cudaStream_t s);
+// 1: single solves run the coarse tail (128^2 and below) as one cluster launch
+int coarse_cluster_mode();
+void set_coarse_cluster(int on);
 // 2D tensor map of an n x n FP32 grid with boxes of cols x rows (false if the
 // driver's encoder is unavailable or rejects the map)
 bool make_grid_map_f32(CUtensorMap *m, void *base, int n, int cols, int rows);

@@ -27,6 +27,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 #include <utility>
@@ -195,27 +196,28 @@ __device__ __forceinline__ void load_split(T *red, T *black, const T *__restrict
 // registers (a thread's share, all independent, so their latencies overlap),
 // scatter() writes them into the colour-split arrays.  Between the two a
 // block can do other work with the loads in flight.
-template <typename T, int R, int C>
+template <typename T, int R, int C, int NT = kThreads, bool COH = false>
 struct SplitLoad {
     using V = typename Prec<T>::vec;
     static constexpr int VW = Prec<T>::VW, CV = C / VW, ITEMS = R * CV;
-    static constexpr int PER = (ITEMS + kThreads - 1) / kThreads;
+    static constexpr int PER = (ITEMS + NT - 1) / NT;
     V v[PER];
     __device__ __forceinline__ void issue(const T *__restrict__ g, int n, int r0, int c0) {
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            const int idx = threadIdx.x + i * kThreads;
+            const int idx = threadIdx.x + i * NT;
             if (idx < ITEMS) {
                 const int rr = idx / CV, cv = idx - rr * CV;
                 const int gr = (r0 + rr) & (n - 1), gc = (c0 + cv * VW) & (n - 1);
-                v[i] = __ldg(reinterpret_cast<const V *>(g + (size_t)gr * n + gc));
+                const V *src = reinterpret_cast<const V *>(g + (size_t)gr * n + gc);
+                v[i] = COH ? __ldcg(src) : __ldg(src);
             }
         }
     }
     __device__ __forceinline__ void scatter(T *red, T *black) const {
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            const int idx = threadIdx.x + i * kThreads;
+            const int idx = threadIdx.x + i * NT;
             if (idx < ITEMS) {
                 const int rr = idx / CV, cv = idx - rr * CV;
                 scatter_vec(red, black, rr, cv * VW, C / 2, v[i]);
@@ -306,11 +308,11 @@ __device__ __forceinline__ void strip_walk(const T *__restrict__ P, int ra, int 
 // shared-memory bandwidth; there the rows go as NSEG segments of KW = CK - 2
 // consecutive threads each (warps may straddle two segments), which keeps the
 // chain of dependent rows per thread shortest.
-template <int CK, typename T, typename Body>
+template <int CK, int NT = kThreads, typename T, typename Body>
 __device__ __forceinline__ void colour_segments(const T *__restrict__ P, int r_lo, int r_hi, int q,
                                                 Body body) {
     constexpr int KW = CK - 2;
-    constexpr int NSEG = kThreads / KW;
+    constexpr int NSEG = NT / KW;
     const int seg = threadIdx.x / KW;
     if (seg >= NSEG) return;
     const int k = 1 + (threadIdx.x - seg * KW);
@@ -334,17 +336,17 @@ __device__ __forceinline__ void colour_segments(const T *__restrict__ P, int r_l
     }
 }
 
-template <int CK, bool STRIPS, typename T, typename Body>
+template <int CK, bool STRIPS, int NT = kThreads, typename T, typename Body>
 __device__ __forceinline__ void colour_strips(const T *__restrict__ P, int r_lo, int r_hi, int q,
                                               Body body) {
     if constexpr (!STRIPS) {
-        colour_segments<CK>(P, r_lo, r_hi, q, body);
+        colour_segments<CK, NT>(P, r_lo, r_hi, q, body);
         return;
     }
     constexpr int KW = CK - 2;
     constexpr int KM = KW < 32 ? KW : 32;  // columns of the strips
     constexpr int KR = KW - KM;            // remainder columns
-    constexpr int NW = kThreads / 32;
+    constexpr int NW = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rows = r_hi - r_lo;
     if (lane < KM) {
@@ -371,11 +373,11 @@ __device__ __forceinline__ void colour_strips(const T *__restrict__ P, int r_lo,
 // One Gauss-Seidel half-sweep of colour q: x <- (b + (((N + S) + W) + E)) / 4.
 // X and B point at the red arrays; the black ones follow A entries later.
 // STRIPS: the conflict-free strip mapping (tiles of >= 32 rows), else segments.
-template <int CK, int A, bool STRIPS, typename T>
+template <int CK, int A, bool STRIPS, int NT = kThreads, typename T>
 __device__ __forceinline__ void half_sweep(T *X, const T *B, int r_lo, int r_hi, int q) {
     T *Xq = X + q * A;
     const T *Bq = B + q * A;
-    colour_strips<CK, STRIPS>(X + (q ^ 1) * A, r_lo, r_hi, q, [&](int p, T N, T S, T W, T E) {
+    colour_strips<CK, STRIPS, NT>(X + (q ^ 1) * A, r_lo, r_hi, q, [&](int p, T N, T S, T W, T E) {
         Xq[p] = (Bq[p] + (((N + S) + W) + E)) * T(0.25);
     });
 }
@@ -454,7 +456,7 @@ __device__ __forceinline__ bool tma_stage_tile(float *X, float *B, const void *t
     return true;
 }
 
-template <typename T, int NU, int TY_, bool TMA = false>
+template <typename T, int NU, int TY_, bool TMA = false, int NT = kThreads>
 __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict__ xout,
                                           const T *__restrict__ b, int n, T *__restrict__ bc,
                                           int ty0, int tx0, bool zero, const void *tmx = nullptr,
@@ -469,7 +471,7 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
     bool staged = false;
     if constexpr (TMA) staged = tma_stage_tile<NU, TY_>(X, B, tmx, tmb, n, ty0, tx0, zero, err);
     if (!staged) {
-        SplitLoad<T, R, C> lb, lx;
+        SplitLoad<T, R, C, NT> lb, lx;
         lb.issue(b, n, ty0 - H, tx0 - HX);
         if (!zero) lx.issue(x, n, ty0 - H, tx0 - HX);
         lb.scatter(B, B + A);
@@ -485,7 +487,7 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
 #pragma unroll 1
         for (int q = 0; q < 2; ++q) {
             const int j = 2 * s + q + 1;  // valid region shrinks by one per half-sweep
-            half_sweep<CK, A, (TY >= 32)>(X, B, j, R - j, q);
+            half_sweep<CK, A, (TY >= 32), NT>(X, B, j, R - j, q);
             __syncthreads();
         }
     }
@@ -494,7 +496,7 @@ __device__ __forceinline__ void down_tile(const T *__restrict__ x, T *__restrict
     for (int q = 0; q < 2; ++q) {
         const T *Xq = X + q * A;
         T *Bq = B + q * A;
-        colour_strips<CK, (TY >= 32)>(X + (q ^ 1) * A, H - 1, H + TY + 1, q, [&](int p, T N, T S, T W, T E) {
+        colour_strips<CK, (TY >= 32), NT>(X + (q ^ 1) * A, H - 1, H + TY + 1, q, [&](int p, T N, T S, T W, T E) {
             Bq[p] = Bq[p] - (T(4) * Xq[p] - (((N + S) + W) + E));
         });
     }
@@ -591,7 +593,7 @@ struct UpCfg {
     static_assert(JW % NJ == 0 && IW % NJ == 0, "runs must tile the refined range");
 };
 
-template <typename T, int NU, int TY_, int NJ_>
+template <typename T, int NU, int TY_, int NJ_, int NT = kThreads, bool COH = false>
 __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__ xout,
                                         const T *__restrict__ b, const T *__restrict__ ec,
                                         const T *__restrict__ extra, int n, const FirTaps &taps, int ty0,
@@ -614,25 +616,27 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
         // rows' midpoints; column pass: two adjacent fine columns of rs.
         constexpr int CRP = Cfg::CRP;
         float2 *cs2 = reinterpret_cast<float2 *>(cs);
-        constexpr int CV = CC / 4, CITEMS = CRP * CV, CPER = (CITEMS + kThreads - 1) / kThreads;
-        SplitLoad<T, R, C> lx;
+        constexpr int CV = CC / 4, CITEMS = CRP * CV, CPER = (CITEMS + NT - 1) / NT;
+        SplitLoad<T, R, C, NT, COH> lx;
         lx.issue(x, n, ty0 - H, tx0 - HX);
         float4 c0v[CPER], c1v[CPER];
 #pragma unroll
         for (int i = 0; i < CPER; ++i) {
-            const int idx = threadIdx.x + i * kThreads;
+            const int idx = threadIdx.x + i * NT;
             if (idx < CITEMS) {
                 const int rp = idx / CV, cv = idx - rp * CV;
                 const int gr0 = (ty0 / 2 - CHY + 2 * rp) & (nc - 1), gr1 = (gr0 + 1) & (nc - 1);
                 const int gc = (tx0 / 2 - CHX + 4 * cv) & (nc - 1);
-                c0v[i] = __ldg(reinterpret_cast<const float4 *>(ec + (size_t)gr0 * nc + gc));
-                c1v[i] = __ldg(reinterpret_cast<const float4 *>(ec + (size_t)gr1 * nc + gc));
+                const float4 *s0 = reinterpret_cast<const float4 *>(ec + (size_t)gr0 * nc + gc);
+                const float4 *s1 = reinterpret_cast<const float4 *>(ec + (size_t)gr1 * nc + gc);
+                c0v[i] = COH ? __ldcg(s0) : __ldg(s0);
+                c1v[i] = COH ? __ldcg(s1) : __ldg(s1);
             }
         }
         lx.scatter(X, X + A);
 #pragma unroll
         for (int i = 0; i < CPER; ++i) {
-            const int idx = threadIdx.x + i * kThreads;
+            const int idx = threadIdx.x + i * NT;
             if (idx < CITEMS) {
                 const int rp = idx / CV, cv = idx - rp * CV;
                 float4 *dst = reinterpret_cast<float4 *>(cs2 + rp * Cfg::CCP + 4 * cv);
@@ -644,13 +648,13 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
 #pragma unroll
         for (int k = 1; k <= L; ++k) tp[k - 1] = make_float2(Prec<float>::tap(taps, k), Prec<float>::tap(taps, k));
         __syncthreads();
-        SplitLoad<T, R, C> lb;  // b arrives while the row pass runs
+        SplitLoad<T, R, C, NT> lb;  // b arrives while the row pass runs
         if (NU > 0) lb.issue(b, n, ty0 - H, tx0 - HX);
         // Both spline passes map one warp instruction to one row of items (32
         // consecutive, conflict-free) and take each row's remaining items in
         // groups of rows whose runs fall into disjoint banks (strip_rem_rows).
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        constexpr int NWARP = kThreads / 32;
+        constexpr int NWARP = NT / 32;
         auto row_item = [&](int rp, int jr) {
             const int J0 = -H / 2 + jr;
             const float2 *w = cs2 + rp * Cfg::CCP + CHX + J0;  // w[m] = rows (2rp, 2rp+1) at coarse col J0 + m
@@ -685,7 +689,7 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
         // so an item loads 2L + 2 RPI - 2 rows instead of 2L RPI.
         // four rows per item only where two-row items would need a second pass
         // of the block's threads (small tiles: the longer chain would cost more)
-        constexpr int RPI = (IW % 4 == 0 && (IW / 2) * CP > kThreads) ? 4 : 2;
+        constexpr int RPI = (IW % 4 == 0 && (IW / 2) * CP > NT) ? 4 : 2;
         static_assert(IW % RPI == 0, "column-pass items take RPI coarse rows");
         auto col_item = [&](int ip, int cp) {
             const int I0 = -H / 2 + RPI * ip;
@@ -750,7 +754,7 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
 #pragma unroll 1
             for (int q = 0; q < 2; ++q) {
                 const int j = 2 * s + q + 1;
-                half_sweep<CK, A, (TY >= 32)>(X, B, j, R - j, q);
+                half_sweep<CK, A, (TY >= 32), NT>(X, B, j, R - j, q);
                 __syncthreads();
             }
         }
@@ -812,7 +816,7 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
 #pragma unroll 1
         for (int q = 0; q < 2; ++q) {
             const int j = 2 * s + q + 1;
-            half_sweep<CK, A, (TY >= 32)>(X, B, j, R - j, q);
+            half_sweep<CK, A, (TY >= 32), NT>(X, B, j, R - j, q);
             __syncthreads();
         }
     }
@@ -1259,6 +1263,42 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(T *__restrict__ x, co
                                                            FirTaps taps) {
     pdl_enter();
     bottom_body<T>(x, b, n, nlev, nu1, nu2, zero_init, ainv, taps);
+}
+
+// k_coarse_cluster: the down pass of the 128^2 level, the bottom V-cycle of
+// the levels <= 64^2 and the up pass of the 128^2 level in one launch: a
+// thread-block cluster of 8 CTAs of 1024 threads.  CTA r takes tile r of the
+// 128^2 level (32 x 64 points, the tile functions of k_down / k_up with 1024
+// threads; every point's arithmetic is theirs, so the results are the bits of
+// the three separate launches), then CTA 0 runs the bottom V-cycle while the
+// others wait, then every CTA prolongs, corrects and post-smooths its tile.
+// The phases are ordered by the cluster's hardware barrier with release /
+// acquire semantics, which also makes one phase's global writes visible to
+// the next; the loads of data written inside the launch (the smoothed tile t
+// and the bottom's correction xb) bypass the non-coherent read-only path.
+constexpr int kCoarseCTAs = 8;
+constexpr int kCoarseN = 128;  // the level above the bottom solve (64^2 and below)
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int NU1, int NU2>
+__global__ void __cluster_dims__(kCoarseCTAs, 1, 1) __launch_bounds__(kBottomThreads)
+    k_coarse_cluster(float *__restrict__ x, float *__restrict__ t, const float *__restrict__ b,
+                     float *__restrict__ xb, float *__restrict__ bb, int nlev, const float *__restrict__ ainv,
+                     FirTaps taps) {
+    pdl_enter();
+    constexpr int n = kCoarseN, TY = 32;
+    constexpr int tpr = n / kTX;
+    static_assert((n / TY) * tpr == kCoarseCTAs, "one tile per CTA");
+    const int r = blockIdx.x;
+    const int ty0 = (r / tpr) * TY, tx0 = (r % tpr) * kTX;
+    down_tile<float, NU1, TY, false, kBottomThreads>(x, t, b, n, bb, ty0, tx0, true);
+    cluster_barrier();
+    if (r == 0) bottom_body<float>(xb, bb, n / 2, nlev, NU1, NU2, 1, ainv, taps);
+    cluster_barrier();
+    up_tile<float, NU2, TY, 2, kBottomThreads, true>(t, x, b, xb, nullptr, n, taps, ty0, tx0);
 }
 
 // one block per grid of the table
@@ -2180,6 +2220,25 @@ cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu
                                         x, b, n, nlev, nu1, nu2, zero_init ? 1 : 0, ainv, taps);
         if (le_ != cudaSuccess) return le_;
     }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_cluster(float *x, float *t, const float *b, float *xb, float *bb, int coarsest, int nu1,
+                                  int nu2, const float *ainv, const FirTaps &taps, cudaStream_t s) {
+    if (nu1 != 2 || nu2 != 2 || coarsest < 4 || coarsest > kCoarseN / 2) return cudaErrorInvalidValue;
+    int nlev = 0;
+    for (int m = kCoarseN / 2; m >= coarsest; m >>= 1) ++nlev;
+    if (((kCoarseN / 2) >> (nlev - 1)) != coarsest || nlev > 8) return cudaErrorInvalidValue;
+    size_t smem = bottom_smem_max() * sizeof(float);
+    smem = std::max(smem, DownCfg<float, 2, 32>::smem);
+    smem = std::max(smem, UpCfg<float, 2, 32, 2>::smem);
+    auto k = k_coarse_cluster<2, 2>;
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = set_smem_once(k, smem, done);
+    if (e != cudaSuccess) return e;
+    e = launch_kernel(k, kCoarseCTAs, kBottomThreads, smem, s, x, t, b, xb, bb, nlev, ainv, taps);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }

@@ -102,6 +102,17 @@ std::atomic<int> g_tma_tiles{0};
 
 int tma_tiles_mode() { return g_tma_tiles.load(std::memory_order_relaxed); }
 
+namespace {
+std::atomic<int> g_coarse_cluster{1};
+}
+
+int coarse_cluster_mode() { return g_coarse_cluster.load(std::memory_order_relaxed); }
+
+void set_coarse_cluster(int on) {
+    const int old = g_coarse_cluster.exchange(on ? 1 : 0);
+    if (old != (on ? 1 : 0)) g_epoch.fetch_add(1);
+}
+
 void set_tma_tiles(int on) {
     const int old = g_tma_tiles.exchange(on ? 1 : 0);
     if (old != (on ? 1 : 0)) g_epoch.fetch_add(1);

@@ -76,6 +76,8 @@ SIGNATURES = {
     "mg_trainer_set_lr": (_I, [_VP, _D]),
     "mg_trainer_set_tensor_cores": (_I, [_VP, _I]),
     "mg_set_tma_tiles": (_I, [_I]),
+    "mg_set_coarse_cluster": (_I, [_I]),
+    "mg_get_coarse_cluster": (_I, []),
     "mg_get_tma_tiles": (_I, []),
     "mg_trainer_get_tensor_cores": (_I, [_VP, C.POINTER(_I)]),
     "mg_trainer_get_weights": (_I, [_VP, _VP, _SZ]),
@@ -335,6 +337,15 @@ def set_launch_overlap(mode):
     """Programmatic dependent launch between library kernels: 0 / False off,
     1 / True every kernel, 2 kernels of grids of at most one wave."""
     _check(load().mg_set_launch_overlap(int(mode)))
+
+
+def set_coarse_cluster(on: bool):
+    """Run a single solve's 128^2 level and bottom V-cycle as one 8-CTA cluster launch (True) or three launches."""
+    _check(load().mg_set_coarse_cluster(int(bool(on))))
+
+
+def get_coarse_cluster() -> bool:
+    return bool(load().mg_get_coarse_cluster())
 
 
 def set_tma_tiles(on: bool):
