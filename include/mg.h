@@ -281,7 +281,9 @@ mg_status mg_autotune(mg_ctx *ctx, const char *cache_path, int *n_timed);
  * blocks (about one wave: the coarse levels, the bottom solve, the outer and
  * convergence kernels).  Results are identical in every mode; graphs recorded
  * before a change are re-recorded.  Returns MG_ERR_INVALID_ARG for other
- * modes.  (Measured on GB300: both modes slower for these graphs, hence off.) */
+ * modes.  (Measured on GB300: both modes slower for these graphs, hence off.)  Every
+ * kernel waits on its predecessors at its start and signals its dependents
+ * when each block exits. */
 mg_status mg_set_launch_overlap(int enable);
 int mg_get_launch_overlap(void);
 

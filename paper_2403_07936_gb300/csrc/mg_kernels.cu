@@ -58,14 +58,13 @@ constexpr int kThreads = 256;  // threads per tile block
 
 // Programmatic dependent launch.  Every kernel of the path starts with
 // pdl_enter(): griddepcontrol.wait blocks until the grids this one depends on
-// have completed and their writes are visible, then launch_dependents lets
-// the next kernel in the stream start launching (its blocks get scheduled on
-// SMs that this grid's tail leaves idle, and wait there in turn).  For a
-// kernel launched without the attribute both instructions return at once.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// have completed and their writes are visible.  A block signals its
+// dependents implicitly when it exits, so the next kernel in the stream is
+// launched once every block of this grid has finished its work (its launch
+// then overlaps this grid's completion and memory flush) and never takes SM
+// resources from blocks of this grid still waiting to run.  For a kernel
+// launched without the attribute the wait returns at once.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Packed FP32x2 arithmetic (Blackwell): two IEEE round-to-nearest float
 // operations per instruction, lane by lane the same bits as the scalar ones.
