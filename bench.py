@@ -162,7 +162,9 @@ def read_capture(kernel_kind):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 50 ms while the timed region runs."""
+    """nvidia-smi clock/throttle samples every 10 ms while the timed region runs
+    (the region starts once the first sample is in, so start-up latency of
+    nvidia-smi does not leave the region unsampled)."""
 
     def __init__(self, gpu_index):
         self.path = tempfile.mktemp(suffix=".csv")
@@ -174,10 +176,16 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.005)
         return self
 
     def __exit__(self, *exc):
