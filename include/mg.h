@@ -130,10 +130,19 @@ mg_status mg_set_prolong_policy(mg_ctx *ctx, double n_gan, double s_thres);
  * Returns MG_ERR_BAD_WEIGHTS on any mismatch. */
 mg_status mg_load_prolong_weights(mg_ctx *ctx, const void *blob, size_t bytes);
 
+/* Cold starts (Algorithm 6 iterates from an initial guess; the configurations
+ * here start from p = 0): with on = 1 the context's solves (mg_solve,
+ * mg_two_level_solve) start from x = 0 and never read x, so a host x is not
+ * copied to the device (the device copy, or a device x, is zeroed there);
+ * on = 0 (the default): x is the initial guess.  MG_ERR_INVALID_ARG for a
+ * null context or other values. */
+mg_status mg_set_zero_guess(mg_ctx *ctx, int on);
+
 /* Solve A x = f to ||f - A x||_2 / ||f||_2 <= tol.  f: N*N doubles (device or
  * host), not modified.  x: N*N doubles (device or host), the initial guess on
- * entry (warm start; zeros for a cold start) and the zero-mean solution on
- * return.  info may be NULL.  Returns MG_ERR_NOT_CONVERGED (x = last iterate)
+ * entry (warm start; zeros for a cold start, or any contents after
+ * mg_set_zero_guess(ctx, 1)) and the zero-mean solution on return.  info may
+ * be NULL.  Returns MG_ERR_NOT_CONVERGED (x = last iterate)
  * if max_cycles V-cycles do not reach tol, MG_ERR_NONFINITE for NaN/Inf. */
 mg_status mg_solve(mg_ctx *ctx, const double *f, double *x, double tol, mg_prolong prolong,
                    mg_solve_info *info);

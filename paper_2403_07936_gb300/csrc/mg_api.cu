@@ -141,6 +141,7 @@ struct mg_ctx {
     // outer step, chosen from the residual with contraction rho (0: fixed `inner`)
     int adapt_max = 3;
     double rho = 0.06;
+    bool zero_guess = false;  // solves start from x = 0 and do not read x (mg_set_zero_guess)
     cudaStream_t stream = nullptr;
     Level lv[kMaxLevels];
     void *h32_block = nullptr, *h64_block = nullptr;
@@ -395,14 +396,18 @@ static mg_status vcycle32_top(mg_ctx *c, bool zero, mg_prolong prolong) {
     return vcycle_rec<float>(c, 0, x, t, b, zero);
 }
 
+// Device views of f and x for a call; host buffers are staged into the
+// context's device copies.  zero_x: x is output only (a solve from x = 0): a
+// host x is not copied in and the device copy, or a device x, is zeroed.
 static mg_status resolve_io(mg_ctx *c, const double *f, double *x, const double **fd, double **xd,
-                            bool *staged) {
+                            bool *staged, bool zero_x = false) {
     const size_t bytes = (size_t)c->N * c->N * sizeof(double);
     const bool fdev = is_device_pointer(f), xdev = is_device_pointer(x);
     *staged = !xdev;
     if (fdev && xdev) {
         *fd = f;
         *xd = x;
+        if (zero_x) MG_CUDA(cudaMemsetAsync(x, 0, bytes, c->stream));
         return MG_OK;
     }
     if (!c->f_stage) MG_CUDA(cudaMalloc(&c->f_stage, bytes));
@@ -415,8 +420,10 @@ static mg_status resolve_io(mg_ctx *c, const double *f, double *x, const double 
     }
     if (xdev) {
         *xd = x;
+        if (zero_x) MG_CUDA(cudaMemsetAsync(x, 0, bytes, c->stream));
     } else {
-        MG_CUDA(cudaMemcpyAsync(c->x_stage, x, bytes, cudaMemcpyHostToDevice, c->stream));
+        if (zero_x) MG_CUDA(cudaMemsetAsync(c->x_stage, 0, bytes, c->stream));
+        else MG_CUDA(cudaMemcpyAsync(c->x_stage, x, bytes, cudaMemcpyHostToDevice, c->stream));
         *xd = c->x_stage;
     }
     return MG_OK;
@@ -1781,7 +1788,7 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     const double *fd;
     double *xd;
     bool staged;
-    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged));
+    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged, c->zero_guess));
     const int N = c->N;
     const double N2 = (double)N * N;
     const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
@@ -2019,7 +2026,7 @@ mg_status mg_two_level_solve(mg_ctx *c, const double *f, double *x, double tol, 
     const double *fd;
     double *xd;
     bool staged;
-    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged));
+    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged, c->zero_guess));
     const int N = c->N;
     const double N2 = (double)N * N;
     const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
@@ -2202,6 +2209,15 @@ mg_status mg_set_launch_overlap(int enable) {
 }
 
 int mg_get_launch_overlap(void) { return launch_overlap_mode(); }
+
+mg_status mg_set_zero_guess(mg_ctx *c, int on) {
+    if (!c || (on != 0 && on != 1)) {
+        set_err("null context or zero-guess flag not 0 / 1");
+        return MG_ERR_INVALID_ARG;
+    }
+    c->zero_guess = on != 0;
+    return MG_OK;
+}
 
 mg_status mg_set_coarse_cluster(int on) {
     if (on != 0 && on != 1) {

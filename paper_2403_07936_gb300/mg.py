@@ -76,6 +76,7 @@ SIGNATURES = {
     "mg_trainer_set_lr": (_I, [_VP, _D]),
     "mg_trainer_set_tensor_cores": (_I, [_VP, _I]),
     "mg_set_tma_tiles": (_I, [_I]),
+    "mg_set_zero_guess": (_I, [_VP, _I]),
     "mg_set_coarse_cluster": (_I, [_I]),
     "mg_get_coarse_cluster": (_I, []),
     "mg_get_tma_tiles": (_I, []),
@@ -235,6 +236,10 @@ class Context:
         if check and st != MG_OK:
             _check(st)
         return d
+
+    def set_zero_guess(self, on: bool):
+        """Solves start from x = 0 and never read x (no host-to-device copy of a host x)."""
+        _check(load().mg_set_zero_guess(self._h, int(bool(on))))
 
     def vcycle(self, f, x, prolong: str = "cubic"):
         _check(load().mg_vcycle(self._h, ptr(f), ptr(x), PROLONG[prolong]))

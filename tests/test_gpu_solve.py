@@ -395,3 +395,31 @@ def test_adaptive_cycles_respect_the_cycle_cap(mg):
         x = torch.zeros_like(ft)
         info = ctx.solve(ft, x, check=False)
         assert info["status"] == "MG_ERR_NOT_CONVERGED" and info["vcycles"] == 5
+
+
+@pytest.mark.parametrize("host", [True, False], ids=["host-buffers", "device-buffers"])
+def test_zero_guess_ignores_the_contents_of_x(mg, host):
+    """mg_set_zero_guess: a solve starts from x = 0 whatever x holds (a host x
+    is not copied in), with the bits of a solve from an x of zeros."""
+    n = 512
+    f = turbulent_source(n, default_kmax(n), config_seed(2, 61))
+    ft = torch.tensor(f, device=DEV)
+    ctx = mg.Context(_levels(n), n)
+    x0 = torch.zeros_like(ft)
+    i0 = ctx.solve(ft, x0, tol=1e-10)
+    torch.cuda.synchronize()
+    ctx.set_zero_guess(True)
+    garbage = torch.full((n, n), 1e30, dtype=torch.float64)
+    if host:
+        fh = torch.tensor(f).pin_memory()
+        xg = garbage.pin_memory()
+        i1 = ctx.solve(fh, xg, tol=1e-10)
+        got = xg.numpy()
+    else:
+        xg = garbage.to(DEV)
+        i1 = ctx.solve(ft, xg, tol=1e-10)
+        torch.cuda.synchronize()
+        got = xg.cpu().numpy()
+    ctx.set_zero_guess(False)
+    assert i1["vcycles"] == i0["vcycles"] and np.array_equal(got, x0.cpu().numpy())
+    assert mg.load().mg_set_zero_guess(ctx.handle, 2) == 1  # MG_ERR_INVALID_ARG
