@@ -44,7 +44,8 @@ PROBE_NAMES = {1: "k_down<float,2> (finest: 2 RB-GS sweeps + residual + FW)",
                2: "k_up<float,2> (finest: cubic prolongation + correction + 2 RB-GS sweeps)",
                3: "k_outer_residual (binary64 operands, exact integer stencil sum, one rounding to float, norms)",
                4: "k_update (FP64 x += e)",
-               5: "coarse levels (1024^2 down to the bottom kernel and back, one span per V-cycle)"}
+               5: "coarse levels (1024^2 down to the bottom kernel and back, one span per V-cycle)",
+               6: "k_update_residual (FP64 x + e into the other iterate buffer, fused with the next outer residual)"}
 # FP32 finest-level stencils (V(2,2)): the per-point algorithmic bytes of the
 # unfused steps a launch performs, 4 B x (2 sweeps x 3 words + 2.25 words of
 # residual + restriction, or of prolongation + correction) = 33 B, against the
@@ -786,7 +787,7 @@ def main():
     # kind (the probe runs the host-loop execution mode, whose kernels are the
     # graph's).  First pick the kernel kind with the largest time per solve.
     kernel_ms = {}
-    for kind in (1, 2, 3, 4, 5):
+    for kind in (1, 2, 3, 4, 5, 6):
         ctx.probe(kind, 256)
         timed_solves(ctx, 1, f_dev, x)
         n_l, ms, by = ctx.probe_read()

@@ -320,6 +320,20 @@ int mg_get_tma_tiles(void);
 mg_status mg_set_coarse_cluster(int on);
 int mg_get_coarse_cluster(void);
 
+/* Launch form of a mixed solve's outer step (FP64 defect correction: x += e,
+ * then r = f - A x for the convergence test and the next step; grids of
+ * N >= 32).  on = 1 (the default): the update and the next residual run as
+ * one launch that reads x and e once, writes x + e into the other buffer of a
+ * pair (the caller's x and a context buffer, alternating each outer step) and
+ * forms the residual of x + e from the same loads; the solve's projection
+ * writes the caller's x.  on = 0: an update launch and a residual launch.  x,
+ * the residuals and every decision are identical bit for bit; the reported
+ * update_norm is the same sum in another order (equal to about 1e-15
+ * relative).  Graphs recorded before a change are re-recorded.
+ * MG_ERR_INVALID_ARG for other values. */
+mg_status mg_set_fused_update(int on);
+int mg_get_fused_update(void);
+
 /* Read or set one table entry (n a power of two >= 128, nu 0..4). */
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant);
 mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);
@@ -399,7 +413,8 @@ unsigned long long mg_kernel_launches(void);
  * 2 = finest-level prolongation/post-smoothing kernel, 3 = outer residual
  * (the exact sum of the FP64 iterate's residual), 4 = FP64 update, 5 = the
  * coarse part of an FP32 V-cycle (every
- * launch below the finest level, as one span); 0 disables.  At most
+ * launch below the finest level, as one span), 6 = the FP64 update fused with
+ * the next outer residual (mg_set_fused_update); 0 disables.  At most
  * `capacity` launches (spans) are recorded until mg_probe_read. */
 mg_status mg_probe_kernel(mg_ctx *ctx, int kind, int capacity);
 

@@ -149,6 +149,10 @@ struct mg_ctx {
     // each solve's first outer residual (mixed contexts; FP64 ones use lv[0].b64)
     double *bsc64 = nullptr;
     int *ebt = nullptr;  // per residual task of the finest grid: bsc64's alignment exponent (N >= kResMinN)
+    // the second FP64 iterate of a mixed solve whose outer steps fuse the
+    // update with the next residual (N >= kResMinN): the steps alternate
+    // between the solve's x and this buffer
+    double *xalt = nullptr;
     float *ainv32 = nullptr;
     double *ainv64 = nullptr;
     FirTaps taps;
@@ -186,7 +190,15 @@ struct mg_ctx {
 };
 
 enum { kGrpF = 0, kGrpR = 1, kGrpU = 2, kGrpX = 3 };
-enum { kProbeNone = 0, kProbeDown = 1, kProbeUp = 2, kProbeResidual = 3, kProbeUpdate = 4, kProbeCoarse = 5 };
+enum {
+    kProbeNone = 0,
+    kProbeDown = 1,
+    kProbeUp = 2,
+    kProbeResidual = 3,
+    kProbeUpdate = 4,
+    kProbeCoarse = 5,
+    kProbeUpdateResidual = 6
+};
 
 // Algorithmic bytes of the coarse part of a V-cycle below level l0: 13 B per
 // point for each tile kernel (down and up) of every tiled level, and the
@@ -240,6 +252,8 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
     const size_t ebt_off = total;
     const bool tasks = !fp64 && c->N >= kResMinN;
     if (tasks) total += align_up(res_tasks(c->N) * sizeof(int));
+    const size_t xalt_off = total;
+    if (tasks) total += align_up((size_t)c->N * c->N * sizeof(double));
     MG_CUDA(cudaMalloc(&blk, total));
     MG_CUDA(cudaMemsetAsync(blk, 0, total, c->stream));
     char *p = (char *)blk;
@@ -258,7 +272,10 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
         p += 3 * bytes;
     }
     if (!fp64) c->bsc64 = (double *)((char *)blk + bsc_off);
-    if (tasks) c->ebt = (int *)((char *)blk + ebt_off);
+    if (tasks) {
+        c->ebt = (int *)((char *)blk + ebt_off);
+        c->xalt = (double *)((char *)blk + xalt_off);
+    }
     if (!fp64) {
         int bc = 0, br = 0;
         down_tma_box(2, &bc, &br);
@@ -309,6 +326,18 @@ static cudaError_t solve_residual(mg_ctx *c, const double *fd, const double *xd,
                                            reinterpret_cast<long long *>(c->bsc64), c->ebt, c->red(kGrpR), s);
     return launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr, first,
                                  scaled_rhs(c, mixed), !first, c->red(kGrpR), s);
+}
+
+// Whether a solve fuses each outer step's update with the next residual.
+static bool fused_update(const mg_ctx *c, bool mixed) { return mixed && c->N >= kResMinN && c->xalt && fused_update_mode(); }
+
+// The update of outer step k (from 1) fused with the residual that follows
+// it; par_dev (the graph's device step counter, k - 1 when the kernel runs)
+// or else k - 1 selects which buffer of (xd, xalt) holds the step's x.
+static cudaError_t solve_update_residual(mg_ctx *c, double *xd, const int *par_dev, int par_host, double h2,
+                                         cudaStream_t s) {
+    return launch_update_residual_tasks(xd, c->xalt, par_dev, par_host, c->lv[0].x32, c->N, h2, c->lv[0].b32,
+                                        reinterpret_cast<long long *>(c->bsc64), c->ebt, c->red(kGrpR), s);
 }
 
 template <typename T> static T *lvx(mg_ctx *c, int l);
@@ -522,6 +551,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
     mg_status st = MG_OK;
     long long n_pro = 0, n_body = 0, n_epi = 0, n_sr = 0;
     const bool use_policy = mixed && prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax;
+    const bool fuse = fused_update(c, mixed);
     auto fail = [&](cudaError_t e, const char *what) {
         set_err("graph recording (%s) failed: %s", what, cudaGetErrorString(e));
         st = MG_ERR_CUDA;
@@ -581,7 +611,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
             }
             if (e != cudaSuccess) { fail(e, "if handle"); break; }
             if (st != MG_OK) break;
-            e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
+            if (!fuse) e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
         } else if (adaptive) {
             // V-cycle 1 always; V-cycles 2 .. step each behind an IF node
             st = vcycle32_top(c, true, prolong);
@@ -616,19 +646,23 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
             }
             if (st != MG_OK) break;
             if (e != cudaSuccess) { fail(e, "optional cycles"); break; }
-            e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
+            if (!fuse) e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
         } else if (mixed) {
             for (int k = 0; k < c->inner && st == MG_OK; ++k) st = vcycle32_top(c, k == 0, prolong);
             if (st != MG_OK) break;
-            e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
+            if (!fuse) e = launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s);
         } else {
             st = vcycle_rec<double>(c, 0, xd, c->lv[0].t64, c->lv[0].b64, false);
             if (st != MG_OK) break;
         }
-        if (e == cudaSuccess) e = solve_residual(c, fd, xd, mixed, false, h2, s);
+        // the fused form reads the step counter before k_check advances it
         if (e == cudaSuccess)
-            e = launch_check(c->dstate, c->out(kGrpR), mixed ? c->out(kGrpU) : nullptr, c->out(kGrpF),
-                             N2, h2, tol, step, c->max_cycles, false, handle, s, rho, ifh);
+            e = fuse ? solve_update_residual(c, xd, &c->dstate->outer, 0, h2, s)
+                     : solve_residual(c, fd, xd, mixed, false, h2, s);
+        if (e == cudaSuccess)
+            e = launch_check(c->dstate, c->out(kGrpR),
+                             mixed ? (fuse ? c->out(kGrpR) + 1 : c->out(kGrpU)) : nullptr, c->out(kGrpF), N2, h2,
+                             tol, step, c->max_cycles, false, handle, s, rho, ifh);
         if (e != cudaSuccess) { fail(e, "body"); break; }
         e = cudaStreamEndCapture(s, &body);
         capturing = false;
@@ -639,8 +673,11 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
         e = cudaStreamBeginCaptureToGraph(s, g, &cond, nullptr, 1, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { fail(e, "begin epilogue"); break; }
         capturing = true;
-        e = launch_sum(xd, N, c->red(kGrpX), s);
-        if (e == cudaSuccess) e = launch_project(xd, N, c->out(kGrpX), s, &c->dstate->zero_source);
+        // after k outer steps of the fused form, x is in xalt when k is odd
+        e = launch_sum(xd, N, c->red(kGrpX), s, fuse ? c->xalt : nullptr, fuse ? &c->dstate->outer : nullptr);
+        if (e == cudaSuccess)
+            e = launch_project(xd, N, c->out(kGrpX), s, &c->dstate->zero_source, fuse ? c->xalt : nullptr,
+                               fuse ? &c->dstate->outer : nullptr);
         if (e != cudaSuccess) { fail(e, "epilogue"); break; }
         e = cudaStreamEndCapture(s, &g);
         capturing = false;
@@ -1844,14 +1881,23 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     // the prolongation policy, decided on the host with the same rule as k_policy
     const bool use_policy = mixed && prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax;
     const bool adaptive = mixed && !use_policy && c->rho > 0.0 && c->adapt_max > 1;
+    const bool fuse = fused_update(c, mixed);
     int sr_used = 0;
     bool sr_step = false, fallback = false;
     double rel_prev = 0.0;
     for (;;) {
-        probe_begin(c, kProbeResidual);
-        // the first residual computes and stores b = h^2 (f - mu), later ones load it
-        MG_CUDA(solve_residual(c, fd, xd, mixed, first, h2, s));
-        probe_end(c, kProbeResidual, N2 * ((first ? 24.0 : 16.0) + (mixed ? 4.0 : 0.0)));
+        if (first || !fuse) {
+            probe_begin(c, kProbeResidual);
+            // the first residual computes and stores b = h^2 (f - mu), later ones load it
+            MG_CUDA(solve_residual(c, fd, xd, mixed, first, h2, s));
+            probe_end(c, kProbeResidual, N2 * ((first ? 24.0 : 16.0) + (mixed ? 4.0 : 0.0)));
+        } else {
+            // the update of the outer step just run, fused with this residual:
+            // x + e (12 bytes a point in, 8 out), b (8 in), the float residual (4 out)
+            probe_begin(c, kProbeUpdateResidual);
+            MG_CUDA(solve_update_residual(c, xd, nullptr, (outer - 1) & 1, h2, s));
+            probe_end(c, kProbeUpdateResidual, N2 * 32.0);
+        }
         MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 2 * kMaxSlots,
                                 cudaMemcpyDeviceToHost, s));
         MG_CUDA(cudaStreamSynchronize(s));
@@ -1903,18 +1949,24 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
                 }
                 MG_TRY(vcycle32_top(c, k == 0, pk));
             }
-            probe_begin(c, kProbeUpdate);
-            MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
-            probe_end(c, kProbeUpdate, N2 * 20.0);
+            if (!fuse) {
+                probe_begin(c, kProbeUpdate);
+                MG_CUDA(launch_update(xd, c->lv[0].x32, N, c->red(kGrpU), s));
+                probe_end(c, kProbeUpdate, N2 * 20.0);
+            }
         } else {
             MG_TRY(vcycle_rec<double>(c, 0, xd, c->lv[0].t64, c->lv[0].b64, false));
             ++cycles;
         }
         ++outer;
     }
+    // the fused form leaves x in xalt after an odd number of outer steps
+    const double *x_last = (fuse && (outer & 1)) ? c->xalt : nullptr;
     if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
-        MG_CUDA(launch_sum(xd, N, c->red(kGrpX), s));
-        MG_CUDA(launch_project(xd, N, c->out(kGrpX), s));
+        MG_CUDA(launch_sum(xd, N, c->red(kGrpX), s, x_last));
+        MG_CUDA(launch_project(xd, N, c->out(kGrpX), s, nullptr, x_last));
+    } else if (x_last) {
+        MG_CUDA(cudaMemcpyAsync(xd, x_last, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, s));
     }
     if (staged) MG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
     MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 4 * kMaxSlots,
@@ -1932,7 +1984,8 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         info->vcycles = cycles;
         info->rel_residual = rel;
         info->removed_mean = mu;
-        info->update_norm = mixed && outer > 0 ? sqrt(c->host_out[kGrpU * kMaxSlots]) : 0.0;
+        info->update_norm =
+            mixed && outer > 0 ? sqrt(c->host_out[fuse ? kGrpR * kMaxSlots + 1 : kGrpU * kMaxSlots]) : 0.0;
         info->sr_cycles = sr_used;
         info->prolong_used = sr_used > 0 ? MG_PROLONG_SR : MG_PROLONG_CUBIC;
         info->sr_fallback = fallback ? 1 : 0;
@@ -2230,6 +2283,17 @@ mg_status mg_set_coarse_cluster(int on) {
 
 int mg_get_coarse_cluster(void) { return coarse_cluster_mode(); }
 
+mg_status mg_set_fused_update(int on) {
+    if (on != 0 && on != 1) {
+        set_err("fused update: 0 (separate update and residual) or 1 (one fused launch)");
+        return MG_ERR_INVALID_ARG;
+    }
+    set_fused_update(on);
+    return MG_OK;
+}
+
+int mg_get_fused_update(void) { return fused_update_mode(); }
+
 mg_status mg_set_tma_tiles(int on) {
     if (on != 0 && on != 1) {
         set_err("TMA tiles: 0 (vector loads) or 1 (TMA-staged interior tiles)");
@@ -2262,7 +2326,7 @@ mg_status mg_set_tile_variant(int kind, int n, int nu, int variant) {
 }
 
 mg_status mg_probe_kernel(mg_ctx *c, int kind, int capacity) {
-    if (!c || kind < kProbeNone || kind > kProbeCoarse || capacity < 0 || capacity > 4096) {
+    if (!c || kind < kProbeNone || kind > kProbeUpdateResidual || capacity < 0 || capacity > 4096) {
         set_err("invalid probe request");
         return MG_ERR_INVALID_ARG;
     }

@@ -375,6 +375,10 @@ cudaError_t launch_coarse_cluster(float *x, float *t, const float *b, float *xb,
 // 1: single solves run the coarse tail (128^2 and below) as one cluster launch
 int coarse_cluster_mode();
 void set_coarse_cluster(int on);
+// 1: single mixed solves fuse each outer step's update with the next residual
+// (launch_update_residual_tasks) on a pair of FP64 iterates
+int fused_update_mode();
+void set_fused_update(int on);
 // 2D tensor map of an n x n FP32 grid with boxes of cols x rows (false if the
 // driver's encoder is unavailable or rejects the map)
 bool make_grid_map_f32(CUtensorMap *m, void *base, int n, int cols, int rows);
@@ -559,10 +563,23 @@ cudaError_t launch_outer_residual(const double *f, const double *x, int n, doubl
                                   const double *mu_sum, double mu_host, float *s32,
                                   bool want_fnorm, double *bsc, bool load_b, Reduction red, cudaStream_t s);
 cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaStream_t s);
-// x -= sum / n^2, or x = 0 where *zero_flag is set (zero_flag may be null)
-cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s,
-                           const int *zero_flag = nullptr);
-cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s);
+// An outer step's update fused with the next (steady) task-tiled residual:
+// x_new = x_old + e into the other buffer of the pair (xa, xb), the residual
+// of x_new into s32, out[0] = sum of its squares, out[1] = sum of e^2.  The
+// source is xb when the parity (*par_dev if non-null, else par_host) is odd.
+// x_new and the residual are bit for bit those of launch_update followed by
+// launch_outer_residual_tasks(first = false).
+cudaError_t launch_update_residual_tasks(double *xa, double *xb, const int *par_dev, int par_host, const float *e,
+                                         int n, double h2, float *s32, long long *bint, int *ebt, Reduction red,
+                                         cudaStream_t s);
+// x -= sum / n^2, or x = 0 where *zero_flag is set (zero_flag may be null);
+// with alt given the values are read from alt (when par is null or *par is
+// odd; par is a device pointer, read when the kernel runs).
+cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag = nullptr,
+                           const double *alt = nullptr, const int *par = nullptr);
+// the sum of x (of alt when alt is given and par is null or *par is odd)
+cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s, const double *alt = nullptr,
+                       const int *par = nullptr);
 // out[i] = the integer-pipe conversion of in[i] (dir 0: double -> float, 1: float -> double)
 cudaError_t launch_convert(int dir, size_t count, const void *in, void *out, cudaStream_t s);
 

@@ -1319,9 +1319,18 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom_batched(const BottomG
 // threads with kUnroll independent points per iteration (loads in flight).
 constexpr int kUnroll = 4;
 
-__global__ void __launch_bounds__(kRedThreads) k_sum(const double *__restrict__ a, size_t N,
-                                                     Reduction red) {
+// The sums and the projection below read `alt` instead of their own array
+// when par is null or *par is odd (the launchers pass alt = a when there is no
+// alternative): a mixed solve whose fused update alternates a pair of FP64
+// iterates sums and projects whichever holds the last one.
+__device__ __forceinline__ const double *pick_src(const double *a, const double *alt, const int *par) {
+    return (par ? (*par & 1) : 1) ? alt : a;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum(const double *a0, size_t N, Reduction red,
+                                                     const double *alt, const int *par) {
     pdl_enter();
+    const double *__restrict__ a = pick_src(a0, alt, par);
     __shared__ double sh[32];
     double v = 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -1342,8 +1351,10 @@ __global__ void __launch_bounds__(kRedThreads) k_sum(const double *__restrict__ 
 // The same sum on 16-byte-aligned data (N a multiple of 4): two 16-byte loads
 // per thread and iteration, four groups in flight, so that enough loads are
 // outstanding to cover the memory latency (the scalar form is latency-bound).
-__global__ void __launch_bounds__(kRedThreads) k_sum_v(const double *__restrict__ a, size_t N, Reduction red) {
+__global__ void __launch_bounds__(kRedThreads) k_sum_v(const double *a0, size_t N, Reduction red,
+                                                       const double *alt, const int *par) {
     pdl_enter();
+    const double *__restrict__ a = pick_src(a0, alt, par);
     __shared__ double sh[32];
     double v = 0.0;
     const size_t G = N >> 1, stride = (size_t)gridDim.x * blockDim.x;
@@ -1477,11 +1488,17 @@ __device__ __forceinline__ float aligned_to_f32(long long acc, int E) {
     return exact_to_f32(acc, E);
 }
 
-template <bool FIRST>
+// UPD (steady residuals only): the task first applies the outer step's FP64
+// update x + e to every value it loads (its own rows, the neighbour rows and
+// the halo columns, by the addition the update kernel makes), stores its own
+// rows to xo and sums their e^2 into ee; the residual is then that of x + e.
+template <bool FIRST, bool UPD = false>
 __device__ __forceinline__ void residual_task(int task, int n, int lg, const double *__restrict__ f, double mu,
                                               double h2, long long *__restrict__ bint, int *__restrict__ ebt,
                                               const double *__restrict__ x, float *__restrict__ s32, SqSum &ss,
-                                              double &ff) {
+                                              double &ff, const float *__restrict__ e = nullptr,
+                                              double *__restrict__ xo = nullptr, SqSum *ee = nullptr) {
+    static_assert(!(FIRST && UPD), "the first residual of a solve has no update");
     constexpr int R = kResRows;
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1495,6 +1512,21 @@ __device__ __forceinline__ void residual_task(int task, int n, int lg, const dou
     const int hk = lane & 15;
     double hv = 0.0;
     if (hk < R) hv = x[((size_t)(r0 + hk) << lg) + ((lane < 16 ? c0 - 1 : c0 + 32) & (n - 1))];
+    if (UPD) {
+        float ev[R + 2];
+#pragma unroll
+        for (int k = 0; k < R + 2; ++k) ev[k] = e[((size_t)((r0 - 1 + k) & (n - 1)) << lg) + c];
+        float he = 0.f;
+        if (hk < R) he = e[((size_t)(r0 + hk) << lg) + ((lane < 16 ? c0 - 1 : c0 + 32) & (n - 1))];
+#pragma unroll
+        for (int k = 0; k < R + 2; ++k) xv[k] = xv[k] + f32_to_f64(ev[k]);
+        hv = hv + f32_to_f64(he);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            xo[((size_t)(r0 + k) << lg) + c] = xv[k + 1];
+            ee->add(ev[k + 1]);
+        }
+    }
     long long bq[R];
     int eb;
     if (FIRST) {
@@ -1560,6 +1592,34 @@ __global__ void __launch_bounds__(kRedThreads, FIRST ? 2 : 3) k_outer_residual_t
     double vals[2];
     vals[0] = block_sum(ss.value(), sh);
     vals[1] = FIRST ? block_sum(ff, sh) : 0.0;
+    reduce_finish<2>(red, vals, sh);
+}
+
+// An outer step's FP64 update fused with the next outer residual (mixed
+// solves of n >= kResMinN): x_new = x_old + e, written to the other buffer of
+// the pair (xa, xb), and the task-tiled residual of x_new from the same loads,
+// with out[0] = sum of the float residual's squares and out[1] = sum of e^2.
+// Every task reads x_old and writes x_new in different buffers, so no task
+// reads what another writes; each stored x_new and each residual is bit for
+// bit that of k_update_v followed by k_outer_residual_t<false>.  The source
+// buffer is xb when the parity (*par_dev, else par_host) is odd, else xa.
+__global__ void __launch_bounds__(kRedThreads, 3) k_update_residual_t(
+    double *xa, double *xb, const int *__restrict__ par_dev, int par_host, const float *__restrict__ e, int n,
+    double h2, float *__restrict__ s32, long long *__restrict__ bint, int *__restrict__ ebt, Reduction red) {
+    pdl_enter();
+    __shared__ double sh[32];
+    const int par = par_dev ? (*par_dev & 1) : (par_host & 1);
+    const double *__restrict__ x = par ? xb : xa;
+    double *__restrict__ xo = par ? xa : xb;
+    const int lg = __ffs(n) - 1;
+    SqSum ss, ee;
+    double ff = 0.0;
+    const int ntask = (n >> 5) * (n / kResRows), wpb = blockDim.x >> 5;
+    for (int t = blockIdx.x * wpb + (int)(threadIdx.x >> 5); t < ntask; t += gridDim.x * wpb)
+        residual_task<false, true>(t, n, lg, nullptr, 0.0, h2, bint, ebt, x, s32, ss, ff, e, xo, &ee);
+    double vals[2];
+    vals[0] = block_sum(ss.value(), sh);
+    vals[1] = block_sum(ee.value(), sh);
     reduce_finish<2>(red, vals, sh);
 }
 
@@ -1701,32 +1761,34 @@ __global__ void k_convert(int dir, size_t count, const void *__restrict__ in, vo
     }
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_project(double *__restrict__ x, size_t N,
-                                                         const double *__restrict__ sum,
-                                                         const int *__restrict__ zero_flag) {
+__global__ void __launch_bounds__(kRedThreads) k_project(double *x, size_t N, const double *__restrict__ sum,
+                                                         const int *__restrict__ zero_flag, const double *alt,
+                                                         const int *par) {
     pdl_enter();
     const bool zero = zero_flag && *zero_flag;
     const double mu = *sum / (double)N;
+    const double *src = pick_src(x, alt, par);
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
-        x[p] = zero ? 0.0 : x[p] - mu;
+        x[p] = zero ? 0.0 : src[p] - mu;
 }
 
 // The same projection on 16-byte-aligned x (N a multiple of 4), two 16-byte
 // words per thread and iteration.
-__global__ void __launch_bounds__(kRedThreads) k_project_v(double *__restrict__ x, size_t N,
-                                                           const double *__restrict__ sum,
-                                                           const int *__restrict__ zero_flag) {
+__global__ void __launch_bounds__(kRedThreads) k_project_v(double *x, size_t N, const double *__restrict__ sum,
+                                                           const int *__restrict__ zero_flag, const double *alt,
+                                                           const int *par) {
     pdl_enter();
     const bool zero = zero_flag && *zero_flag;
     const double mu = *sum / (double)N;
     double2 *x2 = reinterpret_cast<double2 *>(x);
+    const double2 *s2 = reinterpret_cast<const double2 *>(pick_src(x, alt, par));
     const size_t G = N >> 1, stride = (size_t)gridDim.x * blockDim.x;
     for (size_t g0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g0 < G; g0 += 2 * stride) {
         double2 t[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const size_t g = g0 + u * stride;
-            if (g < G) t[u] = x2[g];
+            if (g < G) t[u] = s2[g];
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -2255,19 +2317,21 @@ template cudaError_t launch_bottom<float>(float *, const float *, int, int, int,
 template cudaError_t launch_bottom<double>(double *, const double *, int, int, int, int, bool,
                                            const double *, const FirTaps &, cudaStream_t);
 
-cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s) {
+cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s, const double *alt, const int *par) {
+    if (par && !alt) return cudaErrorInvalidValue;
     {
         const size_t N = (size_t)n * n;
-        const bool vec = (reinterpret_cast<uintptr_t>(f) & 15) == 0 && N % 4 == 0;
-        cudaError_t le_ = vec ? launch_kernel(k_sum_v, kWideBlocks, kRedThreads, 0, s, f, N, red)
-                              : launch_kernel(k_sum, kRedBlocks, kRedThreads, 0, s, f, N, red);
+        const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(alt)) & 15) == 0 && N % 4 == 0;
+        const double *alt_k = alt ? alt : x;
+        cudaError_t le_ = vec ? launch_kernel(k_sum_v, kWideBlocks, kRedThreads, 0, s, x, N, red, alt_k, par)
+                              : launch_kernel(k_sum, kRedBlocks, kRedThreads, 0, s, x, N, red, alt_k, par);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);
     return cudaGetLastError();
 }
-cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s) {
-    return launch_source_sum(x, n, red, s);
+cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s) {
+    return launch_sum(f, n, red, s, nullptr, nullptr);
 }
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum, double *b,
                               cudaStream_t s) {
@@ -2322,6 +2386,16 @@ cudaError_t launch_outer_residual_tasks(const double *f, const double *x, int n,
     count_launches(1);
     return cudaGetLastError();
 }
+cudaError_t launch_update_residual_tasks(double *xa, double *xb, const int *par_dev, int par_host, const float *e,
+                                         int n, double h2, float *s32, long long *bint, int *ebt, Reduction red,
+                                         cudaStream_t s) {
+    if (n < kResMinN || !xa || !xb || xa == xb || !e || !s32 || !bint || !ebt) return cudaErrorInvalidValue;
+    const cudaError_t le = launch_kernel(k_update_residual_t, kResBlocks, kRedThreads, 0, s, xa, xb, par_dev,
+                                         par_host, e, n, h2, s32, bint, ebt, red);
+    if (le != cudaSuccess) return le;
+    count_launches(1);
+    return cudaGetLastError();
+}
 cudaError_t launch_bspline_coef(const float *e, float *c, int nc, int dir, cudaStream_t s) {
     if (nc < 4 || (dir != 0 && dir != 1) || e == c) return cudaErrorInvalidValue;
     BspTaps t;
@@ -2366,12 +2440,17 @@ cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaS
     count_launches(1);
     return cudaGetLastError();
 }
-cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag) {
+cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag,
+                           const double *alt, const int *par) {
+    if (par && !alt) return cudaErrorInvalidValue;
     {
         const size_t N = (size_t)n * n;
-        const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0 && N % 4 == 0;
-        cudaError_t le_ = vec ? launch_kernel(k_project_v, kWideBlocks, kRedThreads, 0, s, x, N, sum, zero_flag)
-                              : launch_kernel(k_project, kRedBlocks, kRedThreads, 0, s, x, N, sum, zero_flag);
+        const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(alt)) & 15) == 0 && N % 4 == 0;
+        const double *alt_k = alt ? alt : x;
+        cudaError_t le_ = vec ? launch_kernel(k_project_v, kWideBlocks, kRedThreads, 0, s, x, N, sum, zero_flag,
+                                              alt_k, par)
+                              : launch_kernel(k_project, kRedBlocks, kRedThreads, 0, s, x, N, sum, zero_flag,
+                                              alt_k, par);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);

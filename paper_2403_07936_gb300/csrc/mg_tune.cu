@@ -113,6 +113,17 @@ void set_coarse_cluster(int on) {
     if (old != (on ? 1 : 0)) g_epoch.fetch_add(1);
 }
 
+namespace {
+std::atomic<int> g_fused_update{1};
+}
+
+int fused_update_mode() { return g_fused_update.load(std::memory_order_relaxed); }
+
+void set_fused_update(int on) {
+    const int old = g_fused_update.exchange(on ? 1 : 0);
+    if (old != (on ? 1 : 0)) g_epoch.fetch_add(1);
+}
+
 void set_tma_tiles(int on) {
     const int old = g_tma_tiles.exchange(on ? 1 : 0);
     if (old != (on ? 1 : 0)) g_epoch.fetch_add(1);

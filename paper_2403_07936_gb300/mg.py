@@ -79,6 +79,8 @@ SIGNATURES = {
     "mg_set_zero_guess": (_I, [_VP, _I]),
     "mg_set_coarse_cluster": (_I, [_I]),
     "mg_get_coarse_cluster": (_I, []),
+    "mg_set_fused_update": (_I, [_I]),
+    "mg_get_fused_update": (_I, []),
     "mg_get_tma_tiles": (_I, []),
     "mg_trainer_get_tensor_cores": (_I, [_VP, C.POINTER(_I)]),
     "mg_trainer_get_weights": (_I, [_VP, _VP, _SZ]),
@@ -268,7 +270,8 @@ class Context:
         return n.value
 
     def probe(self, kind: int, capacity: int = 256):
-        """Time one kernel kind with CUDA events (1 down, 2 up, 3 residual, 4 update)."""
+        """Time one kernel kind with CUDA events (1 down, 2 up, 3 residual, 4 update, 5 coarse span,
+        6 update fused with the next residual)."""
         _check(load().mg_probe_kernel(self._h, kind, capacity))
 
     def probe_read(self):
@@ -351,6 +354,15 @@ def set_coarse_cluster(on: bool):
 
 def get_coarse_cluster() -> bool:
     return bool(load().mg_get_coarse_cluster())
+
+
+def set_fused_update(on: bool):
+    """Fuse each outer step's FP64 update with the next outer residual (True) or launch them apart."""
+    _check(load().mg_set_fused_update(int(bool(on))))
+
+
+def get_fused_update() -> bool:
+    return bool(load().mg_get_fused_update())
 
 
 def set_tma_tiles(on: bool):
