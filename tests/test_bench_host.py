@@ -46,7 +46,7 @@ def test_capture_record_is_ignored_for_another_source(monkeypatch):
 def test_capture_record_matches_the_committed_kernels():
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
         d = json.load(fh)
-    for kind in ("1", "2", "3"):
+    for kind in ("1", "2", "3", "6"):
         assert d[kind]["source_sha1"] == bench.kernel_source_sha(), f"kind {kind}: recapture or refresh"
         assert os.path.exists(os.path.join(ROOT, d[kind]["profile"]))
 
