@@ -133,7 +133,10 @@ mg_status mg_load_prolong_weights(mg_ctx *ctx, const void *blob, size_t bytes);
 /* Cold starts (Algorithm 6 iterates from an initial guess; the configurations
  * here start from p = 0): with on = 1 the context's solves (mg_solve,
  * mg_two_level_solve) start from x = 0 and never read x, so a host x is not
- * copied to the device (the device copy, or a device x, is zeroed there);
+ * copied to the device.  Mixed solves of N >= 32 with the fused outer step
+ * (mg_set_fused_update) take x = 0 in their first residual and first update
+ * without reading or zeroing x; other solves zero the device copy, or a
+ * device x, first.  The result is bit for bit that of a solve from x = 0.
  * on = 0 (the default): x is the initial guess.  MG_ERR_INVALID_ARG for a
  * null context or other values. */
 mg_status mg_set_zero_guess(mg_ctx *ctx, int on);

@@ -122,6 +122,7 @@ struct SolveGraph {
     double *x = nullptr;
     int prolong = -1;
     double tol = 0.0;
+    bool xzero = false;  // recorded for a cold start whose kernels do not read x
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long n_pro = 0, n_body = 0, n_epi = 0;  // kernels per part
@@ -319,11 +320,13 @@ static double *scaled_rhs(mg_ctx *c, bool mixed) { return mixed ? c->bsc64 : c->
 // (first) sums (f - mu)^2 and stores b = h^2 (f - mu); later ones load b.
 // Mixed solves of N >= kResMinN use the task-tiled kernel (b stored aligned).
 static cudaError_t solve_residual(mg_ctx *c, const double *fd, const double *xd, bool mixed, bool first,
-                                  double h2, cudaStream_t s) {
+                                  double h2, cudaStream_t s, bool xzero = false) {
     const int N = c->N;
     if (mixed && N >= kResMinN)
         return launch_outer_residual_tasks(fd, xd, N, h2, c->out(kGrpF), 0.0, c->lv[0].b32, first,
-                                           reinterpret_cast<long long *>(c->bsc64), c->ebt, c->red(kGrpR), s);
+                                           reinterpret_cast<long long *>(c->bsc64), c->ebt, c->red(kGrpR), s,
+                                           xzero);
+    if (xzero) return cudaErrorInvalidValue;
     return launch_outer_residual(fd, xd, N, h2, c->out(kGrpF), 0.0, mixed ? c->lv[0].b32 : nullptr, first,
                                  scaled_rhs(c, mixed), !first, c->red(kGrpR), s);
 }
@@ -331,13 +334,20 @@ static cudaError_t solve_residual(mg_ctx *c, const double *fd, const double *xd,
 // Whether a solve fuses each outer step's update with the next residual.
 static bool fused_update(const mg_ctx *c, bool mixed) { return mixed && c->N >= kResMinN && c->xalt && fused_update_mode(); }
 
+// Whether a solve's kernels take the cold start themselves (mg_set_zero_guess
+// with the fused outer step): the first residual and the first update treat
+// x as zero without reading it, so x is neither zeroed nor copied in.
+static bool kernels_take_zero(const mg_ctx *c, bool mixed) { return c->zero_guess && fused_update(c, mixed); }
+
 // The update of outer step k (from 1) fused with the residual that follows
-// it; par_dev (the graph's device step counter, k - 1 when the kernel runs)
-// or else k - 1 selects which buffer of (xd, xalt) holds the step's x.
-static cudaError_t solve_update_residual(mg_ctx *c, double *xd, const int *par_dev, int par_host, double h2,
-                                         cudaStream_t s) {
-    return launch_update_residual_tasks(xd, c->xalt, par_dev, par_host, c->lv[0].x32, c->N, h2, c->lv[0].b32,
-                                        reinterpret_cast<long long *>(c->bsc64), c->ebt, c->red(kGrpR), s);
+// it; step_dev (the graph's device step counter, k - 1 when the kernel runs)
+// or else step_host = k - 1 selects which buffer of (xd, xalt) holds the
+// step's x; with xzero step 0 starts from x = 0 without reading it.
+static cudaError_t solve_update_residual(mg_ctx *c, double *xd, const int *step_dev, int step_host, bool xzero,
+                                         double h2, cudaStream_t s) {
+    return launch_update_residual_tasks(xd, c->xalt, step_dev, step_host, xzero, c->lv[0].x32, c->N, h2,
+                                        c->lv[0].b32, reinterpret_cast<long long *>(c->bsc64), c->ebt,
+                                        c->red(kGrpR), s);
 }
 
 template <typename T> static T *lvx(mg_ctx *c, int l);
@@ -429,10 +439,13 @@ static mg_status vcycle32_top(mg_ctx *c, bool zero, mg_prolong prolong) {
 // context's device copies.  zero_x: x is output only (a solve from x = 0): a
 // host x is not copied in and the device copy, or a device x, is zeroed.
 static mg_status resolve_io(mg_ctx *c, const double *f, double *x, const double **fd, double **xd,
-                            bool *staged, bool zero_x = false) {
+                            bool *staged, bool zero_x = false, bool kernels_zero = false) {
     const size_t bytes = (size_t)c->N * c->N * sizeof(double);
     const bool fdev = is_device_pointer(f), xdev = is_device_pointer(x);
     *staged = !xdev;
+    // with kernels_zero the solve's kernels take x = 0 without reading x
+    zero_x = zero_x && !kernels_zero;
+    const bool copy_x = !zero_x && !kernels_zero;
     if (fdev && xdev) {
         *fd = f;
         *xd = x;
@@ -452,7 +465,7 @@ static mg_status resolve_io(mg_ctx *c, const double *f, double *x, const double 
         if (zero_x) MG_CUDA(cudaMemsetAsync(x, 0, bytes, c->stream));
     } else {
         if (zero_x) MG_CUDA(cudaMemsetAsync(c->x_stage, 0, bytes, c->stream));
-        else MG_CUDA(cudaMemcpyAsync(c->x_stage, x, bytes, cudaMemcpyHostToDevice, c->stream));
+        else if (copy_x) MG_CUDA(cudaMemcpyAsync(c->x_stage, x, bytes, cudaMemcpyHostToDevice, c->stream));
         *xd = c->x_stage;
     }
     return MG_OK;
@@ -552,6 +565,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
     long long n_pro = 0, n_body = 0, n_epi = 0, n_sr = 0;
     const bool use_policy = mixed && prolong == MG_PROLONG_SR && c->levels > 1 && c->lv[0].n > kBottomMax;
     const bool fuse = fused_update(c, mixed);
+    const bool xz = kernels_take_zero(c, mixed);  // cold start: x is not read
     auto fail = [&](cudaError_t e, const char *what) {
         set_err("graph recording (%s) failed: %s", what, cudaGetErrorString(e));
         st = MG_ERR_CUDA;
@@ -572,7 +586,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
         capturing = true;
         e = launch_source_sum(fd, N, c->red(kGrpF), s);
         // the first residual also stores the scaled right-hand side b = h^2 (f - mu)
-        if (e == cudaSuccess) e = solve_residual(c, fd, xd, mixed, true, h2, s);
+        if (e == cudaSuccess) e = solve_residual(c, fd, xd, mixed, true, h2, s, xz);
         if (e == cudaSuccess)
             e = launch_check(c->dstate, c->out(kGrpR), nullptr, c->out(kGrpF), N2, h2, tol, step,
                              c->max_cycles, true, handle, s, rho, ifh);
@@ -657,7 +671,7 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
         }
         // the fused form reads the step counter before k_check advances it
         if (e == cudaSuccess)
-            e = fuse ? solve_update_residual(c, xd, &c->dstate->outer, 0, h2, s)
+            e = fuse ? solve_update_residual(c, xd, &c->dstate->outer, 0, xz, h2, s)
                      : solve_residual(c, fd, xd, mixed, false, h2, s);
         if (e == cudaSuccess)
             e = launch_check(c->dstate, c->out(kGrpR),
@@ -674,10 +688,11 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
         if (e != cudaSuccess) { fail(e, "begin epilogue"); break; }
         capturing = true;
         // after k outer steps of the fused form, x is in xalt when k is odd
-        e = launch_sum(xd, N, c->red(kGrpX), s, fuse ? c->xalt : nullptr, fuse ? &c->dstate->outer : nullptr);
+        // (on a cold start with no outer step run, x is zero and not read)
+        e = launch_sum(xd, N, c->red(kGrpX), s, fuse ? c->xalt : nullptr, fuse ? &c->dstate->outer : nullptr, xz);
         if (e == cudaSuccess)
             e = launch_project(xd, N, c->out(kGrpX), s, &c->dstate->zero_source, fuse ? c->xalt : nullptr,
-                               fuse ? &c->dstate->outer : nullptr);
+                               fuse ? &c->dstate->outer : nullptr, xz);
         if (e != cudaSuccess) { fail(e, "epilogue"); break; }
         e = cudaStreamEndCapture(s, &g);
         capturing = false;
@@ -716,8 +731,9 @@ static mg_status record_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_
 static mg_status get_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_prolong prolong, double tol,
                                  SolveGraph **out) {
     SolveGraph *lru = &c->graphs[0];
+    const bool xz = kernels_take_zero(c, c->prec == MG_PREC_MIXED);
     for (SolveGraph &g : c->graphs) {
-        if (g.exec && g.f == fd && g.x == xd && g.prolong == (int)prolong && g.tol == tol &&
+        if (g.exec && g.f == fd && g.x == xd && g.prolong == (int)prolong && g.tol == tol && g.xzero == xz &&
             g.epoch == tune_epoch()) {
             g.stamp = ++c->graph_clock;
             *out = &g;
@@ -731,6 +747,7 @@ static mg_status get_solve_graph(mg_ctx *c, const double *fd, double *xd, mg_pro
     const unsigned epoch = tune_epoch();
     MG_TRY(record_solve_graph(c, fd, xd, prolong, tol, lru));
     lru->epoch = epoch;
+    lru->xzero = xz;
     lru->stamp = ++c->graph_clock;
     *out = lru;
     return MG_OK;
@@ -1825,7 +1842,8 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
     const double *fd;
     double *xd;
     bool staged;
-    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged, c->zero_guess));
+    const bool xz = kernels_take_zero(c, mixed);
+    MG_TRY(resolve_io(c, f, x, &fd, &xd, &staged, c->zero_guess, xz));
     const int N = c->N;
     const double N2 = (double)N * N;
     const double h = 2.0 * 3.14159265358979323846 / N, h2 = h * h;
@@ -1889,14 +1907,16 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         if (first || !fuse) {
             probe_begin(c, kProbeResidual);
             // the first residual computes and stores b = h^2 (f - mu), later ones load it
-            MG_CUDA(solve_residual(c, fd, xd, mixed, first, h2, s));
-            probe_end(c, kProbeResidual, N2 * ((first ? 24.0 : 16.0) + (mixed ? 4.0 : 0.0)));
+            MG_CUDA(solve_residual(c, fd, xd, mixed, first, h2, s, first && xz));
+            // read f 8 (b 8 later), x 8 unless a cold start's kernels skip it; write b 8 (first), s 4
+            probe_end(c, kProbeResidual, N2 * ((first ? 24.0 : 16.0) - (first && xz ? 8.0 : 0.0) + (mixed ? 4.0 : 0.0)));
         } else {
             // the update of the outer step just run, fused with this residual:
-            // x + e (12 bytes a point in, 8 out), b (8 in), the float residual (4 out)
+            // x + e (12 bytes a point in, 8 out; a cold start's first step
+            // does not read x), b (8 in), the float residual (4 out)
             probe_begin(c, kProbeUpdateResidual);
-            MG_CUDA(solve_update_residual(c, xd, nullptr, (outer - 1) & 1, h2, s));
-            probe_end(c, kProbeUpdateResidual, N2 * 32.0);
+            MG_CUDA(solve_update_residual(c, xd, nullptr, outer - 1, xz, h2, s));
+            probe_end(c, kProbeUpdateResidual, N2 * (xz && outer == 1 ? 24.0 : 32.0));
         }
         MG_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * 2 * kMaxSlots,
                                 cudaMemcpyDeviceToHost, s));
@@ -1960,8 +1980,10 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *x, double tol, mg_prolong
         }
         ++outer;
     }
-    // the fused form leaves x in xalt after an odd number of outer steps
+    // the fused form leaves x in xalt after an odd number of outer steps; a
+    // cold start that ran none has not written x
     const double *x_last = (fuse && (outer & 1)) ? c->xalt : nullptr;
+    if (xz && outer == 0) MG_CUDA(cudaMemsetAsync(xd, 0, sizeof(double) * N * N, s));
     if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
         MG_CUDA(launch_sum(xd, N, c->red(kGrpX), s, x_last));
         MG_CUDA(launch_project(xd, N, c->out(kGrpX), s, nullptr, x_last));

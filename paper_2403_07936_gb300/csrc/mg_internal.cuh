@@ -552,9 +552,10 @@ cudaError_t launch_prolong_factor(float *ef, const float *c, int n, int lgf, cud
 constexpr int kResRows = 8;
 constexpr int kResMinN = 32;
 inline size_t res_tasks(int n) { return (size_t)(n / 32) * (size_t)(n / kResRows); }
+// xzero (first only): x is zero (a cold start) and is not read.
 cudaError_t launch_outer_residual_tasks(const double *f, const double *x, int n, double h2, const double *mu_sum,
                                         double mu_host, float *s32, bool first, long long *bint, int *ebt,
-                                        Reduction red, cudaStream_t s);
+                                        Reduction red, cudaStream_t s, bool xzero = false);
 
 // Scaled outer residual.  b = h^2 (f - mu) is computed from f in FP64 (and
 // stored to bsc when bsc is given), or with load_b taken from bsc as an
@@ -566,20 +567,23 @@ cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaS
 // An outer step's update fused with the next (steady) task-tiled residual:
 // x_new = x_old + e into the other buffer of the pair (xa, xb), the residual
 // of x_new into s32, out[0] = sum of its squares, out[1] = sum of e^2.  The
-// source is xb when the parity (*par_dev if non-null, else par_host) is odd.
-// x_new and the residual are bit for bit those of launch_update followed by
-// launch_outer_residual_tasks(first = false).
-cudaError_t launch_update_residual_tasks(double *xa, double *xb, const int *par_dev, int par_host, const float *e,
-                                         int n, double h2, float *s32, long long *bint, int *ebt, Reduction red,
-                                         cudaStream_t s);
+// outer step index k from 0 (*step_dev if non-null, else step_host) selects
+// the source: xb when k is odd, else xa; with zero_first, step 0's source is
+// zero and is not read.  x_new and the residual are bit for bit those of
+// launch_update followed by launch_outer_residual_tasks(first = false).
+cudaError_t launch_update_residual_tasks(double *xa, double *xb, const int *step_dev, int step_host, bool zero_first,
+                                         const float *e, int n, double h2, float *s32, long long *bint, int *ebt,
+                                         Reduction red, cudaStream_t s);
 // x -= sum / n^2, or x = 0 where *zero_flag is set (zero_flag may be null);
 // with alt given the values are read from alt (when par is null or *par is
-// odd; par is a device pointer, read when the kernel runs).
+// odd; par is a device pointer, read when the kernel runs); with zero_first
+// (par required) the values are zero when *par == 0 and nothing is read.
 cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag = nullptr,
-                           const double *alt = nullptr, const int *par = nullptr);
-// the sum of x (of alt when alt is given and par is null or *par is odd)
+                           const double *alt = nullptr, const int *par = nullptr, bool zero_first = false);
+// the sum of x (of alt when alt is given and par is null or *par is odd; 0
+// with zero_first when *par == 0)
 cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s, const double *alt = nullptr,
-                       const int *par = nullptr);
+                       const int *par = nullptr, bool zero_first = false);
 // out[i] = the integer-pipe conversion of in[i] (dir 0: double -> float, 1: float -> double)
 cudaError_t launch_convert(int dir, size_t count, const void *in, void *out, cudaStream_t s);
 

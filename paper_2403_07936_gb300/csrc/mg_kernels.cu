@@ -1322,15 +1322,20 @@ constexpr int kUnroll = 4;
 // The sums and the projection below read `alt` instead of their own array
 // when par is null or *par is odd (the launchers pass alt = a when there is no
 // alternative): a mixed solve whose fused update alternates a pair of FP64
-// iterates sums and projects whichever holds the last one.
-__device__ __forceinline__ const double *pick_src(const double *a, const double *alt, const int *par) {
+// iterates sums and projects whichever holds the last one.  With zero_first
+// and *par == 0 (no outer step ran on a cold start) the values are zero:
+// pick_src returns null and nothing is read.
+__device__ __forceinline__ const double *pick_src(const double *a, const double *alt, const int *par,
+                                                  int zero_first) {
+    if (par && zero_first && *par == 0) return nullptr;
     return (par ? (*par & 1) : 1) ? alt : a;
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_sum(const double *a0, size_t N, Reduction red,
-                                                     const double *alt, const int *par) {
+                                                     const double *alt, const int *par, int zero_first) {
     pdl_enter();
-    const double *__restrict__ a = pick_src(a0, alt, par);
+    const double *__restrict__ a = pick_src(a0, alt, par, zero_first);
+    if (!a) N = 0;
     __shared__ double sh[32];
     double v = 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -1352,9 +1357,10 @@ __global__ void __launch_bounds__(kRedThreads) k_sum(const double *a0, size_t N,
 // per thread and iteration, four groups in flight, so that enough loads are
 // outstanding to cover the memory latency (the scalar form is latency-bound).
 __global__ void __launch_bounds__(kRedThreads) k_sum_v(const double *a0, size_t N, Reduction red,
-                                                       const double *alt, const int *par) {
+                                                       const double *alt, const int *par, int zero_first) {
     pdl_enter();
-    const double *__restrict__ a = pick_src(a0, alt, par);
+    const double *__restrict__ a = pick_src(a0, alt, par, zero_first);
+    if (!a) N = 0;
     __shared__ double sh[32];
     double v = 0.0;
     const size_t G = N >> 1, stride = (size_t)gridDim.x * blockDim.x;
@@ -1492,7 +1498,8 @@ __device__ __forceinline__ float aligned_to_f32(long long acc, int E) {
 // update x + e to every value it loads (its own rows, the neighbour rows and
 // the halo columns, by the addition the update kernel makes), stores its own
 // rows to xo and sums their e^2 into ee; the residual is then that of x + e.
-template <bool FIRST, bool UPD = false>
+// XZERO: x is zero (a solve's cold start) and is not read.
+template <bool FIRST, bool UPD = false, bool XZERO = false>
 __device__ __forceinline__ void residual_task(int task, int n, int lg, const double *__restrict__ f, double mu,
                                               double h2, long long *__restrict__ bint, int *__restrict__ ebt,
                                               const double *__restrict__ x, float *__restrict__ s32, SqSum &ss,
@@ -1507,11 +1514,11 @@ __device__ __forceinline__ void residual_task(int task, int n, int lg, const dou
     const int c = c0 + lane;
     double xv[R + 2];  // rows r0 - 1 .. r0 + R of column c
 #pragma unroll
-    for (int k = 0; k < R + 2; ++k) xv[k] = x[((size_t)((r0 - 1 + k) & (n - 1)) << lg) + c];
+    for (int k = 0; k < R + 2; ++k) xv[k] = XZERO ? 0.0 : x[((size_t)((r0 - 1 + k) & (n - 1)) << lg) + c];
     // halo columns: lane k < R holds x[r0 + k][c0 - 1], lane 16 + k holds x[r0 + k][c0 + 32]
     const int hk = lane & 15;
     double hv = 0.0;
-    if (hk < R) hv = x[((size_t)(r0 + hk) << lg) + ((lane < 16 ? c0 - 1 : c0 + 32) & (n - 1))];
+    if (!XZERO && hk < R) hv = x[((size_t)(r0 + hk) << lg) + ((lane < 16 ? c0 - 1 : c0 + 32) & (n - 1))];
     if (UPD) {
         float ev[R + 2];
 #pragma unroll
@@ -1576,10 +1583,12 @@ __device__ __forceinline__ void residual_task(int task, int n, int lg, const dou
     }
 }
 
+// xzero (first residuals only): x is zero and is not read.
 template <bool FIRST>
 __global__ void __launch_bounds__(kRedThreads, FIRST ? 2 : 3) k_outer_residual_t(
     const double *__restrict__ f, const double *__restrict__ x, int n, double h2, const double *__restrict__ fsum,
-    double mu_host, float *__restrict__ s32, long long *__restrict__ bint, int *__restrict__ ebt, Reduction red) {
+    double mu_host, float *__restrict__ s32, long long *__restrict__ bint, int *__restrict__ ebt, Reduction red,
+    int xzero) {
     pdl_enter();
     __shared__ double sh[32];
     const int lg = __ffs(n) - 1;
@@ -1587,8 +1596,13 @@ __global__ void __launch_bounds__(kRedThreads, FIRST ? 2 : 3) k_outer_residual_t
     SqSum ss;  // squares of the float residual (see residual_norm_note)
     double ff = 0.0;
     const int ntask = (n >> 5) * (n / kResRows), wpb = blockDim.x >> 5;
-    for (int t = blockIdx.x * wpb + (int)(threadIdx.x >> 5); t < ntask; t += gridDim.x * wpb)
-        residual_task<FIRST>(t, n, lg, f, mu, h2, bint, ebt, x, s32, ss, ff);
+    const int t0 = blockIdx.x * wpb + (int)(threadIdx.x >> 5), ts = gridDim.x * wpb;
+    if (FIRST && xzero) {
+        for (int t = t0; t < ntask; t += ts)
+            residual_task<FIRST, false, FIRST>(t, n, lg, f, mu, h2, bint, ebt, x, s32, ss, ff);
+    } else {
+        for (int t = t0; t < ntask; t += ts) residual_task<FIRST>(t, n, lg, f, mu, h2, bint, ebt, x, s32, ss, ff);
+    }
     double vals[2];
     vals[0] = block_sum(ss.value(), sh);
     vals[1] = FIRST ? block_sum(ff, sh) : 0.0;
@@ -1601,22 +1615,31 @@ __global__ void __launch_bounds__(kRedThreads, FIRST ? 2 : 3) k_outer_residual_t
 // with out[0] = sum of the float residual's squares and out[1] = sum of e^2.
 // Every task reads x_old and writes x_new in different buffers, so no task
 // reads what another writes; each stored x_new and each residual is bit for
-// bit that of k_update_v followed by k_outer_residual_t<false>.  The source
-// buffer is xb when the parity (*par_dev, else par_host) is odd, else xa.
+// bit that of k_update_v followed by k_outer_residual_t<false>.  The outer
+// step index k (*step_dev, else step_host; from 0) selects the buffers: the
+// source is xb when k is odd, else xa; with zero_first the source of step 0
+// is zero (a solve's cold start) and is not read.
 __global__ void __launch_bounds__(kRedThreads, 3) k_update_residual_t(
-    double *xa, double *xb, const int *__restrict__ par_dev, int par_host, const float *__restrict__ e, int n,
-    double h2, float *__restrict__ s32, long long *__restrict__ bint, int *__restrict__ ebt, Reduction red) {
+    double *xa, double *xb, const int *__restrict__ step_dev, int step_host, int zero_first,
+    const float *__restrict__ e, int n, double h2, float *__restrict__ s32, long long *__restrict__ bint,
+    int *__restrict__ ebt, Reduction red) {
     pdl_enter();
     __shared__ double sh[32];
-    const int par = par_dev ? (*par_dev & 1) : (par_host & 1);
-    const double *__restrict__ x = par ? xb : xa;
-    double *__restrict__ xo = par ? xa : xb;
+    const int step = step_dev ? *step_dev : step_host;
+    const double *__restrict__ x = (step & 1) ? xb : xa;
+    double *__restrict__ xo = (step & 1) ? xa : xb;
     const int lg = __ffs(n) - 1;
     SqSum ss, ee;
     double ff = 0.0;
     const int ntask = (n >> 5) * (n / kResRows), wpb = blockDim.x >> 5;
-    for (int t = blockIdx.x * wpb + (int)(threadIdx.x >> 5); t < ntask; t += gridDim.x * wpb)
-        residual_task<false, true>(t, n, lg, nullptr, 0.0, h2, bint, ebt, x, s32, ss, ff, e, xo, &ee);
+    const int t0 = blockIdx.x * wpb + (int)(threadIdx.x >> 5), ts = gridDim.x * wpb;
+    if (zero_first && step == 0) {
+        for (int t = t0; t < ntask; t += ts)
+            residual_task<false, true, true>(t, n, lg, nullptr, 0.0, h2, bint, ebt, x, s32, ss, ff, e, xo, &ee);
+    } else {
+        for (int t = t0; t < ntask; t += ts)
+            residual_task<false, true>(t, n, lg, nullptr, 0.0, h2, bint, ebt, x, s32, ss, ff, e, xo, &ee);
+    }
     double vals[2];
     vals[0] = block_sum(ss.value(), sh);
     vals[1] = block_sum(ee.value(), sh);
@@ -1763,32 +1786,32 @@ __global__ void k_convert(int dir, size_t count, const void *__restrict__ in, vo
 
 __global__ void __launch_bounds__(kRedThreads) k_project(double *x, size_t N, const double *__restrict__ sum,
                                                          const int *__restrict__ zero_flag, const double *alt,
-                                                         const int *par) {
+                                                         const int *par, int zero_first) {
     pdl_enter();
     const bool zero = zero_flag && *zero_flag;
     const double mu = *sum / (double)N;
-    const double *src = pick_src(x, alt, par);
+    const double *src = pick_src(x, alt, par, zero_first);
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
-        x[p] = zero ? 0.0 : src[p] - mu;
+        x[p] = zero ? 0.0 : (src ? src[p] : 0.0) - mu;
 }
 
 // The same projection on 16-byte-aligned x (N a multiple of 4), two 16-byte
 // words per thread and iteration.
 __global__ void __launch_bounds__(kRedThreads) k_project_v(double *x, size_t N, const double *__restrict__ sum,
                                                            const int *__restrict__ zero_flag, const double *alt,
-                                                           const int *par) {
+                                                           const int *par, int zero_first) {
     pdl_enter();
     const bool zero = zero_flag && *zero_flag;
     const double mu = *sum / (double)N;
     double2 *x2 = reinterpret_cast<double2 *>(x);
-    const double2 *s2 = reinterpret_cast<const double2 *>(pick_src(x, alt, par));
+    const double2 *s2 = reinterpret_cast<const double2 *>(pick_src(x, alt, par, zero_first));
     const size_t G = N >> 1, stride = (size_t)gridDim.x * blockDim.x;
     for (size_t g0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g0 < G; g0 += 2 * stride) {
         double2 t[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const size_t g = g0 + u * stride;
-            if (g < G) t[u] = s2[g];
+            if (g < G) t[u] = s2 ? s2[g] : make_double2(0.0, 0.0);
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -2317,21 +2340,23 @@ template cudaError_t launch_bottom<float>(float *, const float *, int, int, int,
 template cudaError_t launch_bottom<double>(double *, const double *, int, int, int, int, bool,
                                            const double *, const FirTaps &, cudaStream_t);
 
-cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s, const double *alt, const int *par) {
-    if (par && !alt) return cudaErrorInvalidValue;
+cudaError_t launch_sum(const double *x, int n, Reduction red, cudaStream_t s, const double *alt, const int *par,
+                       bool zero_first) {
+    if ((par && !alt) || (zero_first && !par)) return cudaErrorInvalidValue;
     {
         const size_t N = (size_t)n * n;
         const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(alt)) & 15) == 0 && N % 4 == 0;
         const double *alt_k = alt ? alt : x;
-        cudaError_t le_ = vec ? launch_kernel(k_sum_v, kWideBlocks, kRedThreads, 0, s, x, N, red, alt_k, par)
-                              : launch_kernel(k_sum, kRedBlocks, kRedThreads, 0, s, x, N, red, alt_k, par);
+        const int zf = zero_first ? 1 : 0;
+        cudaError_t le_ = vec ? launch_kernel(k_sum_v, kWideBlocks, kRedThreads, 0, s, x, N, red, alt_k, par, zf)
+                              : launch_kernel(k_sum, kRedBlocks, kRedThreads, 0, s, x, N, red, alt_k, par, zf);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t launch_source_sum(const double *f, int n, Reduction red, cudaStream_t s) {
-    return launch_sum(f, n, red, s, nullptr, nullptr);
+    return launch_sum(f, n, red, s, nullptr, nullptr, false);
 }
 cudaError_t launch_scaled_rhs(const double *f, int n, double h2, const double *f_sum, double *b,
                               cudaStream_t s) {
@@ -2375,23 +2400,24 @@ cudaError_t launch_outer_residual(const double *f, const double *x, int n, doubl
 }
 cudaError_t launch_outer_residual_tasks(const double *f, const double *x, int n, double h2, const double *mu_sum,
                                         double mu_host, float *s32, bool first, long long *bint, int *ebt,
-                                        Reduction red, cudaStream_t s) {
-    if (n < kResMinN || !s32 || !bint || !ebt) return cudaErrorInvalidValue;
+                                        Reduction red, cudaStream_t s, bool xzero) {
+    if (n < kResMinN || !s32 || !bint || !ebt || (xzero && !first)) return cudaErrorInvalidValue;
     const cudaError_t e =
         first ? launch_kernel(k_outer_residual_t<true>, kRedBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
-                              s32, bint, ebt, red)
+                              s32, bint, ebt, red, xzero ? 1 : 0)
               : launch_kernel(k_outer_residual_t<false>, kResBlocks, kRedThreads, 0, s, f, x, n, h2, mu_sum, mu_host,
-                              s32, bint, ebt, red);
+                              s32, bint, ebt, red, 0);
     if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }
-cudaError_t launch_update_residual_tasks(double *xa, double *xb, const int *par_dev, int par_host, const float *e,
-                                         int n, double h2, float *s32, long long *bint, int *ebt, Reduction red,
-                                         cudaStream_t s) {
-    if (n < kResMinN || !xa || !xb || xa == xb || !e || !s32 || !bint || !ebt) return cudaErrorInvalidValue;
-    const cudaError_t le = launch_kernel(k_update_residual_t, kResBlocks, kRedThreads, 0, s, xa, xb, par_dev,
-                                         par_host, e, n, h2, s32, bint, ebt, red);
+cudaError_t launch_update_residual_tasks(double *xa, double *xb, const int *step_dev, int step_host, bool zero_first,
+                                         const float *e, int n, double h2, float *s32, long long *bint, int *ebt,
+                                         Reduction red, cudaStream_t s) {
+    if (n < kResMinN || !xa || !xb || xa == xb || !e || !s32 || !bint || !ebt || step_host < 0)
+        return cudaErrorInvalidValue;
+    const cudaError_t le = launch_kernel(k_update_residual_t, kResBlocks, kRedThreads, 0, s, xa, xb, step_dev,
+                                         step_host, zero_first ? 1 : 0, e, n, h2, s32, bint, ebt, red);
     if (le != cudaSuccess) return le;
     count_launches(1);
     return cudaGetLastError();
@@ -2441,16 +2467,17 @@ cudaError_t launch_update(double *x, const float *e, int n, Reduction red, cudaS
     return cudaGetLastError();
 }
 cudaError_t launch_project(double *x, int n, const double *sum, cudaStream_t s, const int *zero_flag,
-                           const double *alt, const int *par) {
-    if (par && !alt) return cudaErrorInvalidValue;
+                           const double *alt, const int *par, bool zero_first) {
+    if ((par && !alt) || (zero_first && !par)) return cudaErrorInvalidValue;
     {
         const size_t N = (size_t)n * n;
         const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(alt)) & 15) == 0 && N % 4 == 0;
         const double *alt_k = alt ? alt : x;
+        const int zf = zero_first ? 1 : 0;
         cudaError_t le_ = vec ? launch_kernel(k_project_v, kWideBlocks, kRedThreads, 0, s, x, N, sum, zero_flag,
-                                              alt_k, par)
+                                              alt_k, par, zf)
                               : launch_kernel(k_project, kRedBlocks, kRedThreads, 0, s, x, N, sum, zero_flag,
-                                              alt_k, par);
+                                              alt_k, par, zf);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);

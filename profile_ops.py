@@ -20,7 +20,8 @@ ops:
          error: s = max|e|, conv 1->64, the tensor-core layers, conv 64->1
   solve  a whole solve of a seeded turbulent source (host-loop execution, so
          every kernel is a separate launch), mixed or FP64 (--precision);
-         time per solve
+         time per solve; --cold-start declares x = 0 to the library
+         (mg_set_zero_guess), as the bench does
   train  one Adam step of the SR generator trainer on a batch of 4 periodic
          crops of 128^2 coarse pixels (the training configuration; the
          tensor-core GEMMs, or the FP32 CUDA-core GEMMs with --fp32-gemm); time
@@ -51,6 +52,7 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32", help="down / up: element type")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed", help="solve: precision")
     ap.add_argument("--fp32-gemm", action="store_true", help="train: FP32 CUDA-core GEMMs instead of tensor cores")
+    ap.add_argument("--cold-start", action="store_true", help="solve: declare x = 0 (mg_set_zero_guess)")
     args = ap.parse_args()
 
     import torch
@@ -91,6 +93,8 @@ def main():
         from synthetic.sources import default_kmax, turbulent_source
         ctx = mg.Context(int(math.log2(n // 8)) + 1, n, precision=args.precision)
         ctx.set_graph_execution(False)
+        if args.cold_start:
+            ctx.set_zero_guess(True)
         f = torch.tensor(turbulent_source(n, default_kmax(n), 1), device=dev)
         x = torch.zeros_like(f)
 

@@ -155,3 +155,41 @@ def test_fused_update_switch(mg):
         assert mg.get_fused_update()
     finally:
         mg.set_fused_update(mode)
+
+
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "hostloop"])
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "separate"])
+@pytest.mark.parametrize("host", [False, True], ids=["device", "host"])
+def test_cold_start_never_reads_x(mg, graphs, fused, host):
+    """mg_set_zero_guess: with the fused outer step the first residual and the
+    first update take x = 0 without reading x (x holds NaN here, which any read
+    would carry into the result); the bits are those of a solve from zeros."""
+    n = 256
+    f = turbulent_source(n, default_kmax(n), config_seed(2, 95))
+    ctx = mg.Context(_levels(n), n)
+    ctx.set_graph_execution(graphs)
+    ft = torch.tensor(f, device=DEV)
+    x0 = torch.zeros_like(ft)
+    ref = ctx.solve(ft, x0, tol=1e-10)
+    torch.cuda.synchronize()
+    mode = mg.get_fused_update()
+    try:
+        mg.set_fused_update(fused)
+        ctx.set_zero_guess(True)
+        for tol, expect in ((1e-10, None), (2.0, "zeros")):  # tol >= 1: no outer step runs
+            xg = torch.full((n, n), float("nan"), dtype=torch.float64)
+            if host:
+                fi, xg = torch.tensor(f).pin_memory(), xg.pin_memory()
+            else:
+                fi, xg = ft, xg.to(DEV)
+            info = ctx.solve(fi, xg, tol=tol)
+            torch.cuda.synchronize()
+            got = xg.cpu().numpy()
+            if expect == "zeros":
+                assert info["outer_iters"] == 0 and np.array_equal(got, np.zeros((n, n)))
+            else:
+                assert info["vcycles"] == ref["vcycles"] and info["rel_residual"] == ref["rel_residual"]
+                assert np.array_equal(got, x0.cpu().numpy())
+    finally:
+        ctx.set_zero_guess(False)
+        mg.set_fused_update(mode)
