@@ -465,11 +465,13 @@ mg_status mg_op_vcycle(int dtype, int n, int coarsest, void *x, const void *b, i
  * one static device array of 256*256 doubles (512 KiB) that every GPU loading
  * the library keeps until exit, so coarsest must be 4, 8 or 16 and n <= 64;
  * larger sizes return MG_ERR_INVALID_ARG.  No cudaMalloc/cudaFree or other
- * allocating call is made.  The first call on a device looks up the array's
- * address there (cudaGetSymbolAddress) - make that first call before any
- * stream capture - and keeps it for the process, so the entry point must not
- * be used across a cudaDeviceReset.  All calls share the array and rewrite
- * it, so calls that overlap on the GPU (unordered streams) race.
+ * allocating call is made.  Every call made outside stream capture looks up
+ * the array's address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing) - make one such call before any stream capture - and a
+ * call on a capturing stream uses the address the last uncaptured call found
+ * (so a capture that spans a cudaDeviceReset needs an uncaptured call after
+ * the reset first).  All calls share the array and rewrite it, so calls that
+ * overlap on the GPU (unordered streams) race.
  * Asynchronous on `stream`. */
 mg_status mg_op_vcycle_static(int dtype, int n, int coarsest, void *x, const void *b, int nu1,
                               int nu2, int zero_init, void *stream);

@@ -69,8 +69,11 @@ __global__ void k_build_pinv(T *__restrict__ out, int m) {
     out[e] = (T)(acc / Nc);
 }
 
-// Look up the array's device address once per device (the current device).
-mg_status static_scratch(void **addr, char *err, size_t errlen) {
+// The array's device address on the current device.  It is looked up again
+// on every call made outside stream capture (the lookup allocates nothing, and
+// a context reset reloads the module at another address); a call on a
+// capturing stream takes the address cached by the last uncaptured call.
+mg_status static_scratch(void **addr, cudaStream_t s, char *err, size_t errlen) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -78,8 +81,13 @@ mg_status static_scratch(void **addr, char *err, size_t errlen) {
                  cudaGetErrorString(e));
         return MG_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // unknown: keep the cached address
+    }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_pinv_addr[dev]) {
+    if (!g_pinv_addr[dev] || cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_pinv);
         if (e != cudaSuccess || !p) {
@@ -129,10 +137,10 @@ extern "C" mg_status mg_op_vcycle_static(int dtype, int n, int coarsest, void *x
                  kStaticMax, mg::kStaticCoarsestMax, mg::kStaticPinvEntries, n, coarsest);
         return fail(MG_ERR_INVALID_ARG);
     }
-    void *pinv = nullptr;
-    mg_status st = mg::static_scratch(&pinv, err, sizeof err);
-    if (st != MG_OK) return fail(st);
     cudaStream_t s = (cudaStream_t)stream;
+    void *pinv = nullptr;
+    mg_status st = mg::static_scratch(&pinv, s, err, sizeof err);
+    if (st != MG_OK) return fail(st);
     cudaError_t e = dtype == 0
         ? mg::run<double>((double *)x, (const double *)b, n, coarsest, nu1, nu2, zero_init != 0,
                           (double *)pinv, s)

@@ -91,3 +91,27 @@ def test_static_vcycle_neither_waits_nor_holds_memory(lib):
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
 
+
+
+def test_static_vcycle_records_into_a_cuda_graph(lib):
+    """The call can be captured into a CUDA graph (global capture mode, in
+    which an allocation or a device-wide synchronisation inside the call would
+    make the capture fail); each replay gives the bits of an uncaptured call."""
+    x0, b = _case(64, torch.float64, 11)
+    side = torch.cuda.Stream()
+    x_ref = x0.clone()
+    st = lib.mg_op_vcycle_static(0, 64, 8, C.c_void_p(x_ref.data_ptr()), C.c_void_p(b.data_ptr()), 2, 2, 0,
+                                 C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.mg_last_error()
+    torch.cuda.synchronize()
+    x = x0.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        st = lib.mg_op_vcycle_static(0, 64, 8, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()), 2, 2, 0,
+                                     C.c_void_p(side.cuda_stream))
+    assert st == 0, lib.mg_last_error()
+    for _ in range(2):
+        x.copy_(x0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(x, x_ref)
