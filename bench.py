@@ -990,9 +990,15 @@ def main():
                       "accuracy_check": "by the oracle in the CPU-baseline leg (null when that leg is skipped)"},
             "fp64_vcycle": {"value": value64, "unit": "solves/s", "steps": k64,
                             "ms_per_step": sum(t64) / k64 * 1e3,
-                            "roofline": {"bound": "fp64 pipe", "kernel": "k_up<double> (73 % of an FP64 solve)",
-                                         "fp64_pipe_active_pct": 80.6, "dram_throughput_pct": 1.0,
-                                         "source": "ncu capture, profiles/k_up_k_down_fp64_2048.md",
+                            "roofline": {"bound": "fp64 pipe",
+                                         "kernel": "k_up<double> (53 % of an FP64 solve) after k_refine_rows "
+                                                   "(10 %), the prolongation's pass along x once per level",
+                                         "fp64_pipe_active_pct": {"k_up<double>": 66.5, "k_refine_rows": 83.3},
+                                         "dram_throughput_pct": {"k_up<double>": 2.1, "k_refine_rows": 0.9},
+                                         "source": "ncu captures of the 2048^2 launches, "
+                                                   "profiles/k_up_k_down_fp64_2048.md (k_up<double> taken at one "
+                                                   "block per SM, before its tile dropped the unused coarse-tile "
+                                                   "space for two)",
                                          "note": "the FP64 V-cycle's stencils are bound by the FP64 pipe (1/64 of "
                                                  "the FP32 rate on GB300), not by HBM"},
                             "vcycles": info64[-1]["vcycles"], "err_inf_vs_exact_fft": err64},

@@ -337,6 +337,18 @@ int mg_get_coarse_cluster(void);
 mg_status mg_set_fused_update(int on);
 int mg_get_fused_update(void);
 
+/* Where the FP64 V-cycle's cubic prolongation (Sec. 2.2, Algorithm 6's
+ * prolongate step) runs its pass along x.  on = 1 (the default): once per
+ * level, over the whole coarse error, into a context buffer of (N/2) x N
+ * doubles, before the up pass loads the refined rows; on = 0: inside every
+ * tile of the up pass, which also refines the 2L - 1 coarse halo rows its
+ * pass along y reads (the FP64 filter has L = 28 taps per side).  Results are
+ * identical bit for bit; graphs recorded before a change are re-recorded.
+ * FP32 V-cycles always refine per tile.  MG_ERR_INVALID_ARG for other
+ * values. */
+mg_status mg_set_fp64_separate_x_pass(int on);
+int mg_get_fp64_separate_x_pass(void);
+
 /* Read or set one table entry (n a power of two >= 128, nu 0..4). */
 mg_status mg_get_tile_variant(int kind, int n, int nu, int *variant);
 mg_status mg_set_tile_variant(int kind, int n, int nu, int variant);

@@ -154,6 +154,9 @@ struct mg_ctx {
     // update with the next residual (N >= kResMinN): the steps alternate
     // between the solve's x and this buffer
     double *xalt = nullptr;
+    // FP64 hierarchies: the coarse error of the level being prolonged, refined
+    // along x once ((N/2) x N doubles; launch_refine_rows)
+    double *xr64 = nullptr;
     float *ainv32 = nullptr;
     double *ainv64 = nullptr;
     FirTaps taps;
@@ -255,6 +258,9 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
     if (tasks) total += align_up(res_tasks(c->N) * sizeof(int));
     const size_t xalt_off = total;
     if (tasks) total += align_up((size_t)c->N * c->N * sizeof(double));
+    const size_t xr_off = total;
+    const bool xr = fp64 && c->N >= 128;
+    if (xr) total += align_up((size_t)c->N / 2 * c->N * sizeof(double));
     MG_CUDA(cudaMalloc(&blk, total));
     MG_CUDA(cudaMemsetAsync(blk, 0, total, c->stream));
     char *p = (char *)blk;
@@ -277,6 +283,7 @@ static mg_status ensure_hierarchy(mg_ctx *c, bool fp64) {
         c->ebt = (int *)((char *)blk + ebt_off);
         c->xalt = (double *)((char *)blk + xalt_off);
     }
+    if (xr) c->xr64 = (double *)((char *)blk + xr_off);
     if (!fp64) {
         int bc = 0, br = 0;
         down_tma_box(2, &bc, &br);
@@ -407,7 +414,15 @@ static mg_status vcycle_rec(mg_ctx *c, int l, T *x, T *t, const T *b, bool zero)
     MG_TRY(vcycle_rec<T>(c, l + 1, xc, tc, bc, true));
     if (l == 0) probe_end(c, kProbeCoarse, coarse_bytes<T>(c, 1));
     if (l == 0) probe_begin(c, kProbeUp);
-    MG_CUDA(launch_up<T>(t, x, b, xc, n, c->nu2, c->taps, c->stream));
+    const T *xr = nullptr;
+    if constexpr (std::is_same<T, double>::value) {
+        // the x pass of the prolongation once for the level, not per tile
+        if (c->xr64 && fp64_separate_x_pass_mode()) {
+            MG_CUDA(launch_refine_rows(xc, c->xr64, n, c->taps, c->stream));
+            xr = c->xr64;
+        }
+    }
+    MG_CUDA(launch_up<T>(t, x, b, xc, n, c->nu2, c->taps, c->stream, nullptr, -1, nullptr, xr));
     if (l == 0) probe_end(c, kProbeUp, nn * (2 + (c->nu2 > 0 ? 1 : 0) + 0.25));
     return MG_OK;
 }
@@ -2304,6 +2319,17 @@ mg_status mg_set_coarse_cluster(int on) {
 }
 
 int mg_get_coarse_cluster(void) { return coarse_cluster_mode(); }
+
+mg_status mg_set_fp64_separate_x_pass(int on) {
+    if (on != 0 && on != 1) {
+        set_err("FP64 x pass: 0 (per tile) or 1 (once per level)");
+        return MG_ERR_INVALID_ARG;
+    }
+    set_fp64_separate_x_pass(on);
+    return MG_OK;
+}
+
+int mg_get_fp64_separate_x_pass(void) { return fp64_separate_x_pass_mode(); }
 
 mg_status mg_set_fused_update(int on) {
     if (on != 0 && on != 1) {

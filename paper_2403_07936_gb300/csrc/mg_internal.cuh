@@ -379,6 +379,10 @@ void set_coarse_cluster(int on);
 // (launch_update_residual_tasks) on a pair of FP64 iterates
 int fused_update_mode();
 void set_fused_update(int on);
+// 1: FP64 V-cycles refine each level's coarse error along x once
+// (launch_refine_rows) before k_up, instead of per tile
+int fp64_separate_x_pass_mode();
+void set_fp64_separate_x_pass(int on);
 // 2D tensor map of an n x n FP32 grid with boxes of cols x rows (false if the
 // driver's encoder is unavailable or rejects the map)
 bool make_grid_map_f32(CUtensorMap *m, void *base, int n, int cols, int rows);
@@ -399,7 +403,12 @@ cudaError_t launch_down(const T *x, T *xout, const T *b, int n, int nu, bool zer
 template <typename T>
 cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
                       const FirTaps &taps, cudaStream_t s, const T *extra = nullptr, int variant = -1,
-                      const int *extra_flag = nullptr);
+                      const int *extra_flag = nullptr, const T *xr = nullptr);
+// The prolongation's x pass on its own (FP64): xr[I][2J] = ec[I][J], xr[I][2J+1]
+// = the row pass's midpoint, for the (n/2) x (n/2) coarse error ec; xr is
+// (n/2) x n.  launch_up<double> with xr loads these rows instead of refining
+// them per tile (bit-identical).  n a power of two >= 128.
+cudaError_t launch_refine_rows(const double *ec, double *xr, int n, const FirTaps &taps, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bottom(T *x, const T *b, int n, int coarsest, int nu1, int nu2, bool zero_init,
                           const T *ainv, const FirTaps &taps, cudaStream_t s);

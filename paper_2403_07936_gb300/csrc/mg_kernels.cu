@@ -589,14 +589,19 @@ struct UpCfg {
     static constexpr int CCP = (CC + 15) / 16 * 16 + 4;
     static constexpr int U = cmax(2 * A, 2 * CRP * CCP);  // coarse tile, then b (after the row pass)
     static constexpr size_t smem = (2ull * A + U + (size_t)CR * FW) * sizeof(T);
+    // with pre-refined rows (no coarse tile): x, b, then the refined rows
+    static constexpr size_t smem_xr = (4ull * A + (size_t)CR * FW) * sizeof(T);
     static_assert(JW % NJ == 0 && IW % NJ == 0, "runs must tile the refined range");
 };
 
+// xr (optional, one-run tiles only): the coarse error already refined along x
+// by k_refine_rows, (n/2) x n; the tile then loads its refined rows instead of
+// running the row pass (the same values: the pass's arithmetic per midpoint).
 template <typename T, int NU, int TY_, int NJ_, int NT = kThreads, bool COH = false>
 __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__ xout,
                                         const T *__restrict__ b, const T *__restrict__ ec,
                                         const T *__restrict__ extra, int n, const FirTaps &taps, int ty0,
-                                        int tx0) {
+                                        int tx0, const T *__restrict__ xr = nullptr) {
     using Cfg = UpCfg<T, NU, TY_, NJ_>;
     constexpr int TY = Cfg::TY, TX = Cfg::TX, NJ = Cfg::NJ, H = Cfg::H, HX = Cfg::HX, R = Cfg::R,
                   C = Cfg::C, CK = Cfg::CK, A = Cfg::A, L = Cfg::L, JW = Cfg::JW, IW = Cfg::IW,
@@ -605,7 +610,9 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
     T *X = reinterpret_cast<T *>(smem_raw);  // red at X, black at X + A
     T *cs = X + 2 * A;                          // coarse tile [CR][CC] (row pass only)
     T *B = X + 2 * A;                           // b, loaded over cs after the row pass
-    T *rs = X + 2 * A + Cfg::U;                 // x-refined coarse rows [CR][FW]
+    constexpr bool kXR = NJ == 1 && std::is_same<T, double>::value;  // pre-refined rows accepted
+    const bool use_xr = kXR && xr != nullptr;
+    T *rs = X + 2 * A + (use_xr ? 2 * A : Cfg::U);  // x-refined coarse rows [CR][FW]
     const int nc = n >> 1;
 
     if constexpr (std::is_same<T, float>::value && NJ == 2) {
@@ -761,12 +768,26 @@ __device__ __forceinline__ void up_tile(const T *__restrict__ x, T *__restrict__
         return;
     }
     load_split<T, R, C>(X, X + A, x, n, ty0 - H, tx0 - HX);
-    load_tile<T, CR, CC, CC>(cs, ec, nc, ty0 / 2 - CHY, tx0 / 2 - CHX);
+    if constexpr (kXR) {
+        if (use_xr) {
+            // rs[cr][c] = xr[coarse row ty0 / 2 - CHY + cr][fine column tx0 - H + c]
+            using V = typename Prec<T>::vec;
+            constexpr int VW = Prec<T>::VW, FV = FW / VW;
+            static_assert(FW % VW == 0 && H % VW == 0, "refined rows load as whole vectors");
+            for (int idx = threadIdx.x; idx < CR * FV; idx += blockDim.x) {
+                const int cr = idx / FV, cv = idx - cr * FV;
+                const int gr = (ty0 / 2 - CHY + cr) & (nc - 1), gc = (tx0 - H + cv * VW) & (n - 1);
+                *reinterpret_cast<V *>(rs + cr * FW + cv * VW) =
+                    __ldg(reinterpret_cast<const V *>(xr + (size_t)gr * n + gc));
+            }
+        }
+    }
+    if (!use_xr) load_tile<T, CR, CC, CC>(cs, ec, nc, ty0 / 2 - CHY, tx0 / 2 - CHX);
     __syncthreads();
 
     // refine along x: coarse row cr, midpoints of J0..J0+NJ-1 (and the nodes)
     constexpr int NRUN = JW / NJ;
-    for (int item = threadIdx.x; item < CR * NRUN; item += blockDim.x) {
+    for (int item = threadIdx.x; item < (use_xr ? 0 : CR * NRUN); item += blockDim.x) {
         const int cr = item / NRUN, jr = item - cr * NRUN;
         const int J0 = -H / 2 + jr * NJ;
         const T *w = cs + cr * CC + CHX + J0;  // w[m] = e_c[J0 + m]
@@ -827,10 +848,38 @@ template <typename T, int NU, int TY, int NJ>
 __global__ void __launch_bounds__(kThreads) k_up(const T *__restrict__ x, T *__restrict__ xout,
                                                  const T *__restrict__ b, const T *__restrict__ ec,
                                                  const T *__restrict__ extra, const int *__restrict__ extra_flag,
-                                                 int n, FirTaps taps) {
+                                                 int n, FirTaps taps, const T *__restrict__ xr) {
     pdl_enter();
     const T *ex = (extra && (!extra_flag || *extra_flag)) ? extra : nullptr;
-    up_tile<T, NU, TY, NJ>(x, xout, b, ec, ex, n, taps, blockIdx.y * TY, blockIdx.x * kTX);
+    up_tile<T, NU, TY, NJ>(x, xout, b, ec, ex, n, taps, blockIdx.y * TY, blockIdx.x * kTX, xr);
+}
+
+// The x pass of the cubic prolongation on its own (FP64 V-cycles): xr[I][2J]
+// = ec[I][J] and xr[I][2J + 1] = the midpoint sum of k_up's row pass, for
+// every coarse row I once (inside k_up a tile refines its rows plus the
+// 2L - 1 halo rows its column pass reads, 3.75 times its own rows with the
+// FP64 filter's L = 28 taps on 32-row tiles).  Blocks of kRefineJ threads
+// take kRefineJ consecutive coarse columns of one row, staged with their
+// taps' halo in shared memory.
+constexpr int kRefineJ = 64;
+template <typename T>
+__global__ void __launch_bounds__(kRefineJ) k_refine_rows(const T *__restrict__ ec, T *__restrict__ xr, int n,
+                                                          FirTaps taps) {
+    pdl_enter();
+    constexpr int L = Prec<T>::L, W = kRefineJ + 2 * L - 1;
+    __shared__ T row[W];
+    const int nc = n >> 1, I = blockIdx.y, J0 = blockIdx.x * kRefineJ;
+    const T *er = ec + (size_t)I * nc;
+    for (int i = threadIdx.x; i < W; i += kRefineJ) row[i] = er[(J0 - L + 1 + i) & (nc - 1)];
+    __syncthreads();
+    const int j = threadIdx.x;
+    const T *w = row + j + L - 1;  // w[m] = ec[I][J0 + j + m]
+    T acc = T(0);
+#pragma unroll
+    for (int k = L; k >= 1; --k) acc += Prec<T>::tap(taps, k) * (w[k] + w[1 - k]);
+    T *out = xr + (size_t)I * n + 2 * (J0 + j);
+    out[0] = w[0];
+    out[1] = acc;
 }
 
 template <typename T, int NU, int TY, int NJ>
@@ -2175,16 +2224,18 @@ cudaError_t down_impl(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_
 
 template <typename T, int NU, int TY, int NJ>
 cudaError_t up_impl(const T *x, T *xout, const T *b, const T *ec, const T *extra, const int *eflag, int n,
-                    const FirTaps &taps, cudaStream_t s) {
+                    const FirTaps &taps, cudaStream_t s, const T *xr = nullptr) {
     using Cfg = UpCfg<T, NU, TY, NJ>;
     auto k = k_up<T, NU, TY, NJ>;
     static std::atomic<unsigned> done{0};
     cudaError_t e = set_smem_once(k, Cfg::smem, done);
     if (e != cudaSuccess) return e;
     dim3 grid(n / Cfg::TX, n / Cfg::TY);
+    // pre-refined rows need no coarse tile: less shared memory, more blocks per SM
+    const size_t smem = (NJ == 1 && std::is_same<T, double>::value && xr) ? Cfg::smem_xr : Cfg::smem;
     {
-        cudaError_t le_ = launch_kernel(k, grid, kThreads, Cfg::smem, s,
-                                        x, xout, b, ec, extra, eflag, n, taps);
+        cudaError_t le_ = launch_kernel(k, grid, kThreads, smem, s,
+                                        x, xout, b, ec, extra, eflag, n, taps, xr);
         if (le_ != cudaSuccess) return le_;
     }
     count_launches(1);
@@ -2207,9 +2258,10 @@ cudaError_t down_var(const T *x, T *xout, const T *b, int n, T *bc, cudaStream_t
 
 template <typename T, int NU>
 cudaError_t up_var(const T *x, T *xout, const T *b, const T *ec, const T *extra, const int *eflag, int n,
-                   const FirTaps &taps, cudaStream_t s, int variant) {
+                   const FirTaps &taps, cudaStream_t s, int variant, const T *xr) {
     if constexpr (std::is_same<T, double>::value) {
-        return up_impl<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>(x, xout, b, ec, extra, eflag, n, taps, s);
+        return up_impl<T, NU, Fixed64<double>::TY, Fixed64<double>::NJ>(x, xout, b, ec, extra, eflag, n, taps, s,
+                                                                        xr);
     } else {
 #define MG_UP_ROWS(TYV)                                                                                  \
     case TYV:                                                                                            \
@@ -2274,17 +2326,28 @@ cudaError_t launch_down_tma(const float *x, float *xout, const float *b, int n, 
 
 template <typename T>
 cudaError_t launch_up(const T *x, T *xout, const T *b, const T *ec, int n, int nu,
-                      const FirTaps &taps, cudaStream_t s, const T *extra, int variant, const int *extra_flag) {
+                      const FirTaps &taps, cudaStream_t s, const T *extra, int variant, const int *extra_flag,
+                      const T *xr) {
     if (n < 64 || !ec || x == xout || variant < -1 || variant >= kTileVariants) return cudaErrorInvalidValue;
+    if (xr && !std::is_same<T, double>::value) return cudaErrorInvalidValue;  // FP64 tiles only
     if (variant < 0) variant = tile_variant(1, n, nu);
     switch (nu) {
-        case 0: return up_var<T, 0>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
-        case 1: return up_var<T, 1>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
-        case 2: return up_var<T, 2>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
-        case 3: return up_var<T, 3>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
-        case 4: return up_var<T, 4>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant);
+        case 0: return up_var<T, 0>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant, xr);
+        case 1: return up_var<T, 1>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant, xr);
+        case 2: return up_var<T, 2>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant, xr);
+        case 3: return up_var<T, 3>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant, xr);
+        case 4: return up_var<T, 4>(x, xout, b, ec, extra, extra_flag, n, taps, s, variant, xr);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_refine_rows(const double *ec, double *xr, int n, const FirTaps &taps, cudaStream_t s) {
+    if (n < 2 * kRefineJ || (n & (n - 1)) || !ec || !xr) return cudaErrorInvalidValue;
+    const cudaError_t e =
+        launch_kernel(k_refine_rows<double>, dim3((n / 2) / kRefineJ, n / 2), kRefineJ, 0, s, ec, xr, n, taps);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -2332,9 +2395,11 @@ template cudaError_t launch_down<float>(const float *, float *, const float *, i
 template cudaError_t launch_down<double>(const double *, double *, const double *, int, int, bool,
                                          double *, cudaStream_t, int);
 template cudaError_t launch_up<float>(const float *, float *, const float *, const float *, int, int,
-                                      const FirTaps &, cudaStream_t, const float *, int, const int *);
+                                      const FirTaps &, cudaStream_t, const float *, int, const int *,
+                                      const float *);
 template cudaError_t launch_up<double>(const double *, double *, const double *, const double *, int,
-                                       int, const FirTaps &, cudaStream_t, const double *, int, const int *);
+                                       int, const FirTaps &, cudaStream_t, const double *, int, const int *,
+                                       const double *);
 template cudaError_t launch_bottom<float>(float *, const float *, int, int, int, int, bool, const float *,
                                           const FirTaps &, cudaStream_t);
 template cudaError_t launch_bottom<double>(double *, const double *, int, int, int, int, bool,

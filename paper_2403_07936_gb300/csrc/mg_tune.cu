@@ -114,6 +114,17 @@ void set_coarse_cluster(int on) {
 }
 
 namespace {
+std::atomic<int> g_fp64_x_pass{1};
+}
+
+int fp64_separate_x_pass_mode() { return g_fp64_x_pass.load(std::memory_order_relaxed); }
+
+void set_fp64_separate_x_pass(int on) {
+    const int old = g_fp64_x_pass.exchange(on ? 1 : 0);
+    if (old != (on ? 1 : 0)) g_epoch.fetch_add(1);
+}
+
+namespace {
 std::atomic<int> g_fused_update{1};
 }
 

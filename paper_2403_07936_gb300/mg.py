@@ -81,6 +81,8 @@ SIGNATURES = {
     "mg_get_coarse_cluster": (_I, []),
     "mg_set_fused_update": (_I, [_I]),
     "mg_get_fused_update": (_I, []),
+    "mg_set_fp64_separate_x_pass": (_I, [_I]),
+    "mg_get_fp64_separate_x_pass": (_I, []),
     "mg_get_tma_tiles": (_I, []),
     "mg_trainer_get_tensor_cores": (_I, [_VP, C.POINTER(_I)]),
     "mg_trainer_get_weights": (_I, [_VP, _VP, _SZ]),
@@ -363,6 +365,15 @@ def set_fused_update(on: bool):
 
 def get_fused_update() -> bool:
     return bool(load().mg_get_fused_update())
+
+
+def set_fp64_separate_x_pass(on: bool):
+    """FP64 V-cycles: refine each level's coarse error along x once (True) or inside every up-pass tile."""
+    _check(load().mg_set_fp64_separate_x_pass(int(bool(on))))
+
+
+def get_fp64_separate_x_pass() -> bool:
+    return bool(load().mg_get_fp64_separate_x_pass())
 
 
 def set_tma_tiles(on: bool):
