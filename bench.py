@@ -378,7 +378,7 @@ SR_TENSOR_FLOP_PER_COARSE_PX = 2 * 64 * 576 * (16 + 4)  # 16 convs 64->64 and co
 
 
 def _levels(n, coarsest=8):
-    return int(round(np.log2(n // coarsest))) + 1
+    return (n // coarsest).bit_length()  # log2(n / coarsest) + 1 for powers of two
 
 
 def _events_time(stream, fn, reps):

@@ -818,6 +818,9 @@ struct BatchPlan {
     int *d_bm = nullptr;   // [0] next step's V-cycles, [1] V-cycles run (adaptive)
     int h_bm[2] = {0, 0};
     unsigned epoch = 0;
+    // every right-hand side's outer step fuses the update with the next
+    // residual on its context's iterate pair (x, xalt)
+    bool fused = false;
     BatchRed red(int g) const { return BatchRed{d_partials, d_counters, d_out + (size_t)g * B * kMaxSlots}; }
     double *out(int g) const { return d_out + (size_t)g * B * kMaxSlots; }
 };
@@ -856,6 +859,10 @@ static mg_status batch_build(BatchPlan *p) {
         maxN = n > maxN ? n : maxN;
     }
     p->rhs_blocks = blk;
+    p->fused = fused_update_mode() != 0;
+    for (int r = 0; r < B; ++r) p->fused = p->fused && rhs[r].n >= kResMinN && p->ctxs[r]->xalt;
+    if (p->fused)
+        for (int r = 0; r < B; ++r) rhs[r].xalt = p->ctxs[r]->xalt;
     // SR groups: right-hand sides of one fine size whose coarse grid the
     // generator takes (>= 128, a multiple of 128); smaller ones stay cubic
     std::vector<int> sr_group(B, -1), sr_index(B, -1);
@@ -1071,13 +1078,21 @@ static mg_status batch_build(BatchPlan *p) {
         } else {
             for (int k = 0; k < step; ++k) run_cycle(k == 0 ? 0 : 1);
         }
-        if (e == cudaSuccess) e = launch_update_batched(p->d_rhs, B, blk, p->d_active, p->red(kGrpU), s);
+        if (p->fused) {
+            // each right-hand side's step count is read before k_check_b advances it
+            if (e == cudaSuccess)
+                e = launch_update_residual_batched(p->d_rhs, B, blk, p->d_state, p->d_active, p->red(kGrpR), s);
+        } else {
+            if (e == cudaSuccess) e = launch_update_batched(p->d_rhs, B, blk, p->d_active, p->red(kGrpU), s);
+            if (e == cudaSuccess)
+                e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), false, false, p->d_active,
+                                                  p->red(kGrpR), s);
+        }
+        // (the fused form leaves each sum of e^2 beside its residual's)
         if (e == cudaSuccess)
-            e = launch_outer_residual_batched(p->d_rhs, B, blk, p->out(kGrpF), false, false, p->d_active,
-                                              p->red(kGrpR), s);
-        if (e == cudaSuccess)
-            e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR), p->out(kGrpU), p->out(kGrpF), p->tol,
-                                     step, c0->max_cycles, false, p->d_active, handle, true, s, rho, ifh, p->d_bm);
+            e = launch_check_batched(p->d_state, p->d_rhs, B, p->out(kGrpR),
+                                     p->fused ? p->out(kGrpR) + 1 : p->out(kGrpU), p->out(kGrpF), p->tol, step,
+                                     c0->max_cycles, false, p->d_active, handle, true, s, rho, ifh, p->d_bm);
         if (e != cudaSuccess) break;
         e = cudaStreamEndCapture(s, &body);
         capturing = false;
@@ -1087,8 +1102,9 @@ static mg_status batch_build(BatchPlan *p) {
         e = cudaStreamBeginCaptureToGraph(s, p->graph, &cond, nullptr, 1, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) break;
         capturing = true;
-        e = launch_sum_batched(p->d_rhs, B, blk, true, p->red(kGrpX), s);
-        if (e == cudaSuccess) e = launch_project_batched(p->d_rhs, B, blk, p->out(kGrpX), p->d_state, s);
+        e = launch_sum_batched(p->d_rhs, B, blk, true, p->red(kGrpX), s, p->fused ? p->d_state : nullptr);
+        if (e == cudaSuccess)
+            e = launch_project_batched(p->d_rhs, B, blk, p->out(kGrpX), p->d_state, s, p->fused);
         if (e != cudaSuccess) break;
         e = cudaStreamEndCapture(s, &p->graph);
         capturing = false;

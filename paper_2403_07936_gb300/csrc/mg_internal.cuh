@@ -320,6 +320,9 @@ struct RhsDesc {  // outer kernels: blocks [blk0, blk0 + nblk) serve this right-
     int m_prev;      // V-cycles it ran in the previous outer step (0: the launch's common count)
     double h2;
     int sr = 0;      // its finest transition adds the SR correction (batched SR solves)
+    // the second FP64 iterate of a batch whose outer steps fuse the update with
+    // the next residual (launch_update_residual_batched); null otherwise
+    double *xalt = nullptr;
 };
 struct BatchRed {
     double *partials;   // [blocks][kMaxSlots]
@@ -517,8 +520,10 @@ cudaError_t launch_up_batched(const TileGrid *tab, int ngrid, int nblocks, int n
 cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int nu2, const int *active,
                                   const FirTaps &taps, cudaStream_t s);
 // sums of f (of_x = false) or of x (of_x = true) per right-hand side -> red.out[r][0]
+// of_x with st: each right-hand side's x is read from its xalt when its slot's
+// outer-step count is odd (a batch with the fused outer step)
 cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of_x, BatchRed red,
-                               cudaStream_t s);
+                               cudaStream_t s, const DevState *st = nullptr);
 // want_fnorm: the right-hand sides at their first residual (all with
 // first_all, else those whose descriptor says first) compute b = h^2 (f - mu)
 // in FP64, store it to bsc and sum (f - mu)^2; all others load b from bsc.
@@ -527,8 +532,17 @@ cudaError_t launch_outer_residual_batched(const RhsDesc *rd, int nrhs, int nbloc
                                           cudaStream_t s);
 cudaError_t launch_update_batched(const RhsDesc *rd, int nrhs, int nblocks, const int *active, BatchRed red,
                                   cudaStream_t s);
+// fused: each right-hand side's last iterate is in its xalt when its slot's
+// outer-step count is odd (the projection writes x)
 cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *xsum,
-                                   const DevState *st, cudaStream_t s);
+                                   const DevState *st, cudaStream_t s, bool fused = false);
+// Batched launch_update_residual_tasks: every active right-hand side (n >=
+// kResMinN, xalt set) takes x + e from one buffer of (x, xalt) to the other,
+// by its slot's outer-step count (st[slot].outer, read before the check
+// advances it), and its residual; out[slot][0] = the residual's sum of
+// squares, out[slot][1] = that of e.
+cudaError_t launch_update_residual_batched(const RhsDesc *rd, int nrhs, int nblocks, const DevState *st,
+                                           const int *active, BatchRed red, cudaStream_t s);
 // first: every entry is at its first residual (else each entry's own flag);
 // use_handle: set the graph loop condition (inside a graph only)
 // rho > 0: adaptive inner cycles (batch_m: [0] the next step's V-cycles, [1] total run; ifh: IF handles)

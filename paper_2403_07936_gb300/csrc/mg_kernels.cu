@@ -1978,14 +1978,21 @@ __device__ __forceinline__ void batch_finish(const BatchRed &red, int slot, int 
     if (threadIdx.x == 0) red.counters[rhs] = 0u;
 }
 
+// The x of a right-hand side of a batch with the fused outer step: its xalt
+// after an odd number of outer steps (st non-null), else x.
+__device__ __forceinline__ const double *batch_x(const RhsDesc &d, const DevState *st) {
+    return (st && d.xalt && (st[d.slot].outer & 1)) ? d.xalt : d.x;
+}
+
 template <bool OF_X>
-__global__ void __launch_bounds__(kRedThreads) k_sum_b(const RhsDesc *__restrict__ rd, int nrhs, BatchRed red) {
+__global__ void __launch_bounds__(kRedThreads) k_sum_b(const RhsDesc *__restrict__ rd, int nrhs, BatchRed red,
+                                                       const DevState *__restrict__ st) {
     pdl_enter();
     __shared__ double sh[32];
     const int r = find_rhs(rd, nrhs);
     const RhsDesc d = rd[r];
     const size_t N = (size_t)d.n * d.n;
-    const double *a = OF_X ? d.x : d.f;
+    const double *a = OF_X ? batch_x(d, st) : d.f;
     double v = 0.0;
     for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x)
         v += a[p];
@@ -2079,14 +2086,40 @@ __global__ void __launch_bounds__(kRedThreads) k_update_b(const RhsDesc *__restr
 
 __global__ void __launch_bounds__(kRedThreads) k_project_b(const RhsDesc *__restrict__ rd, int nrhs,
                                                            const double *__restrict__ xsum,
-                                                           const DevState *__restrict__ st) {
+                                                           const DevState *__restrict__ st, int fused) {
     pdl_enter();
     const RhsDesc d = rd[find_rhs(rd, nrhs)];
     const size_t N = (size_t)d.n * d.n;
     const bool zero = st[d.slot].zero_source != 0;
     const double mu = xsum[(size_t)d.slot * kMaxSlots] / (double)N;
+    const double *src = batch_x(d, fused ? st : nullptr);
     for (size_t p = (size_t)(blockIdx.x - d.blk0) * blockDim.x + threadIdx.x; p < N; p += (size_t)d.nblk * blockDim.x)
-        d.x[p] = zero ? 0.0 : d.x[p] - mu;
+        d.x[p] = zero ? 0.0 : src[p] - mu;
+}
+
+// Batched k_update_residual_t: one right-hand side's blocks take its tasks;
+// the slot's outer-step count selects the source of (x, xalt).
+__global__ void __launch_bounds__(kRedThreads, 3) k_update_residual_b(const RhsDesc *__restrict__ rd, int nrhs,
+                                                                      const DevState *__restrict__ st,
+                                                                      const int *__restrict__ active, BatchRed red) {
+    pdl_enter();
+    __shared__ double sh[32];
+    const RhsDesc d = rd[find_rhs(rd, nrhs)];
+    if (active && !active[d.slot]) return;
+    const int step = st[d.slot].outer;
+    const double *__restrict__ x = (step & 1) ? d.xalt : d.x;
+    double *__restrict__ xo = (step & 1) ? d.x : d.xalt;
+    const int n = d.n, lg = __ffs(n) - 1, wpb = blockDim.x >> 5;
+    const int ntask = (n >> 5) * (n / kResRows);
+    long long *bint = reinterpret_cast<long long *>(d.bsc);
+    SqSum ss, ee;
+    double ff = 0.0;
+    for (int t = (blockIdx.x - d.blk0) * wpb + (int)(threadIdx.x >> 5); t < ntask; t += d.nblk * wpb)
+        residual_task<false, true>(t, n, lg, nullptr, 0.0, d.h2, bint, d.ebt, x, d.s32, ss, ff, d.e, xo, &ee);
+    double vals[2];
+    vals[0] = block_sum(ss.value(), sh);
+    vals[1] = block_sum(ee.value(), sh);
+    batch_finish<2>(red, d.slot, d.blk0, d.nblk, vals, sh);
 }
 
 // Convergence test of every listed right-hand side still active (or at its
@@ -2660,17 +2693,18 @@ cudaError_t launch_bottom_batched(const BottomGrid *tab, int ngrid, int nu1, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of_x, BatchRed red, cudaStream_t s) {
+cudaError_t launch_sum_batched(const RhsDesc *rd, int nrhs, int nblocks, bool of_x, BatchRed red, cudaStream_t s,
+                               const DevState *st) {
     if (of_x)
         {
             cudaError_t le_ = launch_kernel(k_sum_b<true>, nblocks, kRedThreads, 0, s,
-                                            rd, nrhs, red);
+                                            rd, nrhs, red, st);
             if (le_ != cudaSuccess) return le_;
         }
     else
         {
             cudaError_t le_ = launch_kernel(k_sum_b<false>, nblocks, kRedThreads, 0, s,
-                                            rd, nrhs, red);
+                                            rd, nrhs, red, (const DevState *)nullptr);
             if (le_ != cudaSuccess) return le_;
         }
     count_launches(1);
@@ -2709,12 +2743,21 @@ cudaError_t launch_update_batched(const RhsDesc *rd, int nrhs, int nblocks, cons
 }
 
 cudaError_t launch_project_batched(const RhsDesc *rd, int nrhs, int nblocks, const double *xsum,
-                                   const DevState *st, cudaStream_t s) {
+                                   const DevState *st, cudaStream_t s, bool fused) {
     {
         cudaError_t le_ = launch_kernel(k_project_b, nblocks, kRedThreads, 0, s,
-                                        rd, nrhs, xsum, st);
+                                        rd, nrhs, xsum, st, fused ? 1 : 0);
         if (le_ != cudaSuccess) return le_;
     }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_residual_batched(const RhsDesc *rd, int nrhs, int nblocks, const DevState *st,
+                                           const int *active, BatchRed red, cudaStream_t s) {
+    if (!st) return cudaErrorInvalidValue;
+    const cudaError_t e = launch_kernel(k_update_residual_b, nblocks, kRedThreads, 0, s, rd, nrhs, st, active, red);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }

@@ -193,3 +193,40 @@ def test_cold_start_never_reads_x(mg, graphs, fused, host):
     finally:
         ctx.set_zero_guess(False)
         mg.set_fused_update(mode)
+
+
+def test_batched_fused_update_gives_the_bits_of_separate_launches(mg):
+    """The batched graph's fused outer step: each member alternates its own
+    iterate pair by its own outer-step count (members here end after
+    different numbers of outer steps, one warm-started near its solution), and
+    the projection reads each member's last buffer; the bits are those of the
+    separate update and residual launches."""
+    sizes = [256, 512, 64, 1024, 256]
+    fs = [turbulent_source(n, default_kmax(n), config_seed(3, 200 + i)) for i, n in enumerate(sizes)]
+    fts = [torch.tensor(f, device=DEV) for f in fs]
+    warm = {}
+    for i, tol in ((1, 1e-11), (4, 1e-6)):  # converged (no outer step), and part way
+        ci = mg.Context(_levels(sizes[i]), sizes[i])
+        w = torch.zeros_like(fts[i])
+        ci.solve(fts[i], w, tol=tol)
+        warm[i] = w
+    mode = mg.get_fused_update()
+    out = {}
+    try:
+        for on in (False, True):
+            mg.set_fused_update(on)
+            ctxs = [mg.Context(_levels(n), n) for n in sizes]
+            xs = [warm[i].clone() if i in warm else torch.zeros_like(ft) for i, ft in enumerate(fts)]
+            infos = mg.solve_batched(ctxs, fts, xs, tol=1e-10)
+            torch.cuda.synchronize()
+            out[on] = ([x.cpu().numpy() for x in xs], infos)
+    finally:
+        mg.set_fused_update(mode)
+    (x0, i0), (x1, i1) = out[False], out[True]
+    for k in range(len(sizes)):
+        for key in ("vcycles", "outer_iters", "rel_residual"):
+            assert i0[k][key] == i1[k][key], (k, key)
+        assert np.array_equal(x0[k], x1[k]), k
+        xe = omg.exact_solve_fft(fs[k] - fs[k].mean())
+        assert np.abs(x1[k] - xe).max() <= 1e-9 * np.abs(xe).max()
+    assert len({i["outer_iters"] % 2 for i in i1}) == 2  # both buffers of a pair hold a result
