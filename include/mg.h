@@ -325,7 +325,8 @@ int mg_get_coarse_cluster(void);
 
 /* Launch form of a mixed solve's outer step (FP64 defect correction: x += e,
  * then r = f - A x for the convergence test and the next step; grids of
- * N >= 32).  on = 1 (the default): the update and the next residual run as
+ * N >= 32; mixed precision is this library's design, the paper has no
+ * counterpart).  on = 1 (the default): the update and the next residual run as
  * one launch that reads x and e once, writes x + e into the other buffer of a
  * pair (the caller's x and a context buffer, alternating each outer step) and
  * forms the residual of x + e from the same loads; the solve's projection
